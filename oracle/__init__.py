@@ -1,0 +1,192 @@
+"""CPU oracle for the vector-valued Allen-Cahn segmentation step.
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, by the smoke check and by
+the benchmark's CPU-baseline leg, never by the product path. The arithmetic
+lives in ``ac_oracle.c`` (plain sequential FP64 C); this module compiles it
+with gcc and marshals numpy arrays through ctypes.
+
+Every function follows a passage of Kay & Tomasi: the P1 matrices (Sec. 3.1),
+projection by simplex (Sec. 4.2), colour means and fitting terms (Eq.
+VV_fidelity, Sec. 4.4), the step problem (Sec. 3.2, Eq. alpha), the Gibbs
+clamp-and-redistribute loop (Sec. 3.3), SSC over all levels (Sec. 3.2) and the
+rounded composite (Sec. 4.3).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ac_oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "libac_oracle.so")
+ROW = 7
+
+_dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_bp = np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle library in-tree (gcc -O2, portable flags only)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        i, i64, d = C.c_int, C.c_int64, C.c_double
+        L.or_assemble.argtypes = [i, i, _dp, _ip, _dp, _ip]
+        L.or_moments.argtypes = [i, i, _dp, _dp]
+        L.or_means.argtypes = [i, i, i, _dp, _dp, C.c_void_p, _dp, C.c_void_p]
+        L.or_rhs.argtypes = [i, i, i, _dp, _dp, _dp, d, d, d, _dp]
+        L.or_energy.argtypes = [i, i, i, _dp, _dp, d, d]
+        L.or_energy.restype = d
+        L.or_project_simplex_batch.argtypes = [i, i64, _dp, _dp, _ip]
+        L.or_natural_residual.argtypes = [i, i, i, _dp, _dp, d, d]
+        L.or_natural_residual.restype = d
+        L.or_num_levels.argtypes = [i, i, i]
+        ip = C.POINTER(C.c_int)
+        dpp = C.POINTER(C.c_double)
+        L.or_ssc_solve.argtypes = [i, i, i, _dp, _dp, d, d, d, i, i, i, i, ip, dpp]
+        L.or_pgs_solve.argtypes = [i, i, i, _dp, _dp, d, d, d, i, ip, dpp]
+        L.or_step.argtypes = [i, i, i, _dp, _dp, _dp, d, d, d, d, i, i, i, i, i, ip, dpp]
+        L.or_labels.argtypes = [i, i, i, _dp, _bp, _bp]
+        _lib = L
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def n_nodes(W, H):
+    return (W + 1) * (H + 1)
+
+
+def assemble(W: int, H: int):
+    """Lumped mass Mhat (n,) and stiffness A as a dense-row list: returns
+    (mhat, cols (n,7), vals (n,7), cnt (n,)) assembled triangle by triangle."""
+    n = n_nodes(W, H)
+    mhat = np.zeros(n)
+    col = np.zeros((n, ROW), np.int32)
+    val = np.zeros((n, ROW))
+    cnt = np.zeros(n, np.int32)
+    if lib().or_assemble(W, H, mhat, col, val, cnt):
+        raise ValueError("or_assemble failed")
+    return mhat, col, val, cnt
+
+
+def moments(img: np.ndarray) -> np.ndarray:
+    """Projection by simplex: (n, 5) array of m0, m1 (RGB), m2 per node."""
+    H, W, _ = img.shape
+    m = np.zeros((n_nodes(W, H), 5))
+    lib().or_moments(W, H, _f64(img), m)
+    return m
+
+
+def means(u: np.ndarray, m: np.ndarray, W: int, H: int, c_prev=None):
+    """Colour means c (N, 3) and masses (N,) of phase field u (n, N)."""
+    N = u.shape[1]
+    c = np.zeros((N, 3))
+    mass = np.zeros(N)
+    cp = None if c_prev is None else _f64(c_prev)
+    lib().or_means(W, H, N, _f64(u), _f64(m), None if cp is None else cp.ctypes.data, c, mass.ctypes.data)
+    return c, mass
+
+
+def rhs(ut, m, c, W, H, eps, lam, tau):
+    N = ut.shape[1]
+    b = np.zeros_like(_f64(ut))
+    lib().or_rhs(W, H, N, _f64(ut), _f64(m), _f64(c), eps, lam, tau, b)
+    return b
+
+
+def energy(u, m, W, H, eps, lam) -> float:
+    return lib().or_energy(W, H, u.shape[1], _f64(u), _f64(m), eps, lam)
+
+
+def project_simplex(y: np.ndarray):
+    """Paper's clamp-and-redistribute projection of each row of y (k, N).
+    Returns (x, passes)."""
+    y = _f64(np.atleast_2d(y))
+    x = np.zeros_like(y)
+    passes = np.zeros(y.shape[0], np.int32)
+    lib().or_project_simplex_batch(y.shape[1], y.shape[0], y, x, passes)
+    return x, passes
+
+
+def natural_residual(u, b, W, H, eps, tau) -> float:
+    return lib().or_natural_residual(W, H, u.shape[1], _f64(u), _f64(b), eps, tau)
+
+
+def num_levels(W, H, coarse_min=4) -> int:
+    return lib().or_num_levels(W, H, coarse_min)
+
+
+def ssc_solve(u0, b, W, H, eps, tau, tol=1e-13, max_iter=500, nu1=1, nu2=1, coarse_min=4):
+    """Successive subspace correction over all levels. Returns (u, iters, rho, status)."""
+    u = _f64(u0).copy()
+    it, rho = C.c_int(0), C.c_double(0)
+    st = lib().or_ssc_solve(W, H, u.shape[1], u, _f64(b), eps, tau, tol, max_iter, nu1, nu2, coarse_min,
+                            C.byref(it), C.byref(rho))
+    if st < 0:
+        raise ValueError("or_ssc_solve: bad arguments")
+    return u, it.value, rho.value, st
+
+
+def pgs_solve(u0, b, W, H, eps, tau, tol=1e-13, max_sweeps=100000):
+    """Plain lexicographic projected Gauss-Seidel. Returns (u, sweeps, rho, status)."""
+    u = _f64(u0).copy()
+    it, rho = C.c_int(0), C.c_double(0)
+    st = lib().or_pgs_solve(W, H, u.shape[1], u, _f64(b), eps, tau, tol, max_sweeps, C.byref(it), C.byref(rho))
+    if st < 0:
+        raise ValueError("or_pgs_solve: bad arguments")
+    return u, it.value, rho.value, st
+
+
+def step(u, m, c, W, H, eps, lam, tau, tol=1e-13, method="ssc", max_iter=500, nu1=1, nu2=1, coarse_min=4):
+    """One time step. Returns (u_next, c_t, iters, rho, status); c is the
+    previous means (used for empty phases) and is not modified."""
+    u = _f64(u).copy()
+    c = _f64(c).copy()
+    it, rho = C.c_int(0), C.c_double(0)
+    meth = {"ssc": 0, "pgs": 1}[method]
+    st = lib().or_step(W, H, u.shape[1], u, _f64(m), c, eps, lam, tau, tol, meth, max_iter, nu1, nu2, coarse_min,
+                       C.byref(it), C.byref(rho))
+    if st < 0:
+        raise ValueError("or_step: bad arguments")
+    return u, c, it.value, rho.value, st
+
+
+def labels(u, W, H):
+    """Rounded composite: (node labels (H+1, W+1), pixel labels (H, W)), int8."""
+    nl = np.zeros(n_nodes(W, H), np.int8)
+    pl = np.zeros(W * H, np.int8)
+    lib().or_labels(W, H, u.shape[1], _f64(u), nl, pl)
+    return nl.reshape(H + 1, W + 1), pl.reshape(H, W)
+
+
+def run(img, u0, eps, lam, tau, steps, tol=1e-13, method="ssc", **kw):
+    """T steps from u0 on img. Returns (u_T, c_last, per-step stats list)."""
+    H, W, _ = img.shape
+    m = moments(img)
+    u = _f64(u0)
+    c = np.zeros((u.shape[1], 3))
+    stats = []
+    for _ in range(steps):
+        u, c, it, rho, st = step(u, m, c, W, H, eps, lam, tau, tol=tol, method=method, **kw)
+        stats.append((it, rho, st))
+    return u, c, stats
