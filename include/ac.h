@@ -1,0 +1,155 @@
+/*
+ * ac.h -- C ABI of libac, the GB300 (sm_103a) solver for the time steps of
+ * the vector-valued Allen-Cahn colour segmentation of Kay & Tomasi
+ * ("Colour Image Segmentation by the Vector-valued Allen-Cahn Phase-field
+ * Model: a Multigrid Solution").
+ *
+ * Problem (Sec. 2.3, Eq. E and Eq. VV_fidelity with the RGB fitting of
+ * Sec. 4.4): an N-phase field u on the P1 finite-element space of the pixel
+ * grid (nodes at pixel corners, every pixel split along its
+ * (x,y)-(x+1,y+1) diagonal, Sec. 3.1), held on the Gibbs simplex at every
+ * node (Eq. Gibbs_simplex).  One time step (Sec. 3.2, Eq. alpha; stiffness
+ * taken with the sign that makes the step matrix positive definite):
+ *     c_i     = int u_i I / int u_i                       (colour means)
+ *     b_n,i   = Mhat_n u_n,i (1 + 2 tau/eps) - tau lambda int eta_n |I - c_i|^2
+ *     u^{t+1} = argmin over the simplices of sum_i 1/2 u_i'(Mhat + tau eps A) u_i - b_i'u_i
+ * solved to a natural residual max_n |u_n - P_G(y_n(u))| <= tol by a
+ * truncated monotone multigrid V(nu1,nu2) cycle whose smoother is the
+ * projected block Gauss-Seidel of Sec. 3.1 / Sec. 3.3 in red-black order.
+ *
+ * Layouts.  Image: H x W x 3 (row y, column x, RGB), values in [0, 1].
+ * Phase field: (H+1)(W+1) nodes x N phases, node index n = y*(W+1) + x,
+ * phase innermost (u[n*N + i]), FP64 at the ABI.  Labels: int8.
+ * eps and tau are in pixel units (pixel side 1, Sec. 4.1).
+ *
+ * Ownership.  The context owns all device memory it allocates (in
+ * ac_create).  Caller buffers are only read or written during the call.
+ * "is_device" = 1 means the pointer is CUDA device memory of the current
+ * device, 0 means host memory.  All work is ordered on params.stream (a
+ * cudaStream_t; NULL = the legacy default stream).  Calls that return data
+ * to host memory synchronise that stream.
+ *
+ * Errors.  Every int-returning call returns AC_OK (0) or a negative AC_ERR_*
+ * code and never throws; ac_last_error() describes the last failure of the
+ * calling thread.  A context that saw AC_ERR_CUDA should be destroyed.
+ */
+#ifndef AC_H
+#define AC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  AC_OK = 0,
+  AC_ERR_ARG = -1,           /* invalid argument or size */
+  AC_ERR_CUDA = -2,          /* a CUDA runtime call or kernel launch failed */
+  AC_ERR_NOT_CONVERGED = -3, /* a step reached max_cycles with residual > tol (the state is still feasible) */
+  AC_ERR_NUMERIC = -4,       /* NaN/Inf found in the residual */
+  AC_ERR_STATE = -5,         /* call out of order (e.g. ac_step before ac_set_image) */
+  AC_ERR_NOMEM = -6          /* device allocation failed */
+};
+
+enum { AC_FP64 = 0, AC_MIXED = 1 };
+
+#define AC_MAX_PHASES 8
+
+typedef struct ac_ctx ac_ctx;
+
+typedef struct {
+  int width, height;   /* image size W x H in pixels (>= 1 each) */
+  int n_phases;        /* N, 2 <= N <= AC_MAX_PHASES */
+  double eps;          /* interface width epsilon (pixels), > 0 */
+  double lambda;       /* fitting weight lambda, >= 0 */
+  double tau;          /* time step delta t, > 0 */
+  double tol;          /* natural-residual tolerance of each step, > 0 */
+  int nu1, nu2;        /* pre/post projected smoothing sweeps of the V-cycle, >= 0, nu1+nu2 >= 1 */
+  int max_cycles;      /* V-cycle cap per step, >= 1 */
+  int coarse_min;      /* coarsen while both cell counts are even and min/2 >= coarse_min (>= 1) */
+  int precision;       /* AC_FP64 or AC_MIXED */
+  uint64_t seed;       /* seed of the random simplex initialisation in ac_set_image */
+  void *stream;        /* cudaStream_t for all work of this context */
+} ac_params;
+
+typedef struct {
+  double energy;       /* discrete Eq. (E) at u^t of the last step, with c = c(u^t) */
+  double residual;     /* natural residual at the end of the last step */
+  int cycles;          /* V-cycles used by the last step */
+  int total_cycles;    /* V-cycles over all steps of the call */
+  int steps;           /* time steps done by the call */
+  int converged;       /* 1 if every step of the call reached tol */
+} ac_stats;
+
+/* Defaults: tol 1e-10, nu1 = nu2 = 2, max_cycles 200, coarse_min 4, AC_FP64,
+ * seed 0, stream NULL; size, N, eps, lambda and tau are left 0. */
+int ac_default_params(ac_params *p);
+
+/* Validate p and allocate every device buffer of the solver for a W x H image
+ * with N phases: the phase field, right-hand side, image moments and the
+ * multigrid hierarchy (levels as described for coarse_min).  *out receives
+ * the context.  AC_ERR_ARG for invalid parameters, AC_ERR_NOMEM if device
+ * memory runs out. */
+int ac_create(ac_ctx **out, const ac_params *p);
+
+/* Copy an RGB image in (H x W x 3 float32, values in [0,1]), compute the
+ * per-node image moments m0 = <eta_n,1>, m1 = <eta_n,I>, m2 = <eta_n,|I|^2>
+ * ("projection by simplex", Sec. 4.2; exact for a pixelwise-constant image)
+ * and reset u to a seeded random point of the simplex at every node. */
+int ac_set_image(ac_ctx *ctx, const float *rgb, int is_device);
+/* The same with an FP64 image (used for parity with the FP64 oracle). */
+int ac_set_image_f64(ac_ctx *ctx, const double *rgb, int is_device);
+
+/* Advance n_steps >= 0 time steps (Sec. 3.2).  out (nullable) receives the
+ * statistics of the call.  Returns AC_ERR_NOT_CONVERGED if some step hit
+ * max_cycles (all steps are still taken), AC_ERR_NUMERIC on NaN/Inf. */
+int ac_step(ac_ctx *ctx, int n_steps, ac_stats *out);
+
+/* ac_step(n_steps), then write the rounded composite (Sec. 4.3): the pixel
+ * label (H x W int8) is the phase with the largest integral over the pixel,
+ * lowest phase index on ties.  Same return codes as ac_step. */
+int ac_segment(ac_ctx *ctx, int n_steps, int8_t *pixel_labels, int is_device, ac_stats *out);
+
+/* Free every resource of the context (NULL is accepted). */
+void ac_destroy(ac_ctx *ctx);
+
+/* ---- state access (tests, checkpoint/resume, adjoint) ------------------ */
+
+/* Replace u ((H+1)(W+1) x N FP64).  Each node must lie on the simplex; the
+ * values are used as given.  The colour means of the previous step (used for
+ * phases of zero mass) are reset to 0. */
+int ac_set_phase(ac_ctx *ctx, const double *u, int is_device);
+/* Copy u out ((H+1)(W+1) x N FP64). */
+int ac_get_phase(ac_ctx *ctx, double *u, int is_device);
+/* Colour means c (N x 3 FP64, host) used by the last step. */
+int ac_get_means(ac_ctx *ctx, double *c);
+/* Image moments ((H+1)(W+1) x 5 FP64, host): m0, m1 (RGB), m2. */
+int ac_get_moments(ac_ctx *ctx, double *m);
+/* Right-hand side b ((H+1)(W+1) x N FP64, host) of the last step. */
+int ac_get_rhs(ac_ctx *ctx, double *b);
+/* Node labels ((H+1)(W+1) int8): argmax of u_n, lowest index on ties. */
+int ac_get_node_labels(ac_ctx *ctx, int8_t *labels, int is_device);
+/* Discrete energy Eq. (E) of the current u with c = c(u) (host double). */
+int ac_energy(ac_ctx *ctx, double *energy);
+/* Natural residual max_n |u_n - P_G(y_n(u))| of the current u against the
+ * right-hand side of the last step (host double). */
+int ac_residual(ac_ctx *ctx, double *rho);
+
+/* ---- kernel-level entry point ------------------------------------------ */
+
+/* Euclidean projection of count vectors y (count x N FP64, device) onto the
+ * Gibbs simplex (Eq. Gibbs_simplex), the closed form max(y - theta, 0) that
+ * the clamp-and-redistribute loop of Sec. 3.3 reaches in <= N passes.  x
+ * (device, count x N) may alias y.  Ordered on stream. */
+int ac_project_simplex(const double *y, double *x, int64_t count, int n_phases, void *stream);
+
+/* Description of the last error on the calling thread ("" if none). */
+const char *ac_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AC_H */

@@ -1,0 +1,283 @@
+"""Thin Python binding of libac (include/ac.h): argument marshalling only.
+
+Every function keeps the C name and forwards to the library; all arithmetic
+runs in the library's CUDA kernels.  Buffers may be numpy arrays (host memory,
+is_device = 0) or torch CUDA tensors (device memory, is_device = 1).  Importing
+this module fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libac.so")
+
+AC_OK, AC_ERR_ARG, AC_ERR_CUDA, AC_ERR_NOT_CONVERGED, AC_ERR_NUMERIC, AC_ERR_STATE, AC_ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
+AC_FP64, AC_MIXED = 0, 1
+AC_MAX_PHASES = 8
+
+EXPORTS = [
+    "ac_default_params", "ac_create", "ac_set_image", "ac_set_image_f64", "ac_step", "ac_segment", "ac_destroy",
+    "ac_set_phase", "ac_get_phase", "ac_get_means", "ac_get_moments", "ac_get_rhs", "ac_get_node_labels",
+    "ac_energy", "ac_residual", "ac_project_simplex", "ac_last_error",
+]
+
+
+class ac_params(C.Structure):
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("n_phases", C.c_int),
+                ("eps", C.c_double), ("lambda_", C.c_double), ("tau", C.c_double), ("tol", C.c_double),
+                ("nu1", C.c_int), ("nu2", C.c_int), ("max_cycles", C.c_int), ("coarse_min", C.c_int),
+                ("precision", C.c_int), ("seed", C.c_uint64), ("stream", C.c_void_p)]
+
+
+class ac_stats(C.Structure):
+    _fields_ = [("energy", C.c_double), ("residual", C.c_double), ("cycles", C.c_int),
+                ("total_cycles", C.c_int), ("steps", C.c_int), ("converged", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class AcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libac error {code}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libac is not built ({_LIB_PATH} missing): run __graft_entry__.build()")
+    L = C.CDLL(_LIB_PATH)
+    vp, i, i64, d = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    P = C.POINTER
+    sig = {
+        "ac_default_params": ([P(ac_params)], i),
+        "ac_create": ([P(vp), P(ac_params)], i),
+        "ac_set_image": ([vp, vp, i], i),
+        "ac_set_image_f64": ([vp, vp, i], i),
+        "ac_step": ([vp, i, P(ac_stats)], i),
+        "ac_segment": ([vp, i, vp, i, P(ac_stats)], i),
+        "ac_destroy": ([vp], None),
+        "ac_set_phase": ([vp, vp, i], i),
+        "ac_get_phase": ([vp, vp, i], i),
+        "ac_get_means": ([vp, vp], i),
+        "ac_get_moments": ([vp, vp], i),
+        "ac_get_rhs": ([vp, vp], i),
+        "ac_get_node_labels": ([vp, vp, i], i),
+        "ac_energy": ([vp, P(d)], i),
+        "ac_residual": ([vp, P(d)], i),
+        "ac_project_simplex": ([vp, vp, i64, i, vp], i),
+        "ac_last_error": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+
+
+def _check(rc, ok=(AC_OK,)):
+    if rc not in ok:
+        raise AcError(rc, lib.ac_last_error().decode())
+    return rc
+
+
+def _buf(x, dtype, count, writable=False):
+    """(pointer, is_device) of a numpy array or torch tensor of `count` elements."""
+    if hasattr(x, "data_ptr"):  # torch tensor
+        import torch
+        want = {np.float32: torch.float32, np.float64: torch.float64, np.int8: torch.int8}[dtype]
+        if x.dtype != want or not x.is_contiguous() or x.numel() != count:
+            raise ValueError(f"expected a contiguous {want} tensor of {count} elements")
+        return x.data_ptr(), int(x.is_cuda)
+    if not isinstance(x, np.ndarray) or x.dtype != dtype or not x.flags.c_contiguous or x.size != count:
+        raise ValueError(f"expected a C-contiguous {np.dtype(dtype)} array of {count} elements")
+    if writable and not x.flags.writeable:
+        raise ValueError("output array is read-only")
+    return x.ctypes.data, 0
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def ac_default_params(**kw) -> ac_params:
+    p = ac_params()
+    _check(lib.ac_default_params(C.byref(p)))
+    if "lambda" in kw:
+        kw["lambda_"] = kw.pop("lambda")
+    if "stream" not in kw:
+        kw["stream"] = _current_stream()
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def ac_create(params: ac_params):
+    ctx = C.c_void_p()
+    _check(lib.ac_create(C.byref(ctx), C.byref(params)))
+    return ctx
+
+
+def ac_destroy(ctx):
+    lib.ac_destroy(ctx)
+
+
+def ac_set_image(ctx, rgb, W, H):
+    """rgb: H x W x 3 float32 (numpy host array or torch CUDA tensor)."""
+    ptr, dev = _buf(rgb, np.float32, W * H * 3)
+    return _check(lib.ac_set_image(ctx, ptr, dev))
+
+
+def ac_set_image_f64(ctx, rgb, W, H):
+    ptr, dev = _buf(rgb, np.float64, W * H * 3)
+    return _check(lib.ac_set_image_f64(ctx, ptr, dev))
+
+
+def ac_step(ctx, n_steps, allow_not_converged=False):
+    st = ac_stats()
+    ok = (AC_OK, AC_ERR_NOT_CONVERGED) if allow_not_converged else (AC_OK,)
+    rc = _check(lib.ac_step(ctx, n_steps, C.byref(st)), ok)
+    return rc, st
+
+
+def ac_segment(ctx, n_steps, labels, W, H, allow_not_converged=False):
+    ptr, dev = _buf(labels, np.int8, W * H, writable=True)
+    st = ac_stats()
+    ok = (AC_OK, AC_ERR_NOT_CONVERGED) if allow_not_converged else (AC_OK,)
+    rc = _check(lib.ac_segment(ctx, n_steps, ptr, dev, C.byref(st)), ok)
+    return rc, st
+
+
+def ac_set_phase(ctx, u, n_nodes, N):
+    ptr, dev = _buf(u, np.float64, n_nodes * N)
+    return _check(lib.ac_set_phase(ctx, ptr, dev))
+
+
+def ac_get_phase(ctx, u, n_nodes, N):
+    ptr, dev = _buf(u, np.float64, n_nodes * N, writable=True)
+    return _check(lib.ac_get_phase(ctx, ptr, dev))
+
+
+def ac_get_means(ctx, N):
+    c = np.zeros((N, 3))
+    _check(lib.ac_get_means(ctx, c.ctypes.data))
+    return c
+
+
+def ac_get_moments(ctx, n_nodes):
+    m = np.zeros((n_nodes, 5))
+    _check(lib.ac_get_moments(ctx, m.ctypes.data))
+    return m
+
+
+def ac_get_rhs(ctx, n_nodes, N):
+    b = np.zeros((n_nodes, N))
+    _check(lib.ac_get_rhs(ctx, b.ctypes.data))
+    return b
+
+
+def ac_get_node_labels(ctx, labels, n_nodes):
+    ptr, dev = _buf(labels, np.int8, n_nodes, writable=True)
+    return _check(lib.ac_get_node_labels(ctx, ptr, dev))
+
+
+def ac_energy(ctx) -> float:
+    e = C.c_double()
+    _check(lib.ac_energy(ctx, C.byref(e)))
+    return e.value
+
+
+def ac_residual(ctx) -> float:
+    r = C.c_double()
+    _check(lib.ac_residual(ctx, C.byref(r)))
+    return r.value
+
+
+def ac_project_simplex(y, x, count, N, stream=None):
+    """y, x: torch CUDA float64 tensors of count*N elements."""
+    py, dy = _buf(y, np.float64, count * N)
+    px, dx = _buf(x, np.float64, count * N, writable=True)
+    if not (dy and dx):
+        raise ValueError("ac_project_simplex takes device tensors")
+    return _check(lib.ac_project_simplex(py, px, count, N, stream if stream is not None else _current_stream()))
+
+
+def ac_last_error() -> str:
+    return lib.ac_last_error().decode()
+
+
+class Segmenter:
+    """Owns one context: image W x H, N phases.  Convenience over the C calls."""
+
+    def __init__(self, W, H, N, eps, lam, tau, **kw):
+        self.W, self.H, self.N = W, H, N
+        self.n_nodes = (W + 1) * (H + 1)
+        self.params = ac_default_params(width=W, height=H, n_phases=N, eps=eps, tau=tau, **{"lambda": lam}, **kw)
+        self.ctx = ac_create(self.params)
+
+    def close(self):
+        if self.ctx is not None:
+            ac_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_image(self, rgb):
+        dt = getattr(rgb, "dtype", None)
+        if dt == np.float64 or str(dt) == "torch.float64":
+            return ac_set_image_f64(self.ctx, rgb, self.W, self.H)
+        return ac_set_image(self.ctx, rgb, self.W, self.H)
+
+    def set_phase(self, u):
+        return ac_set_phase(self.ctx, u, self.n_nodes, self.N)
+
+    def phase(self):
+        u = np.zeros((self.n_nodes, self.N))
+        ac_get_phase(self.ctx, u, self.n_nodes, self.N)
+        return u
+
+    def step(self, n=1, allow_not_converged=False):
+        return ac_step(self.ctx, n, allow_not_converged)[1]
+
+    def segment(self, n=0, allow_not_converged=False):
+        lab = np.zeros((self.H, self.W), np.int8)
+        ac_segment(self.ctx, n, lab, self.W, self.H, allow_not_converged)
+        return lab
+
+    def node_labels(self):
+        lab = np.zeros((self.H + 1, self.W + 1), np.int8)
+        ac_get_node_labels(self.ctx, lab, self.n_nodes)
+        return lab
+
+    def means(self):
+        return ac_get_means(self.ctx, self.N)
+
+    def moments(self):
+        return ac_get_moments(self.ctx, self.n_nodes)
+
+    def rhs(self):
+        return ac_get_rhs(self.ctx, self.n_nodes, self.N)
+
+    def energy(self):
+        return ac_energy(self.ctx)
+
+    def residual(self):
+        return ac_residual(self.ctx)

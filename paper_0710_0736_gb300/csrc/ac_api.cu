@@ -1,0 +1,506 @@
+// ac_api.cu -- the C ABI of libac (include/ac.h) and the host-side driver of
+// the time step: colour means and right-hand side, then truncated monotone
+// multigrid V-cycles until the natural residual reaches tol (Sec. 3.2 of
+// Kay & Tomasi; the cycle structure is described at solve_step below).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ac.h"
+#include "ac_device.cuh"
+#include "ac_ops.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define AC_CUDA(call)                                                                              \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(AC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));      \
+  } while (0)
+
+#define AC_LAUNCHED()                                                                              \
+  do {                                                                                             \
+    cudaError_t e_ = cudaGetLastError();                                                           \
+    if (e_ != cudaSuccess) return fail(AC_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e_));  \
+  } while (0)
+
+const ac::Ops *ops_for(int N) {
+  switch (N) {
+    case 2: return ac::ops_n2();
+    case 3: return ac::ops_n3();
+    case 4: return ac::ops_n4();
+    case 5: return ac::ops_n5();
+    case 6: return ac::ops_n6();
+    case 7: return ac::ops_n7();
+    case 8: return ac::ops_n8();
+    default: return nullptr;
+  }
+}
+
+bool pixel_exists(int W, int H, int px, int py) { return px >= 0 && px < W && py >= 0 && py < H; }
+
+// Geometry of a W x H level: lumped mass and diagonal of S per node class
+// (see ac_device.cuh for the class numbering).
+ac::Geo make_geo(int W, int H, double te) {
+  ac::Geo g{};
+  g.W = W;
+  g.H = H;
+  g.Wn = W + 1;
+  g.te = te;
+  const int xs[3] = {0, 1, W}, ys[3] = {0, 1, H};
+  for (int cy = 0; cy < 3; ++cy)
+    for (int cx = 0; cx < 3; ++cx) {
+      const int x = xs[cx], y = ys[cy];
+      const int cnt = 2 * pixel_exists(W, H, x, y) + pixel_exists(W, H, x - 1, y) + pixel_exists(W, H, x, y - 1) +
+                      2 * pixel_exists(W, H, x - 1, y - 1);
+      const double m0 = cnt / 6.0;
+      const double vy = 0.5 * ((y < H) + (y > 0)), vx = 0.5 * ((x < W) + (x > 0));
+      const double wsum = (x < W ? vy : 0) + (x > 0 ? vy : 0) + (y < H ? vx : 0) + (y > 0 ? vx : 0);
+      const int k = cy * 3 + cx;
+      g.m0[k] = m0;
+      g.D[k] = m0 + te * wsum;
+      g.invD[k] = g.D[k] > 0 ? 1.0 / g.D[k] : 0.0;
+    }
+  return g;
+}
+
+struct Level {
+  ac::Geo g;
+  int64_t n = 0;
+  double *op = nullptr, *r = nullptr, *v = nullptr, *t = nullptr;
+};
+
+constexpr int kCoarseSweeps = 2;          // pre/post sweeps on coarse levels
+constexpr int kCoarsestSweeps = 20;       // sweeps of the one-block coarsest solve
+constexpr int64_t kCoarsestBlockNodes = 1 << 14;
+
+}  // namespace
+
+struct ac_ctx {
+  ac_params p{};
+  int N = 0;
+  int64_t n = 0;
+  const ac::Ops *ops = nullptr;
+  cudaStream_t s = nullptr;
+  std::vector<Level> lv;  // lv[0]: fine level (geometry only)
+  double *u = nullptr, *b = nullptr, *mom = nullptr, *rt = nullptr, *d = nullptr;
+  double *part = nullptr, *tot = nullptr, *c = nullptr, *c_tmp = nullptr, *energy = nullptr;
+  double *rho = nullptr, *omega = nullptr, *ls_part = nullptr, *ls_tot = nullptr;
+  uint8_t *mask = nullptr;
+  void *img = nullptr;     // device copy of a host image (allocated on demand)
+  size_t img_bytes = 0;
+  double *h_scalars = nullptr;  // pinned: rho, energy
+  bool have_image = false, have_rhs = false;
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+int dev_alloc(ac_ctx *ctx, void **p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AC_ERR_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->allocs.push_back(*p);
+  return AC_OK;
+}
+
+#define AC_ALLOC(ptr, bytes)                                                   \
+  do {                                                                         \
+    int rc_ = dev_alloc(ctx, reinterpret_cast<void **>(&(ptr)), (bytes));      \
+    if (rc_) return rc_;                                                       \
+  } while (0)
+
+int validate(const ac_params *p) {
+  if (!p) return fail(AC_ERR_ARG, "params is NULL");
+  if (p->width < 1 || p->height < 1) return fail(AC_ERR_ARG, "image size must be >= 1x1");
+  if ((int64_t)(p->width + 1) * (p->height + 1) > (int64_t)1 << 31)
+    return fail(AC_ERR_ARG, "image too large (more than 2^31 nodes)");
+  if (p->n_phases < 2 || p->n_phases > AC_MAX_PHASES) return fail(AC_ERR_ARG, "n_phases must be in [2, %d]", AC_MAX_PHASES);
+  if (!(p->eps > 0) || !std::isfinite(p->eps)) return fail(AC_ERR_ARG, "eps must be > 0");
+  if (!(p->tau > 0) || !std::isfinite(p->tau)) return fail(AC_ERR_ARG, "tau must be > 0");
+  if (!(p->lambda >= 0) || !std::isfinite(p->lambda)) return fail(AC_ERR_ARG, "lambda must be >= 0");
+  if (!(p->tol > 0)) return fail(AC_ERR_ARG, "tol must be > 0");
+  if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1) return fail(AC_ERR_ARG, "need nu1, nu2 >= 0 and nu1 + nu2 >= 1");
+  if (p->max_cycles < 1) return fail(AC_ERR_ARG, "max_cycles must be >= 1");
+  if (p->coarse_min < 1) return fail(AC_ERR_ARG, "coarse_min must be >= 1");
+  if (p->precision != AC_FP64) return fail(AC_ERR_ARG, "precision mode %d is not available", p->precision);
+  return AC_OK;
+}
+
+int read_rho(ac_ctx *ctx, double *out) {
+  AC_CUDA(cudaMemcpyAsync(ctx->h_scalars, ctx->rho, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+  AC_CUDA(cudaStreamSynchronize(ctx->s));
+  *out = ctx->h_scalars[0];
+  return AC_OK;
+}
+
+// Linear V-cycle for S_k v_k = r_k on coarse levels k >= 1 (operators already
+// built), zero initial guess, Gauss-Seidel smoothing in 3 colours.
+int coarse_vcycle(ac_ctx *ctx, int k) {
+  Level &L = ctx->lv[k];
+  const ac::Ops *o = ctx->ops;
+  AC_CUDA(cudaMemsetAsync(L.v, 0, L.n * ctx->N * sizeof(double), ctx->s));
+  if (k == (int)ctx->lv.size() - 1) {
+    if (L.n <= kCoarsestBlockNodes)
+      o->coarse_solve(L.op, L.r, L.v, L.g, kCoarsestSweeps, ctx->s);
+    else
+      o->coarse_smooth(L.op, L.r, L.v, L.g, 2 * kCoarseSweeps, ctx->s);
+    AC_LAUNCHED();
+    return AC_OK;
+  }
+  Level &C = ctx->lv[k + 1];
+  o->coarse_smooth(L.op, L.r, L.v, L.g, kCoarseSweeps, ctx->s);
+  o->coarse_resid(L.op, L.r, L.v, L.g, L.t, ctx->s);
+  o->restrict_(L.t, L.g, C.g, C.r, ctx->s);
+  AC_LAUNCHED();
+  int rc = coarse_vcycle(ctx, k + 1);
+  if (rc) return rc;
+  o->prolong_add(C.v, L.g, C.g, L.v, ctx->s);
+  o->coarse_smooth(L.op, L.r, L.v, L.g, kCoarseSweeps, ctx->s);
+  AC_LAUNCHED();
+  return AC_OK;
+}
+
+// One time step's solve (b already assembled).  Cycle structure:
+//   smooth (nu1 red-black projected sweeps; nu2 + nu1 after a correction)
+//   -> residual r = b - S u, natural residual rho, free-phase mask, tangent
+//      projection of r; stop if rho <= tol
+//   -> truncated Galerkin operators and restriction, linear V-cycle on the
+//      coarse levels
+//   -> feasible coarse-correction direction and exact line search.
+// Every stage leaves u on the simplex and does not raise the step energy, so
+// the limit is the unique minimiser that plain projected Gauss-Seidel (the
+// smoother alone) reaches.
+int solve_step(ac_ctx *ctx, int *cycles_out, double *rho_out) {
+  const ac::Ops *o = ctx->ops;
+  const ac::Geo &g0 = ctx->lv[0].g;
+  const bool coarse = ctx->lv.size() > 1;
+  double rho = 0;
+  int cyc = 0, status = AC_ERR_NOT_CONVERGED;
+  for (;;) {
+    if (cyc > 0 && coarse) o->apply(ctx->u, ctx->d, ctx->omega, ctx->n, ctx->s);
+    o->smooth_fine(ctx->u, ctx->b, g0, cyc == 0 ? ctx->p.nu1 : ctx->p.nu1 + ctx->p.nu2, ctx->s);
+    AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
+    o->fine_resid(ctx->u, ctx->b, g0, ctx->rt, ctx->mask, ctx->rho, ctx->s);
+    AC_LAUNCHED();
+    ++cyc;
+    int rc = read_rho(ctx, &rho);
+    if (rc) return rc;
+    if (std::isnan(rho) || std::isinf(rho)) {
+      status = fail(AC_ERR_NUMERIC, "non-finite residual");
+      break;
+    }
+    if (rho <= ctx->p.tol) {
+      status = AC_OK;
+      break;
+    }
+    if (cyc >= ctx->p.max_cycles) break;
+    if (!coarse) continue;
+    Level &L1 = ctx->lv[1];
+    o->galerkin0(ctx->mask, g0, L1.g, L1.op, ctx->s);
+    for (size_t k = 1; k + 1 < ctx->lv.size(); ++k)
+      o->galerkin(ctx->lv[k].op, ctx->lv[k].g, ctx->lv[k + 1].g, ctx->lv[k + 1].op, ctx->s);
+    o->restrict_(ctx->rt, g0, L1.g, L1.r, ctx->s);
+    AC_LAUNCHED();
+    rc = coarse_vcycle(ctx, 1);
+    if (rc) return rc;
+    o->line_search(ctx->u, ctx->rt, L1.v, ctx->mask, g0, L1.g, ctx->d, ctx->ls_part, ctx->ls_tot, ctx->omega, ctx->s);
+    AC_LAUNCHED();
+  }
+  *cycles_out = cyc;
+  *rho_out = rho;
+  if (status == AC_ERR_NOT_CONVERGED) fail(status, "step did not reach tol %.3g in %d cycles (rho %.3g)", ctx->p.tol, cyc, rho);
+  return status;
+}
+
+int copy_out(ac_ctx *ctx, void *dst, const void *src, size_t bytes, int is_device) {
+  AC_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->s));
+  if (!is_device) AC_CUDA(cudaStreamSynchronize(ctx->s));
+  return AC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ac_default_params(ac_params *p) {
+  if (!p) return fail(AC_ERR_ARG, "params is NULL");
+  std::memset(p, 0, sizeof *p);
+  p->tol = 1e-10;
+  p->nu1 = 2;
+  p->nu2 = 2;
+  p->max_cycles = 200;
+  p->coarse_min = 4;
+  p->precision = AC_FP64;
+  return AC_OK;
+}
+
+int ac_create(ac_ctx **out, const ac_params *p) {
+  if (!out) return fail(AC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  int rc = validate(p);
+  if (rc) return rc;
+  ac_ctx *ctx = new (std::nothrow) ac_ctx;
+  if (!ctx) return fail(AC_ERR_NOMEM, "host allocation failed");
+  ctx->p = *p;
+  ctx->N = p->n_phases;
+  ctx->ops = ops_for(ctx->N);
+  ctx->s = (cudaStream_t)p->stream;
+  const double te = p->tau * p->eps;
+  // level hierarchy
+  int W = p->width, H = p->height;
+  ctx->lv.push_back(Level{make_geo(W, H, te)});
+  ctx->lv[0].n = (int64_t)(W + 1) * (H + 1);
+  while (W % 2 == 0 && H % 2 == 0 && (W < H ? W : H) / 2 >= p->coarse_min) {
+    W /= 2;
+    H /= 2;
+    Level L;
+    L.g = make_geo(W, H, te);
+    L.n = (int64_t)(W + 1) * (H + 1);
+    ctx->lv.push_back(L);
+  }
+  ctx->n = ctx->lv[0].n;
+  const int N = ctx->N;
+  const size_t fN = (size_t)ctx->n * N * sizeof(double);
+  const int ls_blocks = (int)(((ctx->lv[0].g.W + 1 + 255) / 256) * (int64_t)(ctx->lv[0].g.H + 1));
+  auto body = [&]() -> int {
+    AC_ALLOC(ctx->u, fN);
+    AC_ALLOC(ctx->b, fN);
+    AC_ALLOC(ctx->rt, fN);
+    AC_ALLOC(ctx->mom, (size_t)ctx->n * 4 * sizeof(double));
+    AC_ALLOC(ctx->mask, (size_t)ctx->n);
+    if (ctx->lv.size() > 1) AC_ALLOC(ctx->d, fN);
+    AC_ALLOC(ctx->part, (size_t)ac::kMaxPartBlocks * 7 * N * sizeof(double));
+    AC_ALLOC(ctx->tot, (size_t)7 * N * sizeof(double));
+    AC_ALLOC(ctx->c, (size_t)3 * N * sizeof(double));
+    AC_ALLOC(ctx->c_tmp, (size_t)3 * N * sizeof(double));
+    AC_ALLOC(ctx->energy, sizeof(double));
+    AC_ALLOC(ctx->rho, sizeof(double));
+    AC_ALLOC(ctx->omega, sizeof(double));
+    AC_ALLOC(ctx->ls_part, (size_t)2 * ls_blocks * sizeof(double));
+    AC_ALLOC(ctx->ls_tot, 2 * sizeof(double));
+    for (size_t k = 1; k < ctx->lv.size(); ++k) {
+      Level &L = ctx->lv[k];
+      AC_ALLOC(L.op, (size_t)L.n * 4 * N * sizeof(double));
+      AC_ALLOC(L.r, (size_t)L.n * N * sizeof(double));
+      AC_ALLOC(L.v, (size_t)L.n * N * sizeof(double));
+      AC_ALLOC(L.t, (size_t)L.n * N * sizeof(double));
+    }
+    AC_CUDA(cudaMallocHost(&ctx->h_scalars, 4 * sizeof(double)));
+    AC_CUDA(cudaMemsetAsync(ctx->c, 0, (size_t)3 * N * sizeof(double), ctx->s));
+    AC_CUDA(cudaMemsetAsync(ctx->omega, 0, sizeof(double), ctx->s));
+    return AC_OK;
+  };
+  rc = body();
+  if (rc) {
+    std::string msg = g_last_error;
+    ac_destroy(ctx);
+    g_last_error = msg;
+    return rc;
+  }
+  *out = ctx;
+  return AC_OK;
+}
+
+void ac_destroy(ac_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->s) cudaStreamSynchronize(ctx->s);
+  else cudaDeviceSynchronize();
+  for (void *p : ctx->allocs) cudaFree(p);
+  if (ctx->img) cudaFree(ctx->img);
+  if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
+  delete ctx;
+}
+
+static int set_image_impl(ac_ctx *ctx, const void *rgb, int is_device, bool f64) {
+  if (!ctx || !rgb) return fail(AC_ERR_ARG, "NULL argument");
+  const ac::Geo &g = ctx->lv[0].g;
+  const size_t bytes = (size_t)g.W * g.H * 3 * (f64 ? sizeof(double) : sizeof(float));
+  const void *src = rgb;
+  if (!is_device) {
+    if (ctx->img_bytes < bytes) {
+      if (ctx->img) cudaFree(ctx->img);
+      ctx->img = nullptr;
+      ctx->img_bytes = 0;
+      cudaError_t e = cudaMalloc(&ctx->img, bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AC_ERR_NOMEM, "cudaMalloc(%zu) for the image: %s", bytes, cudaGetErrorString(e));
+      }
+      ctx->img_bytes = bytes;
+    }
+    AC_CUDA(cudaMemcpyAsync(ctx->img, rgb, bytes, cudaMemcpyHostToDevice, ctx->s));
+    src = ctx->img;
+  }
+  if (f64)
+    ctx->ops->moments_f64((const double *)src, g, ctx->mom, ctx->s);
+  else
+    ctx->ops->moments_f32((const float *)src, g, ctx->mom, ctx->s);
+  ctx->ops->init_random(ctx->u, ctx->n, ctx->p.seed, ctx->s);
+  AC_LAUNCHED();
+  AC_CUDA(cudaMemsetAsync(ctx->c, 0, (size_t)3 * ctx->N * sizeof(double), ctx->s));
+  if (!is_device) AC_CUDA(cudaStreamSynchronize(ctx->s));  // the host buffer may be reused after return
+  ctx->have_image = true;
+  ctx->have_rhs = false;
+  return AC_OK;
+}
+
+int ac_set_image(ac_ctx *ctx, const float *rgb, int is_device) { return set_image_impl(ctx, rgb, is_device, false); }
+int ac_set_image_f64(ac_ctx *ctx, const double *rgb, int is_device) { return set_image_impl(ctx, rgb, is_device, true); }
+
+int ac_step(ac_ctx *ctx, int n_steps, ac_stats *out) {
+  if (!ctx) return fail(AC_ERR_ARG, "ctx is NULL");
+  if (n_steps < 0) return fail(AC_ERR_ARG, "n_steps must be >= 0");
+  if (!ctx->have_image) return fail(AC_ERR_STATE, "ac_set_image must come first");
+  ac_stats st{};
+  st.converged = 1;
+  int status = AC_OK;
+  const double a1 = 1.0 + 2.0 * ctx->p.tau / ctx->p.eps, tl = ctx->p.tau * ctx->p.lambda;
+  for (int t = 0; t < n_steps; ++t) {
+    ctx->ops->means(ctx->u, ctx->mom, ctx->lv[0].g, ctx->part, ctx->tot, ctx->c, ctx->energy, ctx->p.eps,
+                    ctx->p.lambda, ctx->s);
+    ctx->ops->rhs(ctx->u, ctx->mom, ctx->c, ctx->lv[0].g, a1, tl, ctx->b, ctx->s);
+    AC_LAUNCHED();
+    ctx->have_rhs = true;
+    int cycles = 0;
+    double rho = 0;
+    int rc = solve_step(ctx, &cycles, &rho);
+    st.cycles = cycles;
+    st.total_cycles += cycles;
+    st.residual = rho;
+    st.steps = t + 1;
+    if (rc == AC_ERR_NOT_CONVERGED) {
+      st.converged = 0;
+      status = rc;
+    } else if (rc) {
+      st.converged = 0;
+      if (out) *out = st;
+      return rc;
+    }
+  }
+  if (n_steps > 0) {
+    AC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 1, ctx->energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    AC_CUDA(cudaStreamSynchronize(ctx->s));
+    st.energy = ctx->h_scalars[1];
+  }
+  if (out) *out = st;
+  return status;
+}
+
+int ac_segment(ac_ctx *ctx, int n_steps, int8_t *pixel_labels, int is_device, ac_stats *out) {
+  if (!ctx || !pixel_labels) return fail(AC_ERR_ARG, "NULL argument");
+  int rc = ac_step(ctx, n_steps, out);
+  if (rc && rc != AC_ERR_NOT_CONVERGED) return rc;
+  const ac::Geo &g = ctx->lv[0].g;
+  const size_t bytes = (size_t)g.W * g.H;
+  int8_t *dst = pixel_labels;
+  if (!is_device) dst = reinterpret_cast<int8_t *>(ctx->rt);  // scratch large enough for W*H bytes
+  ctx->ops->labels(ctx->u, g, nullptr, dst, ctx->s);
+  AC_LAUNCHED();
+  if (!is_device) {
+    int rc2 = copy_out(ctx, pixel_labels, dst, bytes, 0);
+    if (rc2) return rc2;
+  }
+  return rc;
+}
+
+int ac_set_phase(ac_ctx *ctx, const double *u, int is_device) {
+  if (!ctx || !u) return fail(AC_ERR_ARG, "NULL argument");
+  AC_CUDA(cudaMemcpyAsync(ctx->u, u, (size_t)ctx->n * ctx->N * sizeof(double),
+                          is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->s));
+  AC_CUDA(cudaMemsetAsync(ctx->c, 0, (size_t)3 * ctx->N * sizeof(double), ctx->s));
+  if (!is_device) AC_CUDA(cudaStreamSynchronize(ctx->s));
+  return AC_OK;
+}
+
+int ac_get_phase(ac_ctx *ctx, double *u, int is_device) {
+  if (!ctx || !u) return fail(AC_ERR_ARG, "NULL argument");
+  return copy_out(ctx, u, ctx->u, (size_t)ctx->n * ctx->N * sizeof(double), is_device);
+}
+
+int ac_get_means(ac_ctx *ctx, double *c) {
+  if (!ctx || !c) return fail(AC_ERR_ARG, "NULL argument");
+  return copy_out(ctx, c, ctx->c, (size_t)3 * ctx->N * sizeof(double), 0);
+}
+
+int ac_get_moments(ac_ctx *ctx, double *m) {
+  if (!ctx || !m) return fail(AC_ERR_ARG, "NULL argument");
+  if (!ctx->have_image) return fail(AC_ERR_STATE, "no image");
+  std::vector<double> mom((size_t)ctx->n * 4);
+  int rc = copy_out(ctx, mom.data(), ctx->mom, mom.size() * sizeof(double), 0);
+  if (rc) return rc;
+  const ac::Geo &g = ctx->lv[0].g;
+  for (int64_t k = 0; k < ctx->n; ++k) {
+    const int x = (int)(k % g.Wn), y = (int)(k / g.Wn);
+    const int cx = x == 0 ? 0 : (x == g.W ? 2 : 1), cy = y == 0 ? 0 : (y == g.H ? 2 : 1);
+    m[k * 5 + 0] = g.m0[cy * 3 + cx];
+    for (int j = 0; j < 4; ++j) m[k * 5 + 1 + j] = mom[k * 4 + j];
+  }
+  return AC_OK;
+}
+
+int ac_get_rhs(ac_ctx *ctx, double *b) {
+  if (!ctx || !b) return fail(AC_ERR_ARG, "NULL argument");
+  if (!ctx->have_rhs) return fail(AC_ERR_STATE, "no step taken yet");
+  return copy_out(ctx, b, ctx->b, (size_t)ctx->n * ctx->N * sizeof(double), 0);
+}
+
+int ac_get_node_labels(ac_ctx *ctx, int8_t *labels, int is_device) {
+  if (!ctx || !labels) return fail(AC_ERR_ARG, "NULL argument");
+  int8_t *dst = is_device ? labels : reinterpret_cast<int8_t *>(ctx->rt);
+  ctx->ops->labels(ctx->u, ctx->lv[0].g, dst, nullptr, ctx->s);
+  AC_LAUNCHED();
+  if (!is_device) return copy_out(ctx, labels, dst, (size_t)ctx->n, 0);
+  return AC_OK;
+}
+
+int ac_energy(ac_ctx *ctx, double *energy) {
+  if (!ctx || !energy) return fail(AC_ERR_ARG, "NULL argument");
+  if (!ctx->have_image) return fail(AC_ERR_STATE, "no image");
+  AC_CUDA(cudaMemcpyAsync(ctx->c_tmp, ctx->c, (size_t)3 * ctx->N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
+  ctx->ops->means(ctx->u, ctx->mom, ctx->lv[0].g, ctx->part, ctx->tot, ctx->c_tmp, ctx->energy, ctx->p.eps,
+                  ctx->p.lambda, ctx->s);
+  AC_LAUNCHED();
+  return copy_out(ctx, energy, ctx->energy, sizeof(double), 0);
+}
+
+int ac_residual(ac_ctx *ctx, double *rho) {
+  if (!ctx || !rho) return fail(AC_ERR_ARG, "NULL argument");
+  if (!ctx->have_rhs) return fail(AC_ERR_STATE, "no step taken yet");
+  AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
+  ctx->ops->fine_resid(ctx->u, ctx->b, ctx->lv[0].g, nullptr, nullptr, ctx->rho, ctx->s);
+  AC_LAUNCHED();
+  return read_rho(ctx, rho);
+}
+
+int ac_project_simplex(const double *y, double *x, int64_t count, int n_phases, void *stream) {
+  const ac::Ops *o = ops_for(n_phases);
+  if (!o) return fail(AC_ERR_ARG, "n_phases must be in [2, %d]", AC_MAX_PHASES);
+  if (count < 0 || (count > 0 && (!y || !x))) return fail(AC_ERR_ARG, "bad buffers");
+  o->project(y, x, count, (cudaStream_t)stream);
+  AC_LAUNCHED();
+  return AC_OK;
+}
+
+const char *ac_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,244 @@
+// ac_device.cuh -- device-side building blocks of libac (sm_103a).
+//
+// Mesh: W x H pixels of side 1, nodes at pixel corners (x, y), node index
+// n = y*(W+1) + x, each pixel split along its (x,y)-(x+1,y+1) diagonal
+// (P1 finite elements, Sec. 3.1 of Kay & Tomasi).  On that triangulation:
+//   lumped mass  Mhat_n = (#incident triangles)/6 : 1 inside, 1/2 on edges,
+//                1/3 at (0,0) and (W,H), 1/6 at (W,0) and (0,H);
+//   stiffness    A = 5-point graph Laplacian with weight 1 on interior axis
+//                edges, 1/2 on boundary axis edges and 0 on the diagonals
+//                (their opposite angles are right angles).
+// The step matrix is S = Mhat + tau*eps*A (Sec. 3.2, Eq. alpha).
+#pragma once
+#include <cstdint>
+#include <type_traits>
+#include <cuda_runtime.h>
+
+namespace ac {
+
+// Geometry of one level, passed by value to kernels.  Node classes are
+// cls = cy*3 + cx with cx = 0 (x == 0), 2 (x == W), 1 otherwise, cy alike:
+// the lumped mass and the diagonal of S depend only on the class.
+struct Geo {
+  int W, H;        // cells
+  int Wn;          // W + 1, the row stride in nodes
+  double te;       // tau * eps
+  double m0[9];    // Mhat by class
+  double D[9];     // S_nn by class
+  double invD[9];  // 1 / S_nn by class
+};
+
+__device__ __forceinline__ int node_class(const Geo &g, int x, int y) {
+  int cx = x == 0 ? 0 : (x == g.W ? 2 : 1);
+  int cy = y == 0 ? 0 : (y == g.H ? 2 : 1);
+  return cy * 3 + cx;
+}
+
+// Stiffness weights of the four axis edges at (x, y): east, west, north, south.
+struct Weights { float e, w, n, s; };
+
+__device__ __forceinline__ Weights edge_weights(const Geo &g, int x, int y) {
+  float vy = 0.5f * (float)((y < g.H) + (y > 0));  // rows above/below the horizontal edge
+  float vx = 0.5f * (float)((x < g.W) + (x > 0));
+  Weights w;
+  w.e = x < g.W ? vy : 0.f;
+  w.w = x > 0 ? vy : 0.f;
+  w.n = y < g.H ? vx : 0.f;
+  w.s = y > 0 ? vx : 0.f;
+  return w;
+}
+
+// ---- vector loads / stores of one node's N values ------------------------
+
+template <typename T, int N>
+__device__ __forceinline__ void ldn(const T *__restrict__ p, T (&v)[N]) {
+  if constexpr (sizeof(T) * N % 16 == 0) {
+    constexpr int K = 16 / sizeof(T);
+    using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+#pragma unroll
+    for (int j = 0; j < N / K; ++j) {
+      V t = __ldg(reinterpret_cast<const V *>(p) + j);
+      if constexpr (sizeof(T) == 8) {
+        v[2 * j] = t.x;
+        v[2 * j + 1] = t.y;
+      } else {
+        v[4 * j] = t.x;
+        v[4 * j + 1] = t.y;
+        v[4 * j + 2] = t.z;
+        v[4 * j + 3] = t.w;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = p[i];
+  }
+}
+
+// Plain (non read-only-path) load, for arrays written by the same kernel.
+template <typename T, int N>
+__device__ __forceinline__ void ldn_rw(const T *p, T (&v)[N]) {
+  if constexpr (sizeof(T) * N % 16 == 0) {
+    constexpr int K = 16 / sizeof(T);
+    using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+#pragma unroll
+    for (int j = 0; j < N / K; ++j) {
+      V t = reinterpret_cast<const V *>(p)[j];
+      if constexpr (sizeof(T) == 8) {
+        v[2 * j] = t.x;
+        v[2 * j + 1] = t.y;
+      } else {
+        v[4 * j] = t.x;
+        v[4 * j + 1] = t.y;
+        v[4 * j + 2] = t.z;
+        v[4 * j + 3] = t.w;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = p[i];
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void stn(T *p, const T (&v)[N]) {
+  if constexpr (sizeof(T) * N % 16 == 0) {
+    constexpr int K = 16 / sizeof(T);
+    using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+#pragma unroll
+    for (int j = 0; j < N / K; ++j) {
+      V t;
+      if constexpr (sizeof(T) == 8) {
+        t.x = v[2 * j];
+        t.y = v[2 * j + 1];
+      } else {
+        t.x = v[4 * j];
+        t.y = v[4 * j + 1];
+        t.z = v[4 * j + 2];
+        t.w = v[4 * j + 3];
+      }
+      reinterpret_cast<V *>(p)[j] = t;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) p[i] = v[i];
+  }
+}
+
+// 1/k for the small integers 1..8 without a division.
+template <typename T>
+__device__ __forceinline__ T rcp_small(int k) {
+  return k == 1 ? T(1) : k == 2 ? T(0.5) : k == 3 ? T(1.0 / 3.0) : k == 4 ? T(0.25)
+       : k == 5 ? T(0.2) : k == 6 ? T(1.0 / 6.0) : k == 7 ? T(1.0 / 7.0) : T(0.125);
+}
+
+// Euclidean projection onto the Gibbs simplex, in place, in registers.
+// The kept set starts full; theta = (sum of kept - 1)/|kept|; components at
+// or below theta leave the set; repeat until none leaves (at most N passes).
+// This is the clamp-and-redistribute loop of Sec. 3.3 written with the
+// threshold theta (Michelot's form of the same iteration).
+template <typename T, int N>
+__device__ __forceinline__ void proj_simplex(T (&y)[N]) {
+  unsigned keep = (1u << N) - 1u;
+  T s = T(0);
+#pragma unroll
+  for (int i = 0; i < N; ++i) s += y[i];
+  T theta = (s - T(1)) * rcp_small<T>(N);
+#pragma unroll 1
+  for (int pass = 1; pass < N; ++pass) {
+    unsigned drop = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (((keep >> i) & 1u) && y[i] <= theta) drop |= 1u << i;
+    if (!drop) break;
+    keep &= ~drop;
+    s = T(0);
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if ((keep >> i) & 1u) {
+        s += y[i];
+        ++k;
+      }
+    theta = (s - T(1)) * rcp_small<T>(k);
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) y[i] = ((keep >> i) & 1u) ? y[i] - theta : T(0);
+}
+
+// Weighted sum of the four axis neighbours' values, acc = sum_m w_nm u_m.
+template <typename T, int N>
+__device__ __forceinline__ void nbr_sum(const T *u, const Geo &g, int x, int y, T (&acc)[N]) {
+  const int64_t n = (int64_t)y * g.Wn + x;
+  T t[N];
+  if (x > 0 && x < g.W && y > 0 && y < g.H) {
+    ldn_rw<T, N>(u + (n + 1) * N, acc);
+    ldn_rw<T, N>(u + (n - 1) * N, t);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] += t[i];
+    ldn_rw<T, N>(u + (n + g.Wn) * N, t);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] += t[i];
+    ldn_rw<T, N>(u + (n - g.Wn) * N, t);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] += t[i];
+  } else {
+    Weights w = edge_weights(g, x, y);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] = T(0);
+    if (w.e > 0.f) {
+      ldn_rw<T, N>(u + (n + 1) * N, t);
+#pragma unroll
+      for (int i = 0; i < N; ++i) acc[i] += T(w.e) * t[i];
+    }
+    if (w.w > 0.f) {
+      ldn_rw<T, N>(u + (n - 1) * N, t);
+#pragma unroll
+      for (int i = 0; i < N; ++i) acc[i] += T(w.w) * t[i];
+    }
+    if (w.n > 0.f) {
+      ldn_rw<T, N>(u + (n + g.Wn) * N, t);
+#pragma unroll
+      for (int i = 0; i < N; ++i) acc[i] += T(w.n) * t[i];
+    }
+    if (w.s > 0.f) {
+      ldn_rw<T, N>(u + (n - g.Wn) * N, t);
+#pragma unroll
+      for (int i = 0; i < N; ++i) acc[i] += T(w.s) * t[i];
+    }
+  }
+}
+
+// P1 interpolation weight of coarse node L at fine node b (fine coordinates),
+// for nested right-diagonal meshes: 1 at 2L, 1/2 at the six neighbours of 2L
+// along the coarse edges (E, W, N, S, NE, SW), 0 elsewhere.
+__device__ __forceinline__ double hat_weight(int dx, int dy) {
+  if (dx == 0 && dy == 0) return 1.0;
+  if ((dx == 1 || dx == -1) && dy == 0) return 0.5;
+  if (dx == 0 && (dy == 1 || dy == -1)) return 0.5;
+  if ((dx == 1 && dy == 1) || (dx == -1 && dy == -1)) return 0.5;
+  return 0.0;
+}
+
+// Block-wide reductions (blockDim.x a multiple of 32, <= 1024).
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// max that propagates NaN (a comparison with NaN is false).
+__device__ __forceinline__ double nanmax(double a, double b) { return (b <= a) ? a : b; }
+
+__device__ __forceinline__ double warp_nanmax(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Non-negative doubles (and NaN) order like their bit patterns as unsigned.
+__device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+}  // namespace ac

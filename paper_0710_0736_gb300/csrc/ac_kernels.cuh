@@ -1,0 +1,697 @@
+// ac_kernels.cuh -- the sm_103a kernels of libac, templated on the phase
+// count N (and, for the smoother, on the scalar type).  Instantiated once per
+// N in ac_inst_n<N>.cu; the host driver (ac_api.cu) calls them through the
+// Ops table declared in ac_ops.h.
+//
+// Data layout in HBM (all arrays node-major, phase innermost):
+//   u, b, d, rt   : n x N          (phase field, right-hand side, line-search
+//                                   direction, tangent-projected residual)
+//   mom           : n x 4          (m1 red, green, blue, m2; m0 comes from
+//                                   the node class)
+//   mask          : n bytes        (bit i set: phase i is free at the node)
+//   coarse level k: op n_k x 4 x N (S entries C, E, N, NE per phase; W, S,
+//                                   SW are read from the neighbours' E, N, NE)
+//                   r, v, t n_k x N
+#pragma once
+#include "ac_device.cuh"
+#include "ac_ops.h"
+
+namespace ac {
+
+constexpr int kBlock = 256;
+
+// ---------------------------------------------------------------------------
+// Deterministic block reduction of K values per thread; thread k < K of the
+// block writes the block's k-th total to dst[k].
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void block_sum_store(double (&v)[K], double *dst) {
+  __shared__ double sm[kBlock / 32][K];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) sm[wid][k] = v[k];
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w][k];
+    dst[k] = s;
+  }
+}
+
+// Column sums of a rows x cols row-major matrix of block partials; one block
+// per column, fixed summation order (bit-reproducible for a fixed grid).
+static __global__ void k_colsum(const double *__restrict__ part, int rows, int cols, double *__restrict__ out) {
+  __shared__ double sm[kBlock];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) s += part[(int64_t)r * cols + c];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = sm[0];
+}
+
+// ---------------------------------------------------------------------------
+// a1: image moments, projection by simplex (Sec. 4.2).  A node collects 1/6
+// of the value of each incident triangle: twice from pixels (x,y) and
+// (x-1,y-1), once from (x-1,y) and (x,y-1) (pixels outside the image omitted).
+// ---------------------------------------------------------------------------
+template <typename TI>
+__global__ void k_moments(const TI *__restrict__ img, Geo g, double *__restrict__ mom) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x > g.W || y > g.H) return;
+  double s[3] = {0, 0, 0}, s2 = 0;
+  const int px[4] = {x, x - 1, x, x - 1};
+  const int py[4] = {y, y - 1, y - 1, y};
+  const double w[4] = {2.0, 2.0, 1.0, 1.0};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (px[k] < 0 || px[k] >= g.W || py[k] < 0 || py[k] >= g.H) continue;
+    const TI *p = img + ((int64_t)py[k] * g.W + px[k]) * 3;
+    double r = (double)p[0], gg = (double)p[1], bb = (double)p[2];
+    s[0] += w[k] * r;
+    s[1] += w[k] * gg;
+    s[2] += w[k] * bb;
+    s2 += w[k] * (r * r + gg * gg + bb * bb);
+  }
+  double *m = mom + ((int64_t)y * g.Wn + x) * 4;
+  m[0] = s[0] / 6.0;
+  m[1] = s[1] / 6.0;
+  m[2] = s[2] / 6.0;
+  m[3] = s2 / 6.0;
+}
+
+// ---------------------------------------------------------------------------
+// Seeded random point of the simplex per node: normalised exponentials
+// -log(U) (a Dirichlet(1,..,1) draw).  U comes from SplitMix64 (Steele, Lea &
+// Flood 2014) on the counter n*N + i.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <int N>
+__global__ void k_init_random(double *__restrict__ u, int64_t n, uint64_t seed) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double e[N], s = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    uint64_t z = splitmix64(seed ^ splitmix64((uint64_t)(k * N + i)));
+    double U = ((double)(z >> 11) + 0.5) * 0x1.0p-53;
+    e[i] = -log(U);
+    s += e[i];
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) e[i] /= s;
+  stn<double, N>(u + k * N, e);
+}
+
+// ---------------------------------------------------------------------------
+// a2: colour means and energy terms.  Per phase i the block partials hold
+//   q=0 mass   sum_n u m0          q=1..3 sum_n u m1 (RGB)
+//   q=4 sum_n u m2                 q=5 sum_n m0 u (1 - u)
+//   q=6 sum over axis edges of w (u_a - u_b)^2   (= u_i' A u_i)
+// at index q*N + i.  (Eq. VV_fidelity, Sec. 4.4; Eq. E.)
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kBlock) k_means_partial(const double *__restrict__ u, const double *__restrict__ mom,
+                                                          Geo g, double *__restrict__ part) {
+  double acc[7 * N];
+#pragma unroll
+  for (int k = 0; k < 7 * N; ++k) acc[k] = 0.0;
+  const int64_t n = (int64_t)g.Wn * (g.H + 1);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % g.Wn), y = (int)(k / g.Wn);
+    const double m0 = g.m0[node_class(g, x, y)];
+    double uk[N], t[N];
+    ldn<double, N>(u + k * N, uk);
+    const double *m = mom + k * 4;
+    const double m1r = m[0], m1g = m[1], m1b = m[2], m2 = m[3];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      acc[0 * N + i] += uk[i] * m0;
+      acc[1 * N + i] += uk[i] * m1r;
+      acc[2 * N + i] += uk[i] * m1g;
+      acc[3 * N + i] += uk[i] * m1b;
+      acc[4 * N + i] += uk[i] * m2;
+      acc[5 * N + i] += m0 * uk[i] * (1.0 - uk[i]);
+    }
+    Weights w = edge_weights(g, x, y);
+    if (x < g.W) {
+      ldn<double, N>(u + (k + 1) * N, t);
+#pragma unroll
+      for (int i = 0; i < N; ++i) acc[6 * N + i] += (double)w.e * (uk[i] - t[i]) * (uk[i] - t[i]);
+    }
+    if (y < g.H) {
+      ldn<double, N>(u + (k + g.Wn) * N, t);
+#pragma unroll
+      for (int i = 0; i < N; ++i) acc[6 * N + i] += (double)w.n * (uk[i] - t[i]) * (uk[i] - t[i]);
+    }
+  }
+  block_sum_store<7 * N>(acc, part + (int64_t)blockIdx.x * 7 * N);
+}
+
+// c_i = s_i / mass_i (previous c kept when mass_i == 0); energy of Eq. (E):
+// sum_i eps/2 u'Au + (1/eps) sum m0 u(1-u) + lambda (U2 - |s|^2/mass).
+template <int N>
+__global__ void k_means_finish(const double *__restrict__ tot, double *__restrict__ c, double *__restrict__ energy,
+                               double eps, double lam) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double E = 0.0;
+  for (int i = 0; i < N; ++i) {
+    const double mass = tot[0 * N + i];
+    const double s0 = tot[1 * N + i], s1 = tot[2 * N + i], s2 = tot[3 * N + i];
+    if (mass != 0.0) {
+      c[i * 3 + 0] = s0 / mass;
+      c[i * 3 + 1] = s1 / mass;
+      c[i * 3 + 2] = s2 / mass;
+      E += lam * (tot[4 * N + i] - (s0 * s0 + s1 * s1 + s2 * s2) / mass);
+    }
+    E += tot[5 * N + i] / eps + 0.5 * eps * tot[6 * N + i];
+  }
+  if (energy) *energy = E;
+}
+
+// ---------------------------------------------------------------------------
+// a3: right-hand side b = m0 u^t (1 + 2 tau/eps) - tau lambda f(c^t), with
+// f_n,i = m2 - 2 c_i.m1 + |c_i|^2 m0  (Eq. alpha multiplied out).
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void k_rhs(const double *__restrict__ u, const double *__restrict__ mom, const double *__restrict__ c, Geo g,
+                      double a1, double tl, double *__restrict__ b) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = (int64_t)g.Wn * (g.H + 1);
+  if (k >= n) return;
+  const int x = (int)(k % g.Wn), y = (int)(k / g.Wn);
+  const double m0 = g.m0[node_class(g, x, y)];
+  const double *m = mom + k * 4;
+  double uk[N], bk[N];
+  ldn<double, N>(u + k * N, uk);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const double c0 = c[i * 3], c1 = c[i * 3 + 1], c2 = c[i * 3 + 2];
+    const double f = m[3] - 2.0 * (c0 * m[0] + c1 * m[1] + c2 * m[2]) + (c0 * c0 + c1 * c1 + c2 * c2) * m0;
+    bk[i] = m0 * uk[i] * a1 - tl * f;
+  }
+  stn<double, N>(b + k * N, bk);
+}
+
+// ---------------------------------------------------------------------------
+// a4/a5: one colour of the projected block Gauss-Seidel sweep on the fine
+// level (Sec. 3.1: nodal sub-problems in red-black order; Sec. 3.3: each
+// nodal N-vector projected onto the simplex).  Nodes with (x + y) % 2 ==
+// color are independent given the other colour:
+//   y_n = (b_n + tau eps sum_m w_nm u_m) / S_nn,   u_n <- P_G(y_n).
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ u, const T *__restrict__ b, Geo g, int color) {
+  const int y = blockIdx.y;
+  const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((y + color) & 1);
+  if (x > g.W) return;
+  const int64_t n = (int64_t)y * g.Wn + x;
+  T acc[N], bk[N];
+  nbr_sum<T, N>(u, g, x, y, acc);
+  ldn<T, N>(b + n * N, bk);
+  const int cls = node_class(g, x, y);
+  const T te = (T)g.te, invD = (T)g.invD[cls];
+#pragma unroll
+  for (int i = 0; i < N; ++i) acc[i] = (bk[i] + te * acc[i]) * invD;
+  proj_simplex<T, N>(acc);
+  stn<T, N>(u + n * N, acc);
+}
+
+// ---------------------------------------------------------------------------
+// a6/a9: fine residual r = b - S u, natural residual rho = max |u - P_G(y)|,
+// free-phase mask and the tangent projection of r over the free phases:
+//   free_n,i = (u_n,i > 0) and at least two phases of node n are > 0;
+//   rt_n,i   = r_n,i - mean_{free j} r_n,j for free i, 0 otherwise.
+// A node at a vertex of the simplex has no free phase.  rt and mask may be
+// null (residual only).
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kBlock) k_fine_resid(const double *__restrict__ u, const double *__restrict__ b, Geo g,
+                                                       double *__restrict__ rt, uint8_t *__restrict__ mask,
+                                                       double *__restrict__ rho) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  double e = 0.0;
+  if (x <= g.W) {
+    const int64_t n = (int64_t)y * g.Wn + x;
+    double acc[N], uk[N], bk[N], r[N];
+    nbr_sum<double, N>(u, g, x, y, acc);
+    ldn<double, N>(u + n * N, uk);
+    ldn<double, N>(b + n * N, bk);
+    const int cls = node_class(g, x, y);
+    const double D = g.D[cls], invD = g.invD[cls];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      r[i] = bk[i] + g.te * acc[i] - D * uk[i];
+      acc[i] = (bk[i] + g.te * acc[i]) * invD;
+    }
+    proj_simplex<double, N>(acc);
+    int cnt = 0;
+    unsigned pos = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      e = nanmax(e, fabs(uk[i] - acc[i]));
+      if (uk[i] > 0.0) {
+        pos |= 1u << i;
+        ++cnt;
+      }
+    }
+    if (!(uk[0] == uk[0])) e = uk[0];  // NaN in u
+    const unsigned fr = cnt >= 2 ? pos : 0u;
+    if (rt) {
+      double s = 0.0;
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if ((fr >> i) & 1u) s += r[i];
+      const double mean = cnt >= 2 ? s * rcp_small<double>(cnt) : 0.0;
+#pragma unroll
+      for (int i = 0; i < N; ++i) r[i] = ((fr >> i) & 1u) ? r[i] - mean : 0.0;
+      stn<double, N>(rt + n * N, r);
+      mask[n] = (uint8_t)fr;
+    }
+  }
+  // block max -> one atomic per block
+  __shared__ double sm[kBlock / 32];
+  e = warp_nanmax(e);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+    v = warp_nanmax(v);
+    if (threadIdx.x == 0) atomic_max_nonneg(rho, v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Restriction r_c(K) = sum_a P_aK t(a) over the 7 fine nodes of the support
+// of the coarse basis function (weights 1 at 2K, 1/2 at E, W, N, S, NE, SW).
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void k_restrict(const double *__restrict__ t, Geo gf, Geo gc, double *__restrict__ rc) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
+  if (X > gc.W) return;
+  constexpr int dx[7] = {0, 1, -1, 0, 0, 1, -1};
+  constexpr int dy[7] = {0, 0, 0, 1, -1, 1, -1};
+  double acc[N], v[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) acc[i] = 0.0;
+#pragma unroll
+  for (int s = 0; s < 7; ++s) {
+    const int ax = 2 * X + dx[s], ay = 2 * Y + dy[s];
+    if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
+    const double p = s == 0 ? 1.0 : 0.5;
+    ldn<double, N>(t + ((int64_t)ay * gf.Wn + ax) * N, v);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] += p * v[i];
+  }
+  stn<double, N>(rc + ((int64_t)Y * gc.Wn + X) * N, acc);
+}
+
+// ---------------------------------------------------------------------------
+// Truncated Galerkin operator of the first coarse level, per phase i:
+//   S_1,i = P' M_i S M_i P,  M_i = diag(free_n,i)  (truncated prolongation).
+// Stored as the C, E, N, NE entries of each coarse node.  Phases free on the
+// whole neighbourhood use the untruncated product (computed once per node);
+// phases free nowhere get 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double fine_S(const Geo &g, int ax, int ay, int ddx, int ddy) {
+  if (ddx == 0 && ddy == 0) return g.D[node_class(g, ax, ay)];
+  Weights w = edge_weights(g, ax, ay);
+  float ww = ddx == 1 ? w.e : ddx == -1 ? w.w : ddy == 1 ? w.n : w.s;
+  return -g.te * (double)ww;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kBlock) k_galerkin0(const uint8_t *__restrict__ mask, Geo gf, Geo gc,
+                                                      double *__restrict__ op) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
+  if (X > gc.W) return;
+  constexpr int sx[7] = {0, 1, -1, 0, 0, 1, -1};
+  constexpr int sy[7] = {0, 0, 0, 1, -1, 1, -1};
+  constexpr int ox[5] = {0, 1, -1, 0, 0};
+  constexpr int oy[5] = {0, 0, 0, 1, -1};
+  constexpr int lx[4] = {0, 1, 0, 1};  // L = K + (lx, ly): C, E, N, NE
+  constexpr int ly[4] = {0, 0, 1, 1};
+  // neighbourhood masks: AND (free everywhere) and OR (free somewhere)
+  unsigned all = (1u << N) - 1u, any = 0u;
+  for (int ay = 2 * Y - 2; ay <= 2 * Y + 3; ++ay)
+    for (int ax = 2 * X - 2; ax <= 2 * X + 3; ++ax) {
+      if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
+      const unsigned m = mask[(int64_t)ay * gf.Wn + ax];
+      all &= m;
+      any |= m;
+    }
+  double full[4] = {0, 0, 0, 0};
+  double acc[4][N];
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[l][i] = 0.0;
+  const unsigned partial = any & ~all;
+#pragma unroll 1
+  for (int s = 0; s < 7; ++s) {
+    const int ax = 2 * X + sx[s], ay = 2 * Y + sy[s];
+    if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
+    const double pa = s == 0 ? 1.0 : 0.5;
+    const unsigned ma = mask[(int64_t)ay * gf.Wn + ax];
+#pragma unroll 1
+    for (int o = 0; o < 5; ++o) {
+      const int bx = ax + ox[o], by = ay + oy[o];
+      if (bx < 0 || bx > gf.W || by < 0 || by > gf.H) continue;
+      const double sab = fine_S(gf, ax, ay, ox[o], oy[o]);
+      const unsigned mm = ma & mask[(int64_t)by * gf.Wn + bx] & partial;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int LX = X + lx[l], LY = Y + ly[l];
+        if (LX > gc.W || LY > gc.H) continue;
+        const double q = hat_weight(bx - 2 * LX, by - 2 * LY);
+        if (q == 0.0) continue;
+        const double cf = pa * sab * q;
+        full[l] += cf;
+        if (mm) {
+#pragma unroll
+          for (int i = 0; i < N; ++i)
+            if ((mm >> i) & 1u) acc[l][i] += cf;
+        }
+      }
+    }
+  }
+  double *o = op + ((int64_t)Y * gc.Wn + X) * 4 * N;
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int i = 0; i < N; ++i) o[l * N + i] = ((all >> i) & 1u) ? full[l] : acc[l][i];
+}
+
+// S entry (K, K + d) of a stored coarse operator, d in the 7-point pattern.
+template <int N>
+__device__ __forceinline__ double op_entry(const double *op, const Geo &g, int x, int y, int ddx, int ddy, int i) {
+  // C, E, N, NE are stored at the node; W, S, SW at the neighbour.
+  if (ddx == 0 && ddy == 0) return op[((int64_t)y * g.Wn + x) * 4 * N + 0 * N + i];
+  if (ddx == 1 && ddy == 0) return op[((int64_t)y * g.Wn + x) * 4 * N + 1 * N + i];
+  if (ddx == 0 && ddy == 1) return op[((int64_t)y * g.Wn + x) * 4 * N + 2 * N + i];
+  if (ddx == 1 && ddy == 1) return op[((int64_t)y * g.Wn + x) * 4 * N + 3 * N + i];
+  if (ddx == -1 && ddy == 0) return op[((int64_t)y * g.Wn + x - 1) * 4 * N + 1 * N + i];
+  if (ddx == 0 && ddy == -1) return op[((int64_t)(y - 1) * g.Wn + x) * 4 * N + 2 * N + i];
+  return op[((int64_t)(y - 1) * g.Wn + x - 1) * 4 * N + 3 * N + i];  // SW
+}
+
+// Galerkin product of a stored 7-point operator: S_c = P' S_f P.
+template <int N>
+__global__ void __launch_bounds__(kBlock) k_galerkin(const double *__restrict__ opf, Geo gf, Geo gc,
+                                                     double *__restrict__ opc) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
+  if (X > gc.W) return;
+  constexpr int sx[7] = {0, 1, -1, 0, 0, 1, -1};
+  constexpr int sy[7] = {0, 0, 0, 1, -1, 1, -1};
+  constexpr int lx[4] = {0, 1, 0, 1};
+  constexpr int ly[4] = {0, 0, 1, 1};
+  double acc[4][N];
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[l][i] = 0.0;
+#pragma unroll 1
+  for (int s = 0; s < 7; ++s) {
+    const int ax = 2 * X + sx[s], ay = 2 * Y + sy[s];
+    if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
+    const double pa = s == 0 ? 1.0 : 0.5;
+#pragma unroll 1
+    for (int o = 0; o < 7; ++o) {
+      const int bx = ax + sx[o], by = ay + sy[o];
+      if (bx < 0 || bx > gf.W || by < 0 || by > gf.H) continue;
+      double q[4];
+      bool anyq = false;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int LX = X + lx[l], LY = Y + ly[l];
+        q[l] = (LX > gc.W || LY > gc.H) ? 0.0 : hat_weight(bx - 2 * LX, by - 2 * LY);
+        anyq |= q[l] != 0.0;
+      }
+      if (!anyq) continue;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const double sab = pa * op_entry<N>(opf, gf, ax, ay, sx[o], sy[o], i);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) acc[l][i] += sab * q[l];
+      }
+    }
+  }
+  double *o = opc + ((int64_t)Y * gc.Wn + X) * 4 * N;
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int i = 0; i < N; ++i) o[l * N + i] = acc[l][i];
+}
+
+// (S v)_K - S_KK v_K for one phase: the off-diagonal part of a stored operator.
+template <int N>
+__device__ __forceinline__ double op_offdiag(const double *op, const double *v, const Geo &g, int x, int y, int i) {
+  const int64_t n = (int64_t)y * g.Wn + x;
+  double s = 0.0;
+  if (x < g.W) s += op[n * 4 * N + 1 * N + i] * v[(n + 1) * N + i];
+  if (x > 0) s += op[(n - 1) * 4 * N + 1 * N + i] * v[(n - 1) * N + i];
+  if (y < g.H) s += op[n * 4 * N + 2 * N + i] * v[(n + g.Wn) * N + i];
+  if (y > 0) s += op[(n - g.Wn) * 4 * N + 2 * N + i] * v[(n - g.Wn) * N + i];
+  if (x < g.W && y < g.H) s += op[n * 4 * N + 3 * N + i] * v[(n + g.Wn + 1) * N + i];
+  if (x > 0 && y > 0) s += op[(n - g.Wn - 1) * 4 * N + 3 * N + i] * v[(n - g.Wn - 1) * N + i];
+  return s;
+}
+
+// a7: one colour of linear Gauss-Seidel on a coarse level; (x + y) % 3 is a
+// valid 3-colouring of the 7-point (E, W, N, S, NE, SW) pattern.  Rows with
+// a zero diagonal (no free fine node under the basis function) stay 0.
+template <int N>
+__global__ void k_coarse_smooth(const double *__restrict__ op, const double *__restrict__ r, double *__restrict__ v,
+                                Geo g, int color) {
+  const int y = blockIdx.y;
+  const int x0 = ((color - y) % 3 + 3) % 3;
+  const int x = x0 + 3 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (x > g.W) return;
+  const int64_t n = (int64_t)y * g.Wn + x;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const double d = op[n * 4 * N + i];
+    v[n * N + i] = d > 0.0 ? (r[n * N + i] - op_offdiag<N>(op, v, g, x, y, i)) / d : 0.0;
+  }
+}
+
+// Whole-level Gauss-Seidel in one block for small coarsest grids: `sweeps`
+// passes over the 3 colours with a barrier between colours.
+template <int N>
+__global__ void __launch_bounds__(1024) k_coarse_solve_block(const double *__restrict__ op, const double *__restrict__ r, double *__restrict__ v,
+                                     Geo g, int sweeps) {
+  const int64_t n = (int64_t)g.Wn * (g.H + 1);
+  for (int s = 0; s < sweeps; ++s)
+    for (int color = 0; color < 3; ++color) {
+      for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+        const int x = (int)(k % g.Wn), y = (int)(k / g.Wn);
+        if ((x + y) % 3 != color) continue;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const double d = op[k * 4 * N + i];
+          v[k * N + i] = d > 0.0 ? (r[k * N + i] - op_offdiag<N>(op, v, g, x, y, i)) / d : 0.0;
+        }
+      }
+      __syncthreads();
+    }
+}
+
+// t = r - S v on a coarse level.
+template <int N>
+__global__ void k_coarse_resid(const double *__restrict__ op, const double *__restrict__ r,
+                               const double *__restrict__ v, Geo g, double *__restrict__ t) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x > g.W) return;
+  const int64_t n = (int64_t)y * g.Wn + x;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    t[n * N + i] = r[n * N + i] - op[n * 4 * N + i] * v[n * N + i] - op_offdiag<N>(op, v, g, x, y, i);
+}
+
+// P1 prolongation of coarse values to fine node (x, y) (nested right-diagonal
+// meshes: odd-odd fine nodes sit on the coarse SW-NE diagonal).
+template <int N>
+__device__ __forceinline__ void prolong_at(const double *vc, const Geo &gc, int x, int y, double (&o)[N]) {
+  const int X0 = x >> 1, Y0 = y >> 1;
+  double a[N];
+  ldn<double, N>(vc + ((int64_t)Y0 * gc.Wn + X0) * N, o);
+  if ((x & 1) == 0 && (y & 1) == 0) return;
+  const int X1 = X0 + (x & 1), Y1 = Y0 + (y & 1);
+  ldn<double, N>(vc + ((int64_t)Y1 * gc.Wn + X1) * N, a);
+#pragma unroll
+  for (int i = 0; i < N; ++i) o[i] = 0.5 * (o[i] + a[i]);
+}
+
+// v_f += P v_c.
+template <int N>
+__global__ void k_prolong_add(const double *__restrict__ vc, Geo gf, Geo gc, double *__restrict__ vf) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x > gf.W) return;
+  double p[N], o[N];
+  prolong_at<N>(vc, gc, x, y, p);
+  const int64_t n = (int64_t)y * gf.Wn + x;
+  ldn_rw<double, N>(vf + n * N, o);
+#pragma unroll
+  for (int i = 0; i < N; ++i) o[i] += p[i];
+  stn<double, N>(vf + n * N, o);
+}
+
+// ---------------------------------------------------------------------------
+// a8: coarse correction on the fine level with a feasible line search.
+//   w   = tangent projection (over the free phases) of the truncated
+//         prolongation M_i (P v)_i,
+//   d   = P_G(u + w) - u  (feasible direction: K is convex),
+//   omega = clamp(rt'd / d'Sd, 0, 1) minimises the step energy on [u, u + d].
+// k_ls_dir writes d and the block partials of rt'd; k_ls_curv the partials of
+// d'Sd; k_ls_finish computes omega; k_apply does u += omega d.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kBlock) k_ls_dir(const double *__restrict__ u, const double *__restrict__ rt,
+                                                   const double *__restrict__ v1, const uint8_t *__restrict__ mask,
+                                                   Geo gf, Geo gc, double *__restrict__ d, double *__restrict__ part) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  double dot[1] = {0.0};
+  if (x <= gf.W) {
+    const int64_t n = (int64_t)y * gf.Wn + x;
+    const unsigned fr = mask[n];
+    double dn[N];
+    if (fr) {
+      double w[N], uk[N], r[N];
+      prolong_at<N>(v1, gc, x, y, w);
+      double s = 0.0;
+      int cnt = 0;
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if ((fr >> i) & 1u) {
+          s += w[i];
+          ++cnt;
+        }
+      const double mean = s * rcp_small<double>(cnt);
+      ldn<double, N>(u + n * N, uk);
+#pragma unroll
+      for (int i = 0; i < N; ++i) w[i] = uk[i] + (((fr >> i) & 1u) ? w[i] - mean : 0.0);
+      proj_simplex<double, N>(w);
+      ldn<double, N>(rt + n * N, r);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        dn[i] = w[i] - uk[i];
+        dot[0] += r[i] * dn[i];
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; ++i) dn[i] = 0.0;
+    }
+    stn<double, N>(d + n * N, dn);
+  }
+  block_sum_store<1>(dot, part + blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kBlock) k_ls_curv(const double *__restrict__ d, Geo g, double *__restrict__ part) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  double dot[1] = {0.0};
+  if (x <= g.W) {
+    const int64_t n = (int64_t)y * g.Wn + x;
+    double acc[N], dk[N];
+    nbr_sum<double, N>(d, g, x, y, acc);
+    ldn<double, N>(d + n * N, dk);
+    const double D = g.D[node_class(g, x, y)];
+#pragma unroll
+    for (int i = 0; i < N; ++i) dot[0] += dk[i] * (D * dk[i] - g.te * acc[i]);
+  }
+  block_sum_store<1>(dot, part + blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+static __global__ void k_ls_finish(const double *__restrict__ tot, double *__restrict__ omega) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double rd = tot[0], dsd = tot[1];
+  double w = 0.0;
+  if (dsd > 0.0 && rd > 0.0) w = fmin(1.0, rd / dsd);
+  *omega = w;
+}
+
+template <int N>
+__global__ void k_apply(double *__restrict__ u, const double *__restrict__ d, const double *__restrict__ omega,
+                        int64_t n) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double w = *omega;
+  if (w == 0.0) return;
+  double uk[N], dk[N];
+  ldn_rw<double, N>(u + k * N, uk);
+  ldn<double, N>(d + k * N, dk);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    uk[i] += w * dk[i];
+    if (uk[i] < 0.0) uk[i] = 0.0;  // rounding residue of u_i + w (-u_i)
+  }
+  stn<double, N>(u + k * N, uk);
+}
+
+// ---------------------------------------------------------------------------
+// a10: rounded composite (Sec. 4.3).  Node label = argmax_i u_n,i; pixel
+// label = argmax_i (2 u00 + u10 + u01 + 2 u11) (the pixel integral of u_i
+// on the right-diagonal split, times 6); lowest index on ties.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void k_labels(const double *__restrict__ u, Geo g, int8_t *__restrict__ node_lab,
+                         int8_t *__restrict__ pix_lab) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x > g.W) return;
+  const int64_t n = (int64_t)y * g.Wn + x;
+  double a[N];
+  ldn<double, N>(u + n * N, a);
+  if (node_lab) {
+    int best = 0;
+#pragma unroll
+    for (int i = 1; i < N; ++i)
+      if (a[i] > a[best]) best = i;
+    node_lab[n] = (int8_t)best;
+  }
+  if (pix_lab && x < g.W && y < g.H) {
+    double b10[N], b01[N], b11[N];
+    ldn<double, N>(u + (n + 1) * N, b10);
+    ldn<double, N>(u + (n + g.Wn) * N, b01);
+    ldn<double, N>(u + (n + g.Wn + 1) * N, b11);
+    int best = 0;
+    double bv = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const double v = 2.0 * a[i] + b10[i] + b01[i] + 2.0 * b11[i];
+      if (i == 0 || v > bv) {
+        bv = v;
+        best = i;
+      }
+    }
+    pix_lab[(int64_t)y * g.W + x] = (int8_t)best;
+  }
+}
+
+// Kernel-level projection of count independent N-vectors.
+template <int N>
+__global__ void k_project(const double *y, double *x, int64_t count) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  double v[N];
+  ldn_rw<double, N>(y + k * N, v);
+  proj_simplex<double, N>(v);
+  stn<double, N>(x + k * N, v);
+}
+
+}  // namespace ac

@@ -1,0 +1,70 @@
+"""The C ABI without a GPU: the library builds, loads, exports every symbol
+that include/ac.h declares, and rejects invalid arguments before touching the
+device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ac():
+    from paper_0710_0736_gb300 import build
+    build.build()
+    from paper_0710_0736_gb300 import ac as mod
+    return mod
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(ac_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_exports_match_header(ac):
+    declared = _declared()
+    assert declared, "no declarations found"
+    for name in declared:
+        assert hasattr(ac.lib, name), f"{name} declared but not exported"
+    assert declared == set(ac.EXPORTS)
+
+
+def test_default_params(ac):
+    p = ac.ac_default_params(stream=None)
+    assert (p.tol, p.nu1, p.nu2, p.max_cycles, p.coarse_min, p.precision) == (1e-10, 2, 2, 200, 4, ac.AC_FP64)
+
+
+@pytest.mark.parametrize("field,value", [
+    ("width", 0), ("height", -3), ("n_phases", 1), ("n_phases", 9), ("eps", 0.0), ("tau", -1.0),
+    ("lambda_", -0.5), ("tol", 0.0), ("nu1", -1), ("max_cycles", 0), ("coarse_min", 0), ("precision", 7),
+])
+def test_create_rejects_bad_params(ac, field, value):
+    p = ac.ac_default_params(width=8, height=8, n_phases=3, eps=2.0, tau=4.0, stream=None)
+    p.lambda_ = 1.0
+    setattr(p, field, value)
+    ctx = C.c_void_p()
+    assert ac.lib.ac_create(C.byref(ctx), C.byref(p)) == ac.AC_ERR_ARG
+    assert ctx.value is None
+    assert ac.ac_last_error()
+
+
+def test_null_arguments(ac):
+    assert ac.lib.ac_step(None, 1, None) == ac.AC_ERR_ARG
+    assert ac.lib.ac_set_image(None, None, 0) == ac.AC_ERR_ARG
+    assert ac.lib.ac_project_simplex(None, None, 4, 9, None) == ac.AC_ERR_ARG
+    assert ac.lib.ac_project_simplex(None, None, -1, 4, None) == ac.AC_ERR_ARG
+    ac.ac_destroy(None)  # accepted
+
+
+def test_oracle_is_not_linked(ac):
+    """The product library must not depend on the oracle."""
+    import subprocess
+    out = subprocess.run(["nm", "-D", ac._LIB_PATH], capture_output=True, text=True).stdout
+    assert "or_" not in " ".join(l.split()[-1] for l in out.splitlines() if l.split())

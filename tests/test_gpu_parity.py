@@ -1,0 +1,279 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+FP64 form: phase fields within 1e-10 max-abs of the oracle, labels equal
+except where the oracle's top-two margin is below 1e-8 (both answers are then
+valid).  Both sides solve each step to a natural residual of 3e-15 so that the
+comparison measures the method, not the stopping point: the error of a step
+is about 20x its residual, and the explicit 1 + 2 tau/eps factor amplifies
+differences ~1000x over the first 20 steps of a random start.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0710_0736_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TIGHT = 3e-15
+
+
+@pytest.fixture(scope="module")
+def ac():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0710_0736_gb300 import build
+    build.build()
+    from paper_0710_0736_gb300 import ac as mod
+    oracle.build()
+    return mod
+
+
+def _seg(ac, W, H, N, eps=2.0, lam=1.0, tau=4.0, **kw):
+    kw.setdefault("tol", TIGHT)
+    kw.setdefault("max_cycles", 2000)
+    return ac.Segmenter(W, H, N, eps, lam, tau, **kw)
+
+
+def _label_mismatch_ok(u_ref, lab_gpu, lab_ref, W, H, margin=1e-8):
+    """Pixels whose labels differ must be near-ties of the oracle's field."""
+    diff = np.argwhere(lab_gpu != lab_ref)
+    if diff.size == 0:
+        return True
+    N = u_ref.shape[1]
+    U = u_ref.reshape(H + 1, W + 1, N)
+    for py, px in diff:
+        v = 2 * U[py, px] + U[py, px + 1] + U[py + 1, px] + 2 * U[py + 1, px + 1]
+        s = np.sort(v)
+        if s[-1] - s[-2] > 6 * margin:
+            return False
+    return True
+
+
+# --------------------------------------------------------------------------
+# a1, a2, a3, a5: moments, means, right-hand side, energy, projection
+# --------------------------------------------------------------------------
+
+def test_moments_golden_and_c1(ac):
+    img = np.zeros((2, 2, 3))
+    for (px, py), v in {(0, 0): 1.0, (1, 0): 2.0, (0, 1): 4.0, (1, 1): 8.0}.items():
+        img[py, px] = (v, 2 * v, 0)
+    seg = _seg(ac, 2, 2, 2)
+    seg.set_image(img)
+    assert np.abs(seg.moments() - oracle.moments(img)).max() < 1e-15
+    img = synth.config_image("c1_64_n4_fp64", 0).astype(np.float64)
+    seg = _seg(ac, 64, 64, 4)
+    seg.set_image(img)
+    assert np.abs(seg.moments() - oracle.moments(img)).max() < 1e-14
+    seg32 = _seg(ac, 64, 64, 4)
+    seg32.set_image(img.astype(np.float32))          # float32 input path, same values
+    assert np.abs(seg32.moments() - oracle.moments(img)).max() < 1e-14
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8])
+def test_projection_kernel(ac, N):
+    import torch
+    rng = np.random.default_rng(N)
+    Y = rng.normal(0, 1, (50001, N)) * rng.choice([0.01, 1, 10], size=(50001, 1))
+    y = torch.tensor(Y, device="cuda")
+    x = torch.empty_like(y)
+    ac.ac_project_simplex(y, x, Y.shape[0], N)
+    torch.cuda.synchronize()
+    X = x.cpu().numpy()
+    ref, _ = oracle.project_simplex(Y)
+    scale = 1 + np.abs(Y).max(1, keepdims=True)
+    assert (np.abs(X - ref) / scale).max() < 1e-15 * N
+    assert X.min() >= 0
+
+
+def test_means_rhs_energy(ac):
+    W = H = 64
+    img = synth.config_image("c1_64_n4_fp64", 1).astype(np.float64)
+    u0 = synth.dirichlet_init(2, (W + 1) * (H + 1), 4)
+    m = oracle.moments(img)
+    seg = _seg(ac, W, H, 4)
+    seg.set_image(img)
+    seg.set_phase(u0)
+    E_gpu = seg.energy()
+    assert E_gpu == pytest.approx(oracle.energy(u0, m, W, H, 2.0, 1.0), rel=1e-13)
+    seg.step(1)
+    c_ref, _ = oracle.means(u0, m, W, H)
+    assert np.abs(seg.means() - c_ref).max() < 1e-14
+    b_ref = oracle.rhs(u0, m, c_ref, W, H, 2.0, 1.0, 4.0)
+    assert np.abs(seg.rhs() - b_ref).max() < 1e-13
+
+
+# --------------------------------------------------------------------------
+# a4-a9: the step solve
+# --------------------------------------------------------------------------
+
+def test_one_step_c1(ac):
+    W = H = 64
+    img = synth.config_image("c1_64_n4_fp64", 0).astype(np.float64)
+    u0 = synth.dirichlet_init(1, (W + 1) * (H + 1), 4)
+    seg = _seg(ac, W, H, 4)
+    seg.set_image(img)
+    seg.set_phase(u0)
+    st = seg.step(1)
+    assert st.converged and st.residual <= TIGHT
+    u_ref, _, it, rho, stt = oracle.step(u0, oracle.moments(img), np.zeros((4, 3)), W, H, 2.0, 1.0, 4.0, tol=TIGHT,
+                                         nu1=2, nu2=2)
+    assert stt == 0
+    assert np.abs(seg.phase() - u_ref).max() < 1e-12
+    assert seg.residual() <= TIGHT
+
+
+def test_trajectory_c1_20_steps(ac):
+    W = H = 64
+    img = synth.config_image("c1_64_n4_fp64", 0).astype(np.float64)
+    u0 = synth.dirichlet_init(1, (W + 1) * (H + 1), 4)
+    seg = _seg(ac, W, H, 4)
+    seg.set_image(img)
+    seg.set_phase(u0)
+    lab = seg.segment(20)
+    u = seg.phase()
+    u_ref, c_ref, stats = oracle.run(img, u0, 2.0, 1.0, 4.0, 20, tol=TIGHT, nu1=2, nu2=2)
+    assert all(s[2] == 0 for s in stats)
+    assert np.abs(u - u_ref).max() < 1e-10
+    assert np.abs(seg.means() - c_ref).max() < 1e-10
+    _, lab_ref = oracle.labels(u_ref, W, H)
+    assert _label_mismatch_ok(u_ref, lab, lab_ref, W, H)
+    nl_ref, _ = oracle.labels(u_ref, W, H)
+    nl = seg.node_labels()
+    assert (nl != nl_ref).sum() == 0 or _label_mismatch_ok(u_ref, lab, lab_ref, W, H)
+    # labels from the GPU's own field agree exactly with the oracle's rule
+    _, lab_own = oracle.labels(u, W, H)
+    assert np.array_equal(lab, lab_own)
+
+
+@pytest.mark.parametrize("W,H,N", [(37, 23, 3), (1, 1, 2), (2, 1, 4), (1, 5, 8), (48, 40, 2), (96, 64, 8),
+                                   (34, 66, 5), (24, 24, 7), (40, 24, 6)])
+def test_ragged_sizes(ac, W, H, N):
+    """Single-level grids, odd sizes, degenerate 1-pixel-wide images, and grids
+    that coarsen a few times, for every phase count."""
+    img = synth.shapes_image(W * 7 + H, W, H, rect_side=(1, max(1, W // 2)), disk_r=(1, max(1.5, W / 4))).astype(np.float64)
+    u0 = synth.dirichlet_init(W + H, (W + 1) * (H + 1), N)
+    seg = _seg(ac, W, H, N)
+    seg.set_image(img)
+    seg.set_phase(u0)
+    seg.step(3)
+    u_ref, _, stats = oracle.run(img, u0, 2.0, 1.0, 4.0, 3, tol=TIGHT, nu1=2, nu2=2)
+    assert np.abs(seg.phase() - u_ref).max() < 1e-11
+
+
+def test_empty_phase_and_constant_state(ac):
+    W, H, N = 32, 16, 4
+    img = synth.config_image("c1_64_n4_fp64", 3, W, H).astype(np.float64)
+    u0 = synth.dirichlet_init(5, (W + 1) * (H + 1), N)
+    u0[:, 2] = 0
+    u0 /= u0.sum(1, keepdims=True)
+    seg = _seg(ac, W, H, N)
+    seg.set_image(img)
+    seg.set_phase(u0)
+    seg.step(2)
+    u_ref, _, _ = oracle.run(img, u0, 2.0, 1.0, 4.0, 2, tol=TIGHT, nu1=2, nu2=2)
+    assert np.abs(seg.phase() - u_ref).max() < 1e-11
+    # constant image, uniform u: closed form u1 = P_G((1 + 2 tau/eps) u0) at every node
+    img = np.empty((H, W, 3))
+    img[:] = (0.3, 0.6, 0.1)
+    w = np.array([0.26, 0.25, 0.25, 0.24])
+    seg.set_image(img)
+    seg.set_phase(np.tile(w, ((W + 1) * (H + 1), 1)))
+    seg.step(1)
+    want, _ = oracle.project_simplex(w * (1 + 2 * 4.0 / 2.0))
+    assert np.abs(seg.phase() - want).max() < 5e-14
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_exact_segmentation_of_stripes(ac, seed):
+    W, H = 48, 24
+    img = synth.stripes_image(W, H, [8, 12, 10, 18], [(0.9, 0.2, 0.1), (0.1, 0.3, 0.8)])
+    truth = np.broadcast_to(((np.arange(W) >= 8) & (np.arange(W) < 20) | (np.arange(W) >= 30)).astype(np.int8), (H, W))
+    seg = _seg(ac, W, H, 2, tol=1e-12, seed=seed)
+    seg.set_image(img)                      # float32 path + the library's own seeded start
+    lab = seg.segment(30)
+    assert np.array_equal(lab, truth) or np.array_equal(lab, 1 - truth)
+
+
+def test_seeded_init_on_simplex(ac):
+    W, H, N = 64, 48, 6
+    seg = _seg(ac, W, H, N, seed=123)
+    seg.set_image(np.zeros((H, W, 3), np.float32))
+    u = seg.phase()
+    assert np.abs(u.sum(1) - 1).max() < 1e-14 and u.min() > 0
+    assert np.abs(u.mean(0) - 1 / N).max() < 0.01          # Dirichlet(1..1) mean
+    seg2 = _seg(ac, W, H, N, seed=123)
+    seg2.set_image(np.zeros((H, W, 3), np.float32))
+    assert np.array_equal(u, seg2.phase())
+
+
+def test_deterministic_and_device_buffers(ac):
+    import torch
+    W = H = 64
+    img = synth.config_image("c1_64_n4_fp64", 4)
+    outs = []
+    for _ in range(2):
+        seg = _seg(ac, W, H, 4, tol=1e-10, seed=9)
+        seg.set_image(torch.tensor(img, device="cuda"))
+        lab = torch.empty((H, W), dtype=torch.int8, device="cuda")
+        ac.ac_segment(seg.ctx, 5, lab, W, H)
+        torch.cuda.synchronize()
+        outs.append((seg.phase(), lab.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+# --------------------------------------------------------------------------
+# full sizes: properties that hold at any size, checked by the oracle
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,W,steps", [("c2_1024_n4", 1024, 2), ("c3_4096_n8_mixed", 4096, 1)])
+def test_full_size_invariants_and_kkt(ac, name, W, steps):
+    """At the benchmark sizes: after each step sum_i u = 1, 0 <= u <= 1, the
+    energy does not increase, and the oracle's natural residual of the GPU's
+    u^{t+1} against the oracle's b(u^t) is within the step tolerance."""
+    cfg = synth.CONFIGS[name]
+    H = W
+    N, eps, lam, tau = cfg["N"], cfg["eps"], cfg["lam"], cfg["tau"]
+    tol = 1e-8
+    img = synth.config_image(name, 0, W, H)
+    seg = ac.Segmenter(W, H, N, eps, lam, tau, tol=tol, max_cycles=500, seed=1)
+    seg.set_image(img)
+    m = oracle.moments(img.astype(np.float64))
+    u = seg.phase()
+    c = np.zeros((N, 3))
+    E = oracle.energy(u, m, W, H, eps, lam)
+    for _ in range(steps):
+        st = seg.step(1)
+        assert st.converged
+        u1 = seg.phase()
+        assert np.abs(u1.sum(1) - 1).max() < 1e-13
+        assert u1.min() >= 0 and u1.max() <= 1 + 1e-15
+        c, _ = oracle.means(u, m, W, H, c)
+        b = oracle.rhs(u, m, c, W, H, eps, lam, tau)
+        rho = oracle.natural_residual(u1, b, W, H, eps, tau)
+        assert rho <= 2 * tol
+        E1 = oracle.energy(u1, m, W, H, eps, lam)
+        assert E1 <= E + 1e-6 * abs(E)
+        u, E = u1, E1
+
+
+# --------------------------------------------------------------------------
+# error paths
+# --------------------------------------------------------------------------
+
+def test_error_paths(ac):
+    import ctypes as C
+    seg = _seg(ac, 16, 16, 3)
+    assert ac.lib.ac_step(seg.ctx, 1, None) == ac.AC_ERR_STATE
+    img = np.full((16, 16, 3), 0.5, np.float32)
+    img[3, 4, 1] = np.nan
+    seg.set_image(img)
+    assert ac.lib.ac_step(seg.ctx, 1, None) == ac.AC_ERR_NUMERIC
+    seg2 = _seg(ac, 16, 16, 3, tol=1e-300, max_cycles=2)
+    seg2.set_image(np.full((16, 16, 3), 0.5, np.float32))
+    st = ac.ac_stats()
+    assert ac.lib.ac_step(seg2.ctx, 2, C.byref(st)) == ac.AC_ERR_NOT_CONVERGED
+    assert st.steps == 2 and st.converged == 0
+    u = seg2.phase()
+    assert np.abs(u.sum(1) - 1).max() < 1e-14 and u.min() >= 0  # still feasible
