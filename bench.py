@@ -1,0 +1,299 @@
+#!/usr/bin/env python3
+"""Benchmark of the vector-valued Allen-Cahn time step on GB300.
+
+Workload (default): the 4096 x 4096 RGB Voronoi-ramp image (8 regions, ramps
+<= 0.2, noise sigma 0.05), N = 8 phases, eps = 3, lambda = 2, tau = 9, each
+time step solved to a natural residual of 1e-6.  A "step" is one time step:
+colour means + energy, right-hand side, and V-cycles until the tolerance.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference ...   # the CPU oracle on the same workload
+
+One JSON line on rank 0.  value = time steps per second of the whole job
+(replicas: every rank advances its own image, no exchange).  The timed region
+is K steps bracketed by a barrier and a device synchronize, timed with CUDA
+events on the solver's stream; the phase field (1.07 GB in FP64) is larger
+than L2, so no flush is needed between steps.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Allen-Cahn steps/s & GDOF/s at 4096² N=8; % HBM peak; vs plain FP64 GPU"
+WORKLOAD = "c3_4096_n8_mixed"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--tol", type=float, default=None)
+    ap.add_argument("--crop", type=int, default=256, help="side of the image crop the CPU oracle times")
+    ap.add_argument("--cpu-steps", type=int, default=3, help="oracle steps in the cpu_baseline sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_0710_0736_gb300 import synth
+    cfg = dict(synth.CONFIGS[WORKLOAD])
+    cfg["W"] = cfg["H"] = args.size
+    if args.tol is not None:
+        cfg["tol"] = args.tol
+    return cfg
+
+
+def workload_config(cfg, args, extra=None):
+    d = {
+        "workload": f"{cfg['W']}x{cfg['H']} RGB Voronoi-ramp image (8 regions, ramp<=0.2, noise 0.05), "
+                    f"N={cfg['N']}, eps={cfg['eps']}, lambda={cfg['lam']}, tau={cfg['tau']}, "
+                    f"V({2},{2}) to natural residual {cfg['tol']:g}",
+        "nodes": (cfg["W"] + 1) * (cfg["H"] + 1),
+        "n_phases": cfg["N"],
+        "precision": args.precision,
+        "tol": cfg["tol"],
+        "l2": "no flush: the phase field and right-hand side (1.07 GB each in FP64) exceed the 129 MB L2",
+    }
+    if extra:
+        d.update(extra)
+    return d
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(io.StringIO(out)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                smax = float(row[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, row[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# --------------------------------------------------------------------------
+
+def oracle_sample(cfg, crop, steps, seed=0):
+    """Time `steps` oracle steps (paper-literal SSC, V(2,2)) on the top-left
+    crop x crop corner of the workload image; returns per-step seconds."""
+    import oracle
+    from paper_0710_0736_gb300 import synth
+    oracle.build()
+    img = synth.config_image(WORKLOAD, seed, cfg["W"], cfg["H"])[:crop, :crop].astype(np.float64)
+    m = oracle.moments(img)
+    u = synth.dirichlet_init(seed, (crop + 1) ** 2, cfg["N"])
+    c = np.zeros((cfg["N"], 3))
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        u, c, it, rho, st = oracle.step(u, m, c, crop, crop, cfg["eps"], cfg["lam"], cfg["tau"], tol=cfg["tol"],
+                                        nu1=2, nu2=2, max_iter=1000)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfg = workload(args)
+    times = oracle_sample(cfg, args.crop, args.warmup + args.steps)
+    timed = times[args.warmup:]
+    full_nodes = (cfg["W"] + 1) * (cfg["H"] + 1)
+    crop_nodes = (args.crop + 1) ** 2
+    sec_full = float(np.mean(timed)) * full_nodes / crop_nodes  # the method's cost is linear in the nodes
+    value = 1.0 / sec_full
+    sample = (f"{args.steps} oracle steps (SSC, V(2,2), tol {cfg['tol']:g}) on the {args.crop}x{args.crop} corner "
+              f"of the workload image after {args.warmup} untimed, scaled by nodes {full_nodes}/{crop_nodes}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_full * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(cfg, args, {"precision": "fp64"}),
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_0710_0736_gb300 import ac, synth
+
+    cfg = workload(args)
+    W, H, N = cfg["W"], cfg["H"], cfg["N"]
+    n_nodes = (W + 1) * (H + 1)
+    prec = ac.AC_FP64 if args.precision == "fp64" else ac.AC_MIXED
+    img = synth.config_image(WORKLOAD, rank, W, H)
+    stream = torch.cuda.current_stream()
+    seg = ac.Segmenter(W, H, N, cfg["eps"], cfg["lam"], cfg["tau"], tol=cfg["tol"], max_cycles=1000, seed=rank,
+                       precision=prec, stream=stream.cuda_stream)
+    seg.set_image(torch.from_numpy(img).cuda())
+    seg.step(args.warmup, allow_not_converged=True)
+
+    ac.ac_set_profiling(seg.ctx, True)
+    launches0 = ac.ac_get_profile(seg.ctx).total_launches
+    clocks = Clocks(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    rc, st = ac.ac_step(seg.ctx, args.steps, allow_not_converged=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = ac.ac_get_profile(seg.ctx)
+    ac.ac_set_profiling(seg.ctx, False)
+    launches = prof.total_launches - launches0
+
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    sw = torch.tensor([float(st.fine_sweeps)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(sw, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    value = world * args.steps / (ms_max / 1e3)
+    gdof = N * n_nodes * float(sw.item()) / (ms_max / 1e3) / 1e9
+
+    # roofline of the dominant kernel: the fine red-black smoother
+    peaks, peak_kind = measured_peaks()
+    sm_launches = prof.launches[ac.PROF_CLASSES.index("smooth")]
+    sm_ms = prof.ms[ac.PROF_CLASSES.index("smooth")]
+    avg_launch_s = sm_ms / 1e3 / max(1, sm_launches)
+    achieved = prof.smooth_bytes_per_launch / avg_launch_s / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_smooth_fine (one colour of a red-black projected sweep)",
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
+                "bytes_per_launch": prof.smooth_bytes_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
+                "share_of_step_time": sm_ms / max(1e-9, ms)}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_img = torch.from_numpy(img).pin_memory()
+        labels = torch.empty((H, W), dtype=torch.int8).pin_memory()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ac.ac_set_image(seg.ctx, host_img, W, H)
+        for _ in range(args.steps):
+            ac.ac_segment(seg.ctx, 1, labels, W, H, allow_not_converged=True)
+        torch.cuda.synchronize()
+        el = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(el, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * args.steps / float(el.item()), "unit": "steps/s",
+               "h2d_bytes_per_step": host_img.numel() * 4 / args.steps, "d2h_bytes_per_step": labels.numel(),
+               "path": "ac_set_image from pinned host memory once, then per step ac_segment(1 step) with the "
+                       "pixel labels read back to pinned host memory"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        times = oracle_sample(cfg, args.crop, args.cpu_steps)
+        full_nodes, crop_nodes = n_nodes, (args.crop + 1) ** 2
+        cpu = {"value": 1.0 / (float(np.mean(times)) * full_nodes / crop_nodes), "unit": "steps/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"{args.cpu_steps} oracle steps (SSC, V(2,2), tol {cfg['tol']:g}) on the {args.crop}x"
+                         f"{args.crop} corner of the workload image, {sum(times):.1f} s, scaled by nodes "
+                         f"{full_nodes}/{crop_nodes}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+                "data": "synthetic",
+                "config": workload_config(cfg, args, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+                "gdof_per_s": gdof, "vcycles_per_step": st.total_cycles / max(1, st.steps),
+                "fine_sweeps_per_step": st.fine_sweeps / max(1, st.steps), "residual": st.residual,
+                "all_converged": bool(st.converged), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk,
+                "profile_ms": dict(zip(ac.PROF_CLASSES, [round(v, 3) for v in prof.ms]))}
+        print(json.dumps(line), flush=True)
+    seg.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -81,7 +81,26 @@ typedef struct {
   int total_cycles;    /* V-cycles over all steps of the call */
   int steps;           /* time steps done by the call */
   int converged;       /* 1 if every step of the call reached tol */
+  int64_t fine_sweeps; /* red-black projected sweeps on the fine level over the call */
 } ac_stats;
+
+/* Kernel classes of the profile (no counterpart in the paper: instrumentation). */
+enum {
+  AC_PROF_SMOOTH = 0,  /* fine red-black projected Gauss-Seidel, one launch per colour */
+  AC_PROF_RESID,       /* fine residual, natural residual, mask, tangent projection */
+  AC_PROF_COARSE,      /* coarse-level smoothing, residuals and coarsest solve */
+  AC_PROF_TRANSFER,    /* truncated Galerkin operators, restriction, prolongation */
+  AC_PROF_LINESEARCH,  /* coarse-correction direction, line search, update */
+  AC_PROF_SETUP,       /* colour means, energy and right-hand side of a step */
+  AC_PROF_COUNT
+};
+
+typedef struct {
+  double ms[AC_PROF_COUNT];        /* summed device time per class (CUDA events on the context's stream) */
+  int64_t launches[AC_PROF_COUNT]; /* kernel launches per class while profiling was on */
+  double smooth_bytes_per_launch;  /* algorithmic HBM bytes of one smoother launch: 1.5 n N sizeof(scalar) */
+  int64_t total_launches;          /* every kernel launched by this context since creation */
+} ac_profile;
 
 /* Defaults: tol 1e-10, nu1 = nu2 = 2, max_cycles 200, coarse_min 4, AC_FP64,
  * seed 0, stream NULL; size, N, eps, lambda and tau are left 0. */
@@ -144,6 +163,16 @@ int ac_residual(ac_ctx *ctx, double *rho);
  * the clamp-and-redistribute loop of Sec. 3.3 reaches in <= N passes.  x
  * (device, count x N) may alias y.  Ordered on stream. */
 int ac_project_simplex(const double *y, double *x, int64_t count, int n_phases, void *stream);
+
+/* ---- instrumentation (no counterpart in the paper) ------------------------ */
+
+/* Turn per-class kernel timing on (1) or off (0) and clear the accumulated
+ * profile.  While on, every kernel group is bracketed by CUDA events on the
+ * context's stream. */
+int ac_set_profiling(ac_ctx *ctx, int enable);
+/* Synchronise the stream and return the profile accumulated since the last
+ * ac_set_profiling call (total_launches counts from creation). */
+int ac_get_profile(ac_ctx *ctx, ac_profile *out);
 
 /* Description of the last error on the calling thread ("" if none). */
 const char *ac_last_error(void);

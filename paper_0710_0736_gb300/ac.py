@@ -21,8 +21,9 @@ AC_MAX_PHASES = 8
 EXPORTS = [
     "ac_default_params", "ac_create", "ac_set_image", "ac_set_image_f64", "ac_step", "ac_segment", "ac_destroy",
     "ac_set_phase", "ac_get_phase", "ac_get_means", "ac_get_moments", "ac_get_rhs", "ac_get_node_labels",
-    "ac_energy", "ac_residual", "ac_project_simplex", "ac_last_error",
+    "ac_energy", "ac_residual", "ac_project_simplex", "ac_set_profiling", "ac_get_profile", "ac_last_error",
 ]
+PROF_CLASSES = ["smooth", "resid", "coarse", "transfer", "linesearch", "setup"]
 
 
 class ac_params(C.Structure):
@@ -34,10 +35,22 @@ class ac_params(C.Structure):
 
 class ac_stats(C.Structure):
     _fields_ = [("energy", C.c_double), ("residual", C.c_double), ("cycles", C.c_int),
-                ("total_cycles", C.c_int), ("steps", C.c_int), ("converged", C.c_int)]
+                ("total_cycles", C.c_int), ("steps", C.c_int), ("converged", C.c_int),
+                ("fine_sweeps", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ac_profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 6), ("launches", C.c_int64 * 6), ("smooth_bytes_per_launch", C.c_double),
+                ("total_launches", C.c_int64)]
+
+    def as_dict(self):
+        return {"ms": dict(zip(PROF_CLASSES, list(self.ms))),
+                "launches": dict(zip(PROF_CLASSES, list(self.launches))),
+                "smooth_bytes_per_launch": self.smooth_bytes_per_launch,
+                "total_launches": self.total_launches}
 
 
 class AcError(RuntimeError):
@@ -69,6 +82,8 @@ def _load():
         "ac_energy": ([vp, P(d)], i),
         "ac_residual": ([vp, P(d)], i),
         "ac_project_simplex": ([vp, vp, i64, i, vp], i),
+        "ac_set_profiling": ([vp, i], i),
+        "ac_get_profile": ([vp, P(ac_profile)], i),
         "ac_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -214,6 +229,16 @@ def ac_project_simplex(y, x, count, N, stream=None):
     if not (dy and dx):
         raise ValueError("ac_project_simplex takes device tensors")
     return _check(lib.ac_project_simplex(py, px, count, N, stream if stream is not None else _current_stream()))
+
+
+def ac_set_profiling(ctx, enable=True):
+    return _check(lib.ac_set_profiling(ctx, int(bool(enable))))
+
+
+def ac_get_profile(ctx) -> ac_profile:
+    p = ac_profile()
+    _check(lib.ac_get_profile(ctx, C.byref(p)))
+    return p
 
 
 def ac_last_error() -> str:

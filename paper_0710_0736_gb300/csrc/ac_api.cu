@@ -108,6 +108,15 @@ struct ac_ctx {
   double *h_scalars = nullptr;  // pinned: rho, energy
   bool have_image = false, have_rhs = false;
   std::vector<void *> allocs;
+  // instrumentation
+  int64_t total_launches = 0;
+  bool profiling = false;
+  struct Pending { cudaEvent_t a, b; int cls; };
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<Pending> pending;
+  double prof_ms[AC_PROF_COUNT] = {};
+  int64_t prof_launches[AC_PROF_COUNT] = {};
 };
 
 namespace {
@@ -146,6 +155,63 @@ int validate(const ac_params *p) {
   return AC_OK;
 }
 
+// Sum the finished event pairs into the profile and recycle the events.
+int prof_harvest(ac_ctx *ctx) {
+  if (ctx->pending.empty()) return AC_OK;
+  AC_CUDA(cudaStreamSynchronize(ctx->s));
+  for (const auto &p : ctx->pending) {
+    float ms = 0.f;
+    AC_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+    ctx->prof_ms[p.cls] += ms;
+  }
+  ctx->pending.clear();
+  ctx->ev_used = 0;
+  return AC_OK;
+}
+
+int prof_event(ac_ctx *ctx, cudaEvent_t *e) {
+  if (ctx->ev_used == ctx->ev_pool.size()) {
+    cudaEvent_t ev;
+    AC_CUDA(cudaEventCreate(&ev));
+    ctx->ev_pool.push_back(ev);
+  }
+  *e = ctx->ev_pool[ctx->ev_used++];
+  return AC_OK;
+}
+
+// Run one launcher call: count its kernels, check the launch, and bracket it
+// with events on the context's stream while profiling.
+template <class F>
+int timed(ac_ctx *ctx, int cls, F &&f) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (ctx->profiling) {
+    if (ctx->pending.size() >= (1u << 15)) {
+      int rc = prof_harvest(ctx);
+      if (rc) return rc;
+    }
+    int rc = prof_event(ctx, &a);
+    if (!rc) rc = prof_event(ctx, &b);
+    if (rc) return rc;
+    AC_CUDA(cudaEventRecord(a, ctx->s));
+  }
+  const int k = f();
+  ctx->total_launches += k;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(AC_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+  if (ctx->profiling) {
+    AC_CUDA(cudaEventRecord(b, ctx->s));
+    ctx->pending.push_back({a, b, cls});
+    ctx->prof_launches[cls] += k;
+  }
+  return AC_OK;
+}
+
+#define AC_RUN(cls, expr)                                       \
+  do {                                                          \
+    int rc_ = timed(ctx, (cls), [&]() { return (expr); });      \
+    if (rc_) return rc_;                                        \
+  } while (0)
+
 int read_rho(ac_ctx *ctx, double *out) {
   AC_CUDA(cudaMemcpyAsync(ctx->h_scalars, ctx->rho, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
   AC_CUDA(cudaStreamSynchronize(ctx->s));
@@ -161,22 +227,19 @@ int coarse_vcycle(ac_ctx *ctx, int k) {
   AC_CUDA(cudaMemsetAsync(L.v, 0, L.n * ctx->N * sizeof(double), ctx->s));
   if (k == (int)ctx->lv.size() - 1) {
     if (L.n <= kCoarsestBlockNodes)
-      o->coarse_solve(L.op, L.r, L.v, L.g, kCoarsestSweeps, ctx->s);
+      AC_RUN(AC_PROF_COARSE, o->coarse_solve(L.op, L.r, L.v, L.g, kCoarsestSweeps, ctx->s));
     else
-      o->coarse_smooth(L.op, L.r, L.v, L.g, 2 * kCoarseSweeps, ctx->s);
-    AC_LAUNCHED();
+      AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.g, 2 * kCoarseSweeps, ctx->s));
     return AC_OK;
   }
   Level &C = ctx->lv[k + 1];
-  o->coarse_smooth(L.op, L.r, L.v, L.g, kCoarseSweeps, ctx->s);
-  o->coarse_resid(L.op, L.r, L.v, L.g, L.t, ctx->s);
-  o->restrict_(L.t, L.g, C.g, C.r, ctx->s);
-  AC_LAUNCHED();
+  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.g, kCoarseSweeps, ctx->s));
+  AC_RUN(AC_PROF_COARSE, o->coarse_resid(L.op, L.r, L.v, L.g, L.t, ctx->s));
+  AC_RUN(AC_PROF_TRANSFER, o->restrict_(L.t, L.g, C.g, C.r, ctx->s));
   int rc = coarse_vcycle(ctx, k + 1);
   if (rc) return rc;
-  o->prolong_add(C.v, L.g, C.g, L.v, ctx->s);
-  o->coarse_smooth(L.op, L.r, L.v, L.g, kCoarseSweeps, ctx->s);
-  AC_LAUNCHED();
+  AC_RUN(AC_PROF_TRANSFER, o->prolong_add(C.v, L.g, C.g, L.v, ctx->s));
+  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.g, kCoarseSweeps, ctx->s));
   return AC_OK;
 }
 
@@ -190,18 +253,20 @@ int coarse_vcycle(ac_ctx *ctx, int k) {
 // Every stage leaves u on the simplex and does not raise the step energy, so
 // the limit is the unique minimiser that plain projected Gauss-Seidel (the
 // smoother alone) reaches.
-int solve_step(ac_ctx *ctx, int *cycles_out, double *rho_out) {
+int solve_step(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_out) {
   const ac::Ops *o = ctx->ops;
   const ac::Geo &g0 = ctx->lv[0].g;
   const bool coarse = ctx->lv.size() > 1;
   double rho = 0;
   int cyc = 0, status = AC_ERR_NOT_CONVERGED;
+  int64_t sweeps = 0;
   for (;;) {
-    if (cyc > 0 && coarse) o->apply(ctx->u, ctx->d, ctx->omega, ctx->n, ctx->s);
-    o->smooth_fine(ctx->u, ctx->b, g0, cyc == 0 ? ctx->p.nu1 : ctx->p.nu1 + ctx->p.nu2, ctx->s);
+    if (cyc > 0 && coarse) AC_RUN(AC_PROF_LINESEARCH, o->apply(ctx->u, ctx->d, ctx->omega, ctx->n, ctx->s));
+    const int nsw = cyc == 0 ? ctx->p.nu1 : ctx->p.nu1 + ctx->p.nu2;
+    AC_RUN(AC_PROF_SMOOTH, o->smooth_fine(ctx->u, ctx->b, g0, nsw, ctx->s));
+    sweeps += nsw;
     AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
-    o->fine_resid(ctx->u, ctx->b, g0, ctx->rt, ctx->mask, ctx->rho, ctx->s);
-    AC_LAUNCHED();
+    AC_RUN(AC_PROF_RESID, o->fine_resid(ctx->u, ctx->b, g0, ctx->rt, ctx->mask, ctx->rho, ctx->s));
     ++cyc;
     int rc = read_rho(ctx, &rho);
     if (rc) return rc;
@@ -216,18 +281,18 @@ int solve_step(ac_ctx *ctx, int *cycles_out, double *rho_out) {
     if (cyc >= ctx->p.max_cycles) break;
     if (!coarse) continue;
     Level &L1 = ctx->lv[1];
-    o->galerkin0(ctx->mask, g0, L1.g, L1.op, ctx->s);
+    AC_RUN(AC_PROF_TRANSFER, o->galerkin0(ctx->mask, g0, L1.g, L1.op, ctx->s));
     for (size_t k = 1; k + 1 < ctx->lv.size(); ++k)
-      o->galerkin(ctx->lv[k].op, ctx->lv[k].g, ctx->lv[k + 1].g, ctx->lv[k + 1].op, ctx->s);
-    o->restrict_(ctx->rt, g0, L1.g, L1.r, ctx->s);
-    AC_LAUNCHED();
+      AC_RUN(AC_PROF_TRANSFER, o->galerkin(ctx->lv[k].op, ctx->lv[k].g, ctx->lv[k + 1].g, ctx->lv[k + 1].op, ctx->s));
+    AC_RUN(AC_PROF_TRANSFER, o->restrict_(ctx->rt, g0, L1.g, L1.r, ctx->s));
     rc = coarse_vcycle(ctx, 1);
     if (rc) return rc;
-    o->line_search(ctx->u, ctx->rt, L1.v, ctx->mask, g0, L1.g, ctx->d, ctx->ls_part, ctx->ls_tot, ctx->omega, ctx->s);
-    AC_LAUNCHED();
+    AC_RUN(AC_PROF_LINESEARCH, o->line_search(ctx->u, ctx->rt, L1.v, ctx->mask, g0, L1.g, ctx->d, ctx->ls_part,
+                                              ctx->ls_tot, ctx->omega, ctx->s));
   }
   *cycles_out = cyc;
   *rho_out = rho;
+  *sweeps_out = sweeps;
   if (status == AC_ERR_NOT_CONVERGED) fail(status, "step did not reach tol %.3g in %d cycles (rho %.3g)", ctx->p.tol, cyc, rho);
   return status;
 }
@@ -325,6 +390,7 @@ void ac_destroy(ac_ctx *ctx) {
   if (!ctx) return;
   if (ctx->s) cudaStreamSynchronize(ctx->s);
   else cudaDeviceSynchronize();
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   for (void *p : ctx->allocs) cudaFree(p);
   if (ctx->img) cudaFree(ctx->img);
   if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
@@ -352,11 +418,10 @@ static int set_image_impl(ac_ctx *ctx, const void *rgb, int is_device, bool f64)
     src = ctx->img;
   }
   if (f64)
-    ctx->ops->moments_f64((const double *)src, g, ctx->mom, ctx->s);
+    AC_RUN(AC_PROF_SETUP, ctx->ops->moments_f64((const double *)src, g, ctx->mom, ctx->s));
   else
-    ctx->ops->moments_f32((const float *)src, g, ctx->mom, ctx->s);
-  ctx->ops->init_random(ctx->u, ctx->n, ctx->p.seed, ctx->s);
-  AC_LAUNCHED();
+    AC_RUN(AC_PROF_SETUP, ctx->ops->moments_f32((const float *)src, g, ctx->mom, ctx->s));
+  AC_RUN(AC_PROF_SETUP, ctx->ops->init_random(ctx->u, ctx->n, ctx->p.seed, ctx->s));
   AC_CUDA(cudaMemsetAsync(ctx->c, 0, (size_t)3 * ctx->N * sizeof(double), ctx->s));
   if (!is_device) AC_CUDA(cudaStreamSynchronize(ctx->s));  // the host buffer may be reused after return
   ctx->have_image = true;
@@ -376,14 +441,15 @@ int ac_step(ac_ctx *ctx, int n_steps, ac_stats *out) {
   int status = AC_OK;
   const double a1 = 1.0 + 2.0 * ctx->p.tau / ctx->p.eps, tl = ctx->p.tau * ctx->p.lambda;
   for (int t = 0; t < n_steps; ++t) {
-    ctx->ops->means(ctx->u, ctx->mom, ctx->lv[0].g, ctx->part, ctx->tot, ctx->c, ctx->energy, ctx->p.eps,
-                    ctx->p.lambda, ctx->s);
-    ctx->ops->rhs(ctx->u, ctx->mom, ctx->c, ctx->lv[0].g, a1, tl, ctx->b, ctx->s);
-    AC_LAUNCHED();
+    AC_RUN(AC_PROF_SETUP, ctx->ops->means(ctx->u, ctx->mom, ctx->lv[0].g, ctx->part, ctx->tot, ctx->c, ctx->energy,
+                                          ctx->p.eps, ctx->p.lambda, ctx->s));
+    AC_RUN(AC_PROF_SETUP, ctx->ops->rhs(ctx->u, ctx->mom, ctx->c, ctx->lv[0].g, a1, tl, ctx->b, ctx->s));
     ctx->have_rhs = true;
     int cycles = 0;
     double rho = 0;
-    int rc = solve_step(ctx, &cycles, &rho);
+    int64_t sweeps = 0;
+    int rc = solve_step(ctx, &cycles, &rho, &sweeps);
+    st.fine_sweeps += sweeps;
     st.cycles = cycles;
     st.total_cycles += cycles;
     st.residual = rho;
@@ -414,8 +480,7 @@ int ac_segment(ac_ctx *ctx, int n_steps, int8_t *pixel_labels, int is_device, ac
   const size_t bytes = (size_t)g.W * g.H;
   int8_t *dst = pixel_labels;
   if (!is_device) dst = reinterpret_cast<int8_t *>(ctx->rt);  // scratch large enough for W*H bytes
-  ctx->ops->labels(ctx->u, g, nullptr, dst, ctx->s);
-  AC_LAUNCHED();
+  AC_RUN(AC_PROF_SETUP, ctx->ops->labels(ctx->u, g, nullptr, dst, ctx->s));
   if (!is_device) {
     int rc2 = copy_out(ctx, pixel_labels, dst, bytes, 0);
     if (rc2) return rc2;
@@ -467,8 +532,7 @@ int ac_get_rhs(ac_ctx *ctx, double *b) {
 int ac_get_node_labels(ac_ctx *ctx, int8_t *labels, int is_device) {
   if (!ctx || !labels) return fail(AC_ERR_ARG, "NULL argument");
   int8_t *dst = is_device ? labels : reinterpret_cast<int8_t *>(ctx->rt);
-  ctx->ops->labels(ctx->u, ctx->lv[0].g, dst, nullptr, ctx->s);
-  AC_LAUNCHED();
+  AC_RUN(AC_PROF_SETUP, ctx->ops->labels(ctx->u, ctx->lv[0].g, dst, nullptr, ctx->s));
   if (!is_device) return copy_out(ctx, labels, dst, (size_t)ctx->n, 0);
   return AC_OK;
 }
@@ -477,9 +541,8 @@ int ac_energy(ac_ctx *ctx, double *energy) {
   if (!ctx || !energy) return fail(AC_ERR_ARG, "NULL argument");
   if (!ctx->have_image) return fail(AC_ERR_STATE, "no image");
   AC_CUDA(cudaMemcpyAsync(ctx->c_tmp, ctx->c, (size_t)3 * ctx->N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
-  ctx->ops->means(ctx->u, ctx->mom, ctx->lv[0].g, ctx->part, ctx->tot, ctx->c_tmp, ctx->energy, ctx->p.eps,
-                  ctx->p.lambda, ctx->s);
-  AC_LAUNCHED();
+  AC_RUN(AC_PROF_SETUP, ctx->ops->means(ctx->u, ctx->mom, ctx->lv[0].g, ctx->part, ctx->tot, ctx->c_tmp,
+                                        ctx->energy, ctx->p.eps, ctx->p.lambda, ctx->s));
   return copy_out(ctx, energy, ctx->energy, sizeof(double), 0);
 }
 
@@ -487,8 +550,7 @@ int ac_residual(ac_ctx *ctx, double *rho) {
   if (!ctx || !rho) return fail(AC_ERR_ARG, "NULL argument");
   if (!ctx->have_rhs) return fail(AC_ERR_STATE, "no step taken yet");
   AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
-  ctx->ops->fine_resid(ctx->u, ctx->b, ctx->lv[0].g, nullptr, nullptr, ctx->rho, ctx->s);
-  AC_LAUNCHED();
+  AC_RUN(AC_PROF_RESID, ctx->ops->fine_resid(ctx->u, ctx->b, ctx->lv[0].g, nullptr, nullptr, ctx->rho, ctx->s));
   return read_rho(ctx, rho);
 }
 
@@ -498,6 +560,31 @@ int ac_project_simplex(const double *y, double *x, int64_t count, int n_phases, 
   if (count < 0 || (count > 0 && (!y || !x))) return fail(AC_ERR_ARG, "bad buffers");
   o->project(y, x, count, (cudaStream_t)stream);
   AC_LAUNCHED();
+  return AC_OK;
+}
+
+int ac_set_profiling(ac_ctx *ctx, int enable) {
+  if (!ctx) return fail(AC_ERR_ARG, "ctx is NULL");
+  int rc = prof_harvest(ctx);
+  if (rc) return rc;
+  for (int k = 0; k < AC_PROF_COUNT; ++k) {
+    ctx->prof_ms[k] = 0;
+    ctx->prof_launches[k] = 0;
+  }
+  ctx->profiling = enable != 0;
+  return AC_OK;
+}
+
+int ac_get_profile(ac_ctx *ctx, ac_profile *out) {
+  if (!ctx || !out) return fail(AC_ERR_ARG, "NULL argument");
+  int rc = prof_harvest(ctx);
+  if (rc) return rc;
+  for (int k = 0; k < AC_PROF_COUNT; ++k) {
+    out->ms[k] = ctx->prof_ms[k];
+    out->launches[k] = ctx->prof_launches[k];
+  }
+  out->smooth_bytes_per_launch = 1.5 * (double)ctx->n * ctx->N * sizeof(double);
+  out->total_launches = ctx->total_launches;
   return AC_OK;
 }
 

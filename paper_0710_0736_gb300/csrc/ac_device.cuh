@@ -227,8 +227,8 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// max that propagates NaN (a comparison with NaN is false).
-__device__ __forceinline__ double nanmax(double a, double b) { return (b <= a) ? a : b; }
+// max that propagates a NaN held in either argument.
+__device__ __forceinline__ double nanmax(double a, double b) { return (a != a || b <= a) ? a : b; }
 
 __device__ __forceinline__ double warp_nanmax(double v) {
 #pragma unroll

@@ -59,16 +59,19 @@ def test_moments_golden_and_c1(ac):
     img = np.zeros((2, 2, 3))
     for (px, py), v in {(0, 0): 1.0, (1, 0): 2.0, (0, 1): 4.0, (1, 1): 8.0}.items():
         img[py, px] = (v, 2 * v, 0)
+    def close(a, b):  # a few ulps of the value (sums in another order)
+        return (np.abs(a - b) <= 4e-16 * np.maximum(1.0, np.abs(b))).all()
+
     seg = _seg(ac, 2, 2, 2)
     seg.set_image(img)
-    assert np.abs(seg.moments() - oracle.moments(img)).max() < 1e-15
+    assert close(seg.moments(), oracle.moments(img))
     img = synth.config_image("c1_64_n4_fp64", 0).astype(np.float64)
     seg = _seg(ac, 64, 64, 4)
     seg.set_image(img)
-    assert np.abs(seg.moments() - oracle.moments(img)).max() < 1e-14
+    assert close(seg.moments(), oracle.moments(img))
     seg32 = _seg(ac, 64, 64, 4)
     seg32.set_image(img.astype(np.float32))          # float32 input path, same values
-    assert np.abs(seg32.moments() - oracle.moments(img)).max() < 1e-14
+    assert close(seg32.moments(), oracle.moments(img))
 
 
 @pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8])
