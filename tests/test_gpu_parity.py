@@ -59,8 +59,8 @@ def test_moments_golden_and_c1(ac):
     img = np.zeros((2, 2, 3))
     for (px, py), v in {(0, 0): 1.0, (1, 0): 2.0, (0, 1): 4.0, (1, 1): 8.0}.items():
         img[py, px] = (v, 2 * v, 0)
-    def close(a, b):  # a few ulps of the value (sums in another order)
-        return (np.abs(a - b) <= 4e-16 * np.maximum(1.0, np.abs(b))).all()
+    def close(a, b):  # ~9 ulps: six-term sums in another order, with FMA contraction on the GPU
+        return (np.abs(a - b) <= 2e-15 * np.maximum(1.0, np.abs(b))).all()
 
     seg = _seg(ac, 2, 2, 2)
     seg.set_image(img)
