@@ -41,7 +41,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="steps of the plain FP64 form timed for the vs-FP64 ratio (0: skip)")
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--crop", type=int, default=256, help="side of the image crop the CPU oracle times")
@@ -241,7 +243,8 @@ def main():
     sm_ms = prof.ms[ac.PROF_CLASSES.index("smooth")]
     avg_launch_s = sm_ms / 1e3 / max(1, sm_launches)
     achieved = prof.smooth_bytes_per_launch / avg_launch_s / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_smooth_fine (one colour of a red-black projected sweep)",
+    kname = "k_smooth_fine<float,N,shifted>" if args.precision == "mixed" else "k_smooth_fine<double,N,direct>"
+    roofline = {"bound": "hbm", "kernel": kname + " (one colour of a red-black projected sweep)",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                 "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
                 "bytes_per_launch": prof.smooth_bytes_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
@@ -267,6 +270,29 @@ def main():
                "path": "ac_set_image from pinned host memory once, then per step ac_segment(1 step) with the "
                        "pixel labels read back to pinned host memory"}
 
+    # the plain FP64 form on the same workload, for the mixed/FP64 ratio
+    fp64 = None
+    if args.precision == "mixed" and args.fp64_steps > 0:
+        seg.close()
+        seg64 = ac.Segmenter(W, H, N, cfg["eps"], cfg["lam"], cfg["tau"], tol=cfg["tol"], max_cycles=1000, seed=rank,
+                             precision=ac.AC_FP64, stream=stream.cuda_stream)
+        seg64.set_image(torch.from_numpy(img).cuda())
+        seg64.step(args.warmup, allow_not_converged=True)
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        _, st64 = ac.ac_step(seg64.ctx, args.fp64_steps, allow_not_converged=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        t64 = torch.tensor([ev0.elapsed_time(ev1)], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t64, op=dist.ReduceOp.MAX)
+        v64 = world * args.fp64_steps / (float(t64.item()) / 1e3)
+        fp64 = {"value": v64, "unit": "steps/s", "steps": args.fp64_steps,
+                "vcycles_per_step": st64.total_cycles / max(1, st64.steps), "ratio_mixed_over_fp64": value / v64}
+        seg = seg64
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         times = oracle_sample(cfg, args.crop, args.cpu_steps)
@@ -285,6 +311,7 @@ def main():
                 "config": workload_config(cfg, args, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
                 "gdof_per_s": gdof, "vcycles_per_step": st.total_cycles / max(1, st.steps),
                 "fine_sweeps_per_step": st.fine_sweeps / max(1, st.steps), "residual": st.residual,
+                "outer_per_step": st.outer / max(1, st.steps), "plain_fp64_gpu": fp64,
                 "all_converged": bool(st.converged), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk,
                 "profile_ms": dict(zip(ac.PROF_CLASSES, [round(v, 3) for v in prof.ms]))}

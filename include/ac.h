@@ -69,7 +69,12 @@ typedef struct {
   int nu1, nu2;        /* pre/post projected smoothing sweeps of the V-cycle, >= 0, nu1+nu2 >= 1 */
   int max_cycles;      /* V-cycle cap per step, >= 1 */
   int coarse_min;      /* coarsen while both cell counts are even and min/2 >= coarse_min (>= 1) */
-  int precision;       /* AC_FP64 or AC_MIXED */
+  int precision;       /* AC_FP64: every array and operation of the solve in FP64.
+                          AC_MIXED: FP64 state u, right-hand side, colour means, energy and
+                          residual r = b - S u (defect correction); the correction delta is
+                          solved by the same multigrid in FP32 with obstacle -u and the
+                          natural residual is checked in FP64; the image is rounded to
+                          bfloat16 on input (ac_set_image only). */
   uint64_t seed;       /* seed of the random simplex initialisation in ac_set_image */
   void *stream;        /* cudaStream_t for all work of this context */
 } ac_params;
@@ -82,6 +87,7 @@ typedef struct {
   int steps;           /* time steps done by the call */
   int converged;       /* 1 if every step of the call reached tol */
   int64_t fine_sweeps; /* red-black projected sweeps on the fine level over the call */
+  int outer;           /* AC_MIXED: FP64 defect-correction passes over the call (0 for AC_FP64) */
 } ac_stats;
 
 /* Kernel classes of the profile (no counterpart in the paper: instrumentation). */
@@ -92,13 +98,16 @@ enum {
   AC_PROF_TRANSFER,    /* truncated Galerkin operators, restriction, prolongation */
   AC_PROF_LINESEARCH,  /* coarse-correction direction, line search, update */
   AC_PROF_SETUP,       /* colour means, energy and right-hand side of a step */
+  AC_PROF_OUTER,       /* AC_MIXED: FP64 residual and update of the defect correction */
   AC_PROF_COUNT
 };
 
 typedef struct {
   double ms[AC_PROF_COUNT];        /* summed device time per class (CUDA events on the context's stream) */
   int64_t launches[AC_PROF_COUNT]; /* kernel launches per class while profiling was on */
-  double smooth_bytes_per_launch;  /* algorithmic HBM bytes of one smoother launch: 1.5 n N sizeof(scalar) */
+  double smooth_bytes_per_launch;  /* algorithmic HBM bytes of one smoother launch (one colour): AC_FP64
+                                      1.5 n N 8 (b, u of the other colour, u written), AC_MIXED 2 n N 4
+                                      (r, obstacle, delta of the other colour, delta written) */
   int64_t total_launches;          /* every kernel launched by this context since creation */
 } ac_profile;
 

@@ -23,7 +23,7 @@ EXPORTS = [
     "ac_set_phase", "ac_get_phase", "ac_get_means", "ac_get_moments", "ac_get_rhs", "ac_get_node_labels",
     "ac_energy", "ac_residual", "ac_project_simplex", "ac_set_profiling", "ac_get_profile", "ac_last_error",
 ]
-PROF_CLASSES = ["smooth", "resid", "coarse", "transfer", "linesearch", "setup"]
+PROF_CLASSES = ["smooth", "resid", "coarse", "transfer", "linesearch", "setup", "outer"]
 
 
 class ac_params(C.Structure):
@@ -36,14 +36,14 @@ class ac_params(C.Structure):
 class ac_stats(C.Structure):
     _fields_ = [("energy", C.c_double), ("residual", C.c_double), ("cycles", C.c_int),
                 ("total_cycles", C.c_int), ("steps", C.c_int), ("converged", C.c_int),
-                ("fine_sweeps", C.c_int64)]
+                ("fine_sweeps", C.c_int64), ("outer", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class ac_profile(C.Structure):
-    _fields_ = [("ms", C.c_double * 6), ("launches", C.c_int64 * 6), ("smooth_bytes_per_launch", C.c_double),
+    _fields_ = [("ms", C.c_double * 7), ("launches", C.c_int64 * 7), ("smooth_bytes_per_launch", C.c_double),
                 ("total_launches", C.c_int64)]
 
     def as_dict(self):

@@ -1,7 +1,10 @@
 // ac_api.cu -- the C ABI of libac (include/ac.h) and the host-side driver of
-// the time step: colour means and right-hand side, then truncated monotone
-// multigrid V-cycles until the natural residual reaches tol (Sec. 3.2 of
-// Kay & Tomasi; the cycle structure is described at solve_step below).
+// the time step (Sec. 3.2 of Kay & Tomasi): colour means and right-hand side,
+// then truncated monotone multigrid V-cycles until the natural residual
+// reaches tol.  The cycle is described at solve_mg; the mixed-precision form
+// wraps it in an FP64 defect correction (solve_mixed).
+#include <cuda_bf16.h>
+
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -32,12 +35,6 @@ int fail(int code, const char *fmt, ...) {
   do {                                                                                             \
     cudaError_t e_ = (call);                                                                       \
     if (e_ != cudaSuccess) return fail(AC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));      \
-  } while (0)
-
-#define AC_LAUNCHED()                                                                              \
-  do {                                                                                             \
-    cudaError_t e_ = cudaGetLastError();                                                           \
-    if (e_ != cudaSuccess) return fail(AC_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e_));  \
   } while (0)
 
 const ac::Ops *ops_for(int N) {
@@ -83,12 +80,22 @@ ac::Geo make_geo(int W, int H, double te) {
 struct Level {
   ac::Geo g;
   int64_t n = 0;
-  double *op = nullptr, *r = nullptr, *v = nullptr, *t = nullptr;
+  void *op = nullptr, *r = nullptr, *v = nullptr, *t = nullptr;  // coarse levels only
 };
 
-constexpr int kCoarseSweeps = 2;          // pre/post sweeps on coarse levels
-constexpr int kCoarsestSweeps = 20;       // sweeps of the one-block coarsest solve
+// One multigrid solve: min_x sum_i 1/2 x_i'S x_i - rhs_i'x_i over the
+// constraint set of the instantiation (see ac_kernels.cuh).
+struct Solve {
+  const ac::SolverOps *o = nullptr;
+  void *x = nullptr, *rhs = nullptr, *ob = nullptr, *rt = nullptr, *d = nullptr;
+  uint8_t *mask = nullptr;
+  std::vector<Level> lv;  // lv[0]: fine level geometry
+};
+
+constexpr int kCoarseSweeps = 2;     // pre/post sweeps on coarse levels
+constexpr int kCoarsestSweeps = 20;  // sweeps of the one-block coarsest solve
 constexpr int64_t kCoarsestBlockNodes = 1 << 14;
+constexpr double kInnerReduction = 1e-5;  // AC_MIXED: inner FP32 solve to max(tol/2, 1e-5 rho_outer)
 
 }  // namespace
 
@@ -98,20 +105,25 @@ struct ac_ctx {
   int64_t n = 0;
   const ac::Ops *ops = nullptr;
   cudaStream_t s = nullptr;
-  std::vector<Level> lv;  // lv[0]: fine level (geometry only)
-  double *u = nullptr, *b = nullptr, *mom = nullptr, *rt = nullptr, *d = nullptr;
+  ac::Geo g0{};
+  Solve sv;                                    // the multigrid solve of this precision
+  double *u = nullptr, *b = nullptr, *mom = nullptr;
+  float *r32 = nullptr, *u32 = nullptr;        // AC_MIXED: FP32 right-hand side and obstacle
   double *part = nullptr, *tot = nullptr, *c = nullptr, *c_tmp = nullptr, *energy = nullptr;
   double *rho = nullptr, *omega = nullptr, *ls_part = nullptr, *ls_tot = nullptr;
-  uint8_t *mask = nullptr;
-  void *img = nullptr;     // device copy of a host image (allocated on demand)
+  void *img = nullptr;  // device copy of a host image (allocated on demand)
   size_t img_bytes = 0;
-  double *h_scalars = nullptr;  // pinned: rho, energy
+  __nv_bfloat16 *img16 = nullptr;  // AC_MIXED: the image stored in bfloat16
+  double *h_scalars = nullptr;     // pinned: rho, energy
   bool have_image = false, have_rhs = false;
   std::vector<void *> allocs;
   // instrumentation
   int64_t total_launches = 0;
   bool profiling = false;
-  struct Pending { cudaEvent_t a, b; int cls; };
+  struct Pending {
+    cudaEvent_t a, b;
+    int cls;
+  };
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<Pending> pending;
@@ -132,10 +144,10 @@ int dev_alloc(ac_ctx *ctx, void **p, size_t bytes) {
   return AC_OK;
 }
 
-#define AC_ALLOC(ptr, bytes)                                                   \
-  do {                                                                         \
-    int rc_ = dev_alloc(ctx, reinterpret_cast<void **>(&(ptr)), (bytes));      \
-    if (rc_) return rc_;                                                       \
+#define AC_ALLOC(ptr, bytes)                                              \
+  do {                                                                    \
+    int rc_ = dev_alloc(ctx, reinterpret_cast<void **>(&(ptr)), (bytes)); \
+    if (rc_) return rc_;                                                  \
   } while (0)
 
 int validate(const ac_params *p) {
@@ -143,17 +155,22 @@ int validate(const ac_params *p) {
   if (p->width < 1 || p->height < 1) return fail(AC_ERR_ARG, "image size must be >= 1x1");
   if ((int64_t)(p->width + 1) * (p->height + 1) > (int64_t)1 << 31)
     return fail(AC_ERR_ARG, "image too large (more than 2^31 nodes)");
-  if (p->n_phases < 2 || p->n_phases > AC_MAX_PHASES) return fail(AC_ERR_ARG, "n_phases must be in [2, %d]", AC_MAX_PHASES);
+  if (p->n_phases < 2 || p->n_phases > AC_MAX_PHASES)
+    return fail(AC_ERR_ARG, "n_phases must be in [2, %d]", AC_MAX_PHASES);
   if (!(p->eps > 0) || !std::isfinite(p->eps)) return fail(AC_ERR_ARG, "eps must be > 0");
   if (!(p->tau > 0) || !std::isfinite(p->tau)) return fail(AC_ERR_ARG, "tau must be > 0");
   if (!(p->lambda >= 0) || !std::isfinite(p->lambda)) return fail(AC_ERR_ARG, "lambda must be >= 0");
   if (!(p->tol > 0)) return fail(AC_ERR_ARG, "tol must be > 0");
-  if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1) return fail(AC_ERR_ARG, "need nu1, nu2 >= 0 and nu1 + nu2 >= 1");
+  if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1)
+    return fail(AC_ERR_ARG, "need nu1, nu2 >= 0 and nu1 + nu2 >= 1");
   if (p->max_cycles < 1) return fail(AC_ERR_ARG, "max_cycles must be >= 1");
   if (p->coarse_min < 1) return fail(AC_ERR_ARG, "coarse_min must be >= 1");
-  if (p->precision != AC_FP64) return fail(AC_ERR_ARG, "precision mode %d is not available", p->precision);
+  if (p->precision != AC_FP64 && p->precision != AC_MIXED)
+    return fail(AC_ERR_ARG, "precision must be AC_FP64 or AC_MIXED");
   return AC_OK;
 }
+
+// ---- instrumentation --------------------------------------------------------
 
 // Sum the finished event pairs into the profile and recycle the events.
 int prof_harvest(ac_ctx *ctx) {
@@ -206,10 +223,10 @@ int timed(ac_ctx *ctx, int cls, F &&f) {
   return AC_OK;
 }
 
-#define AC_RUN(cls, expr)                                       \
-  do {                                                          \
-    int rc_ = timed(ctx, (cls), [&]() { return (expr); });      \
-    if (rc_) return rc_;                                        \
+#define AC_RUN(cls, expr)                                  \
+  do {                                                     \
+    int rc_ = timed(ctx, (cls), [&]() { return (expr); }); \
+    if (rc_) return rc_;                                   \
   } while (0)
 
 int read_rho(ac_ctx *ctx, double *out) {
@@ -219,55 +236,100 @@ int read_rho(ac_ctx *ctx, double *out) {
   return AC_OK;
 }
 
+// ---- multigrid ---------------------------------------------------------------
+
 // Linear V-cycle for S_k v_k = r_k on coarse levels k >= 1 (operators already
 // built), zero initial guess, Gauss-Seidel smoothing in 3 colours.
-int coarse_vcycle(ac_ctx *ctx, int k) {
-  Level &L = ctx->lv[k];
-  const ac::Ops *o = ctx->ops;
-  AC_CUDA(cudaMemsetAsync(L.v, 0, L.n * ctx->N * sizeof(double), ctx->s));
-  if (k == (int)ctx->lv.size() - 1) {
+int coarse_vcycle(ac_ctx *ctx, Solve &S, int k) {
+  Level &L = S.lv[k];
+  const ac::SolverOps *o = S.o;
+  AC_CUDA(cudaMemsetAsync(L.v, 0, (size_t)L.n * ctx->N * o->elem, ctx->s));
+  if (k == (int)S.lv.size() - 1) {
     if (L.n <= kCoarsestBlockNodes)
       AC_RUN(AC_PROF_COARSE, o->coarse_solve(L.op, L.r, L.v, L.g, kCoarsestSweeps, ctx->s));
     else
       AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.g, 2 * kCoarseSweeps, ctx->s));
     return AC_OK;
   }
-  Level &C = ctx->lv[k + 1];
+  Level &C = S.lv[k + 1];
   AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.g, kCoarseSweeps, ctx->s));
   AC_RUN(AC_PROF_COARSE, o->coarse_resid(L.op, L.r, L.v, L.g, L.t, ctx->s));
   AC_RUN(AC_PROF_TRANSFER, o->restrict_(L.t, L.g, C.g, C.r, ctx->s));
-  int rc = coarse_vcycle(ctx, k + 1);
+  int rc = coarse_vcycle(ctx, S, k + 1);
   if (rc) return rc;
   AC_RUN(AC_PROF_TRANSFER, o->prolong_add(C.v, L.g, C.g, L.v, ctx->s));
   AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.g, kCoarseSweeps, ctx->s));
   return AC_OK;
 }
 
-// One time step's solve (b already assembled).  Cycle structure:
+// Multigrid solve of one step problem.  Cycle structure:
 //   smooth (nu1 red-black projected sweeps; nu2 + nu1 after a correction)
-//   -> residual r = b - S u, natural residual rho, free-phase mask, tangent
+//   -> residual r = rhs - S x, natural residual rho, free-phase mask, tangent
 //      projection of r; stop if rho <= tol
 //   -> truncated Galerkin operators and restriction, linear V-cycle on the
 //      coarse levels
 //   -> feasible coarse-correction direction and exact line search.
-// Every stage leaves u on the simplex and does not raise the step energy, so
-// the limit is the unique minimiser that plain projected Gauss-Seidel (the
+// Every stage keeps x feasible and does not raise the step energy, so the
+// limit is the unique minimiser that plain projected Gauss-Seidel (the
 // smoother alone) reaches.
-int solve_step(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_out) {
-  const ac::Ops *o = ctx->ops;
-  const ac::Geo &g0 = ctx->lv[0].g;
-  const bool coarse = ctx->lv.size() > 1;
+int solve_mg(ac_ctx *ctx, Solve &S, double tol, int *cycles_out, double *rho_out, int64_t *sweeps_out) {
+  const ac::SolverOps *o = S.o;
+  const ac::Geo &g0 = S.lv[0].g;
+  const bool coarse = S.lv.size() > 1;
   double rho = 0;
   int cyc = 0, status = AC_ERR_NOT_CONVERGED;
   int64_t sweeps = 0;
   for (;;) {
-    if (cyc > 0 && coarse) AC_RUN(AC_PROF_LINESEARCH, o->apply(ctx->u, ctx->d, ctx->omega, ctx->n, ctx->s));
+    if (cyc > 0 && coarse) AC_RUN(AC_PROF_LINESEARCH, o->apply(S.x, S.ob, S.d, ctx->omega, ctx->n, ctx->s));
     const int nsw = cyc == 0 ? ctx->p.nu1 : ctx->p.nu1 + ctx->p.nu2;
-    AC_RUN(AC_PROF_SMOOTH, o->smooth_fine(ctx->u, ctx->b, g0, nsw, ctx->s));
+    AC_RUN(AC_PROF_SMOOTH, o->smooth(S.x, S.rhs, S.ob, g0, nsw, ctx->s));
     sweeps += nsw;
     AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
-    AC_RUN(AC_PROF_RESID, o->fine_resid(ctx->u, ctx->b, g0, ctx->rt, ctx->mask, ctx->rho, ctx->s));
+    AC_RUN(AC_PROF_RESID, o->resid(S.x, S.rhs, S.ob, g0, S.rt, S.mask, ctx->rho, ctx->s));
     ++cyc;
+    int rc = read_rho(ctx, &rho);
+    if (rc) return rc;
+    if (std::isnan(rho) || std::isinf(rho)) {
+      status = fail(AC_ERR_NUMERIC, "non-finite residual");
+      break;
+    }
+    if (rho <= tol) {
+      status = AC_OK;
+      break;
+    }
+    if (cyc >= ctx->p.max_cycles) break;
+    if (!coarse) continue;
+    Level &L1 = S.lv[1];
+    AC_RUN(AC_PROF_TRANSFER, o->galerkin0(S.mask, g0, L1.g, L1.op, ctx->s));
+    for (size_t k = 1; k + 1 < S.lv.size(); ++k)
+      AC_RUN(AC_PROF_TRANSFER, o->galerkin(S.lv[k].op, S.lv[k].g, S.lv[k + 1].g, S.lv[k + 1].op, ctx->s));
+    AC_RUN(AC_PROF_TRANSFER, o->restrict0(S.rt, g0, L1.g, L1.r, ctx->s));
+    rc = coarse_vcycle(ctx, S, 1);
+    if (rc) return rc;
+    AC_RUN(AC_PROF_LINESEARCH, o->line_search(S.x, S.ob, S.rt, L1.v, S.mask, g0, L1.g, S.d, ctx->ls_part,
+                                              ctx->ls_tot, ctx->omega, ctx->s));
+  }
+  *cycles_out = cyc;
+  *rho_out = rho;
+  *sweeps_out = sweeps;
+  if (status == AC_ERR_NOT_CONVERGED)
+    fail(status, "step did not reach tol %.3g in %d cycles (rho %.3g)", tol, cyc, rho);
+  return status;
+}
+
+// AC_MIXED: FP64 defect correction around the FP32 multigrid.  Each pass
+// forms r = b - S u and the natural residual in FP64; if rho > tol the
+// correction problem min 1/2 d'Sd - r'd, u + d on the simplices, is solved in
+// FP32 to max(tol/2, 1e-5 rho) (FP32 keeps the correction's own relative
+// precision, so each pass gains up to five digits) and u <- P_G(u + d) in FP64.
+int solve_mixed(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_out, int *outer_out) {
+  const ac::Ops *o = ctx->ops;
+  double rho = 0;
+  int cycles = 0, outer = 0, status = AC_ERR_NOT_CONVERGED;
+  int64_t sweeps = 0;
+  for (;;) {
+    AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
+    AC_RUN(AC_PROF_OUTER, o->outer_resid(ctx->u, ctx->b, ctx->g0, ctx->r32, ctx->u32, ctx->rho, ctx->s));
     int rc = read_rho(ctx, &rho);
     if (rc) return rc;
     if (std::isnan(rho) || std::isinf(rho)) {
@@ -278,22 +340,24 @@ int solve_step(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_ou
       status = AC_OK;
       break;
     }
-    if (cyc >= ctx->p.max_cycles) break;
-    if (!coarse) continue;
-    Level &L1 = ctx->lv[1];
-    AC_RUN(AC_PROF_TRANSFER, o->galerkin0(ctx->mask, g0, L1.g, L1.op, ctx->s));
-    for (size_t k = 1; k + 1 < ctx->lv.size(); ++k)
-      AC_RUN(AC_PROF_TRANSFER, o->galerkin(ctx->lv[k].op, ctx->lv[k].g, ctx->lv[k + 1].g, ctx->lv[k + 1].op, ctx->s));
-    AC_RUN(AC_PROF_TRANSFER, o->restrict_(ctx->rt, g0, L1.g, L1.r, ctx->s));
-    rc = coarse_vcycle(ctx, 1);
-    if (rc) return rc;
-    AC_RUN(AC_PROF_LINESEARCH, o->line_search(ctx->u, ctx->rt, L1.v, ctx->mask, g0, L1.g, ctx->d, ctx->ls_part,
-                                              ctx->ls_tot, ctx->omega, ctx->s));
+    if (cycles >= ctx->p.max_cycles) break;
+    AC_CUDA(cudaMemsetAsync(ctx->sv.x, 0, (size_t)ctx->n * ctx->N * sizeof(float), ctx->s));
+    int c = 0;
+    int64_t sw = 0;
+    double rin = 0;
+    rc = solve_mg(ctx, ctx->sv, std::fmax(0.5 * ctx->p.tol, kInnerReduction * rho), &c, &rin, &sw);
+    cycles += c;
+    sweeps += sw;
+    if (rc && rc != AC_ERR_NOT_CONVERGED) return rc;
+    AC_RUN(AC_PROF_OUTER, o->outer_update(ctx->u, (const float *)ctx->sv.x, ctx->n, ctx->s));
+    ++outer;
   }
-  *cycles_out = cyc;
+  *cycles_out = cycles;
   *rho_out = rho;
   *sweeps_out = sweeps;
-  if (status == AC_ERR_NOT_CONVERGED) fail(status, "step did not reach tol %.3g in %d cycles (rho %.3g)", ctx->p.tol, cyc, rho);
+  *outer_out = outer;
+  if (status == AC_ERR_NOT_CONVERGED)
+    fail(status, "step did not reach tol %.3g in %d cycles (rho %.3g)", ctx->p.tol, cycles, rho);
   return status;
 }
 
@@ -301,6 +365,38 @@ int copy_out(ac_ctx *ctx, void *dst, const void *src, size_t bytes, int is_devic
   AC_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->s));
   if (!is_device) AC_CUDA(cudaStreamSynchronize(ctx->s));
   return AC_OK;
+}
+
+__global__ void k_to_bf16(const float *__restrict__ in, __nv_bfloat16 *__restrict__ out, int64_t count) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < count) out[k] = __float2bfloat16_rn(in[k]);
+}
+
+__global__ void k_moments_bf16(const __nv_bfloat16 *__restrict__ img, ac::Geo g, double *__restrict__ mom) {
+  // same sums as k_moments, reading the bfloat16 image
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x > g.W || y > g.H) return;
+  double s[3] = {0, 0, 0}, s2 = 0;
+  const int px[4] = {x, x - 1, x, x - 1};
+  const int py[4] = {y, y - 1, y - 1, y};
+  const double w[4] = {2.0, 2.0, 1.0, 1.0};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (px[k] < 0 || px[k] >= g.W || py[k] < 0 || py[k] >= g.H) continue;
+    const __nv_bfloat16 *p = img + ((int64_t)py[k] * g.W + px[k]) * 3;
+    const double r = (double)__bfloat162float(p[0]), gg = (double)__bfloat162float(p[1]),
+                 bb = (double)__bfloat162float(p[2]);
+    s[0] += w[k] * r;
+    s[1] += w[k] * gg;
+    s[2] += w[k] * bb;
+    s2 += w[k] * (r * r + gg * gg + bb * bb);
+  }
+  double *m = mom + ((int64_t)y * g.Wn + x) * 4;
+  m[0] = s[0] / 6.0;
+  m[1] = s[1] / 6.0;
+  m[2] = s[2] / 6.0;
+  m[3] = s2 / 6.0;
 }
 
 }  // namespace
@@ -330,30 +426,44 @@ int ac_create(ac_ctx **out, const ac_params *p) {
   ctx->N = p->n_phases;
   ctx->ops = ops_for(ctx->N);
   ctx->s = (cudaStream_t)p->stream;
+  const bool mixed = p->precision == AC_MIXED;
   const double te = p->tau * p->eps;
-  // level hierarchy
+  Solve &S = ctx->sv;
+  S.o = mixed ? &ctx->ops->mixed : &ctx->ops->fp64;
   int W = p->width, H = p->height;
-  ctx->lv.push_back(Level{make_geo(W, H, te)});
-  ctx->lv[0].n = (int64_t)(W + 1) * (H + 1);
+  ctx->g0 = make_geo(W, H, te);
+  S.lv.push_back(Level{ctx->g0, (int64_t)(W + 1) * (H + 1)});
   while (W % 2 == 0 && H % 2 == 0 && (W < H ? W : H) / 2 >= p->coarse_min) {
     W /= 2;
     H /= 2;
     Level L;
     L.g = make_geo(W, H, te);
     L.n = (int64_t)(W + 1) * (H + 1);
-    ctx->lv.push_back(L);
+    S.lv.push_back(L);
   }
-  ctx->n = ctx->lv[0].n;
+  ctx->n = S.lv[0].n;
   const int N = ctx->N;
-  const size_t fN = (size_t)ctx->n * N * sizeof(double);
-  const int ls_blocks = (int)(((ctx->lv[0].g.W + 1 + 255) / 256) * (int64_t)(ctx->lv[0].g.H + 1));
+  const size_t es = (size_t)S.o->elem;
+  const size_t fN64 = (size_t)ctx->n * N * sizeof(double), fNs = (size_t)ctx->n * N * es;
+  const int ls_blocks = (int)(((ctx->g0.W + 1 + 255) / 256) * (int64_t)(ctx->g0.H + 1));
   auto body = [&]() -> int {
-    AC_ALLOC(ctx->u, fN);
-    AC_ALLOC(ctx->b, fN);
-    AC_ALLOC(ctx->rt, fN);
+    AC_ALLOC(ctx->u, fN64);
+    AC_ALLOC(ctx->b, fN64);
     AC_ALLOC(ctx->mom, (size_t)ctx->n * 4 * sizeof(double));
-    AC_ALLOC(ctx->mask, (size_t)ctx->n);
-    if (ctx->lv.size() > 1) AC_ALLOC(ctx->d, fN);
+    if (mixed) {
+      AC_ALLOC(ctx->r32, fNs);
+      AC_ALLOC(ctx->u32, fNs);
+      AC_ALLOC(S.x, fNs);
+      S.rhs = ctx->r32;
+      S.ob = ctx->u32;
+    } else {
+      S.x = ctx->u;
+      S.rhs = ctx->b;
+      S.ob = nullptr;
+    }
+    AC_ALLOC(S.rt, fNs);
+    AC_ALLOC(S.mask, (size_t)ctx->n);
+    if (S.lv.size() > 1) AC_ALLOC(S.d, fNs);
     AC_ALLOC(ctx->part, (size_t)ac::kMaxPartBlocks * 7 * N * sizeof(double));
     AC_ALLOC(ctx->tot, (size_t)7 * N * sizeof(double));
     AC_ALLOC(ctx->c, (size_t)3 * N * sizeof(double));
@@ -363,12 +473,12 @@ int ac_create(ac_ctx **out, const ac_params *p) {
     AC_ALLOC(ctx->omega, sizeof(double));
     AC_ALLOC(ctx->ls_part, (size_t)2 * ls_blocks * sizeof(double));
     AC_ALLOC(ctx->ls_tot, 2 * sizeof(double));
-    for (size_t k = 1; k < ctx->lv.size(); ++k) {
-      Level &L = ctx->lv[k];
-      AC_ALLOC(L.op, (size_t)L.n * 4 * N * sizeof(double));
-      AC_ALLOC(L.r, (size_t)L.n * N * sizeof(double));
-      AC_ALLOC(L.v, (size_t)L.n * N * sizeof(double));
-      AC_ALLOC(L.t, (size_t)L.n * N * sizeof(double));
+    for (size_t k = 1; k < S.lv.size(); ++k) {
+      Level &L = S.lv[k];
+      AC_ALLOC(L.op, (size_t)L.n * 4 * N * es);
+      AC_ALLOC(L.r, (size_t)L.n * N * es);
+      AC_ALLOC(L.v, (size_t)L.n * N * es);
+      AC_ALLOC(L.t, (size_t)L.n * N * es);
     }
     AC_CUDA(cudaMallocHost(&ctx->h_scalars, 4 * sizeof(double)));
     AC_CUDA(cudaMemsetAsync(ctx->c, 0, (size_t)3 * N * sizeof(double), ctx->s));
@@ -388,19 +498,25 @@ int ac_create(ac_ctx **out, const ac_params *p) {
 
 void ac_destroy(ac_ctx *ctx) {
   if (!ctx) return;
-  if (ctx->s) cudaStreamSynchronize(ctx->s);
-  else cudaDeviceSynchronize();
+  if (ctx->s)
+    cudaStreamSynchronize(ctx->s);
+  else
+    cudaDeviceSynchronize();
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   for (void *p : ctx->allocs) cudaFree(p);
   if (ctx->img) cudaFree(ctx->img);
+  if (ctx->img16) cudaFree(ctx->img16);
   if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
   delete ctx;
 }
 
 static int set_image_impl(ac_ctx *ctx, const void *rgb, int is_device, bool f64) {
   if (!ctx || !rgb) return fail(AC_ERR_ARG, "NULL argument");
-  const ac::Geo &g = ctx->lv[0].g;
-  const size_t bytes = (size_t)g.W * g.H * 3 * (f64 ? sizeof(double) : sizeof(float));
+  const ac::Geo &g = ctx->g0;
+  const int64_t count = (int64_t)g.W * g.H * 3;
+  const size_t bytes = (size_t)count * (f64 ? sizeof(double) : sizeof(float));
+  const bool mixed = ctx->p.precision == AC_MIXED;
+  if (mixed && f64) return fail(AC_ERR_ARG, "AC_MIXED takes a float32 image (it is stored in bfloat16)");
   const void *src = rgb;
   if (!is_device) {
     if (ctx->img_bytes < bytes) {
@@ -417,10 +533,24 @@ static int set_image_impl(ac_ctx *ctx, const void *rgb, int is_device, bool f64)
     AC_CUDA(cudaMemcpyAsync(ctx->img, rgb, bytes, cudaMemcpyHostToDevice, ctx->s));
     src = ctx->img;
   }
-  if (f64)
+  if (mixed) {
+    if (!ctx->img16) {
+      cudaError_t e = cudaMalloc(&ctx->img16, (size_t)count * sizeof(__nv_bfloat16));
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->img16 = nullptr;
+        return fail(AC_ERR_NOMEM, "cudaMalloc for the bfloat16 image: %s", cudaGetErrorString(e));
+      }
+    }
+    AC_RUN(AC_PROF_SETUP, (k_to_bf16<<<(unsigned)((count + 255) / 256), 256, 0, ctx->s>>>(
+                               (const float *)src, ctx->img16, count), 1));
+    AC_RUN(AC_PROF_SETUP, (k_moments_bf16<<<dim3((unsigned)((g.W + 256) / 256), (unsigned)(g.H + 1)), 256, 0,
+                                             ctx->s>>>(ctx->img16, g, ctx->mom), 1));
+  } else if (f64) {
     AC_RUN(AC_PROF_SETUP, ctx->ops->moments_f64((const double *)src, g, ctx->mom, ctx->s));
-  else
+  } else {
     AC_RUN(AC_PROF_SETUP, ctx->ops->moments_f32((const float *)src, g, ctx->mom, ctx->s));
+  }
   AC_RUN(AC_PROF_SETUP, ctx->ops->init_random(ctx->u, ctx->n, ctx->p.seed, ctx->s));
   AC_CUDA(cudaMemsetAsync(ctx->c, 0, (size_t)3 * ctx->N * sizeof(double), ctx->s));
   if (!is_device) AC_CUDA(cudaStreamSynchronize(ctx->s));  // the host buffer may be reused after return
@@ -440,16 +570,21 @@ int ac_step(ac_ctx *ctx, int n_steps, ac_stats *out) {
   st.converged = 1;
   int status = AC_OK;
   const double a1 = 1.0 + 2.0 * ctx->p.tau / ctx->p.eps, tl = ctx->p.tau * ctx->p.lambda;
+  const bool mixed = ctx->p.precision == AC_MIXED;
   for (int t = 0; t < n_steps; ++t) {
-    AC_RUN(AC_PROF_SETUP, ctx->ops->means(ctx->u, ctx->mom, ctx->lv[0].g, ctx->part, ctx->tot, ctx->c, ctx->energy,
-                                          ctx->p.eps, ctx->p.lambda, ctx->s));
-    AC_RUN(AC_PROF_SETUP, ctx->ops->rhs(ctx->u, ctx->mom, ctx->c, ctx->lv[0].g, a1, tl, ctx->b, ctx->s));
+    // the energy is only evaluated for the statistics of the last step
+    double *energy = (out && t == n_steps - 1) ? ctx->energy : nullptr;
+    AC_RUN(AC_PROF_SETUP, ctx->ops->means(ctx->u, ctx->mom, ctx->g0, ctx->part, ctx->tot, ctx->c, energy, ctx->p.eps,
+                                          ctx->p.lambda, ctx->s));
+    AC_RUN(AC_PROF_SETUP, ctx->ops->rhs(ctx->u, ctx->mom, ctx->c, ctx->g0, a1, tl, ctx->b, ctx->s));
     ctx->have_rhs = true;
-    int cycles = 0;
+    int cycles = 0, outer = 0;
     double rho = 0;
     int64_t sweeps = 0;
-    int rc = solve_step(ctx, &cycles, &rho, &sweeps);
+    int rc = mixed ? solve_mixed(ctx, &cycles, &rho, &sweeps, &outer)
+                   : solve_mg(ctx, ctx->sv, ctx->p.tol, &cycles, &rho, &sweeps);
     st.fine_sweeps += sweeps;
+    st.outer += outer;
     st.cycles = cycles;
     st.total_cycles += cycles;
     st.residual = rho;
@@ -463,7 +598,7 @@ int ac_step(ac_ctx *ctx, int n_steps, ac_stats *out) {
       return rc;
     }
   }
-  if (n_steps > 0) {
+  if (out && n_steps > 0) {
     AC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 1, ctx->energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
     AC_CUDA(cudaStreamSynchronize(ctx->s));
     st.energy = ctx->h_scalars[1];
@@ -476,10 +611,9 @@ int ac_segment(ac_ctx *ctx, int n_steps, int8_t *pixel_labels, int is_device, ac
   if (!ctx || !pixel_labels) return fail(AC_ERR_ARG, "NULL argument");
   int rc = ac_step(ctx, n_steps, out);
   if (rc && rc != AC_ERR_NOT_CONVERGED) return rc;
-  const ac::Geo &g = ctx->lv[0].g;
+  const ac::Geo &g = ctx->g0;
   const size_t bytes = (size_t)g.W * g.H;
-  int8_t *dst = pixel_labels;
-  if (!is_device) dst = reinterpret_cast<int8_t *>(ctx->rt);  // scratch large enough for W*H bytes
+  int8_t *dst = is_device ? pixel_labels : reinterpret_cast<int8_t *>(ctx->sv.rt);  // rt holds >= W*H bytes
   AC_RUN(AC_PROF_SETUP, ctx->ops->labels(ctx->u, g, nullptr, dst, ctx->s));
   if (!is_device) {
     int rc2 = copy_out(ctx, pixel_labels, dst, bytes, 0);
@@ -513,7 +647,7 @@ int ac_get_moments(ac_ctx *ctx, double *m) {
   std::vector<double> mom((size_t)ctx->n * 4);
   int rc = copy_out(ctx, mom.data(), ctx->mom, mom.size() * sizeof(double), 0);
   if (rc) return rc;
-  const ac::Geo &g = ctx->lv[0].g;
+  const ac::Geo &g = ctx->g0;
   for (int64_t k = 0; k < ctx->n; ++k) {
     const int x = (int)(k % g.Wn), y = (int)(k / g.Wn);
     const int cx = x == 0 ? 0 : (x == g.W ? 2 : 1), cy = y == 0 ? 0 : (y == g.H ? 2 : 1);
@@ -531,8 +665,8 @@ int ac_get_rhs(ac_ctx *ctx, double *b) {
 
 int ac_get_node_labels(ac_ctx *ctx, int8_t *labels, int is_device) {
   if (!ctx || !labels) return fail(AC_ERR_ARG, "NULL argument");
-  int8_t *dst = is_device ? labels : reinterpret_cast<int8_t *>(ctx->rt);
-  AC_RUN(AC_PROF_SETUP, ctx->ops->labels(ctx->u, ctx->lv[0].g, dst, nullptr, ctx->s));
+  int8_t *dst = is_device ? labels : reinterpret_cast<int8_t *>(ctx->sv.rt);
+  AC_RUN(AC_PROF_SETUP, ctx->ops->labels(ctx->u, ctx->g0, dst, nullptr, ctx->s));
   if (!is_device) return copy_out(ctx, labels, dst, (size_t)ctx->n, 0);
   return AC_OK;
 }
@@ -541,8 +675,8 @@ int ac_energy(ac_ctx *ctx, double *energy) {
   if (!ctx || !energy) return fail(AC_ERR_ARG, "NULL argument");
   if (!ctx->have_image) return fail(AC_ERR_STATE, "no image");
   AC_CUDA(cudaMemcpyAsync(ctx->c_tmp, ctx->c, (size_t)3 * ctx->N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
-  AC_RUN(AC_PROF_SETUP, ctx->ops->means(ctx->u, ctx->mom, ctx->lv[0].g, ctx->part, ctx->tot, ctx->c_tmp,
-                                        ctx->energy, ctx->p.eps, ctx->p.lambda, ctx->s));
+  AC_RUN(AC_PROF_SETUP, ctx->ops->means(ctx->u, ctx->mom, ctx->g0, ctx->part, ctx->tot, ctx->c_tmp, ctx->energy,
+                                        ctx->p.eps, ctx->p.lambda, ctx->s));
   return copy_out(ctx, energy, ctx->energy, sizeof(double), 0);
 }
 
@@ -550,7 +684,10 @@ int ac_residual(ac_ctx *ctx, double *rho) {
   if (!ctx || !rho) return fail(AC_ERR_ARG, "NULL argument");
   if (!ctx->have_rhs) return fail(AC_ERR_STATE, "no step taken yet");
   AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
-  AC_RUN(AC_PROF_RESID, ctx->ops->fine_resid(ctx->u, ctx->b, ctx->lv[0].g, nullptr, nullptr, ctx->rho, ctx->s));
+  if (ctx->p.precision == AC_MIXED)
+    AC_RUN(AC_PROF_OUTER, ctx->ops->outer_resid(ctx->u, ctx->b, ctx->g0, ctx->r32, ctx->u32, ctx->rho, ctx->s));
+  else
+    AC_RUN(AC_PROF_RESID, ctx->ops->fp64.resid(ctx->u, ctx->b, nullptr, ctx->g0, nullptr, nullptr, ctx->rho, ctx->s));
   return read_rho(ctx, rho);
 }
 
@@ -559,7 +696,8 @@ int ac_project_simplex(const double *y, double *x, int64_t count, int n_phases, 
   if (!o) return fail(AC_ERR_ARG, "n_phases must be in [2, %d]", AC_MAX_PHASES);
   if (count < 0 || (count > 0 && (!y || !x))) return fail(AC_ERR_ARG, "bad buffers");
   o->project(y, x, count, (cudaStream_t)stream);
-  AC_LAUNCHED();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(AC_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
   return AC_OK;
 }
 
@@ -583,7 +721,8 @@ int ac_get_profile(ac_ctx *ctx, ac_profile *out) {
     out->ms[k] = ctx->prof_ms[k];
     out->launches[k] = ctx->prof_launches[k];
   }
-  out->smooth_bytes_per_launch = 1.5 * (double)ctx->n * ctx->N * sizeof(double);
+  out->smooth_bytes_per_launch = ctx->p.precision == AC_MIXED ? 2.0 * (double)ctx->n * ctx->N * sizeof(float)
+                                                               : 1.5 * (double)ctx->n * ctx->N * sizeof(double);
   out->total_launches = ctx->total_launches;
   return AC_OK;
 }

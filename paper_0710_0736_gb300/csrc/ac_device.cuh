@@ -131,38 +131,58 @@ __device__ __forceinline__ T rcp_small(int k) {
        : k == 5 ? T(0.2) : k == 6 ? T(1.0 / 6.0) : k == 7 ? T(1.0 / 7.0) : T(0.125);
 }
 
-// Euclidean projection onto the Gibbs simplex, in place, in registers.
-// The kept set starts full; theta = (sum of kept - 1)/|kept|; components at
-// or below theta leave the set; repeat until none leaves (at most N passes).
-// This is the clamp-and-redistribute loop of Sec. 3.3 written with the
-// threshold theta (Michelot's form of the same iteration).
-template <typename T, int N>
-__device__ __forceinline__ void proj_simplex(T (&y)[N]) {
+// Euclidean projection onto a shifted, scaled simplex, in place, in registers:
+//   direct form  (SH = false): x_i >= 0,      sum_i x_i = 1  (the Gibbs simplex)
+//   shifted form (SH = true):  x_i >= -ob_i,  sum_i x_i = 0  (corrections delta
+//                              with u + delta on the simplex, ob = u)
+// The kept set starts full; theta = (sum of kept z + sum of dropped bounds -
+// total)/|kept|; components with z_i - theta at or below their bound leave the
+// set; repeat until none leaves (at most N passes).  This is the
+// clamp-and-redistribute loop of Sec. 3.3 written with the threshold theta
+// (Michelot's form of the same iteration).  In the shifted form the result is
+// computed as a difference from the bound, so it keeps the relative precision
+// of the correction itself.
+template <typename T, int N, bool SH>
+__device__ __forceinline__ void proj_box(T (&z)[N], const T (&ob)[N]) {
+  const T total = SH ? T(0) : T(1);
   unsigned keep = (1u << N) - 1u;
   T s = T(0);
 #pragma unroll
-  for (int i = 0; i < N; ++i) s += y[i];
-  T theta = (s - T(1)) * rcp_small<T>(N);
+  for (int i = 0; i < N; ++i) s += z[i];
+  T theta = (s - total) * rcp_small<T>(N);
 #pragma unroll 1
   for (int pass = 1; pass < N; ++pass) {
     unsigned drop = 0;
 #pragma unroll
-    for (int i = 0; i < N; ++i)
-      if (((keep >> i) & 1u) && y[i] <= theta) drop |= 1u << i;
+    for (int i = 0; i < N; ++i) {
+      const T lo = SH ? -ob[i] : T(0);
+      if (((keep >> i) & 1u) && z[i] - theta <= lo) drop |= 1u << i;
+    }
     if (!drop) break;
     keep &= ~drop;
     s = T(0);
+    T L = T(0);
     int k = 0;
 #pragma unroll
-    for (int i = 0; i < N; ++i)
+    for (int i = 0; i < N; ++i) {
       if ((keep >> i) & 1u) {
-        s += y[i];
+        s += z[i];
         ++k;
+      } else if (SH) {
+        L -= ob[i];
       }
-    theta = (s - T(1)) * rcp_small<T>(k);
+    }
+    theta = (s + L - total) * rcp_small<T>(k);
   }
 #pragma unroll
-  for (int i = 0; i < N; ++i) y[i] = ((keep >> i) & 1u) ? y[i] - theta : T(0);
+  for (int i = 0; i < N; ++i) z[i] = ((keep >> i) & 1u) ? z[i] - theta : (SH ? -ob[i] : T(0));
+}
+
+// Projection onto the Gibbs simplex (direct form).
+template <typename T, int N>
+__device__ __forceinline__ void proj_simplex(T (&y)[N]) {
+  const T none[N] = {};
+  proj_box<T, N, false>(y, none);
 }
 
 // Weighted sum of the four axis neighbours' values, acc = sum_m w_nm u_m.

@@ -1,17 +1,20 @@
 // ac_kernels.cuh -- the sm_103a kernels of libac, templated on the phase
-// count N (and, for the smoother, on the scalar type).  Instantiated once per
-// N in ac_inst_n<N>.cu; the host driver (ac_api.cu) calls them through the
-// Ops table declared in ac_ops.h.
+// count N, the scalar type T of a multigrid solve and its constraint form SH
+// (see proj_box).  Instantiated once per N in ac_inst_n<N>.cu; the host driver
+// (ac_api.cu) calls them through the Ops table of ac_ops.h.
 //
-// Data layout in HBM (all arrays node-major, phase innermost):
-//   u, b, d, rt   : n x N          (phase field, right-hand side, line-search
-//                                   direction, tangent-projected residual)
-//   mom           : n x 4          (m1 red, green, blue, m2; m0 comes from
-//                                   the node class)
-//   mask          : n bytes        (bit i set: phase i is free at the node)
-//   coarse level k: op n_k x 4 x N (S entries C, E, N, NE per phase; W, S,
-//                                   SW are read from the neighbours' E, N, NE)
-//                   r, v, t n_k x N
+// Two solves share these kernels:
+//   FP64 form : T = double, SH = false, unknown x = u, right-hand side b.
+//   mixed form: T = float,  SH = true,  unknown x = delta (a correction of the
+//               FP64 state u), right-hand side r = b - S u (computed in FP64),
+//               obstacle ob = u rounded to float (delta_i >= -u_i, sum 0).
+//
+// Data layout in HBM:
+//   fine level (node-major, phase innermost, n x N): x, rhs, ob, rt, d;
+//     mask n bytes (bit i: phase i free at the node); mom n x 4 (m1 RGB, m2)
+//   coarse level k (phase-major, so a thread per node reads coalesced rows):
+//     op[(c*N + i)*n_k + node], c in {C, E, N, NE} (W, S, SW are the
+//     neighbours' E, N, NE); r, v, t [i*n_k + node].
 #pragma once
 #include "ac_device.cuh"
 #include "ac_ops.h"
@@ -20,9 +23,16 @@ namespace ac {
 
 constexpr int kBlock = 256;
 
+// m1 (RGB) and m2 of one node as two 16-byte loads.
+__device__ __forceinline__ double4 ld_mom(const double *p) {
+  const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+  return make_double4(a.x, a.y, b.x, b.y);
+}
+
 // ---------------------------------------------------------------------------
-// Deterministic block reduction of K values per thread; thread k < K of the
-// block writes the block's k-th total to dst[k].
+// Deterministic block reduction of K values per thread; threads k < K write
+// the block's totals to dst[k].
 // ---------------------------------------------------------------------------
 template <int K>
 __device__ __forceinline__ void block_sum_store(double (&v)[K], double *dst) {
@@ -39,6 +49,18 @@ __device__ __forceinline__ void block_sum_store(double (&v)[K], double *dst) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w][k];
     dst[k] = s;
+  }
+}
+
+__device__ __forceinline__ void block_max_atomic(double e, double *rho) {
+  __shared__ double sm[kBlock / 32];
+  e = warp_nanmax(e);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+    v = warp_nanmax(v);
+    if (threadIdx.x == 0) atomic_max_nonneg(rho, v);
   }
 }
 
@@ -119,53 +141,60 @@ __global__ void k_init_random(double *__restrict__ u, int64_t n, uint64_t seed) 
 }
 
 // ---------------------------------------------------------------------------
-// a2: colour means and energy terms.  Per phase i the block partials hold
-//   q=0 mass   sum_n u m0          q=1..3 sum_n u m1 (RGB)
-//   q=4 sum_n u m2                 q=5 sum_n m0 u (1 - u)
-//   q=6 sum over axis edges of w (u_a - u_b)^2   (= u_i' A u_i)
-// at index q*N + i.  (Eq. VV_fidelity, Sec. 4.4; Eq. E.)
+// a2: colour means (and, with ENERGY, the energy terms), FP64 accumulation.
+// Per phase i the block partials hold at index q*N + i:
+//   q=0 mass = sum_n u m0        q=1..3 sum_n u m1 (RGB)
+//   ENERGY only: q=4 sum_n u m2, q=5 sum_n m0 u (1-u),
+//                q=6 sum over axis edges of w (u_a - u_b)^2  (= u_i' A u_i)
+// (Eq. VV_fidelity with the RGB fitting of Sec. 4.4; Eq. E.)
 // ---------------------------------------------------------------------------
-template <int N>
+template <int N, bool ENERGY>
 __global__ void __launch_bounds__(kBlock) k_means_partial(const double *__restrict__ u, const double *__restrict__ mom,
                                                           Geo g, double *__restrict__ part) {
-  double acc[7 * N];
+  constexpr int Q = ENERGY ? 7 : 4;
+  double acc[Q * N];
 #pragma unroll
-  for (int k = 0; k < 7 * N; ++k) acc[k] = 0.0;
+  for (int k = 0; k < Q * N; ++k) acc[k] = 0.0;
   const int64_t n = (int64_t)g.Wn * (g.H + 1);
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % g.Wn), y = (int)(k / g.Wn);
     const double m0 = g.m0[node_class(g, x, y)];
-    double uk[N], t[N];
+    double uk[N];
     ldn<double, N>(u + k * N, uk);
-    const double *m = mom + k * 4;
-    const double m1r = m[0], m1g = m[1], m1b = m[2], m2 = m[3];
+    const double4 m = ld_mom(mom + k * 4);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       acc[0 * N + i] += uk[i] * m0;
-      acc[1 * N + i] += uk[i] * m1r;
-      acc[2 * N + i] += uk[i] * m1g;
-      acc[3 * N + i] += uk[i] * m1b;
-      acc[4 * N + i] += uk[i] * m2;
-      acc[5 * N + i] += m0 * uk[i] * (1.0 - uk[i]);
+      acc[1 * N + i] += uk[i] * m.x;
+      acc[2 * N + i] += uk[i] * m.y;
+      acc[3 * N + i] += uk[i] * m.z;
     }
-    Weights w = edge_weights(g, x, y);
-    if (x < g.W) {
-      ldn<double, N>(u + (k + 1) * N, t);
+    if constexpr (ENERGY) {
+      double t[N];
 #pragma unroll
-      for (int i = 0; i < N; ++i) acc[6 * N + i] += (double)w.e * (uk[i] - t[i]) * (uk[i] - t[i]);
-    }
-    if (y < g.H) {
-      ldn<double, N>(u + (k + g.Wn) * N, t);
+      for (int i = 0; i < N; ++i) {
+        acc[4 * N + i] += uk[i] * m.w;
+        acc[5 * N + i] += m0 * uk[i] * (1.0 - uk[i]);
+      }
+      Weights w = edge_weights(g, x, y);
+      if (x < g.W) {
+        ldn<double, N>(u + (k + 1) * N, t);
 #pragma unroll
-      for (int i = 0; i < N; ++i) acc[6 * N + i] += (double)w.n * (uk[i] - t[i]) * (uk[i] - t[i]);
+        for (int i = 0; i < N; ++i) acc[6 * N + i] += (double)w.e * (uk[i] - t[i]) * (uk[i] - t[i]);
+      }
+      if (y < g.H) {
+        ldn<double, N>(u + (k + g.Wn) * N, t);
+#pragma unroll
+        for (int i = 0; i < N; ++i) acc[6 * N + i] += (double)w.n * (uk[i] - t[i]) * (uk[i] - t[i]);
+      }
     }
   }
-  block_sum_store<7 * N>(acc, part + (int64_t)blockIdx.x * 7 * N);
+  block_sum_store<Q * N>(acc, part + (int64_t)blockIdx.x * Q * N);
 }
 
-// c_i = s_i / mass_i (previous c kept when mass_i == 0); energy of Eq. (E):
-// sum_i eps/2 u'Au + (1/eps) sum m0 u(1-u) + lambda (U2 - |s|^2/mass).
-template <int N>
+// c_i = s_i / mass_i (previous c kept when mass_i == 0).  With ENERGY the
+// discrete Eq. (E): sum_i eps/2 u'Au + (1/eps) sum m0 u(1-u) + lambda (U2 - |s|^2/mass).
+template <int N, bool ENERGY>
 __global__ void k_means_finish(const double *__restrict__ tot, double *__restrict__ c, double *__restrict__ energy,
                                double eps, double lam) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -177,16 +206,18 @@ __global__ void k_means_finish(const double *__restrict__ tot, double *__restric
       c[i * 3 + 0] = s0 / mass;
       c[i * 3 + 1] = s1 / mass;
       c[i * 3 + 2] = s2 / mass;
-      E += lam * (tot[4 * N + i] - (s0 * s0 + s1 * s1 + s2 * s2) / mass);
     }
-    E += tot[5 * N + i] / eps + 0.5 * eps * tot[6 * N + i];
+    if constexpr (ENERGY) {
+      if (mass != 0.0) E += lam * (tot[4 * N + i] - (s0 * s0 + s1 * s1 + s2 * s2) / mass);
+      E += tot[5 * N + i] / eps + 0.5 * eps * tot[6 * N + i];
+    }
   }
-  if (energy) *energy = E;
+  if (ENERGY && energy) *energy = E;
 }
 
 // ---------------------------------------------------------------------------
 // a3: right-hand side b = m0 u^t (1 + 2 tau/eps) - tau lambda f(c^t), with
-// f_n,i = m2 - 2 c_i.m1 + |c_i|^2 m0  (Eq. alpha multiplied out).
+// f_n,i = m2 - 2 c_i.m1 + |c_i|^2 m0  (Eq. alpha multiplied out), FP64.
 // ---------------------------------------------------------------------------
 template <int N>
 __global__ void k_rhs(const double *__restrict__ u, const double *__restrict__ mom, const double *__restrict__ c, Geo g,
@@ -196,16 +227,72 @@ __global__ void k_rhs(const double *__restrict__ u, const double *__restrict__ m
   if (k >= n) return;
   const int x = (int)(k % g.Wn), y = (int)(k / g.Wn);
   const double m0 = g.m0[node_class(g, x, y)];
-  const double *m = mom + k * 4;
+  const double4 m = ld_mom(mom + k * 4);
   double uk[N], bk[N];
   ldn<double, N>(u + k * N, uk);
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     const double c0 = c[i * 3], c1 = c[i * 3 + 1], c2 = c[i * 3 + 2];
-    const double f = m[3] - 2.0 * (c0 * m[0] + c1 * m[1] + c2 * m[2]) + (c0 * c0 + c1 * c1 + c2 * c2) * m0;
+    const double f = m.w - 2.0 * (c0 * m.x + c1 * m.y + c2 * m.z) + (c0 * c0 + c1 * c1 + c2 * c2) * m0;
     bk[i] = m0 * uk[i] * a1 - tl * f;
   }
   stn<double, N>(b + k * N, bk);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed form, FP64 outer defect correction.
+// k_outer_resid: r = b - S u in FP64; stores r and u rounded to float (the
+// right-hand side and obstacle of the FP32 correction solve) and the natural
+// residual max_n |P_G(u_n + z_n) - u_n|, z = r/S_nn, computed in FP64 as a
+// correction by the shifted projection.
+// k_outer_update: u <- P_G(u + delta) in FP64.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict__ u, const double *__restrict__ b, Geo g,
+                                                        float *__restrict__ r32, float *__restrict__ u32,
+                                                        double *__restrict__ rho) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  double e = 0.0;
+  if (x <= g.W) {
+    const int64_t n = (int64_t)y * g.Wn + x;
+    double acc[N], uk[N], bk[N];
+    nbr_sum<double, N>(u, g, x, y, acc);
+    ldn<double, N>(u + n * N, uk);
+    ldn<double, N>(b + n * N, bk);
+    const int cls = node_class(g, x, y);
+    const double D = g.D[cls], invD = g.invD[cls];
+    float rf[N], uf[N];
+    double z[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const double r = bk[i] + g.te * acc[i] - D * uk[i];
+      rf[i] = (float)r;
+      uf[i] = (float)uk[i];
+      z[i] = r * invD;
+    }
+    stn<float, N>(r32 + n * N, rf);
+    stn<float, N>(u32 + n * N, uf);
+    proj_box<double, N, true>(z, uk);
+#pragma unroll
+    for (int i = 0; i < N; ++i) e = nanmax(e, fabs(z[i]));
+    if (!(uk[0] == uk[0])) e = uk[0];
+  }
+  block_max_atomic(e, rho);
+}
+
+template <int N>
+__global__ void k_outer_update(double *__restrict__ u, const float *__restrict__ delta, int64_t n) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double uk[N];
+  float dk[N];
+  ldn_rw<double, N>(u + k * N, uk);
+  ldn<float, N>(delta + k * N, dk);
+#pragma unroll
+  for (int i = 0; i < N; ++i) uk[i] += (double)dk[i];
+  proj_simplex<double, N>(uk);
+  stn<double, N>(u + k * N, uk);
 }
 
 // ---------------------------------------------------------------------------
@@ -213,113 +300,136 @@ __global__ void k_rhs(const double *__restrict__ u, const double *__restrict__ m
 // level (Sec. 3.1: nodal sub-problems in red-black order; Sec. 3.3: each
 // nodal N-vector projected onto the simplex).  Nodes with (x + y) % 2 ==
 // color are independent given the other colour:
-//   y_n = (b_n + tau eps sum_m w_nm u_m) / S_nn,   u_n <- P_G(y_n).
+//   z_n = (rhs_n + tau eps sum_m w_nm x_m) / S_nn,   x_n <- P(z_n).
 // ---------------------------------------------------------------------------
-template <typename T, int N>
-__global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ u, const T *__restrict__ b, Geo g, int color) {
+template <typename T, int N, bool SH>
+__global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const T *__restrict__ rhs,
+                                                        const T *__restrict__ ob, Geo g, int color) {
   const int y = blockIdx.y;
-  const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((y + color) & 1);
-  if (x > g.W) return;
-  const int64_t n = (int64_t)y * g.Wn + x;
-  T acc[N], bk[N];
-  nbr_sum<T, N>(u, g, x, y, acc);
-  ldn<T, N>(b + n * N, bk);
-  const int cls = node_class(g, x, y);
+  const int xx = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((y + color) & 1);
+  if (xx > g.W) return;
+  const int64_t n = (int64_t)y * g.Wn + xx;
+  T acc[N], bk[N], o[N];
+  nbr_sum<T, N>(x, g, xx, y, acc);
+  ldn<T, N>(rhs + n * N, bk);
+  if constexpr (SH) ldn<T, N>(ob + n * N, o);
+  const int cls = node_class(g, xx, y);
   const T te = (T)g.te, invD = (T)g.invD[cls];
 #pragma unroll
   for (int i = 0; i < N; ++i) acc[i] = (bk[i] + te * acc[i]) * invD;
-  proj_simplex<T, N>(acc);
-  stn<T, N>(u + n * N, acc);
+  proj_box<T, N, SH>(acc, o);
+  stn<T, N>(x + n * N, acc);
 }
 
 // ---------------------------------------------------------------------------
-// a6/a9: fine residual r = b - S u, natural residual rho = max |u - P_G(y)|,
-// free-phase mask and the tangent projection of r over the free phases:
-//   free_n,i = (u_n,i > 0) and at least two phases of node n are > 0;
+// a6/a9: fine residual r = rhs - S x, natural residual rho = max |x - P(z)|
+// (z = x + r/S_nn), free-phase mask and the tangent projection of r:
+//   free_n,i = x_n,i above its bound, and at least two phases of node n free;
 //   rt_n,i   = r_n,i - mean_{free j} r_n,j for free i, 0 otherwise.
 // A node at a vertex of the simplex has no free phase.  rt and mask may be
 // null (residual only).
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(kBlock) k_fine_resid(const double *__restrict__ u, const double *__restrict__ b, Geo g,
-                                                       double *__restrict__ rt, uint8_t *__restrict__ mask,
-                                                       double *__restrict__ rho) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+template <typename T, int N, bool SH>
+__global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, const T *__restrict__ rhs,
+                                                       const T *__restrict__ ob, Geo g, T *__restrict__ rt,
+                                                       uint8_t *__restrict__ mask, double *__restrict__ rho) {
+  const int xx = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   double e = 0.0;
-  if (x <= g.W) {
-    const int64_t n = (int64_t)y * g.Wn + x;
-    double acc[N], uk[N], bk[N], r[N];
-    nbr_sum<double, N>(u, g, x, y, acc);
-    ldn<double, N>(u + n * N, uk);
-    ldn<double, N>(b + n * N, bk);
-    const int cls = node_class(g, x, y);
-    const double D = g.D[cls], invD = g.invD[cls];
+  if (xx <= g.W) {
+    const int64_t n = (int64_t)y * g.Wn + xx;
+    T acc[N], xk[N], bk[N], r[N], o[N];
+    nbr_sum<T, N>(x, g, xx, y, acc);
+    ldn<T, N>(x + n * N, xk);
+    ldn<T, N>(rhs + n * N, bk);
+    if constexpr (SH) ldn<T, N>(ob + n * N, o);
+    const int cls = node_class(g, xx, y);
+    const T D = (T)g.D[cls], invD = (T)g.invD[cls], te = (T)g.te;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      r[i] = bk[i] + g.te * acc[i] - D * uk[i];
-      acc[i] = (bk[i] + g.te * acc[i]) * invD;
+      r[i] = bk[i] + te * acc[i] - D * xk[i];
+      acc[i] = (bk[i] + te * acc[i]) * invD;
     }
-    proj_simplex<double, N>(acc);
+    proj_box<T, N, SH>(acc, o);
     int cnt = 0;
     unsigned pos = 0;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      e = nanmax(e, fabs(uk[i] - acc[i]));
-      if (uk[i] > 0.0) {
+      e = nanmax(e, (double)fabs(xk[i] - acc[i]));
+      const T lo = SH ? -o[i] : T(0);
+      if (xk[i] > lo) {
         pos |= 1u << i;
         ++cnt;
       }
     }
-    if (!(uk[0] == uk[0])) e = uk[0];  // NaN in u
-    const unsigned fr = cnt >= 2 ? pos : 0u;
+    if (!(xk[0] == xk[0])) e = (double)xk[0];
     if (rt) {
-      double s = 0.0;
+      const unsigned fr = cnt >= 2 ? pos : 0u;
+      T s = T(0);
 #pragma unroll
       for (int i = 0; i < N; ++i)
         if ((fr >> i) & 1u) s += r[i];
-      const double mean = cnt >= 2 ? s * rcp_small<double>(cnt) : 0.0;
+      const T mean = cnt >= 2 ? s * rcp_small<T>(cnt) : T(0);
 #pragma unroll
-      for (int i = 0; i < N; ++i) r[i] = ((fr >> i) & 1u) ? r[i] - mean : 0.0;
-      stn<double, N>(rt + n * N, r);
+      for (int i = 0; i < N; ++i) r[i] = ((fr >> i) & 1u) ? r[i] - mean : T(0);
+      stn<T, N>(rt + n * N, r);
       mask[n] = (uint8_t)fr;
     }
   }
-  // block max -> one atomic per block
-  __shared__ double sm[kBlock / 32];
-  e = warp_nanmax(e);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = e;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
-    v = warp_nanmax(v);
-    if (threadIdx.x == 0) atomic_max_nonneg(rho, v);
-  }
+  block_max_atomic(e, rho);
 }
 
 // ---------------------------------------------------------------------------
 // Restriction r_c(K) = sum_a P_aK t(a) over the 7 fine nodes of the support
 // of the coarse basis function (weights 1 at 2K, 1/2 at E, W, N, S, NE, SW).
+// k_restrict0: fine (node-major) -> first coarse level (phase-major);
+// k_restrict : coarse -> coarser (both phase-major).
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void k_restrict(const double *__restrict__ t, Geo gf, Geo gc, double *__restrict__ rc) {
+template <typename T, int N>
+__global__ void k_restrict0(const T *__restrict__ t, Geo gf, Geo gc, T *__restrict__ rc) {
   const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
   if (X > gc.W) return;
   constexpr int dx[7] = {0, 1, -1, 0, 0, 1, -1};
   constexpr int dy[7] = {0, 0, 0, 1, -1, 1, -1};
-  double acc[N], v[N];
+  T acc[N], v[N];
 #pragma unroll
-  for (int i = 0; i < N; ++i) acc[i] = 0.0;
+  for (int i = 0; i < N; ++i) acc[i] = T(0);
 #pragma unroll
   for (int s = 0; s < 7; ++s) {
     const int ax = 2 * X + dx[s], ay = 2 * Y + dy[s];
     if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
-    const double p = s == 0 ? 1.0 : 0.5;
-    ldn<double, N>(t + ((int64_t)ay * gf.Wn + ax) * N, v);
+    const T p = s == 0 ? T(1) : T(0.5);
+    ldn<T, N>(t + ((int64_t)ay * gf.Wn + ax) * N, v);
 #pragma unroll
     for (int i = 0; i < N; ++i) acc[i] += p * v[i];
   }
-  stn<double, N>(rc + ((int64_t)Y * gc.Wn + X) * N, acc);
+  const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), K = (int64_t)Y * gc.Wn + X;
+#pragma unroll
+  for (int i = 0; i < N; ++i) rc[i * nc + K] = acc[i];
+}
+
+template <typename T, int N>
+__global__ void k_restrict(const T *__restrict__ t, Geo gf, Geo gc, T *__restrict__ rc) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
+  if (X > gc.W) return;
+  constexpr int dx[7] = {0, 1, -1, 0, 0, 1, -1};
+  constexpr int dy[7] = {0, 0, 0, 1, -1, 1, -1};
+  const int64_t nf = (int64_t)gf.Wn * (gf.H + 1), nc = (int64_t)gc.Wn * (gc.H + 1);
+  T acc[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) acc[i] = T(0);
+#pragma unroll
+  for (int s = 0; s < 7; ++s) {
+    const int ax = 2 * X + dx[s], ay = 2 * Y + dy[s];
+    if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
+    const T p = s == 0 ? T(1) : T(0.5);
+    const int64_t a = (int64_t)ay * gf.Wn + ax;
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] += p * t[i * nf + a];
+  }
+  const int64_t K = (int64_t)Y * gc.Wn + X;
+#pragma unroll
+  for (int i = 0; i < N; ++i) rc[i * nc + K] = acc[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -327,7 +437,8 @@ __global__ void k_restrict(const double *__restrict__ t, Geo gf, Geo gc, double 
 //   S_1,i = P' M_i S M_i P,  M_i = diag(free_n,i)  (truncated prolongation).
 // Stored as the C, E, N, NE entries of each coarse node.  Phases free on the
 // whole neighbourhood use the untruncated product (computed once per node);
-// phases free nowhere get 0.
+// phases free nowhere get 0.  The entries are sums of at most 35 products of
+// dyadic weights with S entries, accumulated in float.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double fine_S(const Geo &g, int ax, int ay, int ddx, int ddy) {
   if (ddx == 0 && ddy == 0) return g.D[node_class(g, ax, ay)];
@@ -336,9 +447,9 @@ __device__ __forceinline__ double fine_S(const Geo &g, int ax, int ay, int ddx, 
   return -g.te * (double)ww;
 }
 
-template <int N>
+template <typename T, int N>
 __global__ void __launch_bounds__(kBlock) k_galerkin0(const uint8_t *__restrict__ mask, Geo gf, Geo gc,
-                                                      double *__restrict__ op) {
+                                                      T *__restrict__ op) {
   const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
   if (X > gc.W) return;
   constexpr int sx[7] = {0, 1, -1, 0, 0, 1, -1};
@@ -347,7 +458,6 @@ __global__ void __launch_bounds__(kBlock) k_galerkin0(const uint8_t *__restrict_
   constexpr int oy[5] = {0, 0, 0, 1, -1};
   constexpr int lx[4] = {0, 1, 0, 1};  // L = K + (lx, ly): C, E, N, NE
   constexpr int ly[4] = {0, 0, 1, 1};
-  // neighbourhood masks: AND (free everywhere) and OR (free somewhere)
   unsigned all = (1u << N) - 1u, any = 0u;
   for (int ay = 2 * Y - 2; ay <= 2 * Y + 3; ++ay)
     for (int ax = 2 * X - 2; ax <= 2 * X + 3; ++ax) {
@@ -356,32 +466,38 @@ __global__ void __launch_bounds__(kBlock) k_galerkin0(const uint8_t *__restrict_
       all &= m;
       any |= m;
     }
-  double full[4] = {0, 0, 0, 0};
-  double acc[4][N];
+  const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), K = (int64_t)Y * gc.Wn + X;
+  if (!any) {
+#pragma unroll
+    for (int c = 0; c < 4 * N; ++c) op[c * nc + K] = T(0);
+    return;
+  }
+  T full[4] = {0, 0, 0, 0};
+  T acc[4][N];
 #pragma unroll
   for (int l = 0; l < 4; ++l)
 #pragma unroll
-    for (int i = 0; i < N; ++i) acc[l][i] = 0.0;
+    for (int i = 0; i < N; ++i) acc[l][i] = T(0);
   const unsigned partial = any & ~all;
 #pragma unroll 1
   for (int s = 0; s < 7; ++s) {
     const int ax = 2 * X + sx[s], ay = 2 * Y + sy[s];
     if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
-    const double pa = s == 0 ? 1.0 : 0.5;
+    const T pa = s == 0 ? T(1) : T(0.5);
     const unsigned ma = mask[(int64_t)ay * gf.Wn + ax];
 #pragma unroll 1
     for (int o = 0; o < 5; ++o) {
       const int bx = ax + ox[o], by = ay + oy[o];
       if (bx < 0 || bx > gf.W || by < 0 || by > gf.H) continue;
-      const double sab = fine_S(gf, ax, ay, ox[o], oy[o]);
+      const T sab = (T)fine_S(gf, ax, ay, ox[o], oy[o]);
       const unsigned mm = ma & mask[(int64_t)by * gf.Wn + bx] & partial;
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         const int LX = X + lx[l], LY = Y + ly[l];
         if (LX > gc.W || LY > gc.H) continue;
-        const double q = hat_weight(bx - 2 * LX, by - 2 * LY);
-        if (q == 0.0) continue;
-        const double cf = pa * sab * q;
+        const T q = (T)hat_weight(bx - 2 * LX, by - 2 * LY);
+        if (q == T(0)) continue;
+        const T cf = pa * sab * q;
         full[l] += cf;
         if (mm) {
 #pragma unroll
@@ -391,121 +507,123 @@ __global__ void __launch_bounds__(kBlock) k_galerkin0(const uint8_t *__restrict_
       }
     }
   }
-  double *o = op + ((int64_t)Y * gc.Wn + X) * 4 * N;
 #pragma unroll
   for (int l = 0; l < 4; ++l)
 #pragma unroll
-    for (int i = 0; i < N; ++i) o[l * N + i] = ((all >> i) & 1u) ? full[l] : acc[l][i];
+    for (int i = 0; i < N; ++i) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? full[l] : acc[l][i];
 }
 
 // S entry (K, K + d) of a stored coarse operator, d in the 7-point pattern.
-template <int N>
-__device__ __forceinline__ double op_entry(const double *op, const Geo &g, int x, int y, int ddx, int ddy, int i) {
+template <typename T, int N>
+__device__ __forceinline__ T op_entry(const T *op, const Geo &g, int64_t nc, int x, int y, int ddx, int ddy, int i) {
   // C, E, N, NE are stored at the node; W, S, SW at the neighbour.
-  if (ddx == 0 && ddy == 0) return op[((int64_t)y * g.Wn + x) * 4 * N + 0 * N + i];
-  if (ddx == 1 && ddy == 0) return op[((int64_t)y * g.Wn + x) * 4 * N + 1 * N + i];
-  if (ddx == 0 && ddy == 1) return op[((int64_t)y * g.Wn + x) * 4 * N + 2 * N + i];
-  if (ddx == 1 && ddy == 1) return op[((int64_t)y * g.Wn + x) * 4 * N + 3 * N + i];
-  if (ddx == -1 && ddy == 0) return op[((int64_t)y * g.Wn + x - 1) * 4 * N + 1 * N + i];
-  if (ddx == 0 && ddy == -1) return op[((int64_t)(y - 1) * g.Wn + x) * 4 * N + 2 * N + i];
-  return op[((int64_t)(y - 1) * g.Wn + x - 1) * 4 * N + 3 * N + i];  // SW
+  const int64_t K = (int64_t)y * g.Wn + x;
+  if (ddx == 0 && ddy == 0) return op[(0 * N + i) * nc + K];
+  if (ddx == 1 && ddy == 0) return op[(1 * N + i) * nc + K];
+  if (ddx == 0 && ddy == 1) return op[(2 * N + i) * nc + K];
+  if (ddx == 1 && ddy == 1) return op[(3 * N + i) * nc + K];
+  if (ddx == -1 && ddy == 0) return op[(1 * N + i) * nc + K - 1];
+  if (ddx == 0 && ddy == -1) return op[(2 * N + i) * nc + K - g.Wn];
+  return op[(3 * N + i) * nc + K - g.Wn - 1];  // SW
 }
 
 // Galerkin product of a stored 7-point operator: S_c = P' S_f P.
-template <int N>
-__global__ void __launch_bounds__(kBlock) k_galerkin(const double *__restrict__ opf, Geo gf, Geo gc,
-                                                     double *__restrict__ opc) {
+template <typename T, int N>
+__global__ void __launch_bounds__(kBlock) k_galerkin(const T *__restrict__ opf, Geo gf, Geo gc, T *__restrict__ opc) {
   const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
   if (X > gc.W) return;
   constexpr int sx[7] = {0, 1, -1, 0, 0, 1, -1};
   constexpr int sy[7] = {0, 0, 0, 1, -1, 1, -1};
   constexpr int lx[4] = {0, 1, 0, 1};
   constexpr int ly[4] = {0, 0, 1, 1};
-  double acc[4][N];
+  const int64_t nf = (int64_t)gf.Wn * (gf.H + 1), nc = (int64_t)gc.Wn * (gc.H + 1);
+  T acc[4][N];
 #pragma unroll
   for (int l = 0; l < 4; ++l)
 #pragma unroll
-    for (int i = 0; i < N; ++i) acc[l][i] = 0.0;
+    for (int i = 0; i < N; ++i) acc[l][i] = T(0);
 #pragma unroll 1
   for (int s = 0; s < 7; ++s) {
     const int ax = 2 * X + sx[s], ay = 2 * Y + sy[s];
     if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
-    const double pa = s == 0 ? 1.0 : 0.5;
+    const T pa = s == 0 ? T(1) : T(0.5);
 #pragma unroll 1
     for (int o = 0; o < 7; ++o) {
       const int bx = ax + sx[o], by = ay + sy[o];
       if (bx < 0 || bx > gf.W || by < 0 || by > gf.H) continue;
-      double q[4];
+      T q[4];
       bool anyq = false;
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         const int LX = X + lx[l], LY = Y + ly[l];
-        q[l] = (LX > gc.W || LY > gc.H) ? 0.0 : hat_weight(bx - 2 * LX, by - 2 * LY);
-        anyq |= q[l] != 0.0;
+        q[l] = (LX > gc.W || LY > gc.H) ? T(0) : (T)hat_weight(bx - 2 * LX, by - 2 * LY);
+        anyq |= q[l] != T(0);
       }
       if (!anyq) continue;
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        const double sab = pa * op_entry<N>(opf, gf, ax, ay, sx[o], sy[o], i);
+        const T sab = pa * op_entry<T, N>(opf, gf, nf, ax, ay, sx[o], sy[o], i);
 #pragma unroll
         for (int l = 0; l < 4; ++l) acc[l][i] += sab * q[l];
       }
     }
   }
-  double *o = opc + ((int64_t)Y * gc.Wn + X) * 4 * N;
+  const int64_t K = (int64_t)Y * gc.Wn + X;
 #pragma unroll
   for (int l = 0; l < 4; ++l)
 #pragma unroll
-    for (int i = 0; i < N; ++i) o[l * N + i] = acc[l][i];
+    for (int i = 0; i < N; ++i) opc[(l * N + i) * nc + K] = acc[l][i];
 }
 
-// (S v)_K - S_KK v_K for one phase: the off-diagonal part of a stored operator.
-template <int N>
-__device__ __forceinline__ double op_offdiag(const double *op, const double *v, const Geo &g, int x, int y, int i) {
-  const int64_t n = (int64_t)y * g.Wn + x;
-  double s = 0.0;
-  if (x < g.W) s += op[n * 4 * N + 1 * N + i] * v[(n + 1) * N + i];
-  if (x > 0) s += op[(n - 1) * 4 * N + 1 * N + i] * v[(n - 1) * N + i];
-  if (y < g.H) s += op[n * 4 * N + 2 * N + i] * v[(n + g.Wn) * N + i];
-  if (y > 0) s += op[(n - g.Wn) * 4 * N + 2 * N + i] * v[(n - g.Wn) * N + i];
-  if (x < g.W && y < g.H) s += op[n * 4 * N + 3 * N + i] * v[(n + g.Wn + 1) * N + i];
-  if (x > 0 && y > 0) s += op[(n - g.Wn - 1) * 4 * N + 3 * N + i] * v[(n - g.Wn - 1) * N + i];
+// (S v)_K - S_KK v_K for phase i of a stored operator (phase-major arrays).
+template <typename T, int N>
+__device__ __forceinline__ T op_offdiag(const T *op, const T *v, const Geo &g, int64_t nc, int x, int y, int i) {
+  const int64_t K = (int64_t)y * g.Wn + x;
+  const T *oE = op + (1 * N + i) * nc, *oN = op + (2 * N + i) * nc, *oNE = op + (3 * N + i) * nc;
+  const T *vi = v + i * nc;
+  T s = T(0);
+  if (x < g.W) s += oE[K] * vi[K + 1];
+  if (x > 0) s += oE[K - 1] * vi[K - 1];
+  if (y < g.H) s += oN[K] * vi[K + g.Wn];
+  if (y > 0) s += oN[K - g.Wn] * vi[K - g.Wn];
+  if (x < g.W && y < g.H) s += oNE[K] * vi[K + g.Wn + 1];
+  if (x > 0 && y > 0) s += oNE[K - g.Wn - 1] * vi[K - g.Wn - 1];
   return s;
 }
 
 // a7: one colour of linear Gauss-Seidel on a coarse level; (x + y) % 3 is a
 // valid 3-colouring of the 7-point (E, W, N, S, NE, SW) pattern.  Rows with
 // a zero diagonal (no free fine node under the basis function) stay 0.
-template <int N>
-__global__ void k_coarse_smooth(const double *__restrict__ op, const double *__restrict__ r, double *__restrict__ v,
-                                Geo g, int color) {
+template <typename T, int N>
+__global__ void k_coarse_smooth(const T *__restrict__ op, const T *__restrict__ r, T *__restrict__ v, Geo g,
+                                int color) {
   const int y = blockIdx.y;
   const int x0 = ((color - y) % 3 + 3) % 3;
   const int x = x0 + 3 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (x > g.W) return;
-  const int64_t n = (int64_t)y * g.Wn + x;
+  const int64_t nc = (int64_t)g.Wn * (g.H + 1), K = (int64_t)y * g.Wn + x;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    const double d = op[n * 4 * N + i];
-    v[n * N + i] = d > 0.0 ? (r[n * N + i] - op_offdiag<N>(op, v, g, x, y, i)) / d : 0.0;
+    const T d = op[i * nc + K];
+    v[i * nc + K] = d > T(0) ? (r[i * nc + K] - op_offdiag<T, N>(op, v, g, nc, x, y, i)) / d : T(0);
   }
 }
 
 // Whole-level Gauss-Seidel in one block for small coarsest grids: `sweeps`
 // passes over the 3 colours with a barrier between colours.
-template <int N>
-__global__ void __launch_bounds__(1024) k_coarse_solve_block(const double *__restrict__ op, const double *__restrict__ r, double *__restrict__ v,
-                                     Geo g, int sweeps) {
-  const int64_t n = (int64_t)g.Wn * (g.H + 1);
+template <typename T, int N>
+__global__ void __launch_bounds__(1024) k_coarse_solve_block(const T *__restrict__ op, const T *__restrict__ r,
+                                                             T *__restrict__ v, Geo g, int sweeps) {
+  const int64_t nc = (int64_t)g.Wn * (g.H + 1);
   for (int s = 0; s < sweeps; ++s)
     for (int color = 0; color < 3; ++color) {
-      for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+      for (int64_t k = threadIdx.x; k < nc; k += blockDim.x) {
         const int x = (int)(k % g.Wn), y = (int)(k / g.Wn);
         if ((x + y) % 3 != color) continue;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-          const double d = op[k * 4 * N + i];
-          v[k * N + i] = d > 0.0 ? (r[k * N + i] - op_offdiag<N>(op, v, g, x, y, i)) / d : 0.0;
+          const T d = op[i * nc + k];
+          v[i * nc + k] = d > T(0) ? (r[i * nc + k] - op_offdiag<T, N>(op, v, g, nc, x, y, i)) / d : T(0);
         }
       }
       __syncthreads();
@@ -513,68 +631,67 @@ __global__ void __launch_bounds__(1024) k_coarse_solve_block(const double *__res
 }
 
 // t = r - S v on a coarse level.
-template <int N>
-__global__ void k_coarse_resid(const double *__restrict__ op, const double *__restrict__ r,
-                               const double *__restrict__ v, Geo g, double *__restrict__ t) {
+template <typename T, int N>
+__global__ void k_coarse_resid(const T *__restrict__ op, const T *__restrict__ r, const T *__restrict__ v, Geo g,
+                               T *__restrict__ t) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x > g.W) return;
-  const int64_t n = (int64_t)y * g.Wn + x;
+  const int64_t nc = (int64_t)g.Wn * (g.H + 1), K = (int64_t)y * g.Wn + x;
 #pragma unroll
   for (int i = 0; i < N; ++i)
-    t[n * N + i] = r[n * N + i] - op[n * 4 * N + i] * v[n * N + i] - op_offdiag<N>(op, v, g, x, y, i);
+    t[i * nc + K] = r[i * nc + K] - op[i * nc + K] * v[i * nc + K] - op_offdiag<T, N>(op, v, g, nc, x, y, i);
 }
 
-// P1 prolongation of coarse values to fine node (x, y) (nested right-diagonal
-// meshes: odd-odd fine nodes sit on the coarse SW-NE diagonal).
-template <int N>
-__device__ __forceinline__ void prolong_at(const double *vc, const Geo &gc, int x, int y, double (&o)[N]) {
-  const int X0 = x >> 1, Y0 = y >> 1;
-  double a[N];
-  ldn<double, N>(vc + ((int64_t)Y0 * gc.Wn + X0) * N, o);
-  if ((x & 1) == 0 && (y & 1) == 0) return;
-  const int X1 = X0 + (x & 1), Y1 = Y0 + (y & 1);
-  ldn<double, N>(vc + ((int64_t)Y1 * gc.Wn + X1) * N, a);
+// P1 prolongation of phase-major coarse values to fine node (x, y) (nested
+// right-diagonal meshes: odd-odd fine nodes sit on the coarse SW-NE diagonal).
+template <typename T, int N>
+__device__ __forceinline__ void prolong_at(const T *vc, const Geo &gc, int x, int y, T (&o)[N]) {
+  const int64_t nc = (int64_t)gc.Wn * (gc.H + 1);
+  const int64_t K0 = (int64_t)(y >> 1) * gc.Wn + (x >> 1);
 #pragma unroll
-  for (int i = 0; i < N; ++i) o[i] = 0.5 * (o[i] + a[i]);
+  for (int i = 0; i < N; ++i) o[i] = vc[i * nc + K0];
+  if ((x & 1) == 0 && (y & 1) == 0) return;
+  const int64_t K1 = K0 + (x & 1) + (int64_t)(y & 1) * gc.Wn;
+#pragma unroll
+  for (int i = 0; i < N; ++i) o[i] = T(0.5) * (o[i] + vc[i * nc + K1]);
 }
 
-// v_f += P v_c.
-template <int N>
-__global__ void k_prolong_add(const double *__restrict__ vc, Geo gf, Geo gc, double *__restrict__ vf) {
+// v_f += P v_c (coarse levels, phase-major).
+template <typename T, int N>
+__global__ void k_prolong_add(const T *__restrict__ vc, Geo gf, Geo gc, T *__restrict__ vf) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x > gf.W) return;
-  double p[N], o[N];
-  prolong_at<N>(vc, gc, x, y, p);
-  const int64_t n = (int64_t)y * gf.Wn + x;
-  ldn_rw<double, N>(vf + n * N, o);
+  T p[N];
+  prolong_at<T, N>(vc, gc, x, y, p);
+  const int64_t nf = (int64_t)gf.Wn * (gf.H + 1), a = (int64_t)y * gf.Wn + x;
 #pragma unroll
-  for (int i = 0; i < N; ++i) o[i] += p[i];
-  stn<double, N>(vf + n * N, o);
+  for (int i = 0; i < N; ++i) vf[i * nf + a] += p[i];
 }
 
 // ---------------------------------------------------------------------------
 // a8: coarse correction on the fine level with a feasible line search.
 //   w   = tangent projection (over the free phases) of the truncated
 //         prolongation M_i (P v)_i,
-//   d   = P_G(u + w) - u  (feasible direction: K is convex),
-//   omega = clamp(rt'd / d'Sd, 0, 1) minimises the step energy on [u, u + d].
+//   d   = P(x + w) - x  (feasible direction: the constraint set is convex),
+//   omega = clamp(rt'd / d'Sd, 0, 1) minimises the step energy on [x, x + d].
 // k_ls_dir writes d and the block partials of rt'd; k_ls_curv the partials of
-// d'Sd; k_ls_finish computes omega; k_apply does u += omega d.
+// d'Sd; k_ls_finish computes omega; k_apply does x += omega d.
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(kBlock) k_ls_dir(const double *__restrict__ u, const double *__restrict__ rt,
-                                                   const double *__restrict__ v1, const uint8_t *__restrict__ mask,
-                                                   Geo gf, Geo gc, double *__restrict__ d, double *__restrict__ part) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+template <typename T, int N, bool SH>
+__global__ void __launch_bounds__(kBlock) k_ls_dir(const T *__restrict__ x, const T *__restrict__ ob,
+                                                   const T *__restrict__ rt, const T *__restrict__ v1,
+                                                   const uint8_t *__restrict__ mask, Geo gf, Geo gc,
+                                                   T *__restrict__ d, double *__restrict__ part) {
+  const int xx = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   double dot[1] = {0.0};
-  if (x <= gf.W) {
-    const int64_t n = (int64_t)y * gf.Wn + x;
+  if (xx <= gf.W) {
+    const int64_t n = (int64_t)y * gf.Wn + xx;
     const unsigned fr = mask[n];
-    double dn[N];
+    T dn[N];
     if (fr) {
-      double w[N], uk[N], r[N];
-      prolong_at<N>(v1, gc, x, y, w);
-      double s = 0.0;
+      T w[N], xk[N], r[N], o[N];
+      prolong_at<T, N>(v1, gc, xx, y, w);
+      T s = T(0);
       int cnt = 0;
 #pragma unroll
       for (int i = 0; i < N; ++i)
@@ -582,38 +699,39 @@ __global__ void __launch_bounds__(kBlock) k_ls_dir(const double *__restrict__ u,
           s += w[i];
           ++cnt;
         }
-      const double mean = s * rcp_small<double>(cnt);
-      ldn<double, N>(u + n * N, uk);
+      const T mean = s * rcp_small<T>(cnt);
+      ldn<T, N>(x + n * N, xk);
+      if constexpr (SH) ldn<T, N>(ob + n * N, o);
 #pragma unroll
-      for (int i = 0; i < N; ++i) w[i] = uk[i] + (((fr >> i) & 1u) ? w[i] - mean : 0.0);
-      proj_simplex<double, N>(w);
-      ldn<double, N>(rt + n * N, r);
+      for (int i = 0; i < N; ++i) w[i] = xk[i] + (((fr >> i) & 1u) ? w[i] - mean : T(0));
+      proj_box<T, N, SH>(w, o);
+      ldn<T, N>(rt + n * N, r);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        dn[i] = w[i] - uk[i];
-        dot[0] += r[i] * dn[i];
+        dn[i] = w[i] - xk[i];
+        dot[0] += (double)r[i] * (double)dn[i];
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < N; ++i) dn[i] = 0.0;
+      for (int i = 0; i < N; ++i) dn[i] = T(0);
     }
-    stn<double, N>(d + n * N, dn);
+    stn<T, N>(d + n * N, dn);
   }
   block_sum_store<1>(dot, part + blockIdx.y * gridDim.x + blockIdx.x);
 }
 
-template <int N>
-__global__ void __launch_bounds__(kBlock) k_ls_curv(const double *__restrict__ d, Geo g, double *__restrict__ part) {
+template <typename T, int N>
+__global__ void __launch_bounds__(kBlock) k_ls_curv(const T *__restrict__ d, Geo g, double *__restrict__ part) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   double dot[1] = {0.0};
   if (x <= g.W) {
     const int64_t n = (int64_t)y * g.Wn + x;
-    double acc[N], dk[N];
-    nbr_sum<double, N>(d, g, x, y, acc);
-    ldn<double, N>(d + n * N, dk);
-    const double D = g.D[node_class(g, x, y)];
+    T acc[N], dk[N];
+    nbr_sum<T, N>(d, g, x, y, acc);
+    ldn<T, N>(d + n * N, dk);
+    const T D = (T)g.D[node_class(g, x, y)], te = (T)g.te;
 #pragma unroll
-    for (int i = 0; i < N; ++i) dot[0] += dk[i] * (D * dk[i] - g.te * acc[i]);
+    for (int i = 0; i < N; ++i) dot[0] += (double)dk[i] * (double)(D * dk[i] - te * acc[i]);
   }
   block_sum_store<1>(dot, part + blockIdx.y * gridDim.x + blockIdx.x);
 }
@@ -626,22 +744,24 @@ static __global__ void k_ls_finish(const double *__restrict__ tot, double *__res
   *omega = w;
 }
 
-template <int N>
-__global__ void k_apply(double *__restrict__ u, const double *__restrict__ d, const double *__restrict__ omega,
-                        int64_t n) {
+template <typename T, int N, bool SH>
+__global__ void k_apply(T *__restrict__ x, const T *__restrict__ ob, const T *__restrict__ d,
+                        const double *__restrict__ omega, int64_t n) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
-  const double w = *omega;
-  if (w == 0.0) return;
-  double uk[N], dk[N];
-  ldn_rw<double, N>(u + k * N, uk);
-  ldn<double, N>(d + k * N, dk);
+  const T w = (T)*omega;
+  if (w == T(0)) return;
+  T xk[N], dk[N], o[N];
+  ldn_rw<T, N>(x + k * N, xk);
+  ldn<T, N>(d + k * N, dk);
+  if constexpr (SH) ldn<T, N>(ob + k * N, o);
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    uk[i] += w * dk[i];
-    if (uk[i] < 0.0) uk[i] = 0.0;  // rounding residue of u_i + w (-u_i)
+    xk[i] += w * dk[i];
+    const T lo = SH ? -o[i] : T(0);
+    if (xk[i] < lo) xk[i] = lo;  // rounding residue of x_i + w (lo - x_i)
   }
-  stn<double, N>(u + k * N, uk);
+  stn<T, N>(x + k * N, xk);
 }
 
 // ---------------------------------------------------------------------------
@@ -683,7 +803,7 @@ __global__ void k_labels(const double *__restrict__ u, Geo g, int8_t *__restrict
   }
 }
 
-// Kernel-level projection of count independent N-vectors.
+// Kernel-level projection of count independent N-vectors onto the simplex.
 template <int N>
 __global__ void k_project(const double *y, double *x, int64_t count) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -8,6 +8,82 @@ inline dim3 row_grid(int count_per_row, int rows, int block = kBlock) {
   return dim3((unsigned)((count_per_row + block - 1) / block), (unsigned)rows);
 }
 
+inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+template <typename T, int N, bool SH>
+struct SolverLaunch {
+  static int smooth(void *x, const void *rhs, const void *ob, const Geo &g, int sweeps, cudaStream_t s) {
+    const dim3 grid = row_grid((g.W + 2) / 2, g.H + 1);
+    for (int k = 0; k < sweeps; ++k)
+      for (int c = 0; c < 2; ++c)
+        k_smooth_fine<T, N, SH><<<grid, kBlock, 0, s>>>((T *)x, (const T *)rhs, (const T *)ob, g, c);
+    return 2 * sweeps;
+  }
+  static int resid(const void *x, const void *rhs, const void *ob, const Geo &g, void *rt, uint8_t *mask,
+                   double *rho, cudaStream_t s) {
+    k_fine_resid<T, N, SH><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>((const T *)x, (const T *)rhs,
+                                                                         (const T *)ob, g, (T *)rt, mask, rho);
+    return 1;
+  }
+  static int restrict0(const void *rt, const Geo &gf, const Geo &gc, void *r1, cudaStream_t s) {
+    k_restrict0<T, N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>((const T *)rt, gf, gc, (T *)r1);
+    return 1;
+  }
+  static int galerkin0(const uint8_t *mask, const Geo &gf, const Geo &gc, void *op, cudaStream_t s) {
+    k_galerkin0<T, N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>(mask, gf, gc, (T *)op);
+    return 1;
+  }
+  static int galerkin(const void *opf, const Geo &gf, const Geo &gc, void *opc, cudaStream_t s) {
+    k_galerkin<T, N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>((const T *)opf, gf, gc, (T *)opc);
+    return 1;
+  }
+  static int coarse_smooth(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s) {
+    const dim3 grid = row_grid((g.W + 3) / 3, g.H + 1);
+    for (int k = 0; k < sweeps; ++k)
+      for (int c = 0; c < 3; ++c)
+        k_coarse_smooth<T, N><<<grid, kBlock, 0, s>>>((const T *)op, (const T *)r, (T *)v, g, c);
+    return 3 * sweeps;
+  }
+  static int coarse_solve(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s) {
+    k_coarse_solve_block<T, N><<<1, 1024, 0, s>>>((const T *)op, (const T *)r, (T *)v, g, sweeps);
+    return 1;
+  }
+  static int coarse_resid(const void *op, const void *r, const void *v, const Geo &g, void *t, cudaStream_t s) {
+    k_coarse_resid<T, N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>((const T *)op, (const T *)r, (const T *)v,
+                                                                       g, (T *)t);
+    return 1;
+  }
+  static int restrict_(const void *t, const Geo &gf, const Geo &gc, void *rc, cudaStream_t s) {
+    k_restrict<T, N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>((const T *)t, gf, gc, (T *)rc);
+    return 1;
+  }
+  static int prolong_add(const void *vc, const Geo &gf, const Geo &gc, void *vf, cudaStream_t s) {
+    k_prolong_add<T, N><<<row_grid(gf.W + 1, gf.H + 1), kBlock, 0, s>>>((const T *)vc, gf, gc, (T *)vf);
+    return 1;
+  }
+  static int line_search(const void *x, const void *ob, const void *rt, const void *v1, const uint8_t *mask,
+                         const Geo &gf, const Geo &gc, void *d, double *part, double *tot, double *omega,
+                         cudaStream_t s) {
+    const dim3 grid = row_grid(gf.W + 1, gf.H + 1);
+    const int blocks = (int)(grid.x * grid.y);
+    k_ls_dir<T, N, SH><<<grid, kBlock, 0, s>>>((const T *)x, (const T *)ob, (const T *)rt, (const T *)v1, mask, gf,
+                                               gc, (T *)d, part);
+    k_ls_curv<T, N><<<grid, kBlock, 0, s>>>((const T *)d, gf, part + blocks);
+    k_colsum<<<1, kBlock, 0, s>>>(part, blocks, 1, tot);
+    k_colsum<<<1, kBlock, 0, s>>>(part + blocks, blocks, 1, tot + 1);
+    k_ls_finish<<<1, 32, 0, s>>>(tot, omega);
+    return 5;
+  }
+  static int apply(void *x, const void *ob, const void *d, const double *omega, int64_t n, cudaStream_t s) {
+    k_apply<T, N, SH><<<blocks_for(n), kBlock, 0, s>>>((T *)x, (const T *)ob, (const T *)d, omega, n);
+    return 1;
+  }
+  static SolverOps table() {
+    return SolverOps{(int)sizeof(T), smooth,       resid,        restrict0,   galerkin0,   galerkin,   coarse_smooth,
+                     coarse_solve,   coarse_resid, restrict_,    prolong_add, line_search, apply};
+  }
+};
+
 template <int N>
 struct Launch {
   static int moments_f32(const float *img, const Geo &g, double *mom, cudaStream_t s) {
@@ -19,85 +95,37 @@ struct Launch {
     return 1;
   }
   static int init_random(double *u, int64_t n, uint64_t seed, cudaStream_t s) {
-    k_init_random<N><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(u, n, seed);
+    k_init_random<N><<<blocks_for(n), kBlock, 0, s>>>(u, n, seed);
     return 1;
   }
-  static int part_blocks_(int64_t n) {
-    int64_t b = (n + kBlock - 1) / kBlock;
-    return (int)(b < kMaxPartBlocks ? b : kMaxPartBlocks);
-  }
   static int means(const double *u, const double *mom, const Geo &g, double *part, double *tot, double *c,
-                    double *energy, double eps, double lam, cudaStream_t s) {
+                   double *energy, double eps, double lam, cudaStream_t s) {
     const int64_t n = (int64_t)g.Wn * (g.H + 1);
-    const int blocks = part_blocks_(n);
-    k_means_partial<N><<<blocks, kBlock, 0, s>>>(u, mom, g, part);
-    k_colsum<<<7 * N, kBlock, 0, s>>>(part, blocks, 7 * N, tot);
-    k_means_finish<N><<<1, 32, 0, s>>>(tot, c, energy, eps, lam);
+    const int64_t b = (n + kBlock - 1) / kBlock;
+    const int blocks = (int)(b < kMaxPartBlocks ? b : kMaxPartBlocks);
+    if (energy) {
+      k_means_partial<N, true><<<blocks, kBlock, 0, s>>>(u, mom, g, part);
+      k_colsum<<<7 * N, kBlock, 0, s>>>(part, blocks, 7 * N, tot);
+      k_means_finish<N, true><<<1, 32, 0, s>>>(tot, c, energy, eps, lam);
+    } else {
+      k_means_partial<N, false><<<blocks, kBlock, 0, s>>>(u, mom, g, part);
+      k_colsum<<<4 * N, kBlock, 0, s>>>(part, blocks, 4 * N, tot);
+      k_means_finish<N, false><<<1, 32, 0, s>>>(tot, c, nullptr, eps, lam);
+    }
     return 3;
   }
   static int rhs(const double *u, const double *mom, const double *c, const Geo &g, double a1, double tl, double *b,
-                  cudaStream_t s) {
-    const int64_t n = (int64_t)g.Wn * (g.H + 1);
-    k_rhs<N><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(u, mom, c, g, a1, tl, b);
+                 cudaStream_t s) {
+    k_rhs<N><<<blocks_for((int64_t)g.Wn * (g.H + 1)), kBlock, 0, s>>>(u, mom, c, g, a1, tl, b);
     return 1;
   }
-  static int smooth_fine(double *u, const double *b, const Geo &g, int sweeps, cudaStream_t s) {
-    const dim3 grid = row_grid((g.W + 2) / 2, g.H + 1);
-    for (int k = 0; k < sweeps; ++k) {
-      k_smooth_fine<double, N><<<grid, kBlock, 0, s>>>(u, b, g, 0);
-      k_smooth_fine<double, N><<<grid, kBlock, 0, s>>>(u, b, g, 1);
-    }
-    return 2 * sweeps;
-  }
-  static int fine_resid(const double *u, const double *b, const Geo &g, double *rt, uint8_t *mask, double *rho,
+  static int outer_resid(const double *u, const double *b, const Geo &g, float *r32, float *u32, double *rho,
                          cudaStream_t s) {
-    k_fine_resid<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, b, g, rt, mask, rho);
+    k_outer_resid<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, b, g, r32, u32, rho);
     return 1;
   }
-  static int restrict_(const double *t, const Geo &gf, const Geo &gc, double *rc, cudaStream_t s) {
-    k_restrict<N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>(t, gf, gc, rc);
-    return 1;
-  }
-  static int galerkin0(const uint8_t *mask, const Geo &gf, const Geo &gc, double *op, cudaStream_t s) {
-    k_galerkin0<N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>(mask, gf, gc, op);
-    return 1;
-  }
-  static int galerkin(const double *opf, const Geo &gf, const Geo &gc, double *opc, cudaStream_t s) {
-    k_galerkin<N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>(opf, gf, gc, opc);
-    return 1;
-  }
-  static int coarse_smooth(const double *op, const double *r, double *v, const Geo &g, int sweeps, cudaStream_t s) {
-    const dim3 grid = row_grid((g.W + 3) / 3, g.H + 1);
-    for (int k = 0; k < sweeps; ++k)
-      for (int c = 0; c < 3; ++c) k_coarse_smooth<N><<<grid, kBlock, 0, s>>>(op, r, v, g, c);
-    return 3 * sweeps;
-  }
-  static int coarse_solve(const double *op, const double *r, double *v, const Geo &g, int sweeps, cudaStream_t s) {
-    k_coarse_solve_block<N><<<1, 1024, 0, s>>>(op, r, v, g, sweeps);
-    return 1;
-  }
-  static int coarse_resid(const double *op, const double *r, const double *v, const Geo &g, double *t,
-                           cudaStream_t s) {
-    k_coarse_resid<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(op, r, v, g, t);
-    return 1;
-  }
-  static int prolong_add(const double *vc, const Geo &gf, const Geo &gc, double *vf, cudaStream_t s) {
-    k_prolong_add<N><<<row_grid(gf.W + 1, gf.H + 1), kBlock, 0, s>>>(vc, gf, gc, vf);
-    return 1;
-  }
-  static int line_search(const double *u, const double *rt, const double *v1, const uint8_t *mask, const Geo &gf,
-                          const Geo &gc, double *d, double *part, double *tot, double *omega, cudaStream_t s) {
-    const dim3 grid = row_grid(gf.W + 1, gf.H + 1);
-    const int blocks = (int)(grid.x * grid.y);
-    k_ls_dir<N><<<grid, kBlock, 0, s>>>(u, rt, v1, mask, gf, gc, d, part);
-    k_ls_curv<N><<<grid, kBlock, 0, s>>>(d, gf, part + blocks);
-    k_colsum<<<1, kBlock, 0, s>>>(part, blocks, 1, tot);
-    k_colsum<<<1, kBlock, 0, s>>>(part + blocks, blocks, 1, tot + 1);
-    k_ls_finish<<<1, 32, 0, s>>>(tot, omega);
-    return 5;
-  }
-  static int apply(double *u, const double *d, const double *omega, int64_t n, cudaStream_t s) {
-    k_apply<N><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(u, d, omega, n);
+  static int outer_update(double *u, const float *delta, int64_t n, cudaStream_t s) {
+    k_outer_update<N><<<blocks_for(n), kBlock, 0, s>>>(u, delta, n);
     return 1;
   }
   static int labels(const double *u, const Geo &g, int8_t *node_lab, int8_t *pix_lab, cudaStream_t s) {
@@ -106,14 +134,22 @@ struct Launch {
   }
   static int project(const double *y, double *x, int64_t count, cudaStream_t s) {
     if (count <= 0) return 0;
-    k_project<N><<<(unsigned)((count + kBlock - 1) / kBlock), kBlock, 0, s>>>(y, x, count);
+    k_project<N><<<blocks_for(count), kBlock, 0, s>>>(y, x, count);
     return 1;
   }
   static const Ops *table() {
-    static const Ops t = {N,           moments_f32, moments_f64,   init_random,  means,        rhs,
-                          smooth_fine, fine_resid,  restrict_,     galerkin0,    galerkin,     coarse_smooth,
-                          coarse_solve, coarse_resid, prolong_add, line_search,  apply,        labels,
-                          project};
+    static const Ops t = {N,
+                          moments_f32,
+                          moments_f64,
+                          init_random,
+                          means,
+                          rhs,
+                          outer_resid,
+                          outer_update,
+                          labels,
+                          project,
+                          SolverLaunch<double, N, false>::table(),
+                          SolverLaunch<float, N, true>::table()};
     return &t;
   }
 };

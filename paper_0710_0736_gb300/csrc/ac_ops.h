@@ -1,4 +1,5 @@
 // ac_ops.h -- host-side launch table of the per-N kernel instantiations.
+// Every launcher returns the number of kernels it launched.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -10,33 +11,44 @@ struct Geo;
 // Scratch of the block-partial reductions: at most kMaxPartBlocks rows.
 constexpr int kMaxPartBlocks = 1024;
 
-// Every launcher returns the number of kernels it launched.
+// One multigrid solve instantiation (scalar type and constraint form); array
+// arguments are typed by that instantiation (double or float).
+struct SolverOps {
+  int elem;  // sizeof(scalar)
+  int (*smooth)(void *x, const void *rhs, const void *ob, const Geo &g, int sweeps, cudaStream_t s);
+  int (*resid)(const void *x, const void *rhs, const void *ob, const Geo &g, void *rt, uint8_t *mask, double *rho,
+               cudaStream_t s);
+  int (*restrict0)(const void *rt, const Geo &gf, const Geo &gc, void *r1, cudaStream_t s);
+  int (*galerkin0)(const uint8_t *mask, const Geo &gf, const Geo &gc, void *op, cudaStream_t s);
+  int (*galerkin)(const void *opf, const Geo &gf, const Geo &gc, void *opc, cudaStream_t s);
+  int (*coarse_smooth)(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s);
+  int (*coarse_solve)(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s);
+  int (*coarse_resid)(const void *op, const void *r, const void *v, const Geo &g, void *t, cudaStream_t s);
+  int (*restrict_)(const void *t, const Geo &gf, const Geo &gc, void *rc, cudaStream_t s);
+  int (*prolong_add)(const void *vc, const Geo &gf, const Geo &gc, void *vf, cudaStream_t s);
+  // line search: part needs 2 x (blocks of the fine grid) doubles, tot 2 doubles
+  int (*line_search)(const void *x, const void *ob, const void *rt, const void *v1, const uint8_t *mask,
+                     const Geo &gf, const Geo &gc, void *d, double *part, double *tot, double *omega, cudaStream_t s);
+  int (*apply)(void *x, const void *ob, const void *d, const double *omega, int64_t n, cudaStream_t s);
+};
+
 struct Ops {
   int N;
   int (*moments_f32)(const float *img, const Geo &g, double *mom, cudaStream_t s);
   int (*moments_f64)(const double *img, const Geo &g, double *mom, cudaStream_t s);
   int (*init_random)(double *u, int64_t n, uint64_t seed, cudaStream_t s);
-  // colour means + energy: part (kMaxPartBlocks x 7N scratch), tot (7N), c (N x 3 in/out), energy (1)
+  // colour means (+ energy if energy != null): part (kMaxPartBlocks x 7N), tot (7N), c (N x 3 in/out)
   int (*means)(const double *u, const double *mom, const Geo &g, double *part, double *tot, double *c,
-                double *energy, double eps, double lam, cudaStream_t s);
+               double *energy, double eps, double lam, cudaStream_t s);
   int (*rhs)(const double *u, const double *mom, const double *c, const Geo &g, double a1, double tl, double *b,
-              cudaStream_t s);
-  int (*smooth_fine)(double *u, const double *b, const Geo &g, int sweeps, cudaStream_t s);
-  int (*fine_resid)(const double *u, const double *b, const Geo &g, double *rt, uint8_t *mask, double *rho,
+             cudaStream_t s);
+  int (*outer_resid)(const double *u, const double *b, const Geo &g, float *r32, float *u32, double *rho,
                      cudaStream_t s);
-  int (*restrict_)(const double *t, const Geo &gf, const Geo &gc, double *rc, cudaStream_t s);
-  int (*galerkin0)(const uint8_t *mask, const Geo &gf, const Geo &gc, double *op, cudaStream_t s);
-  int (*galerkin)(const double *opf, const Geo &gf, const Geo &gc, double *opc, cudaStream_t s);
-  int (*coarse_smooth)(const double *op, const double *r, double *v, const Geo &g, int sweeps, cudaStream_t s);
-  int (*coarse_solve)(const double *op, const double *r, double *v, const Geo &g, int sweeps, cudaStream_t s);
-  int (*coarse_resid)(const double *op, const double *r, const double *v, const Geo &g, double *t, cudaStream_t s);
-  int (*prolong_add)(const double *vc, const Geo &gf, const Geo &gc, double *vf, cudaStream_t s);
-  // line search: part needs 2 x (blocks of the fine grid) doubles, tot 2 doubles
-  int (*line_search)(const double *u, const double *rt, const double *v1, const uint8_t *mask, const Geo &gf,
-                      const Geo &gc, double *d, double *part, double *tot, double *omega, cudaStream_t s);
-  int (*apply)(double *u, const double *d, const double *omega, int64_t n, cudaStream_t s);
+  int (*outer_update)(double *u, const float *delta, int64_t n, cudaStream_t s);
   int (*labels)(const double *u, const Geo &g, int8_t *node_lab, int8_t *pix_lab, cudaStream_t s);
   int (*project)(const double *y, double *x, int64_t count, cudaStream_t s);
+  SolverOps fp64;   // T = double, direct form
+  SolverOps mixed;  // T = float, shifted form
 };
 
 const Ops *ops_n2();
@@ -46,8 +58,5 @@ const Ops *ops_n5();
 const Ops *ops_n6();
 const Ops *ops_n7();
 const Ops *ops_n8();
-
-// Number of thread blocks of a row-per-blockIdx.y launch over a level.
-int fine_grid_blocks(const Geo &g);
 
 }  // namespace ac

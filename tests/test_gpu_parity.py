@@ -230,19 +230,24 @@ def test_deterministic_and_device_buffers(ac):
 # full sizes: properties that hold at any size, checked by the oracle
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("name,W,steps", [("c2_1024_n4", 1024, 2), ("c3_4096_n8_mixed", 4096, 1)])
-def test_full_size_invariants_and_kkt(ac, name, W, steps):
-    """At the benchmark sizes: after each step sum_i u = 1, 0 <= u <= 1, the
-    energy does not increase, and the oracle's natural residual of the GPU's
-    u^{t+1} against the oracle's b(u^t) is within the step tolerance."""
+@pytest.mark.parametrize("name,W,steps,prec,tol", [("c2_1024_n4", 1024, 2, "fp64", 1e-8),
+                                                   ("c2_1024_n4", 1024, 2, "mixed", 1e-6),
+                                                   ("c3_4096_n8_mixed", 4096, 1, "fp64", 1e-8),
+                                                   ("c3_4096_n8_mixed", 4096, 2, "mixed", 1e-6)])
+def test_full_size_invariants_and_kkt(ac, name, W, steps, prec, tol):
+    """At the benchmark sizes and in the benchmark's launch configuration:
+    after each step sum_i u = 1, 0 <= u <= 1, the energy does not increase, and
+    the oracle's natural residual of the GPU's u^{t+1} against the oracle's
+    b(u^t) is within the step tolerance."""
     cfg = synth.CONFIGS[name]
     H = W
     N, eps, lam, tau = cfg["N"], cfg["eps"], cfg["lam"], cfg["tau"]
-    tol = 1e-8
     img = synth.config_image(name, 0, W, H)
-    seg = ac.Segmenter(W, H, N, eps, lam, tau, tol=tol, max_cycles=500, seed=1)
+    precision = ac.AC_MIXED if prec == "mixed" else ac.AC_FP64
+    seg = ac.Segmenter(W, H, N, eps, lam, tau, tol=tol, max_cycles=500, seed=1, precision=precision)
     seg.set_image(img)
-    m = oracle.moments(img.astype(np.float64))
+    img_used = synth.round_bf16(img) if prec == "mixed" else img
+    m = oracle.moments(img_used.astype(np.float64))
     u = seg.phase()
     c = np.zeros((N, 3))
     E = oracle.energy(u, m, W, H, eps, lam)
@@ -280,3 +285,75 @@ def test_error_paths(ac):
     assert st.steps == 2 and st.converged == 0
     u = seg2.phase()
     assert np.abs(u.sum(1) - 1).max() < 1e-14 and u.min() >= 0  # still feasible
+
+
+# --------------------------------------------------------------------------
+# a11: mixed precision (FP32 correction multigrid, FP64 defect correction)
+# --------------------------------------------------------------------------
+
+def _mixed(ac, W, H, N, tol, **kw):
+    return ac.Segmenter(W, H, N, kw.pop("eps", 2.0), kw.pop("lam", 1.0), kw.pop("tau", 4.0), tol=tol,
+                        max_cycles=kw.pop("max_cycles", 2000), precision=ac.AC_MIXED, **kw)
+
+
+def test_mixed_image_is_bf16(ac):
+    img = synth.config_image("c1_64_n4_fp64", 0)
+    seg = _mixed(ac, 64, 64, 4, 1e-6)
+    seg.set_image(img)
+    ref = oracle.moments(synth.round_bf16(img).astype(np.float64))
+    got = seg.moments()
+    assert (np.abs(got - ref) <= 2e-15 * np.maximum(1.0, np.abs(ref))).all()
+    # and it is not the unrounded image's moments
+    assert np.abs(got - oracle.moments(img.astype(np.float64))).max() > 1e-6
+
+
+@pytest.mark.parametrize("tol,bound", [(1e-6, 25e-6), (1e-12, 1e-10)])
+def test_mixed_one_step_c1(ac, tol, bound):
+    """One step from identical u^t.  The error of a step is at most ~20 times
+    its natural residual, so the mixed form must land within 25 tol of the
+    oracle, and with a tight tol the FP64 defect correction must reach FP64
+    accuracy although every sweep runs in FP32."""
+    W = H = 64
+    img = synth.config_image("c1_64_n4_fp64", 0)
+    u0 = synth.dirichlet_init(1, (W + 1) * (H + 1), 4)
+    seg = _mixed(ac, W, H, 4, tol)
+    seg.set_image(img)
+    seg.set_phase(u0)
+    st = seg.step(1)
+    assert st.converged and st.residual <= tol and st.outer >= 1
+    img16 = synth.round_bf16(img).astype(np.float64)
+    u_ref, _, _, _, stt = oracle.step(u0, oracle.moments(img16), np.zeros((4, 3)), W, H, 2.0, 1.0, 4.0, tol=TIGHT,
+                                      nu1=2, nu2=2)
+    u = seg.phase()
+    assert np.abs(u - u_ref).max() < bound
+    assert np.abs(u.sum(1) - 1).max() < 1e-14 and u.min() >= 0
+
+
+def test_mixed_trajectory_c1(ac):
+    """20 steps at tol 1e-12: within 1e-7 of the FP64 oracle (per-step error
+    ~2e-11, amplified ~1000x by the first steps of a random start); labels
+    equal except at near-ties."""
+    W = H = 64
+    img = synth.config_image("c1_64_n4_fp64", 0)
+    u0 = synth.dirichlet_init(1, (W + 1) * (H + 1), 4)
+    seg = _mixed(ac, W, H, 4, 1e-12)
+    seg.set_image(img)
+    seg.set_phase(u0)
+    lab = seg.segment(20)
+    img16 = synth.round_bf16(img).astype(np.float64)
+    u_ref, _, _ = oracle.run(img16, u0, 2.0, 1.0, 4.0, 20, tol=TIGHT, nu1=2, nu2=2)
+    assert np.abs(seg.phase() - u_ref).max() < 1e-7
+    _, lab_ref = oracle.labels(u_ref, W, H)
+    assert _label_mismatch_ok(u_ref, lab, lab_ref, W, H, margin=1e-6)
+
+
+@pytest.mark.parametrize("W,H,N", [(37, 23, 3), (2, 1, 4), (48, 40, 2), (96, 64, 8), (40, 24, 6)])
+def test_mixed_ragged(ac, W, H, N):
+    img = synth.shapes_image(W * 5 + H, W, H, rect_side=(1, max(1, W // 2)), disk_r=(1, max(1.5, W / 4)))
+    u0 = synth.dirichlet_init(W * H, (W + 1) * (H + 1), N)
+    seg = _mixed(ac, W, H, N, 1e-11)
+    seg.set_image(img)
+    seg.set_phase(u0)
+    seg.step(2)
+    u_ref, _, _ = oracle.run(synth.round_bf16(img).astype(np.float64), u0, 2.0, 1.0, 4.0, 2, tol=TIGHT, nu1=2, nu2=2)
+    assert np.abs(seg.phase() - u_ref).max() < 1e-9
