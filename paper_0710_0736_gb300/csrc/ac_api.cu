@@ -83,6 +83,26 @@ struct Level {
   void *op = nullptr, *r = nullptr, *v = nullptr, *t = nullptr;  // coarse levels only
 };
 
+// Untruncated entries of P'SP on the first coarse level, one representative
+// coarse node per boundary class.
+ac::Galerkin0Table galerkin0_table(const ac::Geo &gf, const ac::Geo &gc) {
+  ac::Galerkin0Table t{};
+  const int lx[4] = {0, 1, 0, 1}, ly[4] = {0, 0, 1, 1};
+  bool seen[25] = {};
+  for (int Y = 0; Y <= gc.H; ++Y) {
+    if (Y > 2 && Y < gc.H - 2) continue;  // rows of class 2 are all alike
+    for (int X = 0; X <= gc.W; ++X) {
+      if (X > 2 && X < gc.W - 2) continue;
+      const int c = ac::g0_class(Y, gc.H) * 5 + ac::g0_class(X, gc.W);
+      if (seen[c]) continue;
+      seen[c] = true;
+      for (int l = 0; l < 4; ++l)
+        t.v[c][l] = ac::galerkin0_entry(gf, gc, X, Y, lx[l], ly[l], [](int, int) { return true; });
+    }
+  }
+  return t;
+}
+
 // One multigrid solve: min_x sum_i 1/2 x_i'S x_i - rhs_i'x_i over the
 // constraint set of the instantiation (see ac_kernels.cuh).
 struct Solve {
@@ -90,12 +110,14 @@ struct Solve {
   void *x = nullptr, *rhs = nullptr, *ob = nullptr, *rt = nullptr, *d = nullptr;
   uint8_t *mask = nullptr;
   std::vector<Level> lv;  // lv[0]: fine level geometry
+  ac::Galerkin0Table tab0{};
 };
 
-constexpr int kCoarseSweeps = 2;     // pre/post sweeps on coarse levels
+constexpr int kCoarseSweeps = 2;     // pre/post l1-Jacobi sweeps on coarse levels (even)
 constexpr int kCoarsestSweeps = 20;  // sweeps of the one-block coarsest solve
 constexpr int64_t kCoarsestBlockNodes = 1 << 14;
-constexpr double kInnerReduction = 1e-5;  // AC_MIXED: inner FP32 solve to max(tol/2, 1e-5 rho_outer)
+constexpr double kInnerReduction = 1e-4;  // AC_MIXED: inner FP32 solve to max(tol/2, 1e-4 rho_outer) ...
+constexpr int kInnerMaxCycles = 40;       // ... or at most this many V-cycles per defect-correction pass
 
 }  // namespace
 
@@ -248,17 +270,17 @@ int coarse_vcycle(ac_ctx *ctx, Solve &S, int k) {
     if (L.n <= kCoarsestBlockNodes)
       AC_RUN(AC_PROF_COARSE, o->coarse_solve(L.op, L.r, L.v, L.g, kCoarsestSweeps, ctx->s));
     else
-      AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.g, 2 * kCoarseSweeps, ctx->s));
+      AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, 2 * kCoarseSweeps, ctx->s));
     return AC_OK;
   }
   Level &C = S.lv[k + 1];
-  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.g, kCoarseSweeps, ctx->s));
+  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, ctx->s));
   AC_RUN(AC_PROF_COARSE, o->coarse_resid(L.op, L.r, L.v, L.g, L.t, ctx->s));
   AC_RUN(AC_PROF_TRANSFER, o->restrict_(L.t, L.g, C.g, C.r, ctx->s));
   int rc = coarse_vcycle(ctx, S, k + 1);
   if (rc) return rc;
   AC_RUN(AC_PROF_TRANSFER, o->prolong_add(C.v, L.g, C.g, L.v, ctx->s));
-  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.g, kCoarseSweeps, ctx->s));
+  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, ctx->s));
   return AC_OK;
 }
 
@@ -272,7 +294,8 @@ int coarse_vcycle(ac_ctx *ctx, Solve &S, int k) {
 // Every stage keeps x feasible and does not raise the step energy, so the
 // limit is the unique minimiser that plain projected Gauss-Seidel (the
 // smoother alone) reaches.
-int solve_mg(ac_ctx *ctx, Solve &S, double tol, int *cycles_out, double *rho_out, int64_t *sweeps_out) {
+int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out, double *rho_out,
+             int64_t *sweeps_out) {
   const ac::SolverOps *o = S.o;
   const ac::Geo &g0 = S.lv[0].g;
   const bool coarse = S.lv.size() > 1;
@@ -297,10 +320,10 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int *cycles_out, double *rho_out
       status = AC_OK;
       break;
     }
-    if (cyc >= ctx->p.max_cycles) break;
+    if (cyc >= max_cycles) break;
     if (!coarse) continue;
     Level &L1 = S.lv[1];
-    AC_RUN(AC_PROF_TRANSFER, o->galerkin0(S.mask, g0, L1.g, L1.op, ctx->s));
+    AC_RUN(AC_PROF_TRANSFER, o->galerkin0(S.mask, g0, L1.g, S.tab0, L1.op, ctx->s));
     for (size_t k = 1; k + 1 < S.lv.size(); ++k)
       AC_RUN(AC_PROF_TRANSFER, o->galerkin(S.lv[k].op, S.lv[k].g, S.lv[k + 1].g, S.lv[k + 1].op, ctx->s));
     AC_RUN(AC_PROF_TRANSFER, o->restrict0(S.rt, g0, L1.g, L1.r, ctx->s));
@@ -320,8 +343,10 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int *cycles_out, double *rho_out
 // AC_MIXED: FP64 defect correction around the FP32 multigrid.  Each pass
 // forms r = b - S u and the natural residual in FP64; if rho > tol the
 // correction problem min 1/2 d'Sd - r'd, u + d on the simplices, is solved in
-// FP32 to max(tol/2, 1e-5 rho) (FP32 keeps the correction's own relative
-// precision, so each pass gains up to five digits) and u <- P_G(u + d) in FP64.
+// FP32 to max(tol/2, 1e-4 rho) or kInnerMaxCycles V-cycles (FP32 keeps the
+// correction's own relative precision, except for components driven onto
+// their bound, whose precision is that of u; the next pass removes that) and
+// u <- P_G(u + d) in FP64.
 int solve_mixed(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_out, int *outer_out) {
   const ac::Ops *o = ctx->ops;
   double rho = 0;
@@ -345,7 +370,8 @@ int solve_mixed(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_o
     int c = 0;
     int64_t sw = 0;
     double rin = 0;
-    rc = solve_mg(ctx, ctx->sv, std::fmax(0.5 * ctx->p.tol, kInnerReduction * rho), &c, &rin, &sw);
+    const int cap = ctx->p.max_cycles - cycles < kInnerMaxCycles ? ctx->p.max_cycles - cycles : kInnerMaxCycles;
+    rc = solve_mg(ctx, ctx->sv, std::fmax(0.5 * ctx->p.tol, kInnerReduction * rho), cap, &c, &rin, &sw);
     cycles += c;
     sweeps += sw;
     if (rc && rc != AC_ERR_NOT_CONVERGED) return rc;
@@ -442,6 +468,7 @@ int ac_create(ac_ctx **out, const ac_params *p) {
     S.lv.push_back(L);
   }
   ctx->n = S.lv[0].n;
+  if (S.lv.size() > 1) S.tab0 = galerkin0_table(S.lv[0].g, S.lv[1].g);
   const int N = ctx->N;
   const size_t es = (size_t)S.o->elem;
   const size_t fN64 = (size_t)ctx->n * N * sizeof(double), fNs = (size_t)ctx->n * N * es;
@@ -582,7 +609,7 @@ int ac_step(ac_ctx *ctx, int n_steps, ac_stats *out) {
     double rho = 0;
     int64_t sweeps = 0;
     int rc = mixed ? solve_mixed(ctx, &cycles, &rho, &sweeps, &outer)
-                   : solve_mg(ctx, ctx->sv, ctx->p.tol, &cycles, &rho, &sweeps);
+                   : solve_mg(ctx, ctx->sv, ctx->p.tol, ctx->p.max_cycles, &cycles, &rho, &sweeps);
     st.fine_sweeps += sweeps;
     st.outer += outer;
     st.cycles = cycles;

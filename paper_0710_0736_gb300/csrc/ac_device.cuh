@@ -28,7 +28,7 @@ struct Geo {
   double invD[9];  // 1 / S_nn by class
 };
 
-__device__ __forceinline__ int node_class(const Geo &g, int x, int y) {
+__host__ __device__ __forceinline__ int node_class(const Geo &g, int x, int y) {
   int cx = x == 0 ? 0 : (x == g.W ? 2 : 1);
   int cy = y == 0 ? 0 : (y == g.H ? 2 : 1);
   return cy * 3 + cx;
@@ -37,7 +37,7 @@ __device__ __forceinline__ int node_class(const Geo &g, int x, int y) {
 // Stiffness weights of the four axis edges at (x, y): east, west, north, south.
 struct Weights { float e, w, n, s; };
 
-__device__ __forceinline__ Weights edge_weights(const Geo &g, int x, int y) {
+__host__ __device__ __forceinline__ Weights edge_weights(const Geo &g, int x, int y) {
   float vy = 0.5f * (float)((y < g.H) + (y > 0));  // rows above/below the horizontal edge
   float vx = 0.5f * (float)((x < g.W) + (x > 0));
   Weights w;
@@ -231,12 +231,57 @@ __device__ __forceinline__ void nbr_sum(const T *u, const Geo &g, int x, int y, 
 // P1 interpolation weight of coarse node L at fine node b (fine coordinates),
 // for nested right-diagonal meshes: 1 at 2L, 1/2 at the six neighbours of 2L
 // along the coarse edges (E, W, N, S, NE, SW), 0 elsewhere.
-__device__ __forceinline__ double hat_weight(int dx, int dy) {
+__host__ __device__ __forceinline__ double hat_weight(int dx, int dy) {
   if (dx == 0 && dy == 0) return 1.0;
   if ((dx == 1 || dx == -1) && dy == 0) return 0.5;
   if (dx == 0 && (dy == 1 || dy == -1)) return 0.5;
   if ((dx == 1 && dy == 1) || (dx == -1 && dy == -1)) return 0.5;
   return 0.0;
+}
+
+// Entry S_ab of the fine step matrix S = Mhat + tau eps A for b = a + (ddx, ddy),
+// (ddx, ddy) in {0, E, W, N, S}, both nodes inside the level.
+__host__ __device__ __forceinline__ double fine_S(const Geo &g, int ax, int ay, int ddx, int ddy) {
+  if (ddx == 0 && ddy == 0) return g.D[node_class(g, ax, ay)];
+  Weights w = edge_weights(g, ax, ay);
+  float ww = ddx == 1 ? w.e : ddx == -1 ? w.w : ddy == 1 ? w.n : w.s;
+  return -g.te * (double)ww;
+}
+
+// Untruncated first-level Galerkin entries (C, E, N, NE) of P'SP by coarse-node
+// class: x class 0, 1, 2 (interior), 3, 4 for X = 0, 1, other, Wc-1, Wc (y
+// alike), index cy*5 + cx.
+struct Galerkin0Table {
+  double v[25][4];
+};
+
+__host__ __device__ __forceinline__ int g0_class(int X, int Wc) {
+  return X == 0 ? 0 : X == 1 ? 1 : X == Wc ? 4 : X == Wc - 1 ? 3 : 2;
+}
+
+// The first-level Galerkin entry (K, K + (lx, ly)) of P' M S M P, where M keeps
+// the fine nodes whose bit `bit` is set in mask(x, y) (mask == nullptr: all).
+template <class MaskF>
+__host__ __device__ inline double galerkin0_entry(const Geo &gf, const Geo &gc, int X, int Y, int lx, int ly,
+                                                  MaskF free_at) {
+  const int sx[7] = {0, 1, -1, 0, 0, 1, -1};
+  const int sy[7] = {0, 0, 0, 1, -1, 1, -1};
+  const int ox[5] = {0, 1, -1, 0, 0};
+  const int oy[5] = {0, 0, 0, 1, -1};
+  const int LX = X + lx, LY = Y + ly;
+  if (LX > gc.W || LY > gc.H) return 0.0;
+  double acc = 0.0;
+  for (int s = 0; s < 7; ++s) {
+    const int ax = 2 * X + sx[s], ay = 2 * Y + sy[s];
+    if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H || !free_at(ax, ay)) continue;
+    const double pa = s == 0 ? 1.0 : 0.5;
+    for (int o = 0; o < 5; ++o) {
+      const int bx = ax + ox[o], by = ay + oy[o];
+      if (bx < 0 || bx > gf.W || by < 0 || by > gf.H || !free_at(bx, by)) continue;
+      acc += pa * fine_S(gf, ax, ay, ox[o], oy[o]) * hat_weight(bx - 2 * LX, by - 2 * LY);
+    }
+  }
+  return acc;
 }
 
 // Block-wide reductions (blockDim.x a multiple of 32, <= 1024).

@@ -436,20 +436,13 @@ __global__ void k_restrict(const T *__restrict__ t, Geo gf, Geo gc, T *__restric
 // Truncated Galerkin operator of the first coarse level, per phase i:
 //   S_1,i = P' M_i S M_i P,  M_i = diag(free_n,i)  (truncated prolongation).
 // Stored as the C, E, N, NE entries of each coarse node.  Phases free on the
-// whole neighbourhood use the untruncated product (computed once per node);
-// phases free nowhere get 0.  The entries are sums of at most 35 products of
-// dyadic weights with S entries, accumulated in float.
+// whole neighbourhood take the untruncated product from a per-class table;
+// phases free nowhere get 0; only phases free on part of it are summed here
+// (at most 35 products of dyadic weights with S entries).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double fine_S(const Geo &g, int ax, int ay, int ddx, int ddy) {
-  if (ddx == 0 && ddy == 0) return g.D[node_class(g, ax, ay)];
-  Weights w = edge_weights(g, ax, ay);
-  float ww = ddx == 1 ? w.e : ddx == -1 ? w.w : ddy == 1 ? w.n : w.s;
-  return -g.te * (double)ww;
-}
-
 template <typename T, int N>
 __global__ void __launch_bounds__(kBlock) k_galerkin0(const uint8_t *__restrict__ mask, Geo gf, Geo gc,
-                                                      T *__restrict__ op) {
+                                                      Galerkin0Table tab, T *__restrict__ op) {
   const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
   if (X > gc.W) return;
   constexpr int sx[7] = {0, 1, -1, 0, 0, 1, -1};
@@ -467,30 +460,34 @@ __global__ void __launch_bounds__(kBlock) k_galerkin0(const uint8_t *__restrict_
       any |= m;
     }
   const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), K = (int64_t)Y * gc.Wn + X;
-  if (!any) {
+  const double *tv = tab.v[g0_class(Y, gc.H) * 5 + g0_class(X, gc.W)];
+  const unsigned partial = any & ~all;
+  if (!partial) {
 #pragma unroll
-    for (int c = 0; c < 4 * N; ++c) op[c * nc + K] = T(0);
+    for (int l = 0; l < 4; ++l)
+#pragma unroll
+      for (int i = 0; i < N; ++i) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? (T)tv[l] : T(0);
     return;
   }
-  T full[4] = {0, 0, 0, 0};
   T acc[4][N];
 #pragma unroll
   for (int l = 0; l < 4; ++l)
 #pragma unroll
     for (int i = 0; i < N; ++i) acc[l][i] = T(0);
-  const unsigned partial = any & ~all;
 #pragma unroll 1
   for (int s = 0; s < 7; ++s) {
     const int ax = 2 * X + sx[s], ay = 2 * Y + sy[s];
     if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
     const T pa = s == 0 ? T(1) : T(0.5);
-    const unsigned ma = mask[(int64_t)ay * gf.Wn + ax];
+    const unsigned ma = mask[(int64_t)ay * gf.Wn + ax] & partial;
+    if (!ma) continue;
 #pragma unroll 1
     for (int o = 0; o < 5; ++o) {
       const int bx = ax + ox[o], by = ay + oy[o];
       if (bx < 0 || bx > gf.W || by < 0 || by > gf.H) continue;
       const T sab = (T)fine_S(gf, ax, ay, ox[o], oy[o]);
-      const unsigned mm = ma & mask[(int64_t)by * gf.Wn + bx] & partial;
+      const unsigned mm = ma & mask[(int64_t)by * gf.Wn + bx];
+      if (!mm) continue;
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         const int LX = X + lx[l], LY = Y + ly[l];
@@ -498,19 +495,16 @@ __global__ void __launch_bounds__(kBlock) k_galerkin0(const uint8_t *__restrict_
         const T q = (T)hat_weight(bx - 2 * LX, by - 2 * LY);
         if (q == T(0)) continue;
         const T cf = pa * sab * q;
-        full[l] += cf;
-        if (mm) {
 #pragma unroll
-          for (int i = 0; i < N; ++i)
-            if ((mm >> i) & 1u) acc[l][i] += cf;
-        }
+        for (int i = 0; i < N; ++i)
+          if ((mm >> i) & 1u) acc[l][i] += cf;
       }
     }
   }
 #pragma unroll
   for (int l = 0; l < 4; ++l)
 #pragma unroll
-    for (int i = 0; i < N; ++i) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? full[l] : acc[l][i];
+    for (int i = 0; i < N; ++i) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? (T)tv[l] : acc[l][i];
 }
 
 // S entry (K, K + d) of a stored coarse operator, d in the 7-point pattern.
@@ -591,26 +585,35 @@ __device__ __forceinline__ T op_offdiag(const T *op, const T *v, const Geo &g, i
   return s;
 }
 
-// a7: one colour of linear Gauss-Seidel on a coarse level; (x + y) % 3 is a
-// valid 3-colouring of the 7-point (E, W, N, S, NE, SW) pattern.  Rows with
-// a zero diagonal (no free fine node under the basis function) stay 0.
+// a7: one l1-Jacobi sweep on a coarse level, vout = vin + (r - S vin) / l1,
+// l1 = sum_j |S_Kj| (convergent for any symmetric positive definite S; one
+// coalesced launch per sweep).  Rows with a zero diagonal stay 0.
 template <typename T, int N>
-__global__ void k_coarse_smooth(const T *__restrict__ op, const T *__restrict__ r, T *__restrict__ v, Geo g,
-                                int color) {
-  const int y = blockIdx.y;
-  const int x0 = ((color - y) % 3 + 3) % 3;
-  const int x = x0 + 3 * (blockIdx.x * blockDim.x + threadIdx.x);
+__global__ void k_coarse_jacobi(const T *__restrict__ op, const T *__restrict__ r, const T *__restrict__ vin,
+                                T *__restrict__ vout, Geo g) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x > g.W) return;
   const int64_t nc = (int64_t)g.Wn * (g.H + 1), K = (int64_t)y * g.Wn + x;
+  const bool e = x < g.W, w = x > 0, nn = y < g.H, ss = y > 0;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
+    const T *oE = op + (1 * N + i) * nc, *oN = op + (2 * N + i) * nc, *oNE = op + (3 * N + i) * nc;
+    const T *vi = vin + i * nc;
     const T d = op[i * nc + K];
-    v[i * nc + K] = d > T(0) ? (r[i * nc + K] - op_offdiag<T, N>(op, v, g, nc, x, y, i)) / d : T(0);
+    T sv = d * vi[K], l1 = fabs(d), c;
+    if (e) { c = oE[K]; sv += c * vi[K + 1]; l1 += fabs(c); }
+    if (w) { c = oE[K - 1]; sv += c * vi[K - 1]; l1 += fabs(c); }
+    if (nn) { c = oN[K]; sv += c * vi[K + g.Wn]; l1 += fabs(c); }
+    if (ss) { c = oN[K - g.Wn]; sv += c * vi[K - g.Wn]; l1 += fabs(c); }
+    if (e && nn) { c = oNE[K]; sv += c * vi[K + g.Wn + 1]; l1 += fabs(c); }
+    if (w && ss) { c = oNE[K - g.Wn - 1]; sv += c * vi[K - g.Wn - 1]; l1 += fabs(c); }
+    vout[i * nc + K] = d > T(0) ? vi[K] + (r[i * nc + K] - sv) / l1 : T(0);
   }
 }
 
 // Whole-level Gauss-Seidel in one block for small coarsest grids: `sweeps`
-// passes over the 3 colours with a barrier between colours.
+// passes over 3 colours ((x + y) % 3 is a valid colouring of the 7-point
+// E, W, N, S, NE, SW pattern) with a barrier between colours.
 template <typename T, int N>
 __global__ void __launch_bounds__(1024) k_coarse_solve_block(const T *__restrict__ op, const T *__restrict__ r,
                                                              T *__restrict__ v, Geo g, int sweeps) {

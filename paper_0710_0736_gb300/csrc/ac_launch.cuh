@@ -29,20 +29,24 @@ struct SolverLaunch {
     k_restrict0<T, N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>((const T *)rt, gf, gc, (T *)r1);
     return 1;
   }
-  static int galerkin0(const uint8_t *mask, const Geo &gf, const Geo &gc, void *op, cudaStream_t s) {
-    k_galerkin0<T, N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>(mask, gf, gc, (T *)op);
+  static int galerkin0(const uint8_t *mask, const Geo &gf, const Geo &gc, const Galerkin0Table &tab, void *op,
+                       cudaStream_t s) {
+    k_galerkin0<T, N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>(mask, gf, gc, tab, (T *)op);
     return 1;
   }
   static int galerkin(const void *opf, const Geo &gf, const Geo &gc, void *opc, cudaStream_t s) {
     k_galerkin<T, N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>((const T *)opf, gf, gc, (T *)opc);
     return 1;
   }
-  static int coarse_smooth(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s) {
-    const dim3 grid = row_grid((g.W + 3) / 3, g.H + 1);
-    for (int k = 0; k < sweeps; ++k)
-      for (int c = 0; c < 3; ++c)
-        k_coarse_smooth<T, N><<<grid, kBlock, 0, s>>>((const T *)op, (const T *)r, (T *)v, g, c);
-    return 3 * sweeps;
+  static int coarse_smooth(const void *op, const void *r, void *v, void *tmp, const Geo &g, int sweeps,
+                           cudaStream_t s) {
+    const dim3 grid = row_grid(g.W + 1, g.H + 1);
+    for (int k = 0; k < sweeps; ++k) {
+      const T *in = (const T *)(k % 2 == 0 ? v : tmp);
+      T *out = (T *)(k % 2 == 0 ? tmp : v);
+      k_coarse_jacobi<T, N><<<grid, kBlock, 0, s>>>((const T *)op, (const T *)r, in, out, g);
+    }
+    return sweeps;
   }
   static int coarse_solve(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s) {
     k_coarse_solve_block<T, N><<<1, 1024, 0, s>>>((const T *)op, (const T *)r, (T *)v, g, sweeps);

@@ -7,6 +7,7 @@
 namespace ac {
 
 struct Geo;
+struct Galerkin0Table;
 
 // Scratch of the block-partial reductions: at most kMaxPartBlocks rows.
 constexpr int kMaxPartBlocks = 1024;
@@ -19,9 +20,11 @@ struct SolverOps {
   int (*resid)(const void *x, const void *rhs, const void *ob, const Geo &g, void *rt, uint8_t *mask, double *rho,
                cudaStream_t s);
   int (*restrict0)(const void *rt, const Geo &gf, const Geo &gc, void *r1, cudaStream_t s);
-  int (*galerkin0)(const uint8_t *mask, const Geo &gf, const Geo &gc, void *op, cudaStream_t s);
+  int (*galerkin0)(const uint8_t *mask, const Geo &gf, const Geo &gc, const Galerkin0Table &tab, void *op,
+                   cudaStream_t s);
   int (*galerkin)(const void *opf, const Geo &gf, const Geo &gc, void *opc, cudaStream_t s);
-  int (*coarse_smooth)(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s);
+  // l1-Jacobi sweeps ping-ponging v and tmp (sweeps must be even; the result is in v)
+  int (*coarse_smooth)(const void *op, const void *r, void *v, void *tmp, const Geo &g, int sweeps, cudaStream_t s);
   int (*coarse_solve)(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s);
   int (*coarse_resid)(const void *op, const void *r, const void *v, const Geo &g, void *t, cudaStream_t s);
   int (*restrict_)(const void *t, const Geo &gf, const Geo &gc, void *rc, cudaStream_t s);
