@@ -116,7 +116,7 @@ struct Solve {
 constexpr int kCoarseSweeps = 2;     // pre/post l1-Jacobi sweeps on coarse levels (even)
 constexpr int kCoarsestSweeps = 20;  // sweeps of the one-block coarsest solve
 constexpr int64_t kCoarsestBlockNodes = 1 << 14;
-constexpr double kInnerReduction = 1e-4;  // AC_MIXED: inner FP32 solve to max(tol/2, 1e-4 rho_outer) ...
+constexpr double kInnerReduction = 1e-5;  // AC_MIXED: inner FP32 solve to max(tol/2, 1e-5 rho_outer) ...
 constexpr int kInnerMaxCycles = 40;       // ... or at most this many V-cycles per defect-correction pass
 
 }  // namespace
@@ -343,7 +343,7 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
 // AC_MIXED: FP64 defect correction around the FP32 multigrid.  Each pass
 // forms r = b - S u and the natural residual in FP64; if rho > tol the
 // correction problem min 1/2 d'Sd - r'd, u + d on the simplices, is solved in
-// FP32 to max(tol/2, 1e-4 rho) or kInnerMaxCycles V-cycles (FP32 keeps the
+// FP32 to max(tol/2, 1e-5 rho) or kInnerMaxCycles V-cycles (FP32 keeps the
 // correction's own relative precision, except for components driven onto
 // their bound, whose precision is that of u; the next pass removes that) and
 // u <- P_G(u + d) in FP64.
