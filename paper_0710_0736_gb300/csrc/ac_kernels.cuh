@@ -241,8 +241,8 @@ __global__ void k_rhs(const double *__restrict__ u, const double *__restrict__ m
 
 // ---------------------------------------------------------------------------
 // Mixed form, FP64 outer defect correction.
-// k_outer_resid: r = b - S u in FP64, shifted per node by the mean of r over
-// the phases with u > 0; stores r and u rounded to float (the right-hand side
+// k_outer_resid: r = b - S u in FP64, shifted per node by max_i r_i; stores r
+// and u rounded to float (the right-hand side
 // and obstacle of the FP32 correction solve) and the natural
 // residual max_n |P_G(u_n + z_n) - u_n|, z = r/S_nn, computed in FP64 as a
 // correction by the shifted projection.
@@ -264,20 +264,16 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
     const int cls = node_class(g, x, y);
     const double D = g.D[cls], invD = g.invD[cls];
     float rf[N], uf[N];
-    double z[N], r[N], mu = 0.0;
-    int cnt = 0;
+    double z[N], r[N], mu = -INFINITY;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       r[i] = bk[i] + g.te * acc[i] - D * uk[i];
-      if (uk[i] > 0.0) {
-        mu += r[i];
-        ++cnt;
-      }
+      mu = fmax(mu, r[i]);
     }
-    // r carries the node's simplex multiplier (O(1) even at the solution);
-    // subtracting a per-node constant changes neither problem, so remove the
-    // mean over the positive phases before rounding to float.
-    mu = cnt > 0 ? mu * rcp_small<double>(cnt) : 0.0;
+    // r carries the node's simplex multiplier, O(1) even at the solution: at
+    // the minimiser the free phases share max_i r_i and the others lie below.
+    // A per-node constant changes neither problem, so subtract the maximum
+    // before rounding to float; the free phases' residuals stay small.
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       r[i] -= mu;
