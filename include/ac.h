@@ -183,6 +183,27 @@ int ac_set_profiling(ac_ctx *ctx, int enable);
  * ac_set_profiling call (total_launches counts from creation). */
 int ac_get_profile(ac_ctx *ctx, ac_profile *out);
 
+/* ---- colour means without device allocation (no counterpart in the paper) -- */
+
+/* Colour means c_i = int u_i I / int u_i (N x 3 FP64, device) of a phase field
+ * u ((H+1)(W+1) x N FP64, device, the ac_get_phase layout) on an RGB image
+ * (H x W x 3 float32, device), for callers that cannot call cudaMalloc (for
+ * example real-time pipelines that forbid allocation once running, or code
+ * under a framework's fixed device-memory budget).  It allocates nothing: its
+ * reduction scratch is a file-scope __device__ array of 132 KiB (512 blocks x
+ * 32 partial sums plus 32 totals), held by every GPU that loads the library
+ * until the process exits.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every slot the call reads is written
+ * earlier in the same call, so nothing needs clearing, but all calls share
+ * the array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  Ordered on stream.
+ * A phase of zero mass gets c_i = 0.  AC_ERR_ARG for NULL pointers, W or H
+ * < 1, more than 2^31 nodes, or n_phases outside [2, AC_MAX_PHASES] (the
+ * scratch holds 4 sums for at most 8 phases per block). */
+int ac_colour_means_static(const double *u, const float *rgb, int width, int height, int n_phases, double *c,
+                           void *stream);
+
 /* Description of the last error on the calling thread ("" if none). */
 const char *ac_last_error(void);
 

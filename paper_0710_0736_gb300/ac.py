@@ -21,7 +21,8 @@ AC_MAX_PHASES = 8
 EXPORTS = [
     "ac_default_params", "ac_create", "ac_set_image", "ac_set_image_f64", "ac_step", "ac_segment", "ac_destroy",
     "ac_set_phase", "ac_get_phase", "ac_get_means", "ac_get_moments", "ac_get_rhs", "ac_get_node_labels",
-    "ac_energy", "ac_residual", "ac_project_simplex", "ac_set_profiling", "ac_get_profile", "ac_last_error",
+    "ac_energy", "ac_residual", "ac_project_simplex", "ac_set_profiling", "ac_get_profile", "ac_colour_means_static",
+    "ac_last_error",
 ]
 PROF_CLASSES = ["smooth", "resid", "coarse", "transfer", "linesearch", "setup", "outer"]
 
@@ -84,6 +85,7 @@ def _load():
         "ac_project_simplex": ([vp, vp, i64, i, vp], i),
         "ac_set_profiling": ([vp, i], i),
         "ac_get_profile": ([vp, P(ac_profile)], i),
+        "ac_colour_means_static": ([vp, vp, i, i, i, vp, vp], i),
         "ac_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -239,6 +241,17 @@ def ac_get_profile(ctx) -> ac_profile:
     p = ac_profile()
     _check(lib.ac_get_profile(ctx, C.byref(p)))
     return p
+
+
+def ac_colour_means_static(u, rgb, W, H, N, c, stream=None):
+    """Colour means without device allocation; u, rgb, c: torch CUDA tensors
+    (float64 (H+1)(W+1) x N, float32 H x W x 3, float64 N x 3)."""
+    pu, du = _buf(u, np.float64, (W + 1) * (H + 1) * N)
+    pr, dr = _buf(rgb, np.float32, W * H * 3)
+    pc, dc = _buf(c, np.float64, N * 3, writable=True)
+    if not (du and dr and dc):
+        raise ValueError("ac_colour_means_static takes device tensors")
+    return _check(lib.ac_colour_means_static(pu, pr, W, H, N, pc, stream if stream is not None else _current_stream()))
 
 
 def ac_last_error() -> str:

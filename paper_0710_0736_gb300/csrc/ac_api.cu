@@ -757,3 +757,7 @@ int ac_get_profile(ac_ctx *ctx, ac_profile *out) {
 const char *ac_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+namespace ac {
+void set_last_error(const char *msg) { g_last_error = msg; }
+}  // namespace ac
