@@ -103,14 +103,30 @@ ac::Galerkin0Table galerkin0_table(const ac::Geo &gf, const ac::Geo &gc) {
   return t;
 }
 
+// A captured CUDA graph of a fixed launch sequence, with the launches and
+// (when captured while profiling) the event pairs it records per class.
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches[AC_PROF_COUNT] = {};
+  int64_t total = 0;
+  struct Ev {
+    cudaEvent_t a, b;
+    int cls;
+  };
+  std::vector<Ev> evs;
+};
+
 // One multigrid solve: min_x sum_i 1/2 x_i'S x_i - rhs_i'x_i over the
 // constraint set of the instantiation (see ac_kernels.cuh).
 struct Solve {
   const ac::SolverOps *o = nullptr;
-  void *x = nullptr, *rhs = nullptr, *ob = nullptr, *rt = nullptr, *d = nullptr;
+  void *x = nullptr, *x2 = nullptr, *rhs = nullptr, *ob = nullptr, *rt = nullptr, *d = nullptr;
   uint8_t *mask = nullptr;
   std::vector<Level> lv;  // lv[0]: fine level geometry
   ac::Galerkin0Table tab0{};
+  // graphs [profiling][variant]: smoothing + residual of the first / a later
+  // cycle, and the coarse correction with its line search
+  GraphSlot smooth_resid[2][2], correction[2];
 };
 
 constexpr int kCoarseSweeps = 2;     // pre/post l1-Jacobi sweeps on coarse levels (even)
@@ -151,6 +167,9 @@ struct ac_ctx {
   std::vector<Pending> pending;
   double prof_ms[AC_PROF_COUNT] = {};
   int64_t prof_launches[AC_PROF_COUNT] = {};
+  // CUDA graphs (off on the legacy default stream, which cannot be captured)
+  bool use_graphs = false;
+  GraphSlot *capturing = nullptr;
 };
 
 namespace {
@@ -220,27 +239,92 @@ int prof_event(ac_ctx *ctx, cudaEvent_t *e) {
 
 // Run one launcher call: count its kernels, check the launch, and bracket it
 // with events on the context's stream while profiling.
+// While a graph is being captured the launches and event pairs are booked to
+// that graph (and counted each time it is replayed) instead.
 template <class F>
 int timed(ac_ctx *ctx, int cls, F &&f) {
   cudaEvent_t a = nullptr, b = nullptr;
+  GraphSlot *cap = ctx->capturing;
   if (ctx->profiling) {
-    if (ctx->pending.size() >= (1u << 15)) {
-      int rc = prof_harvest(ctx);
+    if (cap) {
+      AC_CUDA(cudaEventCreate(&a));
+      cap->evs.push_back({a, nullptr, cls});
+      AC_CUDA(cudaEventCreate(&b));
+      cap->evs.back().b = b;
+      AC_CUDA(cudaEventRecordWithFlags(a, ctx->s, cudaEventRecordExternal));
+    } else {
+      if (ctx->pending.size() >= (1u << 15)) {
+        int rc = prof_harvest(ctx);
+        if (rc) return rc;
+      }
+      int rc = prof_event(ctx, &a);
+      if (!rc) rc = prof_event(ctx, &b);
       if (rc) return rc;
+      AC_CUDA(cudaEventRecord(a, ctx->s));
     }
-    int rc = prof_event(ctx, &a);
-    if (!rc) rc = prof_event(ctx, &b);
-    if (rc) return rc;
-    AC_CUDA(cudaEventRecord(a, ctx->s));
   }
   const int k = f();
-  ctx->total_launches += k;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(AC_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+  if (cap) {
+    cap->total += k;
+    cap->launches[cls] += k;
+    if (ctx->profiling) AC_CUDA(cudaEventRecordWithFlags(b, ctx->s, cudaEventRecordExternal));
+    return AC_OK;
+  }
+  ctx->total_launches += k;
   if (ctx->profiling) {
     AC_CUDA(cudaEventRecord(b, ctx->s));
     ctx->pending.push_back({a, b, cls});
     ctx->prof_launches[cls] += k;
+  }
+  return AC_OK;
+}
+
+void slot_release(GraphSlot &g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto &e : g.evs) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  g = GraphSlot{};
+}
+
+// Run `enqueue` (a fixed launch sequence on ctx->s) through the graph in
+// `slot`: captured on first use, replayed afterwards.  Without graphs the
+// sequence is launched directly.
+template <class F>
+int run_graph(ac_ctx *ctx, GraphSlot &slot, F &&enqueue) {
+  if (!ctx->use_graphs) return enqueue();
+  if (!slot.exec) {
+    AC_CUDA(cudaStreamBeginCapture(ctx->s, cudaStreamCaptureModeRelaxed));
+    ctx->capturing = &slot;
+    int rc = enqueue();
+    ctx->capturing = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->s, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      slot_release(slot);
+      return rc;
+    }
+    if (e != cudaSuccess) {
+      slot_release(slot);
+      return fail(AC_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&slot.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      slot.exec = nullptr;
+      slot_release(slot);
+      return fail(AC_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+  }
+  AC_CUDA(cudaGraphLaunch(slot.exec, ctx->s));
+  ctx->total_launches += slot.total;
+  if (ctx->profiling) {
+    for (int k = 0; k < AC_PROF_COUNT; ++k) ctx->prof_launches[k] += slot.launches[k];
+    for (const auto &ev : slot.evs) ctx->pending.push_back({ev.a, ev.b, ev.cls});
   }
   return AC_OK;
 }
@@ -251,10 +335,14 @@ int timed(ac_ctx *ctx, int cls, F &&f) {
     if (rc_) return rc_;                                   \
   } while (0)
 
+// Reads rho back (the one device-to-host dependency of a cycle).  While
+// profiling, the finished event pairs are summed here: the graphs re-record
+// their events on every replay.
 int read_rho(ac_ctx *ctx, double *out) {
   AC_CUDA(cudaMemcpyAsync(ctx->h_scalars, ctx->rho, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
   AC_CUDA(cudaStreamSynchronize(ctx->s));
   *out = ctx->h_scalars[0];
+  if (ctx->profiling) return prof_harvest(ctx);
   return AC_OK;
 }
 
@@ -302,15 +390,21 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
   double rho = 0;
   int cyc = 0, status = AC_ERR_NOT_CONVERGED;
   int64_t sweeps = 0;
+  const int prof = ctx->profiling ? 1 : 0;
   for (;;) {
-    if (cyc > 0 && coarse) AC_RUN(AC_PROF_LINESEARCH, o->apply(S.x, S.ob, S.d, ctx->omega, ctx->n, ctx->s));
-    const int nsw = cyc == 0 ? ctx->p.nu1 : ctx->p.nu1 + ctx->p.nu2;
-    AC_RUN(AC_PROF_SMOOTH, o->smooth(S.x, S.rhs, S.ob, g0, nsw, ctx->s));
+    const int later = cyc > 0 ? 1 : 0;  // nu1 + nu2 sweeps, and the pending coarse correction if any
+    const int nsw = later ? ctx->p.nu1 + ctx->p.nu2 : ctx->p.nu1;
+    const void *corr = (later && coarse) ? S.d : nullptr;
+    int rc = run_graph(ctx, S.smooth_resid[prof][later], [&]() -> int {
+      AC_RUN(AC_PROF_SMOOTH, o->smooth(S.x, S.x2, S.rhs, S.ob, corr, ctx->omega, g0, nsw, ctx->s));
+      AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
+      AC_RUN(AC_PROF_RESID, o->resid(S.x, S.rhs, S.ob, g0, S.rt, S.mask, ctx->rho, ctx->s));
+      return AC_OK;
+    });
+    if (rc) return rc;
     sweeps += nsw;
-    AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
-    AC_RUN(AC_PROF_RESID, o->resid(S.x, S.rhs, S.ob, g0, S.rt, S.mask, ctx->rho, ctx->s));
     ++cyc;
-    int rc = read_rho(ctx, &rho);
+    rc = read_rho(ctx, &rho);
     if (rc) return rc;
     if (std::isnan(rho) || std::isinf(rho)) {
       status = fail(AC_ERR_NUMERIC, "non-finite residual");
@@ -322,15 +416,19 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
     }
     if (cyc >= max_cycles) break;
     if (!coarse) continue;
-    Level &L1 = S.lv[1];
-    AC_RUN(AC_PROF_TRANSFER, o->galerkin0(S.mask, g0, L1.g, S.tab0, L1.op, ctx->s));
-    for (size_t k = 1; k + 1 < S.lv.size(); ++k)
-      AC_RUN(AC_PROF_TRANSFER, o->galerkin(S.lv[k].op, S.lv[k].g, S.lv[k + 1].g, S.lv[k + 1].op, ctx->s));
-    AC_RUN(AC_PROF_TRANSFER, o->restrict0(S.rt, g0, L1.g, L1.r, ctx->s));
-    rc = coarse_vcycle(ctx, S, 1);
+    rc = run_graph(ctx, S.correction[prof], [&]() -> int {
+      Level &L1 = S.lv[1];
+      AC_RUN(AC_PROF_TRANSFER, o->galerkin0(S.mask, g0, L1.g, S.tab0, L1.op, ctx->s));
+      for (size_t k = 1; k + 1 < S.lv.size(); ++k)
+        AC_RUN(AC_PROF_TRANSFER, o->galerkin(S.lv[k].op, S.lv[k].g, S.lv[k + 1].g, S.lv[k + 1].op, ctx->s));
+      AC_RUN(AC_PROF_TRANSFER, o->restrict0(S.rt, g0, L1.g, L1.r, ctx->s));
+      int rc2 = coarse_vcycle(ctx, S, 1);
+      if (rc2) return rc2;
+      AC_RUN(AC_PROF_LINESEARCH, o->line_search(S.x, S.ob, S.rt, L1.v, S.mask, g0, L1.g, S.d, ctx->ls_part,
+                                                ctx->ls_tot, ctx->omega, ctx->s));
+      return AC_OK;
+    });
     if (rc) return rc;
-    AC_RUN(AC_PROF_LINESEARCH, o->line_search(S.x, S.ob, S.rt, L1.v, S.mask, g0, L1.g, S.d, ctx->ls_part,
-                                              ctx->ls_tot, ctx->omega, ctx->s));
   }
   *cycles_out = cyc;
   *rho_out = rho;
@@ -452,6 +550,7 @@ int ac_create(ac_ctx **out, const ac_params *p) {
   ctx->N = p->n_phases;
   ctx->ops = ops_for(ctx->N);
   ctx->s = (cudaStream_t)p->stream;
+  ctx->use_graphs = ctx->s != nullptr;  // the legacy default stream cannot be captured
   const bool mixed = p->precision == AC_MIXED;
   const double te = p->tau * p->eps;
   Solve &S = ctx->sv;
@@ -488,6 +587,7 @@ int ac_create(ac_ctx **out, const ac_params *p) {
       S.rhs = ctx->b;
       S.ob = nullptr;
     }
+    AC_ALLOC(S.x2, fNs);
     AC_ALLOC(S.rt, fNs);
     AC_ALLOC(S.mask, (size_t)ctx->n);
     if (S.lv.size() > 1) AC_ALLOC(S.d, fNs);
@@ -529,6 +629,10 @@ void ac_destroy(ac_ctx *ctx) {
     cudaStreamSynchronize(ctx->s);
   else
     cudaDeviceSynchronize();
+  for (int a = 0; a < 2; ++a) {
+    for (int b = 0; b < 2; ++b) slot_release(ctx->sv.smooth_resid[a][b]);
+    slot_release(ctx->sv.correction[a]);
+  }
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   for (void *p : ctx->allocs) cudaFree(p);
   if (ctx->img) cudaFree(ctx->img);
@@ -748,8 +852,8 @@ int ac_get_profile(ac_ctx *ctx, ac_profile *out) {
     out->ms[k] = ctx->prof_ms[k];
     out->launches[k] = ctx->prof_launches[k];
   }
-  out->smooth_bytes_per_launch = ctx->p.precision == AC_MIXED ? 2.0 * (double)ctx->n * ctx->N * sizeof(float)
-                                                               : 1.5 * (double)ctx->n * ctx->N * sizeof(double);
+  out->smooth_bytes_per_launch = ctx->p.precision == AC_MIXED ? 4.0 * (double)ctx->n * ctx->N * sizeof(float)
+                                                               : 3.0 * (double)ctx->n * ctx->N * sizeof(double);
   out->total_launches = ctx->total_launches;
   return AC_OK;
 }

@@ -248,6 +248,25 @@ __host__ __device__ __forceinline__ double fine_S(const Geo &g, int ax, int ay, 
   return -g.te * (double)ww;
 }
 
+// The same entry in the scalar type of a solve (float kernels must not spend
+// GB300's scarce FP64 issue slots on it).
+template <typename T>
+__device__ __forceinline__ T fine_S_t(const Geo &g, int ax, int ay, int ddx, int ddy) {
+  if (ddx == 0 && ddy == 0) return (T)g.D[node_class(g, ax, ay)];
+  Weights w = edge_weights(g, ax, ay);
+  float ww = ddx == 1 ? w.e : ddx == -1 ? w.w : ddy == 1 ? w.n : w.s;
+  return -(T)g.te * (T)ww;
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ T hat_weight_t(int dx, int dy) {
+  if (dx == 0 && dy == 0) return T(1);
+  if ((dx == 1 || dx == -1) && dy == 0) return T(0.5);
+  if (dx == 0 && (dy == 1 || dy == -1)) return T(0.5);
+  if ((dx == 1 && dy == 1) || (dx == -1 && dy == -1)) return T(0.5);
+  return T(0);
+}
+
 // Untruncated first-level Galerkin entries (C, E, N, NE) of P'SP by coarse-node
 // class: x class 0, 1, 2 (interior), 3, 4 for X = 0, 1, other, Wc-1, Wc (y
 // alike), index cy*5 + cx.
@@ -293,11 +312,12 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // max that propagates a NaN held in either argument.
-__device__ __forceinline__ double nanmax(double a, double b) { return (a != a || b <= a) ? a : b; }
+template <typename T>
+__device__ __forceinline__ T nanmax(T a, T b) { return (a != a || b <= a) ? a : b; }
 
 __device__ __forceinline__ double warp_nanmax(double v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = nanmax<double>(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 

@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
     stn<float, N>(u32 + n * N, uf);
     proj_box<double, N, true>(z, uk);
 #pragma unroll
-    for (int i = 0; i < N; ++i) e = nanmax(e, fabs(z[i]));
+    for (int i = 0; i < N; ++i) e = nanmax<double>(e, fabs(z[i]));
     if (!(uk[0] == uk[0])) e = uk[0];
   }
   block_max_atomic(e, rho);
@@ -312,15 +312,29 @@ __global__ void k_outer_update(double *__restrict__ u, const float *__restrict__
 // color are independent given the other colour:
 //   z_n = (rhs_n + tau eps sum_m w_nm x_m) / S_nn,   x_n <- P(z_n).
 // ---------------------------------------------------------------------------
+// With corr != null (first colour of the first sweep after a coarse
+// correction) the neighbours are read as x + omega d: that is exactly the
+// pending update x += omega d, because this pass overwrites its own colour
+// and the next pass overwrites the other one without reading old values.
 template <typename T, int N, bool SH>
 __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const T *__restrict__ rhs,
-                                                        const T *__restrict__ ob, Geo g, int color) {
+                                                        const T *__restrict__ ob, const T *__restrict__ corr,
+                                                        const double *__restrict__ omega, Geo g, int color) {
   const int y = blockIdx.y;
   const int xx = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((y + color) & 1);
   if (xx > g.W) return;
   const int64_t n = (int64_t)y * g.Wn + xx;
   T acc[N], bk[N], o[N];
   nbr_sum<T, N>(x, g, xx, y, acc);
+  if (corr) {
+    const T w = (T)*omega;
+    if (w != T(0)) {
+      T dc[N];
+      nbr_sum<T, N>(corr, g, xx, y, dc);
+#pragma unroll
+      for (int i = 0; i < N; ++i) acc[i] += w * dc[i];
+    }
+  }
   ldn<T, N>(rhs + n * N, bk);
   if constexpr (SH) ldn<T, N>(ob + n * N, o);
   const int cls = node_class(g, xx, y);
@@ -329,6 +343,112 @@ __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const
   for (int i = 0; i < N; ++i) acc[i] = (bk[i] + te * acc[i]) * invD;
   proj_box<T, N, SH>(acc, o);
   stn<T, N>(x + n * N, acc);
+}
+
+// ---------------------------------------------------------------------------
+// a4/a5, fused: SWEEPS full red-black sweeps of a TX x TY tile in one launch.
+// The block stages x_in on the tile plus a ring of width 2*SWEEPS in shared
+// memory (adding omega*corr on the fly when a coarse correction is pending),
+// then runs the 2*SWEEPS colour passes on shrinking rings (pass p updates
+// colour p % 2 on ring 2*SWEEPS-1-p, so every value a pass reads is current),
+// and writes the tile to x_out.  The ring values are recomputed by each
+// neighbouring tile from identical inputs, so the result is exactly that of
+// SWEEPS global red-black sweeps; x_in and x_out must differ (a tile's halo is
+// another tile's interior).  DRAM traffic: x_in, rhs, ob read and x_out
+// written once per launch instead of once per colour pass.
+// ---------------------------------------------------------------------------
+constexpr int kTileX = 64, kTileY = 8;
+
+template <typename T, int N, bool SH, int SWEEPS>
+__global__ void __launch_bounds__(kBlock) k_smooth_tile(const T *__restrict__ xin, T *__restrict__ xout,
+                                                        const T *__restrict__ rhs, const T *__restrict__ ob,
+                                                        const T *__restrict__ corr, const double *__restrict__ omega,
+                                                        Geo g) {
+  constexpr int HL = 2 * SWEEPS;  // halo width
+  constexpr int RW = kTileX + 2 * HL, RH = kTileY + 2 * HL;
+  // staged region, phase-major within each row: tile[(ly*N + i)*RW + lx]
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  const int x0 = blockIdx.x * kTileX - HL, y0 = blockIdx.y * kTileY - HL;  // region origin (global node)
+  const T w = corr ? (T)*omega : T(0);
+  // stage the region (each row is a contiguous span of N values per node in HBM)
+  for (int ly = 0; ly < RH; ++ly) {
+    const int gy = y0 + ly;
+    if (gy < 0 || gy > g.H) continue;
+    const int gx_lo = x0 < 0 ? 0 : x0, gx_hi = (x0 + RW - 1) > g.W ? g.W : (x0 + RW - 1);
+    const int cnt = (gx_hi - gx_lo + 1) * N;
+    const int64_t base = ((int64_t)gy * g.Wn + gx_lo) * N;
+    T *row = tile + (int64_t)ly * N * RW + (gx_lo - x0);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      T v = __ldg(xin + base + e);
+      if (w != T(0)) v += w * __ldg(corr + base + e);
+      const int node = e / N, i = e - node * N;
+      row[i * RW + node] = v;
+    }
+  }
+  __syncthreads();
+  const T te = (T)g.te;
+#pragma unroll 1
+  for (int p = 0; p < 2 * SWEEPS; ++p) {
+    const int ring = 2 * SWEEPS - 1 - p, color = p & 1;
+    const int lx0 = HL - ring, ly0 = HL - ring;
+    const int rw = kTileX + 2 * ring, rh = kTileY + 2 * ring;
+    const int half = (rw + 1) / 2;
+    for (int idx = threadIdx.x; idx < half * rh; idx += blockDim.x) {
+      const int ry = idx / half, k = idx - ry * half;
+      const int ly = ly0 + ry, gy = y0 + ly;
+      const int par = (((x0 + lx0) + gy) & 1) != color ? 1 : 0;  // first column of this colour
+      const int lx = lx0 + 2 * k + par, gx = x0 + lx;
+      if (lx >= lx0 + rw || gx < 0 || gx > g.W || gy < 0 || gy > g.H) continue;
+      T *c = tile + (int64_t)ly * N * RW + lx;  // phase i at c[i*RW]
+      T acc[N], bk[N], o[N];
+      const bool interior = gx > 0 && gx < g.W && gy > 0 && gy < g.H;
+      if (interior) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) acc[i] = c[i * RW + 1] + c[i * RW - 1] + c[(i + N) * RW] + c[(i - N) * RW];
+      } else {
+        const Weights wt = edge_weights(g, gx, gy);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          T a = T(0);
+          if (wt.e > 0.f) a += T(wt.e) * c[i * RW + 1];
+          if (wt.w > 0.f) a += T(wt.w) * c[i * RW - 1];
+          if (wt.n > 0.f) a += T(wt.n) * c[(i + N) * RW];
+          if (wt.s > 0.f) a += T(wt.s) * c[(i - N) * RW];
+          acc[i] = a;
+        }
+      }
+      const int64_t n = (int64_t)gy * g.Wn + gx;
+      ldn<T, N>(rhs + n * N, bk);
+      if constexpr (SH) ldn<T, N>(ob + n * N, o);
+      const T invD = (T)g.invD[node_class(g, gx, gy)];
+#pragma unroll
+      for (int i = 0; i < N; ++i) acc[i] = (bk[i] + te * acc[i]) * invD;
+      proj_box<T, N, SH>(acc, o);
+#pragma unroll
+      for (int i = 0; i < N; ++i) c[i * RW] = acc[i];
+    }
+    __syncthreads();
+  }
+  // write the tile interior back, node-major
+  for (int ly = HL; ly < HL + kTileY; ++ly) {
+    const int gy = y0 + ly;
+    if (gy > g.H) break;
+    const int gx_lo = x0 + HL, gx_hi = (x0 + HL + kTileX - 1) > g.W ? g.W : (x0 + HL + kTileX - 1);
+    if (gx_lo > gx_hi) continue;
+    const int cnt = (gx_hi - gx_lo + 1) * N;
+    const int64_t base = ((int64_t)gy * g.Wn + gx_lo) * N;
+    const T *row = tile + (int64_t)ly * N * RW + HL;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int node = e / N, i = e - node * N;
+      xout[base + e] = row[i * RW + node];
+    }
+  }
+}
+
+template <typename T, int N, int SWEEPS>
+constexpr size_t smooth_tile_smem() {
+  return (size_t)(kTileX + 4 * SWEEPS) * (kTileY + 4 * SWEEPS) * N * sizeof(T);
 }
 
 // ---------------------------------------------------------------------------
@@ -363,15 +483,17 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
     proj_box<T, N, SH>(acc, o);
     int cnt = 0;
     unsigned pos = 0;
+    T et = T(0);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      e = nanmax(e, (double)fabs(xk[i] - acc[i]));
+      et = nanmax<T>(et, fabs(xk[i] - acc[i]));
       const T lo = SH ? -o[i] : T(0);
       if (xk[i] > lo) {
         pos |= 1u << i;
         ++cnt;
       }
     }
+    e = (double)et;
     if (!(xk[0] == xk[0])) e = (double)xk[0];
     if (rt) {
       const unsigned fr = cnt >= 2 ? pos : 0u;
@@ -495,14 +617,14 @@ __global__ void __launch_bounds__(kBlock) k_galerkin0(const uint8_t *__restrict_
     for (int o = 0; o < 5; ++o) {
       const int bx = ax + ox[o], by = ay + oy[o];
       if (bx < 0 || bx > gf.W || by < 0 || by > gf.H) continue;
-      const T sab = (T)fine_S(gf, ax, ay, ox[o], oy[o]);
+      const T sab = fine_S_t<T>(gf, ax, ay, ox[o], oy[o]);
       const unsigned mm = ma & mask[(int64_t)by * gf.Wn + bx];
       if (!mm) continue;
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         const int LX = X + lx[l], LY = Y + ly[l];
         if (LX > gc.W || LY > gc.H) continue;
-        const T q = (T)hat_weight(bx - 2 * LX, by - 2 * LY);
+        const T q = hat_weight_t<T>(bx - 2 * LX, by - 2 * LY);
         if (q == T(0)) continue;
         const T cf = pa * sab * q;
 #pragma unroll
@@ -560,7 +682,7 @@ __global__ void __launch_bounds__(kBlock) k_galerkin(const T *__restrict__ opf, 
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         const int LX = X + lx[l], LY = Y + ly[l];
-        q[l] = (LX > gc.W || LY > gc.H) ? T(0) : (T)hat_weight(bx - 2 * LX, by - 2 * LY);
+        q[l] = (LX > gc.W || LY > gc.H) ? T(0) : hat_weight_t<T>(bx - 2 * LX, by - 2 * LY);
         anyq |= q[l] != T(0);
       }
       if (!anyq) continue;
@@ -688,7 +810,8 @@ __global__ void k_prolong_add(const T *__restrict__ vc, Geo gf, Geo gc, T *__res
 //   d   = P(x + w) - x  (feasible direction: the constraint set is convex),
 //   omega = clamp(rt'd / d'Sd, 0, 1) minimises the step energy on [x, x + d].
 // k_ls_dir writes d and the block partials of rt'd; k_ls_curv the partials of
-// d'Sd; k_ls_finish computes omega; k_apply does x += omega d.
+// d'Sd; k_ls_finish computes omega; the next smoothing pass applies
+// x += omega d (see k_smooth_fine).
 // ---------------------------------------------------------------------------
 template <typename T, int N, bool SH>
 __global__ void __launch_bounds__(kBlock) k_ls_dir(const T *__restrict__ x, const T *__restrict__ ob,
@@ -719,11 +842,13 @@ __global__ void __launch_bounds__(kBlock) k_ls_dir(const T *__restrict__ x, cons
       for (int i = 0; i < N; ++i) w[i] = xk[i] + (((fr >> i) & 1u) ? w[i] - mean : T(0));
       proj_box<T, N, SH>(w, o);
       ldn<T, N>(rt + n * N, r);
+      T loc = T(0);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         dn[i] = w[i] - xk[i];
-        dot[0] += (double)r[i] * (double)dn[i];
+        loc += r[i] * dn[i];
       }
+      dot[0] = (double)loc;
     } else {
 #pragma unroll
       for (int i = 0; i < N; ++i) dn[i] = T(0);
@@ -743,8 +868,10 @@ __global__ void __launch_bounds__(kBlock) k_ls_curv(const T *__restrict__ d, Geo
     nbr_sum<T, N>(d, g, x, y, acc);
     ldn<T, N>(d + n * N, dk);
     const T D = (T)g.D[node_class(g, x, y)], te = (T)g.te;
+    T loc = T(0);
 #pragma unroll
-    for (int i = 0; i < N; ++i) dot[0] += (double)dk[i] * (double)(D * dk[i] - te * acc[i]);
+    for (int i = 0; i < N; ++i) loc += dk[i] * (D * dk[i] - te * acc[i]);
+    dot[0] = (double)loc;
   }
   block_sum_store<1>(dot, part + blockIdx.y * gridDim.x + blockIdx.x);
 }
@@ -755,26 +882,6 @@ static __global__ void k_ls_finish(const double *__restrict__ tot, double *__res
   double w = 0.0;
   if (dsd > 0.0 && rd > 0.0) w = fmin(1.0, rd / dsd);
   *omega = w;
-}
-
-template <typename T, int N, bool SH>
-__global__ void k_apply(T *__restrict__ x, const T *__restrict__ ob, const T *__restrict__ d,
-                        const double *__restrict__ omega, int64_t n) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const T w = (T)*omega;
-  if (w == T(0)) return;
-  T xk[N], dk[N], o[N];
-  ldn_rw<T, N>(x + k * N, xk);
-  ldn<T, N>(d + k * N, dk);
-  if constexpr (SH) ldn<T, N>(ob + k * N, o);
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    xk[i] += w * dk[i];
-    const T lo = SH ? -o[i] : T(0);
-    if (xk[i] < lo) xk[i] = lo;  // rounding residue of x_i + w (lo - x_i)
-  }
-  stn<T, N>(x + k * N, xk);
 }
 
 // ---------------------------------------------------------------------------

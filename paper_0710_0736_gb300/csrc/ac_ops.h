@@ -16,7 +16,11 @@ constexpr int kMaxPartBlocks = 1024;
 // arguments are typed by that instantiation (double or float).
 struct SolverOps {
   int elem;  // sizeof(scalar)
-  int (*smooth)(void *x, const void *rhs, const void *ob, const Geo &g, int sweeps, cudaStream_t s);
+  // sweeps red-black sweeps ending in x (x2: a second buffer of the same size);
+  // with corr != null the pending coarse correction x += (*omega) corr is
+  // applied inside the first launch
+  int (*smooth)(void *x, void *x2, const void *rhs, const void *ob, const void *corr, const double *omega,
+                const Geo &g, int sweeps, cudaStream_t s);
   int (*resid)(const void *x, const void *rhs, const void *ob, const Geo &g, void *rt, uint8_t *mask, double *rho,
                cudaStream_t s);
   int (*restrict0)(const void *rt, const Geo &gf, const Geo &gc, void *r1, cudaStream_t s);
@@ -32,7 +36,6 @@ struct SolverOps {
   // line search: part needs 2 x (blocks of the fine grid) doubles, tot 2 doubles
   int (*line_search)(const void *x, const void *ob, const void *rt, const void *v1, const uint8_t *mask,
                      const Geo &gf, const Geo &gc, void *d, double *part, double *tot, double *omega, cudaStream_t s);
-  int (*apply)(void *x, const void *ob, const void *d, const double *omega, int64_t n, cudaStream_t s);
 };
 
 struct Ops {

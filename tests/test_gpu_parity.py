@@ -226,6 +226,31 @@ def test_deterministic_and_device_buffers(ac):
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graphs_match_direct_launches(ac, precision):
+    """On a capturable stream the V-cycle halves run as CUDA graphs; on the
+    legacy default stream they are launched one by one.  Same arithmetic,
+    same order: the results must be bit-identical, profiling on or off."""
+    W, H, N = 96, 64, 5
+    img = synth.shapes_image(11, W, H, rect_side=(4, 30), disk_r=(3, 12))
+    u0 = synth.dirichlet_init(12, (W + 1) * (H + 1), N)
+    prec = ac.AC_MIXED if precision == "mixed" else ac.AC_FP64
+    outs = []
+    for stream, prof in [(None, False), ("torch", False), ("torch", True)]:
+        kw = {} if stream == "torch" else {"stream": None}
+        seg = ac.Segmenter(W, H, N, 2.0, 1.0, 4.0, tol=1e-9, precision=prec, **kw)
+        seg.set_image(img)
+        seg.set_phase(u0)
+        ac.ac_set_profiling(seg.ctx, prof)
+        st = seg.step(4)
+        outs.append(seg.phase())
+        if prof:
+            p = ac.ac_get_profile(seg.ctx).as_dict()
+            assert p["launches"]["smooth"] > 0 and p["ms"]["smooth"] > 0 and st.fine_sweeps > 0
+        seg.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
 # --------------------------------------------------------------------------
 # full sizes: properties that hold at any size, checked by the oracle
 # --------------------------------------------------------------------------
