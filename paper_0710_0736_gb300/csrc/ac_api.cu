@@ -134,6 +134,12 @@ constexpr int kCoarsestSweeps = 20;  // sweeps of the one-block coarsest solve
 constexpr int64_t kCoarsestBlockNodes = 1 << 14;
 constexpr double kInnerReduction = 1e-5;  // AC_MIXED: inner FP32 solve to max(tol/2, 1e-5 rho_outer) ...
 constexpr int kInnerMaxCycles = 40;       // ... or at most this many V-cycles per defect-correction pass
+// AC_MIXED with tol >= kRho32MinTol checks convergence with the float natural
+// residual and accepts only rho32 <= tol - kRho32Margin: the float projection
+// of z = r/S_nn on the rounded u differs from the FP64 one by at most a few
+// ulps of max(|u|, |z|) <= 1 (2^-21 ~ 4.8e-7 covers 8 ulps).
+constexpr double kRho32MinTol = 1e-5;
+constexpr double kRho32Margin = 4.8e-7;
 
 }  // namespace
 
@@ -450,16 +456,18 @@ int solve_mixed(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_o
   double rho = 0;
   int cycles = 0, outer = 0, status = AC_ERR_NOT_CONVERGED;
   int64_t sweeps = 0;
+  const bool rho32 = ctx->p.tol >= kRho32MinTol;
+  const double accept = rho32 ? ctx->p.tol - kRho32Margin : ctx->p.tol;
   for (;;) {
     AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
-    AC_RUN(AC_PROF_OUTER, o->outer_resid(ctx->u, ctx->b, ctx->g0, ctx->r32, ctx->u32, ctx->rho, ctx->s));
+    AC_RUN(AC_PROF_OUTER, o->outer_resid(ctx->u, ctx->b, ctx->g0, ctx->r32, ctx->u32, ctx->rho, rho32, ctx->s));
     int rc = read_rho(ctx, &rho);
     if (rc) return rc;
     if (std::isnan(rho) || std::isinf(rho)) {
       status = fail(AC_ERR_NUMERIC, "non-finite residual");
       break;
     }
-    if (rho <= ctx->p.tol) {
+    if (rho <= accept) {
       status = AC_OK;
       break;
     }
@@ -816,7 +824,8 @@ int ac_residual(ac_ctx *ctx, double *rho) {
   if (!ctx->have_rhs) return fail(AC_ERR_STATE, "no step taken yet");
   AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
   if (ctx->p.precision == AC_MIXED)
-    AC_RUN(AC_PROF_OUTER, ctx->ops->outer_resid(ctx->u, ctx->b, ctx->g0, ctx->r32, ctx->u32, ctx->rho, ctx->s));
+    AC_RUN(AC_PROF_OUTER,
+           ctx->ops->outer_resid(ctx->u, ctx->b, ctx->g0, ctx->r32, ctx->u32, ctx->rho, false, ctx->s));
   else
     AC_RUN(AC_PROF_RESID, ctx->ops->fp64.resid(ctx->u, ctx->b, nullptr, ctx->g0, nullptr, nullptr, ctx->rho, ctx->s));
   return read_rho(ctx, rho);

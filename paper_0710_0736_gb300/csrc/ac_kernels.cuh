@@ -248,7 +248,7 @@ __global__ void k_rhs(const double *__restrict__ u, const double *__restrict__ m
 // correction by the shifted projection.
 // k_outer_update: u <- P_G(u + delta) in FP64.
 // ---------------------------------------------------------------------------
-template <int N>
+template <int N, bool RHO32>
 __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict__ u, const double *__restrict__ b, Geo g,
                                                         float *__restrict__ r32, float *__restrict__ u32,
                                                         double *__restrict__ rho) {
@@ -283,9 +283,22 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
     }
     stn<float, N>(r32 + n * N, rf);
     stn<float, N>(u32 + n * N, uf);
-    proj_box<double, N, true>(z, uk);
+    if constexpr (RHO32) {
+      // the same projection in float on the rounded data: off by at most a
+      // few float ulps of u (the caller widens tol by that margin)
+      float zf[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) e = nanmax<double>(e, fabs(z[i]));
+      for (int i = 0; i < N; ++i) zf[i] = (float)z[i];
+      proj_box<float, N, true>(zf, uf);
+      float ef = 0.f;
+#pragma unroll
+      for (int i = 0; i < N; ++i) ef = nanmax<float>(ef, fabsf(zf[i]));
+      e = (double)ef;
+    } else {
+      proj_box<double, N, true>(z, uk);
+#pragma unroll
+      for (int i = 0; i < N; ++i) e = nanmax<double>(e, fabs(z[i]));
+    }
     if (!(uk[0] == uk[0])) e = uk[0];
   }
   block_max_atomic(e, rho);
@@ -357,7 +370,13 @@ __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const
 // another tile's interior).  DRAM traffic: x_in, rhs, ob read and x_out
 // written once per launch instead of once per colour pass.
 // ---------------------------------------------------------------------------
-constexpr int kTileX = 64, kTileY = 8;
+#ifndef AC_TILE_X
+#define AC_TILE_X 64
+#endif
+#ifndef AC_TILE_Y
+#define AC_TILE_Y 8
+#endif
+constexpr int kTileX = AC_TILE_X, kTileY = AC_TILE_Y;
 
 template <typename T, int N, bool SH, int SWEEPS>
 __global__ void __launch_bounds__(kBlock) k_smooth_tile(const T *__restrict__ xin, T *__restrict__ xout,

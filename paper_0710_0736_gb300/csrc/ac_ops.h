@@ -48,7 +48,9 @@ struct Ops {
                double *energy, double eps, double lam, cudaStream_t s);
   int (*rhs)(const double *u, const double *mom, const double *c, const Geo &g, double a1, double tl, double *b,
              cudaStream_t s);
-  int (*outer_resid)(const double *u, const double *b, const Geo &g, float *r32, float *u32, double *rho,
+  // rho32: natural residual through the float projection (cheap; accurate to
+  // a few float ulps of u) instead of the FP64 one
+  int (*outer_resid)(const double *u, const double *b, const Geo &g, float *r32, float *u32, double *rho, bool rho32,
                      cudaStream_t s);
   int (*outer_update)(double *u, const float *delta, int64_t n, cudaStream_t s);
   int (*labels)(const double *u, const Geo &g, int8_t *node_lab, int8_t *pix_lab, cudaStream_t s);
