@@ -371,10 +371,10 @@ __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const
 // written once per launch instead of once per colour pass.
 // ---------------------------------------------------------------------------
 #ifndef AC_TILE_X
-#define AC_TILE_X 64
+#define AC_TILE_X 32
 #endif
 #ifndef AC_TILE_Y
-#define AC_TILE_Y 8
+#define AC_TILE_Y 16
 #endif
 constexpr int kTileX = AC_TILE_X, kTileY = AC_TILE_Y;
 
@@ -385,25 +385,30 @@ __global__ void __launch_bounds__(kBlock) k_smooth_tile(const T *__restrict__ xi
                                                         Geo g) {
   constexpr int HL = 2 * SWEEPS;  // halo width
   constexpr int RW = kTileX + 2 * HL, RH = kTileY + 2 * HL;
-  // staged region, phase-major within each row: tile[(ly*N + i)*RW + lx]
+  constexpr int ROW = RW * N;         // values per staged row
+  constexpr int REG = RH * ROW;       // values per staged array
+  // staged region, phase-major within each row: a[(ly*N + i)*RW + lx], for
+  // x, rhs and (shifted form) the obstacle
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *tile = reinterpret_cast<T *>(smem_raw);
+  T *trhs = tile + REG;
+  T *tob = trhs + REG;
   const int x0 = blockIdx.x * kTileX - HL, y0 = blockIdx.y * kTileY - HL;  // region origin (global node)
   const T w = corr ? (T)*omega : T(0);
-  // stage the region (each row is a contiguous span of N values per node in HBM)
-  for (int ly = 0; ly < RH; ++ly) {
-    const int gy = y0 + ly;
-    if (gy < 0 || gy > g.H) continue;
-    const int gx_lo = x0 < 0 ? 0 : x0, gx_hi = (x0 + RW - 1) > g.W ? g.W : (x0 + RW - 1);
-    const int cnt = (gx_hi - gx_lo + 1) * N;
-    const int64_t base = ((int64_t)gy * g.Wn + gx_lo) * N;
-    T *row = tile + (int64_t)ly * N * RW + (gx_lo - x0);
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      T v = __ldg(xin + base + e);
-      if (w != T(0)) v += w * __ldg(corr + base + e);
-      const int node = e / N, i = e - node * N;
-      row[i * RW + node] = v;
-    }
+  // stage: one flat loop over the region so that many loads are in flight
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < REG; idx += blockDim.x) {
+    const int ly = idx / ROW, e = idx - ly * ROW;
+    const int node = e / N, i = e - node * N;
+    const int gy = y0 + ly, gx = x0 + node;
+    if (gy < 0 || gy > g.H || gx < 0 || gx > g.W) continue;
+    const int64_t gi = ((int64_t)gy * g.Wn + gx) * N + i;
+    const int si = (ly * N + i) * RW + node;
+    T v = __ldg(xin + gi);
+    if (w != T(0)) v += w * __ldg(corr + gi);
+    tile[si] = v;
+    trhs[si] = __ldg(rhs + gi);
+    if constexpr (SH) tob[si] = __ldg(ob + gi);
   }
   __syncthreads();
   const T te = (T)g.te;
@@ -419,8 +424,9 @@ __global__ void __launch_bounds__(kBlock) k_smooth_tile(const T *__restrict__ xi
       const int par = (((x0 + lx0) + gy) & 1) != color ? 1 : 0;  // first column of this colour
       const int lx = lx0 + 2 * k + par, gx = x0 + lx;
       if (lx >= lx0 + rw || gx < 0 || gx > g.W || gy < 0 || gy > g.H) continue;
-      T *c = tile + (int64_t)ly * N * RW + lx;  // phase i at c[i*RW]
-      T acc[N], bk[N], o[N];
+      const int off = ly * N * RW + lx;
+      T *c = tile + off;  // phase i at c[i*RW]
+      T acc[N], o[N];
       const bool interior = gx > 0 && gx < g.W && gy > 0 && gy < g.H;
       if (interior) {
 #pragma unroll
@@ -437,12 +443,12 @@ __global__ void __launch_bounds__(kBlock) k_smooth_tile(const T *__restrict__ xi
           acc[i] = a;
         }
       }
-      const int64_t n = (int64_t)gy * g.Wn + gx;
-      ldn<T, N>(rhs + n * N, bk);
-      if constexpr (SH) ldn<T, N>(ob + n * N, o);
       const T invD = (T)g.invD[node_class(g, gx, gy)];
 #pragma unroll
-      for (int i = 0; i < N; ++i) acc[i] = (bk[i] + te * acc[i]) * invD;
+      for (int i = 0; i < N; ++i) {
+        acc[i] = (trhs[off + i * RW] + te * acc[i]) * invD;
+        if constexpr (SH) o[i] = tob[off + i * RW];
+      }
       proj_box<T, N, SH>(acc, o);
 #pragma unroll
       for (int i = 0; i < N; ++i) c[i * RW] = acc[i];
@@ -450,24 +456,20 @@ __global__ void __launch_bounds__(kBlock) k_smooth_tile(const T *__restrict__ xi
     __syncthreads();
   }
   // write the tile interior back, node-major
-  for (int ly = HL; ly < HL + kTileY; ++ly) {
-    const int gy = y0 + ly;
-    if (gy > g.H) break;
-    const int gx_lo = x0 + HL, gx_hi = (x0 + HL + kTileX - 1) > g.W ? g.W : (x0 + HL + kTileX - 1);
-    if (gx_lo > gx_hi) continue;
-    const int cnt = (gx_hi - gx_lo + 1) * N;
-    const int64_t base = ((int64_t)gy * g.Wn + gx_lo) * N;
-    const T *row = tile + (int64_t)ly * N * RW + HL;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int node = e / N, i = e - node * N;
-      xout[base + e] = row[i * RW + node];
-    }
+  constexpr int IROW = kTileX * N;
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < kTileY * IROW; idx += blockDim.x) {
+    const int ty = idx / IROW, e = idx - ty * IROW;
+    const int node = e / N, i = e - node * N;
+    const int gy = y0 + HL + ty, gx = x0 + HL + node;
+    if (gy > g.H || gx > g.W) continue;
+    xout[((int64_t)gy * g.Wn + gx) * N + i] = tile[((HL + ty) * N + i) * RW + HL + node];
   }
 }
 
-template <typename T, int N, int SWEEPS>
+template <typename T, int N, bool SH, int SWEEPS>
 constexpr size_t smooth_tile_smem() {
-  return (size_t)(kTileX + 4 * SWEEPS) * (kTileY + 4 * SWEEPS) * N * sizeof(T);
+  return (SH ? 3 : 2) * (size_t)(kTileX + 4 * SWEEPS) * (kTileY + 4 * SWEEPS) * N * sizeof(T);
 }
 
 // ---------------------------------------------------------------------------

@@ -15,7 +15,7 @@ struct SolverLaunch {
   template <int SW>
   static void tile_launch(const T *in, T *out, const void *rhs, const void *ob, const void *corr, const double *omega,
                           const Geo &g, cudaStream_t s) {
-    constexpr size_t smem = smooth_tile_smem<T, N, SW>();
+    constexpr size_t smem = smooth_tile_smem<T, N, SH, SW>();
     static bool attr = false;  // opt in to more than 48 KB of dynamic shared memory once
     if (!attr) {
       cudaFuncSetAttribute(k_smooth_tile<T, N, SH, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
