@@ -243,8 +243,8 @@ def main():
     sm_ms = prof.ms[ac.PROF_CLASSES.index("smooth")]
     avg_launch_s = sm_ms / 1e3 / max(1, sm_launches)
     achieved = prof.smooth_bytes_per_launch / avg_launch_s / 1e9
-    kname = "k_smooth_tile<float,N,shifted>" if args.precision == "mixed" else "k_smooth_tile<double,N,direct>"
-    roofline = {"bound": "hbm", "kernel": kname + " (one or two tile-fused red-black projected sweeps)",
+    kname = "k_smooth_fine<float,N,shifted>" if args.precision == "mixed" else "k_smooth_fine<double,N,direct>"
+    roofline = {"bound": "hbm", "kernel": kname + " (one colour of a red-black projected sweep)",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                 "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
                 "bytes_per_launch": prof.smooth_bytes_per_launch, "avg_launch_ms": avg_launch_s * 1e3,

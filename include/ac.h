@@ -92,7 +92,7 @@ typedef struct {
 
 /* Kernel classes of the profile (no counterpart in the paper: instrumentation). */
 enum {
-  AC_PROF_SMOOTH = 0,  /* fine red-black projected Gauss-Seidel (tile-fused sweeps) */
+  AC_PROF_SMOOTH = 0,  /* fine red-black projected Gauss-Seidel, one launch per colour */
   AC_PROF_RESID,       /* fine residual, natural residual, mask, tangent projection */
   AC_PROF_COARSE,      /* coarse-level smoothing, residuals and coarsest solve */
   AC_PROF_TRANSFER,    /* truncated Galerkin operators, restriction, prolongation */
@@ -105,10 +105,10 @@ enum {
 typedef struct {
   double ms[AC_PROF_COUNT];        /* summed device time per class (CUDA events on the context's stream) */
   int64_t launches[AC_PROF_COUNT]; /* kernel launches per class while profiling was on */
-  double smooth_bytes_per_launch;  /* algorithmic HBM bytes of one smoother launch (one or two full
-                                      red-black sweeps of the whole grid, tile-fused): AC_FP64 3 n N 8
-                                      (u and b read, u written), AC_MIXED 4 n N 4 (delta, r and the
-                                      obstacle read, delta written) */
+  double smooth_bytes_per_launch;  /* algorithmic HBM bytes of one smoother launch (one colour): AC_FP64
+                                      1.5 n N 8 (b of the colour, u of the other colour read, u of the
+                                      colour written), AC_MIXED 2 n N 4 (r and obstacle of the colour,
+                                      delta of the other colour read, delta of the colour written) */
   int64_t total_launches;          /* every kernel launched by this context since creation */
 } ac_profile;
 

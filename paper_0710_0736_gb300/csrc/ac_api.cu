@@ -120,7 +120,7 @@ struct GraphSlot {
 // constraint set of the instantiation (see ac_kernels.cuh).
 struct Solve {
   const ac::SolverOps *o = nullptr;
-  void *x = nullptr, *x2 = nullptr, *rhs = nullptr, *ob = nullptr, *rt = nullptr, *d = nullptr;
+  void *x = nullptr, *rhs = nullptr, *ob = nullptr, *rt = nullptr, *d = nullptr;
   uint8_t *mask = nullptr;
   std::vector<Level> lv;  // lv[0]: fine level geometry
   ac::Galerkin0Table tab0{};
@@ -402,7 +402,7 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
     const int nsw = later ? ctx->p.nu1 + ctx->p.nu2 : ctx->p.nu1;
     const void *corr = (later && coarse) ? S.d : nullptr;
     int rc = run_graph(ctx, S.smooth_resid[prof][later], [&]() -> int {
-      AC_RUN(AC_PROF_SMOOTH, o->smooth(S.x, S.x2, S.rhs, S.ob, corr, ctx->omega, g0, nsw, ctx->s));
+      AC_RUN(AC_PROF_SMOOTH, o->smooth(S.x, S.rhs, S.ob, corr, ctx->omega, g0, nsw, ctx->s));
       AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
       AC_RUN(AC_PROF_RESID, o->resid(S.x, S.rhs, S.ob, g0, S.rt, S.mask, ctx->rho, ctx->s));
       return AC_OK;
@@ -595,7 +595,6 @@ int ac_create(ac_ctx **out, const ac_params *p) {
       S.rhs = ctx->b;
       S.ob = nullptr;
     }
-    AC_ALLOC(S.x2, fNs);
     AC_ALLOC(S.rt, fNs);
     AC_ALLOC(S.mask, (size_t)ctx->n);
     if (S.lv.size() > 1) AC_ALLOC(S.d, fNs);
@@ -861,8 +860,8 @@ int ac_get_profile(ac_ctx *ctx, ac_profile *out) {
     out->ms[k] = ctx->prof_ms[k];
     out->launches[k] = ctx->prof_launches[k];
   }
-  out->smooth_bytes_per_launch = ctx->p.precision == AC_MIXED ? 4.0 * (double)ctx->n * ctx->N * sizeof(float)
-                                                               : 3.0 * (double)ctx->n * ctx->N * sizeof(double);
+  out->smooth_bytes_per_launch = ctx->p.precision == AC_MIXED ? 2.0 * (double)ctx->n * ctx->N * sizeof(float)
+                                                               : 1.5 * (double)ctx->n * ctx->N * sizeof(double);
   out->total_launches = ctx->total_launches;
   return AC_OK;
 }

@@ -359,120 +359,6 @@ __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const
 }
 
 // ---------------------------------------------------------------------------
-// a4/a5, fused: SWEEPS full red-black sweeps of a TX x TY tile in one launch.
-// The block stages x_in on the tile plus a ring of width 2*SWEEPS in shared
-// memory (adding omega*corr on the fly when a coarse correction is pending),
-// then runs the 2*SWEEPS colour passes on shrinking rings (pass p updates
-// colour p % 2 on ring 2*SWEEPS-1-p, so every value a pass reads is current),
-// and writes the tile to x_out.  The ring values are recomputed by each
-// neighbouring tile from identical inputs, so the result is exactly that of
-// SWEEPS global red-black sweeps; x_in and x_out must differ (a tile's halo is
-// another tile's interior).  DRAM traffic: x_in, rhs, ob read and x_out
-// written once per launch instead of once per colour pass.
-// ---------------------------------------------------------------------------
-#ifndef AC_TILE_X
-#define AC_TILE_X 32
-#endif
-#ifndef AC_TILE_Y
-#define AC_TILE_Y 16
-#endif
-constexpr int kTileX = AC_TILE_X, kTileY = AC_TILE_Y;
-
-template <typename T, int N, bool SH, int SWEEPS>
-__global__ void __launch_bounds__(kBlock) k_smooth_tile(const T *__restrict__ xin, T *__restrict__ xout,
-                                                        const T *__restrict__ rhs, const T *__restrict__ ob,
-                                                        const T *__restrict__ corr, const double *__restrict__ omega,
-                                                        Geo g) {
-  constexpr int HL = 2 * SWEEPS;  // halo width
-  constexpr int RW = kTileX + 2 * HL, RH = kTileY + 2 * HL;
-  constexpr int ROW = RW * N;         // values per staged row
-  constexpr int REG = RH * ROW;       // values per staged array
-  // staged region, phase-major within each row: a[(ly*N + i)*RW + lx], for
-  // x, rhs and (shifted form) the obstacle
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *tile = reinterpret_cast<T *>(smem_raw);
-  T *trhs = tile + REG;
-  T *tob = trhs + REG;
-  const int x0 = blockIdx.x * kTileX - HL, y0 = blockIdx.y * kTileY - HL;  // region origin (global node)
-  const T w = corr ? (T)*omega : T(0);
-  // stage: one flat loop over the region so that many loads are in flight
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < REG; idx += blockDim.x) {
-    const int ly = idx / ROW, e = idx - ly * ROW;
-    const int node = e / N, i = e - node * N;
-    const int gy = y0 + ly, gx = x0 + node;
-    if (gy < 0 || gy > g.H || gx < 0 || gx > g.W) continue;
-    const int64_t gi = ((int64_t)gy * g.Wn + gx) * N + i;
-    const int si = (ly * N + i) * RW + node;
-    T v = __ldg(xin + gi);
-    if (w != T(0)) v += w * __ldg(corr + gi);
-    tile[si] = v;
-    trhs[si] = __ldg(rhs + gi);
-    if constexpr (SH) tob[si] = __ldg(ob + gi);
-  }
-  __syncthreads();
-  const T te = (T)g.te;
-#pragma unroll 1
-  for (int p = 0; p < 2 * SWEEPS; ++p) {
-    const int ring = 2 * SWEEPS - 1 - p, color = p & 1;
-    const int lx0 = HL - ring, ly0 = HL - ring;
-    const int rw = kTileX + 2 * ring, rh = kTileY + 2 * ring;
-    const int half = (rw + 1) / 2;
-    for (int idx = threadIdx.x; idx < half * rh; idx += blockDim.x) {
-      const int ry = idx / half, k = idx - ry * half;
-      const int ly = ly0 + ry, gy = y0 + ly;
-      const int par = (((x0 + lx0) + gy) & 1) != color ? 1 : 0;  // first column of this colour
-      const int lx = lx0 + 2 * k + par, gx = x0 + lx;
-      if (lx >= lx0 + rw || gx < 0 || gx > g.W || gy < 0 || gy > g.H) continue;
-      const int off = ly * N * RW + lx;
-      T *c = tile + off;  // phase i at c[i*RW]
-      T acc[N], o[N];
-      const bool interior = gx > 0 && gx < g.W && gy > 0 && gy < g.H;
-      if (interior) {
-#pragma unroll
-        for (int i = 0; i < N; ++i) acc[i] = c[i * RW + 1] + c[i * RW - 1] + c[(i + N) * RW] + c[(i - N) * RW];
-      } else {
-        const Weights wt = edge_weights(g, gx, gy);
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          T a = T(0);
-          if (wt.e > 0.f) a += T(wt.e) * c[i * RW + 1];
-          if (wt.w > 0.f) a += T(wt.w) * c[i * RW - 1];
-          if (wt.n > 0.f) a += T(wt.n) * c[(i + N) * RW];
-          if (wt.s > 0.f) a += T(wt.s) * c[(i - N) * RW];
-          acc[i] = a;
-        }
-      }
-      const T invD = (T)g.invD[node_class(g, gx, gy)];
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        acc[i] = (trhs[off + i * RW] + te * acc[i]) * invD;
-        if constexpr (SH) o[i] = tob[off + i * RW];
-      }
-      proj_box<T, N, SH>(acc, o);
-#pragma unroll
-      for (int i = 0; i < N; ++i) c[i * RW] = acc[i];
-    }
-    __syncthreads();
-  }
-  // write the tile interior back, node-major
-  constexpr int IROW = kTileX * N;
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < kTileY * IROW; idx += blockDim.x) {
-    const int ty = idx / IROW, e = idx - ty * IROW;
-    const int node = e / N, i = e - node * N;
-    const int gy = y0 + HL + ty, gx = x0 + HL + node;
-    if (gy > g.H || gx > g.W) continue;
-    xout[((int64_t)gy * g.Wn + gx) * N + i] = tile[((HL + ty) * N + i) * RW + HL + node];
-  }
-}
-
-template <typename T, int N, bool SH, int SWEEPS>
-constexpr size_t smooth_tile_smem() {
-  return (SH ? 3 : 2) * (size_t)(kTileX + 4 * SWEEPS) * (kTileY + 4 * SWEEPS) * N * sizeof(T);
-}
-
-// ---------------------------------------------------------------------------
 // a6/a9: fine residual r = rhs - S x, natural residual rho = max |x - P(z)|
 // (z = x + r/S_nn), free-phase mask and the tangent projection of r:
 //   free_n,i = x_n,i above its bound, and at least two phases of node n free;

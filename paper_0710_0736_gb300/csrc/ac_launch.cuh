@@ -12,46 +12,16 @@ inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBl
 
 template <typename T, int N, bool SH>
 struct SolverLaunch {
-  template <int SW>
-  static void tile_launch(const T *in, T *out, const void *rhs, const void *ob, const void *corr, const double *omega,
-                          const Geo &g, cudaStream_t s) {
-    constexpr size_t smem = smooth_tile_smem<T, N, SH, SW>();
-    static bool attr = false;  // opt in to more than 48 KB of dynamic shared memory once
-    if (!attr) {
-      cudaFuncSetAttribute(k_smooth_tile<T, N, SH, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = true;
-    }
-    const dim3 grid((unsigned)((g.W + kTileX) / kTileX), (unsigned)((g.H + kTileY) / kTileY));
-    k_smooth_tile<T, N, SH, SW><<<grid, kBlock, smem, s>>>(in, out, (const T *)rhs, (const T *)ob, (const T *)corr,
-                                                           omega, g);
-  }
-  // `sweeps` red-black sweeps: an even number of tile launches of 1 or 2
-  // sweeps each, ping-ponging x -> x2 -> x; a single sweep uses the in-place
-  // per-colour kernel (two launches).
-  static int smooth(void *x, void *x2, const void *rhs, const void *ob, const void *corr, const double *omega,
-                    const Geo &g, int sweeps, cudaStream_t s) {
-    if (sweeps <= 0) return 0;
-    if (sweeps == 1) {
-      const dim3 grid = row_grid((g.W + 2) / 2, g.H + 1);
+  // `sweeps` red-black sweeps in place, one launch per colour; the pending
+  // coarse correction (corr != null) is applied inside the first launch.
+  static int smooth(void *x, const void *rhs, const void *ob, const void *corr, const double *omega, const Geo &g,
+                    int sweeps, cudaStream_t s) {
+    const dim3 grid = row_grid((g.W + 2) / 2, g.H + 1);
+    for (int k = 0; k < sweeps; ++k)
       for (int c = 0; c < 2; ++c)
         k_smooth_fine<T, N, SH><<<grid, kBlock, 0, s>>>((T *)x, (const T *)rhs, (const T *)ob,
-                                                        c == 0 ? (const T *)corr : nullptr, omega, g, c);
-      return 2;
-    }
-    int launches = (sweeps + 1) / 2;
-    if (launches % 2) ++launches;
-    int two = sweeps - launches;  // launches doing 2 sweeps; the rest do 1
-    T *bufs[2] = {(T *)x, (T *)x2};
-    for (int k = 0; k < launches; ++k) {
-      const T *in = bufs[k % 2];
-      T *out = bufs[(k + 1) % 2];
-      const void *c = k == 0 ? corr : nullptr;
-      if (k < two)
-        tile_launch<2>(in, out, rhs, ob, c, omega, g, s);
-      else
-        tile_launch<1>(in, out, rhs, ob, c, omega, g, s);
-    }
-    return launches;
+                                                        k == 0 && c == 0 ? (const T *)corr : nullptr, omega, g, c);
+    return 2 * sweeps;
   }
   static int resid(const void *x, const void *rhs, const void *ob, const Geo &g, void *rt, uint8_t *mask,
                    double *rho, cudaStream_t s) {

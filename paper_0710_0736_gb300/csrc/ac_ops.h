@@ -16,11 +16,10 @@ constexpr int kMaxPartBlocks = 1024;
 // arguments are typed by that instantiation (double or float).
 struct SolverOps {
   int elem;  // sizeof(scalar)
-  // sweeps red-black sweeps ending in x (x2: a second buffer of the same size);
-  // with corr != null the pending coarse correction x += (*omega) corr is
-  // applied inside the first launch
-  int (*smooth)(void *x, void *x2, const void *rhs, const void *ob, const void *corr, const double *omega,
-                const Geo &g, int sweeps, cudaStream_t s);
+  // sweeps red-black sweeps in place; with corr != null the pending coarse
+  // correction x += (*omega) corr is applied inside the first launch
+  int (*smooth)(void *x, const void *rhs, const void *ob, const void *corr, const double *omega, const Geo &g,
+                int sweeps, cudaStream_t s);
   int (*resid)(const void *x, const void *rhs, const void *ob, const Geo &g, void *rt, uint8_t *mask, double *rho,
                cudaStream_t s);
   int (*restrict0)(const void *rt, const Geo &gf, const Geo &gc, void *r1, cudaStream_t s);
