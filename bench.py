@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--crop", type=int, default=256, help="side of the image crop the CPU oracle times")
     ap.add_argument("--cpu-steps", type=int, default=3, help="oracle steps in the cpu_baseline sample")
+    ap.add_argument("--workload", choices=["single", "batch"], default="single",
+                    help="single: the 4096^2 N=8 image; batch: 256 uneven images (sizes 128^2..1024^2, N 2/4/6)")
+    ap.add_argument("--batch-images", type=int, default=256)
+    ap.add_argument("--streams", type=int, default=16)
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -179,10 +184,83 @@ def run_reference(args):
 # our arm
 # --------------------------------------------------------------------------
 
+def run_batch(args):
+    """The uneven batch: 256 shape images (as the 64x64 workload, scaled) of
+    sizes 128^2..1024^2 and 768x512, N in {2,4,6}, noise sigma U[0.02,0.15],
+    eps 2, lambda 1, tau 4, mixed precision to tol 1e-6.  value = image time
+    steps per second (each timed step advances all images once)."""
+    import torch
+    from paper_0710_0736_gb300 import ac, synth
+    specs = synth.batch_specs(0, args.batch_images)
+    tol = args.tol if args.tol is not None else 1e-6
+    imgs = []
+    for sp in specs:
+        s = sp["W"] / 64.0
+        imgs.append(synth.shapes_image(sp["seed"], sp["W"], sp["H"], sigma=sp["sigma"],
+                                       rect_side=(max(1, int(8 * s)), max(1, int(32 * s))), disk_r=(4 * s, 16 * s)))
+        sp.update(eps=2.0, lam=1.0, tau=4.0, tol=tol, max_cycles=1000)
+
+    def make(precision, streams):
+        for sp in specs:
+            sp["precision"] = precision
+        b = ac.Batch(specs, n_streams=streams)
+        for k, im in enumerate(imgs):
+            b.set_image(k, im)
+        return b
+
+    b = make(ac.AC_MIXED, args.streams)
+    chosen = None
+    t_tune = 0.0
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        chosen = b.tune(trial_steps=2)
+        t_tune = time.perf_counter() - t0
+    b.step(args.warmup, allow_not_converged=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = b.step(args.steps, allow_not_converged=True)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    b.close()
+    # the plain FP64 form, one image after another on one stream
+    b64 = make(ac.AC_FP64, 1)
+    b64.step(1, allow_not_converged=True)
+    k64 = max(1, min(args.steps, args.fp64_steps or 1))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st64 = b64.step(k64, allow_not_converged=True)
+    torch.cuda.synchronize()
+    el64 = time.perf_counter() - t0
+    b64.close()
+    value = st.images * args.steps / el
+    v64 = st64.images * k64 / el64
+    sizes = {}
+    for sp in specs:
+        key = f"{sp['W']}x{sp['H']}/N{sp['N']}"
+        sizes[key] = sizes.get(key, 0) + 1
+    line = {"metric": "batched Allen-Cahn image time steps/s (256 uneven images)", "value": value,
+            "unit": "image-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{st.images} images, sizes 128^2/256^2/512^2/1024^2/768x512, N in 2/4/6, "
+                                   f"tol {tol:g}, mixed precision, {args.streams} streams, autotuned "
+                                   f"{'no' if args.no_tune else 'yes'}", "nodes": st.nodes, "dof": st.dof,
+                       "groups": sizes},
+            "gdof_per_s": st.dof_sweeps / el / 1e9,
+            "vcycles_per_image_step": st.total_cycles / (st.images * args.steps),
+            "all_converged": st.converged_images == st.images, "tune_seconds": t_tune,
+            "plain_fp64_gpu": {"value": v64, "unit": "image-steps/s", "steps": k64, "streams": 1,
+                               "ratio_batched_mixed_over_fp64": value / v64}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     import torch
     import torch.distributed as dist
 

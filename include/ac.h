@@ -184,6 +184,50 @@ int ac_set_profiling(ac_ctx *ctx, int enable);
  * ac_set_profiling call (total_launches counts from creation). */
 int ac_get_profile(ac_ctx *ctx, ac_profile *out);
 
+/* ---- batches of independent images (no counterpart in the paper) -------- */
+
+/* A batch runs many independent images (uneven sizes and phase counts) at
+ * once: one context per image, each with its own CUDA-graph V-cycles, spread
+ * over n_streams CUDA streams (longest-processing-time first on
+ * (W+1)(H+1)N) and advanced by one host worker thread per stream.  Each
+ * image's results are bit-identical to a single-image context with the same
+ * parameters and schedule. */
+typedef struct ac_batch ac_batch;
+
+typedef struct {
+  int images;             /* images in the batch */
+  int steps;              /* time steps per image done by the call */
+  int converged_images;   /* images whose every step reached tol */
+  int64_t total_cycles;   /* V-cycles over all images and steps */
+  int64_t fine_sweeps;    /* fine-level red-black sweeps over all images and steps */
+  int64_t nodes;          /* sum over images of (W+1)(H+1) */
+  int64_t dof;            /* sum over images of N (W+1)(H+1) */
+  double dof_sweeps;      /* sum over images of N (W+1)(H+1) x fine sweeps (for GDOF/s) */
+} ac_batch_stats;
+
+/* params[k] describes image k; its stream field is ignored.  AC_ERR_ARG if
+ * count < 1, n_streams < 1 or any params[k] is invalid. */
+int ac_batch_create(ac_batch **out, const ac_params *params, int count, int n_streams);
+/* ac_set_image / ac_set_phase / ac_get_phase of image k. */
+int ac_batch_set_image(ac_batch *b, int k, const float *rgb, int is_device);
+int ac_batch_set_phase(ac_batch *b, int k, const double *u, int is_device);
+int ac_batch_get_phase(ac_batch *b, int k, double *u, int is_device);
+/* Pixel labels (rounded composite, Sec. 4.3) of image k's current field. */
+int ac_batch_segment(ac_batch *b, int k, int8_t *labels, int is_device);
+/* Advance every image n_steps time steps (Sec. 3.2).  Returns the first
+ * error of any image (AC_ERR_NOT_CONVERGED only if nothing worse happened). */
+int ac_batch_step(ac_batch *b, int n_steps, ac_batch_stats *out);
+/* Autotuner: per group of images with equal size, N and model parameters,
+ * time trial_steps steps of every candidate schedule -- (nu1, nu2) in
+ * {(1,1),(2,1),(1,2),(2,2)} and multigrid depth in {all levels, 5} -- on the
+ * group's first image (its state is restored after each trial) and give the
+ * whole group the fastest candidate that converged.  chosen (nullable,
+ * count x 3 ints) receives nu1, nu2 and depth per image.  Every image needs
+ * its image set first. */
+int ac_batch_tune(ac_batch *b, int trial_steps, int *chosen);
+/* Free the batch (NULL is accepted). */
+void ac_batch_destroy(ac_batch *b);
+
 /* ---- colour means without device allocation (no counterpart in the paper) -- */
 
 /* Colour means c_i = int u_i I / int u_i (N x 3 FP64, device) of a phase field

@@ -22,7 +22,8 @@ EXPORTS = [
     "ac_default_params", "ac_create", "ac_set_image", "ac_set_image_f64", "ac_step", "ac_segment", "ac_destroy",
     "ac_set_phase", "ac_get_phase", "ac_get_means", "ac_get_moments", "ac_get_rhs", "ac_get_node_labels",
     "ac_energy", "ac_residual", "ac_project_simplex", "ac_set_profiling", "ac_get_profile", "ac_colour_means_static",
-    "ac_last_error",
+    "ac_batch_create", "ac_batch_set_image", "ac_batch_set_phase", "ac_batch_get_phase", "ac_batch_segment",
+    "ac_batch_step", "ac_batch_tune", "ac_batch_destroy", "ac_last_error",
 ]
 PROF_CLASSES = ["smooth", "resid", "coarse", "transfer", "linesearch", "setup", "outer"]
 
@@ -52,6 +53,15 @@ class ac_profile(C.Structure):
                 "launches": dict(zip(PROF_CLASSES, list(self.launches))),
                 "smooth_bytes_per_launch": self.smooth_bytes_per_launch,
                 "total_launches": self.total_launches}
+
+
+class ac_batch_stats(C.Structure):
+    _fields_ = [("images", C.c_int), ("steps", C.c_int), ("converged_images", C.c_int),
+                ("total_cycles", C.c_int64), ("fine_sweeps", C.c_int64), ("nodes", C.c_int64), ("dof", C.c_int64),
+                ("dof_sweeps", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class AcError(RuntimeError):
@@ -86,6 +96,14 @@ def _load():
         "ac_set_profiling": ([vp, i], i),
         "ac_get_profile": ([vp, P(ac_profile)], i),
         "ac_colour_means_static": ([vp, vp, i, i, i, vp, vp], i),
+        "ac_batch_create": ([P(vp), P(ac_params), i, i], i),
+        "ac_batch_set_image": ([vp, i, vp, i], i),
+        "ac_batch_set_phase": ([vp, i, vp, i], i),
+        "ac_batch_get_phase": ([vp, i, vp, i], i),
+        "ac_batch_segment": ([vp, i, vp, i], i),
+        "ac_batch_step": ([vp, i, P(ac_batch_stats)], i),
+        "ac_batch_tune": ([vp, i, vp], i),
+        "ac_batch_destroy": ([vp], None),
         "ac_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -254,6 +272,26 @@ def ac_colour_means_static(u, rgb, W, H, N, c, stream=None):
     return _check(lib.ac_colour_means_static(pu, pr, W, H, N, pc, stream if stream is not None else _current_stream()))
 
 
+def ac_batch_create(params_list, n_streams):
+    arr = (ac_params * len(params_list))(*params_list)
+    b = C.c_void_p()
+    _check(lib.ac_batch_create(C.byref(b), arr, len(params_list), n_streams))
+    return b
+
+
+def ac_batch_step(b, n_steps, allow_not_converged=False):
+    st = ac_batch_stats()
+    ok = (AC_OK, AC_ERR_NOT_CONVERGED) if allow_not_converged else (AC_OK,)
+    rc = _check(lib.ac_batch_step(b, n_steps, C.byref(st)), ok)
+    return rc, st
+
+
+def ac_batch_tune(b, count, trial_steps=2):
+    chosen = np.zeros((count, 3), np.int32)
+    _check(lib.ac_batch_tune(b, trial_steps, chosen.ctypes.data))
+    return chosen
+
+
 def ac_last_error() -> str:
     return lib.ac_last_error().decode()
 
@@ -319,3 +357,59 @@ class Segmenter:
 
     def residual(self):
         return ac_residual(self.ctx)
+
+
+class Batch:
+    """Many independent images (uneven sizes and phase counts) advanced together.
+
+    specs: list of dicts with W, H, N and optionally eps, lam, tau, tol,
+    precision, seed, nu1, nu2, coarse_min, max_cycles."""
+
+    def __init__(self, specs, n_streams=8):
+        self.specs = [dict(s) for s in specs]
+        plist = []
+        for sp in self.specs:
+            kw = {k: sp[k] for k in ("tol", "precision", "seed", "nu1", "nu2", "coarse_min", "max_cycles") if k in sp}
+            plist.append(ac_default_params(width=sp["W"], height=sp["H"], n_phases=sp["N"], eps=sp.get("eps", 2.0),
+                                           tau=sp.get("tau", 4.0), stream=None, **{"lambda": sp.get("lam", 1.0)},
+                                           **kw))
+        self.b = ac_batch_create(plist, n_streams)
+
+    def close(self):
+        if self.b is not None:
+            lib.ac_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_image(self, k, rgb):
+        sp = self.specs[k]
+        ptr, dev = _buf(rgb, np.float32, sp["W"] * sp["H"] * 3)
+        return _check(lib.ac_batch_set_image(self.b, k, ptr, dev))
+
+    def set_phase(self, k, u):
+        sp = self.specs[k]
+        ptr, dev = _buf(u, np.float64, (sp["W"] + 1) * (sp["H"] + 1) * sp["N"])
+        return _check(lib.ac_batch_set_phase(self.b, k, ptr, dev))
+
+    def phase(self, k):
+        sp = self.specs[k]
+        u = np.zeros(((sp["W"] + 1) * (sp["H"] + 1), sp["N"]))
+        _check(lib.ac_batch_get_phase(self.b, k, u.ctypes.data, 0))
+        return u
+
+    def labels(self, k):
+        sp = self.specs[k]
+        lab = np.zeros((sp["H"], sp["W"]), np.int8)
+        _check(lib.ac_batch_segment(self.b, k, lab.ctypes.data, 0))
+        return lab
+
+    def step(self, n=1, allow_not_converged=False):
+        return ac_batch_step(self.b, n, allow_not_converged)[1]
+
+    def tune(self, trial_steps=2):
+        return ac_batch_tune(self.b, len(self.specs), trial_steps)

@@ -5,12 +5,17 @@
 // wraps it in an FP64 defect correction (solve_mixed).
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
+#include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/ac.h"
@@ -123,6 +128,7 @@ struct Solve {
   void *x = nullptr, *rhs = nullptr, *ob = nullptr, *rt = nullptr, *d = nullptr;
   uint8_t *mask = nullptr;
   std::vector<Level> lv;  // lv[0]: fine level geometry
+  int depth = 0;          // levels in use (<= lv.size()); a schedule can cut the hierarchy short
   ac::Galerkin0Table tab0{};
   // graphs [profiling][variant]: smoothing + residual of the first / a later
   // cycle, and the coarse correction with its line search
@@ -360,7 +366,7 @@ int coarse_vcycle(ac_ctx *ctx, Solve &S, int k) {
   Level &L = S.lv[k];
   const ac::SolverOps *o = S.o;
   AC_CUDA(cudaMemsetAsync(L.v, 0, (size_t)L.n * ctx->N * o->elem, ctx->s));
-  if (k == (int)S.lv.size() - 1) {
+  if (k == S.depth - 1) {
     if (L.n <= kCoarsestBlockNodes)
       AC_RUN(AC_PROF_COARSE, o->coarse_solve(L.op, L.r, L.v, L.g, kCoarsestSweeps, ctx->s));
     else
@@ -392,7 +398,7 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
              int64_t *sweeps_out) {
   const ac::SolverOps *o = S.o;
   const ac::Geo &g0 = S.lv[0].g;
-  const bool coarse = S.lv.size() > 1;
+  const bool coarse = S.depth > 1;
   double rho = 0;
   int cyc = 0, status = AC_ERR_NOT_CONVERGED;
   int64_t sweeps = 0;
@@ -425,7 +431,7 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
     rc = run_graph(ctx, S.correction[prof], [&]() -> int {
       Level &L1 = S.lv[1];
       AC_RUN(AC_PROF_TRANSFER, o->galerkin0(S.mask, g0, L1.g, S.tab0, L1.op, ctx->s));
-      for (size_t k = 1; k + 1 < S.lv.size(); ++k)
+      for (int k = 1; k + 1 < S.depth; ++k)
         AC_RUN(AC_PROF_TRANSFER, o->galerkin(S.lv[k].op, S.lv[k].g, S.lv[k + 1].g, S.lv[k + 1].op, ctx->s));
       AC_RUN(AC_PROF_TRANSFER, o->restrict0(S.rt, g0, L1.g, L1.r, ctx->s));
       int rc2 = coarse_vcycle(ctx, S, 1);
@@ -575,6 +581,7 @@ int ac_create(ac_ctx **out, const ac_params *p) {
     S.lv.push_back(L);
   }
   ctx->n = S.lv[0].n;
+  S.depth = (int)S.lv.size();
   if (S.lv.size() > 1) S.tab0 = galerkin0_table(S.lv[0].g, S.lv[1].g);
   const int N = ctx->N;
   const size_t es = (size_t)S.o->elem;
@@ -873,3 +880,230 @@ const char *ac_last_error(void) { return g_last_error.c_str(); }
 namespace ac {
 void set_last_error(const char *msg) { g_last_error = msg; }
 }  // namespace ac
+
+// ---------------------------------------------------------------------------
+// Batches of independent images (uneven sizes and phase counts).
+//
+// Every image has its own context (its own CUDA-graph V-cycles); the images
+// are spread over a pool of CUDA streams by longest-processing-time-first on
+// the node count times N, and one host worker thread per stream advances its
+// images, so the GPU runs many images' kernels at once while each image keeps
+// its own convergence control.  Each image's arithmetic is exactly that of a
+// single-image context with the same parameters.
+// ---------------------------------------------------------------------------
+
+struct ac_batch {
+  std::vector<ac_ctx *> ctx;
+  std::vector<cudaStream_t> streams;
+  std::vector<std::vector<int>> assign;  // image indices per stream
+};
+
+namespace {
+
+// Change a context's schedule: pre/post sweeps and the number of multigrid
+// levels in use.  The captured graphs depend on both, so they are dropped.
+void set_schedule(ac_ctx *ctx, int nu1, int nu2, int depth) {
+  for (int a = 0; a < 2; ++a) {
+    for (int b = 0; b < 2; ++b) slot_release(ctx->sv.smooth_resid[a][b]);
+    slot_release(ctx->sv.correction[a]);
+  }
+  ctx->p.nu1 = nu1;
+  ctx->p.nu2 = nu2;
+  const int L = (int)ctx->sv.lv.size();
+  ctx->sv.depth = depth < 1 ? 1 : (depth > L ? L : depth);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ac_batch_create(ac_batch **out, const ac_params *params, int count, int n_streams) {
+  if (!out || !params || count < 1 || n_streams < 1) return fail(AC_ERR_ARG, "bad batch arguments");
+  *out = nullptr;
+  for (int k = 0; k < count; ++k) {
+    int rc = validate(&params[k]);
+    if (rc) return fail(rc, "image %d: %s", k, g_last_error.c_str());
+  }
+  ac_batch *b = new (std::nothrow) ac_batch;
+  if (!b) return fail(AC_ERR_NOMEM, "host allocation failed");
+  if (n_streams > count) n_streams = count;
+  auto cleanup = [&](int rc) {
+    std::string msg = g_last_error;
+    ac_batch_destroy(b);
+    g_last_error = msg;
+    return rc;
+  };
+  for (int i = 0; i < n_streams; ++i) {
+    cudaStream_t st;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(fail(AC_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
+    b->streams.push_back(st);
+  }
+  // longest-processing-time-first assignment of images to streams
+  std::vector<int> order(count);
+  for (int k = 0; k < count; ++k) order[k] = k;
+  auto cost = [&](int k) { return (double)(params[k].width + 1) * (params[k].height + 1) * params[k].n_phases; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost(a) > cost(c); });
+  std::vector<double> load(n_streams, 0.0);
+  b->assign.assign(n_streams, {});
+  std::vector<int> stream_of(count);
+  for (int k : order) {
+    int best = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[best] += cost(k);
+    b->assign[best].push_back(k);
+    stream_of[k] = best;
+  }
+  for (auto &v : b->assign) std::sort(v.begin(), v.end());
+  b->ctx.assign(count, nullptr);
+  for (int k = 0; k < count; ++k) {
+    ac_params p = params[k];
+    p.stream = b->streams[stream_of[k]];
+    int rc = ac_create(&b->ctx[k], &p);
+    if (rc) return cleanup(rc);
+  }
+  *out = b;
+  return AC_OK;
+}
+
+void ac_batch_destroy(ac_batch *b) {
+  if (!b) return;
+  for (ac_ctx *c : b->ctx) ac_destroy(c);
+  for (cudaStream_t st : b->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  delete b;
+}
+
+static int batch_index(ac_batch *b, int k) {
+  if (!b) return fail(AC_ERR_ARG, "batch is NULL");
+  if (k < 0 || k >= (int)b->ctx.size()) return fail(AC_ERR_ARG, "image index %d out of range", k);
+  return AC_OK;
+}
+
+int ac_batch_set_image(ac_batch *b, int k, const float *rgb, int is_device) {
+  int rc = batch_index(b, k);
+  return rc ? rc : ac_set_image(b->ctx[k], rgb, is_device);
+}
+
+int ac_batch_set_phase(ac_batch *b, int k, const double *u, int is_device) {
+  int rc = batch_index(b, k);
+  return rc ? rc : ac_set_phase(b->ctx[k], u, is_device);
+}
+
+int ac_batch_get_phase(ac_batch *b, int k, double *u, int is_device) {
+  int rc = batch_index(b, k);
+  return rc ? rc : ac_get_phase(b->ctx[k], u, is_device);
+}
+
+int ac_batch_segment(ac_batch *b, int k, int8_t *labels, int is_device) {
+  int rc = batch_index(b, k);
+  return rc ? rc : ac_segment(b->ctx[k], 0, labels, is_device, nullptr);
+}
+
+int ac_batch_step(ac_batch *b, int n_steps, ac_batch_stats *out) {
+  if (!b) return fail(AC_ERR_ARG, "batch is NULL");
+  if (n_steps < 0) return fail(AC_ERR_ARG, "n_steps must be >= 0");
+  const int count = (int)b->ctx.size();
+  std::vector<ac_stats> st(count);
+  std::vector<int> rcs(count, AC_OK);
+  std::vector<std::string> msgs(count);
+  std::vector<std::thread> workers;
+  for (size_t s = 0; s < b->streams.size(); ++s)
+    workers.emplace_back([&, s]() {
+      for (int k : b->assign[s]) {
+        rcs[k] = ac_step(b->ctx[k], n_steps, &st[k]);
+        if (rcs[k]) msgs[k] = ac_last_error();
+      }
+    });
+  for (auto &w : workers) w.join();
+  ac_batch_stats agg{};
+  agg.images = count;
+  agg.steps = n_steps;
+  int status = AC_OK;
+  for (int k = 0; k < count; ++k) {
+    agg.total_cycles += st[k].total_cycles;
+    agg.fine_sweeps += st[k].fine_sweeps;
+    agg.converged_images += st[k].converged;
+    agg.nodes += b->ctx[k]->n;
+    agg.dof += b->ctx[k]->n * b->ctx[k]->N;
+    agg.dof_sweeps += (double)st[k].fine_sweeps * (double)(b->ctx[k]->n * b->ctx[k]->N);
+    if (rcs[k] && (status == AC_OK || status == AC_ERR_NOT_CONVERGED)) {
+      status = rcs[k];
+      g_last_error = "image " + std::to_string(k) + ": " + msgs[k];
+    }
+  }
+  if (out) *out = agg;
+  return status;
+}
+
+// Empirical schedule search.  Images with the same size, phase count and
+// model parameters form a group; on the group's first image every candidate
+// (nu1, nu2) in {(1,1), (2,1), (1,2), (2,2)} x depth in {all levels, 5} is run
+// for trial_steps steps from the image's current state (restored after each
+// trial) and timed; the fastest candidate whose steps all converged is applied
+// to the whole group.
+int ac_batch_tune(ac_batch *b, int trial_steps, int *chosen) {
+  if (!b || trial_steps < 1) return fail(AC_ERR_ARG, "bad tune arguments");
+  const int count = (int)b->ctx.size();
+  std::map<std::tuple<int, int, int, int, double, double, double, double>, std::vector<int>> groups;
+  for (int k = 0; k < count; ++k) {
+    const ac_params &p = b->ctx[k]->p;
+    if (!b->ctx[k]->have_image) return fail(AC_ERR_STATE, "image %d has no image set", k);
+    groups[std::make_tuple(p.width, p.height, p.n_phases, p.precision, p.eps, p.lambda, p.tau, p.tol)].push_back(k);
+  }
+  const int nus[4][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}};
+  for (auto &kv : groups) {
+    ac_ctx *c = b->ctx[kv.second.front()];
+    const int L = (int)c->sv.lv.size();
+    void *snap = nullptr;
+    const size_t bytes = (size_t)c->n * c->N * sizeof(double);
+    AC_CUDA(cudaMalloc(&snap, bytes));
+    AC_CUDA(cudaMemcpyAsync(snap, c->u, bytes, cudaMemcpyDeviceToDevice, c->s));
+    double best_t = 1e300;
+    int best[3] = {c->p.nu1, c->p.nu2, L};
+    int rc = AC_OK;
+    for (int nu = 0; nu < 4 && !rc; ++nu)
+      for (int dd = 0; dd < 2 && !rc; ++dd) {
+        const int depth = dd == 0 ? L : (L < 5 ? L : 5);
+        if (dd == 1 && depth == L) continue;
+        set_schedule(c, nus[nu][0], nus[nu][1], depth);
+        rc = ac_set_phase(c, (const double *)snap, 1);
+        if (rc) break;
+        cudaError_t e = cudaStreamSynchronize(c->s);
+        if (e != cudaSuccess) {
+          rc = fail(AC_ERR_CUDA, "%s", cudaGetErrorString(e));
+          break;
+        }
+        ac_stats st{};
+        auto t0 = std::chrono::steady_clock::now();
+        int r = ac_step(c, trial_steps, &st);
+        const double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (r != AC_OK && r != AC_ERR_NOT_CONVERGED) {
+          rc = r;
+          break;
+        }
+        if (st.converged && t < best_t) {
+          best_t = t;
+          best[0] = nus[nu][0];
+          best[1] = nus[nu][1];
+          best[2] = depth;
+        }
+      }
+    int rc2 = rc ? rc : ac_set_phase(c, (const double *)snap, 1);
+    cudaStreamSynchronize(c->s);
+    cudaFree(snap);
+    if (rc2) return rc2;
+    for (int k : kv.second) {
+      set_schedule(b->ctx[k], best[0], best[1], best[2]);
+      if (chosen) {
+        chosen[3 * k + 0] = best[0];
+        chosen[3 * k + 1] = best[1];
+        chosen[3 * k + 2] = best[2];
+      }
+    }
+  }
+  return AC_OK;
+}
+
+}  // extern "C"

@@ -382,3 +382,71 @@ def test_mixed_ragged(ac, W, H, N):
     seg.step(2)
     u_ref, _, _ = oracle.run(synth.round_bf16(img).astype(np.float64), u0, 2.0, 1.0, 4.0, 2, tol=TIGHT, nu1=2, nu2=2)
     assert np.abs(seg.phase() - u_ref).max() < 1e-9
+
+
+# --------------------------------------------------------------------------
+# a12: batches of uneven images
+# --------------------------------------------------------------------------
+
+def _batch_specs():
+    return [dict(W=64, H=64, N=4), dict(W=37, H=23, N=3), dict(W=96, H=64, N=6), dict(W=48, H=40, N=2),
+            dict(W=128, H=128, N=4), dict(W=64, H=32, N=8), dict(W=40, H=24, N=6)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_matches_single_images(ac, precision):
+    """Every image of a batch (uneven sizes and phase counts, 3 streams) ends
+    bit-identical to the same image solved alone."""
+    specs = _batch_specs()
+    prec = ac.AC_MIXED if precision == "mixed" else ac.AC_FP64
+    for sp in specs:
+        sp.update(tol=1e-9, precision=prec)
+    imgs = [synth.shapes_image(7 + k, sp["W"], sp["H"], rect_side=(2, max(2, sp["W"] // 3)),
+                               disk_r=(1, max(1.5, sp["W"] / 5))) for k, sp in enumerate(specs)]
+    u0s = [synth.dirichlet_init(50 + k, (sp["W"] + 1) * (sp["H"] + 1), sp["N"]) for k, sp in enumerate(specs)]
+    b = ac.Batch(specs, n_streams=3)
+    for k in range(len(specs)):
+        b.set_image(k, imgs[k])
+        b.set_phase(k, u0s[k])
+    st = b.step(3)
+    assert st.images == len(specs) and st.converged_images == len(specs)
+    for k, sp in enumerate(specs):
+        seg = ac.Segmenter(sp["W"], sp["H"], sp["N"], 2.0, 1.0, 4.0, tol=1e-9, precision=prec)
+        seg.set_image(imgs[k])
+        seg.set_phase(u0s[k])
+        seg.step(3)
+        assert np.array_equal(b.phase(k), seg.phase()), f"image {k}"
+        assert np.array_equal(b.labels(k), seg.segment(0))
+        seg.close()
+    b.close()
+
+
+def test_batch_autotuner(ac):
+    """The autotuner picks a valid schedule per group; the tuned batch still
+    solves every step to tol (checked by the oracle's natural residual)."""
+    specs = _batch_specs()[:4]
+    for sp in specs:
+        sp.update(tol=1e-8, precision=ac.AC_MIXED)
+    imgs = [synth.shapes_image(3 + k, sp["W"], sp["H"], rect_side=(2, max(2, sp["W"] // 3)),
+                               disk_r=(1, max(1.5, sp["W"] / 5))) for k, sp in enumerate(specs)]
+    b = ac.Batch(specs, n_streams=2)
+    for k in range(len(specs)):
+        b.set_image(k, imgs[k])
+    u_before = [b.phase(k) for k in range(len(specs))]
+    chosen = b.tune(trial_steps=2)
+    for k in range(len(specs)):  # tuning restores the state
+        assert np.array_equal(b.phase(k), u_before[k])
+    assert ((chosen[:, 0] >= 1) & (chosen[:, 0] <= 2) & (chosen[:, 1] >= 1) & (chosen[:, 1] <= 2)).all()
+    assert (chosen[:, 2] >= 1).all()
+    assert b.step(1).converged_images == len(specs)
+    u_prev = [b.phase(k) for k in range(len(specs))]
+    assert b.step(1).converged_images == len(specs)
+    for k, sp in enumerate(specs):
+        W, H = sp["W"], sp["H"]
+        m = oracle.moments(synth.round_bf16(imgs[k]).astype(np.float64))
+        u1 = b.phase(k)
+        assert np.abs(u1.sum(1) - 1).max() < 1e-13 and u1.min() >= 0
+        c, _ = oracle.means(u_prev[k], m, W, H)
+        rhs = oracle.rhs(u_prev[k], m, c, W, H, 2.0, 1.0, 4.0)
+        assert oracle.natural_residual(u1, rhs, W, H, 2.0, 4.0) <= 2e-8
+    b.close()
