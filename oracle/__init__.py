@@ -64,6 +64,7 @@ def lib():
         L.or_pgs_solve.argtypes = [i, i, i, _dp, _dp, d, d, d, i, ip, dpp]
         L.or_step.argtypes = [i, i, i, _dp, _dp, _dp, d, d, d, d, i, i, i, i, i, ip, dpp]
         L.or_labels.argtypes = [i, i, i, _dp, _bp, _bp]
+        L.or_adjoint.argtypes = [i, i, i, _dp, _dp, i, d, d, d, _dp, dpp, dpp, _dp, C.c_void_p, d]
         _lib = L
     return _lib
 
@@ -190,3 +191,40 @@ def run(img, u0, eps, lam, tau, steps, tol=1e-13, method="ssc", **kw):
         u, c, it, rho, st = step(u, m, c, W, H, eps, lam, tau, tol=tol, method=method, **kw)
         stats.append((it, rho, st))
     return u, c, stats
+
+
+def forward_states(img, u0, eps, lam, tau, steps, tol=1e-15, **kw):
+    """u^0..u^T of the oracle's time stepping (list of (n, N) arrays)."""
+    H, W, _ = img.shape
+    m = moments(img)
+    u = _f64(u0)
+    c = np.zeros((u.shape[1], 3))
+    states = [u.copy()]
+    for _ in range(steps):
+        u, c, it, rho, st = step(u, m, c, W, H, eps, lam, tau, tol=tol, **kw)
+        states.append(u.copy())
+    return states
+
+
+def adjoint(img, states, eps, lam, tau, gT, cg_rtol=1e-15):
+    """Gradients of a loss on u^T (gT = dL/du^T) through the steps that
+    produced `states`: returns (dL/dlambda, dL/deps with tau fixed,
+    dL/dI (H, W, 3), dL/du^0 (n, N))."""
+    H, W, _ = img.shape
+    T = len(states) - 1
+    N = states[0].shape[1]
+    st = np.ascontiguousarray(np.stack(states), dtype=np.float64)
+    g_img = np.zeros((H, W, 3))
+    g_u0 = np.zeros_like(st[0])
+    gl, ge = C.c_double(0), C.c_double(0)
+    if lib().or_adjoint(W, H, N, _f64(img), st, T, eps, lam, tau, _f64(gT), C.byref(gl), C.byref(ge), g_img,
+                        g_u0.ctypes.data, cg_rtol):
+        raise ValueError("or_adjoint failed")
+    return gl.value, ge.value, g_img, g_u0
+
+
+def misfit_loss(u, m0, target):
+    """L = 1/2 sum_n Mhat_n |u_n - onehot(target_n)|^2 and dL/du."""
+    onehot = np.eye(u.shape[1])[target.ravel().astype(int)]
+    diff = u - onehot
+    return 0.5 * float((m0[:, None] * diff * diff).sum()), m0[:, None] * diff

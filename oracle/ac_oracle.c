@@ -553,3 +553,157 @@ int or_labels(int W, int H, int N, const double *u, int8_t *node_lab, int8_t *pi
       }
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of T time steps (gradients of a loss on u^T)                      */
+/* ------------------------------------------------------------------------ */
+
+/* The step map u^t -> u^{t+1} of Sec. 3.2 is differentiated with the active
+ * set of u^{t+1} frozen.  At the minimiser the free phases of a node n (those
+ * with u > 0, when there are at least two) satisfy (S u - b)_n,i = mu_n, the
+ * other phases are 0, so du lies in the tangent space V (free phases only,
+ * sum zero per node) and solves  Pi S du = Pi (db - dS u), Pi the orthogonal
+ * projection onto V.  Hence for a loss L with g = dL/du^{t+1}:
+ *     w = (Pi S Pi)^+ Pi g   (w in V),   dL/db = w,   dL/dS = -w u'.
+ * b = Mhat u^t (1 + 2 tau/eps) - tau lambda f(c), f_i = m2 - 2 c_i.m1 + |c_i|^2 m0,
+ * c_i = s_i / M_i (s_i = sum u_i m1, M_i = sum u_i m0) and S = Mhat + tau eps A
+ * (tau held fixed) give the chain rule below. */
+
+/* v -> Pi v over the free set of u (free: u > 0 at nodes with >= 2 such). */
+static void tangent_project(int64_t n, int N, const double *u, const double *v, double *out) {
+  for (int64_t k = 0; k < n; ++k) {
+    int cnt = 0;
+    double s = 0;
+    for (int i = 0; i < N; ++i)
+      if (u[k * N + i] > 0) {
+        ++cnt;
+        s += v[k * N + i];
+      }
+    for (int i = 0; i < N; ++i)
+      out[k * N + i] = (cnt >= 2 && u[k * N + i] > 0) ? v[k * N + i] - s / cnt : 0.0;
+  }
+}
+
+static double dotv(int64_t m, const double *a, const double *b) {
+  double s = 0;
+  for (int64_t k = 0; k < m; ++k) s += a[k] * b[k];
+  return s;
+}
+
+/* Conjugate gradients for (Pi S Pi) w = Pi g in V, from w = 0, until the
+ * residual norm is below rtol times that of Pi g. */
+static int tangent_cg(const or_mesh *m, double te, int N, const double *up, const double *g, double *w, double rtol) {
+  int64_t nn = m->n * N;
+  double *r = calloc(nn, sizeof(double)), *p = calloc(nn, sizeof(double)), *q = calloc(nn, sizeof(double)),
+         *t = calloc(nn, sizeof(double));
+  if (!r || !p || !q || !t) return -1;
+  tangent_project(m->n, N, up, g, r);
+  memset(w, 0, nn * sizeof(double));
+  memcpy(p, r, nn * sizeof(double));
+  double rr = dotv(nn, r, r), r0 = sqrt(rr);
+  int it = 0;
+  while (sqrt(rr) > rtol * r0 && rr > 0 && it < 20 * nn) {
+    for (int64_t k = 0; k < m->n; ++k)
+      for (int i = 0; i < N; ++i) t[k * N + i] = S_row(m, te, k, p, N, i);
+    tangent_project(m->n, N, up, t, q);
+    double a = rr / dotv(nn, p, q);
+    for (int64_t k = 0; k < nn; ++k) {
+      w[k] += a * p[k];
+      r[k] -= a * q[k];
+    }
+    double rr2 = dotv(nn, r, r);
+    for (int64_t k = 0; k < nn; ++k) p[k] = r[k] + (rr2 / rr) * p[k];
+    rr = rr2;
+    ++it;
+  }
+  free(r);
+  free(p);
+  free(q);
+  free(t);
+  return it;
+}
+
+/* states: (T+1) x n x N forward states u^0..u^T produced by or_step with the
+ * same parameters; gT = dL/du^T.  Outputs dL/dlambda, dL/deps (tau fixed),
+ * dL/dI (H x W x 3) and dL/du^0 (n x N, nullable). */
+int or_adjoint(int W, int H, int N, const double *img, const double *states, int T, double eps, double lam, double tau,
+               const double *gT, double *g_lam, double *g_eps, double *g_img, double *g_u0, double cg_rtol) {
+  or_mesh mesh;
+  if (N < 2 || N > OR_MAXN || T < 0 || mesh_build(&mesh, W, H)) return -1;
+  const int64_t n = mesh.n, nn = n * N;
+  const double te = tau * eps, a1 = 1.0 + 2.0 * tau / eps;
+  double *m = malloc(n * 5 * sizeof(double)), *c = malloc((size_t)(T + 1) * N * 3 * sizeof(double));
+  double *g = malloc(nn * sizeof(double)), *gn = malloc(nn * sizeof(double)), *w = malloc(nn * sizeof(double));
+  double *gm = calloc(n * 4, sizeof(double)); /* dL/dm1 (3), dL/dm2 */
+  if (!m || !c || !g || !gn || !w || !gm) return -1;
+  or_moments(W, H, img, m);
+  /* the means the forward used at each step (empty phases keep the previous) */
+  double cprev[OR_MAXN * 3] = {0};
+  for (int t = 0; t < T; ++t) {
+    or_means(W, H, N, states + (int64_t)t * nn, m, cprev, c + (int64_t)t * N * 3, NULL);
+    memcpy(cprev, c + (int64_t)t * N * 3, N * 3 * sizeof(double));
+  }
+  memcpy(g, gT, nn * sizeof(double));
+  double glam = 0, geps = 0;
+  for (int t = T - 1; t >= 0; --t) {
+    const double *u = states + (int64_t)t * nn, *up = states + (int64_t)(t + 1) * nn, *ct = c + (int64_t)t * N * 3;
+    if (tangent_cg(&mesh, te, N, up, g, w, cg_rtol) < 0) return -1;
+    double G[OR_MAXN][3] = {{0}}, M[OR_MAXN] = {0};
+    for (int i = 0; i < N; ++i)
+      for (int64_t k = 0; k < n; ++k) M[i] += u[k * N + i] * m[k * 5];
+    for (int64_t k = 0; k < n; ++k) {
+      const double *mk = m + k * 5;
+      for (int i = 0; i < N; ++i) {
+        const double *ci = ct + i * 3;
+        const double wk = w[k * N + i];
+        double f = mk[4] - 2.0 * (ci[0] * mk[1] + ci[1] * mk[2] + ci[2] * mk[3]) +
+                   (ci[0] * ci[0] + ci[1] * ci[1] + ci[2] * ci[2]) * mk[0];
+        glam += wk * (-tau * f);
+        geps += wk * mk[0] * u[k * N + i] * (-2.0 * tau / (eps * eps));
+        geps += -tau * wk * (S_row(&mesh, te, k, up, N, i) - mesh.mhat[k] * up[k * N + i]) / te;
+        for (int ch = 0; ch < 3; ++ch) G[i][ch] += 2.0 * tau * lam * wk * (mk[1 + ch] - ci[ch] * mk[0]);
+        gm[k * 4 + 3] += -tau * lam * wk;
+        for (int ch = 0; ch < 3; ++ch) gm[k * 4 + ch] += 2.0 * tau * lam * wk * ci[ch];
+      }
+    }
+    for (int64_t k = 0; k < n; ++k) {
+      const double *mk = m + k * 5;
+      for (int i = 0; i < N; ++i) {
+        const double *ci = ct + i * 3;
+        double v = mk[0] * a1 * w[k * N + i];
+        if (M[i] != 0.0)
+          for (int ch = 0; ch < 3; ++ch) {
+            v += G[i][ch] * (mk[1 + ch] - ci[ch] * mk[0]) / M[i];
+            gm[k * 4 + ch] += G[i][ch] * u[k * N + i] / M[i];
+          }
+        gn[k * N + i] = v;
+      }
+    }
+    memcpy(g, gn, nn * sizeof(double));
+  }
+  /* adjoint of the triangle-by-triangle moment assembly (Sec. 4.2) */
+  memset(g_img, 0, (size_t)W * H * 3 * sizeof(double));
+  for (int py = 0; py < H; ++py)
+    for (int px = 0; px < W; ++px) {
+      const double *I = img + ((int64_t)py * W + px) * 3;
+      double *gI = g_img + ((int64_t)py * W + px) * 3;
+      int tri[2][3][2];
+      pixel_triangles(px, py, tri);
+      for (int tt = 0; tt < 2; ++tt)
+        for (int a = 0; a < 3; ++a) {
+          const double *gk = gm + nid(W, tri[tt][a][0], tri[tt][a][1]) * 4;
+          for (int ch = 0; ch < 3; ++ch) gI[ch] += (0.5 / 3.0) * (gk[ch] + 2.0 * I[ch] * gk[3]);
+        }
+    }
+  *g_lam = glam;
+  *g_eps = geps;
+  if (g_u0) memcpy(g_u0, g, nn * sizeof(double));
+  free(m);
+  free(c);
+  free(g);
+  free(gn);
+  free(w);
+  free(gm);
+  mesh_free(&mesh);
+  return 0;
+}
