@@ -184,6 +184,28 @@ int ac_set_profiling(ac_ctx *ctx, int enable);
  * ac_set_profiling call (total_launches counts from creation). */
 int ac_get_profile(ac_ctx *ctx, ac_profile *out);
 
+/* ---- adjoint: gradients of a loss on u after T steps (not in the paper) -- */
+
+/* Run n_steps time steps from the current u (as ac_step), keeping u at steps
+ * 0, k, 2k, ... (k = checkpoint_every, e.g. sqrt(n_steps)) and the colour
+ * means entering them, for ac_adjoint_backward.  Leaves u = u^T. */
+int ac_adjoint_forward(ac_ctx *ctx, int n_steps, int checkpoint_every);
+
+/* Gradients of a loss L through the steps of the last ac_adjoint_forward,
+ * given grad_u = dL/du^T ((H+1)(W+1) x N FP64, device).  Each step (Sec. 3.2)
+ * is differentiated with the active set of u^{t+1} frozen: w solves
+ * (Pi S Pi) w = Pi g in the tangent space of u^{t+1} (free phases, sum zero
+ * per node), by the same truncated V-cycle (FP64, projection Pi in place of
+ * P_G, to 1e-13 max|Pi g|), and dL/db = w, dL/dS = -w u^{t+1}'.  The chain
+ * rule through b = Mhat u^t (1 + 2 tau/eps) - tau lambda f(c(u^t)) and the
+ * image moments then gives dL/dlambda, dL/deps (tau held fixed) (host
+ * doubles), dL/dI (H x W x 3 FP64, device; with respect to the image the
+ * moments used, i.e. after the bfloat16 rounding in AC_MIXED) and dL/du^0
+ * (device, nullable).  Each segment between checkpoints is recomputed from
+ * its checkpoint.  Leaves u = u^T.  AC_ERR_STATE without a forward. */
+int ac_adjoint_backward(ac_ctx *ctx, const double *grad_u, double *grad_lambda, double *grad_eps, double *grad_image,
+                        double *grad_u0);
+
 /* ---- batches of independent images (no counterpart in the paper) -------- */
 
 /* A batch runs many independent images (uneven sizes and phase counts) at

@@ -23,7 +23,8 @@ EXPORTS = [
     "ac_set_phase", "ac_get_phase", "ac_get_means", "ac_get_moments", "ac_get_rhs", "ac_get_node_labels",
     "ac_energy", "ac_residual", "ac_project_simplex", "ac_set_profiling", "ac_get_profile", "ac_colour_means_static",
     "ac_batch_create", "ac_batch_set_image", "ac_batch_set_phase", "ac_batch_get_phase", "ac_batch_segment",
-    "ac_batch_step", "ac_batch_tune", "ac_batch_destroy", "ac_last_error",
+    "ac_batch_step", "ac_batch_tune", "ac_batch_destroy", "ac_adjoint_forward", "ac_adjoint_backward",
+    "ac_last_error",
 ]
 PROF_CLASSES = ["smooth", "resid", "coarse", "transfer", "linesearch", "setup", "outer"]
 
@@ -104,6 +105,8 @@ def _load():
         "ac_batch_step": ([vp, i, P(ac_batch_stats)], i),
         "ac_batch_tune": ([vp, i, vp], i),
         "ac_batch_destroy": ([vp], None),
+        "ac_adjoint_forward": ([vp, i, i], i),
+        "ac_adjoint_backward": ([vp, vp, P(d), P(d), vp, vp], i),
         "ac_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -290,6 +293,24 @@ def ac_batch_tune(b, count, trial_steps=2):
     chosen = np.zeros((count, 3), np.int32)
     _check(lib.ac_batch_tune(b, trial_steps, chosen.ctypes.data))
     return chosen
+
+
+def ac_adjoint_forward(ctx, n_steps, checkpoint_every, allow_not_converged=False):
+    ok = (AC_OK, AC_ERR_NOT_CONVERGED) if allow_not_converged else (AC_OK,)
+    return _check(lib.ac_adjoint_forward(ctx, n_steps, checkpoint_every), ok)
+
+
+def ac_adjoint_backward(ctx, grad_u, grad_image, grad_u0=None, allow_not_converged=False):
+    """grad_u, grad_image, grad_u0: torch CUDA float64 tensors.  Returns
+    (dL/dlambda, dL/deps)."""
+    gl, ge = C.c_double(), C.c_double()
+    ok = (AC_OK, AC_ERR_NOT_CONVERGED) if allow_not_converged else (AC_OK,)
+    for t in (grad_u, grad_image) + ((grad_u0,) if grad_u0 is not None else ()):
+        if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float64"):
+            raise ValueError("ac_adjoint_backward takes contiguous float64 CUDA tensors")
+    _check(lib.ac_adjoint_backward(ctx, grad_u.data_ptr(), C.byref(gl), C.byref(ge), grad_image.data_ptr(),
+                                   None if grad_u0 is None else grad_u0.data_ptr()), ok)
+    return gl.value, ge.value
 
 
 def ac_last_error() -> str:

@@ -16,6 +16,7 @@
 #include <string>
 #include <thread>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/ac.h"
@@ -149,6 +150,23 @@ constexpr double kRho32Margin = 4.8e-7;
 
 }  // namespace
 
+// Adjoint bookkeeping (ac_adjoint_forward / ac_adjoint_backward).
+struct AdjState {
+  bool ready = false;
+  int T = 0, every = 0, ncp = 0;
+  double *cp_u = nullptr;   // checkpoints: u at steps 0, every, 2 every, ... (ncp x n x N)
+  double *cp_c = nullptr;   // the means entering those steps (ncp x N x 3)
+  double *uT = nullptr;     // u after the last step (n x N)
+  double *seg_u = nullptr;  // recomputed states of one segment ((every + 1) x n x N)
+  double *seg_c = nullptr;  // c^t of the segment's steps (every x N x 3)
+  double *seg_M = nullptr;  // masses M^t of the segment's steps (every x N)
+  double *g = nullptr, *g2 = nullptr;  // dL/du (n x N)
+  double *gm = nullptr;     // dL/dm1 (RGB), dL/dm2 per node (n x 4)
+  double *part = nullptr, *tot = nullptr, *scal = nullptr;
+  Solve sv;                 // FP64 tangent-form solve
+  std::vector<void *> allocs;
+};
+
 struct ac_ctx {
   ac_params p{};
   int N = 0;
@@ -164,6 +182,8 @@ struct ac_ctx {
   void *img = nullptr;  // device copy of a host image (allocated on demand)
   size_t img_bytes = 0;
   __nv_bfloat16 *img16 = nullptr;  // AC_MIXED: the image stored in bfloat16
+  double *img64 = nullptr;         // the image as the moments used it, FP64 (for the adjoint)
+  AdjState adj;
   double *h_scalars = nullptr;     // pinned: rho, energy
   bool have_image = false, have_rhs = false;
   std::vector<void *> allocs;
@@ -505,6 +525,17 @@ int copy_out(ac_ctx *ctx, void *dst, const void *src, size_t bytes, int is_devic
   return AC_OK;
 }
 
+template <typename TI>
+__global__ void k_img_f64(const TI *__restrict__ in, double *__restrict__ out, int64_t count) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < count) {
+    if constexpr (std::is_same<TI, __nv_bfloat16>::value)
+      out[k] = (double)__bfloat162float(in[k]);
+    else
+      out[k] = (double)in[k];
+  }
+}
+
 __global__ void k_to_bf16(const float *__restrict__ in, __nv_bfloat16 *__restrict__ out, int64_t count) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k < count) out[k] = __float2bfloat16_rn(in[k]);
@@ -643,10 +674,13 @@ void ac_destroy(ac_ctx *ctx) {
     cudaStreamSynchronize(ctx->s);
   else
     cudaDeviceSynchronize();
-  for (int a = 0; a < 2; ++a) {
-    for (int b = 0; b < 2; ++b) slot_release(ctx->sv.smooth_resid[a][b]);
-    slot_release(ctx->sv.correction[a]);
-  }
+  for (Solve *S : {&ctx->sv, &ctx->adj.sv})
+    for (int a = 0; a < 2; ++a) {
+      for (int b = 0; b < 2; ++b) slot_release(S->smooth_resid[a][b]);
+      slot_release(S->correction[a]);
+    }
+  for (void *p : ctx->adj.allocs) cudaFree(p);
+  if (ctx->img64) cudaFree(ctx->img64);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   for (void *p : ctx->allocs) cudaFree(p);
   if (ctx->img) cudaFree(ctx->img);
@@ -696,9 +730,27 @@ static int set_image_impl(ac_ctx *ctx, const void *rgb, int is_device, bool f64)
   } else {
     AC_RUN(AC_PROF_SETUP, ctx->ops->moments_f32((const float *)src, g, ctx->mom, ctx->s));
   }
+  if (!ctx->img64) {
+    cudaError_t e = cudaMalloc(&ctx->img64, (size_t)count * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ctx->img64 = nullptr;
+      return fail(AC_ERR_NOMEM, "cudaMalloc for the FP64 image: %s", cudaGetErrorString(e));
+    }
+  }
+  {
+    const unsigned nb = (unsigned)((count + 255) / 256);
+    if (mixed)
+      AC_RUN(AC_PROF_SETUP, (k_img_f64<__nv_bfloat16><<<nb, 256, 0, ctx->s>>>(ctx->img16, ctx->img64, count), 1));
+    else if (f64)
+      AC_RUN(AC_PROF_SETUP, (k_img_f64<double><<<nb, 256, 0, ctx->s>>>((const double *)src, ctx->img64, count), 1));
+    else
+      AC_RUN(AC_PROF_SETUP, (k_img_f64<float><<<nb, 256, 0, ctx->s>>>((const float *)src, ctx->img64, count), 1));
+  }
   AC_RUN(AC_PROF_SETUP, ctx->ops->init_random(ctx->u, ctx->n, ctx->p.seed, ctx->s));
   AC_CUDA(cudaMemsetAsync(ctx->c, 0, (size_t)3 * ctx->N * sizeof(double), ctx->s));
   if (!is_device) AC_CUDA(cudaStreamSynchronize(ctx->s));  // the host buffer may be reused after return
+  ctx->adj.ready = false;
   ctx->have_image = true;
   ctx->have_rhs = false;
   return AC_OK;
@@ -880,6 +932,183 @@ const char *ac_last_error(void) { return g_last_error.c_str(); }
 namespace ac {
 void set_last_error(const char *msg) { g_last_error = msg; }
 }  // namespace ac
+
+// ---------------------------------------------------------------------------
+// Adjoint (gradients of a loss on u after T steps).
+// ---------------------------------------------------------------------------
+namespace {
+
+int adj_alloc(ac_ctx *ctx, void **p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AC_ERR_NOMEM, "cudaMalloc(%zu) for the adjoint: %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->adj.allocs.push_back(*p);
+  return AC_OK;
+}
+
+#define ADJ_ALLOC(ptr, bytes)                                              \
+  do {                                                                     \
+    int rc_ = adj_alloc(ctx, reinterpret_cast<void **>(&(ptr)), (bytes));  \
+    if (rc_) return rc_;                                                   \
+  } while (0)
+
+void adj_release(ac_ctx *ctx) {
+  AdjState &A = ctx->adj;
+  for (int a = 0; a < 2; ++a) {
+    for (int b = 0; b < 2; ++b) slot_release(A.sv.smooth_resid[a][b]);
+    slot_release(A.sv.correction[a]);
+  }
+  for (void *p : A.allocs) cudaFree(p);
+  A = AdjState{};
+}
+
+// Buffers of the adjoint for T steps with checkpoints every `every` steps,
+// and the FP64 tangent-form solve on the primary solve's level hierarchy.
+int adj_setup(ac_ctx *ctx, int T, int every) {
+  cudaStreamSynchronize(ctx->s);
+  adj_release(ctx);
+  AdjState &A = ctx->adj;
+  const int N = ctx->N;
+  const size_t fN = (size_t)ctx->n * N * sizeof(double);
+  A.T = T;
+  A.every = every;
+  A.ncp = (T + every - 1) / every;
+  ADJ_ALLOC(A.cp_u, fN * A.ncp);
+  ADJ_ALLOC(A.cp_c, (size_t)A.ncp * N * 3 * sizeof(double));
+  ADJ_ALLOC(A.uT, fN);
+  ADJ_ALLOC(A.seg_u, fN * (every + 1));
+  ADJ_ALLOC(A.seg_c, (size_t)every * N * 3 * sizeof(double));
+  ADJ_ALLOC(A.seg_M, (size_t)every * N * sizeof(double));
+  ADJ_ALLOC(A.g, fN);
+  ADJ_ALLOC(A.g2, fN);
+  ADJ_ALLOC(A.gm, (size_t)ctx->n * 4 * sizeof(double));
+  const int blocks = (int)(((ctx->g0.W + 1 + 255) / 256) * (int64_t)(ctx->g0.H + 1));
+  ADJ_ALLOC(A.part, (size_t)blocks * (2 + 3 * N) * sizeof(double));
+  ADJ_ALLOC(A.tot, (size_t)(2 + 3 * N) * sizeof(double));
+  ADJ_ALLOC(A.scal, 2 * sizeof(double));
+  Solve &S = A.sv;
+  S.o = &ctx->ops->adjoint;
+  S.lv = ctx->sv.lv;
+  for (size_t k = 1; k < S.lv.size(); ++k) {
+    Level &L = S.lv[k];
+    ADJ_ALLOC(L.op, (size_t)L.n * 4 * N * sizeof(double));
+    ADJ_ALLOC(L.r, (size_t)L.n * N * sizeof(double));
+    ADJ_ALLOC(L.v, (size_t)L.n * N * sizeof(double));
+    ADJ_ALLOC(L.t, (size_t)L.n * N * sizeof(double));
+  }
+  S.depth = ctx->sv.depth;
+  S.tab0 = ctx->sv.tab0;
+  ADJ_ALLOC(S.x, fN);
+  ADJ_ALLOC(S.rhs, fN);
+  ADJ_ALLOC(S.ob, fN);
+  ADJ_ALLOC(S.rt, fN);
+  ADJ_ALLOC(S.d, fN);
+  ADJ_ALLOC(S.mask, (size_t)ctx->n);
+  return AC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ac_adjoint_forward(ac_ctx *ctx, int n_steps, int checkpoint_every) {
+  if (!ctx) return fail(AC_ERR_ARG, "ctx is NULL");
+  if (n_steps < 1 || checkpoint_every < 1 || checkpoint_every > n_steps)
+    return fail(AC_ERR_ARG, "need n_steps >= 1 and 1 <= checkpoint_every <= n_steps");
+  if (!ctx->have_image) return fail(AC_ERR_STATE, "ac_set_image must come first");
+  int rc = adj_setup(ctx, n_steps, checkpoint_every);
+  if (rc) return rc;
+  AdjState &A = ctx->adj;
+  const size_t fN = (size_t)ctx->n * ctx->N * sizeof(double), cN = (size_t)ctx->N * 3 * sizeof(double);
+  int status = AC_OK;
+  for (int t = 0; t < n_steps; ++t) {
+    if (t % checkpoint_every == 0) {
+      const int j = t / checkpoint_every;
+      AC_CUDA(cudaMemcpyAsync(A.cp_u + (size_t)j * ctx->n * ctx->N, ctx->u, fN, cudaMemcpyDeviceToDevice, ctx->s));
+      AC_CUDA(cudaMemcpyAsync(A.cp_c + (size_t)j * ctx->N * 3, ctx->c, cN, cudaMemcpyDeviceToDevice, ctx->s));
+    }
+    rc = ac_step(ctx, 1, nullptr);
+    if (rc == AC_ERR_NOT_CONVERGED)
+      status = rc;
+    else if (rc)
+      return rc;
+  }
+  AC_CUDA(cudaMemcpyAsync(A.uT, ctx->u, fN, cudaMemcpyDeviceToDevice, ctx->s));
+  A.ready = true;
+  return status;
+}
+
+int ac_adjoint_backward(ac_ctx *ctx, const double *grad_u, double *grad_lambda, double *grad_eps, double *grad_image,
+                        double *grad_u0) {
+  if (!ctx || !grad_u || !grad_lambda || !grad_eps || !grad_image) return fail(AC_ERR_ARG, "NULL argument");
+  AdjState &A = ctx->adj;
+  if (!A.ready) return fail(AC_ERR_STATE, "ac_adjoint_forward must come first");
+  const int N = ctx->N;
+  const int64_t nN = ctx->n * N;
+  const size_t fN = (size_t)nN * sizeof(double), cN = (size_t)N * 3 * sizeof(double);
+  const double tau = ctx->p.tau, eps = ctx->p.eps, lam = ctx->p.lambda, a1 = 1.0 + 2.0 * tau / eps;
+  const ac::Ops *o = ctx->ops;
+  AC_CUDA(cudaMemcpyAsync(A.g, grad_u, fN, cudaMemcpyDeviceToDevice, ctx->s));
+  AC_CUDA(cudaMemsetAsync(A.gm, 0, (size_t)ctx->n * 4 * sizeof(double), ctx->s));
+  AC_CUDA(cudaMemsetAsync(A.scal, 0, 2 * sizeof(double), ctx->s));
+  int status = AC_OK;
+  for (int j = A.ncp - 1; j >= 0; --j) {
+    const int t0 = j * A.every, t1 = std::min(t0 + A.every, A.T), len = t1 - t0;
+    // recompute the segment's states from its checkpoint (deterministic: the
+    // same arithmetic as the forward)
+    AC_CUDA(cudaMemcpyAsync(ctx->u, A.cp_u + (size_t)j * nN, fN, cudaMemcpyDeviceToDevice, ctx->s));
+    AC_CUDA(cudaMemcpyAsync(ctx->c, A.cp_c + (size_t)j * N * 3, cN, cudaMemcpyDeviceToDevice, ctx->s));
+    AC_CUDA(cudaMemcpyAsync(A.seg_u, ctx->u, fN, cudaMemcpyDeviceToDevice, ctx->s));
+    for (int k = 0; k < len; ++k) {
+      int rc = ac_step(ctx, 1, nullptr);
+      if (rc && rc != AC_ERR_NOT_CONVERGED) return rc;
+      AC_CUDA(cudaMemcpyAsync(A.seg_u + (size_t)(k + 1) * nN, ctx->u, fN, cudaMemcpyDeviceToDevice, ctx->s));
+      AC_CUDA(cudaMemcpyAsync(A.seg_c + (size_t)k * N * 3, ctx->c, cN, cudaMemcpyDeviceToDevice, ctx->s));
+      AC_CUDA(cudaMemcpyAsync(A.seg_M + (size_t)k * N, ctx->tot, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                              ctx->s));
+    }
+    for (int k = len - 1; k >= 0; --k) {
+      const double *u = A.seg_u + (size_t)k * nN, *up = A.seg_u + (size_t)(k + 1) * nN;
+      const double *c = A.seg_c + (size_t)k * N * 3, *M = A.seg_M + (size_t)k * N;
+      Solve &S = A.sv;
+      AC_RUN(AC_PROF_SETUP, o->adj_prepare(up, A.g, ctx->n, (double *)S.ob, (double *)S.rhs, ctx->s));
+      AC_CUDA(cudaMemsetAsync(S.x, 0, fN, ctx->s));
+      AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
+      AC_RUN(AC_PROF_SETUP, o->absmax((const double *)S.rhs, nN, ctx->rho, ctx->s));
+      double gmax = 0;
+      int rc = read_rho(ctx, &gmax);
+      if (rc) return rc;
+      if (gmax > 0) {
+        int cyc = 0;
+        double rho = 0;
+        int64_t sw = 0;
+        rc = solve_mg(ctx, S, 1e-13 * gmax, ctx->p.max_cycles, &cyc, &rho, &sw);
+        if (rc == AC_ERR_NOT_CONVERGED)
+          status = rc;
+        else if (rc)
+          return rc;
+      }
+      const double *w = (const double *)S.x;
+      AC_RUN(AC_PROF_SETUP, o->adj_accum(w, u, up, ctx->mom, c, ctx->g0, tau, eps, lam, A.gm, A.part, A.tot, A.scal,
+                                         ctx->s));
+      AC_RUN(AC_PROF_SETUP, o->adj_back(w, u, ctx->mom, c, A.tot, M, ctx->g0, a1, A.g2, A.gm, ctx->s));
+      std::swap(A.g, A.g2);
+    }
+  }
+  if (grad_u0) AC_CUDA(cudaMemcpyAsync(grad_u0, A.g, fN, cudaMemcpyDeviceToDevice, ctx->s));
+  AC_RUN(AC_PROF_SETUP, o->adj_image(A.gm, ctx->img64, ctx->g0, grad_image, ctx->s));
+  AC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 2, A.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+  AC_CUDA(cudaMemcpyAsync(ctx->u, A.uT, fN, cudaMemcpyDeviceToDevice, ctx->s));  // leave u = u^T
+  AC_CUDA(cudaStreamSynchronize(ctx->s));
+  *grad_lambda = ctx->h_scalars[2];
+  *grad_eps = ctx->h_scalars[3];
+  if (status) fail(status, "an adjoint solve did not reach its tolerance");
+  return status;
+}
+
+}  // extern "C"
 
 // ---------------------------------------------------------------------------
 // Batches of independent images (uneven sizes and phase counts).

@@ -131,58 +131,80 @@ __device__ __forceinline__ T rcp_small(int k) {
        : k == 5 ? T(0.2) : k == 6 ? T(1.0 / 6.0) : k == 7 ? T(1.0 / 7.0) : T(0.125);
 }
 
-// Euclidean projection onto a shifted, scaled simplex, in place, in registers:
-//   direct form  (SH = false): x_i >= 0,      sum_i x_i = 1  (the Gibbs simplex)
-//   shifted form (SH = true):  x_i >= -ob_i,  sum_i x_i = 0  (corrections delta
-//                              with u + delta on the simplex, ob = u)
-// The kept set starts full; theta = (sum of kept z + sum of dropped bounds -
-// total)/|kept|; components with z_i - theta at or below their bound leave the
-// set; repeat until none leaves (at most N passes).  This is the
-// clamp-and-redistribute loop of Sec. 3.3 written with the threshold theta
+// Constraint forms of a multigrid solve.
+enum Form { kDirect = 0, kShifted = 1, kTangent = 2 };
+
+// Nodal projection of the solve's form, in place, in registers:
+//   kDirect  : Euclidean projection onto x_i >= 0, sum_i x_i = 1 (the Gibbs simplex)
+//   kShifted : onto x_i >= -ob_i, sum_i x_i = 0 (corrections delta with u + delta
+//              on the simplex, ob = u)
+//   kTangent : orthogonal projection onto the tangent space of a frozen active
+//              set, ob_i = 1 for the free phases (at least two) and 0 otherwise:
+//              x_i = z_i - mean_free(z) on the free phases, 0 elsewhere
+// For the first two the kept set starts full; theta = (sum of kept z + sum of
+// dropped bounds - total)/|kept|; components with z_i - theta at or below their
+// bound leave the set; repeat until none leaves (at most N passes).  This is
+// the clamp-and-redistribute loop of Sec. 3.3 written with the threshold theta
 // (Michelot's form of the same iteration).  In the shifted form the result is
 // computed as a difference from the bound, so it keeps the relative precision
 // of the correction itself.
-template <typename T, int N, bool SH>
+template <typename T, int N, int FORM>
 __device__ __forceinline__ void proj_box(T (&z)[N], const T (&ob)[N]) {
-  const T total = SH ? T(0) : T(1);
-  unsigned keep = (1u << N) - 1u;
-  T s = T(0);
-#pragma unroll
-  for (int i = 0; i < N; ++i) s += z[i];
-  T theta = (s - total) * rcp_small<T>(N);
-#pragma unroll 1
-  for (int pass = 1; pass < N; ++pass) {
-    unsigned drop = 0;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const T lo = SH ? -ob[i] : T(0);
-      if (((keep >> i) & 1u) && z[i] - theta <= lo) drop |= 1u << i;
-    }
-    if (!drop) break;
-    keep &= ~drop;
-    s = T(0);
-    T L = T(0);
+  if constexpr (FORM == kTangent) {
+    T s = T(0);
     int k = 0;
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      if ((keep >> i) & 1u) {
+    for (int i = 0; i < N; ++i)
+      if (ob[i] != T(0)) {
         s += z[i];
         ++k;
-      } else if (SH) {
-        L -= ob[i];
       }
-    }
-    theta = (s + L - total) * rcp_small<T>(k);
-  }
+    const T mean = k >= 2 ? s * rcp_small<T>(k) : T(0);
 #pragma unroll
-  for (int i = 0; i < N; ++i) z[i] = ((keep >> i) & 1u) ? z[i] - theta : (SH ? -ob[i] : T(0));
+    for (int i = 0; i < N; ++i) z[i] = (k >= 2 && ob[i] != T(0)) ? z[i] - mean : T(0);
+    return;
+  } else {
+    constexpr bool SH = FORM == kShifted;
+    const T total = SH ? T(0) : T(1);
+    unsigned keep = (1u << N) - 1u;
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) s += z[i];
+    T theta = (s - total) * rcp_small<T>(N);
+#pragma unroll 1
+    for (int pass = 1; pass < N; ++pass) {
+      unsigned drop = 0;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const T lo = SH ? -ob[i] : T(0);
+        if (((keep >> i) & 1u) && z[i] - theta <= lo) drop |= 1u << i;
+      }
+      if (!drop) break;
+      keep &= ~drop;
+      s = T(0);
+      T L = T(0);
+      int k = 0;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        if ((keep >> i) & 1u) {
+          s += z[i];
+          ++k;
+        } else if (SH) {
+          L -= ob[i];
+        }
+      }
+      theta = (s + L - total) * rcp_small<T>(k);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) z[i] = ((keep >> i) & 1u) ? z[i] - theta : (SH ? -ob[i] : T(0));
+  }
 }
 
 // Projection onto the Gibbs simplex (direct form).
 template <typename T, int N>
 __device__ __forceinline__ void proj_simplex(T (&y)[N]) {
   const T none[N] = {};
-  proj_box<T, N, false>(y, none);
+  proj_box<T, N, kDirect>(y, none);
 }
 
 // Weighted sum of the four axis neighbours' values, acc = sum_m w_nm u_m.

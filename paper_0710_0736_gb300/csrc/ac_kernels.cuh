@@ -1,13 +1,15 @@
 // ac_kernels.cuh -- the sm_103a kernels of libac, templated on the phase
-// count N, the scalar type T of a multigrid solve and its constraint form SH
-// (see proj_box).  Instantiated once per N in ac_inst_n<N>.cu; the host driver
-// (ac_api.cu) calls them through the Ops table of ac_ops.h.
+// count N, the scalar type T of a multigrid solve and its constraint form
+// FORM (see proj_box).  Instantiated once per N in ac_inst_n<N>.cu; the host
+// driver (ac_api.cu) calls them through the Ops table of ac_ops.h.
 //
-// Two solves share these kernels:
-//   FP64 form : T = double, SH = false, unknown x = u, right-hand side b.
-//   mixed form: T = float,  SH = true,  unknown x = delta (a correction of the
+// Three solves share these kernels:
+//   FP64 form : T = double, kDirect,  unknown x = u, right-hand side b.
+//   mixed form: T = float,  kShifted, unknown x = delta (a correction of the
 //               FP64 state u), right-hand side r = b - S u (computed in FP64),
 //               obstacle ob = u rounded to float (delta_i >= -u_i, sum 0).
+//   adjoint   : T = double, kTangent, unknown x = w, right-hand side Pi g,
+//               ob = the frozen free set of u^{t+1} (1/0 per phase).
 //
 // Data layout in HBM:
 //   fine level (node-major, phase innermost, n x N): x, rhs, ob, rt, d;
@@ -289,13 +291,13 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
       float zf[N];
 #pragma unroll
       for (int i = 0; i < N; ++i) zf[i] = (float)z[i];
-      proj_box<float, N, true>(zf, uf);
+      proj_box<float, N, kShifted>(zf, uf);
       float ef = 0.f;
 #pragma unroll
       for (int i = 0; i < N; ++i) ef = nanmax<float>(ef, fabsf(zf[i]));
       e = (double)ef;
     } else {
-      proj_box<double, N, true>(z, uk);
+      proj_box<double, N, kShifted>(z, uk);
 #pragma unroll
       for (int i = 0; i < N; ++i) e = nanmax<double>(e, fabs(z[i]));
     }
@@ -329,7 +331,7 @@ __global__ void k_outer_update(double *__restrict__ u, const float *__restrict__
 // correction) the neighbours are read as x + omega d: that is exactly the
 // pending update x += omega d, because this pass overwrites its own colour
 // and the next pass overwrites the other one without reading old values.
-template <typename T, int N, bool SH>
+template <typename T, int N, int FORM>
 __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const T *__restrict__ rhs,
                                                         const T *__restrict__ ob, const T *__restrict__ corr,
                                                         const double *__restrict__ omega, Geo g, int color) {
@@ -349,12 +351,12 @@ __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const
     }
   }
   ldn<T, N>(rhs + n * N, bk);
-  if constexpr (SH) ldn<T, N>(ob + n * N, o);
+  if constexpr (FORM != kDirect) ldn<T, N>(ob + n * N, o);
   const int cls = node_class(g, xx, y);
   const T te = (T)g.te, invD = (T)g.invD[cls];
 #pragma unroll
   for (int i = 0; i < N; ++i) acc[i] = (bk[i] + te * acc[i]) * invD;
-  proj_box<T, N, SH>(acc, o);
+  proj_box<T, N, FORM>(acc, o);
   stn<T, N>(x + n * N, acc);
 }
 
@@ -366,7 +368,7 @@ __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const
 // A node at a vertex of the simplex has no free phase.  rt and mask may be
 // null (residual only).
 // ---------------------------------------------------------------------------
-template <typename T, int N, bool SH>
+template <typename T, int N, int FORM>
 __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, const T *__restrict__ rhs,
                                                        const T *__restrict__ ob, Geo g, T *__restrict__ rt,
                                                        uint8_t *__restrict__ mask, double *__restrict__ rho) {
@@ -379,7 +381,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
     nbr_sum<T, N>(x, g, xx, y, acc);
     ldn<T, N>(x + n * N, xk);
     ldn<T, N>(rhs + n * N, bk);
-    if constexpr (SH) ldn<T, N>(ob + n * N, o);
+    if constexpr (FORM != kDirect) ldn<T, N>(ob + n * N, o);
     const int cls = node_class(g, xx, y);
     const T D = (T)g.D[cls], invD = (T)g.invD[cls], te = (T)g.te;
 #pragma unroll
@@ -387,15 +389,16 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
       r[i] = bk[i] + te * acc[i] - D * xk[i];
       acc[i] = (bk[i] + te * acc[i]) * invD;
     }
-    proj_box<T, N, SH>(acc, o);
+    proj_box<T, N, FORM>(acc, o);
     int cnt = 0;
     unsigned pos = 0;
     T et = T(0);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       et = nanmax<T>(et, fabs(xk[i] - acc[i]));
-      const T lo = SH ? -o[i] : T(0);
-      if (xk[i] > lo) {
+      // free: above the bound (direct, shifted), or in the frozen set (tangent)
+      const bool fr = FORM == kTangent ? o[i] != T(0) : xk[i] > (FORM == kShifted ? -o[i] : T(0));
+      if (fr) {
         pos |= 1u << i;
         ++cnt;
       }
@@ -720,7 +723,7 @@ __global__ void k_prolong_add(const T *__restrict__ vc, Geo gf, Geo gc, T *__res
 // d'Sd; k_ls_finish computes omega; the next smoothing pass applies
 // x += omega d (see k_smooth_fine).
 // ---------------------------------------------------------------------------
-template <typename T, int N, bool SH>
+template <typename T, int N, int FORM>
 __global__ void __launch_bounds__(kBlock) k_ls_dir(const T *__restrict__ x, const T *__restrict__ ob,
                                                    const T *__restrict__ rt, const T *__restrict__ v1,
                                                    const uint8_t *__restrict__ mask, Geo gf, Geo gc,
@@ -744,10 +747,10 @@ __global__ void __launch_bounds__(kBlock) k_ls_dir(const T *__restrict__ x, cons
         }
       const T mean = s * rcp_small<T>(cnt);
       ldn<T, N>(x + n * N, xk);
-      if constexpr (SH) ldn<T, N>(ob + n * N, o);
+      if constexpr (FORM != kDirect) ldn<T, N>(ob + n * N, o);
 #pragma unroll
       for (int i = 0; i < N; ++i) w[i] = xk[i] + (((fr >> i) & 1u) ? w[i] - mean : T(0));
-      proj_box<T, N, SH>(w, o);
+      proj_box<T, N, FORM>(w, o);
       ldn<T, N>(rt + n * N, r);
       T loc = T(0);
 #pragma unroll
@@ -789,6 +792,160 @@ static __global__ void k_ls_finish(const double *__restrict__ tot, double *__res
   double w = 0.0;
   if (dsd > 0.0 && rd > 0.0) w = fmin(1.0, rd / dsd);
   *omega = w;
+}
+
+// ---------------------------------------------------------------------------
+// a13: adjoint of a time step (the step map differentiated with the active
+// set of u^{t+1} frozen; see ac_adjoint_backward).  With w the solution of
+// (Pi S Pi) w = Pi g in the tangent space V of u^{t+1}: dL/db = w and
+// dL/dS = -w u^{t+1}'.  FP64 throughout.
+// ---------------------------------------------------------------------------
+
+// Frozen free set of u^{t+1} as 1/0 per phase (free: u > 0 at a node with at
+// least two such phases) and the right-hand side Pi g.
+template <int N>
+__global__ void k_adj_prepare(const double *__restrict__ up, const double *__restrict__ g, int64_t n,
+                              double *__restrict__ freeset, double *__restrict__ rhs) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double uk[N], gk[N], f[N];
+  ldn<double, N>(up + k * N, uk);
+  ldn<double, N>(g + k * N, gk);
+  int cnt = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) cnt += uk[i] > 0.0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) f[i] = (cnt >= 2 && uk[i] > 0.0) ? 1.0 : 0.0;
+  proj_box<double, N, kTangent>(gk, f);
+  stn<double, N>(freeset + k * N, f);
+  stn<double, N>(rhs + k * N, gk);
+}
+
+// Per-node parts of the parameter gradients, block partials of
+//   [0] dL/dlambda = sum w . (-tau f)
+//   [1] dL/deps    = sum w . m0 u^t (-2 tau/eps^2) - tau sum w . A u^{t+1}
+//   [2 + 3i + ch]  G_i = dL/dc_i = 2 tau lambda sum w_i (m1 - c_i m0)
+// and the moment gradients gm (dL/dm1 RGB, dL/dm2) accumulated in place:
+//   dL/dm2 += -tau lambda sum_i w_i,  dL/dm1 += 2 tau lambda sum_i w_i c_i.
+template <int N>
+__global__ void __launch_bounds__(kBlock) k_adj_accum(const double *__restrict__ w, const double *__restrict__ u,
+                                                      const double *__restrict__ up, const double *__restrict__ mom,
+                                                      const double *__restrict__ c, Geo g, double tau, double eps,
+                                                      double lam, double *__restrict__ gm, double *__restrict__ part) {
+  double acc[2 + 3 * N];
+#pragma unroll
+  for (int k = 0; k < 2 + 3 * N; ++k) acc[k] = 0.0;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x <= g.W) {
+    const int64_t n = (int64_t)y * g.Wn + x;
+    const double m0 = g.m0[node_class(g, x, y)];
+    const double4 m = ld_mom(mom + n * 4);
+    double wk[N], uk[N], upk[N], nb[N];
+    ldn<double, N>(w + n * N, wk);
+    ldn<double, N>(u + n * N, uk);
+    ldn<double, N>(up + n * N, upk);
+    nbr_sum<double, N>(up, g, x, y, nb);
+    const Weights wt = edge_weights(g, x, y);
+    const double wsum = (double)wt.e + (double)wt.w + (double)wt.n + (double)wt.s;
+    double sw = 0.0, swc[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const double c0 = c[i * 3], c1 = c[i * 3 + 1], c2 = c[i * 3 + 2];
+      const double f = m.w - 2.0 * (c0 * m.x + c1 * m.y + c2 * m.z) + (c0 * c0 + c1 * c1 + c2 * c2) * m0;
+      acc[0] += wk[i] * (-tau * f);
+      acc[1] += wk[i] * m0 * uk[i] * (-2.0 * tau / (eps * eps)) - tau * wk[i] * (wsum * upk[i] - nb[i]);
+      acc[2 + 3 * i + 0] += 2.0 * tau * lam * wk[i] * (m.x - c0 * m0);
+      acc[2 + 3 * i + 1] += 2.0 * tau * lam * wk[i] * (m.y - c1 * m0);
+      acc[2 + 3 * i + 2] += 2.0 * tau * lam * wk[i] * (m.z - c2 * m0);
+      sw += wk[i];
+      swc[0] += wk[i] * c0;
+      swc[1] += wk[i] * c1;
+      swc[2] += wk[i] * c2;
+    }
+    double *gk = gm + n * 4;
+    gk[0] += 2.0 * tau * lam * swc[0];
+    gk[1] += 2.0 * tau * lam * swc[1];
+    gk[2] += 2.0 * tau * lam * swc[2];
+    gk[3] += -tau * lam * sw;
+  }
+  block_sum_store<2 + 3 * N>(acc, part + (int64_t)(blockIdx.y * gridDim.x + blockIdx.x) * (2 + 3 * N));
+}
+
+// dL/du^t = m0 a1 w + sum_ch G_i,ch (m1_ch - c_i,ch m0) / M_i, and
+// dL/dm1 += sum_i G_i u^t_i / M_i (c_i = s_i/M_i); phases of zero mass kept
+// their previous mean and contribute no c-term.  G at tot[2 + 3i + ch], M_i at
+// mass[i].
+template <int N>
+__global__ void k_adj_back(const double *__restrict__ w, const double *__restrict__ u, const double *__restrict__ mom,
+                           const double *__restrict__ c, const double *__restrict__ tot,
+                           const double *__restrict__ mass, Geo g, double a1, double *__restrict__ gout,
+                           double *__restrict__ gm) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x > g.W) return;
+  const int64_t n = (int64_t)y * g.Wn + x;
+  const double m0 = g.m0[node_class(g, x, y)];
+  const double4 m = ld_mom(mom + n * 4);
+  double wk[N], uk[N], o[N], add[3] = {0, 0, 0};
+  ldn<double, N>(w + n * N, wk);
+  ldn<double, N>(u + n * N, uk);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double v = m0 * a1 * wk[i];
+    const double M = mass[i];
+    if (M != 0.0) {
+      const double G0 = tot[2 + 3 * i], G1 = tot[3 + 3 * i], G2 = tot[4 + 3 * i];
+      v += (G0 * (m.x - c[i * 3] * m0) + G1 * (m.y - c[i * 3 + 1] * m0) + G2 * (m.z - c[i * 3 + 2] * m0)) / M;
+      add[0] += G0 * uk[i] / M;
+      add[1] += G1 * uk[i] / M;
+      add[2] += G2 * uk[i] / M;
+    }
+    o[i] = v;
+  }
+  stn<double, N>(gout + n * N, o);
+  double *gk = gm + n * 4;
+  gk[0] += add[0];
+  gk[1] += add[1];
+  gk[2] += add[2];
+}
+
+// Adjoint of the moment gather (Sec. 4.2): pixel p feeds nodes (px,py) and
+// (px+1,py+1) with weight 2/6 and (px+1,py), (px,py+1) with 1/6, through
+// m1 (I) and m2 (|I|^2): dL/dI_p = sum_n w_np (dL/dm1_n + 2 I_p dL/dm2_n).
+static __global__ void k_adj_image(const double *__restrict__ gm, const double *__restrict__ img, Geo g,
+                            double *__restrict__ gimg) {
+  const int px = blockIdx.x * blockDim.x + threadIdx.x, py = blockIdx.y;
+  if (px >= g.W) return;
+  const int64_t n00 = (int64_t)py * g.Wn + px;
+  const int64_t nodes[4] = {n00, n00 + 1, n00 + g.Wn, n00 + g.Wn + 1};
+  const double wts[4] = {2.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0, 2.0 / 6.0};
+  const double *I = img + ((int64_t)py * g.W + px) * 3;
+  double out[3] = {0, 0, 0};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double *gk = gm + nodes[q] * 4;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) out[ch] += wts[q] * (gk[ch] + 2.0 * I[ch] * gk[3]);
+  }
+  double *o = gimg + ((int64_t)py * g.W + px) * 3;
+  o[0] = out[0];
+  o[1] = out[1];
+  o[2] = out[2];
+}
+
+// acc[0..1] += tot[0..1] (the lambda and eps gradients of one step).
+static __global__ void k_adj_scalars(const double *__restrict__ tot, double *__restrict__ acc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    acc[0] += tot[0];
+    acc[1] += tot[1];
+  }
+}
+
+// max_k |v_k| over count values (atomic max of non-negative doubles).
+static __global__ void k_absmax(const double *__restrict__ v, int64_t count, double *__restrict__ out) {
+  double e = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)
+    e = nanmax<double>(e, fabs(v[k]));
+  block_max_atomic(e, out);
 }
 
 // ---------------------------------------------------------------------------

@@ -10,7 +10,7 @@ inline dim3 row_grid(int count_per_row, int rows, int block = kBlock) {
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
-template <typename T, int N, bool SH>
+template <typename T, int N, int FORM>
 struct SolverLaunch {
   // `sweeps` red-black sweeps in place, one launch per colour; the pending
   // coarse correction (corr != null) is applied inside the first launch.
@@ -19,13 +19,13 @@ struct SolverLaunch {
     const dim3 grid = row_grid((g.W + 2) / 2, g.H + 1);
     for (int k = 0; k < sweeps; ++k)
       for (int c = 0; c < 2; ++c)
-        k_smooth_fine<T, N, SH><<<grid, kBlock, 0, s>>>((T *)x, (const T *)rhs, (const T *)ob,
+        k_smooth_fine<T, N, FORM><<<grid, kBlock, 0, s>>>((T *)x, (const T *)rhs, (const T *)ob,
                                                         k == 0 && c == 0 ? (const T *)corr : nullptr, omega, g, c);
     return 2 * sweeps;
   }
   static int resid(const void *x, const void *rhs, const void *ob, const Geo &g, void *rt, uint8_t *mask,
                    double *rho, cudaStream_t s) {
-    k_fine_resid<T, N, SH><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>((const T *)x, (const T *)rhs,
+    k_fine_resid<T, N, FORM><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>((const T *)x, (const T *)rhs,
                                                                          (const T *)ob, g, (T *)rt, mask, rho);
     return 1;
   }
@@ -74,7 +74,7 @@ struct SolverLaunch {
                          cudaStream_t s) {
     const dim3 grid = row_grid(gf.W + 1, gf.H + 1);
     const int blocks = (int)(grid.x * grid.y);
-    k_ls_dir<T, N, SH><<<grid, kBlock, 0, s>>>((const T *)x, (const T *)ob, (const T *)rt, (const T *)v1, mask, gf,
+    k_ls_dir<T, N, FORM><<<grid, kBlock, 0, s>>>((const T *)x, (const T *)ob, (const T *)rt, (const T *)v1, mask, gf,
                                                gc, (T *)d, part);
     k_ls_curv<T, N><<<grid, kBlock, 0, s>>>((const T *)d, gf, part + blocks);
     k_colsum<<<1, kBlock, 0, s>>>(part, blocks, 1, tot);
@@ -139,6 +139,33 @@ struct Launch {
     k_labels<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, g, node_lab, pix_lab);
     return 1;
   }
+  static int adj_prepare(const double *up, const double *g, int64_t n, double *freeset, double *rhs, cudaStream_t s) {
+    k_adj_prepare<N><<<blocks_for(n), kBlock, 0, s>>>(up, g, n, freeset, rhs);
+    return 1;
+  }
+  static int adj_accum(const double *w, const double *u, const double *up, const double *mom, const double *c,
+                       const Geo &g, double tau, double eps, double lam, double *gm, double *part, double *tot,
+                       double *scal, cudaStream_t s) {
+    const dim3 grid = row_grid(g.W + 1, g.H + 1);
+    const int blocks = (int)(grid.x * grid.y);
+    k_adj_accum<N><<<grid, kBlock, 0, s>>>(w, u, up, mom, c, g, tau, eps, lam, gm, part);
+    k_colsum<<<2 + 3 * N, kBlock, 0, s>>>(part, blocks, 2 + 3 * N, tot);
+    k_adj_scalars<<<1, 32, 0, s>>>(tot, scal);
+    return 3;
+  }
+  static int adj_back(const double *w, const double *u, const double *mom, const double *c, const double *tot,
+                      const double *mass, const Geo &g, double a1, double *gout, double *gm, cudaStream_t s) {
+    k_adj_back<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(w, u, mom, c, tot, mass, g, a1, gout, gm);
+    return 1;
+  }
+  static int adj_image(const double *gm, const double *img, const Geo &g, double *gimg, cudaStream_t s) {
+    k_adj_image<<<row_grid(g.W, g.H), kBlock, 0, s>>>(gm, img, g, gimg);
+    return 1;
+  }
+  static int absmax(const double *v, int64_t count, double *out, cudaStream_t s) {
+    k_absmax<<<kMaxPartBlocks, kBlock, 0, s>>>(v, count, out);
+    return 1;
+  }
   static int project(const double *y, double *x, int64_t count, cudaStream_t s) {
     if (count <= 0) return 0;
     k_project<N><<<blocks_for(count), kBlock, 0, s>>>(y, x, count);
@@ -155,8 +182,14 @@ struct Launch {
                           outer_update,
                           labels,
                           project,
-                          SolverLaunch<double, N, false>::table(),
-                          SolverLaunch<float, N, true>::table()};
+                          SolverLaunch<double, N, kDirect>::table(),
+                          SolverLaunch<float, N, kShifted>::table(),
+                          SolverLaunch<double, N, kTangent>::table(),
+                          adj_prepare,
+                          adj_accum,
+                          adj_back,
+                          adj_image,
+                          absmax};
     return &t;
   }
 };

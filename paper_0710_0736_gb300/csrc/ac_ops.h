@@ -54,8 +54,19 @@ struct Ops {
   int (*outer_update)(double *u, const float *delta, int64_t n, cudaStream_t s);
   int (*labels)(const double *u, const Geo &g, int8_t *node_lab, int8_t *pix_lab, cudaStream_t s);
   int (*project)(const double *y, double *x, int64_t count, cudaStream_t s);
-  SolverOps fp64;   // T = double, direct form
-  SolverOps mixed;  // T = float, shifted form
+  SolverOps fp64;     // T = double, direct form
+  SolverOps mixed;    // T = float, shifted form
+  SolverOps adjoint;  // T = double, tangent form (frozen free set)
+  // adjoint of a time step
+  int (*adj_prepare)(const double *up, const double *g, int64_t n, double *freeset, double *rhs, cudaStream_t s);
+  // part: (blocks of the level) x (2 + 3N), tot: 2 + 3N, scal[0..1] += lambda/eps gradients
+  int (*adj_accum)(const double *w, const double *u, const double *up, const double *mom, const double *c,
+                   const Geo &g, double tau, double eps, double lam, double *gm, double *part, double *tot,
+                   double *scal, cudaStream_t s);
+  int (*adj_back)(const double *w, const double *u, const double *mom, const double *c, const double *tot,
+                  const double *mass, const Geo &g, double a1, double *gout, double *gm, cudaStream_t s);
+  int (*adj_image)(const double *gm, const double *img, const Geo &g, double *gimg, cudaStream_t s);
+  int (*absmax)(const double *v, int64_t count, double *out, cudaStream_t s);
 };
 
 const Ops *ops_n2();

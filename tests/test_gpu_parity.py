@@ -450,3 +450,126 @@ def test_batch_autotuner(ac):
         rhs = oracle.rhs(u_prev[k], m, c, W, H, 2.0, 1.0, 4.0)
         assert oracle.natural_residual(u1, rhs, W, H, 2.0, 4.0) <= 2e-8
     b.close()
+
+
+# --------------------------------------------------------------------------
+# a13: adjoint
+# --------------------------------------------------------------------------
+
+def _adj_problem(seed, W, H, N, n_disk=3):
+    img = synth.shapes_image(seed, W, H, n_rect=1, n_disk=n_disk, rect_side=(2, max(2, W // 3)),
+                             disk_r=(1.5, max(2.0, W / 5)), sigma=0.08).astype(np.float64)
+    u0 = synth.dirichlet_init(seed + 1, (W + 1) * (H + 1), N)
+    target = synth.voronoi_labels(seed + 2, W + 1, H + 1, n_seeds=6, n_labels=N)
+    return img, u0, target
+
+
+def _gpu_grads(ac, img, u0, target, eps, lam, tau, T, every, tol, precision):
+    import torch
+    from paper_0710_0736_gb300.adjoint import SegmentationSteps, misfit_loss
+    image = torch.tensor(img, device="cuda", requires_grad=True)
+    lam_t = torch.tensor(lam, dtype=torch.float64, device="cuda", requires_grad=True)
+    eps_t = torch.tensor(eps, dtype=torch.float64, device="cuda", requires_grad=True)
+    u0_t = torch.tensor(u0, device="cuda", requires_grad=True)
+    uT = SegmentationSteps.apply(image, lam_t, eps_t, u0_t, tau, T, every, tol, precision)
+    m0 = torch.tensor(oracle.moments(img)[:, 0], device="cuda")
+    L = misfit_loss(uT, m0, torch.tensor(target, device="cuda"))
+    L.backward()
+    return (float(L), float(lam_t.grad), float(eps_t.grad), image.grad.cpu().numpy(), u0_t.grad.cpu().numpy())
+
+
+def _gpu_loss(ac, img, u0, target, eps, lam, tau, T, tol, precision):
+    H, W, _ = img.shape
+    seg = ac.Segmenter(W, H, u0.shape[1], eps, lam, tau, tol=tol, precision=precision, max_cycles=2000)
+    seg.set_image(img.astype(np.float32) if precision == ac.AC_MIXED else img)
+    seg.set_phase(u0)
+    seg.step(T)
+    L, _ = oracle.misfit_loss(seg.phase(), oracle.moments(img)[:, 0], target)
+    seg.close()
+    return L
+
+
+def test_adjoint_matches_oracle_gradient(ac):
+    """FP64 forward and adjoint on the GPU against the FP64 oracle adjoint (on
+    the oracle's own forward states): 1e-6 relative."""
+    W, H, N, T, every = 24, 16, 3, 6, 2
+    eps, lam, tau = 2.0, 1.0, 4.0
+    img, u0, target = _adj_problem(0, W, H, N)
+    L, gl, ge, gimg, gu0 = _gpu_grads(ac, img, u0, target, eps, lam, tau, T, every, 1e-14, ac.AC_FP64)
+    states = oracle.forward_states(img, u0, eps, lam, tau, T)
+    m0 = oracle.moments(img)[:, 0]
+    L_ref, gT = oracle.misfit_loss(states[-1], m0, target)
+    rl, re_, rimg, ru0 = oracle.adjoint(img, states, eps, lam, tau, gT)
+    assert L == pytest.approx(L_ref, rel=1e-9)
+    assert gl == pytest.approx(rl, rel=1e-6, abs=1e-9)
+    assert ge == pytest.approx(re_, rel=1e-6, abs=1e-9)
+    assert np.abs(gimg - rimg).max() <= 1e-6 * np.abs(rimg).max()
+    assert np.abs(gu0 - ru0).max() <= 1e-6 * np.abs(ru0).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_adjoint_matches_finite_differences(ac, precision):
+    """Central differences (h = 1e-6) of the GPU forward itself, solved to
+    1e-14 (FP64) / 1e-12 (mixed): lambda, eps and (FP64) image directions.
+    In the mixed form the image is rounded to bfloat16, so its image gradient
+    is compared with the FP64 adjoint on the rounded image instead."""
+    W, H, N, T, every = 32, 24, 4, 8, 3
+    eps, lam, tau = 2.0, 1.0, 4.0
+    prec = ac.AC_MIXED if precision == "mixed" else ac.AC_FP64
+    tol = 1e-12 if precision == "mixed" else 1e-14
+    img, u0, target = _adj_problem(1, W, H, N)
+    if precision == "mixed":
+        img = synth.round_bf16(img.astype(np.float32)).astype(np.float64)
+    L, gl, ge, gimg, gu0 = _gpu_grads(ac, img, u0, target, eps, lam, tau, T, every, tol, prec)
+    h = 1e-6
+
+    def fd(f):
+        return (f(h) - f(-h)) / (2 * h)
+
+    rtol = 1e-6 if precision == "fp64" else 2e-5
+    assert gl == pytest.approx(fd(lambda d: _gpu_loss(ac, img, u0, target, eps, lam + d, tau, T, tol, prec)),
+                               rel=rtol, abs=1e-9)
+    assert ge == pytest.approx(fd(lambda d: _gpu_loss(ac, img, u0, target, eps + d, lam, tau, T, tol, prec)),
+                               rel=rtol, abs=1e-9)
+    rng = np.random.default_rng(2)
+    if precision == "fp64":
+        for _ in range(2):
+            v = rng.normal(size=img.shape)
+            assert (gimg * v).sum() == pytest.approx(
+                fd(lambda d: _gpu_loss(ac, img + d * v, u0, target, eps, lam, tau, T, tol, prec)), rel=1e-6)
+    else:
+        _, _, _, gimg64, _ = _gpu_grads(ac, img, u0, target, eps, lam, tau, T, every, 1e-14, ac.AC_FP64)
+        assert np.abs(gimg - gimg64).max() <= 1e-4 * np.abs(gimg64).max()
+    z = rng.normal(size=u0.shape)
+    z -= z.mean(1, keepdims=True)
+    assert (gu0 * z).sum() == pytest.approx(
+        fd(lambda d: _gpu_loss(ac, img, u0 + d * z, target, eps, lam, tau, T, tol, prec)), rel=rtol, abs=1e-9)
+
+
+def test_adjoint_full_size_c5(ac):
+    """The 512x512, N = 4, T = 64 workload with checkpoints every 8 steps:
+    lambda, eps and two image directions against central differences of the
+    GPU forward (relative 1e-5: the forward's 1e-13 solves are amplified over
+    64 steps)."""
+    cfg = synth.CONFIGS["c5_512_n4_adjoint"]
+    W = H = 512
+    N, eps, lam, tau, T = cfg["N"], cfg["eps"], cfg["lam"], cfg["tau"], 64
+    img = synth.config_image("c5_512_n4_adjoint", 0).astype(np.float64)
+    u0 = synth.dirichlet_init(1, (W + 1) * (H + 1), N)
+    target = synth.voronoi_labels(2, W + 1, H + 1, n_seeds=6, n_labels=4)
+    tol = 1e-13
+    L, gl, ge, gimg, gu0 = _gpu_grads(ac, img, u0, target, eps, lam, tau, T, 8, tol, ac.AC_FP64)
+    h = 1e-5
+
+    def fd(f):
+        return (f(h) - f(-h)) / (2 * h)
+
+    assert gl == pytest.approx(fd(lambda d: _gpu_loss(ac, img, u0, target, eps, lam + d, tau, T, tol, ac.AC_FP64)),
+                               rel=1e-5)
+    assert ge == pytest.approx(fd(lambda d: _gpu_loss(ac, img, u0, target, eps + d, lam, tau, T, tol, ac.AC_FP64)),
+                               rel=1e-5)
+    rng = np.random.default_rng(3)
+    for _ in range(2):
+        v = rng.normal(size=img.shape)
+        assert (gimg * v).sum() == pytest.approx(
+            fd(lambda d: _gpu_loss(ac, img + d * v, u0, target, eps, lam, tau, T, tol, ac.AC_FP64)), rel=1e-5)
