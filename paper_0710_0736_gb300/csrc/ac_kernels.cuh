@@ -248,7 +248,8 @@ __global__ void k_rhs(const double *__restrict__ u, const double *__restrict__ m
 // and obstacle of the FP32 correction solve) and the natural
 // residual max_n |P_G(u_n + z_n) - u_n|, z = r/S_nn, computed in FP64 as a
 // correction by the shifted projection.
-// k_outer_update: u <- P_G(u + delta) in FP64.
+// k_outer_update: u <- P_G(u + delta) in FP64 (components on their bound
+// exactly 0).
 // ---------------------------------------------------------------------------
 template <int N, bool RHO32>
 __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict__ u, const double *__restrict__ b, Geo g,
@@ -306,6 +307,10 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
   block_max_atomic(e, rho);
 }
 
+// A component the FP32 solve put on its bound (delta_i == -float(u_i)) is set
+// to exactly 0 -- u_i + delta_i would leave the rounding residue
+// u_i - float(u_i) -- and the projection then runs over the other components
+// only, so that exact zeros (the active set) are the same as in the FP64 form.
 template <int N>
 __global__ void k_outer_update(double *__restrict__ u, const float *__restrict__ delta, int64_t n) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -314,9 +319,46 @@ __global__ void k_outer_update(double *__restrict__ u, const float *__restrict__
   float dk[N];
   ldn_rw<double, N>(u + k * N, uk);
   ldn<float, N>(delta + k * N, dk);
+  unsigned keep = 0;
+  double s = 0.0;
+  int cnt = 0;
 #pragma unroll
-  for (int i = 0; i < N; ++i) uk[i] += (double)dk[i];
-  proj_simplex<double, N>(uk);
+  for (int i = 0; i < N; ++i) {
+    const bool on_bound = dk[i] == -(float)uk[i];
+    uk[i] = on_bound ? 0.0 : uk[i] + (double)dk[i];
+    if (!on_bound) {
+      keep |= 1u << i;
+      s += uk[i];
+      ++cnt;
+    }
+  }
+  if (cnt == 0) {  // cannot happen for a feasible correction; fall back to the full projection
+    proj_simplex<double, N>(uk);
+    stn<double, N>(u + k * N, uk);
+    return;
+  }
+  // Michelot's iteration over the kept components (target sum 1)
+  double theta = (s - 1.0) * rcp_small<double>(cnt);
+#pragma unroll 1
+  for (int pass = 1; pass < N; ++pass) {
+    unsigned drop = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (((keep >> i) & 1u) && uk[i] <= theta) drop |= 1u << i;
+    if (!drop || drop == keep) break;
+    keep &= ~drop;
+    s = 0.0;
+    cnt = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if ((keep >> i) & 1u) {
+        s += uk[i];
+        ++cnt;
+      }
+    theta = (s - 1.0) * rcp_small<double>(cnt);
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) uk[i] = ((keep >> i) & 1u) ? uk[i] - theta : 0.0;
   stn<double, N>(u + k * N, uk);
 }
 
