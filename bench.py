@@ -48,8 +48,11 @@ def parse():
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--crop", type=int, default=256, help="side of the image crop the CPU oracle times")
     ap.add_argument("--cpu-steps", type=int, default=3, help="oracle steps in the cpu_baseline sample")
-    ap.add_argument("--workload", choices=["single", "batch"], default="single",
-                    help="single: the 4096^2 N=8 image; batch: 256 uneven images (sizes 128^2..1024^2, N 2/4/6)")
+    ap.add_argument("--workload", choices=["single", "batch", "adjoint"], default="single",
+                    help="single: the 4096^2 N=8 image; batch: 256 uneven images (sizes 128^2..1024^2, N 2/4/6); "
+                         "adjoint: gradients through 64 steps of the 512^2 N=4 disks image")
+    ap.add_argument("--adj-steps", type=int, default=64, help="time steps differentiated (adjoint workload)")
+    ap.add_argument("--adj-every", type=int, default=8, help="checkpoint interval (adjoint workload)")
     ap.add_argument("--batch-images", type=int, default=256)
     ap.add_argument("--streams", type=int, default=16)
     ap.add_argument("--no-tune", action="store_true")
@@ -255,12 +258,116 @@ def run_batch(args):
     return 0
 
 
+def run_adjoint(args):
+    """Gradients through T = 64 time steps of the 512 x 512, N = 4 disks image
+    (12 disks, noise 0.08; eps 2, lambda 1, tau 4, each step solved to 1e-10)
+    of the misfit L = 1/2 sum Mhat |u^T - onehot(target)|^2 to a 6-seed Voronoi
+    target, with respect to lambda, eps, the image and u^0.  One "step" here
+    is one gradient evaluation: the forward with checkpoints every 8 steps
+    (ac_adjoint_forward), then the backward sweep (ac_adjoint_backward),
+    which recomputes each segment from its checkpoint.  value = gradient
+    evaluations per second."""
+    import torch
+    import oracle
+    from paper_0710_0736_gb300 import ac, synth
+    name = "c5_512_n4_adjoint"
+    cfg = dict(synth.CONFIGS[name])
+    W, H, N, T, every = cfg["W"], cfg["H"], cfg["N"], args.adj_steps, args.adj_every
+    tol = args.tol if args.tol is not None else cfg["tol"]
+    img = synth.config_image(name, 0).astype(np.float64)
+    u0 = synth.dirichlet_init(1, (W + 1) * (H + 1), N)
+    target = synth.voronoi_labels(2, W + 1, H + 1, n_seeds=6, n_labels=N)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", 0)
+    onehot = np.eye(N)[target.ravel().astype(int)]
+    m0 = None
+
+    def measure(precision, steps, warmup):
+        nonlocal m0
+        seg = ac.Segmenter(W, H, N, cfg["eps"], cfg["lam"], cfg["tau"], tol=tol, max_cycles=2000,
+                           precision=precision, stream=stream.cuda_stream)
+        if precision == ac.AC_MIXED:
+            seg.set_image(torch.tensor(img, dtype=torch.float32, device=dev))
+        else:
+            seg.set_image(torch.tensor(img, device=dev))
+        if m0 is None:
+            m0 = torch.tensor(seg.moments()[:, 0], device=dev)
+        u0_d = torch.tensor(u0, device=dev)
+        oh = torch.tensor(onehot, device=dev)
+        uT = torch.empty_like(u0_d)
+        g_img = torch.empty((H, W, 3), dtype=torch.float64, device=dev)
+        g_u0 = torch.empty_like(u0_d)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        t_fwd = t_bwd = 0.0
+        cycles = 0
+        for it in range(warmup + steps):
+            seg.set_phase(u0_d)
+            if it == warmup:
+                torch.cuda.synchronize()
+            evs[0].record(stream)
+            ac.ac_adjoint_forward(seg.ctx, T, every)
+            evs[1].record(stream)
+            ac.ac_get_phase(seg.ctx, uT, seg.n_nodes, N)
+            grad = m0[:, None] * (uT - oh)  # dL/du^T of the misfit
+            gl, ge = ac.ac_adjoint_backward(seg.ctx, grad.contiguous(), g_img, g_u0)
+            evs[2].record(stream)
+            torch.cuda.synchronize()
+            if it >= warmup:
+                t_fwd += evs[0].elapsed_time(evs[1])
+                t_bwd += evs[1].elapsed_time(evs[2])
+        seg.close()
+        return t_fwd / steps, t_bwd / steps, gl, ge
+
+    clocks = Clocks(0)
+    clocks.start()
+    fwd_ms, bwd_ms, gl, ge = measure(ac.AC_FP64, args.steps, args.warmup)
+    clk = clocks.stop()
+    # the mixed-precision forward (FP32 sweeps, FP64 defect correction) with the same FP64 adjoint
+    mfwd_ms, mbwd_ms, mgl, mge = measure(ac.AC_MIXED, max(1, args.steps // 2), args.warmup)
+    ms = fwd_ms + bwd_ms
+    value = 1e3 / ms
+
+    cpu = None
+    if not args.no_cpu:
+        crop, Tc = 128, 8
+        ic = img[:crop, :crop]
+        uc = synth.dirichlet_init(1, (crop + 1) ** 2, N)
+        tc = synth.voronoi_labels(2, crop + 1, crop + 1, n_seeds=6, n_labels=N)
+        t0 = time.perf_counter()
+        states = oracle.forward_states(ic, uc, cfg["eps"], cfg["lam"], cfg["tau"], Tc, tol=tol)
+        _, gT = oracle.misfit_loss(states[-1], oracle.moments(ic)[:, 0], tc)
+        oracle.adjoint(ic, states, cfg["eps"], cfg["lam"], cfg["tau"], gT, cg_rtol=1e-12)
+        sec = time.perf_counter() - t0
+        scale = ((W + 1) * (H + 1)) / (crop + 1) ** 2 * T / Tc
+        cpu = {"value": 1.0 / (sec * scale), "unit": "gradient evaluations/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle forward ({Tc} steps, SSC to {tol:g}) + FP64 adjoint (tangent CG to 1e-12) on "
+                         f"the {crop}x{crop} corner, {sec:.1f} s, scaled by nodes and steps x{scale:.0f}"}
+    line = {"metric": "adjoint gradient evaluations/s (64 steps, 512^2 N=4)", "value": value,
+            "unit": "gradient evaluations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{W}x{H} disks image (12 disks, noise 0.08), N={N}, eps={cfg['eps']}, "
+                                   f"lambda={cfg['lam']}, tau={cfg['tau']}, {T} steps to tol {tol:g}, "
+                                   f"checkpoints every {every}, misfit to a 6-seed Voronoi target",
+                       "l2": "no flush: 14 MB of checkpoints plus segment states; small case, L2-resident"},
+            "forward_ms": fwd_ms, "backward_ms": bwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
+            "grad_lambda": gl, "grad_eps": ge,
+            "mixed_forward": {"forward_ms": mfwd_ms, "backward_ms": mbwd_ms, "grad_lambda": mgl, "grad_eps": mge,
+                              "value": 1e3 / (mfwd_ms + mbwd_ms)},
+            "cpu_baseline": cpu, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     import torch
     import torch.distributed as dist
 

@@ -475,7 +475,7 @@ def _gpu_grads(ac, img, u0, target, eps, lam, tau, T, every, tol, precision):
     m0 = torch.tensor(oracle.moments(img)[:, 0], device="cuda")
     L = misfit_loss(uT, m0, torch.tensor(target, device="cuda"))
     L.backward()
-    return (float(L), float(lam_t.grad), float(eps_t.grad), image.grad.cpu().numpy(), u0_t.grad.cpu().numpy())
+    return (float(L.detach()), float(lam_t.grad), float(eps_t.grad), image.grad.cpu().numpy(), u0_t.grad.cpu().numpy())
 
 
 def _gpu_loss(ac, img, u0, target, eps, lam, tau, T, tol, precision):
@@ -555,18 +555,23 @@ def test_adjoint_mixed_forward(ac):
 
 def test_adjoint_full_size_c5(ac):
     """The 512x512, N = 4 workload (12 disks, noise 0.08, Voronoi target of 6
-    seeds) over 16 steps with checkpoints every 4: lambda, eps and two image
-    directions against central differences (h = 1e-7) of the GPU forward,
-    relative 1e-6.  (Over the full 64 steps the difference quotients of this
-    chaotic start wander by ~0.5% with h: the 1e-13 solves are amplified
-    ~1000x by the first steps; at 8 and 16 steps they agree to ~3e-8.)"""
+    seeds) over 16 steps with checkpoints every 4, every step solved to 1e-14,
+    against central differences (h = 1e-7) of the GPU forward.
+
+    Rounding noise of the forward, amplified by the first steps of a random
+    start, leaves ~5e-11 of noise in L, i.e. ~2.5e-4 in a difference quotient
+    at h = 1e-7; larger h meets kinks (active-set changes; h = 1e-6 is off by
+    1e-5 relative).  So lambda, eps and an image direction correlated with the
+    gradient's sign (directional derivative ~|g|_1) are held to 1e-6 relative,
+    and a random image direction (derivative ~|g|_2 ~ 300) to that noise floor.
+    Over the full 64 steps the quotients wander by ~0.5% with h."""
     W = H = 512
     cfg = synth.CONFIGS["c5_512_n4_adjoint"]
     N, eps, lam, tau, T = cfg["N"], cfg["eps"], cfg["lam"], cfg["tau"], 16
     img = synth.config_image("c5_512_n4_adjoint", 0).astype(np.float64)
     u0 = synth.dirichlet_init(1, (W + 1) * (H + 1), N)
     target = synth.voronoi_labels(2, W + 1, H + 1, n_seeds=6, n_labels=4)
-    tol = 1e-13
+    tol = 1e-14
     L, gl, ge, gimg, gu0 = _gpu_grads(ac, img, u0, target, eps, lam, tau, T, 4, tol, ac.AC_FP64)
     h = 1e-7
 
@@ -578,7 +583,9 @@ def test_adjoint_full_size_c5(ac):
     assert ge == pytest.approx(fd(lambda d: _gpu_loss(ac, img, u0, target, eps + d, lam, tau, T, tol, ac.AC_FP64)),
                                rel=1e-6)
     rng = np.random.default_rng(3)
-    for _ in range(2):
-        v = rng.normal(size=img.shape)
-        assert (gimg * v).sum() == pytest.approx(
-            fd(lambda d: _gpu_loss(ac, img + d * v, u0, target, eps, lam, tau, T, tol, ac.AC_FP64)), rel=1e-6)
+    v = np.sign(gimg) * rng.uniform(0.5, 1.5, size=img.shape)
+    assert (gimg * v).sum() == pytest.approx(
+        fd(lambda d: _gpu_loss(ac, img + d * v, u0, target, eps, lam, tau, T, tol, ac.AC_FP64)), rel=1e-6)
+    v = rng.normal(size=img.shape)
+    assert (gimg * v).sum() == pytest.approx(
+        fd(lambda d: _gpu_loss(ac, img + d * v, u0, target, eps, lam, tau, T, tol, ac.AC_FP64)), abs=1e-3)
