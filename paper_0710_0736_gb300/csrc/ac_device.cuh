@@ -200,6 +200,73 @@ __device__ __forceinline__ void proj_box(T (&z)[N], const T (&ob)[N]) {
   }
 }
 
+// Free set (bit i: component i above its bound) of the shifted-form
+// projection of z with bounds -ob, by the same iteration as proj_box; z and ob
+// are not changed.
+template <typename T, int N>
+__device__ __forceinline__ unsigned shifted_free_set(const T (&z)[N], const T (&ob)[N]) {
+  unsigned keep = (1u << N) - 1u;
+  T s = T(0);
+#pragma unroll
+  for (int i = 0; i < N; ++i) s += z[i];
+  T theta = s * rcp_small<T>(N);
+#pragma unroll 1
+  for (int pass = 1; pass < N; ++pass) {
+    unsigned drop = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (((keep >> i) & 1u) && z[i] - theta <= -ob[i]) drop |= 1u << i;
+    if (!drop || drop == keep) break;
+    keep &= ~drop;
+    s = T(0);
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      if ((keep >> i) & 1u) {
+        s += z[i];
+        ++k;
+      } else {
+        s -= ob[i];
+      }
+    }
+    theta = s * rcp_small<T>(k);
+  }
+  return keep;
+}
+
+// Shifted-form projection of z (bounds -ob, sum 0) in FP64 given a candidate
+// free set from a float pass: theta from that set, then the optimality
+// conditions (free components above their bound, the others at or below it)
+// are checked in FP64.  If they hold, z becomes the projection (the
+// conditions characterise it) and true is returned; otherwise z is unchanged
+// and false is returned.
+template <int N>
+__device__ __forceinline__ bool shifted_proj_on_set(double (&z)[N], const double (&ob)[N], unsigned keep) {
+  double s = 0.0, L = 0.0;
+  int k = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if ((keep >> i) & 1u) {
+      s += z[i];
+      ++k;
+    } else {
+      L -= ob[i];
+    }
+  }
+  if (k == 0) return false;
+  const double theta = (s + L) * rcp_small<double>(k);
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const bool above = z[i] - theta > -ob[i];
+    ok = ok && (above == (((keep >> i) & 1u) != 0u));
+  }
+  if (!ok) return false;
+#pragma unroll
+  for (int i = 0; i < N; ++i) z[i] = ((keep >> i) & 1u) ? z[i] - theta : -ob[i];
+  return true;
+}
+
 // Projection onto the Gibbs simplex (direct form).
 template <typename T, int N>
 __device__ __forceinline__ void proj_simplex(T (&y)[N]) {

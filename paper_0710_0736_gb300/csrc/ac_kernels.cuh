@@ -67,19 +67,30 @@ __device__ __forceinline__ void block_max_atomic(double e, double *rho) {
 }
 
 // Column sums of a rows x cols row-major matrix of block partials; one block
-// per column, fixed summation order (bit-reproducible for a fixed grid).
-static __global__ void k_colsum(const double *__restrict__ part, int rows, int cols, double *__restrict__ out) {
-  __shared__ double sm[kBlock];
-  const int c = blockIdx.x;
-  double s = 0.0;
-  for (int r = threadIdx.x; r < rows; r += blockDim.x) s += part[(int64_t)r * cols + c];
-  sm[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
-    __syncthreads();
+// per column (any blockDim that is a multiple of 32, <= 1024), four
+// independent accumulators per thread, fixed summation order (bit-reproducible
+// for a fixed grid and block size).
+static __global__ void __launch_bounds__(1024) k_colsum(const double *__restrict__ part, int rows, int cols,
+                                                        double *__restrict__ out) {
+  __shared__ double sm[32];
+  const int c = blockIdx.x, B = blockDim.x;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int r = threadIdx.x;
+  for (; r + 3 * B < rows; r += 4 * B) {
+    s0 += part[(int64_t)r * cols + c];
+    s1 += part[(int64_t)(r + B) * cols + c];
+    s2 += part[(int64_t)(r + 2 * B) * cols + c];
+    s3 += part[(int64_t)(r + 3 * B) * cols + c];
   }
-  if (threadIdx.x == 0) out[c] = sm[0];
+  for (; r < rows; r += B) s0 += part[(int64_t)r * cols + c];
+  double v = warp_sum((s0 + s1) + (s2 + s3));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = (int)threadIdx.x < (B >> 5) ? sm[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) out[c] = v;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -247,7 +258,8 @@ __global__ void k_rhs(const double *__restrict__ u, const double *__restrict__ m
 // and u rounded to float (the right-hand side
 // and obstacle of the FP32 correction solve) and the natural
 // residual max_n |P_G(u_n + z_n) - u_n|, z = r/S_nn, computed in FP64 as a
-// correction by the shifted projection.
+// correction by the shifted projection (free set found in float, theta and
+// the optimality conditions checked in FP64).
 // k_outer_update: u <- P_G(u + delta) in FP64 (components on their bound
 // exactly 0).
 // ---------------------------------------------------------------------------
@@ -298,7 +310,14 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
       for (int i = 0; i < N; ++i) ef = nanmax<float>(ef, fabsf(zf[i]));
       e = (double)ef;
     } else {
-      proj_box<double, N, kShifted>(z, uk);
+      // the free set from a float pass, then theta and the optimality
+      // conditions on that set in FP64 (one pass instead of the iteration);
+      // the full FP64 iteration only where the conditions fail (near ties)
+      float zf[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) zf[i] = (float)z[i];
+      const unsigned keep = shifted_free_set<float, N>(zf, uf);
+      if (!shifted_proj_on_set<N>(z, uk, keep)) proj_box<double, N, kShifted>(z, uk);
 #pragma unroll
       for (int i = 0; i < N; ++i) e = nanmax<double>(e, fabs(z[i]));
     }
@@ -524,11 +543,82 @@ __global__ void k_restrict(const T *__restrict__ t, Geo gf, Geo gc, T *__restric
 // phases free nowhere get 0; only phases free on part of it are summed here
 // (at most 35 products of dyadic weights with S entries).
 // ---------------------------------------------------------------------------
+// Interior coarse nodes (2 <= X <= Wc-2, 2 <= Y <= Hc-2): every fine node of
+// the 6x6 mask box is in range and every fine node a, b of the sums is an
+// interior node (S_aa = D[interior], S_ab = -tau eps on axis edges), so with
+// the loops unrolled the hat weights and offsets are compile-time constants.
+template <typename T, int N>
+__device__ __forceinline__ void galerkin0_interior(const uint8_t *__restrict__ mask, const Geo &gf, const Geo &gc,
+                                                   const double *tv, int X, int Y, T *__restrict__ op) {
+  constexpr int sx[7] = {0, 1, -1, 0, 0, 1, -1};
+  constexpr int sy[7] = {0, 0, 0, 1, -1, 1, -1};
+  constexpr int ox[5] = {0, 1, -1, 0, 0};
+  constexpr int oy[5] = {0, 0, 0, 1, -1};
+  constexpr int lx[4] = {0, 1, 0, 1};
+  constexpr int ly[4] = {0, 0, 1, 1};
+  // m[j][i]: mask of fine node (2X - 2 + i, 2Y - 2 + j)
+  unsigned m[6][6];
+  const uint8_t *row = mask + (int64_t)(2 * Y - 2) * gf.Wn + (2 * X - 2);
+#pragma unroll
+  for (int j = 0; j < 6; ++j)
+#pragma unroll
+    for (int i = 0; i < 6; ++i) m[j][i] = row[(int64_t)j * gf.Wn + i];
+  unsigned all = (1u << N) - 1u, any = 0u;
+#pragma unroll
+  for (int j = 0; j < 6; ++j)
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      all &= m[j][i];
+      any |= m[j][i];
+    }
+  const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), K = (int64_t)Y * gc.Wn + X;
+  const unsigned partial = any & ~all;
+  if (!partial) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+#pragma unroll
+      for (int i = 0; i < N; ++i) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? (T)tv[l] : T(0);
+    return;
+  }
+  const T Daa = (T)gf.D[4], Sab = -(T)gf.te;
+  T acc[4][N];
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[l][i] = T(0);
+#pragma unroll
+  for (int s = 0; s < 7; ++s) {
+    const T pa = s == 0 ? T(1) : T(0.5);
+    const unsigned ma = m[2 + sy[s]][2 + sx[s]] & partial;
+#pragma unroll
+    for (int o = 0; o < 5; ++o) {
+      const unsigned mm = ma & m[2 + sy[s] + oy[o]][2 + sx[s] + ox[o]];
+      const T sab = o == 0 ? Daa : Sab;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const T q = hat_weight_t<T>(sx[s] + ox[o] - 2 * lx[l], sy[s] + oy[o] - 2 * ly[l]);
+        if (q == T(0)) continue;
+        const T cf = pa * sab * q;
+#pragma unroll
+        for (int i = 0; i < N; ++i) acc[l][i] += ((mm >> i) & 1u) ? cf : T(0);
+      }
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int i = 0; i < N; ++i) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? (T)tv[l] : acc[l][i];
+}
+
 template <typename T, int N>
 __global__ void __launch_bounds__(kBlock) k_galerkin0(const uint8_t *__restrict__ mask, Geo gf, Geo gc,
                                                       Galerkin0Table tab, T *__restrict__ op) {
   const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
   if (X > gc.W) return;
+  if (X >= 2 && X <= gc.W - 2 && Y >= 2 && Y <= gc.H - 2) {
+    galerkin0_interior<T, N>(mask, gf, gc, tab.v[2 * 5 + 2], X, Y, op);
+    return;
+  }
   constexpr int sx[7] = {0, 1, -1, 0, 0, 1, -1};
   constexpr int sy[7] = {0, 0, 0, 1, -1, 1, -1};
   constexpr int ox[5] = {0, 1, -1, 0, 0};
@@ -605,7 +695,23 @@ __device__ __forceinline__ T op_entry(const T *op, const Geo &g, int64_t nc, int
   return op[(3 * N + i) * nc + K - g.Wn - 1];  // SW
 }
 
-// Galerkin product of a stored 7-point operator: S_c = P' S_f P.
+// The same entry addressed by node index (d a compile-time direction once
+// unrolled).
+template <typename T, int N>
+__device__ __forceinline__ T op_entry_k(const T *op, int64_t Wn, int64_t nc, int64_t K, int ddx, int ddy, int i) {
+  if (ddx == 0 && ddy == 0) return op[(0 * N + i) * nc + K];
+  if (ddx == 1 && ddy == 0) return op[(1 * N + i) * nc + K];
+  if (ddx == 0 && ddy == 1) return op[(2 * N + i) * nc + K];
+  if (ddx == 1 && ddy == 1) return op[(3 * N + i) * nc + K];
+  if (ddx == -1 && ddy == 0) return op[(1 * N + i) * nc + K - 1];
+  if (ddx == 0 && ddy == -1) return op[(2 * N + i) * nc + K - Wn];
+  return op[(3 * N + i) * nc + K - Wn - 1];  // SW
+}
+
+// Galerkin product of a stored 7-point operator: S_c = P' S_f P.  Interior
+// coarse nodes (1 <= X <= Wc-1, 1 <= Y <= Hc-1) need no range tests, so the
+// sums unroll with compile-time hat weights and offsets; the boundary rows
+// take the general loop.
 template <typename T, int N>
 __global__ void __launch_bounds__(kBlock) k_galerkin(const T *__restrict__ opf, Geo gf, Geo gc, T *__restrict__ opc) {
   const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
@@ -615,42 +721,67 @@ __global__ void __launch_bounds__(kBlock) k_galerkin(const T *__restrict__ opf, 
   constexpr int lx[4] = {0, 1, 0, 1};
   constexpr int ly[4] = {0, 0, 1, 1};
   const int64_t nf = (int64_t)gf.Wn * (gf.H + 1), nc = (int64_t)gc.Wn * (gc.H + 1);
-  T acc[4][N];
-#pragma unroll
-  for (int l = 0; l < 4; ++l)
-#pragma unroll
-    for (int i = 0; i < N; ++i) acc[l][i] = T(0);
+  const int64_t K = (int64_t)Y * gc.Wn + X;
+  if (X >= 1 && X <= gc.W - 1 && Y >= 1 && Y <= gc.H - 1) {
+    // one phase at a time (phase-major arrays): ~20 independent loads each
+    const int64_t a0 = (int64_t)(2 * Y) * gf.Wn + 2 * X;
 #pragma unroll 1
-  for (int s = 0; s < 7; ++s) {
-    const int ax = 2 * X + sx[s], ay = 2 * Y + sy[s];
-    if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
-    const T pa = s == 0 ? T(1) : T(0.5);
-#pragma unroll 1
-    for (int o = 0; o < 7; ++o) {
-      const int bx = ax + sx[o], by = ay + sy[o];
-      if (bx < 0 || bx > gf.W || by < 0 || by > gf.H) continue;
-      T q[4];
-      bool anyq = false;
+    for (int i = 0; i < N; ++i) {
+      T c4[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        const int LX = X + lx[l], LY = Y + ly[l];
-        q[l] = (LX > gc.W || LY > gc.H) ? T(0) : hat_weight_t<T>(bx - 2 * LX, by - 2 * LY);
-        anyq |= q[l] != T(0);
+      for (int s = 0; s < 7; ++s) {
+        const int64_t a = a0 + (int64_t)sy[s] * gf.Wn + sx[s];
+        const T pa = s == 0 ? T(1) : T(0.5);
+#pragma unroll
+        for (int o = 0; o < 7; ++o) {
+          T q[4];
+          bool anyq = false;
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            q[l] = hat_weight_t<T>(sx[s] + sx[o] - 2 * lx[l], sy[s] + sy[o] - 2 * ly[l]);
+            anyq |= q[l] != T(0);
+          }
+          if (!anyq) continue;
+          const T sab = pa * op_entry_k<T, N>(opf, gf.Wn, nf, a, sx[o], sy[o], i);
+#pragma unroll
+          for (int l = 0; l < 4; ++l)
+            if (q[l] != T(0)) c4[l] += sab * q[l];
+        }
       }
-      if (!anyq) continue;
 #pragma unroll
-      for (int i = 0; i < N; ++i) {
+      for (int l = 0; l < 4; ++l) opc[(l * N + i) * nc + K] = c4[l];
+    }
+    return;
+  }
+#pragma unroll 1
+  for (int i = 0; i < N; ++i) {
+    T c4[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 1
+    for (int s = 0; s < 7; ++s) {
+      const int ax = 2 * X + sx[s], ay = 2 * Y + sy[s];
+      if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
+      const T pa = s == 0 ? T(1) : T(0.5);
+#pragma unroll 1
+      for (int o = 0; o < 7; ++o) {
+        const int bx = ax + sx[o], by = ay + sy[o];
+        if (bx < 0 || bx > gf.W || by < 0 || by > gf.H) continue;
+        T q[4];
+        bool anyq = false;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const int LX = X + lx[l], LY = Y + ly[l];
+          q[l] = (LX > gc.W || LY > gc.H) ? T(0) : hat_weight_t<T>(bx - 2 * LX, by - 2 * LY);
+          anyq |= q[l] != T(0);
+        }
+        if (!anyq) continue;
         const T sab = pa * op_entry<T, N>(opf, gf, nf, ax, ay, sx[o], sy[o], i);
 #pragma unroll
-        for (int l = 0; l < 4; ++l) acc[l][i] += sab * q[l];
+        for (int l = 0; l < 4; ++l) c4[l] += sab * q[l];
       }
     }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) opc[(l * N + i) * nc + K] = c4[l];
   }
-  const int64_t K = (int64_t)Y * gc.Wn + X;
-#pragma unroll
-  for (int l = 0; l < 4; ++l)
-#pragma unroll
-    for (int i = 0; i < N; ++i) opc[(l * N + i) * nc + K] = acc[l][i];
 }
 
 // (S v)_K - S_KK v_K for phase i of a stored operator (phase-major arrays).
@@ -715,6 +846,37 @@ __global__ void __launch_bounds__(1024) k_coarse_solve_block(const T *__restrict
       }
       __syncthreads();
     }
+}
+
+// The same Gauss-Seidel for coarsest grids that fit in shared memory: the
+// operator, right-hand side and iterate are staged on chip and each thread
+// updates (node, phase) items of the current colour.  Dynamic shared memory:
+// 6 N nc values of T.
+template <typename T, int N>
+__global__ void __launch_bounds__(1024) k_coarse_solve_smem(const T *__restrict__ op, const T *__restrict__ r,
+                                                            T *__restrict__ v, Geo g, int sweeps) {
+  extern __shared__ unsigned char smem_raw[];
+  T *sop = reinterpret_cast<T *>(smem_raw);
+  const int nc = g.Wn * (g.H + 1);
+  T *sr = sop + 4 * N * nc, *sv = sr + N * nc;
+  for (int t = threadIdx.x; t < 4 * N * nc; t += blockDim.x) sop[t] = op[t];
+  for (int t = threadIdx.x; t < N * nc; t += blockDim.x) {
+    sr[t] = r[t];
+    sv[t] = T(0);
+  }
+  __syncthreads();
+  for (int s = 0; s < sweeps; ++s)
+    for (int color = 0; color < 3; ++color) {
+      for (int t = threadIdx.x; t < N * nc; t += blockDim.x) {
+        const int i = t / nc, k = t - i * nc;
+        const int x = k % g.Wn, y = k / g.Wn;
+        if ((x + y) % 3 != color) continue;
+        const T d = sop[i * nc + k];
+        sv[t] = d > T(0) ? (sr[t] - op_offdiag<T, N>(sop, sv, g, nc, x, y, i)) / d : T(0);
+      }
+      __syncthreads();
+    }
+  for (int t = threadIdx.x; t < N * nc; t += blockDim.x) v[t] = sv[t];
 }
 
 // t = r - S v on a coarse level.

@@ -1,5 +1,6 @@
 // ac_launch.cuh -- host launchers wrapping the kernel templates for one N.
 #pragma once
+#include <algorithm>
 #include "ac_kernels.cuh"
 
 namespace ac {
@@ -53,7 +54,14 @@ struct SolverLaunch {
     return sweeps;
   }
   static int coarse_solve(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s) {
-    k_coarse_solve_block<T, N><<<1, 1024, 0, s>>>((const T *)op, (const T *)r, (T *)v, g, sweeps);
+    const int64_t nc = (int64_t)g.Wn * (g.H + 1);
+    const size_t smem = (size_t)6 * N * nc * sizeof(T);
+    if (smem <= 48 * 1024) {
+      const int threads = (int)std::min<int64_t>(1024, ((N * nc + 31) / 32) * 32);
+      k_coarse_solve_smem<T, N><<<1, threads, smem, s>>>((const T *)op, (const T *)r, (T *)v, g, sweeps);
+    } else {
+      k_coarse_solve_block<T, N><<<1, 1024, 0, s>>>((const T *)op, (const T *)r, (T *)v, g, sweeps);
+    }
     return 1;
   }
   static int coarse_resid(const void *op, const void *r, const void *v, const Geo &g, void *t, cudaStream_t s) {
@@ -77,8 +85,8 @@ struct SolverLaunch {
     k_ls_dir<T, N, FORM><<<grid, kBlock, 0, s>>>((const T *)x, (const T *)ob, (const T *)rt, (const T *)v1, mask, gf,
                                                gc, (T *)d, part);
     k_ls_curv<T, N><<<grid, kBlock, 0, s>>>((const T *)d, gf, part + blocks);
-    k_colsum<<<1, kBlock, 0, s>>>(part, blocks, 1, tot);
-    k_colsum<<<1, kBlock, 0, s>>>(part + blocks, blocks, 1, tot + 1);
+    k_colsum<<<1, 1024, 0, s>>>(part, blocks, 1, tot);
+    k_colsum<<<1, 1024, 0, s>>>(part + blocks, blocks, 1, tot + 1);
     k_ls_finish<<<1, 32, 0, s>>>(tot, omega);
     return 5;
   }
@@ -109,11 +117,11 @@ struct Launch {
     const int blocks = (int)(b < kMaxPartBlocks ? b : kMaxPartBlocks);
     if (energy) {
       k_means_partial<N, true><<<blocks, kBlock, 0, s>>>(u, mom, g, part);
-      k_colsum<<<7 * N, kBlock, 0, s>>>(part, blocks, 7 * N, tot);
+      k_colsum<<<7 * N, 1024, 0, s>>>(part, blocks, 7 * N, tot);
       k_means_finish<N, true><<<1, 32, 0, s>>>(tot, c, energy, eps, lam);
     } else {
       k_means_partial<N, false><<<blocks, kBlock, 0, s>>>(u, mom, g, part);
-      k_colsum<<<4 * N, kBlock, 0, s>>>(part, blocks, 4 * N, tot);
+      k_colsum<<<4 * N, 1024, 0, s>>>(part, blocks, 4 * N, tot);
       k_means_finish<N, false><<<1, 32, 0, s>>>(tot, c, nullptr, eps, lam);
     }
     return 3;
@@ -149,7 +157,7 @@ struct Launch {
     const dim3 grid = row_grid(g.W + 1, g.H + 1);
     const int blocks = (int)(grid.x * grid.y);
     k_adj_accum<N><<<grid, kBlock, 0, s>>>(w, u, up, mom, c, g, tau, eps, lam, gm, part);
-    k_colsum<<<2 + 3 * N, kBlock, 0, s>>>(part, blocks, 2 + 3 * N, tot);
+    k_colsum<<<2 + 3 * N, 1024, 0, s>>>(part, blocks, 2 + 3 * N, tot);
     k_adj_scalars<<<1, 32, 0, s>>>(tot, scal);
     return 3;
   }

@@ -561,10 +561,11 @@ def test_adjoint_full_size_c5(ac):
     Rounding noise of the forward, amplified by the first steps of a random
     start, leaves ~5e-11 of noise in L, i.e. ~2.5e-4 in a difference quotient
     at h = 1e-7; larger h meets kinks (active-set changes; h = 1e-6 is off by
-    1e-5 relative).  So lambda, eps and an image direction correlated with the
-    gradient's sign (directional derivative ~|g|_1) are held to 1e-6 relative,
-    and a random image direction (derivative ~|g|_2 ~ 300) to that noise floor.
-    Over the full 64 steps the quotients wander by ~0.5% with h."""
+    1e-5 relative).  lambda and eps are held to 1e-6 relative, two random image
+    directions (derivatives ~300) to 1e-3 absolute, that noise floor.  (A
+    direction aligned with the gradient's signs moves every interface at once
+    and meets kinks within +-h: its quotient is off by ~1e-3 relative.)  Over
+    the full 64 steps the quotients wander by ~0.5% with h."""
     W = H = 512
     cfg = synth.CONFIGS["c5_512_n4_adjoint"]
     N, eps, lam, tau, T = cfg["N"], cfg["eps"], cfg["lam"], cfg["tau"], 16
@@ -583,9 +584,7 @@ def test_adjoint_full_size_c5(ac):
     assert ge == pytest.approx(fd(lambda d: _gpu_loss(ac, img, u0, target, eps + d, lam, tau, T, tol, ac.AC_FP64)),
                                rel=1e-6)
     rng = np.random.default_rng(3)
-    v = np.sign(gimg) * rng.uniform(0.5, 1.5, size=img.shape)
-    assert (gimg * v).sum() == pytest.approx(
-        fd(lambda d: _gpu_loss(ac, img + d * v, u0, target, eps, lam, tau, T, tol, ac.AC_FP64)), rel=1e-6)
-    v = rng.normal(size=img.shape)
-    assert (gimg * v).sum() == pytest.approx(
-        fd(lambda d: _gpu_loss(ac, img + d * v, u0, target, eps, lam, tau, T, tol, ac.AC_FP64)), abs=1e-3)
+    for _ in range(2):
+        v = rng.normal(size=img.shape)
+        assert (gimg * v).sum() == pytest.approx(
+            fd(lambda d: _gpu_loss(ac, img + d * v, u0, target, eps, lam, tau, T, tol, ac.AC_FP64)), abs=1e-3)
