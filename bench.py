@@ -46,6 +46,8 @@ def parse():
                     help="steps of the plain FP64 form timed for the vs-FP64 ratio (0: skip)")
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--tol", type=float, default=None)
+    ap.add_argument("--nu1", type=int, default=2, help="pre-smoothing red-black sweeps per V-cycle")
+    ap.add_argument("--nu2", type=int, default=2, help="post-smoothing red-black sweeps per V-cycle")
     ap.add_argument("--crop", type=int, default=256, help="side of the image crop the CPU oracle times")
     ap.add_argument("--cpu-steps", type=int, default=3, help="oracle steps in the cpu_baseline sample")
     ap.add_argument("--workload", choices=["single", "batch", "adjoint"], default="single",
@@ -74,7 +76,7 @@ def workload_config(cfg, args, extra=None):
     d = {
         "workload": f"{cfg['W']}x{cfg['H']} RGB Voronoi-ramp image (8 regions, ramp<=0.2, noise 0.05), "
                     f"N={cfg['N']}, eps={cfg['eps']}, lambda={cfg['lam']}, tau={cfg['tau']}, "
-                    f"V({2},{2}) to natural residual {cfg['tol']:g}",
+                    f"V({args.nu1},{args.nu2}) to natural residual {cfg['tol']:g}",
         "nodes": (cfg["W"] + 1) * (cfg["H"] + 1),
         "n_phases": cfg["N"],
         "precision": args.precision,
@@ -430,7 +432,7 @@ def main():
     img = synth.config_image(WORKLOAD, rank, W, H)
     stream = torch.cuda.current_stream()
     seg = ac.Segmenter(W, H, N, cfg["eps"], cfg["lam"], cfg["tau"], tol=cfg["tol"], max_cycles=1000, seed=rank,
-                       precision=prec, stream=stream.cuda_stream)
+                       precision=prec, stream=stream.cuda_stream, nu1=args.nu1, nu2=args.nu2)
     seg.set_image(torch.from_numpy(img).cuda())
     seg.step(args.warmup, allow_not_converged=True)
 
@@ -500,7 +502,7 @@ def main():
     if args.precision == "mixed" and args.fp64_steps > 0:
         seg.close()
         seg64 = ac.Segmenter(W, H, N, cfg["eps"], cfg["lam"], cfg["tau"], tol=cfg["tol"], max_cycles=1000, seed=rank,
-                             precision=ac.AC_FP64, stream=stream.cuda_stream)
+                             precision=ac.AC_FP64, stream=stream.cuda_stream, nu1=args.nu1, nu2=args.nu2)
         seg64.set_image(torch.from_numpy(img).cuda())
         seg64.step(args.warmup, allow_not_converged=True)
         barrier()

@@ -543,33 +543,38 @@ __global__ void k_restrict(const T *__restrict__ t, Geo gf, Geo gc, T *__restric
 // phases free nowhere get 0; only phases free on part of it are summed here
 // (at most 35 products of dyadic weights with S entries).
 // ---------------------------------------------------------------------------
-// Interior coarse nodes (2 <= X <= Wc-2, 2 <= Y <= Hc-2): every fine node of
-// the 6x6 mask box is in range and every fine node a, b of the sums is an
-// interior node (S_aa = D[interior], S_ab = -tau eps on axis edges), so with
-// the loops unrolled the hat weights and offsets are compile-time constants.
-template <typename T, int N>
-__device__ __forceinline__ void galerkin0_interior(const uint8_t *__restrict__ mask, const Geo &gf, const Geo &gc,
-                                                   const double *tv, int X, int Y, T *__restrict__ op) {
+// One coarse node of the truncated first-level operator.  The 6x6 box of fine
+// masks around the node is loaded once (0 outside the grid: such nodes drop
+// out of every product) and the sums over the 7 fine nodes a of the coarse
+// hat and their 5 stencil neighbours b unroll completely, so hat weights and
+// offsets are compile-time constants.  INTERIOR (2 <= X <= Wc-2,
+// 2 <= Y <= Hc-2): every box node is in the grid and every a, b is an interior
+// fine node (S_aa = D[interior], S_ab = -tau eps), so range tests and
+// stencil lookups drop out.
+template <typename T, int N, bool INTERIOR>
+__device__ __forceinline__ void galerkin0_node(const uint8_t *__restrict__ mask, const Geo &gf, const Geo &gc,
+                                               const double *tv, int X, int Y, T *__restrict__ op) {
   constexpr int sx[7] = {0, 1, -1, 0, 0, 1, -1};
   constexpr int sy[7] = {0, 0, 0, 1, -1, 1, -1};
   constexpr int ox[5] = {0, 1, -1, 0, 0};
   constexpr int oy[5] = {0, 0, 0, 1, -1};
   constexpr int lx[4] = {0, 1, 0, 1};
   constexpr int ly[4] = {0, 0, 1, 1};
-  // m[j][i]: mask of fine node (2X - 2 + i, 2Y - 2 + j)
+  // m[j][i]: mask of fine node (2X - 2 + i, 2Y - 2 + j), 0 outside the grid
   unsigned m[6][6];
-  const uint8_t *row = mask + (int64_t)(2 * Y - 2) * gf.Wn + (2 * X - 2);
-#pragma unroll
-  for (int j = 0; j < 6; ++j)
-#pragma unroll
-    for (int i = 0; i < 6; ++i) m[j][i] = row[(int64_t)j * gf.Wn + i];
   unsigned all = (1u << N) - 1u, any = 0u;
+  const int64_t row0 = (int64_t)(2 * Y - 2) * gf.Wn + (2 * X - 2);
 #pragma unroll
   for (int j = 0; j < 6; ++j)
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      all &= m[j][i];
-      any |= m[j][i];
+      const int fx = 2 * X - 2 + i, fy = 2 * Y - 2 + j;
+      const bool v = INTERIOR || (fx >= 0 && fx <= gf.W && fy >= 0 && fy <= gf.H);
+      m[j][i] = v ? (unsigned)mask[row0 + (int64_t)j * gf.Wn + i] : 0u;
+      if (v) {
+        all &= m[j][i];
+        any |= m[j][i];
+      }
     }
   const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), K = (int64_t)Y * gc.Wn + X;
   const unsigned partial = any & ~all;
@@ -580,34 +585,67 @@ __device__ __forceinline__ void galerkin0_interior(const uint8_t *__restrict__ m
       for (int i = 0; i < N; ++i) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? (T)tv[l] : T(0);
     return;
   }
-  const T Daa = (T)gf.D[4], Sab = -(T)gf.te;
-  T acc[4][N];
+  if constexpr (INTERIOR) {
+    const T Daa = (T)gf.D[4], Sab = -(T)gf.te;
+    T acc[4][N];
 #pragma unroll
-  for (int l = 0; l < 4; ++l)
+    for (int l = 0; l < 4; ++l)
 #pragma unroll
-    for (int i = 0; i < N; ++i) acc[l][i] = T(0);
+      for (int i = 0; i < N; ++i) acc[l][i] = T(0);
 #pragma unroll
-  for (int s = 0; s < 7; ++s) {
-    const T pa = s == 0 ? T(1) : T(0.5);
-    const unsigned ma = m[2 + sy[s]][2 + sx[s]] & partial;
+    for (int s = 0; s < 7; ++s) {
+      const T pa = s == 0 ? T(1) : T(0.5);
+      const unsigned ma = m[2 + sy[s]][2 + sx[s]] & partial;
 #pragma unroll
-    for (int o = 0; o < 5; ++o) {
-      const unsigned mm = ma & m[2 + sy[s] + oy[o]][2 + sx[s] + ox[o]];
-      const T sab = o == 0 ? Daa : Sab;
+      for (int o = 0; o < 5; ++o) {
+        const unsigned mm = ma & m[2 + sy[s] + oy[o]][2 + sx[s] + ox[o]];
+        const T sab = o == 0 ? Daa : Sab;
 #pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        const T q = hat_weight_t<T>(sx[s] + ox[o] - 2 * lx[l], sy[s] + oy[o] - 2 * ly[l]);
-        if (q == T(0)) continue;
-        const T cf = pa * sab * q;
+        for (int l = 0; l < 4; ++l) {
+          const T q = hat_weight_t<T>(sx[s] + ox[o] - 2 * lx[l], sy[s] + oy[o] - 2 * ly[l]);
+          if (q == T(0)) continue;
+          const T cf = pa * sab * q;
 #pragma unroll
-        for (int i = 0; i < N; ++i) acc[l][i] += ((mm >> i) & 1u) ? cf : T(0);
+          for (int i = 0; i < N; ++i) acc[l][i] += ((mm >> i) & 1u) ? cf : T(0);
+        }
       }
     }
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+#pragma unroll
+      for (int i = 0; i < N; ++i) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? (T)tv[l] : acc[l][i];
+  } else {
+    // boundary nodes: one phase at a time (few registers), stencil entries by
+    // node class
+    bool lval[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) lval[l] = (lx[l] == 0 || X < gc.W) && (ly[l] == 0 || Y < gc.H);
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+      T c4[4] = {T(0), T(0), T(0), T(0)};
+      if (((partial >> i) & 1u)) {
+#pragma unroll
+        for (int s = 0; s < 7; ++s) {
+          const T pa = s == 0 ? T(1) : T(0.5);
+          const unsigned ma = (m[2 + sy[s]][2 + sx[s]] >> i) & 1u;
+#pragma unroll
+          for (int o = 0; o < 5; ++o) {
+            const unsigned mm = ma & (m[2 + sy[s] + oy[o]][2 + sx[s] + ox[o]] >> i);
+            if (!(mm & 1u)) continue;
+            const T sab = fine_S_t<T>(gf, 2 * X + sx[s], 2 * Y + sy[s], ox[o], oy[o]);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+              const T q = hat_weight_t<T>(sx[s] + ox[o] - 2 * lx[l], sy[s] + oy[o] - 2 * ly[l]);
+              if (q == T(0) || !lval[l]) continue;
+              c4[l] += pa * sab * q;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < 4; ++l) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? (T)tv[l] : c4[l];
+    }
   }
-#pragma unroll
-  for (int l = 0; l < 4; ++l)
-#pragma unroll
-    for (int i = 0; i < N; ++i) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? (T)tv[l] : acc[l][i];
 }
 
 template <typename T, int N>
@@ -615,88 +653,16 @@ __global__ void __launch_bounds__(kBlock) k_galerkin0(const uint8_t *__restrict_
                                                       Galerkin0Table tab, T *__restrict__ op) {
   const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
   if (X > gc.W) return;
-  if (X >= 2 && X <= gc.W - 2 && Y >= 2 && Y <= gc.H - 2) {
-    galerkin0_interior<T, N>(mask, gf, gc, tab.v[2 * 5 + 2], X, Y, op);
-    return;
-  }
-  constexpr int sx[7] = {0, 1, -1, 0, 0, 1, -1};
-  constexpr int sy[7] = {0, 0, 0, 1, -1, 1, -1};
-  constexpr int ox[5] = {0, 1, -1, 0, 0};
-  constexpr int oy[5] = {0, 0, 0, 1, -1};
-  constexpr int lx[4] = {0, 1, 0, 1};  // L = K + (lx, ly): C, E, N, NE
-  constexpr int ly[4] = {0, 0, 1, 1};
-  unsigned all = (1u << N) - 1u, any = 0u;
-  for (int ay = 2 * Y - 2; ay <= 2 * Y + 3; ++ay)
-    for (int ax = 2 * X - 2; ax <= 2 * X + 3; ++ax) {
-      if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
-      const unsigned m = mask[(int64_t)ay * gf.Wn + ax];
-      all &= m;
-      any |= m;
-    }
-  const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), K = (int64_t)Y * gc.Wn + X;
-  const double *tv = tab.v[g0_class(Y, gc.H) * 5 + g0_class(X, gc.W)];
-  const unsigned partial = any & ~all;
-  if (!partial) {
-#pragma unroll
-    for (int l = 0; l < 4; ++l)
-#pragma unroll
-      for (int i = 0; i < N; ++i) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? (T)tv[l] : T(0);
-    return;
-  }
-  T acc[4][N];
-#pragma unroll
-  for (int l = 0; l < 4; ++l)
-#pragma unroll
-    for (int i = 0; i < N; ++i) acc[l][i] = T(0);
-#pragma unroll 1
-  for (int s = 0; s < 7; ++s) {
-    const int ax = 2 * X + sx[s], ay = 2 * Y + sy[s];
-    if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
-    const T pa = s == 0 ? T(1) : T(0.5);
-    const unsigned ma = mask[(int64_t)ay * gf.Wn + ax] & partial;
-    if (!ma) continue;
-#pragma unroll 1
-    for (int o = 0; o < 5; ++o) {
-      const int bx = ax + ox[o], by = ay + oy[o];
-      if (bx < 0 || bx > gf.W || by < 0 || by > gf.H) continue;
-      const T sab = fine_S_t<T>(gf, ax, ay, ox[o], oy[o]);
-      const unsigned mm = ma & mask[(int64_t)by * gf.Wn + bx];
-      if (!mm) continue;
-#pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        const int LX = X + lx[l], LY = Y + ly[l];
-        if (LX > gc.W || LY > gc.H) continue;
-        const T q = hat_weight_t<T>(bx - 2 * LX, by - 2 * LY);
-        if (q == T(0)) continue;
-        const T cf = pa * sab * q;
-#pragma unroll
-        for (int i = 0; i < N; ++i)
-          if ((mm >> i) & 1u) acc[l][i] += cf;
-      }
-    }
-  }
-#pragma unroll
-  for (int l = 0; l < 4; ++l)
-#pragma unroll
-    for (int i = 0; i < N; ++i) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? (T)tv[l] : acc[l][i];
+  if (X >= 2 && X <= gc.W - 2 && Y >= 2 && Y <= gc.H - 2)
+    galerkin0_node<T, N, true>(mask, gf, gc, tab.v[2 * 5 + 2], X, Y, op);
+  else
+    galerkin0_node<T, N, false>(mask, gf, gc, tab.v[g0_class(Y, gc.H) * 5 + g0_class(X, gc.W)], X, Y, op);
 }
 
-// S entry (K, K + d) of a stored coarse operator, d in the 7-point pattern.
-template <typename T, int N>
-__device__ __forceinline__ T op_entry(const T *op, const Geo &g, int64_t nc, int x, int y, int ddx, int ddy, int i) {
-  // C, E, N, NE are stored at the node; W, S, SW at the neighbour.
-  const int64_t K = (int64_t)y * g.Wn + x;
-  if (ddx == 0 && ddy == 0) return op[(0 * N + i) * nc + K];
-  if (ddx == 1 && ddy == 0) return op[(1 * N + i) * nc + K];
-  if (ddx == 0 && ddy == 1) return op[(2 * N + i) * nc + K];
-  if (ddx == 1 && ddy == 1) return op[(3 * N + i) * nc + K];
-  if (ddx == -1 && ddy == 0) return op[(1 * N + i) * nc + K - 1];
-  if (ddx == 0 && ddy == -1) return op[(2 * N + i) * nc + K - g.Wn];
-  return op[(3 * N + i) * nc + K - g.Wn - 1];  // SW
-}
 
-// The same entry addressed by node index (d a compile-time direction once
-// unrolled).
+// S entry (K, K + d) of a stored coarse operator, d in the 7-point pattern
+// (a compile-time direction once unrolled): C, E, N, NE are stored at the
+// node, W, S, SW at the neighbour.
 template <typename T, int N>
 __device__ __forceinline__ T op_entry_k(const T *op, int64_t Wn, int64_t nc, int64_t K, int ddx, int ddy, int i) {
   if (ddx == 0 && ddy == 0) return op[(0 * N + i) * nc + K];
@@ -708,77 +674,66 @@ __device__ __forceinline__ T op_entry_k(const T *op, int64_t Wn, int64_t nc, int
   return op[(3 * N + i) * nc + K - Wn - 1];  // SW
 }
 
-// Galerkin product of a stored 7-point operator: S_c = P' S_f P.  Interior
-// coarse nodes (1 <= X <= Wc-1, 1 <= Y <= Hc-1) need no range tests, so the
-// sums unroll with compile-time hat weights and offsets; the boundary rows
-// take the general loop.
-template <typename T, int N>
-__global__ void __launch_bounds__(kBlock) k_galerkin(const T *__restrict__ opf, Geo gf, Geo gc, T *__restrict__ opc) {
-  const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
-  if (X > gc.W) return;
+// One phase of the Galerkin product S_c = P' S_f P at coarse node (X, Y):
+// the C, E, N, NE entries.  The loops over the 7 fine nodes a of the coarse
+// hat and their 7 stencil neighbours b unroll completely, so the hat weights
+// and stencil directions are compile-time constants and each phase's ~20 loads
+// issue together.  INTERIOR (1 <= X <= Wc-1, 1 <= Y <= Hc-1) drops the range
+// predicates that the boundary rows need.
+template <typename T, int N, bool INTERIOR>
+__device__ __forceinline__ void galerkin_phase(const T *__restrict__ opf, const Geo &gf, const Geo &gc, int64_t nf,
+                                               int X, int Y, int i, T (&c4)[4]) {
   constexpr int sx[7] = {0, 1, -1, 0, 0, 1, -1};
   constexpr int sy[7] = {0, 0, 0, 1, -1, 1, -1};
   constexpr int lx[4] = {0, 1, 0, 1};
   constexpr int ly[4] = {0, 0, 1, 1};
+  bool lval[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) lval[l] = INTERIOR || ((lx[l] == 0 || X < gc.W) && (ly[l] == 0 || Y < gc.H));
+  const int64_t a0 = (int64_t)(2 * Y) * gf.Wn + 2 * X;
+#pragma unroll
+  for (int s = 0; s < 7; ++s) {
+    const int ax = 2 * X + sx[s], ay = 2 * Y + sy[s];
+    const bool va = INTERIOR || (ax >= 0 && ax <= gf.W && ay >= 0 && ay <= gf.H);
+    const int64_t a = a0 + (int64_t)sy[s] * gf.Wn + sx[s];
+    const T pa = s == 0 ? T(1) : T(0.5);
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+      T q[4];
+      bool anyq = false;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        q[l] = hat_weight_t<T>(sx[s] + sx[o] - 2 * lx[l], sy[s] + sy[o] - 2 * ly[l]);
+        anyq |= q[l] != T(0);
+      }
+      if (!anyq) continue;
+      const int bx = ax + sx[o], by = ay + sy[o];
+      const bool vb = INTERIOR || (va && bx >= 0 && bx <= gf.W && by >= 0 && by <= gf.H);
+      if (!vb) continue;
+      const T sab = pa * op_entry_k<T, N>(opf, gf.Wn, nf, a, sx[o], sy[o], i);
+#pragma unroll
+      for (int l = 0; l < 4; ++l)
+        if (q[l] != T(0) && lval[l]) c4[l] += sab * q[l];
+    }
+  }
+}
+
+// Galerkin product of a stored 7-point operator: S_c = P' S_f P, one phase at
+// a time (phase-major arrays).
+template <typename T, int N>
+__global__ void __launch_bounds__(kBlock) k_galerkin(const T *__restrict__ opf, Geo gf, Geo gc, T *__restrict__ opc) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
+  if (X > gc.W) return;
   const int64_t nf = (int64_t)gf.Wn * (gf.H + 1), nc = (int64_t)gc.Wn * (gc.H + 1);
   const int64_t K = (int64_t)Y * gc.Wn + X;
-  if (X >= 1 && X <= gc.W - 1 && Y >= 1 && Y <= gc.H - 1) {
-    // one phase at a time (phase-major arrays): ~20 independent loads each
-    const int64_t a0 = (int64_t)(2 * Y) * gf.Wn + 2 * X;
-#pragma unroll 1
-    for (int i = 0; i < N; ++i) {
-      T c4[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-      for (int s = 0; s < 7; ++s) {
-        const int64_t a = a0 + (int64_t)sy[s] * gf.Wn + sx[s];
-        const T pa = s == 0 ? T(1) : T(0.5);
-#pragma unroll
-        for (int o = 0; o < 7; ++o) {
-          T q[4];
-          bool anyq = false;
-#pragma unroll
-          for (int l = 0; l < 4; ++l) {
-            q[l] = hat_weight_t<T>(sx[s] + sx[o] - 2 * lx[l], sy[s] + sy[o] - 2 * ly[l]);
-            anyq |= q[l] != T(0);
-          }
-          if (!anyq) continue;
-          const T sab = pa * op_entry_k<T, N>(opf, gf.Wn, nf, a, sx[o], sy[o], i);
-#pragma unroll
-          for (int l = 0; l < 4; ++l)
-            if (q[l] != T(0)) c4[l] += sab * q[l];
-        }
-      }
-#pragma unroll
-      for (int l = 0; l < 4; ++l) opc[(l * N + i) * nc + K] = c4[l];
-    }
-    return;
-  }
+  const bool interior = X >= 1 && X <= gc.W - 1 && Y >= 1 && Y <= gc.H - 1;
 #pragma unroll 1
   for (int i = 0; i < N; ++i) {
     T c4[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll 1
-    for (int s = 0; s < 7; ++s) {
-      const int ax = 2 * X + sx[s], ay = 2 * Y + sy[s];
-      if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
-      const T pa = s == 0 ? T(1) : T(0.5);
-#pragma unroll 1
-      for (int o = 0; o < 7; ++o) {
-        const int bx = ax + sx[o], by = ay + sy[o];
-        if (bx < 0 || bx > gf.W || by < 0 || by > gf.H) continue;
-        T q[4];
-        bool anyq = false;
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-          const int LX = X + lx[l], LY = Y + ly[l];
-          q[l] = (LX > gc.W || LY > gc.H) ? T(0) : hat_weight_t<T>(bx - 2 * LX, by - 2 * LY);
-          anyq |= q[l] != T(0);
-        }
-        if (!anyq) continue;
-        const T sab = pa * op_entry<T, N>(opf, gf, nf, ax, ay, sx[o], sy[o], i);
-#pragma unroll
-        for (int l = 0; l < 4; ++l) c4[l] += sab * q[l];
-      }
-    }
+    if (interior)
+      galerkin_phase<T, N, true>(opf, gf, gc, nf, X, Y, i, c4);
+    else
+      galerkin_phase<T, N, false>(opf, gf, gc, nf, X, Y, i, c4);
 #pragma unroll
     for (int l = 0; l < 4; ++l) opc[(l * N + i) * nc + K] = c4[l];
   }
