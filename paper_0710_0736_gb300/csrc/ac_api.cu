@@ -385,22 +385,24 @@ int read_rho(ac_ctx *ctx, double *out) {
 int coarse_vcycle(ac_ctx *ctx, Solve &S, int k) {
   Level &L = S.lv[k];
   const ac::SolverOps *o = S.o;
-  AC_CUDA(cudaMemsetAsync(L.v, 0, (size_t)L.n * ctx->N * o->elem, ctx->s));
   if (k == S.depth - 1) {
-    if (L.n <= kCoarsestBlockNodes)
+    if (L.n <= kCoarsestBlockNodes) {
+      AC_CUDA(cudaMemsetAsync(L.v, 0, (size_t)L.n * ctx->N * o->elem, ctx->s));
       AC_RUN(AC_PROF_COARSE, o->coarse_solve(L.op, L.r, L.v, L.g, kCoarsestSweeps, ctx->s));
-    else
-      AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, 2 * kCoarseSweeps, ctx->s));
+    } else {
+      AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, 2 * kCoarseSweeps, true, ctx->s));
+    }
     return AC_OK;
   }
   Level &C = S.lv[k + 1];
-  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, ctx->s));
+  // v starts at 0: the first sweep writes every node without reading v
+  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, true, ctx->s));
   AC_RUN(AC_PROF_COARSE, o->coarse_resid(L.op, L.r, L.v, L.g, L.t, ctx->s));
   AC_RUN(AC_PROF_TRANSFER, o->restrict_(L.t, L.g, C.g, C.r, ctx->s));
   int rc = coarse_vcycle(ctx, S, k + 1);
   if (rc) return rc;
   AC_RUN(AC_PROF_TRANSFER, o->prolong_add(C.v, L.g, C.g, L.v, ctx->s));
-  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, ctx->s));
+  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, false, ctx->s));
   return AC_OK;
 }
 

@@ -757,28 +757,43 @@ __device__ __forceinline__ T op_offdiag(const T *op, const T *v, const Geo &g, i
 
 // a7: one l1-Jacobi sweep on a coarse level, vout = vin + (r - S vin) / l1,
 // l1 = sum_j |S_Kj| (convergent for any symmetric positive definite S; one
-// coalesced launch per sweep).  Rows with a zero diagonal stay 0.
-template <typename T, int N>
-__global__ void k_coarse_jacobi(const T *__restrict__ op, const T *__restrict__ r, const T *__restrict__ vin,
-                                T *__restrict__ vout, Geo g) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-  if (x > g.W) return;
-  const int64_t nc = (int64_t)g.Wn * (g.H + 1), K = (int64_t)y * g.Wn + x;
-  const bool e = x < g.W, w = x > 0, nn = y < g.H, ss = y > 0;
+// coalesced launch per sweep).  Rows with a zero diagonal stay 0.  ZERO_IN:
+// vin = 0 (the first sweep of a V-cycle level), so vout = r / l1 and vin is
+// not read.  Interior nodes take a branch-free copy of the same arithmetic so
+// that the loads of all phases can be in flight together.
+template <typename T, int N, bool ZERO_IN, bool INTERIOR>
+__device__ __forceinline__ void jacobi_node(const T *__restrict__ op, const T *__restrict__ r,
+                                            const T *__restrict__ vin, T *__restrict__ vout, const Geo &g, int64_t nc,
+                                            int x, int y) {
+  const int64_t K = (int64_t)y * g.Wn + x;
+  const bool e = INTERIOR || x < g.W, w = INTERIOR || x > 0, nn = INTERIOR || y < g.H, ss = INTERIOR || y > 0;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     const T *oE = op + (1 * N + i) * nc, *oN = op + (2 * N + i) * nc, *oNE = op + (3 * N + i) * nc;
     const T *vi = vin + i * nc;
     const T d = op[i * nc + K];
-    T sv = d * vi[K], l1 = fabs(d), c;
-    if (e) { c = oE[K]; sv += c * vi[K + 1]; l1 += fabs(c); }
-    if (w) { c = oE[K - 1]; sv += c * vi[K - 1]; l1 += fabs(c); }
-    if (nn) { c = oN[K]; sv += c * vi[K + g.Wn]; l1 += fabs(c); }
-    if (ss) { c = oN[K - g.Wn]; sv += c * vi[K - g.Wn]; l1 += fabs(c); }
-    if (e && nn) { c = oNE[K]; sv += c * vi[K + g.Wn + 1]; l1 += fabs(c); }
-    if (w && ss) { c = oNE[K - g.Wn - 1]; sv += c * vi[K - g.Wn - 1]; l1 += fabs(c); }
-    vout[i * nc + K] = d > T(0) ? vi[K] + (r[i * nc + K] - sv) / l1 : T(0);
+    T sv = ZERO_IN ? T(0) : d * vi[K], l1 = fabs(d), c;
+    if (e) { c = oE[K]; if (!ZERO_IN) sv += c * vi[K + 1]; l1 += fabs(c); }
+    if (w) { c = oE[K - 1]; if (!ZERO_IN) sv += c * vi[K - 1]; l1 += fabs(c); }
+    if (nn) { c = oN[K]; if (!ZERO_IN) sv += c * vi[K + g.Wn]; l1 += fabs(c); }
+    if (ss) { c = oN[K - g.Wn]; if (!ZERO_IN) sv += c * vi[K - g.Wn]; l1 += fabs(c); }
+    if (e && nn) { c = oNE[K]; if (!ZERO_IN) sv += c * vi[K + g.Wn + 1]; l1 += fabs(c); }
+    if (w && ss) { c = oNE[K - g.Wn - 1]; if (!ZERO_IN) sv += c * vi[K - g.Wn - 1]; l1 += fabs(c); }
+    const T v0 = ZERO_IN ? T(0) : vi[K];
+    vout[i * nc + K] = d > T(0) ? v0 + (r[i * nc + K] - sv) / l1 : T(0);
   }
+}
+
+template <typename T, int N, bool ZERO_IN>
+__global__ void k_coarse_jacobi(const T *__restrict__ op, const T *__restrict__ r, const T *__restrict__ vin,
+                                T *__restrict__ vout, Geo g) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x > g.W) return;
+  const int64_t nc = (int64_t)g.Wn * (g.H + 1);
+  if (x > 0 && x < g.W && y > 0 && y < g.H)
+    jacobi_node<T, N, ZERO_IN, true>(op, r, vin, vout, g, nc, x, y);
+  else
+    jacobi_node<T, N, ZERO_IN, false>(op, r, vin, vout, g, nc, x, y);
 }
 
 // Whole-level Gauss-Seidel in one block for small coarsest grids: `sweeps`
@@ -834,13 +849,30 @@ __global__ void __launch_bounds__(1024) k_coarse_solve_smem(const T *__restrict_
   for (int t = threadIdx.x; t < N * nc; t += blockDim.x) v[t] = sv[t];
 }
 
-// t = r - S v on a coarse level.
+// t = r - S v on a coarse level (interior nodes branch-free, as in
+// k_coarse_jacobi; the same arithmetic and order as op_offdiag).
 template <typename T, int N>
 __global__ void k_coarse_resid(const T *__restrict__ op, const T *__restrict__ r, const T *__restrict__ v, Geo g,
                                T *__restrict__ t) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x > g.W) return;
   const int64_t nc = (int64_t)g.Wn * (g.H + 1), K = (int64_t)y * g.Wn + x;
+  if (x > 0 && x < g.W && y > 0 && y < g.H) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const T *oE = op + (1 * N + i) * nc, *oN = op + (2 * N + i) * nc, *oNE = op + (3 * N + i) * nc;
+      const T *vi = v + i * nc;
+      T s = T(0);
+      s += oE[K] * vi[K + 1];
+      s += oE[K - 1] * vi[K - 1];
+      s += oN[K] * vi[K + g.Wn];
+      s += oN[K - g.Wn] * vi[K - g.Wn];
+      s += oNE[K] * vi[K + g.Wn + 1];
+      s += oNE[K - g.Wn - 1] * vi[K - g.Wn - 1];
+      t[i * nc + K] = r[i * nc + K] - op[i * nc + K] * vi[K] - s;
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < N; ++i)
     t[i * nc + K] = r[i * nc + K] - op[i * nc + K] * v[i * nc + K] - op_offdiag<T, N>(op, v, g, nc, x, y, i);

@@ -44,12 +44,15 @@ struct SolverLaunch {
     return 1;
   }
   static int coarse_smooth(const void *op, const void *r, void *v, void *tmp, const Geo &g, int sweeps,
-                           cudaStream_t s) {
+                           bool zero_start, cudaStream_t s) {
     const dim3 grid = row_grid(g.W + 1, g.H + 1);
     for (int k = 0; k < sweeps; ++k) {
       const T *in = (const T *)(k % 2 == 0 ? v : tmp);
       T *out = (T *)(k % 2 == 0 ? tmp : v);
-      k_coarse_jacobi<T, N><<<grid, kBlock, 0, s>>>((const T *)op, (const T *)r, in, out, g);
+      if (k == 0 && zero_start)
+        k_coarse_jacobi<T, N, true><<<grid, kBlock, 0, s>>>((const T *)op, (const T *)r, in, out, g);
+      else
+        k_coarse_jacobi<T, N, false><<<grid, kBlock, 0, s>>>((const T *)op, (const T *)r, in, out, g);
     }
     return sweeps;
   }

@@ -27,7 +27,10 @@ struct SolverOps {
                    cudaStream_t s);
   int (*galerkin)(const void *opf, const Geo &gf, const Geo &gc, void *opc, cudaStream_t s);
   // l1-Jacobi sweeps ping-ponging v and tmp (sweeps must be even; the result is in v)
-  int (*coarse_smooth)(const void *op, const void *r, void *v, void *tmp, const Geo &g, int sweeps, cudaStream_t s);
+  // `sweeps` (even) l1-Jacobi sweeps ending in v; zero_start: v = 0 on entry
+  // (it is then neither read nor needs clearing)
+  int (*coarse_smooth)(const void *op, const void *r, void *v, void *tmp, const Geo &g, int sweeps, bool zero_start,
+                       cudaStream_t s);
   int (*coarse_solve)(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s);
   int (*coarse_resid)(const void *op, const void *r, const void *v, const Geo &g, void *t, cudaStream_t s);
   int (*restrict_)(const void *t, const Geo &gf, const Geo &gc, void *rc, cudaStream_t s);
