@@ -80,8 +80,13 @@ ac::Geo make_geo(int W, int H, double te) {
       g.D[k] = m0 + te * wsum;
       g.invD[k] = g.D[k] > 0 ? 1.0 / g.D[k] : 0.0;
     }
+  g.half = ((int64_t)(W + 1) * (H + 1) + 1) / 2;
   return g;
 }
+
+// Node slots of a fine-level array (FP32 arrays are split by colour, see
+// ac::fslot: two halves of (n + 1) / 2 slots).
+int64_t fine_slots(int64_t n) { return 2 * ((n + 1) / 2); }
 
 struct Level {
   ac::Geo g;
@@ -500,7 +505,7 @@ int solve_mixed(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_o
       break;
     }
     if (cycles >= ctx->p.max_cycles) break;
-    AC_CUDA(cudaMemsetAsync(ctx->sv.x, 0, (size_t)ctx->n * ctx->N * sizeof(float), ctx->s));
+    AC_CUDA(cudaMemsetAsync(ctx->sv.x, 0, (size_t)fine_slots(ctx->n) * ctx->N * sizeof(float), ctx->s));
     int c = 0;
     int64_t sw = 0;
     double rin = 0;
@@ -509,7 +514,7 @@ int solve_mixed(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_o
     cycles += c;
     sweeps += sw;
     if (rc && rc != AC_ERR_NOT_CONVERGED) return rc;
-    AC_RUN(AC_PROF_OUTER, o->outer_update(ctx->u, (const float *)ctx->sv.x, ctx->n, ctx->s));
+    AC_RUN(AC_PROF_OUTER, o->outer_update(ctx->u, (const float *)ctx->sv.x, ctx->g0, ctx->s));
     ++outer;
   }
   *cycles_out = cycles;
@@ -618,7 +623,8 @@ int ac_create(ac_ctx **out, const ac_params *p) {
   if (S.lv.size() > 1) S.tab0 = galerkin0_table(S.lv[0].g, S.lv[1].g);
   const int N = ctx->N;
   const size_t es = (size_t)S.o->elem;
-  const size_t fN64 = (size_t)ctx->n * N * sizeof(double), fNs = (size_t)ctx->n * N * es;
+  // FP32 fine arrays are split by colour (fslot): 2 ((n + 1) / 2) node slots
+  const size_t fN64 = (size_t)ctx->n * N * sizeof(double), fNs = (size_t)fine_slots(ctx->n) * N * es;
   const int ls_blocks = (int)(((ctx->g0.W + 1 + 255) / 256) * (int64_t)(ctx->g0.H + 1));
   auto body = [&]() -> int {
     AC_ALLOC(ctx->u, fN64);

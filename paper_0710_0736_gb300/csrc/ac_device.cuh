@@ -26,12 +26,28 @@ struct Geo {
   double m0[9];    // Mhat by class
   double D[9];     // S_nn by class
   double invD[9];  // 1 / S_nn by class
+  int64_t half;    // ((W + 1)(H + 1) + 1) / 2: colour-split stride of the FP32 fine arrays
 };
 
 __host__ __device__ __forceinline__ int node_class(const Geo &g, int x, int y) {
   int cx = x == 0 ? 0 : (x == g.W ? 2 : 1);
   int cy = y == 0 ? 0 : (y == g.H ? 2 : 1);
   return cy * 3 + cx;
+}
+
+// Storage slot of fine node (x, y) in an array of element type T.  FP32
+// arrays (the mixed form's correction solve) are split by red-black colour:
+// colour c = (x + y) & 1 holds its nodes at c * half + ((y Wn + x) >> 1),
+// which is one-to-one within a colour for any row stride, so one colour's
+// sweep reads and writes contiguous memory only.  FP64 arrays keep the plain
+// node order y Wn + x.
+template <typename T>
+__host__ __device__ __forceinline__ int64_t fslot(const Geo &g, int x, int y) {
+  const int64_t n = (int64_t)y * g.Wn + x;
+  if constexpr (sizeof(T) == 4)
+    return (((x + y) & 1) ? g.half : 0) + (n >> 1);
+  else
+    return n;
 }
 
 // Stiffness weights of the four axis edges at (x, y): east, west, north, south.
@@ -274,20 +290,20 @@ __device__ __forceinline__ void proj_simplex(T (&y)[N]) {
   proj_box<T, N, kDirect>(y, none);
 }
 
-// Weighted sum of the four axis neighbours' values, acc = sum_m w_nm u_m.
+// Weighted sum of the four axis neighbours' values, acc = sum_m w_nm u_m (u
+// in the storage order of fslot<T>).
 template <typename T, int N>
 __device__ __forceinline__ void nbr_sum(const T *u, const Geo &g, int x, int y, T (&acc)[N]) {
-  const int64_t n = (int64_t)y * g.Wn + x;
   T t[N];
   if (x > 0 && x < g.W && y > 0 && y < g.H) {
-    ldn_rw<T, N>(u + (n + 1) * N, acc);
-    ldn_rw<T, N>(u + (n - 1) * N, t);
+    ldn_rw<T, N>(u + fslot<T>(g, x + 1, y) * N, acc);
+    ldn_rw<T, N>(u + fslot<T>(g, x - 1, y) * N, t);
 #pragma unroll
     for (int i = 0; i < N; ++i) acc[i] += t[i];
-    ldn_rw<T, N>(u + (n + g.Wn) * N, t);
+    ldn_rw<T, N>(u + fslot<T>(g, x, y + 1) * N, t);
 #pragma unroll
     for (int i = 0; i < N; ++i) acc[i] += t[i];
-    ldn_rw<T, N>(u + (n - g.Wn) * N, t);
+    ldn_rw<T, N>(u + fslot<T>(g, x, y - 1) * N, t);
 #pragma unroll
     for (int i = 0; i < N; ++i) acc[i] += t[i];
   } else {
@@ -295,22 +311,22 @@ __device__ __forceinline__ void nbr_sum(const T *u, const Geo &g, int x, int y, 
 #pragma unroll
     for (int i = 0; i < N; ++i) acc[i] = T(0);
     if (w.e > 0.f) {
-      ldn_rw<T, N>(u + (n + 1) * N, t);
+      ldn_rw<T, N>(u + fslot<T>(g, x + 1, y) * N, t);
 #pragma unroll
       for (int i = 0; i < N; ++i) acc[i] += T(w.e) * t[i];
     }
     if (w.w > 0.f) {
-      ldn_rw<T, N>(u + (n - 1) * N, t);
+      ldn_rw<T, N>(u + fslot<T>(g, x - 1, y) * N, t);
 #pragma unroll
       for (int i = 0; i < N; ++i) acc[i] += T(w.w) * t[i];
     }
     if (w.n > 0.f) {
-      ldn_rw<T, N>(u + (n + g.Wn) * N, t);
+      ldn_rw<T, N>(u + fslot<T>(g, x, y + 1) * N, t);
 #pragma unroll
       for (int i = 0; i < N; ++i) acc[i] += T(w.n) * t[i];
     }
     if (w.s > 0.f) {
-      ldn_rw<T, N>(u + (n - g.Wn) * N, t);
+      ldn_rw<T, N>(u + fslot<T>(g, x, y - 1) * N, t);
 #pragma unroll
       for (int i = 0; i < N; ++i) acc[i] += T(w.s) * t[i];
     }

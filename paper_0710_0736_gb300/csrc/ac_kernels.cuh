@@ -296,8 +296,9 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
       uf[i] = (float)uk[i];
       z[i] = r[i] * invD;
     }
-    stn<float, N>(r32 + n * N, rf);
-    stn<float, N>(u32 + n * N, uf);
+    const int64_t sl = fslot<float>(g, x, y);
+    stn<float, N>(r32 + sl * N, rf);
+    stn<float, N>(u32 + sl * N, uf);
     if constexpr (RHO32) {
       // the same projection in float on the rounded data: off by at most a
       // few float ulps of u (the caller widens tol by that margin)
@@ -331,13 +332,14 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
 // u_i - float(u_i) -- and the projection then runs over the other components
 // only, so that exact zeros (the active set) are the same as in the FP64 form.
 template <int N>
-__global__ void k_outer_update(double *__restrict__ u, const float *__restrict__ delta, int64_t n) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
+__global__ void k_outer_update(double *__restrict__ u, const float *__restrict__ delta, Geo g) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x > g.W) return;
+  const int64_t k = (int64_t)y * g.Wn + x;
   double uk[N];
   float dk[N];
   ldn_rw<double, N>(u + k * N, uk);
-  ldn<float, N>(delta + k * N, dk);
+  ldn<float, N>(delta + fslot<float>(g, x, y) * N, dk);
   unsigned keep = 0;
   double s = 0.0;
   int cnt = 0;
@@ -399,7 +401,7 @@ __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const
   const int y = blockIdx.y;
   const int xx = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((y + color) & 1);
   if (xx > g.W) return;
-  const int64_t n = (int64_t)y * g.Wn + xx;
+  const int64_t n = fslot<T>(g, xx, y);
   T acc[N], bk[N], o[N];
   nbr_sum<T, N>(x, g, xx, y, acc);
   if (corr) {
@@ -437,12 +439,12 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
   const int y = blockIdx.y;
   double e = 0.0;
   if (xx <= g.W) {
-    const int64_t n = (int64_t)y * g.Wn + xx;
+    const int64_t n = (int64_t)y * g.Wn + xx, sl = fslot<T>(g, xx, y);
     T acc[N], xk[N], bk[N], r[N], o[N];
     nbr_sum<T, N>(x, g, xx, y, acc);
-    ldn<T, N>(x + n * N, xk);
-    ldn<T, N>(rhs + n * N, bk);
-    if constexpr (FORM != kDirect) ldn<T, N>(ob + n * N, o);
+    ldn<T, N>(x + sl * N, xk);
+    ldn<T, N>(rhs + sl * N, bk);
+    if constexpr (FORM != kDirect) ldn<T, N>(ob + sl * N, o);
     const int cls = node_class(g, xx, y);
     const T D = (T)g.D[cls], invD = (T)g.invD[cls], te = (T)g.te;
 #pragma unroll
@@ -475,7 +477,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
       const T mean = cnt >= 2 ? s * rcp_small<T>(cnt) : T(0);
 #pragma unroll
       for (int i = 0; i < N; ++i) r[i] = ((fr >> i) & 1u) ? r[i] - mean : T(0);
-      stn<T, N>(rt + n * N, r);
+      stn<T, N>(rt + sl * N, r);
       mask[n] = (uint8_t)fr;
     }
   }
@@ -502,7 +504,7 @@ __global__ void k_restrict0(const T *__restrict__ t, Geo gf, Geo gc, T *__restri
     const int ax = 2 * X + dx[s], ay = 2 * Y + dy[s];
     if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
     const T p = s == 0 ? T(1) : T(0.5);
-    ldn<T, N>(t + ((int64_t)ay * gf.Wn + ax) * N, v);
+    ldn<T, N>(t + fslot<T>(gf, ax, ay) * N, v);
 #pragma unroll
     for (int i = 0; i < N; ++i) acc[i] += p * v[i];
   }
@@ -922,7 +924,7 @@ __global__ void __launch_bounds__(kBlock) k_ls_dir(const T *__restrict__ x, cons
   const int xx = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   double dot[1] = {0.0};
   if (xx <= gf.W) {
-    const int64_t n = (int64_t)y * gf.Wn + xx;
+    const int64_t n = (int64_t)y * gf.Wn + xx, sl = fslot<T>(gf, xx, y);
     const unsigned fr = mask[n];
     T dn[N];
     if (fr) {
@@ -937,12 +939,12 @@ __global__ void __launch_bounds__(kBlock) k_ls_dir(const T *__restrict__ x, cons
           ++cnt;
         }
       const T mean = s * rcp_small<T>(cnt);
-      ldn<T, N>(x + n * N, xk);
-      if constexpr (FORM != kDirect) ldn<T, N>(ob + n * N, o);
+      ldn<T, N>(x + sl * N, xk);
+      if constexpr (FORM != kDirect) ldn<T, N>(ob + sl * N, o);
 #pragma unroll
       for (int i = 0; i < N; ++i) w[i] = xk[i] + (((fr >> i) & 1u) ? w[i] - mean : T(0));
       proj_box<T, N, FORM>(w, o);
-      ldn<T, N>(rt + n * N, r);
+      ldn<T, N>(rt + sl * N, r);
       T loc = T(0);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
@@ -954,7 +956,7 @@ __global__ void __launch_bounds__(kBlock) k_ls_dir(const T *__restrict__ x, cons
 #pragma unroll
       for (int i = 0; i < N; ++i) dn[i] = T(0);
     }
-    stn<T, N>(d + n * N, dn);
+    stn<T, N>(d + sl * N, dn);
   }
   block_sum_store<1>(dot, part + blockIdx.y * gridDim.x + blockIdx.x);
 }
@@ -964,10 +966,9 @@ __global__ void __launch_bounds__(kBlock) k_ls_curv(const T *__restrict__ d, Geo
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   double dot[1] = {0.0};
   if (x <= g.W) {
-    const int64_t n = (int64_t)y * g.Wn + x;
     T acc[N], dk[N];
     nbr_sum<T, N>(d, g, x, y, acc);
-    ldn<T, N>(d + n * N, dk);
+    ldn<T, N>(d + fslot<T>(g, x, y) * N, dk);
     const T D = (T)g.D[node_class(g, x, y)], te = (T)g.te;
     T loc = T(0);
 #pragma unroll

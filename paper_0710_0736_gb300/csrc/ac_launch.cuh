@@ -142,8 +142,8 @@ struct Launch {
       k_outer_resid<N, false><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, b, g, r32, u32, rho);
     return 1;
   }
-  static int outer_update(double *u, const float *delta, int64_t n, cudaStream_t s) {
-    k_outer_update<N><<<blocks_for(n), kBlock, 0, s>>>(u, delta, n);
+  static int outer_update(double *u, const float *delta, const Geo &g, cudaStream_t s) {
+    k_outer_update<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, delta, g);
     return 1;
   }
   static int labels(const double *u, const Geo &g, int8_t *node_lab, int8_t *pix_lab, cudaStream_t s) {

@@ -54,7 +54,7 @@ struct Ops {
   // a few float ulps of u) instead of the FP64 one
   int (*outer_resid)(const double *u, const double *b, const Geo &g, float *r32, float *u32, double *rho, bool rho32,
                      cudaStream_t s);
-  int (*outer_update)(double *u, const float *delta, int64_t n, cudaStream_t s);
+  int (*outer_update)(double *u, const float *delta, const Geo &g, cudaStream_t s);
   int (*labels)(const double *u, const Geo &g, int8_t *node_lab, int8_t *pix_lab, cudaStream_t s);
   int (*project)(const double *y, double *x, int64_t count, cudaStream_t s);
   SolverOps fp64;     // T = double, direct form
