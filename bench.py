@@ -132,13 +132,14 @@ class Clocks:
 
 
 # DRAM bytes per node of one launch of k_smooth_fine<float, 8, shifted>: ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) at 2048 x 2048, 456.3 MB over
+# (dram__bytes_read.sum + dram__bytes_write.sum) at 2048 x 2048, 248.7 MB over
 # 4,198,401 nodes (profiles/k_smooth_fine_mixed_2048_n8_ncu.md), scaled to
 # the workload by nodes.  It holds for the kernel source it was taken on: the
 # digest covers the kernel's text and that of the device helpers it calls.
-SMOOTH_TRAFFIC = {"sha256": "09415d42d0e1f169eb269f04ce9e4de9838f85bb7d7856158bc0d2ce96ef6aa4",
-                  "bytes_per_node": 456.30e6 / 4198401, "n_phases": 8, "precision": "mixed"}
-SMOOTH_HELPERS = ("node_class", "edge_weights", "rcp_small", "proj_box", "nbr_sum", "ldn", "ldn_rw", "stn")
+SMOOTH_TRAFFIC = {"sha256": "4da6d4ac883148f37377e2fee18e4f08c53fcf242e415140d8cac439514c1e3d",
+                  "bytes_per_node": (201.545e6 + 47.188e6) / 4198401, "n_phases": 8, "precision": "mixed"}
+SMOOTH_HELPERS = ("node_class", "edge_weights", "fslot", "geo_te", "geo_invD", "omega_t", "rcp_small", "proj_box",
+                  "nbr_sum", "ldn", "ldn_rw", "stn")
 
 
 def _function_text(src, name):

@@ -81,6 +81,11 @@ ac::Geo make_geo(int W, int H, double te) {
       g.invD[k] = g.D[k] > 0 ? 1.0 / g.D[k] : 0.0;
     }
   g.half = ((int64_t)(W + 1) * (H + 1) + 1) / 2;
+  g.tef = (float)g.te;
+  for (int k = 0; k < 9; ++k) {
+    g.Df[k] = (float)g.D[k];
+    g.invDf[k] = (float)g.invD[k];
+  }
   return g;
 }
 
@@ -233,6 +238,7 @@ int validate(const ac_params *p) {
   if (p->width < 1 || p->height < 1) return fail(AC_ERR_ARG, "image size must be >= 1x1");
   if ((int64_t)(p->width + 1) * (p->height + 1) > (int64_t)1 << 31)
     return fail(AC_ERR_ARG, "image too large (more than 2^31 nodes)");
+  if (p->height + 1 > 65535) return fail(AC_ERR_ARG, "image height must be below 65535 (one grid row per node row)");
   if (p->n_phases < 2 || p->n_phases > AC_MAX_PHASES)
     return fail(AC_ERR_ARG, "n_phases must be in [2, %d]", AC_MAX_PHASES);
   if (!(p->eps > 0) || !std::isfinite(p->eps)) return fail(AC_ERR_ARG, "eps must be > 0");
@@ -650,7 +656,7 @@ int ac_create(ac_ctx **out, const ac_params *p) {
     AC_ALLOC(ctx->c_tmp, (size_t)3 * N * sizeof(double));
     AC_ALLOC(ctx->energy, sizeof(double));
     AC_ALLOC(ctx->rho, sizeof(double));
-    AC_ALLOC(ctx->omega, sizeof(double));
+    AC_ALLOC(ctx->omega, 2 * sizeof(double));  // omega and its float rounding
     AC_ALLOC(ctx->ls_part, (size_t)2 * ls_blocks * sizeof(double));
     AC_ALLOC(ctx->ls_tot, 2 * sizeof(double));
     for (size_t k = 1; k < S.lv.size(); ++k) {
@@ -662,7 +668,7 @@ int ac_create(ac_ctx **out, const ac_params *p) {
     }
     AC_CUDA(cudaMallocHost(&ctx->h_scalars, 4 * sizeof(double)));
     AC_CUDA(cudaMemsetAsync(ctx->c, 0, (size_t)3 * N * sizeof(double), ctx->s));
-    AC_CUDA(cudaMemsetAsync(ctx->omega, 0, sizeof(double), ctx->s));
+    AC_CUDA(cudaMemsetAsync(ctx->omega, 0, 2 * sizeof(double), ctx->s));
     return AC_OK;
   };
   rc = body();

@@ -27,7 +27,29 @@ struct Geo {
   double D[9];     // S_nn by class
   double invD[9];  // 1 / S_nn by class
   int64_t half;    // ((W + 1)(H + 1) + 1) / 2: colour-split stride of the FP32 fine arrays
+  float tef, Df[9], invDf[9];  // te, D, invD rounded to float (FP32 kernels do no FP64 conversions)
 };
+
+// te, S_nn, 1/S_nn in a kernel's scalar type.
+template <typename T>
+__host__ __device__ __forceinline__ T geo_te(const Geo &g) {
+  if constexpr (sizeof(T) == 4) return g.tef; else return g.te;
+}
+template <typename T>
+__host__ __device__ __forceinline__ T geo_D(const Geo &g, int cls) {
+  if constexpr (sizeof(T) == 4) return g.Df[cls]; else return g.D[cls];
+}
+template <typename T>
+__host__ __device__ __forceinline__ T geo_invD(const Geo &g, int cls) {
+  if constexpr (sizeof(T) == 4) return g.invDf[cls]; else return g.invD[cls];
+}
+
+// The line-search step omega is kept as a double followed by its float
+// rounding (two doubles of storage); a kernel reads it in its scalar type.
+template <typename T>
+__device__ __forceinline__ T omega_t(const double *omega) {
+  if constexpr (sizeof(T) == 4) return reinterpret_cast<const float *>(omega + 1)[0]; else return omega[0];
+}
 
 __host__ __device__ __forceinline__ int node_class(const Geo &g, int x, int y) {
   int cx = x == 0 ? 0 : (x == g.W ? 2 : 1);
@@ -357,10 +379,10 @@ __host__ __device__ __forceinline__ double fine_S(const Geo &g, int ax, int ay, 
 // GB300's scarce FP64 issue slots on it).
 template <typename T>
 __device__ __forceinline__ T fine_S_t(const Geo &g, int ax, int ay, int ddx, int ddy) {
-  if (ddx == 0 && ddy == 0) return (T)g.D[node_class(g, ax, ay)];
+  if (ddx == 0 && ddy == 0) return geo_D<T>(g, node_class(g, ax, ay));
   Weights w = edge_weights(g, ax, ay);
   float ww = ddx == 1 ? w.e : ddx == -1 ? w.w : ddy == 1 ? w.n : w.s;
-  return -(T)g.te * (T)ww;
+  return -geo_te<T>(g) * (T)ww;
 }
 
 template <typename T>
@@ -420,9 +442,10 @@ __device__ __forceinline__ T warp_sum(T v) {
 template <typename T>
 __device__ __forceinline__ T nanmax(T a, T b) { return (a != a || b <= a) ? a : b; }
 
-__device__ __forceinline__ double warp_nanmax(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_nanmax(T v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = nanmax<double>(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = nanmax<T>(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 

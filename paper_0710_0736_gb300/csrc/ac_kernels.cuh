@@ -54,15 +54,35 @@ __device__ __forceinline__ void block_sum_store(double (&v)[K], double *dst) {
   }
 }
 
-__device__ __forceinline__ void block_max_atomic(double e, double *rho) {
-  __shared__ double sm[kBlock / 32];
-  e = warp_nanmax(e);
+// Block maximum (NaN-propagating) of non-negative values in the kernel's
+// scalar type, folded into *rho by one atomic per block (the conversion of a
+// float maximum to double is exact).
+template <typename T>
+__device__ __forceinline__ void block_max_atomic(T e, double *rho) {
+  __shared__ T sm[kBlock / 32];
+  e = warp_nanmax<T>(e);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = e;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
-    v = warp_nanmax(v);
-    if (threadIdx.x == 0) atomic_max_nonneg(rho, v);
+    T v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : T(0);
+    v = warp_nanmax<T>(v);
+    if (threadIdx.x == 0) atomic_max_nonneg(rho, (double)v);
+  }
+}
+
+// Block sum of one value per thread in the kernel's scalar type; thread 0
+// stores the block's total as a double (FP32 kernels keep the FP64 pipe
+// free; the totals across blocks are summed in FP64).
+template <typename T>
+__device__ __forceinline__ void block_sum_store1(T v, double *dst) {
+  __shared__ T sm[kBlock / 32];
+  v = warp_sum<T>(v);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    T t = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : T(0);
+    t = warp_sum<T>(t);
+    if (threadIdx.x == 0) *dst = (double)t;
   }
 }
 
@@ -405,7 +425,7 @@ __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const
   T acc[N], bk[N], o[N];
   nbr_sum<T, N>(x, g, xx, y, acc);
   if (corr) {
-    const T w = (T)*omega;
+    const T w = omega_t<T>(omega);
     if (w != T(0)) {
       T dc[N];
       nbr_sum<T, N>(corr, g, xx, y, dc);
@@ -416,7 +436,7 @@ __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const
   ldn<T, N>(rhs + n * N, bk);
   if constexpr (FORM != kDirect) ldn<T, N>(ob + n * N, o);
   const int cls = node_class(g, xx, y);
-  const T te = (T)g.te, invD = (T)g.invD[cls];
+  const T te = geo_te<T>(g), invD = geo_invD<T>(g, cls);
 #pragma unroll
   for (int i = 0; i < N; ++i) acc[i] = (bk[i] + te * acc[i]) * invD;
   proj_box<T, N, FORM>(acc, o);
@@ -437,7 +457,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
                                                        uint8_t *__restrict__ mask, double *__restrict__ rho) {
   const int xx = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
-  double e = 0.0;
+  T e = T(0);
   if (xx <= g.W) {
     const int64_t n = (int64_t)y * g.Wn + xx, sl = fslot<T>(g, xx, y);
     T acc[N], xk[N], bk[N], r[N], o[N];
@@ -446,7 +466,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
     ldn<T, N>(rhs + sl * N, bk);
     if constexpr (FORM != kDirect) ldn<T, N>(ob + sl * N, o);
     const int cls = node_class(g, xx, y);
-    const T D = (T)g.D[cls], invD = (T)g.invD[cls], te = (T)g.te;
+    const T D = geo_D<T>(g, cls), invD = geo_invD<T>(g, cls), te = geo_te<T>(g);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       r[i] = bk[i] + te * acc[i] - D * xk[i];
@@ -466,8 +486,8 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
         ++cnt;
       }
     }
-    e = (double)et;
-    if (!(xk[0] == xk[0])) e = (double)xk[0];
+    e = et;
+    if (!(xk[0] == xk[0])) e = xk[0];
     if (rt) {
       const unsigned fr = cnt >= 2 ? pos : 0u;
       T s = T(0);
@@ -481,7 +501,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
       mask[n] = (uint8_t)fr;
     }
   }
-  block_max_atomic(e, rho);
+  block_max_atomic<T>(e, rho);
 }
 
 // ---------------------------------------------------------------------------
@@ -515,26 +535,21 @@ __global__ void k_restrict0(const T *__restrict__ t, Geo gf, Geo gc, T *__restri
 
 template <typename T, int N>
 __global__ void k_restrict(const T *__restrict__ t, Geo gf, Geo gc, T *__restrict__ rc) {
-  const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
+  const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y, i = blockIdx.z;
   if (X > gc.W) return;
   constexpr int dx[7] = {0, 1, -1, 0, 0, 1, -1};
   constexpr int dy[7] = {0, 0, 0, 1, -1, 1, -1};
   const int64_t nf = (int64_t)gf.Wn * (gf.H + 1), nc = (int64_t)gc.Wn * (gc.H + 1);
-  T acc[N];
-#pragma unroll
-  for (int i = 0; i < N; ++i) acc[i] = T(0);
+  const T *ti = t + i * nf;
+  T acc = T(0);
 #pragma unroll
   for (int s = 0; s < 7; ++s) {
     const int ax = 2 * X + dx[s], ay = 2 * Y + dy[s];
     if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
     const T p = s == 0 ? T(1) : T(0.5);
-    const int64_t a = (int64_t)ay * gf.Wn + ax;
-#pragma unroll
-    for (int i = 0; i < N; ++i) acc[i] += p * t[i * nf + a];
+    acc += p * ti[(int64_t)ay * gf.Wn + ax];
   }
-  const int64_t K = (int64_t)Y * gc.Wn + X;
-#pragma unroll
-  for (int i = 0; i < N; ++i) rc[i * nc + K] = acc[i];
+  rc[i * nc + (int64_t)Y * gc.Wn + X] = acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -588,7 +603,7 @@ __device__ __forceinline__ void galerkin0_node(const uint8_t *__restrict__ mask,
     return;
   }
   if constexpr (INTERIOR) {
-    const T Daa = (T)gf.D[4], Sab = -(T)gf.te;
+    const T Daa = geo_D<T>(gf, 4), Sab = -geo_te<T>(gf);
     T acc[4][N];
 #pragma unroll
     for (int l = 0; l < 4; ++l)
@@ -720,25 +735,21 @@ __device__ __forceinline__ void galerkin_phase(const T *__restrict__ opf, const 
   }
 }
 
-// Galerkin product of a stored 7-point operator: S_c = P' S_f P, one phase at
-// a time (phase-major arrays).
+// Galerkin product of a stored 7-point operator: S_c = P' S_f P, one thread
+// per (coarse node, phase) (phase = blockIdx.z; phase-major arrays).
 template <typename T, int N>
 __global__ void __launch_bounds__(kBlock) k_galerkin(const T *__restrict__ opf, Geo gf, Geo gc, T *__restrict__ opc) {
-  const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
+  const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y, i = blockIdx.z;
   if (X > gc.W) return;
   const int64_t nf = (int64_t)gf.Wn * (gf.H + 1), nc = (int64_t)gc.Wn * (gc.H + 1);
   const int64_t K = (int64_t)Y * gc.Wn + X;
-  const bool interior = X >= 1 && X <= gc.W - 1 && Y >= 1 && Y <= gc.H - 1;
-#pragma unroll 1
-  for (int i = 0; i < N; ++i) {
-    T c4[4] = {T(0), T(0), T(0), T(0)};
-    if (interior)
-      galerkin_phase<T, N, true>(opf, gf, gc, nf, X, Y, i, c4);
-    else
-      galerkin_phase<T, N, false>(opf, gf, gc, nf, X, Y, i, c4);
+  T c4[4] = {T(0), T(0), T(0), T(0)};
+  if (X >= 1 && X <= gc.W - 1 && Y >= 1 && Y <= gc.H - 1)
+    galerkin_phase<T, N, true>(opf, gf, gc, nf, X, Y, i, c4);
+  else
+    galerkin_phase<T, N, false>(opf, gf, gc, nf, X, Y, i, c4);
 #pragma unroll
-    for (int l = 0; l < 4; ++l) opc[(l * N + i) * nc + K] = c4[l];
-  }
+  for (int l = 0; l < 4; ++l) opc[(l * N + i) * nc + K] = c4[l];
 }
 
 // (S v)_K - S_KK v_K for phase i of a stored operator (phase-major arrays).
@@ -761,41 +772,39 @@ __device__ __forceinline__ T op_offdiag(const T *op, const T *v, const Geo &g, i
 // l1 = sum_j |S_Kj| (convergent for any symmetric positive definite S; one
 // coalesced launch per sweep).  Rows with a zero diagonal stay 0.  ZERO_IN:
 // vin = 0 (the first sweep of a V-cycle level), so vout = r / l1 and vin is
-// not read.  Interior nodes take a branch-free copy of the same arithmetic so
-// that the loads of all phases can be in flight together.
-template <typename T, int N, bool ZERO_IN, bool INTERIOR>
-__device__ __forceinline__ void jacobi_node(const T *__restrict__ op, const T *__restrict__ r,
-                                            const T *__restrict__ vin, T *__restrict__ vout, const Geo &g, int64_t nc,
-                                            int x, int y) {
+// not read.  One thread per (node, phase) (phase = blockIdx.z): the phases of
+// a coarse level are independent systems.  Interior nodes take a branch-free
+// copy of the same arithmetic.
+template <typename T, bool ZERO_IN, bool INTERIOR>
+__device__ __forceinline__ void jacobi_node(const T *__restrict__ d_, const T *__restrict__ oE,
+                                            const T *__restrict__ oN, const T *__restrict__ oNE,
+                                            const T *__restrict__ r, const T *__restrict__ vi, T *__restrict__ vout,
+                                            const Geo &g, int x, int y) {
   const int64_t K = (int64_t)y * g.Wn + x;
   const bool e = INTERIOR || x < g.W, w = INTERIOR || x > 0, nn = INTERIOR || y < g.H, ss = INTERIOR || y > 0;
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const T *oE = op + (1 * N + i) * nc, *oN = op + (2 * N + i) * nc, *oNE = op + (3 * N + i) * nc;
-    const T *vi = vin + i * nc;
-    const T d = op[i * nc + K];
-    T sv = ZERO_IN ? T(0) : d * vi[K], l1 = fabs(d), c;
-    if (e) { c = oE[K]; if (!ZERO_IN) sv += c * vi[K + 1]; l1 += fabs(c); }
-    if (w) { c = oE[K - 1]; if (!ZERO_IN) sv += c * vi[K - 1]; l1 += fabs(c); }
-    if (nn) { c = oN[K]; if (!ZERO_IN) sv += c * vi[K + g.Wn]; l1 += fabs(c); }
-    if (ss) { c = oN[K - g.Wn]; if (!ZERO_IN) sv += c * vi[K - g.Wn]; l1 += fabs(c); }
-    if (e && nn) { c = oNE[K]; if (!ZERO_IN) sv += c * vi[K + g.Wn + 1]; l1 += fabs(c); }
-    if (w && ss) { c = oNE[K - g.Wn - 1]; if (!ZERO_IN) sv += c * vi[K - g.Wn - 1]; l1 += fabs(c); }
-    const T v0 = ZERO_IN ? T(0) : vi[K];
-    vout[i * nc + K] = d > T(0) ? v0 + (r[i * nc + K] - sv) / l1 : T(0);
-  }
+  const T d = d_[K];
+  T sv = ZERO_IN ? T(0) : d * vi[K], l1 = fabs(d), c;
+  if (e) { c = oE[K]; if (!ZERO_IN) sv += c * vi[K + 1]; l1 += fabs(c); }
+  if (w) { c = oE[K - 1]; if (!ZERO_IN) sv += c * vi[K - 1]; l1 += fabs(c); }
+  if (nn) { c = oN[K]; if (!ZERO_IN) sv += c * vi[K + g.Wn]; l1 += fabs(c); }
+  if (ss) { c = oN[K - g.Wn]; if (!ZERO_IN) sv += c * vi[K - g.Wn]; l1 += fabs(c); }
+  if (e && nn) { c = oNE[K]; if (!ZERO_IN) sv += c * vi[K + g.Wn + 1]; l1 += fabs(c); }
+  if (w && ss) { c = oNE[K - g.Wn - 1]; if (!ZERO_IN) sv += c * vi[K - g.Wn - 1]; l1 += fabs(c); }
+  const T v0 = ZERO_IN ? T(0) : vi[K];
+  vout[K] = d > T(0) ? v0 + (r[K] - sv) / l1 : T(0);
 }
 
 template <typename T, int N, bool ZERO_IN>
 __global__ void k_coarse_jacobi(const T *__restrict__ op, const T *__restrict__ r, const T *__restrict__ vin,
                                 T *__restrict__ vout, Geo g) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, i = blockIdx.z;
   if (x > g.W) return;
   const int64_t nc = (int64_t)g.Wn * (g.H + 1);
+  const T *d = op + i * nc, *oE = op + (1 * N + i) * nc, *oN = op + (2 * N + i) * nc, *oNE = op + (3 * N + i) * nc;
   if (x > 0 && x < g.W && y > 0 && y < g.H)
-    jacobi_node<T, N, ZERO_IN, true>(op, r, vin, vout, g, nc, x, y);
+    jacobi_node<T, ZERO_IN, true>(d, oE, oN, oNE, r + i * nc, vin + i * nc, vout + i * nc, g, x, y);
   else
-    jacobi_node<T, N, ZERO_IN, false>(op, r, vin, vout, g, nc, x, y);
+    jacobi_node<T, ZERO_IN, false>(d, oE, oN, oNE, r + i * nc, vin + i * nc, vout + i * nc, g, x, y);
 }
 
 // Whole-level Gauss-Seidel in one block for small coarsest grids: `sweeps`
@@ -851,33 +860,29 @@ __global__ void __launch_bounds__(1024) k_coarse_solve_smem(const T *__restrict_
   for (int t = threadIdx.x; t < N * nc; t += blockDim.x) v[t] = sv[t];
 }
 
-// t = r - S v on a coarse level (interior nodes branch-free, as in
-// k_coarse_jacobi; the same arithmetic and order as op_offdiag).
+// t = r - S v on a coarse level, one thread per (node, phase) (interior
+// nodes branch-free, as in k_coarse_jacobi; the same arithmetic and order as
+// op_offdiag).
 template <typename T, int N>
 __global__ void k_coarse_resid(const T *__restrict__ op, const T *__restrict__ r, const T *__restrict__ v, Geo g,
                                T *__restrict__ t) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, i = blockIdx.z;
   if (x > g.W) return;
   const int64_t nc = (int64_t)g.Wn * (g.H + 1), K = (int64_t)y * g.Wn + x;
   if (x > 0 && x < g.W && y > 0 && y < g.H) {
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const T *oE = op + (1 * N + i) * nc, *oN = op + (2 * N + i) * nc, *oNE = op + (3 * N + i) * nc;
-      const T *vi = v + i * nc;
-      T s = T(0);
-      s += oE[K] * vi[K + 1];
-      s += oE[K - 1] * vi[K - 1];
-      s += oN[K] * vi[K + g.Wn];
-      s += oN[K - g.Wn] * vi[K - g.Wn];
-      s += oNE[K] * vi[K + g.Wn + 1];
-      s += oNE[K - g.Wn - 1] * vi[K - g.Wn - 1];
-      t[i * nc + K] = r[i * nc + K] - op[i * nc + K] * vi[K] - s;
-    }
+    const T *oE = op + (1 * N + i) * nc, *oN = op + (2 * N + i) * nc, *oNE = op + (3 * N + i) * nc;
+    const T *vi = v + i * nc;
+    T s = T(0);
+    s += oE[K] * vi[K + 1];
+    s += oE[K - 1] * vi[K - 1];
+    s += oN[K] * vi[K + g.Wn];
+    s += oN[K - g.Wn] * vi[K - g.Wn];
+    s += oNE[K] * vi[K + g.Wn + 1];
+    s += oNE[K - g.Wn - 1] * vi[K - g.Wn - 1];
+    t[i * nc + K] = r[i * nc + K] - op[i * nc + K] * vi[K] - s;
     return;
   }
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-    t[i * nc + K] = r[i * nc + K] - op[i * nc + K] * v[i * nc + K] - op_offdiag<T, N>(op, v, g, nc, x, y, i);
+  t[i * nc + K] = r[i * nc + K] - op[i * nc + K] * v[i * nc + K] - op_offdiag<T, N>(op, v, g, nc, x, y, i);
 }
 
 // P1 prolongation of phase-major coarse values to fine node (x, y) (nested
@@ -894,16 +899,18 @@ __device__ __forceinline__ void prolong_at(const T *vc, const Geo &gc, int x, in
   for (int i = 0; i < N; ++i) o[i] = T(0.5) * (o[i] + vc[i * nc + K1]);
 }
 
-// v_f += P v_c (coarse levels, phase-major).
+// v_f += P v_c (coarse levels, phase-major; one thread per (node, phase),
+// the arithmetic of prolong_at).
 template <typename T, int N>
 __global__ void k_prolong_add(const T *__restrict__ vc, Geo gf, Geo gc, T *__restrict__ vf) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, i = blockIdx.z;
   if (x > gf.W) return;
-  T p[N];
-  prolong_at<T, N>(vc, gc, x, y, p);
-  const int64_t nf = (int64_t)gf.Wn * (gf.H + 1), a = (int64_t)y * gf.Wn + x;
-#pragma unroll
-  for (int i = 0; i < N; ++i) vf[i * nf + a] += p[i];
+  const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), nf = (int64_t)gf.Wn * (gf.H + 1);
+  const T *vi = vc + i * nc;
+  const int64_t K0 = (int64_t)(y >> 1) * gc.Wn + (x >> 1);
+  T p = vi[K0];
+  if ((x & 1) || (y & 1)) p = T(0.5) * (p + vi[K0 + (x & 1) + (int64_t)(y & 1) * gc.Wn]);
+  vf[i * nf + (int64_t)y * gf.Wn + x] += p;
 }
 
 // ---------------------------------------------------------------------------
@@ -922,7 +929,7 @@ __global__ void __launch_bounds__(kBlock) k_ls_dir(const T *__restrict__ x, cons
                                                    const uint8_t *__restrict__ mask, Geo gf, Geo gc,
                                                    T *__restrict__ d, double *__restrict__ part) {
   const int xx = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-  double dot[1] = {0.0};
+  T dot = T(0);
   if (xx <= gf.W) {
     const int64_t n = (int64_t)y * gf.Wn + xx, sl = fslot<T>(gf, xx, y);
     const unsigned fr = mask[n];
@@ -951,31 +958,31 @@ __global__ void __launch_bounds__(kBlock) k_ls_dir(const T *__restrict__ x, cons
         dn[i] = w[i] - xk[i];
         loc += r[i] * dn[i];
       }
-      dot[0] = (double)loc;
+      dot = loc;
     } else {
 #pragma unroll
       for (int i = 0; i < N; ++i) dn[i] = T(0);
     }
     stn<T, N>(d + sl * N, dn);
   }
-  block_sum_store<1>(dot, part + blockIdx.y * gridDim.x + blockIdx.x);
+  block_sum_store1<T>(dot, part + blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 template <typename T, int N>
 __global__ void __launch_bounds__(kBlock) k_ls_curv(const T *__restrict__ d, Geo g, double *__restrict__ part) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-  double dot[1] = {0.0};
+  T dot = T(0);
   if (x <= g.W) {
     T acc[N], dk[N];
     nbr_sum<T, N>(d, g, x, y, acc);
     ldn<T, N>(d + fslot<T>(g, x, y) * N, dk);
-    const T D = (T)g.D[node_class(g, x, y)], te = (T)g.te;
+    const T D = geo_D<T>(g, node_class(g, x, y)), te = geo_te<T>(g);
     T loc = T(0);
 #pragma unroll
     for (int i = 0; i < N; ++i) loc += dk[i] * (D * dk[i] - te * acc[i]);
-    dot[0] = (double)loc;
+    dot = loc;
   }
-  block_sum_store<1>(dot, part + blockIdx.y * gridDim.x + blockIdx.x);
+  block_sum_store1<T>(dot, part + blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 static __global__ void k_ls_finish(const double *__restrict__ tot, double *__restrict__ omega) {
@@ -983,7 +990,8 @@ static __global__ void k_ls_finish(const double *__restrict__ tot, double *__res
   const double rd = tot[0], dsd = tot[1];
   double w = 0.0;
   if (dsd > 0.0 && rd > 0.0) w = fmin(1.0, rd / dsd);
-  *omega = w;
+  omega[0] = w;
+  reinterpret_cast<float *>(omega + 1)[0] = (float)w;
 }
 
 // ---------------------------------------------------------------------------

@@ -11,6 +11,17 @@ inline dim3 row_grid(int count_per_row, int rows, int block = kBlock) {
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
+// One thread per (node, phase) of a coarse level: rows of count_per_row
+// nodes, the phase in blockIdx.z; narrow levels get narrower blocks.
+struct PhaseLaunch {
+  dim3 grid;
+  unsigned block;
+};
+inline PhaseLaunch phase_grid(int count_per_row, int rows, int phases) {
+  const unsigned b = count_per_row >= kBlock ? (unsigned)kBlock : (unsigned)(((count_per_row + 31) / 32) * 32);
+  return {dim3((unsigned)((count_per_row + (int)b - 1) / (int)b), (unsigned)rows, (unsigned)phases), b};
+}
+
 template <typename T, int N, int FORM>
 struct SolverLaunch {
   // `sweeps` red-black sweeps in place, one launch per colour; the pending
@@ -40,19 +51,20 @@ struct SolverLaunch {
     return 1;
   }
   static int galerkin(const void *opf, const Geo &gf, const Geo &gc, void *opc, cudaStream_t s) {
-    k_galerkin<T, N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>((const T *)opf, gf, gc, (T *)opc);
+    const PhaseLaunch L = phase_grid(gc.W + 1, gc.H + 1, N);
+    k_galerkin<T, N><<<L.grid, L.block, 0, s>>>((const T *)opf, gf, gc, (T *)opc);
     return 1;
   }
   static int coarse_smooth(const void *op, const void *r, void *v, void *tmp, const Geo &g, int sweeps,
                            bool zero_start, cudaStream_t s) {
-    const dim3 grid = row_grid(g.W + 1, g.H + 1);
+    const PhaseLaunch L = phase_grid(g.W + 1, g.H + 1, N);
     for (int k = 0; k < sweeps; ++k) {
       const T *in = (const T *)(k % 2 == 0 ? v : tmp);
       T *out = (T *)(k % 2 == 0 ? tmp : v);
       if (k == 0 && zero_start)
-        k_coarse_jacobi<T, N, true><<<grid, kBlock, 0, s>>>((const T *)op, (const T *)r, in, out, g);
+        k_coarse_jacobi<T, N, true><<<L.grid, L.block, 0, s>>>((const T *)op, (const T *)r, in, out, g);
       else
-        k_coarse_jacobi<T, N, false><<<grid, kBlock, 0, s>>>((const T *)op, (const T *)r, in, out, g);
+        k_coarse_jacobi<T, N, false><<<L.grid, L.block, 0, s>>>((const T *)op, (const T *)r, in, out, g);
     }
     return sweeps;
   }
@@ -68,16 +80,18 @@ struct SolverLaunch {
     return 1;
   }
   static int coarse_resid(const void *op, const void *r, const void *v, const Geo &g, void *t, cudaStream_t s) {
-    k_coarse_resid<T, N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>((const T *)op, (const T *)r, (const T *)v,
-                                                                       g, (T *)t);
+    const PhaseLaunch L = phase_grid(g.W + 1, g.H + 1, N);
+    k_coarse_resid<T, N><<<L.grid, L.block, 0, s>>>((const T *)op, (const T *)r, (const T *)v, g, (T *)t);
     return 1;
   }
   static int restrict_(const void *t, const Geo &gf, const Geo &gc, void *rc, cudaStream_t s) {
-    k_restrict<T, N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>((const T *)t, gf, gc, (T *)rc);
+    const PhaseLaunch L = phase_grid(gc.W + 1, gc.H + 1, N);
+    k_restrict<T, N><<<L.grid, L.block, 0, s>>>((const T *)t, gf, gc, (T *)rc);
     return 1;
   }
   static int prolong_add(const void *vc, const Geo &gf, const Geo &gc, void *vf, cudaStream_t s) {
-    k_prolong_add<T, N><<<row_grid(gf.W + 1, gf.H + 1), kBlock, 0, s>>>((const T *)vc, gf, gc, (T *)vf);
+    const PhaseLaunch L = phase_grid(gf.W + 1, gf.H + 1, N);
+    k_prolong_add<T, N><<<L.grid, L.block, 0, s>>>((const T *)vc, gf, gc, (T *)vf);
     return 1;
   }
   static int line_search(const void *x, const void *ob, const void *rt, const void *v1, const uint8_t *mask,
