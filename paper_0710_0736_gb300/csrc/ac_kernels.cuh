@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(kBlock) k_means_partial(const double *__restri
   for (int k = 0; k < Q * N; ++k) acc[k] = 0.0;
   const int64_t n = (int64_t)g.Wn * (g.H + 1);
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(k % g.Wn), y = (int)(k / g.Wn);
+    const unsigned k32 = (unsigned)k;  // n <= 2^31: 32-bit division suffices
+    const int x = (int)(k32 % (unsigned)g.Wn), y = (int)(k32 / (unsigned)g.Wn);
     const double m0 = g.m0[node_class(g, x, y)];
     double uk[N];
     ldn<double, N>(u + k * N, uk);
@@ -255,20 +256,30 @@ __global__ void k_means_finish(const double *__restrict__ tot, double *__restric
 template <int N>
 __global__ void k_rhs(const double *__restrict__ u, const double *__restrict__ mom, const double *__restrict__ c, Geo g,
                       double a1, double tl, double *__restrict__ b) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t n = (int64_t)g.Wn * (g.H + 1);
-  if (k >= n) return;
-  const int x = (int)(k % g.Wn), y = (int)(k / g.Wn);
+  // per phase, once per block: 2 tau lambda c_i (RGB) and tau lambda |c_i|^2,
+  // so that b_i = a1 m0 u_i - tau lambda m2 + (2 tau lambda c_i).m1
+  //             - (tau lambda |c_i|^2) m0
+  __shared__ double coef[N][4];
+  if (threadIdx.x < N) {
+    const int i = threadIdx.x;
+    const double c0 = c[i * 3], c1 = c[i * 3 + 1], c2 = c[i * 3 + 2];
+    coef[i][0] = 2.0 * tl * c0;
+    coef[i][1] = 2.0 * tl * c1;
+    coef[i][2] = 2.0 * tl * c2;
+    coef[i][3] = tl * (c0 * c0 + c1 * c1 + c2 * c2);
+  }
+  __syncthreads();
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x > g.W) return;
+  const int64_t k = (int64_t)y * g.Wn + x;
   const double m0 = g.m0[node_class(g, x, y)];
   const double4 m = ld_mom(mom + k * 4);
   double uk[N], bk[N];
   ldn<double, N>(u + k * N, uk);
+  const double base = -tl * m.w, am0 = a1 * m0;
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const double c0 = c[i * 3], c1 = c[i * 3 + 1], c2 = c[i * 3 + 2];
-    const double f = m.w - 2.0 * (c0 * m.x + c1 * m.y + c2 * m.z) + (c0 * c0 + c1 * c1 + c2 * c2) * m0;
-    bk[i] = m0 * uk[i] * a1 - tl * f;
-  }
+  for (int i = 0; i < N; ++i)
+    bk[i] = fma(am0, uk[i], base + coef[i][0] * m.x + coef[i][1] * m.y + coef[i][2] * m.z - coef[i][3] * m0);
   stn<double, N>(b + k * N, bk);
 }
 
@@ -320,11 +331,14 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
     stn<float, N>(r32 + sl * N, rf);
     stn<float, N>(u32 + sl * N, uf);
     if constexpr (RHO32) {
-      // the same projection in float on the rounded data: off by at most a
-      // few float ulps of u (the caller widens tol by that margin)
+      // the same projection in float on the rounded, shifted data: near the
+      // solution the free components' z and theta are O(rho) and a component
+      // on its bound has u_i <= rho, so the float result is within a few
+      // float ulps of rho itself (the caller keeps a relative margin)
       float zf[N];
+      const float invDf = g.invDf[cls];
 #pragma unroll
-      for (int i = 0; i < N; ++i) zf[i] = (float)z[i];
+      for (int i = 0; i < N; ++i) zf[i] = rf[i] * invDf;
       proj_box<float, N, kShifted>(zf, uf);
       float ef = 0.f;
 #pragma unroll
@@ -335,8 +349,9 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
       // conditions on that set in FP64 (one pass instead of the iteration);
       // the full FP64 iteration only where the conditions fail (near ties)
       float zf[N];
+      const float invDf = g.invDf[cls];
 #pragma unroll
-      for (int i = 0; i < N; ++i) zf[i] = (float)z[i];
+      for (int i = 0; i < N; ++i) zf[i] = rf[i] * invDf;
       const unsigned keep = shifted_free_set<float, N>(zf, uf);
       if (!shifted_proj_on_set<N>(z, uk, keep)) proj_box<double, N, kShifted>(z, uk);
 #pragma unroll

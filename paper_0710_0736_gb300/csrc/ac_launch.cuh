@@ -145,7 +145,7 @@ struct Launch {
   }
   static int rhs(const double *u, const double *mom, const double *c, const Geo &g, double a1, double tl, double *b,
                  cudaStream_t s) {
-    k_rhs<N><<<blocks_for((int64_t)g.Wn * (g.H + 1)), kBlock, 0, s>>>(u, mom, c, g, a1, tl, b);
+    k_rhs<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, mom, c, g, a1, tl, b);
     return 1;
   }
   static int outer_resid(const double *u, const double *b, const Geo &g, float *r32, float *u32, double *rho,
