@@ -3,8 +3,10 @@
 
 Workload (default): the 4096 x 4096 RGB Voronoi-ramp image (8 regions, ramps
 <= 0.2, noise sigma 0.05), N = 8 phases, eps = 3, lambda = 2, tau = 9, each
-time step solved to a natural residual of 1e-6.  A "step" is one time step:
-colour means + energy, right-hand side, and V-cycles until the tolerance.
+time step solved to a natural residual of 1e-6 by V(3,3) cycles; 3 untimed
+steps, then the 100 time steps of the workload timed.  A "step" is one time
+step: colour means + energy, right-hand side, and V-cycles until the
+tolerance.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
   python bench.py --impl reference ...   # the CPU oracle on the same workload
@@ -38,7 +40,9 @@ WORKLOAD = "c3_4096_n8_mixed"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 100 time steps of the 4096^2 workload, 30 image steps of the batch, "
+                         "4 gradient evaluations of the adjoint)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
@@ -46,8 +50,8 @@ def parse():
                     help="steps of the plain FP64 form timed for the vs-FP64 ratio (0: skip)")
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--tol", type=float, default=None)
-    ap.add_argument("--nu1", type=int, default=2, help="pre-smoothing red-black sweeps per V-cycle")
-    ap.add_argument("--nu2", type=int, default=2, help="post-smoothing red-black sweeps per V-cycle")
+    ap.add_argument("--nu1", type=int, default=3, help="pre-smoothing red-black sweeps per V-cycle")
+    ap.add_argument("--nu2", type=int, default=3, help="post-smoothing red-black sweeps per V-cycle")
     ap.add_argument("--crop", type=int, default=256, help="side of the image crop the CPU oracle times")
     ap.add_argument("--cpu-steps", type=int, default=3, help="oracle steps in the cpu_baseline sample")
     ap.add_argument("--workload", choices=["single", "batch", "adjoint"], default="single",
@@ -60,7 +64,10 @@ def parse():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = {"single": 100, "batch": 30, "adjoint": 4}[args.workload]
+    return args
 
 
 def workload(args):
@@ -76,7 +83,7 @@ def workload_config(cfg, args, extra=None):
     d = {
         "workload": f"{cfg['W']}x{cfg['H']} RGB Voronoi-ramp image (8 regions, ramp<=0.2, noise 0.05), "
                     f"N={cfg['N']}, eps={cfg['eps']}, lambda={cfg['lam']}, tau={cfg['tau']}, "
-                    f"V({args.nu1},{args.nu2}) to natural residual {cfg['tol']:g}",
+                    f"each step to natural residual {cfg['tol']:g}",
         "nodes": (cfg["W"] + 1) * (cfg["H"] + 1),
         "n_phases": cfg["N"],
         "precision": args.precision,
@@ -207,6 +214,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     cfg = workload(args)
+    # each step a bounded sample: the crop shrinks when many steps are asked
+    # for, so that the whole run stays within a few minutes
+    if args.warmup + args.steps > 20:
+        args.crop = min(args.crop, 128)
     times = oracle_sample(cfg, args.crop, args.warmup + args.steps)
     timed = times[args.warmup:]
     full_nodes = (cfg["W"] + 1) * (cfg["H"] + 1)
@@ -218,7 +229,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_full * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(cfg, args, {"precision": "fp64"}),
+            "config": workload_config(cfg, args, {"precision": "fp64",
+                                                  "solver": "oracle: sequential SSC over all levels, V(2,2), FP64"}),
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -536,7 +548,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
                 "data": "synthetic",
-                "config": workload_config(cfg, args, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+                "config": workload_config(cfg, args, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                                                      "solver": f"truncated monotone multigrid V({args.nu1},{args.nu2})"}),
                 "gdof_per_s": gdof, "vcycles_per_step": st.total_cycles / max(1, st.steps),
                 "fine_sweeps_per_step": st.fine_sweeps / max(1, st.steps), "residual": st.residual,
                 "outer_per_step": st.outer / max(1, st.steps), "plain_fp64_gpu": fp64,

@@ -73,7 +73,8 @@ typedef struct {
                           AC_MIXED: FP64 state u, right-hand side, colour means, energy and
                           residual r = b - S u (defect correction); the correction delta is
                           solved by the same multigrid in FP32 with obstacle -u and the
-                          natural residual is checked in FP64; the image is rounded to
+                          natural residual is checked in float on the FP64 residual
+                          shifted per node by its maximum; the image is rounded to
                           bfloat16 on input (ac_set_image only). */
   uint64_t seed;       /* seed of the random simplex initialisation in ac_set_image */
   void *stream;        /* cudaStream_t for all work of this context */

@@ -146,7 +146,13 @@ struct Solve {
   GraphSlot smooth_resid[2][2], correction[2];
 };
 
-constexpr int kCoarseSweeps = 2;     // pre/post l1-Jacobi sweeps on coarse levels (even)
+// Pre/post l1-Jacobi sweeps on coarse levels (even); a build option
+// (-DAC_COARSE_SWEEPS=k) for tuning.
+#ifndef AC_COARSE_SWEEPS
+#define AC_COARSE_SWEEPS 2
+#endif
+constexpr int kCoarseSweeps = AC_COARSE_SWEEPS;
+static_assert(kCoarseSweeps >= 2 && kCoarseSweeps % 2 == 0, "coarse sweeps: an even count >= 2");
 constexpr int kCoarsestSweeps = 20;  // sweeps of the one-block coarsest solve
 constexpr int64_t kCoarsestBlockNodes = 1 << 14;
 constexpr double kInnerReduction = 1e-5;  // AC_MIXED: inner FP32 solve to max(tol/2, 1e-5 rho_outer) ...
