@@ -143,8 +143,8 @@ class Clocks:
 # 4,198,401 nodes (profiles/k_smooth_fine_mixed_2048_n8_ncu.md), scaled to
 # the workload by nodes.  It holds for the kernel source it was taken on: the
 # digest covers the kernel's text and that of the device helpers it calls.
-SMOOTH_TRAFFIC = {"sha256": "4da6d4ac883148f37377e2fee18e4f08c53fcf242e415140d8cac439514c1e3d",
-                  "bytes_per_node": (201.545e6 + 47.188e6) / 4198401, "n_phases": 8, "precision": "mixed"}
+SMOOTH_TRAFFIC = {"sha256": "318a4651c615373ac2df954c0c3827a00bc82a0795abac18fe55f2b9d398ed73",
+                  "bytes_per_node": (201.545e6 + 47.03e6) / 4198401, "n_phases": 8, "precision": "mixed"}
 SMOOTH_HELPERS = ("node_class", "edge_weights", "fslot", "geo_te", "geo_invD", "omega_t", "rcp_small", "proj_box",
                   "nbr_sum", "ldn", "ldn_rw", "stn")
 

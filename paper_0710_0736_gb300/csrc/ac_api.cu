@@ -449,9 +449,17 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
     const int nsw = later ? ctx->p.nu1 + ctx->p.nu2 : ctx->p.nu1;
     const void *corr = (later && coarse) ? S.d : nullptr;
     int rc = run_graph(ctx, S.smooth_resid[prof][later], [&]() -> int {
-      AC_RUN(AC_PROF_SMOOTH, o->smooth(S.x, S.rhs, S.ob, corr, ctx->omega, g0, nsw, ctx->s));
+      // after at least one sweep the last pass completes its colour's mask
+      // (its tangent residual is 0), and the residual kernel visits the other
+      // colour only.  Those rt slots hold zeros: cleared at allocation and
+      // written by nothing else unless nu1 = 0 lets a first cycle take the
+      // every-node residual, in which case the last pass re-zeroes them.
+      const bool fused = nsw >= 1;
+      void *rt_zero = (fused && ctx->p.nu1 == 0) ? S.rt : nullptr;
+      AC_RUN(AC_PROF_SMOOTH, o->smooth(S.x, S.rhs, S.ob, corr, ctx->omega, g0, nsw, rt_zero,
+                                       fused ? S.mask : nullptr, ctx->s));
       AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
-      AC_RUN(AC_PROF_RESID, o->resid(S.x, S.rhs, S.ob, g0, S.rt, S.mask, ctx->rho, ctx->s));
+      AC_RUN(AC_PROF_RESID, o->resid(S.x, S.rhs, S.ob, g0, S.rt, S.mask, ctx->rho, fused ? 0 : -1, ctx->s));
       return AC_OK;
     });
     if (rc) return rc;
@@ -677,6 +685,7 @@ int ac_create(ac_ctx **out, const ac_params *p) {
     AC_CUDA(cudaMallocHost(&ctx->h_scalars, 4 * sizeof(double)));
     AC_CUDA(cudaMemsetAsync(ctx->c, 0, (size_t)3 * N * sizeof(double), ctx->s));
     AC_CUDA(cudaMemsetAsync(ctx->omega, 0, 2 * sizeof(double), ctx->s));
+    AC_CUDA(cudaMemsetAsync(S.rt, 0, fNs, ctx->s));  // second-colour slots stay 0 (see solve_mg)
     return AC_OK;
   };
   rc = body();
@@ -907,7 +916,8 @@ int ac_residual(ac_ctx *ctx, double *rho) {
     AC_RUN(AC_PROF_OUTER,
            ctx->ops->outer_resid(ctx->u, ctx->b, ctx->g0, ctx->r32, ctx->u32, ctx->rho, false, ctx->s));
   else
-    AC_RUN(AC_PROF_RESID, ctx->ops->fp64.resid(ctx->u, ctx->b, nullptr, ctx->g0, nullptr, nullptr, ctx->rho, ctx->s));
+    AC_RUN(AC_PROF_RESID,
+           ctx->ops->fp64.resid(ctx->u, ctx->b, nullptr, ctx->g0, nullptr, nullptr, ctx->rho, -1, ctx->s));
   return read_rho(ctx, rho);
 }
 
@@ -1028,6 +1038,7 @@ int adj_setup(ac_ctx *ctx, int T, int every) {
   ADJ_ALLOC(S.rt, fN);
   ADJ_ALLOC(S.d, fN);
   ADJ_ALLOC(S.mask, (size_t)ctx->n);
+  AC_CUDA(cudaMemsetAsync(S.rt, 0, fN, ctx->s));  // second-colour slots stay 0 (see solve_mg)
   return AC_OK;
 }
 

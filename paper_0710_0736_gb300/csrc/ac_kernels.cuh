@@ -425,14 +425,17 @@ __global__ void k_outer_update(double *__restrict__ u, const float *__restrict__
 // color are independent given the other colour:
 //   z_n = (rhs_n + tau eps sum_m w_nm x_m) / S_nn,   x_n <- P(z_n).
 // ---------------------------------------------------------------------------
+// MASK: the last pass of a smoothing sequence (its own instantiation, so the
+// other passes keep their register budget).
 // With corr != null (first colour of the first sweep after a coarse
 // correction) the neighbours are read as x + omega d: that is exactly the
 // pending update x += omega d, because this pass overwrites its own colour
 // and the next pass overwrites the other one without reading old values.
-template <typename T, int N, int FORM>
+template <typename T, int N, int FORM, bool MASK>
 __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const T *__restrict__ rhs,
                                                         const T *__restrict__ ob, const T *__restrict__ corr,
-                                                        const double *__restrict__ omega, Geo g, int color) {
+                                                        const double *__restrict__ omega, Geo g, int color,
+                                                        T *__restrict__ rt, uint8_t *__restrict__ mask) {
   const int y = blockIdx.y;
   const int xx = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((y + color) & 1);
   if (xx > g.W) return;
@@ -456,22 +459,49 @@ __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const
   for (int i = 0; i < N; ++i) acc[i] = (bk[i] + te * acc[i]) * invD;
   proj_box<T, N, FORM>(acc, o);
   stn<T, N>(x + n * N, acc);
+  if constexpr (MASK) {
+    // last pass of a smoothing sequence: this node's nodal problem is solved
+    // exactly, so its natural residual is 0 and its residual is constant on
+    // the free phases (tangent part 0); store the free mask (and rt = 0 when
+    // rt != null) here, and k_fine_resid visits the other colour only
+    int cnt = 0;
+    unsigned pos = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const bool fr = FORM == kTangent ? o[i] != T(0) : acc[i] > (FORM == kShifted ? -o[i] : T(0));
+      if (fr) {
+        pos |= 1u << i;
+        ++cnt;
+      }
+    }
+    mask[(int64_t)y * g.Wn + xx] = (uint8_t)(cnt >= 2 ? pos : 0u);
+    if (rt) {
+      T z[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) z[i] = T(0);
+      stn<T, N>(rt + n * N, z);
+    }
+  }
 }
-
 // ---------------------------------------------------------------------------
 // a6/a9: fine residual r = rhs - S x, natural residual rho = max |x - P(z)|
 // (z = x + r/S_nn), free-phase mask and the tangent projection of r:
 //   free_n,i = x_n,i above its bound, and at least two phases of node n free;
 //   rt_n,i   = r_n,i - mean_{free j} r_n,j for free i, 0 otherwise.
 // A node at a vertex of the simplex has no free phase.  rt and mask may be
-// null (residual only).
+// null (residual only).  After a red-black smoothing sequence only the first
+// colour needs this kernel: see k_smooth_fine.
 // ---------------------------------------------------------------------------
 template <typename T, int N, int FORM>
 __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, const T *__restrict__ rhs,
                                                        const T *__restrict__ ob, Geo g, T *__restrict__ rt,
-                                                       uint8_t *__restrict__ mask, double *__restrict__ rho) {
-  const int xx = blockIdx.x * blockDim.x + threadIdx.x;
+                                                       uint8_t *__restrict__ mask, double *__restrict__ rho,
+                                                       int color) {
+  // color < 0: every node; color 0 or 1: the nodes of that colour only (the
+  // other colour's share was stored by the last smoothing pass)
   const int y = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int xx = color < 0 ? t : 2 * t + ((y + color) & 1);
   T e = T(0);
   if (xx <= g.W) {
     const int64_t n = (int64_t)y * g.Wn + xx, sl = fslot<T>(g, xx, y);
@@ -914,18 +944,27 @@ __device__ __forceinline__ void prolong_at(const T *vc, const Geo &gc, int x, in
   for (int i = 0; i < N; ++i) o[i] = T(0.5) * (o[i] + vc[i * nc + K1]);
 }
 
-// v_f += P v_c (coarse levels, phase-major; one thread per (node, phase),
-// the arithmetic of prolong_at).
-template <typename T, int N>
+// v_f += P v_c (coarse levels, phase-major), the arithmetic of prolong_at.
+// PHASES_IN_Z: one thread per (node, phase), phase = blockIdx.z (narrow
+// levels, where latency dominates); otherwise one thread per node doing all
+// phases (wide levels, fewer blocks for the same bytes).
+template <typename T, int N, bool PHASES_IN_Z>
 __global__ void k_prolong_add(const T *__restrict__ vc, Geo gf, Geo gc, T *__restrict__ vf) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, i = blockIdx.z;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x > gf.W) return;
   const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), nf = (int64_t)gf.Wn * (gf.H + 1);
-  const T *vi = vc + i * nc;
-  const int64_t K0 = (int64_t)(y >> 1) * gc.Wn + (x >> 1);
-  T p = vi[K0];
-  if ((x & 1) || (y & 1)) p = T(0.5) * (p + vi[K0 + (x & 1) + (int64_t)(y & 1) * gc.Wn]);
-  vf[i * nf + (int64_t)y * gf.Wn + x] += p;
+  const int64_t K0 = (int64_t)(y >> 1) * gc.Wn + (x >> 1), a = (int64_t)y * gf.Wn + x;
+  const bool mid = (x & 1) || (y & 1);
+  const int64_t K1 = K0 + (x & 1) + (int64_t)(y & 1) * gc.Wn;
+  constexpr int I = PHASES_IN_Z ? 1 : N;
+#pragma unroll
+  for (int j = 0; j < I; ++j) {
+    const int i = PHASES_IN_Z ? (int)blockIdx.z : j;
+    const T *vi = vc + i * nc;
+    T p = vi[K0];
+    if (mid) p = T(0.5) * (p + vi[K1]);
+    vf[i * nf + a] += p;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -983,19 +1022,35 @@ __global__ void __launch_bounds__(kBlock) k_ls_dir(const T *__restrict__ x, cons
   block_sum_store1<T>(dot, part + blockIdx.y * gridDim.x + blockIdx.x);
 }
 
+// d'Sd = sum_n S_nn |d_n|^2 - 2 tau eps sum over axis edges (n, m) of
+// w_nm d_n . d_m, each edge counted once at its west / south end: three
+// node reads per thread (own, east, north) instead of the five of S d.
 template <typename T, int N>
 __global__ void __launch_bounds__(kBlock) k_ls_curv(const T *__restrict__ d, Geo g, double *__restrict__ part) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   T dot = T(0);
   if (x <= g.W) {
-    T acc[N], dk[N];
-    nbr_sum<T, N>(d, g, x, y, acc);
+    T dk[N], t[N];
     ldn<T, N>(d + fslot<T>(g, x, y) * N, dk);
-    const T D = geo_D<T>(g, node_class(g, x, y)), te = geo_te<T>(g);
-    T loc = T(0);
+    const Weights w = edge_weights(g, x, y);
+    T sq = T(0), cross = T(0);
 #pragma unroll
-    for (int i = 0; i < N; ++i) loc += dk[i] * (D * dk[i] - te * acc[i]);
-    dot = loc;
+    for (int i = 0; i < N; ++i) sq += dk[i] * dk[i];
+    if (x < g.W) {
+      ldn<T, N>(d + fslot<T>(g, x + 1, y) * N, t);
+      T e = T(0);
+#pragma unroll
+      for (int i = 0; i < N; ++i) e += dk[i] * t[i];
+      cross += T(w.e) * e;
+    }
+    if (y < g.H) {
+      ldn<T, N>(d + fslot<T>(g, x, y + 1) * N, t);
+      T e = T(0);
+#pragma unroll
+      for (int i = 0; i < N; ++i) e += dk[i] * t[i];
+      cross += T(w.n) * e;
+    }
+    dot = geo_D<T>(g, node_class(g, x, y)) * sq - T(2) * geo_te<T>(g) * cross;
   }
   block_sum_store1<T>(dot, part + blockIdx.y * gridDim.x + blockIdx.x);
 }

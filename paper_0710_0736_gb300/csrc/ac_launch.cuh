@@ -17,6 +17,10 @@ struct PhaseLaunch {
   dim3 grid;
   unsigned block;
 };
+// Levels at least this large take the node-wide variant of the light
+// transfer kernels (one thread per node, all phases).
+constexpr int64_t kWideLevelNodes = 1 << 20;
+
 inline PhaseLaunch phase_grid(int count_per_row, int rows, int phases) {
   const unsigned b = count_per_row >= kBlock ? (unsigned)kBlock : (unsigned)(((count_per_row + 31) / 32) * 32);
   return {dim3((unsigned)((count_per_row + (int)b - 1) / (int)b), (unsigned)rows, (unsigned)phases), b};
@@ -26,19 +30,29 @@ template <typename T, int N, int FORM>
 struct SolverLaunch {
   // `sweeps` red-black sweeps in place, one launch per colour; the pending
   // coarse correction (corr != null) is applied inside the first launch.
+  // With mask != null the last launch (colour 1) also stores its nodes' free
+  // mask (and rt = 0 if rt != null), so that resid(color = 0) completes them.
   static int smooth(void *x, const void *rhs, const void *ob, const void *corr, const double *omega, const Geo &g,
-                    int sweeps, cudaStream_t s) {
+                    int sweeps, void *rt, uint8_t *mask, cudaStream_t s) {
     const dim3 grid = row_grid((g.W + 2) / 2, g.H + 1);
     for (int k = 0; k < sweeps; ++k)
-      for (int c = 0; c < 2; ++c)
-        k_smooth_fine<T, N, FORM><<<grid, kBlock, 0, s>>>((T *)x, (const T *)rhs, (const T *)ob,
-                                                        k == 0 && c == 0 ? (const T *)corr : nullptr, omega, g, c);
+      for (int c = 0; c < 2; ++c) {
+        const T *cr = k == 0 && c == 0 ? (const T *)corr : nullptr;
+        if (mask && k == sweeps - 1 && c == 1)
+          k_smooth_fine<T, N, FORM, true><<<grid, kBlock, 0, s>>>((T *)x, (const T *)rhs, (const T *)ob, cr, omega,
+                                                                g, c, (T *)rt, mask);
+        else
+          k_smooth_fine<T, N, FORM, false><<<grid, kBlock, 0, s>>>((T *)x, (const T *)rhs, (const T *)ob, cr, omega,
+                                                                 g, c, nullptr, nullptr);
+      }
     return 2 * sweeps;
   }
+  // color < 0: every node; 0: the first colour only (after smooth() with a mask)
   static int resid(const void *x, const void *rhs, const void *ob, const Geo &g, void *rt, uint8_t *mask,
-                   double *rho, cudaStream_t s) {
-    k_fine_resid<T, N, FORM><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>((const T *)x, (const T *)rhs,
-                                                                         (const T *)ob, g, (T *)rt, mask, rho);
+                   double *rho, int color, cudaStream_t s) {
+    const dim3 grid = color < 0 ? row_grid(g.W + 1, g.H + 1) : row_grid((g.W + 2) / 2, g.H + 1);
+    k_fine_resid<T, N, FORM><<<grid, kBlock, 0, s>>>((const T *)x, (const T *)rhs, (const T *)ob, g, (T *)rt, mask,
+                                                   rho, color);
     return 1;
   }
   static int restrict0(const void *rt, const Geo &gf, const Geo &gc, void *r1, cudaStream_t s) {
@@ -90,8 +104,12 @@ struct SolverLaunch {
     return 1;
   }
   static int prolong_add(const void *vc, const Geo &gf, const Geo &gc, void *vf, cudaStream_t s) {
-    const PhaseLaunch L = phase_grid(gf.W + 1, gf.H + 1, N);
-    k_prolong_add<T, N><<<L.grid, L.block, 0, s>>>((const T *)vc, gf, gc, (T *)vf);
+    if ((int64_t)(gf.W + 1) * (gf.H + 1) >= kWideLevelNodes) {
+      k_prolong_add<T, N, false><<<row_grid(gf.W + 1, gf.H + 1), kBlock, 0, s>>>((const T *)vc, gf, gc, (T *)vf);
+    } else {
+      const PhaseLaunch L = phase_grid(gf.W + 1, gf.H + 1, N);
+      k_prolong_add<T, N, true><<<L.grid, L.block, 0, s>>>((const T *)vc, gf, gc, (T *)vf);
+    }
     return 1;
   }
   static int line_search(const void *x, const void *ob, const void *rt, const void *v1, const uint8_t *mask,

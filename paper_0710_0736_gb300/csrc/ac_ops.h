@@ -18,10 +18,14 @@ struct SolverOps {
   int elem;  // sizeof(scalar)
   // sweeps red-black sweeps in place; with corr != null the pending coarse
   // correction x += (*omega) corr is applied inside the first launch
+  // correction x += (*omega) corr is applied inside the first launch; with
+  // mask != null the last launch stores its colour's free mask (and rt = 0
+  // for that colour if rt != null)
   int (*smooth)(void *x, const void *rhs, const void *ob, const void *corr, const double *omega, const Geo &g,
-                int sweeps, cudaStream_t s);
+                int sweeps, void *rt, uint8_t *mask, cudaStream_t s);
+  // color < 0: every node; 0: the first colour only (completes a masked smooth)
   int (*resid)(const void *x, const void *rhs, const void *ob, const Geo &g, void *rt, uint8_t *mask, double *rho,
-               cudaStream_t s);
+               int color, cudaStream_t s);
   int (*restrict0)(const void *rt, const Geo &gf, const Geo &gc, void *r1, cudaStream_t s);
   int (*galerkin0)(const uint8_t *mask, const Geo &gf, const Geo &gc, const Galerkin0Table &tab, void *op,
                    cudaStream_t s);

@@ -316,6 +316,29 @@ def test_error_paths(ac):
 # a11: mixed precision (FP32 correction multigrid, FP64 defect correction)
 # --------------------------------------------------------------------------
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("nu1,nu2", [(0, 2), (1, 0), (3, 3)])
+def test_smoothing_schedules(ac, precision, nu1, nu2):
+    """Other V(nu1, nu2) schedules reach the same step.  nu1 = 0 makes the
+    first cycle take the every-node residual; later cycles let the last
+    smoothing pass store its colour's mask and residual and the residual
+    kernel visit the other colour only."""
+    W, H, N = 96, 64, 5
+    img = synth.shapes_image(21, W, H, rect_side=(4, 30), disk_r=(3, 12))
+    u0 = synth.dirichlet_init(22, (W + 1) * (H + 1), N)
+    tol = 1e-12
+    prec = ac.AC_MIXED if precision == "mixed" else ac.AC_FP64
+    seg = ac.Segmenter(W, H, N, 2.0, 1.0, 4.0, tol=tol, max_cycles=3000, precision=prec, nu1=nu1, nu2=nu2)
+    seg.set_image(img)
+    seg.set_phase(u0)
+    st = seg.step(2)
+    assert st.converged
+    img_used = synth.round_bf16(img).astype(np.float64) if precision == "mixed" else img.astype(np.float64)
+    u_ref, _, _ = oracle.run(img_used, u0, 2.0, 1.0, 4.0, 2, tol=TIGHT)
+    assert np.abs(seg.phase() - u_ref).max() < 1e-9
+    seg.close()
+
+
 def _mixed(ac, W, H, N, tol, **kw):
     return ac.Segmenter(W, H, N, kw.pop("eps", 2.0), kw.pop("lam", 1.0), kw.pop("tau", 4.0), tol=tol,
                         max_cycles=kw.pop("max_cycles", 2000), precision=ac.AC_MIXED, **kw)
