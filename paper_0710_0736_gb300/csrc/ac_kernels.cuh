@@ -622,60 +622,67 @@ __device__ __forceinline__ void galerkin0_node(const uint8_t *__restrict__ mask,
   constexpr int oy[5] = {0, 0, 0, 1, -1};
   constexpr int lx[4] = {0, 1, 0, 1};
   constexpr int ly[4] = {0, 0, 1, 1};
-  // m[j][i]: mask of fine node (2X - 2 + i, 2Y - 2 + j), 0 outside the grid
-  unsigned m[6][6];
+  // mask of fine node (2X - 2 + i, 2Y - 2 + j), 0 outside the grid: byte i of
+  // the packed row words pk[j][0] (i < 4) and pk[j][1] (i = 4, 5)
+  unsigned pk[6][2];
   unsigned all = (1u << N) - 1u, any = 0u;
   const int64_t row0 = (int64_t)(2 * Y - 2) * gf.Wn + (2 * X - 2);
 #pragma unroll
-  for (int j = 0; j < 6; ++j)
+  for (int j = 0; j < 6; ++j) {
+    pk[j][0] = pk[j][1] = 0u;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       const int fx = 2 * X - 2 + i, fy = 2 * Y - 2 + j;
       const bool v = INTERIOR || (fx >= 0 && fx <= gf.W && fy >= 0 && fy <= gf.H);
-      m[j][i] = v ? (unsigned)mask[row0 + (int64_t)j * gf.Wn + i] : 0u;
+      const unsigned b = v ? (unsigned)mask[row0 + (int64_t)j * gf.Wn + i] : 0u;
+      pk[j][i >> 2] |= b << (8 * (i & 3));
       if (v) {
-        all &= m[j][i];
-        any |= m[j][i];
+        all &= b;
+        any |= b;
       }
     }
+  }
+  auto m = [&](int j, int i) -> unsigned { return (pk[j][i >> 2] >> (8 * (i & 3))) & 0xffu; };
   const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), K = (int64_t)Y * gc.Wn + X;
   const unsigned partial = any & ~all;
+  T tvT[4];  // the table entries in T, converted once
+#pragma unroll
+  for (int l = 0; l < 4; ++l) tvT[l] = (T)tv[l];
   if (!partial) {
 #pragma unroll
     for (int l = 0; l < 4; ++l)
 #pragma unroll
-      for (int i = 0; i < N; ++i) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? (T)tv[l] : T(0);
+      for (int i = 0; i < N; ++i) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? tvT[l] : T(0);
     return;
   }
   if constexpr (INTERIOR) {
+    // one phase at a time (4 live accumulators), products with compile-time
+    // hat weights and the interior stencil constants
     const T Daa = geo_D<T>(gf, 4), Sab = -geo_te<T>(gf);
-    T acc[4][N];
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+      T c4[4] = {T(0), T(0), T(0), T(0)};
+      if ((partial >> i) & 1u) {
 #pragma unroll
-    for (int l = 0; l < 4; ++l)
+        for (int s = 0; s < 7; ++s) {
+          const T pa = s == 0 ? T(1) : T(0.5);
+          const unsigned ma = (m(2 + sy[s], 2 + sx[s]) >> i) & 1u;
 #pragma unroll
-      for (int i = 0; i < N; ++i) acc[l][i] = T(0);
+          for (int o = 0; o < 5; ++o) {
+            const bool on = (ma & (m(2 + sy[s] + oy[o], 2 + sx[s] + ox[o]) >> i)) != 0u;
+            const T sab = o == 0 ? Daa : Sab;
 #pragma unroll
-    for (int s = 0; s < 7; ++s) {
-      const T pa = s == 0 ? T(1) : T(0.5);
-      const unsigned ma = m[2 + sy[s]][2 + sx[s]] & partial;
-#pragma unroll
-      for (int o = 0; o < 5; ++o) {
-        const unsigned mm = ma & m[2 + sy[s] + oy[o]][2 + sx[s] + ox[o]];
-        const T sab = o == 0 ? Daa : Sab;
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-          const T q = hat_weight_t<T>(sx[s] + ox[o] - 2 * lx[l], sy[s] + oy[o] - 2 * ly[l]);
-          if (q == T(0)) continue;
-          const T cf = pa * sab * q;
-#pragma unroll
-          for (int i = 0; i < N; ++i) acc[l][i] += ((mm >> i) & 1u) ? cf : T(0);
+            for (int l = 0; l < 4; ++l) {
+              const T q = hat_weight_t<T>(sx[s] + ox[o] - 2 * lx[l], sy[s] + oy[o] - 2 * ly[l]);
+              if (q == T(0)) continue;
+              c4[l] += on ? pa * sab * q : T(0);
+            }
+          }
         }
       }
+#pragma unroll
+      for (int l = 0; l < 4; ++l) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? tvT[l] : c4[l];
     }
-#pragma unroll
-    for (int l = 0; l < 4; ++l)
-#pragma unroll
-      for (int i = 0; i < N; ++i) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? (T)tv[l] : acc[l][i];
   } else {
     // boundary nodes: one phase at a time (few registers), stencil entries by
     // node class
@@ -689,10 +696,10 @@ __device__ __forceinline__ void galerkin0_node(const uint8_t *__restrict__ mask,
 #pragma unroll
         for (int s = 0; s < 7; ++s) {
           const T pa = s == 0 ? T(1) : T(0.5);
-          const unsigned ma = (m[2 + sy[s]][2 + sx[s]] >> i) & 1u;
+          const unsigned ma = (m(2 + sy[s], 2 + sx[s]) >> i) & 1u;
 #pragma unroll
           for (int o = 0; o < 5; ++o) {
-            const unsigned mm = ma & (m[2 + sy[s] + oy[o]][2 + sx[s] + ox[o]] >> i);
+            const unsigned mm = ma & (m(2 + sy[s] + oy[o], 2 + sx[s] + ox[o]) >> i);
             if (!(mm & 1u)) continue;
             const T sab = fine_S_t<T>(gf, 2 * X + sx[s], 2 * Y + sy[s], ox[o], oy[o]);
 #pragma unroll
@@ -705,7 +712,7 @@ __device__ __forceinline__ void galerkin0_node(const uint8_t *__restrict__ mask,
         }
       }
 #pragma unroll
-      for (int l = 0; l < 4; ++l) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? (T)tv[l] : c4[l];
+      for (int l = 0; l < 4; ++l) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? tvT[l] : c4[l];
     }
   }
 }
