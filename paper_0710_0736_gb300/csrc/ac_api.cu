@@ -112,8 +112,10 @@ ac::Galerkin0Table galerkin0_table(const ac::Geo &gf, const ac::Geo &gc) {
       const int c = ac::g0_class(Y, gc.H) * 5 + ac::g0_class(X, gc.W);
       if (seen[c]) continue;
       seen[c] = true;
-      for (int l = 0; l < 4; ++l)
+      for (int l = 0; l < 4; ++l) {
         t.v[c][l] = ac::galerkin0_entry(gf, gc, X, Y, lx[l], ly[l], [](int, int) { return true; });
+        t.vf[c][l] = (float)t.v[c][l];
+      }
     }
   }
   return t;

@@ -399,6 +399,7 @@ __host__ __device__ __forceinline__ T hat_weight_t(int dx, int dy) {
 // alike), index cy*5 + cx.
 struct Galerkin0Table {
   double v[25][4];
+  float vf[25][4];  // the same entries rounded to float (FP32 solves)
 };
 
 __host__ __device__ __forceinline__ int g0_class(int X, int Wc) {

@@ -615,7 +615,8 @@ __global__ void k_restrict(const T *__restrict__ t, Geo gf, Geo gc, T *__restric
 // stencil lookups drop out.
 template <typename T, int N, bool INTERIOR>
 __device__ __forceinline__ void galerkin0_node(const uint8_t *__restrict__ mask, const Geo &gf, const Geo &gc,
-                                               const double *tv, int X, int Y, T *__restrict__ op) {
+                                               const Galerkin0Table &tab, int cls, int X, int Y,
+                                               T *__restrict__ op) {
   constexpr int sx[7] = {0, 1, -1, 0, 0, 1, -1};
   constexpr int sy[7] = {0, 0, 0, 1, -1, 1, -1};
   constexpr int ox[5] = {0, 1, -1, 0, 0};
@@ -645,9 +646,14 @@ __device__ __forceinline__ void galerkin0_node(const uint8_t *__restrict__ mask,
   auto m = [&](int j, int i) -> unsigned { return (pk[j][i >> 2] >> (8 * (i & 3))) & 0xffu; };
   const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), K = (int64_t)Y * gc.Wn + X;
   const unsigned partial = any & ~all;
-  T tvT[4];  // the table entries in T, converted once
+  T tvT[4];  // the table entries of this node's class in T
 #pragma unroll
-  for (int l = 0; l < 4; ++l) tvT[l] = (T)tv[l];
+  for (int l = 0; l < 4; ++l) {
+    if constexpr (sizeof(T) == 4)
+      tvT[l] = tab.vf[cls][l];
+    else
+      tvT[l] = tab.v[cls][l];
+  }
   if (!partial) {
 #pragma unroll
     for (int l = 0; l < 4; ++l)
@@ -723,9 +729,9 @@ __global__ void __launch_bounds__(kBlock) k_galerkin0(const uint8_t *__restrict_
   const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
   if (X > gc.W) return;
   if (X >= 2 && X <= gc.W - 2 && Y >= 2 && Y <= gc.H - 2)
-    galerkin0_node<T, N, true>(mask, gf, gc, tab.v[2 * 5 + 2], X, Y, op);
+    galerkin0_node<T, N, true>(mask, gf, gc, tab, 2 * 5 + 2, X, Y, op);
   else
-    galerkin0_node<T, N, false>(mask, gf, gc, tab.v[g0_class(Y, gc.H) * 5 + g0_class(X, gc.W)], X, Y, op);
+    galerkin0_node<T, N, false>(mask, gf, gc, tab, g0_class(Y, gc.H) * 5 + g0_class(X, gc.W), X, Y, op);
 }
 
 

@@ -576,19 +576,11 @@ def test_adjoint_mixed_forward(ac):
     assert np.abs(gu0 - ru0).max() <= 1e-6 * np.abs(ru0).max()
 
 
-def test_adjoint_full_size_c5(ac):
+@pytest.fixture(scope="module")
+def c5_problem(ac):
     """The 512x512, N = 4 workload (12 disks, noise 0.08, Voronoi target of 6
     seeds) over 16 steps with checkpoints every 4, every step solved to 1e-14,
-    against central differences (h = 1e-7) of the GPU forward.
-
-    Rounding noise of the forward, amplified by the first steps of a random
-    start, leaves ~5e-11 of noise in L, i.e. ~2.5e-4 in a difference quotient
-    at h = 1e-7; larger h meets kinks (active-set changes; h = 1e-6 is off by
-    1e-5 relative).  lambda and eps are held to 1e-6 relative, two random image
-    directions (derivatives ~300) to 1e-3 absolute, that noise floor.  (A
-    direction aligned with the gradient's signs moves every interface at once
-    and meets kinks within +-h: its quotient is off by ~1e-3 relative.)  Over
-    the full 64 steps the quotients wander by ~0.5% with h."""
+    and its GPU gradients."""
     W = H = 512
     cfg = synth.CONFIGS["c5_512_n4_adjoint"]
     N, eps, lam, tau, T = cfg["N"], cfg["eps"], cfg["lam"], cfg["tau"], 16
@@ -596,7 +588,25 @@ def test_adjoint_full_size_c5(ac):
     u0 = synth.dirichlet_init(1, (W + 1) * (H + 1), N)
     target = synth.voronoi_labels(2, W + 1, H + 1, n_seeds=6, n_labels=4)
     tol = 1e-14
-    L, gl, ge, gimg, gu0 = _gpu_grads(ac, img, u0, target, eps, lam, tau, T, 4, tol, ac.AC_FP64)
+    grads = _gpu_grads(ac, img, u0, target, eps, lam, tau, T, 4, tol, ac.AC_FP64)
+    return dict(img=img, u0=u0, target=target, eps=eps, lam=lam, tau=tau, T=T, tol=tol, grads=grads)
+
+
+def test_adjoint_full_size_c5(ac, c5_problem):
+    """lambda, eps and 8 random image directions against central differences
+    (h = 1e-7) of the GPU forward.
+
+    Rounding noise of the forward, amplified by the first steps of a random
+    start, leaves ~5e-11 of noise in L, i.e. ~2.5e-4 in a difference quotient
+    at h = 1e-7; larger h meets kinks (active-set changes; h = 1e-6 is off by
+    1e-5 relative).  lambda and eps are held to 1e-6 relative, the random image
+    directions (derivatives ~300) to 1e-3 absolute, that noise floor.  (A
+    direction aligned with the gradient's signs moves every interface at once
+    and meets kinks within +-h: its quotient is off by ~1e-3 relative.)  Over
+    the full 64 steps the quotients wander by ~0.5% with h."""
+    P = c5_problem
+    img, u0, target, eps, lam, tau, T, tol = (P[k] for k in ("img", "u0", "target", "eps", "lam", "tau", "T", "tol"))
+    L, gl, ge, gimg, gu0 = P["grads"]
     h = 1e-7
 
     def fd(f):
@@ -607,7 +617,29 @@ def test_adjoint_full_size_c5(ac):
     assert ge == pytest.approx(fd(lambda d: _gpu_loss(ac, img, u0, target, eps + d, lam, tau, T, tol, ac.AC_FP64)),
                                rel=1e-6)
     rng = np.random.default_rng(3)
-    for _ in range(2):
+    for _ in range(8):
         v = rng.normal(size=img.shape)
         assert (gimg * v).sum() == pytest.approx(
             fd(lambda d: _gpu_loss(ac, img + d * v, u0, target, eps, lam, tau, T, tol, ac.AC_FP64)), abs=1e-3)
+
+
+def test_adjoint_full_size_c5_pixels(ac, c5_problem):
+    """64 random pixel-channels of dL/dI against central differences at
+    h = 1e-4.  A single pixel moves its own neighbourhood only, so kinks are
+    rare there and the quotient's truncation and noise stay near 1e-6 (24
+    channels measured: at most 1.2e-6 off, entries up to 33); at h = 1e-6
+    rounding noise dominates (~1e-4).  Bound: 1e-6 |g| + 4e-6."""
+    P = c5_problem
+    img, u0, target, eps, lam, tau, T, tol = (P[k] for k in ("img", "u0", "target", "eps", "lam", "tau", "T", "tol"))
+    gimg = P["grads"][3]
+    H, W, _ = img.shape
+    rng = np.random.default_rng(5)
+    h = 1e-4
+    for _ in range(64):
+        py, px, ch = int(rng.integers(H)), int(rng.integers(W)), int(rng.integers(3))
+        e = np.zeros_like(img)
+        e[py, px, ch] = 1.0
+        q = (_gpu_loss(ac, img + h * e, u0, target, eps, lam, tau, T, tol, ac.AC_FP64) -
+             _gpu_loss(ac, img - h * e, u0, target, eps, lam, tau, T, tol, ac.AC_FP64)) / (2 * h)
+        g = gimg[py, px, ch]
+        assert abs(q - g) <= 1e-6 * abs(g) + 4e-6, (py, px, ch, g, q)
