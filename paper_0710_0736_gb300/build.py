@@ -40,19 +40,31 @@ def _deps():
         [os.path.join(INCLUDE, "ac.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+STAMP = os.path.join(OUT, "build_flags.txt")
+
+
+def _extra_flags(extra=None):
+    return list(extra or []) + shlex.split(os.environ.get("AC_NVCC_EXTRA", ""))
+
+
+def up_to_date(extra=None) -> bool:
+    """The library exists, is newer than every source, and was built with the
+    same extra flags."""
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return False
+    with open(STAMP) as f:
+        if f.read() != " ".join(_extra_flags(extra)):
+            return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
 def build(force: bool = False, verbose: bool = False, extra=None) -> str:
-    if not force and up_to_date():
+    if not force and up_to_date(extra):
         return LIB
     os.makedirs(OUT, exist_ok=True)
     cc = nvcc()
-    extra = list(extra or []) + shlex.split(os.environ.get("AC_NVCC_EXTRA", ""))
+    extra = _extra_flags(extra)
     procs, objs = [], []
     for src in _sources():
         obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
@@ -73,6 +85,8 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
     tmp = LIB + f".{os.getpid()}.tmp"
     subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(extra))
     return LIB
 
 

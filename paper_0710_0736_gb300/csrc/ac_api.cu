@@ -183,6 +183,8 @@ struct AdjState {
   double *g = nullptr, *g2 = nullptr;  // dL/du (n x N)
   double *gm = nullptr;     // dL/dm1 (RGB), dL/dm2 per node (n x 4)
   double *part = nullptr, *tot = nullptr, *scal = nullptr;
+  double *kw = nullptr, *kr = nullptr, *kp = nullptr, *kq = nullptr, *kq_prev = nullptr;  // flexible CG vectors
+  double *kpart = nullptr, *ktot = nullptr;  // its dot products
   Solve sv;                 // FP64 tangent-form solve
   std::vector<void *> allocs;
 };
@@ -1022,6 +1024,13 @@ int adj_setup(ac_ctx *ctx, int T, int every) {
   ADJ_ALLOC(A.part, (size_t)blocks * (2 + 3 * N) * sizeof(double));
   ADJ_ALLOC(A.tot, (size_t)(2 + 3 * N) * sizeof(double));
   ADJ_ALLOC(A.scal, 2 * sizeof(double));
+  ADJ_ALLOC(A.kw, fN);
+  ADJ_ALLOC(A.kr, fN);
+  ADJ_ALLOC(A.kp, fN);
+  ADJ_ALLOC(A.kq, fN);
+  ADJ_ALLOC(A.kq_prev, fN);
+  ADJ_ALLOC(A.kpart, (size_t)ac::kMaxPartBlocks * 2 * sizeof(double));
+  ADJ_ALLOC(A.ktot, 2 * sizeof(double));
   Solve &S = A.sv;
   S.o = &ctx->ops->adjoint;
   S.lv = ctx->sv.lv;
@@ -1045,6 +1054,69 @@ int adj_setup(ac_ctx *ctx, int T, int every) {
 }
 
 }  // namespace
+
+// Flexible CG (one-vector recurrence) on the adjoint system (Pi S Pi) w = Pi g
+// of one step, preconditioned by the truncated V-cycle of the tangent form
+// (two cycles of solve_mg from zero: pre-smoothing, coarse correction with
+// its line search, post-smoothing).  The line search makes the preconditioner
+// nonlinear, hence the flexible direction update
+//   p_k = z_k - (z_k . q_{k-1}) / (p_{k-1} . q_{k-1}) p_{k-1},   q = Pi S p,
+//   alpha = p_k . r_k / p_k . q_k.
+// Stops when max |r| / S_nn <= tol_rho (the plain solve's natural-residual
+// rule; min S_nn bounds the scaling).  On return A.kw holds w.
+int fcg_adjoint(ac_ctx *ctx, AdjState &A, double tol_rho, int max_iter, int *iters) {
+  Solve &S = A.sv;
+  const ac::Ops *o = ctx->ops;
+  const int64_t nN = ctx->n * ctx->N;
+  const size_t fN = (size_t)nN * sizeof(double);
+  double dmin = ctx->g0.D[0];
+  for (int k = 1; k < 9; ++k) dmin = std::fmin(dmin, ctx->g0.D[k] > 0 ? ctx->g0.D[k] : dmin);
+  const double tol_r = tol_rho * dmin;
+  AC_CUDA(cudaMemsetAsync(A.kw, 0, fN, ctx->s));
+  AC_CUDA(cudaMemcpyAsync(A.kr, S.rhs, fN, cudaMemcpyDeviceToDevice, ctx->s));
+  double pq_prev = 0.0;
+  int it = 0, status = AC_ERR_NOT_CONVERGED;
+  for (; it < max_iter; ++it) {
+    AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
+    AC_RUN(AC_PROF_SETUP, o->absmax(A.kr, nN, ctx->rho, ctx->s));
+    double rmax = 0;
+    int rc = read_rho(ctx, &rmax);
+    if (rc) return rc;
+    if (std::isnan(rmax)) return fail(AC_ERR_NUMERIC, "non-finite adjoint residual");
+    if (rmax <= tol_r) {
+      status = AC_OK;
+      break;
+    }
+    // z = B r: the truncated V-cycle from zero on right-hand side r
+    AC_CUDA(cudaMemcpyAsync(S.rhs, A.kr, fN, cudaMemcpyDeviceToDevice, ctx->s));
+    AC_CUDA(cudaMemsetAsync(S.x, 0, fN, ctx->s));
+    int cyc = 0;
+    double rho = 0;
+    int64_t sw = 0;
+    rc = solve_mg(ctx, S, 0.0, 2, &cyc, &rho, &sw);
+    if (rc && rc != AC_ERR_NOT_CONVERGED) return rc;
+    const double *z = (const double *)S.x;
+    double beta = 0.0;
+    if (it > 0) {
+      AC_RUN(AC_PROF_SETUP, o->dot2(z, A.kq_prev, nullptr, nullptr, nN, A.kpart, A.ktot, ctx->s));
+      AC_CUDA(cudaMemcpyAsync(ctx->h_scalars, A.ktot, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+      AC_CUDA(cudaStreamSynchronize(ctx->s));
+      beta = pq_prev > 0 ? -ctx->h_scalars[0] / pq_prev : 0.0;
+    }
+    AC_RUN(AC_PROF_SETUP, o->fcg_dir(A.kp, z, beta, nN, ctx->s));
+    AC_RUN(AC_PROF_SETUP, o->tangent_apply(A.kp, (const double *)S.ob, ctx->g0, A.kq, ctx->s));
+    AC_RUN(AC_PROF_SETUP, o->dot2(A.kp, A.kr, A.kp, A.kq, nN, A.kpart, A.ktot, ctx->s));
+    AC_CUDA(cudaMemcpyAsync(ctx->h_scalars, A.ktot, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    AC_CUDA(cudaStreamSynchronize(ctx->s));
+    const double pr = ctx->h_scalars[0], pq = ctx->h_scalars[1];
+    if (!(pq > 0)) break;  // p = 0 (r already 0 on the tangent space) or a lost direction
+    AC_RUN(AC_PROF_SETUP, o->fcg_step(A.kw, A.kr, A.kp, A.kq, pr / pq, nN, ctx->s));
+    pq_prev = pq;
+    std::swap(A.kq, A.kq_prev);
+  }
+  *iters = it;
+  return status;
+}
 
 extern "C" {
 
@@ -1115,17 +1187,23 @@ int ac_adjoint_backward(ac_ctx *ctx, const double *grad_u, double *grad_lambda, 
       double gmax = 0;
       int rc = read_rho(ctx, &gmax);
       if (rc) return rc;
+      const double *w = (const double *)S.x;
       if (gmax > 0) {
+#ifdef AC_ADJOINT_PLAIN_VCYCLE
         int cyc = 0;
         double rho = 0;
         int64_t sw = 0;
         rc = solve_mg(ctx, S, 1e-13 * gmax, ctx->p.max_cycles, &cyc, &rho, &sw);
+#else
+        int iters = 0;
+        rc = fcg_adjoint(ctx, A, 1e-13 * gmax, ctx->p.max_cycles, &iters);
+        w = A.kw;
+#endif
         if (rc == AC_ERR_NOT_CONVERGED)
           status = rc;
         else if (rc)
           return rc;
       }
-      const double *w = (const double *)S.x;
       AC_RUN(AC_PROF_SETUP, o->adj_accum(w, u, up, ctx->mom, c, ctx->g0, tau, eps, lam, A.gm, A.part, A.tot, A.scal,
                                          ctx->s));
       AC_RUN(AC_PROF_SETUP, o->adj_back(w, u, ctx->mom, c, A.tot, M, ctx->g0, a1, A.g2, A.gm, ctx->s));

@@ -1224,6 +1224,55 @@ static __global__ void k_adj_scalars(const double *__restrict__ tot, double *__r
 }
 
 // max_k |v_k| over count values (atomic max of non-negative doubles).
+// a13, Krylov acceleration of the adjoint solve (flexible CG with the
+// truncated V-cycle as preconditioner).  q = Pi (S p) with the frozen free set
+// f (1/0 per phase): the adjoint system's operator Pi S Pi on a tangent p.
+template <int N>
+__global__ void k_tangent_apply(const double *__restrict__ p, const double *__restrict__ f, Geo g,
+                                double *__restrict__ q) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x > g.W) return;
+  const int64_t n = (int64_t)y * g.Wn + x;
+  double acc[N], pk[N], fk[N];
+  nbr_sum<double, N>(p, g, x, y, acc);
+  ldn<double, N>(p + n * N, pk);
+  ldn<double, N>(f + n * N, fk);
+  const double D = g.D[node_class(g, x, y)], te = g.te;
+#pragma unroll
+  for (int i = 0; i < N; ++i) acc[i] = D * pk[i] - te * acc[i];
+  proj_box<double, N, kTangent>(acc, fk);
+  stn<double, N>(q + n * N, acc);
+}
+
+// Block partials of two dot products a0.b0 and a1.b1 over `count` doubles
+// (a1 == nullptr: the first only); fixed order for a fixed grid.
+static __global__ void __launch_bounds__(kBlock) k_dot2(const double *__restrict__ a0, const double *__restrict__ b0,
+                                                        const double *__restrict__ a1, const double *__restrict__ b1,
+                                                        int64_t count, double *__restrict__ part) {
+  double acc[2] = {0.0, 0.0};
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
+    acc[0] += a0[k] * b0[k];
+    if (a1) acc[1] += a1[k] * b1[k];
+  }
+  block_sum_store<2>(acc, part + (int64_t)blockIdx.x * 2);
+}
+
+// x += alpha p, r -= alpha q.
+static __global__ void k_fcg_step(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                                  const double *__restrict__ q, double alpha, int64_t count) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  x[k] += alpha * p[k];
+  r[k] -= alpha * q[k];
+}
+
+// p = z + beta p.
+static __global__ void k_fcg_dir(double *__restrict__ p, const double *__restrict__ z, double beta, int64_t count) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  p[k] = z[k] + beta * p[k];
+}
+
 static __global__ void k_absmax(const double *__restrict__ v, int64_t count, double *__restrict__ out) {
   double e = 0.0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)

@@ -205,6 +205,25 @@ struct Launch {
     k_adj_image<<<row_grid(g.W, g.H), kBlock, 0, s>>>(gm, img, g, gimg);
     return 1;
   }
+  static int tangent_apply(const double *p, const double *f, const Geo &g, double *q, cudaStream_t s) {
+    k_tangent_apply<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(p, f, g, q);
+    return 1;
+  }
+  static int dot2(const double *a0, const double *b0, const double *a1, const double *b1, int64_t count,
+                  double *part, double *tot, cudaStream_t s) {
+    k_dot2<<<kMaxPartBlocks, kBlock, 0, s>>>(a0, b0, a1, b1, count, part);
+    k_colsum<<<2, 1024, 0, s>>>(part, kMaxPartBlocks, 2, tot);
+    return 2;
+  }
+  static int fcg_step(double *x, double *r, const double *p, const double *q, double alpha, int64_t count,
+                      cudaStream_t s) {
+    k_fcg_step<<<blocks_for(count), kBlock, 0, s>>>(x, r, p, q, alpha, count);
+    return 1;
+  }
+  static int fcg_dir(double *p, const double *z, double beta, int64_t count, cudaStream_t s) {
+    k_fcg_dir<<<blocks_for(count), kBlock, 0, s>>>(p, z, beta, count);
+    return 1;
+  }
   static int absmax(const double *v, int64_t count, double *out, cudaStream_t s) {
     k_absmax<<<kMaxPartBlocks, kBlock, 0, s>>>(v, count, out);
     return 1;
@@ -232,7 +251,11 @@ struct Launch {
                           adj_accum,
                           adj_back,
                           adj_image,
-                          absmax};
+                          absmax,
+                          tangent_apply,
+                          dot2,
+                          fcg_step,
+                          fcg_dir};
     return &t;
   }
 };

@@ -74,6 +74,14 @@ struct Ops {
                   const double *mass, const Geo &g, double a1, double *gout, double *gm, cudaStream_t s);
   int (*adj_image)(const double *gm, const double *img, const Geo &g, double *gimg, cudaStream_t s);
   int (*absmax)(const double *v, int64_t count, double *out, cudaStream_t s);
+  // flexible CG on the adjoint's tangent system: q = Pi S p; two dots
+  // (part: kMaxPartBlocks x 2, tot: 2); x += alpha p, r -= alpha q; p = z + beta p
+  int (*tangent_apply)(const double *p, const double *f, const Geo &g, double *q, cudaStream_t s);
+  int (*dot2)(const double *a0, const double *b0, const double *a1, const double *b1, int64_t count, double *part,
+              double *tot, cudaStream_t s);
+  int (*fcg_step)(double *x, double *r, const double *p, const double *q, double alpha, int64_t count,
+                  cudaStream_t s);
+  int (*fcg_dir)(double *p, const double *z, double beta, int64_t count, cudaStream_t s);
 };
 
 const Ops *ops_n2();

@@ -600,7 +600,8 @@ def test_adjoint_full_size_c5(ac, c5_problem):
     start, leaves ~5e-11 of noise in L, i.e. ~2.5e-4 in a difference quotient
     at h = 1e-7; larger h meets kinks (active-set changes; h = 1e-6 is off by
     1e-5 relative).  lambda and eps are held to 1e-6 relative, the random image
-    directions (derivatives ~300) to 1e-3 absolute, that noise floor.  (A
+    directions (derivatives ~300-3000) to 1e-6 relative or 1e-3 absolute, that
+    noise floor, whichever is larger.  (A
     direction aligned with the gradient's signs moves every interface at once
     and meets kinks within +-h: its quotient is off by ~1e-3 relative.)  Over
     the full 64 steps the quotients wander by ~0.5% with h."""
@@ -620,7 +621,7 @@ def test_adjoint_full_size_c5(ac, c5_problem):
     for _ in range(8):
         v = rng.normal(size=img.shape)
         assert (gimg * v).sum() == pytest.approx(
-            fd(lambda d: _gpu_loss(ac, img + d * v, u0, target, eps, lam, tau, T, tol, ac.AC_FP64)), abs=1e-3)
+            fd(lambda d: _gpu_loss(ac, img + d * v, u0, target, eps, lam, tau, T, tol, ac.AC_FP64)), rel=1e-6, abs=1e-3)
 
 
 def test_adjoint_full_size_c5_pixels(ac, c5_problem):
