@@ -161,6 +161,16 @@ int ac_get_moments(ac_ctx *ctx, double *m);
 int ac_get_rhs(ac_ctx *ctx, double *b);
 /* Node labels ((H+1)(W+1) int8): argmax of u_n, lowest index on ties. */
 int ac_get_node_labels(ac_ctx *ctx, int8_t *labels, int is_device);
+/* Composite image (Sec. 4.3, post-processing): per pixel, sum_i c_i ubar_i
+ * with c = c(u) the colour means of the current u and ubar_i the pixel mean
+ * of u_i on the right-diagonal split, (2 u(x,y) + u(x+1,y) + u(x,y+1) +
+ * 2 u(x+1,y+1)) / 6.  rounded != 0: the rounded composite, c of the pixel's
+ * label (argmax of ubar, lowest index on ties; the labels of ac_segment).
+ * rgb: H x W x 3 float, row-major, host (is_device = 0) or device memory,
+ * written on the context's stream (host: the call returns after the copy).
+ * Errors: AC_ERR_ARG (NULL), AC_ERR_STATE (no image), AC_ERR_NOMEM,
+ * AC_ERR_CUDA. */
+int ac_get_composite(ac_ctx *ctx, float *rgb, int rounded, int is_device);
 /* Discrete energy Eq. (E) of the current u with c = c(u) (host double). */
 int ac_energy(ac_ctx *ctx, double *energy);
 /* Natural residual max_n |u_n - P_G(y_n(u))| of the current u against the

@@ -180,6 +180,20 @@ def labels(u, W, H):
     return nl.reshape(H + 1, W + 1), pl.reshape(H, W)
 
 
+def composite(u, c, W, H, rounded=False):
+    """Composite image (Sec. 4.3): per pixel sum_i c_i ubar_i, ubar_i the mean
+    of u_i over the pixel (both triangles of the right-diagonal split, i.e.
+    (2 u00 + u10 + u01 + 2 u11) / 6); rounded: c of the pixel label (the
+    rounded composite).  Returns (H, W, 3) float64."""
+    U = np.asarray(u, dtype=np.float64).reshape(H + 1, W + 1, -1)
+    ubar = (2 * U[:-1, :-1] + U[:-1, 1:] + U[1:, :-1] + 2 * U[1:, 1:]) / 6.0
+    c = np.asarray(c, dtype=np.float64)
+    if rounded:
+        _, pix = labels(u, W, H)
+        return c[pix.astype(int)]
+    return ubar @ c
+
+
 def run(img, u0, eps, lam, tau, steps, tol=1e-13, method="ssc", **kw):
     """T steps from u0 on img. Returns (u_T, c_last, per-step stats list)."""
     H, W, _ = img.shape

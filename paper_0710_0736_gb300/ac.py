@@ -21,7 +21,7 @@ AC_MAX_PHASES = 8
 EXPORTS = [
     "ac_default_params", "ac_create", "ac_set_image", "ac_set_image_f64", "ac_step", "ac_segment", "ac_destroy",
     "ac_set_phase", "ac_get_phase", "ac_get_means", "ac_get_moments", "ac_get_rhs", "ac_get_node_labels",
-    "ac_energy", "ac_residual", "ac_project_simplex", "ac_set_profiling", "ac_get_profile", "ac_colour_means_static",
+    "ac_get_composite", "ac_energy", "ac_residual", "ac_project_simplex", "ac_set_profiling", "ac_get_profile", "ac_colour_means_static",
     "ac_batch_create", "ac_batch_set_image", "ac_batch_set_phase", "ac_batch_get_phase", "ac_batch_segment",
     "ac_batch_step", "ac_batch_tune", "ac_batch_destroy", "ac_adjoint_forward", "ac_adjoint_backward",
     "ac_last_error",
@@ -91,6 +91,7 @@ def _load():
         "ac_get_moments": ([vp, vp], i),
         "ac_get_rhs": ([vp, vp], i),
         "ac_get_node_labels": ([vp, vp, i], i),
+        "ac_get_composite": ([vp, vp, i, i], i),
         "ac_energy": ([vp, P(d)], i),
         "ac_residual": ([vp, P(d)], i),
         "ac_project_simplex": ([vp, vp, i64, i, vp], i),
@@ -233,6 +234,12 @@ def ac_get_node_labels(ctx, labels, n_nodes):
     return _check(lib.ac_get_node_labels(ctx, ptr, dev))
 
 
+def ac_get_composite(ctx, rgb, W, H, rounded=False):
+    """Composite (rounded: rounded composite) into rgb, H x W x 3 float32 (numpy or CUDA tensor)."""
+    ptr, dev = _buf(rgb, np.float32, W * H * 3, writable=True)
+    return _check(lib.ac_get_composite(ctx, ptr, 1 if rounded else 0, dev))
+
+
 def ac_energy(ctx) -> float:
     e = C.c_double()
     _check(lib.ac_energy(ctx, C.byref(e)))
@@ -372,6 +379,11 @@ class Segmenter:
 
     def rhs(self):
         return ac_get_rhs(self.ctx, self.n_nodes, self.N)
+
+    def composite(self, rounded=False):
+        out = np.zeros((self.H, self.W, 3), np.float32)
+        ac_get_composite(self.ctx, out, self.W, self.H, rounded)
+        return out
 
     def energy(self):
         return ac_energy(self.ctx)

@@ -903,6 +903,35 @@ int ac_get_node_labels(ac_ctx *ctx, int8_t *labels, int is_device) {
   return AC_OK;
 }
 
+int ac_get_composite(ac_ctx *ctx, float *rgb, int rounded, int is_device) {
+  if (!ctx || !rgb) return fail(AC_ERR_ARG, "NULL argument");
+  if (!ctx->have_image) return fail(AC_ERR_STATE, "no image");
+  const size_t bytes = (size_t)ctx->p.width * ctx->p.height * 3 * sizeof(float);
+  float *dst = rgb;
+  if (!is_device) {
+    if (ctx->img_bytes < bytes) {
+      if (ctx->img) cudaFree(ctx->img);
+      ctx->img = nullptr;
+      ctx->img_bytes = 0;
+      cudaError_t e = cudaMalloc(&ctx->img, bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->img = nullptr;
+        return fail(AC_ERR_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+      }
+      ctx->img_bytes = bytes;
+    }
+    dst = static_cast<float *>(ctx->img);
+  }
+  // the colour means of the current u (a phase of zero mass keeps its last c)
+  AC_CUDA(cudaMemcpyAsync(ctx->c_tmp, ctx->c, (size_t)3 * ctx->N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
+  AC_RUN(AC_PROF_SETUP, ctx->ops->means(ctx->u, ctx->mom, ctx->g0, ctx->part, ctx->tot, ctx->c_tmp, nullptr,
+                                        ctx->p.eps, ctx->p.lambda, ctx->s));
+  AC_RUN(AC_PROF_SETUP, ctx->ops->composite(ctx->u, ctx->c_tmp, ctx->g0, rounded ? 1 : 0, dst, ctx->s));
+  if (!is_device) return copy_out(ctx, rgb, dst, bytes, 0);
+  return AC_OK;
+}
+
 int ac_energy(ac_ctx *ctx, double *energy) {
   if (!ctx || !energy) return fail(AC_ERR_ARG, "NULL argument");
   if (!ctx->have_image) return fail(AC_ERR_STATE, "no image");

@@ -1285,6 +1285,40 @@ static __global__ void k_absmax(const double *__restrict__ v, int64_t count, dou
 // label = argmax_i (2 u00 + u10 + u01 + 2 u11) (the pixel integral of u_i
 // on the right-diagonal split, times 6); lowest index on ties.
 // ---------------------------------------------------------------------------
+// Composite (Sec. 4.3): per pixel sum_i c_i ubar_i, ubar_i = the pixel mean
+// of u_i on the right-diagonal split, (2 u00 + u10 + u01 + 2 u11) / 6;
+// rounded: c of the pixel's label (argmax of ubar, lowest index on ties), the
+// rounded composite.  Output H x W x 3 float.
+template <int N>
+__global__ void k_composite(const double *__restrict__ u, const double *__restrict__ c, Geo g, int rounded,
+                            float *__restrict__ out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= g.W || y >= g.H) return;
+  const int64_t n = (int64_t)y * g.Wn + x;
+  double a[N], b10[N], b01[N], b11[N];
+  ldn<double, N>(u + n * N, a);
+  ldn<double, N>(u + (n + 1) * N, b10);
+  ldn<double, N>(u + (n + g.Wn) * N, b01);
+  ldn<double, N>(u + (n + g.Wn + 1) * N, b11);
+  double rgb[3] = {0.0, 0.0, 0.0};
+  int best = 0;
+  double bv = 0.0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const double v = 2.0 * a[i] + b10[i] + b01[i] + 2.0 * b11[i];
+    if (i == 0 || v > bv) {
+      bv = v;
+      best = i;
+    }
+    const double m = v / 6.0;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) rgb[ch] += c[i * 3 + ch] * m;
+  }
+  float *o = out + ((int64_t)y * g.W + x) * 3;
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) o[ch] = (float)(rounded ? c[best * 3 + ch] : rgb[ch]);
+}
+
 template <int N>
 __global__ void k_labels(const double *__restrict__ u, Geo g, int8_t *__restrict__ node_lab,
                          int8_t *__restrict__ pix_lab) {

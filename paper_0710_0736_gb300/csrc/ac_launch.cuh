@@ -178,6 +178,10 @@ struct Launch {
     k_outer_update<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, delta, g);
     return 1;
   }
+  static int composite(const double *u, const double *c, const Geo &g, int rounded, float *out, cudaStream_t s) {
+    k_composite<N><<<row_grid(g.W, g.H), kBlock, 0, s>>>(u, c, g, rounded, out);
+    return 1;
+  }
   static int labels(const double *u, const Geo &g, int8_t *node_lab, int8_t *pix_lab, cudaStream_t s) {
     k_labels<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, g, node_lab, pix_lab);
     return 1;
@@ -243,6 +247,7 @@ struct Launch {
                           outer_resid,
                           outer_update,
                           labels,
+                          composite,
                           project,
                           SolverLaunch<double, N, kDirect>::table(),
                           SolverLaunch<float, N, kShifted>::table(),

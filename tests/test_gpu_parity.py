@@ -339,6 +339,30 @@ def test_smoothing_schedules(ac, precision, nu1, nu2):
     seg.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_composite_matches_oracle(ac, precision):
+    """ac_get_composite (Sec. 4.3) against the oracle's composite of the GPU's
+    own phase field, with the colour means of that field: float output within
+    2 float ulps of values <= 1; the rounded composite uses the same labels as
+    ac_segment."""
+    W, H, N = 96, 64, 5
+    img = synth.shapes_image(31, W, H, rect_side=(4, 30), disk_r=(3, 12))
+    prec = ac.AC_MIXED if precision == "mixed" else ac.AC_FP64
+    seg = ac.Segmenter(W, H, N, 2.0, 1.0, 4.0, tol=1e-8, max_cycles=3000, precision=prec, seed=7)
+    seg.set_image(img)
+    seg.step(5)
+    u = seg.phase()
+    img_used = synth.round_bf16(img).astype(np.float64) if precision == "mixed" else img.astype(np.float64)
+    c, _ = oracle.means(u, oracle.moments(img_used), W, H, seg.means())
+    for rounded in (False, True):
+        got = seg.composite(rounded)
+        ref = oracle.composite(u, c, W, H, rounded)
+        assert np.abs(got - ref).max() <= 2.4e-7
+    lab = seg.segment(0)
+    assert np.abs(seg.composite(True) - c[lab.astype(int)]).max() <= 1.2e-7
+    seg.close()
+
+
 def _mixed(ac, W, H, N, tol, **kw):
     return ac.Segmenter(W, H, N, kw.pop("eps", 2.0), kw.pop("lam", 1.0), kw.pop("tau", 4.0), tol=tol,
                         max_cycles=kw.pop("max_cycles", 2000), precision=ac.AC_MIXED, **kw)

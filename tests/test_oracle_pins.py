@@ -408,3 +408,50 @@ def test_levels(oracle_mod):
     assert oracle_mod.num_levels(4096, 4096) == 11
     assert oracle_mod.num_levels(768, 512) == 8     # coarsest 6 x 4 cells
     assert oracle_mod.num_levels(37, 64) == 1       # odd cell count: no coarsening
+
+
+# ---------------------------------------------------------------------------
+# Composite image (Sec. 4.3)
+# ---------------------------------------------------------------------------
+
+def test_composite_of_constant_image_is_the_image(oracle_mod):
+    """Every non-empty phase's mean is the constant colour and the pixel means
+    of u sum to 1, so the composite (and the rounded composite) is the image."""
+    W, H, N = 16, 12, 3
+    u = synth.dirichlet_init(0, (W + 1) * (H + 1), N)
+    img = np.full((H, W, 3), [0.3, 0.6, 0.1])
+    c, _ = oracle_mod.means(u, oracle_mod.moments(img), W, H)
+    assert np.abs(oracle_mod.composite(u, c, W, H) - img).max() < 1e-15
+    assert np.abs(oracle_mod.composite(u, c, W, H, rounded=True) - img).max() < 1e-15
+
+
+def test_composite_of_pure_phases_is_the_label_colour(oracle_mod):
+    """A one-hot phase field (node labels) gives, at pixels whose four corners
+    share a label, exactly that label's colour; rounded and plain agree there."""
+    W, H, N = 20, 14, 4
+    lab = synth.voronoi_labels(3, W + 1, H + 1, n_seeds=5, n_labels=N).reshape(-1)
+    u = np.eye(N)[lab]
+    c = np.random.default_rng(1).uniform(size=(N, 3))
+    comp = oracle_mod.composite(u, c, W, H)
+    rnd = oracle_mod.composite(u, c, W, H, rounded=True)
+    L = lab.reshape(H + 1, W + 1)
+    same = (L[:-1, :-1] == L[:-1, 1:]) & (L[:-1, :-1] == L[1:, :-1]) & (L[:-1, :-1] == L[1:, 1:])
+    assert same.sum() > 100
+    np.testing.assert_array_equal(comp[same], c[L[:-1, :-1][same]])
+    np.testing.assert_array_equal(rnd[same], c[L[:-1, :-1][same]])
+
+
+def test_composite_pixel_mean_is_exact_for_linear_fields(oracle_mod):
+    """The pixel mean of a P1 function linear in x and y is its value at the
+    pixel centre (x + 1/2, y + 1/2): pins the weights (2, 1, 1, 2)/6 and the
+    orientation of the diagonal."""
+    W, H = 9, 7
+    y, x = np.meshgrid(np.arange(H + 1), np.arange(W + 1), indexing="ij")
+    t = (0.1 + 0.03 * x + 0.05 * y) / (0.1 + 0.03 * W + 0.05 * H)
+    u = np.stack([t.ravel(), 1 - t.ravel()], axis=1)
+    c = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    comp = oracle_mod.composite(u, c, W, H)
+    yc, xc = np.meshgrid(np.arange(H) + 0.5, np.arange(W) + 0.5, indexing="ij")
+    tc = (0.1 + 0.03 * xc + 0.05 * yc) / (0.1 + 0.03 * W + 0.05 * H)
+    assert np.abs(comp[..., 0] - tc).max() < 1e-15
+    assert np.abs(comp[..., 1] - (1 - tc)).max() < 1e-15
