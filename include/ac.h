@@ -77,6 +77,14 @@ typedef struct {
                           shifted per node by its maximum; the image is rounded to
                           bfloat16 on input (ac_set_image only). */
   uint64_t seed;       /* seed of the random simplex initialisation in ac_set_image */
+  int refine;          /* r in [0, 4]: solve on the pixel grid refined r times (Sec. 4.1, "at least four
+                          nodes per interface"): every pixel becomes 2^r x 2^r cells carrying the pixel's
+                          colour (data projection by copy, Sec. 4.2), with eps, tau, lambda still in pixel
+                          units.  On cells of side 1 this is the plain step with eps' = 2^r eps,
+                          tau' = 2^r tau, lambda' = 2^-r lambda (the system is the pixel-unit one times
+                          4^r).  Images come in and pixel labels, composites and image gradients go out at
+                          W x H; phase fields, node labels and moments are on the refined grid
+                          ((2^r W + 1)(2^r H + 1) nodes); energies are in pixel units. */
   void *stream;        /* cudaStream_t for all work of this context */
 } ac_params;
 

@@ -180,18 +180,53 @@ def labels(u, W, H):
     return nl.reshape(H + 1, W + 1), pl.reshape(H, W)
 
 
-def composite(u, c, W, H, rounded=False):
+def _pixel_means(u, W, H, r=0):
+    """Mean of each u_i over each image pixel: per cell of the right-diagonal
+    split (2 u00 + u10 + u01 + 2 u11) / 6, averaged over the 4^r cells of the
+    pixel when the solve grid is the W x H pixel grid refined r times.
+    Returns (H, W, N)."""
+    s = 1 << r
+    U = np.asarray(u, dtype=np.float64).reshape(H * s + 1, W * s + 1, -1)
+    cell = (2 * U[:-1, :-1] + U[:-1, 1:] + U[1:, :-1] + 2 * U[1:, 1:]) / 6.0
+    return cell.reshape(H, s, W, s, -1).mean(axis=(1, 3))
+
+
+def pixel_labels(u, W, H, r=0):
+    """Pixel labels (Sec. 4.3): argmax_i of the pixel mean of u_i, lowest
+    index on ties.  (H, W) int8."""
+    return np.argmax(_pixel_means(u, W, H, r), axis=2).astype(np.int8)
+
+
+def composite(u, c, W, H, rounded=False, r=0):
     """Composite image (Sec. 4.3): per pixel sum_i c_i ubar_i, ubar_i the mean
     of u_i over the pixel (both triangles of the right-diagonal split, i.e.
-    (2 u00 + u10 + u01 + 2 u11) / 6); rounded: c of the pixel label (the
-    rounded composite).  Returns (H, W, 3) float64."""
-    U = np.asarray(u, dtype=np.float64).reshape(H + 1, W + 1, -1)
-    ubar = (2 * U[:-1, :-1] + U[:-1, 1:] + U[1:, :-1] + 2 * U[1:, 1:]) / 6.0
+    (2 u00 + u10 + u01 + 2 u11) / 6 per cell); rounded: c of the pixel label
+    (the rounded composite).  Returns (H, W, 3) float64."""
+    ubar = _pixel_means(u, W, H, r)
     c = np.asarray(c, dtype=np.float64)
     if rounded:
-        _, pix = labels(u, W, H)
-        return c[pix.astype(int)]
+        return c[np.argmax(ubar, axis=2)]
     return ubar @ c
+
+
+def refine_image(img, r):
+    """The pixel grid refined r times with data projection by copy (Sec. 4.1,
+    4.2): every pixel becomes 2^r x 2^r cells carrying its colour (no
+    interpolation, no new values)."""
+    s = 1 << r
+    return np.repeat(np.repeat(np.asarray(img, dtype=np.float64), s, axis=0), s, axis=1)
+
+
+def refined_params(eps, lam, tau, r):
+    """The step on the refined mesh in pixel units (cells of side h = 2^-r,
+    eps, tau, lambda in pixel units) written on cells of side 1: the lumped
+    mass and the fitting integrals scale with the cell area h^2, the 2-D P1
+    stiffness does not scale, so S_px = h^2 (M + (tau eps / h^2) A) and
+    b_px = h^2 (M u (1 + 2 tau/eps) - tau lambda f): the unit-cell step with
+    eps' = 2^r eps, tau' = 2^r tau (tau' eps' = 4^r tau eps, tau'/eps' =
+    tau/eps) and lambda' = 2^-r lambda (tau' lambda' = tau lambda).
+    Returns (eps', lambda', tau')."""
+    return eps * 2.0 ** r, lam * 2.0 ** -r, tau * 2.0 ** r
 
 
 def run(img, u0, eps, lam, tau, steps, tol=1e-13, method="ssc", **kw):

@@ -33,7 +33,7 @@ class ac_params(C.Structure):
     _fields_ = [("width", C.c_int), ("height", C.c_int), ("n_phases", C.c_int),
                 ("eps", C.c_double), ("lambda_", C.c_double), ("tau", C.c_double), ("tol", C.c_double),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("max_cycles", C.c_int), ("coarse_min", C.c_int),
-                ("precision", C.c_int), ("seed", C.c_uint64), ("stream", C.c_void_p)]
+                ("precision", C.c_int), ("seed", C.c_uint64), ("refine", C.c_int), ("stream", C.c_void_p)]
 
 
 class ac_stats(C.Structure):
@@ -325,11 +325,16 @@ def ac_last_error() -> str:
 
 
 class Segmenter:
-    """Owns one context: image W x H, N phases.  Convenience over the C calls."""
+    """Owns one context: image W x H, N phases.  Convenience over the C calls.
+    With refine = r the phase field, node labels and moments live on the grid
+    refined r times (Wr x Hr cells); images, pixel labels and composites stay
+    W x H."""
 
     def __init__(self, W, H, N, eps, lam, tau, **kw):
         self.W, self.H, self.N = W, H, N
-        self.n_nodes = (W + 1) * (H + 1)
+        r = kw.get("refine", 0)
+        self.Wr, self.Hr = W << r, H << r
+        self.n_nodes = (self.Wr + 1) * (self.Hr + 1)
         self.params = ac_default_params(width=W, height=H, n_phases=N, eps=eps, tau=tau, **{"lambda": lam}, **kw)
         self.ctx = ac_create(self.params)
 
@@ -367,7 +372,7 @@ class Segmenter:
         return lab
 
     def node_labels(self):
-        lab = np.zeros((self.H + 1, self.W + 1), np.int8)
+        lab = np.zeros((self.Hr + 1, self.Wr + 1), np.int8)
         ac_get_node_labels(self.ctx, lab, self.n_nodes)
         return lab
 

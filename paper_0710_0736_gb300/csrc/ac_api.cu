@@ -185,12 +185,18 @@ struct AdjState {
   double *part = nullptr, *tot = nullptr, *scal = nullptr;
   double *kw = nullptr, *kr = nullptr, *kp = nullptr, *kq = nullptr, *kq_prev = nullptr;  // flexible CG vectors
   double *kpart = nullptr, *ktot = nullptr;  // its dot products
+  double *gimg = nullptr;   // dL/dI on the refined grid (refine > 0)
   Solve sv;                 // FP64 tangent-form solve
   std::vector<void *> allocs;
 };
 
 struct ac_ctx {
-  ac_params p{};
+  ac_params p{};          // the solve's parameters (on the refined grid when refine > 0)
+  int r = 0;              // refinements of the pixel grid
+  int W0 = 0, H0 = 0;     // the image size in pixels
+  void *img_up = nullptr; // device image copied onto the refined grid (refine > 0)
+  size_t img_up_bytes = 0;
+  int8_t *lab = nullptr;  // device staging of labels for host copies (nodes of the solve grid)
   int N = 0;
   int64_t n = 0;
   const ac::Ops *ops = nullptr;
@@ -248,9 +254,11 @@ int dev_alloc(ac_ctx *ctx, void **p, size_t bytes) {
 int validate(const ac_params *p) {
   if (!p) return fail(AC_ERR_ARG, "params is NULL");
   if (p->width < 1 || p->height < 1) return fail(AC_ERR_ARG, "image size must be >= 1x1");
-  if ((int64_t)(p->width + 1) * (p->height + 1) > (int64_t)1 << 31)
-    return fail(AC_ERR_ARG, "image too large (more than 2^31 nodes)");
-  if (p->height + 1 > 65535) return fail(AC_ERR_ARG, "image height must be below 65535 (one grid row per node row)");
+  if (p->refine < 0 || p->refine > 4) return fail(AC_ERR_ARG, "refine must be in [0, 4]");
+  const int64_t Wr = (int64_t)p->width << p->refine, Hr = (int64_t)p->height << p->refine;
+  if ((Wr + 1) * (Hr + 1) > (int64_t)1 << 31)
+    return fail(AC_ERR_ARG, "image too large (more than 2^31 nodes on the solve grid)");
+  if (Hr + 1 > 65535) return fail(AC_ERR_ARG, "solve grid height must be below 65535 (one grid row per node row)");
   if (p->n_phases < 2 || p->n_phases > AC_MAX_PHASES)
     return fail(AC_ERR_ARG, "n_phases must be in [2, %d]", AC_MAX_PHASES);
   if (!(p->eps > 0) || !std::isfinite(p->eps)) return fail(AC_ERR_ARG, "eps must be > 0");
@@ -552,10 +560,59 @@ int solve_mixed(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_o
   return status;
 }
 
+// Device staging for labels copied to the host: (W+1)(H+1) bytes of the
+// solve grid, enough for node and pixel labels.
+int label_stage(ac_ctx *ctx, int8_t **out) {
+  if (!ctx->lab) {
+    cudaError_t e = cudaMalloc(&ctx->lab, (size_t)ctx->n);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ctx->lab = nullptr;
+      return fail(AC_ERR_NOMEM, "cudaMalloc for the label staging: %s", cudaGetErrorString(e));
+    }
+  }
+  *out = ctx->lab;
+  return AC_OK;
+}
+
 int copy_out(ac_ctx *ctx, void *dst, const void *src, size_t bytes, int is_device) {
   AC_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->s));
   if (!is_device) AC_CUDA(cudaStreamSynchronize(ctx->s));
   return AC_OK;
+}
+
+// Refined image by copy: cell (x, y) of the solve grid takes pixel
+// (x >> r, y >> r) of the W0-wide input (3 channels).
+template <typename TI>
+__global__ void k_refine_copy(const TI *__restrict__ in, int W0, int r, ac::Geo g, TI *__restrict__ out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= g.W) return;
+  const TI *p = in + ((int64_t)(y >> r) * W0 + (x >> r)) * 3;
+  TI *o = out + ((int64_t)y * g.W + x) * 3;
+  o[0] = p[0];
+  o[1] = p[1];
+  o[2] = p[2];
+}
+
+// Adjoint of the copy: pixel (x, y) of the W0-wide image collects the
+// gradients of its 2^r x 2^r cells of the refined grid (3 channels).
+__global__ void k_refine_sum(const double *__restrict__ fine, int W0, int H0, int r, ac::Geo g,
+                             double *__restrict__ out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= W0 || y >= H0) return;
+  double s[3] = {0.0, 0.0, 0.0};
+  const int side = 1 << r;
+  for (int b = 0; b < side; ++b)
+    for (int a = 0; a < side; ++a) {
+      const double *p = fine + ((int64_t)((y << r) + b) * g.W + ((x << r) + a)) * 3;
+      s[0] += p[0];
+      s[1] += p[1];
+      s[2] += p[2];
+    }
+  double *o = out + ((int64_t)y * W0 + x) * 3;
+  o[0] = s[0];
+  o[1] = s[1];
+  o[2] = s[2];
 }
 
 template <typename TI>
@@ -624,7 +681,20 @@ int ac_create(ac_ctx **out, const ac_params *p) {
   if (rc) return rc;
   ac_ctx *ctx = new (std::nothrow) ac_ctx;
   if (!ctx) return fail(AC_ERR_NOMEM, "host allocation failed");
+  // refinement (Sec. 4.1): the solve runs on cells of side 1 of the refined
+  // grid, where the pixel-unit step (mass and fitting integrals scale by
+  // 4^-r, the 2-D stiffness is scale-invariant) is 4^-r times the plain step
+  // with eps' = 2^r eps, tau' = 2^r tau, lambda' = 2^-r lambda
+  ctx->r = p->refine;
+  ctx->W0 = p->width;
+  ctx->H0 = p->height;
   ctx->p = *p;
+  ctx->p.width = p->width << p->refine;
+  ctx->p.height = p->height << p->refine;
+  ctx->p.eps = std::ldexp(p->eps, p->refine);
+  ctx->p.tau = std::ldexp(p->tau, p->refine);
+  ctx->p.lambda = std::ldexp(p->lambda, -p->refine);
+  p = &ctx->p;
   ctx->N = p->n_phases;
   ctx->ops = ops_for(ctx->N);
   ctx->s = (cudaStream_t)p->stream;
@@ -719,6 +789,8 @@ void ac_destroy(ac_ctx *ctx) {
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   for (void *p : ctx->allocs) cudaFree(p);
   if (ctx->img) cudaFree(ctx->img);
+  if (ctx->img_up) cudaFree(ctx->img_up);
+  if (ctx->lab) cudaFree(ctx->lab);
   if (ctx->img16) cudaFree(ctx->img16);
   if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
   delete ctx;
@@ -727,8 +799,10 @@ void ac_destroy(ac_ctx *ctx) {
 static int set_image_impl(ac_ctx *ctx, const void *rgb, int is_device, bool f64) {
   if (!ctx || !rgb) return fail(AC_ERR_ARG, "NULL argument");
   const ac::Geo &g = ctx->g0;
-  const int64_t count = (int64_t)g.W * g.H * 3;
-  const size_t bytes = (size_t)count * (f64 ? sizeof(double) : sizeof(float));
+  const int64_t count = (int64_t)g.W * g.H * 3;                // on the solve grid
+  const int64_t count0 = (int64_t)ctx->W0 * ctx->H0 * 3;       // the image as given
+  const size_t esz = f64 ? sizeof(double) : sizeof(float);
+  const size_t bytes = (size_t)count0 * esz;
   const bool mixed = ctx->p.precision == AC_MIXED;
   if (mixed && f64) return fail(AC_ERR_ARG, "AC_MIXED takes a float32 image (it is stored in bfloat16)");
   const void *src = rgb;
@@ -746,6 +820,31 @@ static int set_image_impl(ac_ctx *ctx, const void *rgb, int is_device, bool f64)
     }
     AC_CUDA(cudaMemcpyAsync(ctx->img, rgb, bytes, cudaMemcpyHostToDevice, ctx->s));
     src = ctx->img;
+  }
+  if (ctx->r > 0) {
+    // data projection by copy (Sec. 4.2): every cell of the refined grid
+    // takes its pixel's colour
+    const size_t up_bytes = (size_t)count * esz;
+    if (ctx->img_up_bytes < up_bytes) {
+      if (ctx->img_up) cudaFree(ctx->img_up);
+      ctx->img_up = nullptr;
+      ctx->img_up_bytes = 0;
+      cudaError_t e = cudaMalloc(&ctx->img_up, up_bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->img_up = nullptr;
+        return fail(AC_ERR_NOMEM, "cudaMalloc(%zu) for the refined image: %s", up_bytes, cudaGetErrorString(e));
+      }
+      ctx->img_up_bytes = up_bytes;
+    }
+    const dim3 grid((unsigned)((g.W + 255) / 256), (unsigned)g.H);
+    if (f64)
+      AC_RUN(AC_PROF_SETUP, (k_refine_copy<double><<<grid, 256, 0, ctx->s>>>((const double *)src, ctx->W0, ctx->r,
+                                                                              g, (double *)ctx->img_up), 1));
+    else
+      AC_RUN(AC_PROF_SETUP, (k_refine_copy<float><<<grid, 256, 0, ctx->s>>>((const float *)src, ctx->W0, ctx->r, g,
+                                                                             (float *)ctx->img_up), 1));
+    src = ctx->img_up;
   }
   if (mixed) {
     if (!ctx->img16) {
@@ -833,7 +932,7 @@ int ac_step(ac_ctx *ctx, int n_steps, ac_stats *out) {
   if (out && n_steps > 0) {
     AC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 1, ctx->energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
     AC_CUDA(cudaStreamSynchronize(ctx->s));
-    st.energy = ctx->h_scalars[1];
+    st.energy = std::ldexp(ctx->h_scalars[1], -ctx->r);  // pixel units: E = 2^-r E(eps', lambda')
   }
   if (out) *out = st;
   return status;
@@ -844,9 +943,13 @@ int ac_segment(ac_ctx *ctx, int n_steps, int8_t *pixel_labels, int is_device, ac
   int rc = ac_step(ctx, n_steps, out);
   if (rc && rc != AC_ERR_NOT_CONVERGED) return rc;
   const ac::Geo &g = ctx->g0;
-  const size_t bytes = (size_t)g.W * g.H;
-  int8_t *dst = is_device ? pixel_labels : reinterpret_cast<int8_t *>(ctx->sv.rt);  // rt holds >= W*H bytes
-  AC_RUN(AC_PROF_SETUP, ctx->ops->labels(ctx->u, g, nullptr, dst, ctx->s));
+  const size_t bytes = (size_t)ctx->W0 * ctx->H0;
+  int8_t *dst = pixel_labels;
+  if (!is_device) {
+    int rc2 = label_stage(ctx, &dst);
+    if (rc2) return rc2;
+  }
+  AC_RUN(AC_PROF_SETUP, ctx->ops->labels(ctx->u, g, ctx->r, nullptr, dst, ctx->s));
   if (!is_device) {
     int rc2 = copy_out(ctx, pixel_labels, dst, bytes, 0);
     if (rc2) return rc2;
@@ -897,8 +1000,12 @@ int ac_get_rhs(ac_ctx *ctx, double *b) {
 
 int ac_get_node_labels(ac_ctx *ctx, int8_t *labels, int is_device) {
   if (!ctx || !labels) return fail(AC_ERR_ARG, "NULL argument");
-  int8_t *dst = is_device ? labels : reinterpret_cast<int8_t *>(ctx->sv.rt);
-  AC_RUN(AC_PROF_SETUP, ctx->ops->labels(ctx->u, ctx->g0, dst, nullptr, ctx->s));
+  int8_t *dst = labels;
+  if (!is_device) {
+    int rc = label_stage(ctx, &dst);
+    if (rc) return rc;
+  }
+  AC_RUN(AC_PROF_SETUP, ctx->ops->labels(ctx->u, ctx->g0, ctx->r, dst, nullptr, ctx->s));
   if (!is_device) return copy_out(ctx, labels, dst, (size_t)ctx->n, 0);
   return AC_OK;
 }
@@ -906,7 +1013,7 @@ int ac_get_node_labels(ac_ctx *ctx, int8_t *labels, int is_device) {
 int ac_get_composite(ac_ctx *ctx, float *rgb, int rounded, int is_device) {
   if (!ctx || !rgb) return fail(AC_ERR_ARG, "NULL argument");
   if (!ctx->have_image) return fail(AC_ERR_STATE, "no image");
-  const size_t bytes = (size_t)ctx->p.width * ctx->p.height * 3 * sizeof(float);
+  const size_t bytes = (size_t)ctx->W0 * ctx->H0 * 3 * sizeof(float);
   float *dst = rgb;
   if (!is_device) {
     if (ctx->img_bytes < bytes) {
@@ -927,7 +1034,7 @@ int ac_get_composite(ac_ctx *ctx, float *rgb, int rounded, int is_device) {
   AC_CUDA(cudaMemcpyAsync(ctx->c_tmp, ctx->c, (size_t)3 * ctx->N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
   AC_RUN(AC_PROF_SETUP, ctx->ops->means(ctx->u, ctx->mom, ctx->g0, ctx->part, ctx->tot, ctx->c_tmp, nullptr,
                                         ctx->p.eps, ctx->p.lambda, ctx->s));
-  AC_RUN(AC_PROF_SETUP, ctx->ops->composite(ctx->u, ctx->c_tmp, ctx->g0, rounded ? 1 : 0, dst, ctx->s));
+  AC_RUN(AC_PROF_SETUP, ctx->ops->composite(ctx->u, ctx->c_tmp, ctx->g0, ctx->r, rounded ? 1 : 0, dst, ctx->s));
   if (!is_device) return copy_out(ctx, rgb, dst, bytes, 0);
   return AC_OK;
 }
@@ -938,7 +1045,9 @@ int ac_energy(ac_ctx *ctx, double *energy) {
   AC_CUDA(cudaMemcpyAsync(ctx->c_tmp, ctx->c, (size_t)3 * ctx->N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
   AC_RUN(AC_PROF_SETUP, ctx->ops->means(ctx->u, ctx->mom, ctx->g0, ctx->part, ctx->tot, ctx->c_tmp, ctx->energy,
                                         ctx->p.eps, ctx->p.lambda, ctx->s));
-  return copy_out(ctx, energy, ctx->energy, sizeof(double), 0);
+  int rc = copy_out(ctx, energy, ctx->energy, sizeof(double), 0);
+  *energy = std::ldexp(*energy, -ctx->r);  // pixel units: E = 2^-r E(eps', lambda') on the refined cells
+  return rc;
 }
 
 int ac_residual(ac_ctx *ctx, double *rho) {
@@ -1059,6 +1168,7 @@ int adj_setup(ac_ctx *ctx, int T, int every) {
   ADJ_ALLOC(A.kq, fN);
   ADJ_ALLOC(A.kq_prev, fN);
   ADJ_ALLOC(A.kpart, (size_t)ac::kMaxPartBlocks * 2 * sizeof(double));
+  if (ctx->r > 0) ADJ_ALLOC(A.gimg, (size_t)ctx->g0.W * ctx->g0.H * 3 * sizeof(double));
   ADJ_ALLOC(A.ktot, 2 * sizeof(double));
   Solve &S = A.sv;
   S.o = &ctx->ops->adjoint;
@@ -1240,12 +1350,20 @@ int ac_adjoint_backward(ac_ctx *ctx, const double *grad_u, double *grad_lambda, 
     }
   }
   if (grad_u0) AC_CUDA(cudaMemcpyAsync(grad_u0, A.g, fN, cudaMemcpyDeviceToDevice, ctx->s));
-  AC_RUN(AC_PROF_SETUP, o->adj_image(A.gm, ctx->img64, ctx->g0, grad_image, ctx->s));
+  if (ctx->r > 0) {
+    // refined grid: the cells' gradients, then their sums over each pixel
+    // (the adjoint of the copy); lambda' = 2^-r lambda, eps' = 2^r eps
+    AC_RUN(AC_PROF_SETUP, o->adj_image(A.gm, ctx->img64, ctx->g0, A.gimg, ctx->s));
+    AC_RUN(AC_PROF_SETUP, (k_refine_sum<<<dim3((unsigned)((ctx->W0 + 255) / 256), (unsigned)ctx->H0), 256, 0, ctx->s>>>(
+                               A.gimg, ctx->W0, ctx->H0, ctx->r, ctx->g0, grad_image), 1));
+  } else {
+    AC_RUN(AC_PROF_SETUP, o->adj_image(A.gm, ctx->img64, ctx->g0, grad_image, ctx->s));
+  }
   AC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 2, A.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
   AC_CUDA(cudaMemcpyAsync(ctx->u, A.uT, fN, cudaMemcpyDeviceToDevice, ctx->s));  // leave u = u^T
   AC_CUDA(cudaStreamSynchronize(ctx->s));
-  *grad_lambda = ctx->h_scalars[2];
-  *grad_eps = ctx->h_scalars[3];
+  *grad_lambda = std::ldexp(ctx->h_scalars[2], -ctx->r);
+  *grad_eps = std::ldexp(ctx->h_scalars[3], ctx->r);
   if (status) fail(status, "an adjoint solve did not reach its tolerance");
   return status;
 }

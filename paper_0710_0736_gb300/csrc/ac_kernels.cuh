@@ -1281,76 +1281,89 @@ static __global__ void k_absmax(const double *__restrict__ v, int64_t count, dou
 }
 
 // ---------------------------------------------------------------------------
-// a10: rounded composite (Sec. 4.3).  Node label = argmax_i u_n,i; pixel
-// label = argmax_i (2 u00 + u10 + u01 + 2 u11) (the pixel integral of u_i
-// on the right-diagonal split, times 6); lowest index on ties.
+// a10: labels and the composite image (Sec. 4.3), on the pixels of the image
+// (the solve grid may be the pixel grid refined r times).
 // ---------------------------------------------------------------------------
-// Composite (Sec. 4.3): per pixel sum_i c_i ubar_i, ubar_i = the pixel mean
-// of u_i on the right-diagonal split, (2 u00 + u10 + u01 + 2 u11) / 6;
-// rounded: c of the pixel's label (argmax of ubar, lowest index on ties), the
-// rounded composite.  Output H x W x 3 float.
+// Pixel integrals (times 6) of u_i on the right-diagonal split, summed over
+// the 2^r x 2^r cells of pixel (px, py) of the refined grid (r = 0: the cell
+// itself): v_i = sum (2 u00 + u10 + u01 + 2 u11).
 template <int N>
-__global__ void k_composite(const double *__restrict__ u, const double *__restrict__ c, Geo g, int rounded,
-                            float *__restrict__ out) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-  if (x >= g.W || y >= g.H) return;
-  const int64_t n = (int64_t)y * g.Wn + x;
-  double a[N], b10[N], b01[N], b11[N];
-  ldn<double, N>(u + n * N, a);
-  ldn<double, N>(u + (n + 1) * N, b10);
-  ldn<double, N>(u + (n + g.Wn) * N, b01);
-  ldn<double, N>(u + (n + g.Wn + 1) * N, b11);
-  double rgb[3] = {0.0, 0.0, 0.0};
+__device__ __forceinline__ void pixel_integrals(const double *__restrict__ u, const Geo &g, int r, int px, int py,
+                                                double (&v)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = 0.0;
+  const int side = 1 << r;
+  for (int b = 0; b < side; ++b)
+    for (int a = 0; a < side; ++a) {
+      const int64_t n = (int64_t)((py << r) + b) * g.Wn + ((px << r) + a);
+      double a0[N], b10[N], b01[N], b11[N];
+      ldn<double, N>(u + n * N, a0);
+      ldn<double, N>(u + (n + 1) * N, b10);
+      ldn<double, N>(u + (n + g.Wn) * N, b01);
+      ldn<double, N>(u + (n + g.Wn + 1) * N, b11);
+#pragma unroll
+      for (int i = 0; i < N; ++i) v[i] += 2.0 * a0[i] + b10[i] + b01[i] + 2.0 * b11[i];
+    }
+}
+
+// argmax with the lowest index on ties.
+template <int N>
+__device__ __forceinline__ int argmax_low(const double (&v)[N]) {
   int best = 0;
-  double bv = 0.0;
+#pragma unroll
+  for (int i = 1; i < N; ++i)
+    if (v[i] > v[best]) best = i;
+  return best;
+}
+
+// Composite (Sec. 4.3): per pixel sum_i c_i ubar_i, ubar_i = the pixel mean
+// of u_i (pixel_integrals / (6 4^r)); rounded: c of the pixel's label (argmax
+// of ubar, lowest index on ties), the rounded composite.  Output
+// (H >> r) x (W >> r) x 3 float, pixels of the image.
+template <int N>
+__global__ void k_composite(const double *__restrict__ u, const double *__restrict__ c, Geo g, int r, int rounded,
+                            float *__restrict__ out) {
+  const int W0 = g.W >> r, H0 = g.H >> r;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= W0 || y >= H0) return;
+  double v[N];
+  pixel_integrals<N>(u, g, r, x, y, v);
+  const int best = argmax_low<N>(v);
+  const double scale = 1.0 / (6.0 * (double)(1 << (2 * r)));
+  double rgb[3] = {0.0, 0.0, 0.0};
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    const double v = 2.0 * a[i] + b10[i] + b01[i] + 2.0 * b11[i];
-    if (i == 0 || v > bv) {
-      bv = v;
-      best = i;
-    }
-    const double m = v / 6.0;
+    const double m = v[i] * scale;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) rgb[ch] += c[i * 3 + ch] * m;
   }
-  float *o = out + ((int64_t)y * g.W + x) * 3;
+  float *o = out + ((int64_t)y * W0 + x) * 3;
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch) o[ch] = (float)(rounded ? c[best * 3 + ch] : rgb[ch]);
 }
 
+// Node label = argmax_i u_n,i (lowest index on ties), on the solve grid.
 template <int N>
-__global__ void k_labels(const double *__restrict__ u, Geo g, int8_t *__restrict__ node_lab,
-                         int8_t *__restrict__ pix_lab) {
+__global__ void k_labels(const double *__restrict__ u, Geo g, int8_t *__restrict__ node_lab) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x > g.W) return;
   const int64_t n = (int64_t)y * g.Wn + x;
   double a[N];
   ldn<double, N>(u + n * N, a);
-  if (node_lab) {
-    int best = 0;
-#pragma unroll
-    for (int i = 1; i < N; ++i)
-      if (a[i] > a[best]) best = i;
-    node_lab[n] = (int8_t)best;
-  }
-  if (pix_lab && x < g.W && y < g.H) {
-    double b10[N], b01[N], b11[N];
-    ldn<double, N>(u + (n + 1) * N, b10);
-    ldn<double, N>(u + (n + g.Wn) * N, b01);
-    ldn<double, N>(u + (n + g.Wn + 1) * N, b11);
-    int best = 0;
-    double bv = 0.0;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const double v = 2.0 * a[i] + b10[i] + b01[i] + 2.0 * b11[i];
-      if (i == 0 || v > bv) {
-        bv = v;
-        best = i;
-      }
-    }
-    pix_lab[(int64_t)y * g.W + x] = (int8_t)best;
-  }
+  node_lab[n] = (int8_t)argmax_low<N>(a);
+}
+
+// Pixel label = argmax_i of the pixel integral of u_i, (2 u00 + u10 + u01 +
+// 2 u11) per cell of the right-diagonal split, summed over the pixel's 4^r
+// cells; lowest index on ties.  Output (H >> r) x (W >> r).
+template <int N>
+__global__ void k_pixel_labels(const double *__restrict__ u, Geo g, int r, int8_t *__restrict__ pix_lab) {
+  const int W0 = g.W >> r, H0 = g.H >> r;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= W0 || y >= H0) return;
+  double v[N];
+  pixel_integrals<N>(u, g, r, x, y, v);
+  pix_lab[(int64_t)y * W0 + x] = (int8_t)argmax_low<N>(v);
 }
 
 // Kernel-level projection of count independent N-vectors onto the simplex.

@@ -178,13 +178,22 @@ struct Launch {
     k_outer_update<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, delta, g);
     return 1;
   }
-  static int composite(const double *u, const double *c, const Geo &g, int rounded, float *out, cudaStream_t s) {
-    k_composite<N><<<row_grid(g.W, g.H), kBlock, 0, s>>>(u, c, g, rounded, out);
+  static int composite(const double *u, const double *c, const Geo &g, int r, int rounded, float *out,
+                       cudaStream_t s) {
+    k_composite<N><<<row_grid(g.W >> r, g.H >> r), kBlock, 0, s>>>(u, c, g, r, rounded, out);
     return 1;
   }
-  static int labels(const double *u, const Geo &g, int8_t *node_lab, int8_t *pix_lab, cudaStream_t s) {
-    k_labels<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, g, node_lab, pix_lab);
-    return 1;
+  static int labels(const double *u, const Geo &g, int r, int8_t *node_lab, int8_t *pix_lab, cudaStream_t s) {
+    int k = 0;
+    if (node_lab) {
+      k_labels<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, g, node_lab);
+      ++k;
+    }
+    if (pix_lab) {
+      k_pixel_labels<N><<<row_grid(g.W >> r, g.H >> r), kBlock, 0, s>>>(u, g, r, pix_lab);
+      ++k;
+    }
+    return k;
   }
   static int adj_prepare(const double *up, const double *g, int64_t n, double *freeset, double *rhs, cudaStream_t s) {
     k_adj_prepare<N><<<blocks_for(n), kBlock, 0, s>>>(up, g, n, freeset, rhs);

@@ -59,8 +59,9 @@ struct Ops {
   int (*outer_resid)(const double *u, const double *b, const Geo &g, float *r32, float *u32, double *rho, bool rho32,
                      cudaStream_t s);
   int (*outer_update)(double *u, const float *delta, const Geo &g, cudaStream_t s);
-  int (*labels)(const double *u, const Geo &g, int8_t *node_lab, int8_t *pix_lab, cudaStream_t s);
-  int (*composite)(const double *u, const double *c, const Geo &g, int rounded, float *out, cudaStream_t s);
+  // pixel outputs are on the image's pixels: the solve grid g coarsened r times
+  int (*labels)(const double *u, const Geo &g, int r, int8_t *node_lab, int8_t *pix_lab, cudaStream_t s);
+  int (*composite)(const double *u, const double *c, const Geo &g, int r, int rounded, float *out, cudaStream_t s);
   int (*project)(const double *y, double *x, int64_t count, cudaStream_t s);
   SolverOps fp64;     // T = double, direct form
   SolverOps mixed;    // T = float, shifted form

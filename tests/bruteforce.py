@@ -103,3 +103,17 @@ def kkt_violation(S, B, U, act_tol=1e-12):
         if (~inact).any():
             below = max(below, max(0.0, mu - G[n, ~inact].min()))
     return spread, below
+
+
+def prolong_p1(u, W, H):
+    """P1 interpolation of a node field (n, N) on the W x H cell grid to the
+    grid refined once (nested right-diagonal meshes: new nodes on axis edges
+    take the mean of the edge's ends, new nodes on the SW-NE diagonal the mean
+    of the diagonal's ends).  Returns ((2W+1)(2H+1), N)."""
+    U = np.asarray(u, dtype=np.float64).reshape(H + 1, W + 1, -1)
+    F = np.zeros((2 * H + 1, 2 * W + 1, U.shape[2]))
+    F[::2, ::2] = U
+    F[::2, 1::2] = 0.5 * (U[:, :-1] + U[:, 1:])
+    F[1::2, ::2] = 0.5 * (U[:-1] + U[1:])
+    F[1::2, 1::2] = 0.5 * (U[:-1, :-1] + U[1:, 1:])
+    return F.reshape(-1, U.shape[2])

@@ -42,7 +42,7 @@ def test_default_params(ac):
 
 
 @pytest.mark.parametrize("field,value", [
-    ("width", 0), ("height", -3), ("height", 70000), ("n_phases", 1), ("n_phases", 9), ("eps", 0.0), ("tau", -1.0),
+    ("width", 0), ("height", -3), ("height", 70000), ("refine", -1), ("refine", 5), ("n_phases", 1), ("n_phases", 9), ("eps", 0.0), ("tau", -1.0),
     ("lambda_", -0.5), ("tol", 0.0), ("nu1", -1), ("max_cycles", 0), ("coarse_min", 0), ("precision", 7),
 ])
 def test_create_rejects_bad_params(ac, field, value):

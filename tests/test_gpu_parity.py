@@ -363,6 +363,82 @@ def test_composite_matches_oracle(ac, precision):
     seg.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("r", [1, 2])
+def test_refine_matches_oracle(ac, precision, r):
+    """refine = r (Sec. 4.1): the context takes the W x H image and
+    eps, lambda, tau in pixel units; the oracle runs the copy-refined image
+    (refine_image) with refined_params on the same start.  Phase fields
+    within 1e-10 (FP64, both solved to 3e-15) or 1e-7 (mixed, tol 1e-12);
+    pixel labels and composites aggregated over each pixel's cells; the
+    energy in pixel units."""
+    W0, H0, N = 24, 16, 4
+    s = 1 << r
+    img = synth.shapes_image(41 + r, W0, H0, rect_side=(3, 10), disk_r=(2, 6))
+    prec = ac.AC_MIXED if precision == "mixed" else ac.AC_FP64
+    tol = TIGHT if precision == "fp64" else 1e-12
+    u0 = synth.dirichlet_init(43, (W0 * s + 1) * (H0 * s + 1), N)
+    seg = ac.Segmenter(W0, H0, N, 2.0, 1.0, 4.0, tol=tol, max_cycles=3000, precision=prec, refine=r)
+    seg.set_image(img)
+    seg.set_phase(u0)
+    st = seg.step(3)
+    assert st.converged
+    img_used = synth.round_bf16(img).astype(np.float64) if precision == "mixed" else img.astype(np.float64)
+    fine = oracle.refine_image(img_used, r)
+    e2, l2, t2 = oracle.refined_params(2.0, 1.0, 4.0, r)
+    u_ref, _, _ = oracle.run(fine, u0, e2, l2, t2, 3, tol=TIGHT)
+    u = seg.phase()
+    assert np.abs(u - u_ref).max() < (1e-10 if precision == "fp64" else 1e-7)
+    # pixel labels of the W0 x H0 image: equal except at near ties
+    lab = seg.segment(0)
+    ref_lab = oracle.pixel_labels(u, W0, H0, r)
+    diff = lab != ref_lab
+    if diff.any():
+        pm = np.sort(oracle._pixel_means(u, W0, H0, r), axis=2)
+        assert (pm[..., -1] - pm[..., -2])[diff].max() < 1e-12
+    m = oracle.moments(fine)
+    c, _ = oracle.means(u, m, W0 * s, H0 * s, seg.means())
+    for rounded in (False, True):
+        assert np.abs(seg.composite(rounded) - oracle.composite(u, c, W0, H0, rounded, r)).max() <= 2.4e-7
+    E = oracle.energy(u, m, W0 * s, H0 * s, e2, l2) * 2.0 ** -r
+    assert seg.energy() == pytest.approx(E, rel=1e-12)
+    seg.close()
+
+
+def test_refine_adjoint_matches_oracle(ac):
+    """Gradients through T steps on the refined grid, mapped back to the
+    pixel-unit lambda (x 2^-r), eps (x 2^r, tau held fixed) and the W x H
+    image (sum over each pixel's cells, the adjoint of the copy), against the
+    FP64 oracle adjoint of the refined problem: 1e-6 relative."""
+    W0, H0, N, r, T, every = 12, 8, 3, 1, 4, 2
+    s = 1 << r
+    img = synth.shapes_image(51, W0, H0, rect_side=(2, 6), disk_r=(1.5, 4), sigma=0.08).astype(np.float64)
+    u0 = synth.dirichlet_init(52, (W0 * s + 1) * (H0 * s + 1), N)
+    target = synth.voronoi_labels(53, W0 * s + 1, H0 * s + 1, n_seeds=4, n_labels=N)
+    import torch
+    seg = ac.Segmenter(W0, H0, N, 2.0, 1.0, 4.0, tol=1e-14, max_cycles=3000, refine=r)
+    seg.set_image(img)
+    seg.set_phase(u0)
+    ac.ac_adjoint_forward(seg.ctx, T, every)
+    uT = seg.phase()
+    fine = oracle.refine_image(img, r)
+    m0 = oracle.moments(fine)[:, 0]
+    _, gT = oracle.misfit_loss(uT, m0, target)
+    g_img = torch.zeros((H0, W0, 3), dtype=torch.float64, device="cuda")
+    g_u0 = torch.zeros((seg.n_nodes, N), dtype=torch.float64, device="cuda")
+    gl, ge = ac.ac_adjoint_backward(seg.ctx, torch.tensor(gT, device="cuda"), g_img, g_u0)
+    seg.close()
+    e2, l2, t2 = oracle.refined_params(2.0, 1.0, 4.0, r)
+    states = oracle.forward_states(fine, u0, e2, l2, t2, T)
+    rl, re_, rimg, ru0 = oracle.adjoint(fine, states, e2, l2, t2, gT)
+    assert gl == pytest.approx(rl * 2.0 ** -r, rel=1e-6)
+    assert ge == pytest.approx(re_ * 2.0 ** r, rel=1e-6)
+    rimg0 = rimg.reshape(H0, s, W0, s, 3).sum(axis=(1, 3))
+    gi = g_img.cpu().numpy()
+    assert np.abs(gi - rimg0).max() <= 1e-6 * np.abs(rimg0).max()
+    assert np.abs(g_u0.cpu().numpy() - ru0).max() <= 1e-6 * np.abs(ru0).max()
+
+
 def _mixed(ac, W, H, N, tol, **kw):
     return ac.Segmenter(W, H, N, kw.pop("eps", 2.0), kw.pop("lam", 1.0), kw.pop("tau", 4.0), tol=tol,
                         max_cycles=kw.pop("max_cycles", 2000), precision=ac.AC_MIXED, **kw)

@@ -455,3 +455,72 @@ def test_composite_pixel_mean_is_exact_for_linear_fields(oracle_mod):
     tc = (0.1 + 0.03 * xc + 0.05 * yc) / (0.1 + 0.03 * W + 0.05 * H)
     assert np.abs(comp[..., 0] - tc).max() < 1e-15
     assert np.abs(comp[..., 1] - (1 - tc)).max() < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# Pixel-grid refinement with data projection by copy (Sec. 4.1, 4.2)
+# ---------------------------------------------------------------------------
+
+def test_refined_step_is_the_pixel_unit_step(oracle_mod):
+    """On the pixel grid refined r times (cells of side h = 2^-r in pixel
+    units) the P1 lumped mass and the fitting integrals scale with the cell
+    area h^2 and the 2-D stiffness does not scale.  The pixel-unit system
+    (S_px, b_px) built from those facts equals 4^-r times the unit-cell system
+    with refined_params(): same minimiser."""
+    W0, H0, N, r = 6, 4, 3, 1
+    eps, lam, tau = 2.0, 1.5, 4.0
+    s = 1 << r
+    W, H = W0 * s, H0 * s
+    img = np.random.default_rng(0).uniform(size=(H0, W0, 3))
+    fine = oracle_mod.refine_image(img, r)
+    assert fine.shape == (H, W, 3) and np.array_equal(fine[::s, ::s], img)
+    u = synth.dirichlet_init(1, (W + 1) * (H + 1), N)
+    mhat, col, val, cnt = oracle_mod.assemble(W, H)
+    m_unit = oracle_mod.moments(fine)
+    c, _ = oracle_mod.means(u, m_unit, W, H)
+
+    def A_times(v):
+        out = np.zeros_like(v)
+        for k in range(v.shape[0]):
+            for j in range(cnt[k]):
+                out[k] += val[k, j] * v[col[k, j]]
+        return out
+
+    h2 = 4.0 ** -r
+    f_unit = (m_unit[:, 4:5] - 2 * m_unit[:, 1:4] @ c.T + m_unit[:, 0:1] * (c * c).sum(1)[None, :])
+    S_px = h2 * mhat[:, None] * u + tau * eps * A_times(u)
+    b_px = h2 * mhat[:, None] * u * (1 + 2 * tau / eps) - tau * lam * h2 * f_unit
+    e2, l2, t2 = oracle_mod.refined_params(eps, lam, tau, r)
+    S_unit = mhat[:, None] * u + t2 * e2 * A_times(u)
+    b_unit = oracle_mod.rhs(u, m_unit, c, W, H, e2, l2, t2)
+    assert np.abs(S_unit - S_px / h2).max() <= 1e-13 * np.abs(S_unit).max()
+    assert np.abs(b_unit - b_px / h2).max() <= 1e-13 * np.abs(b_unit).max()
+
+
+def test_refined_labels_reduce_to_the_plain_ones(oracle_mod):
+    """r = 0: the pixel-mean labels are the oracle's pixel labels."""
+    W, H, N = 15, 11, 4
+    u = synth.dirichlet_init(3, (W + 1) * (H + 1), N)
+    _, pl = oracle_mod.labels(u, W, H)
+    np.testing.assert_array_equal(oracle_mod.pixel_labels(u, W, H, 0), pl)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_refined_exact_segmentation_of_stripes(oracle_mod, seed):
+    """The noise-free stripes of the exact-segmentation pin, solved on the
+    pixel grid refined once (eps, tau, lambda in pixel units) from the P1
+    interpolation of the unrefined start: the pixel labels are the stripe
+    labels up to a swap, and at the unrefined grid's nodes the phase field is
+    within the discretisation difference (0.1) of the unrefined solution.  (A
+    random start drawn on the refined grid itself coarsens differently and may
+    settle in another local minimum of the non-convex evolution.)"""
+    W, H, r = 48, 24, 1
+    img = synth.stripes_image(W, H, [8, 12, 10, 18], [(0.9, 0.2, 0.1), (0.1, 0.3, 0.8)])
+    truth = np.broadcast_to(((np.arange(W) >= 8) & (np.arange(W) < 20) | (np.arange(W) >= 30)).astype(np.int8), (H, W))
+    u0 = synth.dirichlet_init(seed, (W + 1) * (H + 1), 2)
+    e2, l2, t2 = oracle_mod.refined_params(2.0, 1.0, 4.0, r)
+    u, _, _ = oracle_mod.run(oracle_mod.refine_image(img, r), BF.prolong_p1(u0, W, H), e2, l2, t2, 30, tol=1e-12)
+    pl = oracle_mod.pixel_labels(u, W, H, r)
+    assert np.array_equal(pl, truth) or np.array_equal(pl, 1 - truth)
+    uc, _, _ = oracle_mod.run(img, u0, 2.0, 1.0, 4.0, 30, tol=1e-12)
+    assert np.abs(u.reshape(2 * H + 1, 2 * W + 1, 2)[::2, ::2] - uc.reshape(H + 1, W + 1, 2)).max() < 0.1
