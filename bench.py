@@ -54,9 +54,11 @@ def parse():
     ap.add_argument("--nu2", type=int, default=3, help="post-smoothing red-black sweeps per V-cycle")
     ap.add_argument("--crop", type=int, default=256, help="side of the image crop the CPU oracle times")
     ap.add_argument("--cpu-steps", type=int, default=3, help="oracle steps in the cpu_baseline sample")
-    ap.add_argument("--workload", choices=["single", "batch", "adjoint"], default="single",
+    ap.add_argument("--workload", choices=["single", "batch", "adjoint", "refine"], default="single",
                     help="single: the 4096^2 N=8 image; batch: 256 uneven images (sizes 128^2..1024^2, N 2/4/6); "
-                         "adjoint: gradients through 64 steps of the 512^2 N=4 disks image")
+                         "adjoint: gradients through 64 steps of the 512^2 N=4 disks image; refine: the 1024^2 "
+                         "N=4 disks/polygons image on its pixel grid refined twice (4096^2 cells)")
+    ap.add_argument("--refine", type=int, default=2, help="refinements of the pixel grid (refine workload)")
     ap.add_argument("--adj-steps", type=int, default=64, help="time steps differentiated (adjoint workload)")
     ap.add_argument("--adj-every", type=int, default=8, help="checkpoint interval (adjoint workload)")
     ap.add_argument("--batch-images", type=int, default=256)
@@ -66,7 +68,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = {"single": 100, "batch": 30, "adjoint": 4}[args.workload]
+        args.steps = {"single": 100, "batch": 30, "adjoint": 4, "refine": 20}[args.workload]
     return args
 
 
@@ -414,6 +416,77 @@ def run_adjoint(args):
     return 0
 
 
+def run_refine(args):
+    """The 1024 x 1024 image of 64 disks and convex polygons in 4 colours
+    (noise 0.1; N = 4, eps = 2 px, lambda = 1, tau = 4) on its pixel grid
+    refined r = 2 times (Sec. 4.1: several nodes per interface), i.e. a
+    4096 x 4096 solve grid, mixed precision to natural residual 1e-6.
+    value = time steps per second."""
+    import torch
+    import oracle
+    from paper_0710_0736_gb300 import ac, synth
+    name = "c2_1024_n4"
+    cfg = dict(synth.CONFIGS[name])
+    W, H, N, r = cfg["W"], cfg["H"], cfg["N"], args.refine
+    tol = args.tol if args.tol is not None else cfg["tol_mixed"]
+    img = synth.config_image(name, 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    seg = ac.Segmenter(W, H, N, cfg["eps"], cfg["lam"], cfg["tau"], tol=tol, max_cycles=1000, precision=ac.AC_MIXED,
+                       refine=r, nu1=args.nu1, nu2=args.nu2, stream=stream.cuda_stream)
+    seg.set_image(torch.from_numpy(img).cuda())
+    seg.step(args.warmup, allow_not_converged=True)
+    ac.ac_set_profiling(seg.ctx, True)
+    launches0 = ac.ac_get_profile(seg.ctx).total_launches
+    clocks = Clocks(0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    _, st = ac.ac_step(seg.ctx, args.steps, allow_not_converged=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = ac.ac_get_profile(seg.ctx)
+    seg.close()
+    n = (seg.Wr + 1) * (seg.Hr + 1)
+    peaks, peak_kind = measured_peaks()
+    sm_launches = prof.launches[ac.PROF_CLASSES.index("smooth")]
+    sm_ms = prof.ms[ac.PROF_CLASSES.index("smooth")]
+    achieved = prof.smooth_bytes_per_launch / (sm_ms / 1e3 / max(1, sm_launches)) / 1e9
+    cpu = None
+    if not args.no_cpu:
+        # the oracle on a 64 x 64 corner of the image, refined the same way
+        crop, steps = 64, 2
+        s = 1 << r
+        ic = oracle.refine_image(img[:crop, :crop], r)
+        e2, l2, t2 = oracle.refined_params(cfg["eps"], cfg["lam"], cfg["tau"], r)
+        u = synth.dirichlet_init(0, (crop * s + 1) ** 2, N)
+        t0 = time.perf_counter()
+        oracle.run(ic, u, e2, l2, t2, steps, tol=tol, nu1=2, nu2=2, max_iter=1000)
+        sec = (time.perf_counter() - t0) / steps * n / (crop * s + 1) ** 2
+        cpu = {"value": 1.0 / sec, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{steps} oracle steps (SSC, V(2,2), tol {tol:g}) on the {crop}x{crop} corner refined "
+                         f"{r} times, scaled by nodes"}
+    line = {"metric": "refined-grid Allen-Cahn steps/s (1024^2 image, pixel grid refined twice)",
+            "value": args.steps / (ms / 1e3), "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{W}x{H} disks/polygons image (64 shapes, 4 colours, noise 0.1), N={N}, "
+                                   f"eps={cfg['eps']} px, lambda={cfg['lam']}, tau={cfg['tau']}, refine={r} "
+                                   f"({seg.Wr}x{seg.Hr} cells), mixed, each step to natural residual {tol:g}",
+                       "nodes": n, "solver": f"truncated monotone multigrid V({args.nu1},{args.nu2})"},
+            "gdof_per_s": N * n * st.fine_sweeps / (ms / 1e3) / 1e9,
+            "vcycles_per_step": st.total_cycles / max(1, st.steps), "all_converged": bool(st.converged),
+            "roofline": {"bound": "hbm", "kernel": "k_smooth_fine<float,4,shifted>", "achieved": achieved,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                         "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None},
+            "gpu_launches": int(prof.total_launches - launches0), "cpu_baseline": cpu, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -422,6 +495,8 @@ def main():
         return run_batch(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "refine":
+        return run_refine(args)
     import torch
     import torch.distributed as dist
 
