@@ -97,7 +97,14 @@ struct Level {
   ac::Geo g;
   int64_t n = 0;
   void *op = nullptr, *r = nullptr, *v = nullptr, *t = nullptr;  // coarse levels only
+  void *v2 = nullptr;  // first coarse level, AC_COARSE_CYCLES > 1: the correction so far
 };
+
+// Linear V-cycles on the coarse levels per coarse correction (a build
+// option, -DAC_COARSE_CYCLES=k, for tuning).
+#ifndef AC_COARSE_CYCLES
+#define AC_COARSE_CYCLES 1
+#endif
 
 // Untruncated entries of P'SP on the first coarse level, one representative
 // coarse node per boundary class.
@@ -497,6 +504,17 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
       AC_RUN(AC_PROF_TRANSFER, o->restrict0(S.rt, g0, L1.g, L1.r, ctx->s));
       int rc2 = coarse_vcycle(ctx, S, 1);
       if (rc2) return rc2;
+      for (int extra = 1; extra < AC_COARSE_CYCLES; ++extra) {
+        // v += V(r - S1 v): the level-1 residual as right-hand side of
+        // another V-cycle (pointer swap of r and t for its duration)
+        AC_RUN(AC_PROF_COARSE, o->coarse_resid(L1.op, L1.r, L1.v, L1.g, L1.t, ctx->s));
+        AC_CUDA(cudaMemcpyAsync(L1.v2, L1.v, (size_t)L1.n * ctx->N * o->elem, cudaMemcpyDeviceToDevice, ctx->s));
+        std::swap(L1.r, L1.t);
+        rc2 = coarse_vcycle(ctx, S, 1);
+        std::swap(L1.r, L1.t);
+        if (rc2) return rc2;
+        AC_RUN(AC_PROF_COARSE, o->vec_add(L1.v, L1.v2, L1.n * ctx->N, ctx->s));
+      }
       AC_RUN(AC_PROF_LINESEARCH, o->line_search(S.x, S.ob, S.rt, L1.v, S.mask, g0, L1.g, S.d, ctx->ls_part,
                                                 ctx->ls_tot, ctx->omega, ctx->s));
       return AC_OK;
@@ -755,6 +773,7 @@ int ac_create(ac_ctx **out, const ac_params *p) {
       AC_ALLOC(L.r, (size_t)L.n * N * es);
       AC_ALLOC(L.v, (size_t)L.n * N * es);
       AC_ALLOC(L.t, (size_t)L.n * N * es);
+      if (k == 1 && AC_COARSE_CYCLES > 1) AC_ALLOC(L.v2, (size_t)L.n * N * es);
     }
     AC_CUDA(cudaMallocHost(&ctx->h_scalars, 4 * sizeof(double)));
     AC_CUDA(cudaMemsetAsync(ctx->c, 0, (size_t)3 * N * sizeof(double), ctx->s));

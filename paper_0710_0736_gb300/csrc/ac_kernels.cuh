@@ -943,6 +943,13 @@ __global__ void k_coarse_resid(const T *__restrict__ op, const T *__restrict__ r
   t[i * nc + K] = r[i * nc + K] - op[i * nc + K] * v[i * nc + K] - op_offdiag<T, N>(op, v, g, nc, x, y, i);
 }
 
+// a += b (count values).
+template <typename T>
+__global__ void k_vec_add(T *__restrict__ a, const T *__restrict__ b, int64_t count) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < count) a[k] += b[k];
+}
+
 // P1 prolongation of phase-major coarse values to fine node (x, y) (nested
 // right-diagonal meshes: odd-odd fine nodes sit on the coarse SW-NE diagonal).
 template <typename T, int N>

@@ -98,6 +98,10 @@ struct SolverLaunch {
     k_coarse_resid<T, N><<<L.grid, L.block, 0, s>>>((const T *)op, (const T *)r, (const T *)v, g, (T *)t);
     return 1;
   }
+  static int vec_add(void *a, const void *b, int64_t count, cudaStream_t s) {
+    k_vec_add<T><<<blocks_for(count), kBlock, 0, s>>>((T *)a, (const T *)b, count);
+    return 1;
+  }
   static int restrict_(const void *t, const Geo &gf, const Geo &gc, void *rc, cudaStream_t s) {
     const PhaseLaunch L = phase_grid(gc.W + 1, gc.H + 1, N);
     k_restrict<T, N><<<L.grid, L.block, 0, s>>>((const T *)t, gf, gc, (T *)rc);
@@ -127,7 +131,7 @@ struct SolverLaunch {
   }
   static SolverOps table() {
     return SolverOps{(int)sizeof(T), smooth,       resid,        restrict0,   galerkin0,   galerkin,   coarse_smooth,
-                     coarse_solve,   coarse_resid, restrict_,    prolong_add, line_search};
+                     coarse_solve,   coarse_resid, restrict_,    prolong_add, line_search, vec_add};
   }
 };
 

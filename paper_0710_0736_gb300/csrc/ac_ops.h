@@ -42,6 +42,7 @@ struct SolverOps {
   // line search: part needs 2 x (blocks of the fine grid) doubles, tot 2 doubles
   int (*line_search)(const void *x, const void *ob, const void *rt, const void *v1, const uint8_t *mask,
                      const Geo &gf, const Geo &gc, void *d, double *part, double *tot, double *omega, cudaStream_t s);
+  int (*vec_add)(void *a, const void *b, int64_t count, cudaStream_t s);  // a += b
 };
 
 struct Ops {
