@@ -97,14 +97,7 @@ struct Level {
   ac::Geo g;
   int64_t n = 0;
   void *op = nullptr, *r = nullptr, *v = nullptr, *t = nullptr;  // coarse levels only
-  void *v2 = nullptr;  // first coarse level, AC_COARSE_CYCLES > 1: the correction so far
 };
-
-// Linear V-cycles on the coarse levels per coarse correction (a build
-// option, -DAC_COARSE_CYCLES=k, for tuning).
-#ifndef AC_COARSE_CYCLES
-#define AC_COARSE_CYCLES 1
-#endif
 
 // Untruncated entries of P'SP on the first coarse level, one representative
 // coarse node per boundary class.
@@ -419,28 +412,34 @@ int read_rho(ac_ctx *ctx, double *out) {
 // ---- multigrid ---------------------------------------------------------------
 
 // Linear V-cycle for S_k v_k = r_k on coarse levels k >= 1 (operators already
-// built), zero initial guess, Gauss-Seidel smoothing in 3 colours.
-int coarse_vcycle(ac_ctx *ctx, Solve &S, int k) {
+// built), zero initial guess.  Smoothing runs in fused pairs of l1-Jacobi
+// sweeps that cannot work in place, so a level's two buffers v and t swap
+// roles: *res returns the one that holds v_k.
+int coarse_vcycle(ac_ctx *ctx, Solve &S, int k, void **res) {
   Level &L = S.lv[k];
   const ac::SolverOps *o = S.o;
   if (k == S.depth - 1) {
     if (L.n <= kCoarsestBlockNodes) {
       AC_CUDA(cudaMemsetAsync(L.v, 0, (size_t)L.n * ctx->N * o->elem, ctx->s));
       AC_RUN(AC_PROF_COARSE, o->coarse_solve(L.op, L.r, L.v, L.g, kCoarsestSweeps, ctx->s));
+      *res = L.v;
     } else {
-      AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, 2 * kCoarseSweeps, true, ctx->s));
+      AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, 2 * kCoarseSweeps, true, res, ctx->s));
     }
     return AC_OK;
   }
   Level &C = S.lv[k + 1];
-  // v starts at 0: the first sweep writes every node without reading v
-  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, true, ctx->s));
-  AC_RUN(AC_PROF_COARSE, o->coarse_resid(L.op, L.r, L.v, L.g, L.t, ctx->s));
-  AC_RUN(AC_PROF_TRANSFER, o->restrict_(L.t, L.g, C.g, C.r, ctx->s));
-  int rc = coarse_vcycle(ctx, S, k + 1);
+  // v starts at 0: the first pair of sweeps writes every node without reading v
+  void *v = nullptr;
+  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, true, &v, ctx->s));
+  void *other = v == L.v ? L.t : L.v;
+  AC_RUN(AC_PROF_COARSE, o->coarse_resid(L.op, L.r, v, L.g, other, ctx->s));
+  AC_RUN(AC_PROF_TRANSFER, o->restrict_(other, L.g, C.g, C.r, ctx->s));
+  void *cv = nullptr;
+  int rc = coarse_vcycle(ctx, S, k + 1, &cv);
   if (rc) return rc;
-  AC_RUN(AC_PROF_TRANSFER, o->prolong_add(C.v, L.g, C.g, L.v, ctx->s));
-  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, false, ctx->s));
+  AC_RUN(AC_PROF_TRANSFER, o->prolong_add(cv, L.g, C.g, v, ctx->s));
+  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, v, other, L.g, kCoarseSweeps, false, res, ctx->s));
   return AC_OK;
 }
 
@@ -502,20 +501,10 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
       for (int k = 1; k + 1 < S.depth; ++k)
         AC_RUN(AC_PROF_TRANSFER, o->galerkin(S.lv[k].op, S.lv[k].g, S.lv[k + 1].g, S.lv[k + 1].op, ctx->s));
       AC_RUN(AC_PROF_TRANSFER, o->restrict0(S.rt, g0, L1.g, L1.r, ctx->s));
-      int rc2 = coarse_vcycle(ctx, S, 1);
+      void *v1 = nullptr;
+      int rc2 = coarse_vcycle(ctx, S, 1, &v1);
       if (rc2) return rc2;
-      for (int extra = 1; extra < AC_COARSE_CYCLES; ++extra) {
-        // v += V(r - S1 v): the level-1 residual as right-hand side of
-        // another V-cycle (pointer swap of r and t for its duration)
-        AC_RUN(AC_PROF_COARSE, o->coarse_resid(L1.op, L1.r, L1.v, L1.g, L1.t, ctx->s));
-        AC_CUDA(cudaMemcpyAsync(L1.v2, L1.v, (size_t)L1.n * ctx->N * o->elem, cudaMemcpyDeviceToDevice, ctx->s));
-        std::swap(L1.r, L1.t);
-        rc2 = coarse_vcycle(ctx, S, 1);
-        std::swap(L1.r, L1.t);
-        if (rc2) return rc2;
-        AC_RUN(AC_PROF_COARSE, o->vec_add(L1.v, L1.v2, L1.n * ctx->N, ctx->s));
-      }
-      AC_RUN(AC_PROF_LINESEARCH, o->line_search(S.x, S.ob, S.rt, L1.v, S.mask, g0, L1.g, S.d, ctx->ls_part,
+      AC_RUN(AC_PROF_LINESEARCH, o->line_search(S.x, S.ob, S.rt, v1, S.mask, g0, L1.g, S.d, ctx->ls_part,
                                                 ctx->ls_tot, ctx->omega, ctx->s));
       return AC_OK;
     });
@@ -773,7 +762,6 @@ int ac_create(ac_ctx **out, const ac_params *p) {
       AC_ALLOC(L.r, (size_t)L.n * N * es);
       AC_ALLOC(L.v, (size_t)L.n * N * es);
       AC_ALLOC(L.t, (size_t)L.n * N * es);
-      if (k == 1 && AC_COARSE_CYCLES > 1) AC_ALLOC(L.v2, (size_t)L.n * N * es);
     }
     AC_CUDA(cudaMallocHost(&ctx->h_scalars, 4 * sizeof(double)));
     AC_CUDA(cudaMemsetAsync(ctx->c, 0, (size_t)3 * N * sizeof(double), ctx->s));

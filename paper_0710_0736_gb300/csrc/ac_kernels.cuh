@@ -826,43 +826,81 @@ __device__ __forceinline__ T op_offdiag(const T *op, const T *v, const Geo &g, i
   return s;
 }
 
-// a7: one l1-Jacobi sweep on a coarse level, vout = vin + (r - S vin) / l1,
-// l1 = sum_j |S_Kj| (convergent for any symmetric positive definite S; one
-// coalesced launch per sweep).  Rows with a zero diagonal stay 0.  ZERO_IN:
-// vin = 0 (the first sweep of a V-cycle level), so vout = r / l1 and vin is
-// not read.  One thread per (node, phase) (phase = blockIdx.z): the phases of
-// a coarse level are independent systems.  Interior nodes take a branch-free
-// copy of the same arithmetic.
-template <typename T, bool ZERO_IN, bool INTERIOR>
-__device__ __forceinline__ void jacobi_node(const T *__restrict__ d_, const T *__restrict__ oE,
-                                            const T *__restrict__ oN, const T *__restrict__ oNE,
-                                            const T *__restrict__ r, const T *__restrict__ vi, T *__restrict__ vout,
-                                            const Geo &g, int x, int y) {
-  const int64_t K = (int64_t)y * g.Wn + x;
-  const bool e = INTERIOR || x < g.W, w = INTERIOR || x > 0, nn = INTERIOR || y < g.H, ss = INTERIOR || y > 0;
-  const T d = d_[K];
-  T sv = ZERO_IN ? T(0) : d * vi[K], l1 = fabs(d), c;
-  if (e) { c = oE[K]; if (!ZERO_IN) sv += c * vi[K + 1]; l1 += fabs(c); }
-  if (w) { c = oE[K - 1]; if (!ZERO_IN) sv += c * vi[K - 1]; l1 += fabs(c); }
-  if (nn) { c = oN[K]; if (!ZERO_IN) sv += c * vi[K + g.Wn]; l1 += fabs(c); }
-  if (ss) { c = oN[K - g.Wn]; if (!ZERO_IN) sv += c * vi[K - g.Wn]; l1 += fabs(c); }
-  if (e && nn) { c = oNE[K]; if (!ZERO_IN) sv += c * vi[K + g.Wn + 1]; l1 += fabs(c); }
-  if (w && ss) { c = oNE[K - g.Wn - 1]; if (!ZERO_IN) sv += c * vi[K - g.Wn - 1]; l1 += fabs(c); }
-  const T v0 = ZERO_IN ? T(0) : vi[K];
-  vout[K] = d > T(0) ? v0 + (r[K] - sv) / l1 : T(0);
-}
-
+// a7: l1-Jacobi smoothing on a coarse level, vout = vin + (r - S vin) / l1,
+// l1 = sum_j |S_Kj| (convergent for any symmetric positive definite S).
+// Rows with a zero diagonal stay 0.  ZERO_IN: vin = 0 (the first sweep of a
+// V-cycle level), so the first sweep gives r / l1 and vin is not read.  The
+// phases of a coarse level are independent systems.
+// Two l1-Jacobi sweeps fused, one kJ2X x kJ2Y tile of one phase plane per
+// block (phase = blockIdx.z).  The operator and vin on the tile plus a halo
+// of 2, and r on the tile plus a halo of 1, are staged in shared memory
+// (nodes outside the grid as 0: their coefficients are 0, so they drop out of
+// every sum); the first sweep runs on the tile plus a halo of 1, the second on
+// the tile, which is then written once.  Each node's sums run in the fixed
+// order C, E, W, N, S, NE, SW, so the halo nodes recomputed by neighbouring
+// tiles agree bit for bit; one read and one write of the level per pair of
+// sweeps, and no neighbour loads through L1/L2.  vout must not alias vin
+// unless ZERO_IN (vin unread).
+constexpr int kJ2X = 32, kJ2Y = 16, kJ2Threads = 256;
 template <typename T, int N, bool ZERO_IN>
-__global__ void k_coarse_jacobi(const T *__restrict__ op, const T *__restrict__ r, const T *__restrict__ vin,
-                                T *__restrict__ vout, Geo g) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, i = blockIdx.z;
-  if (x > g.W) return;
+__global__ void __launch_bounds__(kJ2Threads) k_coarse_jacobi2(const T *__restrict__ op, const T *__restrict__ r,
+                                                               const T *vin, T *vout, Geo g) {
+  constexpr int AX = kJ2X + 4, AY = kJ2Y + 4;  // tile + halo 2
+  constexpr int BX = kJ2X + 2, BY = kJ2Y + 2;  // tile + halo 1
+  __shared__ T sC[AY][AX], sE[AY][AX], sN[AY][AX], sNE[AY][AX], sV[AY][AX];
+  __shared__ T sR[BY][BX], sV1[BY][BX];
+  const int i = blockIdx.z;
   const int64_t nc = (int64_t)g.Wn * (g.H + 1);
-  const T *d = op + i * nc, *oE = op + (1 * N + i) * nc, *oN = op + (2 * N + i) * nc, *oNE = op + (3 * N + i) * nc;
-  if (x > 0 && x < g.W && y > 0 && y < g.H)
-    jacobi_node<T, ZERO_IN, true>(d, oE, oN, oNE, r + i * nc, vin + i * nc, vout + i * nc, g, x, y);
-  else
-    jacobi_node<T, ZERO_IN, false>(d, oE, oN, oNE, r + i * nc, vin + i * nc, vout + i * nc, g, x, y);
+  const T *C = op + (0 * N + i) * nc, *E = op + (1 * N + i) * nc, *Nn = op + (2 * N + i) * nc,
+          *NE = op + (3 * N + i) * nc, *ri = r + i * nc, *vi = vin + i * nc;
+  T *vo = vout + i * nc;
+  const int x0 = blockIdx.x * kJ2X - 2, y0 = blockIdx.y * kJ2Y - 2;  // grid position of [0][0] of the A arrays
+  for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
+    const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
+    const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
+    const int64_t K = in ? (int64_t)y * g.Wn + x : 0;
+    sC[ay][ax] = in ? C[K] : T(0);
+    sE[ay][ax] = in ? E[K] : T(0);
+    sN[ay][ax] = in ? Nn[K] : T(0);
+    sNE[ay][ax] = in ? NE[K] : T(0);
+    sV[ay][ax] = (!ZERO_IN && in) ? vi[K] : T(0);
+  }
+  for (int t = threadIdx.x; t < BX * BY; t += kJ2Threads) {
+    const int bx = t % BX, by = t / BX, x = x0 + 1 + bx, y = y0 + 1 + by;
+    const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
+    sR[by][bx] = in ? ri[(int64_t)y * g.Wn + x] : T(0);
+  }
+  __syncthreads();
+  // first sweep on the tile + halo 1: B (bx, by) is A (bx + 1, by + 1)
+  for (int t = threadIdx.x; t < BX * BY; t += kJ2Threads) {
+    const int bx = t % BX, by = t / BX, ax = bx + 1, ay = by + 1;
+    const T d = sC[ay][ax];
+    T sv = ZERO_IN ? T(0) : d * sV[ay][ax], l1 = fabs(d), c;
+    c = sE[ay][ax]; if (!ZERO_IN) sv += c * sV[ay][ax + 1]; l1 += fabs(c);
+    c = sE[ay][ax - 1]; if (!ZERO_IN) sv += c * sV[ay][ax - 1]; l1 += fabs(c);
+    c = sN[ay][ax]; if (!ZERO_IN) sv += c * sV[ay + 1][ax]; l1 += fabs(c);
+    c = sN[ay - 1][ax]; if (!ZERO_IN) sv += c * sV[ay - 1][ax]; l1 += fabs(c);
+    c = sNE[ay][ax]; if (!ZERO_IN) sv += c * sV[ay + 1][ax + 1]; l1 += fabs(c);
+    c = sNE[ay - 1][ax - 1]; if (!ZERO_IN) sv += c * sV[ay - 1][ax - 1]; l1 += fabs(c);
+    const T v0 = ZERO_IN ? T(0) : sV[ay][ax];
+    sV1[by][bx] = d > T(0) ? v0 + (sR[by][bx] - sv) / l1 : T(0);
+  }
+  __syncthreads();
+  // second sweep on the tile: tile (tx, ty) is B (tx + 1, ty + 1), A (tx + 2, ty + 2)
+  for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
+    const int tx = t % kJ2X, ty = t / kJ2X, x = x0 + 2 + tx, y = y0 + 2 + ty;
+    if (x > g.W || y > g.H) continue;
+    const int bx = tx + 1, by = ty + 1, ax = tx + 2, ay = ty + 2;
+    const T d = sC[ay][ax];
+    T sv = d * sV1[by][bx], l1 = fabs(d), c;
+    c = sE[ay][ax]; sv += c * sV1[by][bx + 1]; l1 += fabs(c);
+    c = sE[ay][ax - 1]; sv += c * sV1[by][bx - 1]; l1 += fabs(c);
+    c = sN[ay][ax]; sv += c * sV1[by + 1][bx]; l1 += fabs(c);
+    c = sN[ay - 1][ax]; sv += c * sV1[by - 1][bx]; l1 += fabs(c);
+    c = sNE[ay][ax]; sv += c * sV1[by + 1][bx + 1]; l1 += fabs(c);
+    c = sNE[ay - 1][ax - 1]; sv += c * sV1[by - 1][bx - 1]; l1 += fabs(c);
+    vo[(int64_t)y * g.Wn + x] = d > T(0) ? sV1[by][bx] + (sR[by][bx] - sv) / l1 : T(0);
+  }
 }
 
 // Whole-level Gauss-Seidel in one block for small coarsest grids: `sweeps`
@@ -941,13 +979,6 @@ __global__ void k_coarse_resid(const T *__restrict__ op, const T *__restrict__ r
     return;
   }
   t[i * nc + K] = r[i * nc + K] - op[i * nc + K] * v[i * nc + K] - op_offdiag<T, N>(op, v, g, nc, x, y, i);
-}
-
-// a += b (count values).
-template <typename T>
-__global__ void k_vec_add(T *__restrict__ a, const T *__restrict__ b, int64_t count) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < count) a[k] += b[k];
 }
 
 // P1 prolongation of phase-major coarse values to fine node (x, y) (nested

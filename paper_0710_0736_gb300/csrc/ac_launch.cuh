@@ -70,17 +70,24 @@ struct SolverLaunch {
     return 1;
   }
   static int coarse_smooth(const void *op, const void *r, void *v, void *tmp, const Geo &g, int sweeps,
-                           bool zero_start, cudaStream_t s) {
-    const PhaseLaunch L = phase_grid(g.W + 1, g.H + 1, N);
-    for (int k = 0; k < sweeps; ++k) {
-      const T *in = (const T *)(k % 2 == 0 ? v : tmp);
-      T *out = (T *)(k % 2 == 0 ? tmp : v);
-      if (k == 0 && zero_start)
-        k_coarse_jacobi<T, N, true><<<L.grid, L.block, 0, s>>>((const T *)op, (const T *)r, in, out, g);
-      else
-        k_coarse_jacobi<T, N, false><<<L.grid, L.block, 0, s>>>((const T *)op, (const T *)r, in, out, g);
+                           bool zero_start, void **out, cudaStream_t s) {
+    const dim3 grid((unsigned)((g.W + kJ2X) / kJ2X), (unsigned)((g.H + kJ2Y) / kJ2Y), (unsigned)N);
+    void *cur = v;
+    int k = 0;
+    for (int p = 0; p < sweeps / 2; ++p) {
+      if (p == 0 && zero_start) {
+        // v is not read: the pair can write it
+        k_coarse_jacobi2<T, N, true><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)v, (T *)v, g);
+      } else {
+        void *nxt = cur == v ? tmp : v;
+        k_coarse_jacobi2<T, N, false><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)cur,
+                                                                 (T *)nxt, g);
+        cur = nxt;
+      }
+      ++k;
     }
-    return sweeps;
+    *out = cur;
+    return k;
   }
   static int coarse_solve(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s) {
     const int64_t nc = (int64_t)g.Wn * (g.H + 1);
@@ -96,10 +103,6 @@ struct SolverLaunch {
   static int coarse_resid(const void *op, const void *r, const void *v, const Geo &g, void *t, cudaStream_t s) {
     const PhaseLaunch L = phase_grid(g.W + 1, g.H + 1, N);
     k_coarse_resid<T, N><<<L.grid, L.block, 0, s>>>((const T *)op, (const T *)r, (const T *)v, g, (T *)t);
-    return 1;
-  }
-  static int vec_add(void *a, const void *b, int64_t count, cudaStream_t s) {
-    k_vec_add<T><<<blocks_for(count), kBlock, 0, s>>>((T *)a, (const T *)b, count);
     return 1;
   }
   static int restrict_(const void *t, const Geo &gf, const Geo &gc, void *rc, cudaStream_t s) {
@@ -131,7 +134,7 @@ struct SolverLaunch {
   }
   static SolverOps table() {
     return SolverOps{(int)sizeof(T), smooth,       resid,        restrict0,   galerkin0,   galerkin,   coarse_smooth,
-                     coarse_solve,   coarse_resid, restrict_,    prolong_add, line_search, vec_add};
+                     coarse_solve,   coarse_resid, restrict_,    prolong_add, line_search};
   }
 };
 

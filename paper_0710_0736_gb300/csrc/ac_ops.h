@@ -30,11 +30,11 @@ struct SolverOps {
   int (*galerkin0)(const uint8_t *mask, const Geo &gf, const Geo &gc, const Galerkin0Table &tab, void *op,
                    cudaStream_t s);
   int (*galerkin)(const void *opf, const Geo &gf, const Geo &gc, void *opc, cudaStream_t s);
-  // l1-Jacobi sweeps ping-ponging v and tmp (sweeps must be even; the result is in v)
-  // `sweeps` (even) l1-Jacobi sweeps ending in v; zero_start: v = 0 on entry
-  // (it is then neither read nor needs clearing)
+  // `sweeps` (even) l1-Jacobi sweeps in fused pairs starting from v, using v
+  // and tmp in turn; *out returns the buffer holding the result.  zero_start:
+  // v = 0 on entry (it is then neither read nor needs clearing)
   int (*coarse_smooth)(const void *op, const void *r, void *v, void *tmp, const Geo &g, int sweeps, bool zero_start,
-                       cudaStream_t s);
+                       void **out, cudaStream_t s);
   int (*coarse_solve)(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s);
   int (*coarse_resid)(const void *op, const void *r, const void *v, const Geo &g, void *t, cudaStream_t s);
   int (*restrict_)(const void *t, const Geo &gf, const Geo &gc, void *rc, cudaStream_t s);
@@ -42,7 +42,6 @@ struct SolverOps {
   // line search: part needs 2 x (blocks of the fine grid) doubles, tot 2 doubles
   int (*line_search)(const void *x, const void *ob, const void *rt, const void *v1, const uint8_t *mask,
                      const Geo &gf, const Geo &gc, void *d, double *part, double *tot, double *omega, cudaStream_t s);
-  int (*vec_add)(void *a, const void *b, int64_t count, cudaStream_t s);  // a += b
 };
 
 struct Ops {
