@@ -17,7 +17,6 @@ constexpr int kMaxPartBlocks = 1024;
 struct SolverOps {
   int elem;  // sizeof(scalar)
   // sweeps red-black sweeps in place; with corr != null the pending coarse
-  // correction x += (*omega) corr is applied inside the first launch
   // correction x += (*omega) corr is applied inside the first launch; with
   // mask != null the last launch stores its colour's free mask (and rt = 0
   // for that colour if rt != null)
