@@ -82,9 +82,13 @@ ac::Geo make_geo(int W, int H, double te) {
     }
   g.half = ((int64_t)(W + 1) * (H + 1) + 1) / 2;
   g.tef = (float)g.te;
+  g.teh = (float)g.te;
+  g.tel = (float)(g.te - (double)g.teh);
   for (int k = 0; k < 9; ++k) {
     g.Df[k] = (float)g.D[k];
     g.invDf[k] = (float)g.invD[k];
+    g.m0h[k] = (float)g.m0[k];
+    g.m0l[k] = (float)(g.m0[k] - (double)g.m0h[k]);
   }
   return g;
 }

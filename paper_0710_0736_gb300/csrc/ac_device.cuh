@@ -13,6 +13,7 @@
 #include <cstdint>
 #include <type_traits>
 #include <cuda_runtime.h>
+#include "ac_df64.cuh"
 
 namespace ac {
 
@@ -28,6 +29,7 @@ struct Geo {
   double invD[9];  // 1 / S_nn by class
   int64_t half;    // ((W + 1)(H + 1) + 1) / 2: colour-split stride of the FP32 fine arrays
   float tef, Df[9], invDf[9];  // te, D, invD rounded to float (FP32 kernels do no FP64 conversions)
+  float teh, tel, m0h[9], m0l[9];  // te and Mhat as double-floats h + l (the defect correction's residual)
 };
 
 // te, S_nn, 1/S_nn in a kernel's scalar type.

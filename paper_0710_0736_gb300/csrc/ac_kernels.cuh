@@ -284,17 +284,19 @@ __global__ void k_rhs(const double *__restrict__ u, const double *__restrict__ m
 }
 
 // ---------------------------------------------------------------------------
-// Mixed form, FP64 outer defect correction.
+// Mixed form, outer defect correction.
 // k_outer_resid: r = b - S u in FP64, shifted per node by max_i r_i; stores r
-// and u rounded to float (the right-hand side
-// and obstacle of the FP32 correction solve) and the natural
-// residual max_n |P_G(u_n + z_n) - u_n|, z = r/S_nn, computed in FP64 as a
-// correction by the shifted projection (free set found in float, theta and
-// the optimality conditions checked in FP64).
+// and u rounded to float (the right-hand side and obstacle of the FP32
+// correction solve) and the natural residual max_n |P_G(u_n + z_n) - u_n|,
+// z = r/S_nn, computed in FP64 as a correction by the shifted projection
+// (free set found in float, theta and the optimality conditions checked in
+// FP64).  This is the FP64 check that ac_residual reports.
+// k_outer_resid_df: the same residual in double-float arithmetic, the one
+// the mixed solve runs (below).
 // k_outer_update: u <- P_G(u + delta) in FP64 (components on their bound
 // exactly 0).
 // ---------------------------------------------------------------------------
-template <int N, bool RHO32>
+template <int N>
 __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict__ u, const double *__restrict__ b, Geo g,
                                                         float *__restrict__ r32, float *__restrict__ u32,
                                                         double *__restrict__ rho) {
@@ -324,40 +326,126 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
     for (int i = 0; i < N; ++i) {
       r[i] -= mu;
       rf[i] = (float)r[i];
-      uf[i] = (float)uk[i];
+      uf[i] = f64_to_f32_rn(uk[i]);  // the rounding k_outer_update tests against
       z[i] = r[i] * invD;
     }
     const int64_t sl = fslot<float>(g, x, y);
     stn<float, N>(r32 + sl * N, rf);
     stn<float, N>(u32 + sl * N, uf);
-    if constexpr (RHO32) {
-      // the same projection in float on the rounded, shifted data: near the
-      // solution the free components' z and theta are O(rho) and a component
-      // on its bound has u_i <= rho, so the float result is within a few
-      // float ulps of rho itself (the caller keeps a relative margin)
-      float zf[N];
-      const float invDf = g.invDf[cls];
+    // the free set from a float pass, then theta and the optimality
+    // conditions on that set in FP64 (one pass instead of the iteration);
+    // the full FP64 iteration only where the conditions fail (near ties)
+    float zf[N];
+    const float invDf = g.invDf[cls];
 #pragma unroll
-      for (int i = 0; i < N; ++i) zf[i] = rf[i] * invDf;
-      proj_box<float, N, kShifted>(zf, uf);
-      float ef = 0.f;
+    for (int i = 0; i < N; ++i) zf[i] = rf[i] * invDf;
+    const unsigned keep = shifted_free_set<float, N>(zf, uf);
+    if (!shifted_proj_on_set<N>(z, uk, keep)) proj_box<double, N, kShifted>(z, uk);
 #pragma unroll
-      for (int i = 0; i < N; ++i) ef = nanmax<float>(ef, fabsf(zf[i]));
-      e = (double)ef;
-    } else {
-      // the free set from a float pass, then theta and the optimality
-      // conditions on that set in FP64 (one pass instead of the iteration);
-      // the full FP64 iteration only where the conditions fail (near ties)
-      float zf[N];
-      const float invDf = g.invDf[cls];
-#pragma unroll
-      for (int i = 0; i < N; ++i) zf[i] = rf[i] * invDf;
-      const unsigned keep = shifted_free_set<float, N>(zf, uf);
-      if (!shifted_proj_on_set<N>(z, uk, keep)) proj_box<double, N, kShifted>(z, uk);
-#pragma unroll
-      for (int i = 0; i < N; ++i) e = nanmax<double>(e, fabs(z[i]));
-    }
+    for (int i = 0; i < N; ++i) e = nanmax<double>(e, fabs(z[i]));
     if (!(uk[0] == uk[0])) e = uk[0];
+  }
+  block_max_atomic(e, rho);
+}
+
+// The mixed solve's residual.  b and u are read as binary64 bit patterns
+// and split into float heads and tails on the integer pipe (split_f64), and
+//   r = b - Mhat u + tau eps sum_m w_nm (u_m - u)
+// (the same S u, since S = Mhat + tau eps A and A's rows sum to zero) is
+// formed in double-float arithmetic: the differences u_m - u and their
+// weighted sum by two-sums, the products by mul_f2.  Its error is about
+// 2^-46 of the terms' magnitudes (|b|, Mhat |u|, tau eps |u_m - u|), far
+// below the float rounding of the shifted residual it produces; the FP64
+// pipe sees one conversion per block.  Shift, float rounding and the
+// natural residual in float (accurate to a few float ulps of rho near the
+// solution, see solve_mixed) as in the FP64 kernel.
+template <int N>
+__global__ void __launch_bounds__(kBlock) k_outer_resid_df(const double *__restrict__ u, const double *__restrict__ b,
+                                                           Geo g, float *__restrict__ r32, float *__restrict__ u32,
+                                                           double *__restrict__ rho) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  float e = 0.f;
+  if (x <= g.W) {
+    const int64_t n = (int64_t)y * g.Wn + x;
+    float uh[N], ul[N], uf[N], sh[N], sl[N];
+    bool nan_in;
+    {
+      double t[N];
+      ldn<double, N>(u + n * N, t);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        split_f64(t[i], uh[i], ul[i]);
+        uf[i] = f64_to_f32_rn(t[i]);  // the rounding k_outer_update tests against
+        sh[i] = 0.f;
+        sl[i] = 0.f;
+      }
+      nan_in = f64_isnan(t[0]);
+    }
+    // sum_m w_nm (u_m - u): heads by two-sums, tails and errors in float
+    auto add = [&](int64_t m, float w) {
+      double t[N];
+      ldn<double, N>(u + m * N, t);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float h, l;
+        split_f64(t[i], h, l);
+        const f2 d = two_sum(h, -uh[i]);
+        const f2 s = two_sum(sh[i], w * d.h);
+        sh[i] = s.h;
+        sl[i] += s.l + w * (d.l + (l - ul[i]));
+      }
+    };
+    if (x > 0 && x < g.W && y > 0 && y < g.H) {
+      add(n + 1, 1.f);
+      add(n - 1, 1.f);
+      add(n + g.Wn, 1.f);
+      add(n - g.Wn, 1.f);
+    } else {
+      const Weights w = edge_weights(g, x, y);
+      if (w.e > 0.f) add(n + 1, w.e);
+      if (w.w > 0.f) add(n - 1, w.w);
+      if (w.n > 0.f) add(n + g.Wn, w.n);
+      if (w.s > 0.f) add(n - g.Wn, w.s);
+    }
+    const int cls = node_class(g, x, y);
+    const float m0h = g.m0h[cls], m0l = g.m0l[cls];
+    // r_i = rh_i + rl_i, not renormalised: rh_i the rounded sum of the heads
+    float rh[N], rl[N], mu = -INFINITY;
+    {
+      double t[N];
+      ldn<double, N>(b + n * N, t);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float bh, bl;
+        split_f64(t[i], bh, bl);
+        const f2 p = mul_f2(g.teh, g.tel, sh[i], sl[i]);  // tau eps sum_m w_nm (u_m - u)
+        const f2 q = mul_f2(m0h, m0l, uh[i], ul[i]);      // Mhat u
+        const f2 s1 = two_sum(bh, -q.h);
+        const f2 s2 = two_sum(s1.h, p.h);
+        rh[i] = s2.h;
+        rl[i] = s1.l + s2.l + ((bl - q.l) + p.l);
+        mu = fmaxf(mu, rh[i]);
+      }
+    }
+    // shift by the largest head (any per-node constant serves, see above)
+    float rf[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const f2 a = two_sum(rh[i], -mu);
+      rf[i] = a.h + (a.l + rl[i]);
+    }
+    const int64_t slot = fslot<float>(g, x, y);
+    stn<float, N>(r32 + slot * N, rf);
+    stn<float, N>(u32 + slot * N, uf);
+    float zf[N];
+    const float invDf = g.invDf[cls];
+#pragma unroll
+    for (int i = 0; i < N; ++i) zf[i] = rf[i] * invDf;
+    proj_box<float, N, kShifted>(zf, uf);
+#pragma unroll
+    for (int i = 0; i < N; ++i) e = nanmax<float>(e, fabsf(zf[i]));
+    if (nan_in) e = __int_as_float(0x7fc00000);
   }
   block_max_atomic(e, rho);
 }
@@ -366,26 +454,37 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
 // to exactly 0 -- u_i + delta_i would leave the rounding residue
 // u_i - float(u_i) -- and the projection then runs over the other components
 // only, so that exact zeros (the active set) are the same as in the FP64 form.
+// The float rounding of u_i and the widening of delta_i run on the integer
+// pipe, and each FP64 operation on component i is skipped by the whole warp
+// when no lane keeps that component (one or two of N at most nodes).
 template <int N>
 __global__ void k_outer_update(double *__restrict__ u, const float *__restrict__ delta, Geo g) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x > g.W) return;
+  const unsigned lanes = __activemask();
   const int64_t k = (int64_t)y * g.Wn + x;
   double uk[N];
   float dk[N];
   ldn_rw<double, N>(u + k * N, uk);
   ldn<float, N>(delta + fslot<float>(g, x, y) * N, dk);
   unsigned keep = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (!(dk[i] == -f64_to_f32_rn(uk[i]))) keep |= 1u << i;
+  const unsigned any = __reduce_or_sync(lanes, keep);
   double s = 0.0;
-  int cnt = 0;
+  const int cnt = __popc(keep);
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    const bool on_bound = dk[i] == -(float)uk[i];
-    uk[i] = on_bound ? 0.0 : uk[i] + (double)dk[i];
-    if (!on_bound) {
-      keep |= 1u << i;
-      s += uk[i];
-      ++cnt;
+    if ((any >> i) & 1u) {
+      if ((keep >> i) & 1u) {
+        uk[i] += f32_to_f64(dk[i]);
+        s += uk[i];
+      } else {
+        uk[i] = 0.0;
+      }
+    } else {
+      uk[i] = 0.0;
     }
   }
   if (cnt == 0) {  // cannot happen for a feasible correction; fall back to the full projection
@@ -400,21 +499,18 @@ __global__ void k_outer_update(double *__restrict__ u, const float *__restrict__
     unsigned drop = 0;
 #pragma unroll
     for (int i = 0; i < N; ++i)
-      if (((keep >> i) & 1u) && uk[i] <= theta) drop |= 1u << i;
+      if (((any >> i) & 1u) && ((keep >> i) & 1u) && uk[i] <= theta) drop |= 1u << i;
     if (!drop || drop == keep) break;
     keep &= ~drop;
     s = 0.0;
-    cnt = 0;
 #pragma unroll
     for (int i = 0; i < N; ++i)
-      if ((keep >> i) & 1u) {
-        s += uk[i];
-        ++cnt;
-      }
-    theta = (s - 1.0) * rcp_small<double>(cnt);
+      if (((any >> i) & 1u) && ((keep >> i) & 1u)) s += uk[i];
+    theta = (s - 1.0) * rcp_small<double>(__popc(keep));
   }
 #pragma unroll
-  for (int i = 0; i < N; ++i) uk[i] = ((keep >> i) & 1u) ? uk[i] - theta : 0.0;
+  for (int i = 0; i < N; ++i)
+    if ((any >> i) & 1u) uk[i] = ((keep >> i) & 1u) ? uk[i] - theta : 0.0;
   stn<double, N>(u + k * N, uk);
 }
 

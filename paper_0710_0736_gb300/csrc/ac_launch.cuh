@@ -176,9 +176,9 @@ struct Launch {
   static int outer_resid(const double *u, const double *b, const Geo &g, float *r32, float *u32, double *rho,
                          bool rho32, cudaStream_t s) {
     if (rho32)
-      k_outer_resid<N, true><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, b, g, r32, u32, rho);
+      k_outer_resid_df<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, b, g, r32, u32, rho);
     else
-      k_outer_resid<N, false><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, b, g, r32, u32, rho);
+      k_outer_resid<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, b, g, r32, u32, rho);
     return 1;
   }
   static int outer_update(double *u, const float *delta, const Geo &g, cudaStream_t s) {

@@ -53,8 +53,9 @@ struct Ops {
                double *energy, double eps, double lam, cudaStream_t s);
   int (*rhs)(const double *u, const double *mom, const double *c, const Geo &g, double a1, double tl, double *b,
              cudaStream_t s);
-  // rho32: natural residual through the float projection (cheap; accurate to
-  // a few float ulps of u) instead of the FP64 one
+  // rho32: the solve's residual, formed in double-float arithmetic, with the
+  // natural residual through the float projection (accurate to a few float
+  // ulps of rho near the solution); otherwise FP64 throughout
   int (*outer_resid)(const double *u, const double *b, const Geo &g, float *r32, float *u32, double *rho, bool rho32,
                      cudaStream_t s);
   int (*outer_update)(double *u, const float *delta, const Geo &g, cudaStream_t s);

@@ -1,0 +1,179 @@
+"""Host build of the double-float helpers that the mixed form's defect
+correction runs on the GPU (paper_0710_0736_gb300/csrc/ac_df64.cuh): the
+integer-pipe binary64 <-> binary32 conversions and the binary64 split are
+checked against numpy's IEEE conversions and exact rational arithmetic, the
+error-free transformations against exact sums and products."""
+import os
+import shutil
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_0710_0736_gb300", "csrc")
+
+HARNESS = r"""
+#include "ac_df64.cuh"
+#include <cstdio>
+#include <cstring>
+#include <vector>
+int main(int argc, char **argv) {
+  std::vector<unsigned char> in;
+  unsigned char buf[1 << 16];
+  size_t k;
+  while ((k = fread(buf, 1, sizeof buf, stdin)) > 0) in.insert(in.end(), buf, buf + k);
+  const char mode = argv[1][0];
+  if (mode == 'd') {  // doubles -> (rn, h, l) floats
+    size_t n = in.size() / 8;
+    for (size_t i = 0; i < n; ++i) {
+      double d;
+      std::memcpy(&d, &in[8 * i], 8);
+      float o[3];
+      o[0] = ac::f64_to_f32_rn(d);
+      ac::split_f64(d, o[1], o[2]);
+      fwrite(o, 4, 3, stdout);
+    }
+  } else if (mode == 'f') {  // floats -> doubles
+    size_t n = in.size() / 4;
+    for (size_t i = 0; i < n; ++i) {
+      float f;
+      std::memcpy(&f, &in[4 * i], 4);
+      double d = ac::f32_to_f64(f);
+      fwrite(&d, 8, 1, stdout);
+    }
+  } else {  // float quadruples (a, b, c, d) -> two_sum(a, b), fast_two_sum(a, b), (a + c)(b + d)
+    size_t n = in.size() / 16;
+    for (size_t i = 0; i < n; ++i) {
+      float q[4];
+      std::memcpy(q, &in[16 * i], 16);
+      ac::f2 s = ac::two_sum(q[0], q[1]), f = ac::fast_two_sum(q[0], q[1]), m = ac::mul_f2(q[0], q[2], q[1], q[3]);
+      float o[6] = {s.h, s.l, f.h, f.l, m.h, m.l};
+      fwrite(o, 4, 6, stdout);
+    }
+  }
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no C++ compiler")
+    d = tmp_path_factory.mktemp("df64")
+    src = d / "h.cpp"
+    src.write_text(HARNESS)
+    exe = d / "h"
+    subprocess.run([cxx, "-O2", "-std=c++17", "-ffp-contract=off", "-I", CSRC, str(src), "-o", str(exe)], check=True)
+
+    def run(mode, arr):
+        out = subprocess.run([str(exe), mode], input=np.ascontiguousarray(arr).tobytes(), capture_output=True,
+                             check=True).stdout
+        return out
+
+    return run
+
+
+def _doubles(rng, n):
+    e = rng.integers(-150, 140, n).astype(np.float64)
+    m = rng.random(n) + 1.0
+    d = np.ldexp(m, e.astype(np.int64)) * rng.choice([-1.0, 1.0], n)
+    bits = rng.integers(0, 2**63, n, dtype=np.uint64) | (rng.integers(0, 2, n, dtype=np.uint64) << np.uint64(63))
+    d2 = bits.view(np.float64)
+    d2 = d2[np.isfinite(d2) & (np.abs(d2) < 2.0**140) & (np.abs(d2) > 2.0**-150)]
+    special = [0.0, -0.0, 1.0, -1.0, 0.5, 1.0 / 3.0, 2.0**-126, -(2.0**-126), np.nextafter(2.0**-126, 0),
+               2.0**-97, np.nextafter(2.0**-97, 0), 2.0**-96, float(np.finfo(np.float32).max),
+               np.nextafter(2.0**128, 0), 2.0**128, -(2.0**130), np.inf, -np.inf, np.nan, 1e-300, -1e300]
+    # exact ties and near-ties of the binary32 rounding: 29 dropped bits 1000...0, 1000...1, 0111...1
+    base = np.frombuffer(np.array([1.0, 1.5, 0.75, 3.0 + 2.0**-22], dtype=np.float64).tobytes(), dtype=np.uint64)
+    ties = []
+    for b in base:
+        for low in (0x10000000, 0x10000001, 0x0FFFFFFF, 0x30000000, 0x1FFFFFFF):
+            v = (int(b) & ~0x1FFFFFFF) | low
+            ties.append(np.array([v], dtype=np.uint64).view(np.float64)[0])
+            ties.append(np.array([v | (1 << 29)], dtype=np.uint64).view(np.float64)[0])
+    return np.concatenate([d, d2, np.array(special), np.array(ties), -np.array(ties)])
+
+
+def test_narrow_matches_ieee_rounding(harness):
+    rng = np.random.default_rng(5)
+    d = _doubles(rng, 20000)
+    out = np.frombuffer(harness("d", d), dtype=np.float32).reshape(-1, 3)
+    rn = out[:, 0]
+    a = np.abs(d)
+    normal = (a >= 2.0**-126) & (a < 2.0**128)
+    with np.errstate(over="ignore"):
+        ref = d.astype(np.float32)
+    assert (rn[normal].view(np.uint32) == ref[normal].view(np.uint32)).all()
+    tiny = a < 2.0**-126
+    assert (rn[tiny] == 0).all() and (np.signbit(rn[tiny]) == np.signbit(d[tiny])).all()
+    big = np.isfinite(d) & (a >= 2.0**128)
+    assert np.isinf(rn[big]).all() and (np.sign(rn[big]) == np.sign(d[big])).all()
+    assert np.isnan(rn[np.isnan(d)]).all()
+    assert (np.isinf(rn[np.isinf(d)]) & (np.sign(rn[np.isinf(d)]) == np.sign(d[np.isinf(d)]))).all()
+
+
+def test_split_is_truncation_plus_tail(harness):
+    rng = np.random.default_rng(6)
+    d = _doubles(rng, 20000)
+    out = np.frombuffer(harness("d", d), dtype=np.float32).reshape(-1, 3)
+    h, l = out[:, 1], out[:, 2]
+    a = np.abs(d)
+    normal = np.isfinite(d) & (a >= 2.0**-126) & (a < 2.0**128)
+    # the head is the significand truncated to 24 bits
+    bits = d.view(np.uint64)
+    ah = (bits >> np.uint64(32)).astype(np.uint64) & np.uint64(0x7FFFFFFF)
+    lo = bits & np.uint64(0xFFFFFFFF)
+    t = (((ah - np.uint64(0x38000000)) << np.uint64(3)) & np.uint64(0xFFFFFFFF)) | (lo >> np.uint64(29))
+    assert (h[normal].view(np.uint32) & np.uint32(0x7FFFFFFF) == t[normal].astype(np.uint32)).all()
+    assert (np.signbit(h[normal]) == np.signbit(d[normal])).all()
+    for i in np.flatnonzero(normal):
+        err = abs(Fraction(float(d[i])) - Fraction(float(h[i])) - Fraction(float(l[i])))
+        if a[i] >= 2.0**-97:
+            assert err <= Fraction(float(a[i])) / 2**47, (d[i], h[i], l[i])
+            assert l[i] == 0 or np.signbit(l[i]) == np.signbit(d[i])
+        else:
+            assert l[i] == 0 and err < Fraction(float(a[i])) / 2**23
+    tiny = a < 2.0**-126
+    assert (h[tiny] == 0).all() and (l[tiny] == 0).all()
+    assert np.isnan(h[np.isnan(d)]).all() and (l[~np.isfinite(d)] == 0).all()
+    assert np.isinf(h[np.isinf(d)]).all()
+
+
+def test_widen_is_exact(harness):
+    rng = np.random.default_rng(7)
+    f = rng.integers(0, 2**32, 20000, dtype=np.uint64).astype(np.uint32).view(np.float32)
+    f = np.concatenate([f, np.array([0.0, -0.0, 1.0, np.inf, -np.inf, np.nan, 1e-40, -1e-45,
+                                     np.finfo(np.float32).tiny, np.finfo(np.float32).max], dtype=np.float32)])
+    got = np.frombuffer(harness("f", f), dtype=np.float64)
+    normal = np.isfinite(f) & (np.abs(f) >= np.finfo(np.float32).tiny)
+    assert (got[normal] == f[normal].astype(np.float64)).all()
+    sub = np.isfinite(f) & (np.abs(f) < np.finfo(np.float32).tiny)
+    assert (got[sub] == 0).all() and (np.signbit(got[sub]) == np.signbit(f[sub])).all()
+    assert np.isnan(got[np.isnan(f)]).all()
+    assert (got[np.isinf(f)] == f[np.isinf(f)].astype(np.float64)).all()
+
+
+def test_error_free_transformations(harness):
+    rng = np.random.default_rng(8)
+    n = 4000
+    a = (rng.standard_normal(n) * np.exp2(rng.integers(-30, 30, n))).astype(np.float32)
+    b = (rng.standard_normal(n) * np.exp2(rng.integers(-30, 30, n))).astype(np.float32)
+    # |a| >= |b| for the fast two-sum: order each pair
+    swap = np.abs(a) < np.abs(b)
+    a2, b2 = np.where(swap, b, a), np.where(swap, a, b)
+    # tails below half an ulp of their heads: (a2 + c, b2 + dd) are double-floats
+    c = (a2 * rng.random(n).astype(np.float32) * np.float32(2.0**-25)).astype(np.float32)
+    dd = (b2 * rng.random(n).astype(np.float32) * np.float32(2.0**-25)).astype(np.float32)
+    q = np.stack([a2, b2, c, dd], 1).astype(np.float32)
+    out = np.frombuffer(harness("s", q), dtype=np.float32).reshape(-1, 6)
+    for i in range(n):
+        x, y = Fraction(float(q[i, 0])), Fraction(float(q[i, 1]))
+        assert Fraction(float(out[i, 0])) + Fraction(float(out[i, 1])) == x + y
+        assert Fraction(float(out[i, 2])) + Fraction(float(out[i, 3])) == x + y
+        prod = (x + Fraction(float(q[i, 2]))) * (y + Fraction(float(q[i, 3])))
+        got = Fraction(float(out[i, 4])) + Fraction(float(out[i, 5]))
+        assert abs(got - prod) <= abs(prod) / 2**44
