@@ -165,7 +165,9 @@ int ac_get_phase(ac_ctx *ctx, double *u, int is_device);
 int ac_get_means(ac_ctx *ctx, double *c);
 /* Image moments ((H+1)(W+1) x 5 FP64, host): m0, m1 (RGB), m2. */
 int ac_get_moments(ac_ctx *ctx, double *m);
-/* Right-hand side b ((H+1)(W+1) x N FP64, host) of the last step. */
+/* Right-hand side b ((H+1)(W+1) x N FP64, host) of the last step.  The
+ * mixed form (AC_MIXED) holds b as double-float pairs (about 2^-46 of the
+ * terms' magnitudes); their sums are returned. */
 int ac_get_rhs(ac_ctx *ctx, double *b);
 /* Node labels ((H+1)(W+1) int8): argmax of u_n, lowest index on ties. */
 int ac_get_node_labels(ac_ctx *ctx, int8_t *labels, int is_device);

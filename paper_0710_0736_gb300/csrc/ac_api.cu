@@ -538,7 +538,7 @@ int solve_mixed(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_o
   const double accept = ctx->p.tol * (1.0 - kRho32Rel);
   for (;;) {
     AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
-    AC_RUN(AC_PROF_OUTER, o->outer_resid(ctx->u, ctx->b, ctx->g0, ctx->r32, ctx->u32, ctx->rho, rho32, ctx->s));
+    AC_RUN(AC_PROF_OUTER, o->outer_resid(ctx->u, (const float *)ctx->b, ctx->g0, ctx->r32, ctx->u32, ctx->rho, rho32, ctx->s));
     int rc = read_rho(ctx, &rho);
     if (rc) return rc;
     if (std::isnan(rho) || std::isinf(rho)) {
@@ -916,9 +916,16 @@ int ac_step(ac_ctx *ctx, int n_steps, ac_stats *out) {
   for (int t = 0; t < n_steps; ++t) {
     // the energy is only evaluated for the statistics of the last step
     double *energy = (out && t == n_steps - 1) ? ctx->energy : nullptr;
-    AC_RUN(AC_PROF_SETUP, ctx->ops->means(ctx->u, ctx->mom, ctx->g0, ctx->part, ctx->tot, ctx->c, energy, ctx->p.eps,
-                                          ctx->p.lambda, ctx->s));
-    AC_RUN(AC_PROF_SETUP, ctx->ops->rhs(ctx->u, ctx->mom, ctx->c, ctx->g0, a1, tl, ctx->b, ctx->s));
+    if (mixed)
+      AC_RUN(AC_PROF_SETUP, ctx->ops->means_df(ctx->u, ctx->mom, ctx->g0, ctx->part, ctx->tot, ctx->c, energy,
+                                               ctx->p.eps, ctx->p.lambda, ctx->s));
+    else
+      AC_RUN(AC_PROF_SETUP, ctx->ops->means(ctx->u, ctx->mom, ctx->g0, ctx->part, ctx->tot, ctx->c, energy,
+                                            ctx->p.eps, ctx->p.lambda, ctx->s));
+    if (mixed)
+      AC_RUN(AC_PROF_SETUP, ctx->ops->rhs_df(ctx->u, ctx->mom, ctx->c, ctx->g0, a1, tl, (float *)ctx->b, ctx->s));
+    else
+      AC_RUN(AC_PROF_SETUP, ctx->ops->rhs(ctx->u, ctx->mom, ctx->c, ctx->g0, a1, tl, ctx->b, ctx->s));
     ctx->have_rhs = true;
     int cycles = 0, outer = 0;
     double rho = 0;
@@ -1006,7 +1013,17 @@ int ac_get_moments(ac_ctx *ctx, double *m) {
 int ac_get_rhs(ac_ctx *ctx, double *b) {
   if (!ctx || !b) return fail(AC_ERR_ARG, "NULL argument");
   if (!ctx->have_rhs) return fail(AC_ERR_STATE, "no step taken yet");
-  return copy_out(ctx, b, ctx->b, (size_t)ctx->n * ctx->N * sizeof(double), 0);
+  int rc = copy_out(ctx, b, ctx->b, (size_t)ctx->n * ctx->N * sizeof(double), 0);
+  if (rc || ctx->p.precision != AC_MIXED) return rc;
+  // the mixed form holds b as double-floats, N heads then N tails per node
+  // (the bytes of the node's N doubles): h + l in place, node by node
+  const int N = ctx->N;
+  float hl[2 * AC_MAX_PHASES];
+  for (int64_t k = 0; k < ctx->n; ++k) {
+    std::memcpy(hl, b + k * N, (size_t)2 * N * sizeof(float));
+    for (int i = 0; i < N; ++i) b[k * N + i] = (double)hl[i] + (double)hl[N + i];
+  }
+  return AC_OK;
 }
 
 int ac_get_node_labels(ac_ctx *ctx, int8_t *labels, int is_device) {
@@ -1067,7 +1084,7 @@ int ac_residual(ac_ctx *ctx, double *rho) {
   AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
   if (ctx->p.precision == AC_MIXED)
     AC_RUN(AC_PROF_OUTER,
-           ctx->ops->outer_resid(ctx->u, ctx->b, ctx->g0, ctx->r32, ctx->u32, ctx->rho, false, ctx->s));
+           ctx->ops->outer_resid(ctx->u, (const float *)ctx->b, ctx->g0, ctx->r32, ctx->u32, ctx->rho, false, ctx->s));
   else
     AC_RUN(AC_PROF_RESID,
            ctx->ops->fp64.resid(ctx->u, ctx->b, nullptr, ctx->g0, nullptr, nullptr, ctx->rho, -1, ctx->s));

@@ -175,4 +175,11 @@ AC_HD f2 mul_f2(float ah, float al, float bh, float bl) {
   return {p, e + (ah * bl + al * bh)};
 }
 
+// (a.h + a.l) + (bh + bl): one two-sum on the heads, the tails added in
+// float, renormalised (Dekker's add); the error is about 2^-46 (|a| + |b|).
+AC_HD f2 add_f2(f2 a, float bh, float bl) {
+  const f2 s = two_sum(a.h, bh);
+  return fast_two_sum(s.h, s.l + (a.l + bl));
+}
+
 }  // namespace ac

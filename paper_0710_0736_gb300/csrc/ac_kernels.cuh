@@ -284,7 +284,153 @@ __global__ void k_rhs(const double *__restrict__ u, const double *__restrict__ m
 }
 
 // ---------------------------------------------------------------------------
+// Mixed form: a2 and a3 in double-float arithmetic (GB300's FP64 pipe runs
+// at about 1/64 of the FP32 rate; see ac_df64.cuh).  The stored binary64
+// phase field and moments are split on the integer pipe.
+// k_means_partial_df: per thread, k_means_partial's sums over its nodes
+// (same q layout, with ENERGY the energy terms too) as double-float
+// accumulators renormalised after every addition, converted to FP64 once
+// per thread for the block sums.
+// k_rhs_df: b = m0 u (1 + 2 tau/eps) - tau lambda (m2 - 2 c_i.m1 + |c_i|^2 m0)
+// as double-floats, stored node-major as N heads followed by N tails (the
+// bytes of N doubles); the mixed form's residual reads them as they are.
+// Both err by about 2^-46 of the terms' magnitudes.
+// ---------------------------------------------------------------------------
+template <int N, bool ENERGY>
+__global__ void __launch_bounds__(kBlock) k_means_partial_df(const double *__restrict__ u,
+                                                             const double *__restrict__ mom, Geo g,
+                                                             double *__restrict__ part) {
+  constexpr int Q = ENERGY ? 7 : 4;
+  f2 acc[Q * N];
+#pragma unroll
+  for (int k = 0; k < Q * N; ++k) acc[k] = {0.f, 0.f};
+  const int64_t n = (int64_t)g.Wn * (g.H + 1);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned k32 = (unsigned)k;  // n <= 2^31: 32-bit division suffices
+    const int x = (int)(k32 % (unsigned)g.Wn), y = (int)(k32 / (unsigned)g.Wn);
+    const int cls = node_class(g, x, y);
+    const double4 m = ld_mom(mom + k * 4);
+    float mh[5], ml[5];
+    mh[0] = g.m0h[cls];
+    ml[0] = g.m0l[cls];
+    split_f64(m.x, mh[1], ml[1]);
+    split_f64(m.y, mh[2], ml[2]);
+    split_f64(m.z, mh[3], ml[3]);
+    if constexpr (ENERGY) split_f64(m.w, mh[4], ml[4]);
+    float uh[N], ul[N];
+    {
+      double t[N];
+      ldn<double, N>(u + k * N, t);
+#pragma unroll
+      for (int i = 0; i < N; ++i) split_f64(t[i], uh[i], ul[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const f2 p = mul_f2(uh[i], ul[i], mh[q], ml[q]);
+        acc[q * N + i] = add_f2(acc[q * N + i], p.h, p.l);
+      }
+    }
+    if constexpr (ENERGY) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        f2 p = mul_f2(uh[i], ul[i], mh[4], ml[4]);  // u m2
+        acc[4 * N + i] = add_f2(acc[4 * N + i], p.h, p.l);
+        f2 v = two_sum(1.f, -uh[i]);  // 1 - u
+        v.l -= ul[i];
+        p = mul_f2(uh[i], ul[i], v.h, v.l);
+        p = fast_two_sum(p.h, p.l);
+        p = mul_f2(mh[0], ml[0], p.h, p.l);  // m0 u (1 - u)
+        acc[5 * N + i] = add_f2(acc[5 * N + i], p.h, p.l);
+      }
+      // w (u_a - u_b)^2 over the east and north axis edges of the node
+      const Weights w = edge_weights(g, x, y);
+      auto edge = [&](int64_t nb, float we) {
+        double t[N];
+        ldn<double, N>(u + nb * N, t);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          float h, l;
+          split_f64(t[i], h, l);
+          f2 d = two_sum(uh[i], -h);
+          d = fast_two_sum(d.h, d.l + (ul[i] - l));
+          const f2 p = mul_f2(d.h, d.l, d.h, d.l);
+          acc[6 * N + i] = add_f2(acc[6 * N + i], we * p.h, we * p.l);
+        }
+      };
+      if (x < g.W) edge(k + 1, w.e);
+      if (y < g.H) edge(k + g.Wn, w.n);
+    }
+  }
+  double v[Q * N];
+#pragma unroll
+  for (int k = 0; k < Q * N; ++k) v[k] = f32_to_f64(acc[k].h) + f32_to_f64(acc[k].l);
+  block_sum_store<Q * N>(v, part + (int64_t)blockIdx.x * Q * N);
+}
+
+template <int N>
+__global__ void k_rhs_df(const double *__restrict__ u, const double *__restrict__ mom, const double *__restrict__ c,
+                         Geo g, double a1, double tl, float *__restrict__ b) {
+  // per phase, once per block: 2 tau lambda c_i (RGB) and tau lambda |c_i|^2
+  // as double-floats; a1 = 1 + 2 tau/eps and tau lambda likewise
+  __shared__ float coef[N][4][2];
+  __shared__ float sc[2][2];
+  if (threadIdx.x < N) {
+    const int i = threadIdx.x;
+    const double c0 = c[i * 3], c1 = c[i * 3 + 1], c2 = c[i * 3 + 2];
+    split_f64(2.0 * tl * c0, coef[i][0][0], coef[i][0][1]);
+    split_f64(2.0 * tl * c1, coef[i][1][0], coef[i][1][1]);
+    split_f64(2.0 * tl * c2, coef[i][2][0], coef[i][2][1]);
+    split_f64(tl * (c0 * c0 + c1 * c1 + c2 * c2), coef[i][3][0], coef[i][3][1]);
+  }
+  if (threadIdx.x == 32) {
+    split_f64(a1, sc[0][0], sc[0][1]);
+    split_f64(tl, sc[1][0], sc[1][1]);
+  }
+  __syncthreads();
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x > g.W) return;
+  const int64_t k = (int64_t)y * g.Wn + x;
+  const int cls = node_class(g, x, y);
+  const float m0h = g.m0h[cls], m0l = g.m0l[cls];
+  const double4 m = ld_mom(mom + k * 4);
+  float mh[4], ml[4];
+  split_f64(m.x, mh[0], ml[0]);
+  split_f64(m.y, mh[1], ml[1]);
+  split_f64(m.z, mh[2], ml[2]);
+  split_f64(m.w, mh[3], ml[3]);
+  f2 am0 = mul_f2(sc[0][0], sc[0][1], m0h, m0l);
+  am0 = fast_two_sum(am0.h, am0.l);
+  const f2 base = mul_f2(sc[1][0], sc[1][1], mh[3], ml[3]);  // tau lambda m2
+  double t[N];
+  ldn<double, N>(u + k * N, t);
+  float bh[N], bl[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float uh, ul;
+    split_f64(t[i], uh, ul);
+    f2 p = mul_f2(am0.h, am0.l, uh, ul);
+    f2 s = fast_two_sum(p.h, p.l);
+    s = add_f2(s, -base.h, -base.l);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      p = mul_f2(coef[i][q][0], coef[i][q][1], mh[q], ml[q]);
+      s = add_f2(s, p.h, p.l);
+    }
+    p = mul_f2(coef[i][3][0], coef[i][3][1], m0h, m0l);
+    s = add_f2(s, -p.h, -p.l);
+    bh[i] = s.h;
+    bl[i] = s.l;
+  }
+  stn<float, N>(b + k * 2 * N, bh);
+  stn<float, N>(b + k * 2 * N + N, bl);
+}
+
+// ---------------------------------------------------------------------------
 // Mixed form, outer defect correction.
+// b is the double-float right-hand side of k_rhs_df (N heads, N tails per
+// node).
 // k_outer_resid: r = b - S u in FP64, shifted per node by max_i r_i; stores r
 // and u rounded to float (the right-hand side and obstacle of the FP32
 // correction solve) and the natural residual max_n |P_G(u_n + z_n) - u_n|,
@@ -297,7 +443,7 @@ __global__ void k_rhs(const double *__restrict__ u, const double *__restrict__ m
 // exactly 0).
 // ---------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict__ u, const double *__restrict__ b, Geo g,
+__global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict__ u, const float *__restrict__ b, Geo g,
                                                         float *__restrict__ r32, float *__restrict__ u32,
                                                         double *__restrict__ rho) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -308,7 +454,13 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
     double acc[N], uk[N], bk[N];
     nbr_sum<double, N>(u, g, x, y, acc);
     ldn<double, N>(u + n * N, uk);
-    ldn<double, N>(b + n * N, bk);
+    {
+      float bh[N], bl[N];  // b as k_rhs_df stores it
+      ldn<float, N>(b + n * 2 * N, bh);
+      ldn<float, N>(b + n * 2 * N + N, bl);
+#pragma unroll
+      for (int i = 0; i < N; ++i) bk[i] = (double)bh[i] + (double)bl[i];
+    }
     const int cls = node_class(g, x, y);
     const double D = g.D[cls], invD = g.invD[cls];
     float rf[N], uf[N];
@@ -348,8 +500,9 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
   block_max_atomic(e, rho);
 }
 
-// The mixed solve's residual.  b and u are read as binary64 bit patterns
-// and split into float heads and tails on the integer pipe (split_f64), and
+// The mixed solve's residual.  u is read as binary64 bit patterns and split
+// into float heads and tails on the integer pipe (split_f64), b comes as
+// the double-float pairs of k_rhs_df, and
 //   r = b - Mhat u + tau eps sum_m w_nm (u_m - u)
 // (the same S u, since S = Mhat + tau eps A and A's rows sum to zero) is
 // formed in double-float arithmetic: the differences u_m - u and their
@@ -360,7 +513,7 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
 // natural residual in float (accurate to a few float ulps of rho near the
 // solution, see solve_mixed) as in the FP64 kernel.
 template <int N>
-__global__ void __launch_bounds__(kBlock) k_outer_resid_df(const double *__restrict__ u, const double *__restrict__ b,
+__global__ void __launch_bounds__(kBlock) k_outer_resid_df(const double *__restrict__ u, const float *__restrict__ b,
                                                            Geo g, float *__restrict__ r32, float *__restrict__ u32,
                                                            double *__restrict__ rho) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -413,18 +566,17 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid_df(const double *__restr
     // r_i = rh_i + rl_i, not renormalised: rh_i the rounded sum of the heads
     float rh[N], rl[N], mu = -INFINITY;
     {
-      double t[N];
-      ldn<double, N>(b + n * N, t);
+      float bh[N], bl[N];  // b as k_rhs_df stores it
+      ldn<float, N>(b + n * 2 * N, bh);
+      ldn<float, N>(b + n * 2 * N + N, bl);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        float bh, bl;
-        split_f64(t[i], bh, bl);
         const f2 p = mul_f2(g.teh, g.tel, sh[i], sl[i]);  // tau eps sum_m w_nm (u_m - u)
         const f2 q = mul_f2(m0h, m0l, uh[i], ul[i]);      // Mhat u
-        const f2 s1 = two_sum(bh, -q.h);
+        const f2 s1 = two_sum(bh[i], -q.h);
         const f2 s2 = two_sum(s1.h, p.h);
         rh[i] = s2.h;
-        rl[i] = s1.l + s2.l + ((bl - q.l) + p.l);
+        rl[i] = s1.l + s2.l + ((bl[i] - q.l) + p.l);
         mu = fmaxf(mu, rh[i]);
       }
     }

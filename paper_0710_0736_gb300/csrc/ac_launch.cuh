@@ -173,7 +173,28 @@ struct Launch {
     k_rhs<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, mom, c, g, a1, tl, b);
     return 1;
   }
-  static int outer_resid(const double *u, const double *b, const Geo &g, float *r32, float *u32, double *rho,
+  static int means_df(const double *u, const double *mom, const Geo &g, double *part, double *tot, double *c,
+                      double *energy, double eps, double lam, cudaStream_t s) {
+    const int64_t n = (int64_t)g.Wn * (g.H + 1);
+    const int64_t b = (n + kBlock - 1) / kBlock;
+    const int blocks = (int)(b < kMaxPartBlocks ? b : kMaxPartBlocks);
+    if (energy) {
+      k_means_partial_df<N, true><<<blocks, kBlock, 0, s>>>(u, mom, g, part);
+      k_colsum<<<7 * N, 1024, 0, s>>>(part, blocks, 7 * N, tot);
+      k_means_finish<N, true><<<1, 32, 0, s>>>(tot, c, energy, eps, lam);
+    } else {
+      k_means_partial_df<N, false><<<blocks, kBlock, 0, s>>>(u, mom, g, part);
+      k_colsum<<<4 * N, 1024, 0, s>>>(part, blocks, 4 * N, tot);
+      k_means_finish<N, false><<<1, 32, 0, s>>>(tot, c, nullptr, eps, lam);
+    }
+    return 3;
+  }
+  static int rhs_df(const double *u, const double *mom, const double *c, const Geo &g, double a1, double tl,
+                    float *b, cudaStream_t s) {
+    k_rhs_df<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, mom, c, g, a1, tl, b);
+    return 1;
+  }
+  static int outer_resid(const double *u, const float *b, const Geo &g, float *r32, float *u32, double *rho,
                          bool rho32, cudaStream_t s) {
     if (rho32)
       k_outer_resid_df<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, b, g, r32, u32, rho);
@@ -260,6 +281,8 @@ struct Launch {
                           init_random,
                           means,
                           rhs,
+                          means_df,
+                          rhs_df,
                           outer_resid,
                           outer_update,
                           labels,

@@ -53,10 +53,17 @@ struct Ops {
                double *energy, double eps, double lam, cudaStream_t s);
   int (*rhs)(const double *u, const double *mom, const double *c, const Geo &g, double a1, double tl, double *b,
              cudaStream_t s);
-  // rho32: the solve's residual, formed in double-float arithmetic, with the
-  // natural residual through the float projection (accurate to a few float
-  // ulps of rho near the solution); otherwise FP64 throughout
-  int (*outer_resid)(const double *u, const double *b, const Geo &g, float *r32, float *u32, double *rho, bool rho32,
+  // the mixed form's colour means (+ energy) and right-hand side in
+  // double-float arithmetic; b as N float heads then N float tails per node
+  int (*means_df)(const double *u, const double *mom, const Geo &g, double *part, double *tot, double *c,
+                  double *energy, double eps, double lam, cudaStream_t s);
+  int (*rhs_df)(const double *u, const double *mom, const double *c, const Geo &g, double a1, double tl, float *b,
+                cudaStream_t s);
+  // b from rhs_df.  rho32: the solve's residual, formed in double-float
+  // arithmetic, with the natural residual through the float projection
+  // (accurate to a few float ulps of rho near the solution); otherwise FP64
+  // throughout
+  int (*outer_resid)(const double *u, const float *b, const Geo &g, float *r32, float *u32, double *rho, bool rho32,
                      cudaStream_t s);
   int (*outer_update)(double *u, const float *delta, const Geo &g, cudaStream_t s);
   // pixel outputs are on the image's pixels: the solve grid g coarsened r times

@@ -43,6 +43,14 @@ int main(int argc, char **argv) {
       double d = ac::f32_to_f64(f);
       fwrite(&d, 8, 1, stdout);
     }
+  } else if (mode == 'a') {  // float quadruples (ah, al, bh, bl) -> add_f2
+    size_t n = in.size() / 16;
+    for (size_t i = 0; i < n; ++i) {
+      float q[4];
+      std::memcpy(q, &in[16 * i], 16);
+      ac::f2 r = ac::add_f2({q[0], q[1]}, q[2], q[3]);
+      fwrite(&r, 4, 2, stdout);
+    }
   } else {  // float quadruples (a, b, c, d) -> two_sum(a, b), fast_two_sum(a, b), (a + c)(b + d)
     size_t n = in.size() / 16;
     for (size_t i = 0; i < n; ++i) {
@@ -177,3 +185,22 @@ def test_error_free_transformations(harness):
         prod = (x + Fraction(float(q[i, 2]))) * (y + Fraction(float(q[i, 3])))
         got = Fraction(float(out[i, 4])) + Fraction(float(out[i, 5]))
         assert abs(got - prod) <= abs(prod) / 2**44
+
+
+def test_double_float_add(harness):
+    rng = np.random.default_rng(9)
+    n = 4000
+    ah = (rng.standard_normal(n) * np.exp2(rng.integers(-20, 20, n))).astype(np.float32)
+    bh = (rng.standard_normal(n) * np.exp2(rng.integers(-20, 20, n))).astype(np.float32)
+    bh[: n // 4] = -ah[: n // 4] * np.float32(1 + 2.0**-20)  # near-cancellation
+    al = (ah * rng.uniform(-1, 1, n).astype(np.float32) * np.float32(2.0**-25)).astype(np.float32)
+    bl = (bh * rng.uniform(-1, 1, n).astype(np.float32) * np.float32(2.0**-25)).astype(np.float32)
+    q = np.stack([ah, al, bh, bl], 1).astype(np.float32)
+    out = np.frombuffer(harness("a", q), dtype=np.float32).reshape(-1, 2)
+    for i in range(n):
+        a = Fraction(float(q[i, 0])) + Fraction(float(q[i, 1]))
+        b = Fraction(float(q[i, 2])) + Fraction(float(q[i, 3]))
+        got = Fraction(float(out[i, 0])) + Fraction(float(out[i, 1]))
+        assert abs(got - (a + b)) <= (abs(a) + abs(b)) / 2**46
+        # renormalised: the tail is below one ulp of the head
+        assert abs(float(out[i, 1])) <= abs(float(out[i, 0])) * 2.0**-23

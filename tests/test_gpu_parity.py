@@ -107,6 +107,31 @@ def test_means_rhs_energy(ac):
     assert np.abs(seg.rhs() - b_ref).max() < 1e-13
 
 
+@pytest.mark.parametrize("W,H,N", [(64, 64, 4), (37, 23, 3), (96, 64, 8)])
+def test_mixed_means_rhs_energy_double_float(ac, W, H, N):
+    """The mixed form forms the colour means, the energy and the right-hand
+    side in double-float arithmetic (about 2^-46 of the terms' magnitudes):
+    against the FP64 oracle on the BF16-rounded image, with and without the
+    energy terms in the same pass."""
+    img = synth.shapes_image(W * 7 + H, W, H, rect_side=(1, max(1, W // 2)), disk_r=(1, max(1.5, W / 4)))
+    m = oracle.moments(synth.round_bf16(img).astype(np.float64))
+    u0 = synth.dirichlet_init(W + H, (W + 1) * (H + 1), N)
+    c_ref, _ = oracle.means(u0, m, W, H)
+    b_ref = oracle.rhs(u0, m, c_ref, W, H, 2.0, 1.0, 4.0)
+    E_ref = oracle.energy(u0, m, W, H, 2.0, 1.0)
+    for with_energy in (False, True):
+        seg = _mixed(ac, W, H, N, 1e-6)
+        seg.set_image(img)
+        seg.set_phase(u0)
+        if with_energy:
+            st = seg.step(1)
+            assert st.energy == pytest.approx(E_ref, rel=1e-12)
+        else:
+            assert ac.lib.ac_step(seg.ctx, 1, None) == ac.AC_OK
+        assert np.abs(seg.means() - c_ref).max() < 1e-13
+        assert np.abs(seg.rhs() - b_ref).max() < 2e-12 * max(1.0, np.abs(b_ref).max())
+
+
 # --------------------------------------------------------------------------
 # a4-a9: the step solve
 # --------------------------------------------------------------------------
