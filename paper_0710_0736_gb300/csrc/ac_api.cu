@@ -207,6 +207,7 @@ struct ac_ctx {
   cudaStream_t s = nullptr;
   ac::Geo g0{};
   Solve sv;                                    // the multigrid solve of this precision
+  bool delta_warm = false;  // AC_MIXED: sv.x holds the last step's converged single correction
   double *u = nullptr, *b = nullptr, *mom = nullptr;
   float *r32 = nullptr, *u32 = nullptr;        // AC_MIXED: FP32 right-hand side and obstacle
   double *part = nullptr, *tot = nullptr, *c = nullptr, *c_tmp = nullptr, *energy = nullptr;
@@ -550,7 +551,15 @@ int solve_mixed(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_o
       break;
     }
     if (cycles >= ctx->p.max_cycles) break;
-    AC_CUDA(cudaMemsetAsync(ctx->sv.x, 0, (size_t)fine_slots(ctx->n) * ctx->N * sizeof(float), ctx->s));
+    // The first correction of a step starts from the previous step's
+    // converged correction (u^t - u^(t-1) in float): the step's minimiser is
+    // unique, so the start only changes the V-cycle count (7.8 against 8.1
+    // per step at 4096^2, N=8).  The first smoothing sweep makes it feasible
+    // for the new obstacle, so it needs nu1 >= 1; a later correction of the
+    // same step starts from zero.
+    const bool warm = outer == 0 && ctx->delta_warm && ctx->p.nu1 >= 1;
+    ctx->delta_warm = false;
+    if (!warm) AC_CUDA(cudaMemsetAsync(ctx->sv.x, 0, (size_t)fine_slots(ctx->n) * ctx->N * sizeof(float), ctx->s));
     int c = 0;
     int64_t sw = 0;
     double rin = 0;
@@ -561,6 +570,7 @@ int solve_mixed(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_o
     if (rc && rc != AC_ERR_NOT_CONVERGED) return rc;
     AC_RUN(AC_PROF_OUTER, o->outer_update(ctx->u, (const float *)ctx->sv.x, ctx->g0, ctx->s));
     ++outer;
+    ctx->delta_warm = rc == AC_OK && outer == 1;
   }
   *cycles_out = cycles;
   *rho_out = rho;
