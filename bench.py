@@ -3,7 +3,7 @@
 
 Workload (default): the 4096 x 4096 RGB Voronoi-ramp image (8 regions, ramps
 <= 0.2, noise sigma 0.05), N = 8 phases, eps = 3, lambda = 2, tau = 9, each
-time step solved to a natural residual of 1e-6 by V(3,3) cycles; 3 untimed
+time step solved to a natural residual of 1e-6 by V(2,1) cycles; 3 untimed
 steps, then the 100 time steps of the workload timed.  A "step" is one time
 step: colour means + energy, right-hand side, and V-cycles until the
 tolerance.
@@ -50,8 +50,8 @@ def parse():
                     help="steps of the plain FP64 form timed for the vs-FP64 ratio (0: skip)")
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--tol", type=float, default=None)
-    ap.add_argument("--nu1", type=int, default=3, help="pre-smoothing red-black sweeps per V-cycle")
-    ap.add_argument("--nu2", type=int, default=3, help="post-smoothing red-black sweeps per V-cycle")
+    ap.add_argument("--nu1", type=int, default=2, help="pre-smoothing red-black sweeps per V-cycle")
+    ap.add_argument("--nu2", type=int, default=1, help="post-smoothing red-black sweeps per V-cycle")
     ap.add_argument("--crop", type=int, default=256, help="side of the image crop the CPU oracle times")
     ap.add_argument("--cpu-steps", type=int, default=3, help="oracle steps in the cpu_baseline sample")
     ap.add_argument("--workload", choices=["single", "batch", "adjoint", "refine"], default="single",
