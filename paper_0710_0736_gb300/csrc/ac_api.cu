@@ -444,11 +444,11 @@ int coarse_vcycle(ac_ctx *ctx, Solve &S, int k, void **res) {
   AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, true, &v, ctx->s));
   void *other = v == L.v ? L.t : L.v;
   AC_RUN(AC_PROF_COARSE, o->coarse_resid(L.op, L.r, v, L.g, other, ctx->s));
-  AC_RUN(AC_PROF_TRANSFER, o->restrict_(other, L.g, C.g, C.r, ctx->s));
+  AC_RUN(AC_PROF_TRANSFER, o->restrict_(other, L.g, C.g, C.op, C.r, ctx->s));
   void *cv = nullptr;
   int rc = coarse_vcycle(ctx, S, k + 1, &cv);
   if (rc) return rc;
-  AC_RUN(AC_PROF_TRANSFER, o->prolong_add(cv, L.g, C.g, v, ctx->s));
+  AC_RUN(AC_PROF_TRANSFER, o->prolong_add(cv, L.g, C.g, L.op, v, ctx->s));
   AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, v, other, L.g, kCoarseSweeps, false, res, ctx->s));
   return AC_OK;
 }
@@ -510,7 +510,7 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
       AC_RUN(AC_PROF_TRANSFER, o->galerkin0(S.mask, g0, L1.g, S.tab0, L1.op, ctx->s));
       for (int k = 1; k + 1 < S.depth; ++k)
         AC_RUN(AC_PROF_TRANSFER, o->galerkin(S.lv[k].op, S.lv[k].g, S.lv[k + 1].g, S.lv[k + 1].op, ctx->s));
-      AC_RUN(AC_PROF_TRANSFER, o->restrict0(S.rt, g0, L1.g, L1.r, ctx->s));
+      AC_RUN(AC_PROF_TRANSFER, o->restrict0(S.rt, g0, L1.g, L1.op, L1.r, ctx->s));
       void *v1 = nullptr;
       int rc2 = coarse_vcycle(ctx, S, 1, &v1);
       if (rc2) return rc2;

@@ -802,16 +802,30 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
 // of the coarse basis function (weights 1 at 2K, 1/2 at E, W, N, S, NE, SW).
 // k_restrict0: fine (node-major) -> first coarse level (phase-major);
 // k_restrict : coarse -> coarser (both phase-major).
+// A coarse row with a zero diagonal in the coarse operator opc has no free
+// (or active) fine node of its phase in its support, where t = 0: r_c = 0
+// without reading t.
 // ---------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void k_restrict0(const T *__restrict__ t, Geo gf, Geo gc, T *__restrict__ rc) {
+__global__ void k_restrict0(const T *__restrict__ t, Geo gf, Geo gc, const T *__restrict__ opc,
+                            T *__restrict__ rc) {
   const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
   if (X > gc.W) return;
   constexpr int dx[7] = {0, 1, -1, 0, 0, 1, -1};
   constexpr int dy[7] = {0, 0, 0, 1, -1, 1, -1};
+  const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), K = (int64_t)Y * gc.Wn + X;
   T acc[N], v[N];
+  bool live = false;
 #pragma unroll
-  for (int i = 0; i < N; ++i) acc[i] = T(0);
+  for (int i = 0; i < N; ++i) {
+    acc[i] = T(0);
+    live |= opc[i * nc + K] > T(0);
+  }
+  if (!live) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) rc[i * nc + K] = T(0);
+    return;
+  }
 #pragma unroll
   for (int s = 0; s < 7; ++s) {
     const int ax = 2 * X + dx[s], ay = 2 * Y + dy[s];
@@ -821,18 +835,21 @@ __global__ void k_restrict0(const T *__restrict__ t, Geo gf, Geo gc, T *__restri
 #pragma unroll
     for (int i = 0; i < N; ++i) acc[i] += p * v[i];
   }
-  const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), K = (int64_t)Y * gc.Wn + X;
 #pragma unroll
   for (int i = 0; i < N; ++i) rc[i * nc + K] = acc[i];
 }
 
 template <typename T, int N>
-__global__ void k_restrict(const T *__restrict__ t, Geo gf, Geo gc, T *__restrict__ rc) {
+__global__ void k_restrict(const T *__restrict__ t, Geo gf, Geo gc, const T *__restrict__ opc, T *__restrict__ rc) {
   const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y, i = blockIdx.z;
   if (X > gc.W) return;
   constexpr int dx[7] = {0, 1, -1, 0, 0, 1, -1};
   constexpr int dy[7] = {0, 0, 0, 1, -1, 1, -1};
   const int64_t nf = (int64_t)gf.Wn * (gf.H + 1), nc = (int64_t)gc.Wn * (gc.H + 1);
+  if (!(opc[i * nc + (int64_t)Y * gc.Wn + X] > T(0))) {
+    rc[i * nc + (int64_t)Y * gc.Wn + X] = T(0);
+    return;
+  }
   const T *ti = t + i * nf;
   T acc = T(0);
 #pragma unroll
@@ -1050,10 +1067,24 @@ __global__ void __launch_bounds__(kBlock) k_galerkin(const T *__restrict__ opf, 
   const int64_t nf = (int64_t)gf.Wn * (gf.H + 1), nc = (int64_t)gc.Wn * (gc.H + 1);
   const int64_t K = (int64_t)Y * gc.Wn + X;
   T c4[4] = {T(0), T(0), T(0), T(0)};
-  if (X >= 1 && X <= gc.W - 1 && Y >= 1 && Y <= gc.H - 1)
-    galerkin_phase<T, N, true>(opf, gf, gc, nf, X, Y, i, c4);
-  else
-    galerkin_phase<T, N, false>(opf, gf, gc, nf, X, Y, i, c4);
+  // the coarse row is zero when every fine row under the coarse hat (2X, 2Y
+  // and its E, W, N, S, NE, SW neighbours) is zero
+  bool live = false;
+  {
+    constexpr int sx[7] = {0, 1, -1, 0, 0, 1, -1};
+    constexpr int sy[7] = {0, 0, 0, 1, -1, 1, -1};
+#pragma unroll
+    for (int s = 0; s < 7; ++s) {
+      const int ax = 2 * X + sx[s], ay = 2 * Y + sy[s];
+      if (ax >= 0 && ax <= gf.W && ay >= 0 && ay <= gf.H) live |= opf[i * nf + (int64_t)ay * gf.Wn + ax] > T(0);
+    }
+  }
+  if (live) {
+    if (X >= 1 && X <= gc.W - 1 && Y >= 1 && Y <= gc.H - 1)
+      galerkin_phase<T, N, true>(opf, gf, gc, nf, X, Y, i, c4);
+    else
+      galerkin_phase<T, N, false>(opf, gf, gc, nf, X, Y, i, c4);
+  }
 #pragma unroll
   for (int l = 0; l < 4; ++l) opc[(l * N + i) * nc + K] = c4[l];
 }
@@ -1103,11 +1134,28 @@ __global__ void __launch_bounds__(kJ2Threads) k_coarse_jacobi2(const T *__restri
           *NE = op + (3 * N + i) * nc, *ri = r + i * nc, *vi = vin + i * nc;
   T *vo = vout + i * nc;
   const int x0 = blockIdx.x * kJ2X - 2, y0 = blockIdx.y * kJ2Y - 2;  // grid position of [0][0] of the A arrays
+  // A tile whose rows all have a zero diagonal (no free fine node of this
+  // phase under any of them) has vout = 0 whatever vin: write the zeros and
+  // stop.  After phase separation most tiles of a phase are like that.
+  int live = 0;
+  for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
+    const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
+    const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
+    const T c = in ? C[in ? (int64_t)y * g.Wn + x : 0] : T(0);
+    sC[ay][ax] = c;
+    live |= (ax >= 2 && ax < 2 + kJ2X && ay >= 2 && ay < 2 + kJ2Y && c > T(0)) ? 1 : 0;
+  }
+  if (!__syncthreads_or(live)) {
+    for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
+      const int x = x0 + 2 + t % kJ2X, y = y0 + 2 + t / kJ2X;
+      if (x <= g.W && y <= g.H) vo[(int64_t)y * g.Wn + x] = T(0);
+    }
+    return;
+  }
   for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
     const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
     const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
     const int64_t K = in ? (int64_t)y * g.Wn + x : 0;
-    sC[ay][ax] = in ? C[K] : T(0);
     sE[ay][ax] = in ? E[K] : T(0);
     sN[ay][ax] = in ? Nn[K] : T(0);
     sNE[ay][ax] = in ? NE[K] : T(0);
@@ -1213,6 +1261,12 @@ __global__ void k_coarse_resid(const T *__restrict__ op, const T *__restrict__ r
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, i = blockIdx.z;
   if (x > g.W) return;
   const int64_t nc = (int64_t)g.Wn * (g.H + 1), K = (int64_t)y * g.Wn + x;
+  // a row with a zero diagonal is zero, and so is its r (no free fine node of
+  // the phase under it): t = 0 without reading the row
+  if (!(op[i * nc + K] > T(0))) {
+    t[i * nc + K] = T(0);
+    return;
+  }
   if (x > 0 && x < g.W && y > 0 && y < g.H) {
     const T *oE = op + (1 * N + i) * nc, *oN = op + (2 * N + i) * nc, *oNE = op + (3 * N + i) * nc;
     const T *vi = v + i * nc;
@@ -1246,9 +1300,13 @@ __device__ __forceinline__ void prolong_at(const T *vc, const Geo &gc, int x, in
 // v_f += P v_c (coarse levels, phase-major), the arithmetic of prolong_at.
 // PHASES_IN_Z: one thread per (node, phase), phase = blockIdx.z (narrow
 // levels, where latency dominates); otherwise one thread per node doing all
-// phases (wide levels, fewer blocks for the same bytes).
+// phases (wide levels, fewer blocks for the same bytes).  Rows of the fine
+// level's operator opf with a zero diagonal are skipped: the smoothing that
+// follows sets them to 0 whatever they hold (and their coefficients are 0),
+// and the pre-smoothing left them 0.
 template <typename T, int N, bool PHASES_IN_Z>
-__global__ void k_prolong_add(const T *__restrict__ vc, Geo gf, Geo gc, T *__restrict__ vf) {
+__global__ void k_prolong_add(const T *__restrict__ vc, Geo gf, Geo gc, const T *__restrict__ opf,
+                              T *__restrict__ vf) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x > gf.W) return;
   const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), nf = (int64_t)gf.Wn * (gf.H + 1);
@@ -1259,6 +1317,7 @@ __global__ void k_prolong_add(const T *__restrict__ vc, Geo gf, Geo gc, T *__res
 #pragma unroll
   for (int j = 0; j < I; ++j) {
     const int i = PHASES_IN_Z ? (int)blockIdx.z : j;
+    if (!(opf[i * nf + a] > T(0))) continue;
     const T *vi = vc + i * nc;
     T p = vi[K0];
     if (mid) p = T(0.5) * (p + vi[K1]);

@@ -55,8 +55,9 @@ struct SolverLaunch {
                                                    rho, color);
     return 1;
   }
-  static int restrict0(const void *rt, const Geo &gf, const Geo &gc, void *r1, cudaStream_t s) {
-    k_restrict0<T, N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>((const T *)rt, gf, gc, (T *)r1);
+  static int restrict0(const void *rt, const Geo &gf, const Geo &gc, const void *op1, void *r1, cudaStream_t s) {
+    k_restrict0<T, N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>((const T *)rt, gf, gc, (const T *)op1,
+                                                                        (T *)r1);
     return 1;
   }
   static int galerkin0(const uint8_t *mask, const Geo &gf, const Geo &gc, const Galerkin0Table &tab, void *op,
@@ -105,17 +106,18 @@ struct SolverLaunch {
     k_coarse_resid<T, N><<<L.grid, L.block, 0, s>>>((const T *)op, (const T *)r, (const T *)v, g, (T *)t);
     return 1;
   }
-  static int restrict_(const void *t, const Geo &gf, const Geo &gc, void *rc, cudaStream_t s) {
+  static int restrict_(const void *t, const Geo &gf, const Geo &gc, const void *opc, void *rc, cudaStream_t s) {
     const PhaseLaunch L = phase_grid(gc.W + 1, gc.H + 1, N);
-    k_restrict<T, N><<<L.grid, L.block, 0, s>>>((const T *)t, gf, gc, (T *)rc);
+    k_restrict<T, N><<<L.grid, L.block, 0, s>>>((const T *)t, gf, gc, (const T *)opc, (T *)rc);
     return 1;
   }
-  static int prolong_add(const void *vc, const Geo &gf, const Geo &gc, void *vf, cudaStream_t s) {
+  static int prolong_add(const void *vc, const Geo &gf, const Geo &gc, const void *opf, void *vf, cudaStream_t s) {
     if ((int64_t)(gf.W + 1) * (gf.H + 1) >= kWideLevelNodes) {
-      k_prolong_add<T, N, false><<<row_grid(gf.W + 1, gf.H + 1), kBlock, 0, s>>>((const T *)vc, gf, gc, (T *)vf);
+      k_prolong_add<T, N, false><<<row_grid(gf.W + 1, gf.H + 1), kBlock, 0, s>>>((const T *)vc, gf, gc,
+                                                                                 (const T *)opf, (T *)vf);
     } else {
       const PhaseLaunch L = phase_grid(gf.W + 1, gf.H + 1, N);
-      k_prolong_add<T, N, true><<<L.grid, L.block, 0, s>>>((const T *)vc, gf, gc, (T *)vf);
+      k_prolong_add<T, N, true><<<L.grid, L.block, 0, s>>>((const T *)vc, gf, gc, (const T *)opf, (T *)vf);
     }
     return 1;
   }

@@ -25,7 +25,9 @@ struct SolverOps {
   // color < 0: every node; 0: the first colour only (completes a masked smooth)
   int (*resid)(const void *x, const void *rhs, const void *ob, const Geo &g, void *rt, uint8_t *mask, double *rho,
                int color, cudaStream_t s);
-  int (*restrict0)(const void *rt, const Geo &gf, const Geo &gc, void *r1, cudaStream_t s);
+  // transfers skip the rows whose diagonal in the (coarse or fine) level's
+  // operator is 0: those rows and their residuals are exactly 0
+  int (*restrict0)(const void *rt, const Geo &gf, const Geo &gc, const void *op1, void *r1, cudaStream_t s);
   int (*galerkin0)(const uint8_t *mask, const Geo &gf, const Geo &gc, const Galerkin0Table &tab, void *op,
                    cudaStream_t s);
   int (*galerkin)(const void *opf, const Geo &gf, const Geo &gc, void *opc, cudaStream_t s);
@@ -36,8 +38,8 @@ struct SolverOps {
                        void **out, cudaStream_t s);
   int (*coarse_solve)(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s);
   int (*coarse_resid)(const void *op, const void *r, const void *v, const Geo &g, void *t, cudaStream_t s);
-  int (*restrict_)(const void *t, const Geo &gf, const Geo &gc, void *rc, cudaStream_t s);
-  int (*prolong_add)(const void *vc, const Geo &gf, const Geo &gc, void *vf, cudaStream_t s);
+  int (*restrict_)(const void *t, const Geo &gf, const Geo &gc, const void *opc, void *rc, cudaStream_t s);
+  int (*prolong_add)(const void *vc, const Geo &gf, const Geo &gc, const void *opf, void *vf, cudaStream_t s);
   // line search: part needs 2 x (blocks of the fine grid) doubles, tot 2 doubles
   int (*line_search)(const void *x, const void *ob, const void *rt, const void *v1, const uint8_t *mask,
                      const Geo &gf, const Geo &gc, void *d, double *part, double *tot, double *omega, cudaStream_t s);
