@@ -1382,12 +1382,15 @@ __global__ void __launch_bounds__(kBlock) k_ls_dir(const T *__restrict__ x, cons
 
 // d'Sd = sum_n S_nn |d_n|^2 - 2 tau eps sum over axis edges (n, m) of
 // w_nm d_n . d_m, each edge counted once at its west / south end: three
-// node reads per thread (own, east, north) instead of the five of S d.
+// node reads per thread (own, east, north) instead of the five of S d.  A
+// node with no free phase has d_n = 0 (k_ls_dir), so its terms vanish and
+// only its mask byte is read.
 template <typename T, int N>
-__global__ void __launch_bounds__(kBlock) k_ls_curv(const T *__restrict__ d, Geo g, double *__restrict__ part) {
+__global__ void __launch_bounds__(kBlock) k_ls_curv(const T *__restrict__ d, const uint8_t *__restrict__ mask, Geo g,
+                                                    double *__restrict__ part) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   T dot = T(0);
-  if (x <= g.W) {
+  if (x <= g.W && mask[(int64_t)y * g.Wn + x]) {
     T dk[N], t[N];
     ldn<T, N>(d + fslot<T>(g, x, y) * N, dk);
     const Weights w = edge_weights(g, x, y);

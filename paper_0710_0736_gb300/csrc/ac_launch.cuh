@@ -128,7 +128,7 @@ struct SolverLaunch {
     const int blocks = (int)(grid.x * grid.y);
     k_ls_dir<T, N, FORM><<<grid, kBlock, 0, s>>>((const T *)x, (const T *)ob, (const T *)rt, (const T *)v1, mask, gf,
                                                gc, (T *)d, part);
-    k_ls_curv<T, N><<<grid, kBlock, 0, s>>>((const T *)d, gf, part + blocks);
+    k_ls_curv<T, N><<<grid, kBlock, 0, s>>>((const T *)d, mask, gf, part + blocks);
     k_colsum<<<1, 1024, 0, s>>>(part, blocks, 1, tot);
     k_colsum<<<1, 1024, 0, s>>>(part + blocks, blocks, 1, tot + 1);
     k_ls_finish<<<1, 32, 0, s>>>(tot, omega);
