@@ -512,92 +512,157 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
 // pipe sees one conversion per block.  Shift, float rounding and the
 // natural residual in float (accurate to a few float ulps of rho near the
 // solution, see solve_mixed) as in the FP64 kernel.
+// Each block walks kOrRows rows of a strip of kOrThreads columns (one
+// column per thread, kOrThreads - 2 output columns plus one halo column on
+// each side), so every value of u is loaded and split once: a thread keeps
+// the split rows y - 1, y, y + 1 of its column in registers and finds its
+// west and east neighbours in shared memory.
+constexpr int kOrRows = 16, kOrThreads = 256;
+
 template <int N>
-__global__ void __launch_bounds__(kBlock) k_outer_resid_df(const double *__restrict__ u, const float *__restrict__ b,
-                                                           Geo g, float *__restrict__ r32, float *__restrict__ u32,
-                                                           double *__restrict__ rho) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
-  float e = 0.f;
-  if (x <= g.W) {
-    const int64_t n = (int64_t)y * g.Wn + x;
-    float uh[N], ul[N], uf[N], sh[N], sl[N];
-    bool nan_in;
-    {
-      double t[N];
-      ldn<double, N>(u + n * N, t);
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        split_f64(t[i], uh[i], ul[i]);
-        uf[i] = f64_to_f32_rn(t[i]);  // the rounding k_outer_update tests against
-        sh[i] = 0.f;
-        sl[i] = 0.f;
-      }
-      nan_in = f64_isnan(t[0]);
-    }
-    // sum_m w_nm (u_m - u): heads by two-sums, tails and errors in float
-    auto add = [&](int64_t m, float w) {
-      double t[N];
-      ldn<double, N>(u + m * N, t);
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        float h, l;
-        split_f64(t[i], h, l);
-        const f2 d = two_sum(h, -uh[i]);
-        const f2 s = two_sum(sh[i], w * d.h);
-        sh[i] = s.h;
-        sl[i] += s.l + w * (d.l + (l - ul[i]));
-      }
-    };
-    if (x > 0 && x < g.W && y > 0 && y < g.H) {
-      add(n + 1, 1.f);
-      add(n - 1, 1.f);
-      add(n + g.Wn, 1.f);
-      add(n - g.Wn, 1.f);
-    } else {
-      const Weights w = edge_weights(g, x, y);
-      if (w.e > 0.f) add(n + 1, w.e);
-      if (w.w > 0.f) add(n - 1, w.w);
-      if (w.n > 0.f) add(n + g.Wn, w.n);
-      if (w.s > 0.f) add(n - g.Wn, w.s);
-    }
-    const int cls = node_class(g, x, y);
-    const float m0h = g.m0h[cls], m0l = g.m0l[cls];
-    // r_i = rh_i + rl_i, not renormalised: rh_i the rounded sum of the heads
-    float rh[N], rl[N], mu = -INFINITY;
-    {
-      float bh[N], bl[N];  // b as k_rhs_df stores it
-      ldn<float, N>(b + n * 2 * N, bh);
-      ldn<float, N>(b + n * 2 * N + N, bl);
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const f2 p = mul_f2(g.teh, g.tel, sh[i], sl[i]);  // tau eps sum_m w_nm (u_m - u)
-        const f2 q = mul_f2(m0h, m0l, uh[i], ul[i]);      // Mhat u
-        const f2 s1 = two_sum(bh[i], -q.h);
-        const f2 s2 = two_sum(s1.h, p.h);
-        rh[i] = s2.h;
-        rl[i] = s1.l + s2.l + ((bl[i] - q.l) + p.l);
-        mu = fmaxf(mu, rh[i]);
-      }
-    }
-    // shift by the largest head (any per-node constant serves, see above)
-    float rf[N];
+__device__ __forceinline__ void or_load_row(const double *__restrict__ u, const Geo &g, bool col, int x, int y,
+                                            float (&h)[N], float (&l)[N], float (&f)[N]) {
+  if (col && y >= 0 && y <= g.H) {
+    double t[N];
+    ldn<double, N>(u + ((int64_t)y * g.Wn + x) * N, t);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const f2 a = two_sum(rh[i], -mu);
-      rf[i] = a.h + (a.l + rl[i]);
+      split_f64(t[i], h[i], l[i]);
+      f[i] = f64_to_f32_rn(t[i]);  // the rounding k_outer_update tests against
     }
-    const int64_t slot = fslot<float>(g, x, y);
-    stn<float, N>(r32 + slot * N, rf);
-    stn<float, N>(u32 + slot * N, uf);
-    float zf[N];
-    const float invDf = g.invDf[cls];
+  } else {
 #pragma unroll
-    for (int i = 0; i < N; ++i) zf[i] = rf[i] * invDf;
-    proj_box<float, N, kShifted>(zf, uf);
+    for (int i = 0; i < N; ++i) h[i] = l[i] = f[i] = 0.f;
+  }
+}
+
+// sum_m w_nm (u_m - u) for one neighbour m, heads by two-sums, tails and
+// errors in float
+template <int N>
+__device__ __forceinline__ void or_add(const float (&mh)[N], const float (&ml)[N], const float (&uh)[N],
+                                       const float (&ul)[N], float w, float (&sh)[N], float (&sl)[N]) {
 #pragma unroll
-    for (int i = 0; i < N; ++i) e = nanmax<float>(e, fabsf(zf[i]));
-    if (nan_in) e = __int_as_float(0x7fc00000);
+  for (int i = 0; i < N; ++i) {
+    const f2 d = two_sum(mh[i], -uh[i]);
+    const f2 s = two_sum(sh[i], w * d.h);
+    sh[i] = s.h;
+    sl[i] += s.l + w * (d.l + (ml[i] - ul[i]));
+  }
+}
+
+// One output node (x, y) of k_outer_resid_df: r from the split rows (west
+// and east neighbours from the shared row, north and south from the thread's
+// own registers), r32 and u32 stored, and the node's natural-residual term
+// returned (NaN if u is).
+template <int N>
+__device__ __forceinline__ float or_node(const float *__restrict__ b, const Geo &g, int x, int y,
+                                         const float (&rh_s)[N][kOrThreads], const float (&rl_s)[N][kOrThreads],
+                                         int tx, const float (&ph)[N], const float (&pl)[N], const float (&uh)[N],
+                                         const float (&ul)[N], const float (&uf)[N], const float (&nh)[N],
+                                         const float (&nl)[N], float *__restrict__ r32, float *__restrict__ u32) {
+  float sh[N], sl[N];
+  {
+    float eh[N], el[N], wh[N], wl[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      eh[i] = rh_s[i][tx + 1];
+      el[i] = rl_s[i][tx + 1];
+      wh[i] = rh_s[i][tx - 1];
+      wl[i] = rl_s[i][tx - 1];
+      sh[i] = 0.f;
+      sl[i] = 0.f;
+    }
+    if (x > 0 && x < g.W && y > 0 && y < g.H) {
+      or_add<N>(eh, el, uh, ul, 1.f, sh, sl);
+      or_add<N>(wh, wl, uh, ul, 1.f, sh, sl);
+      or_add<N>(nh, nl, uh, ul, 1.f, sh, sl);
+      or_add<N>(ph, pl, uh, ul, 1.f, sh, sl);
+    } else {
+      const Weights w = edge_weights(g, x, y);
+      if (w.e > 0.f) or_add<N>(eh, el, uh, ul, w.e, sh, sl);
+      if (w.w > 0.f) or_add<N>(wh, wl, uh, ul, w.w, sh, sl);
+      if (w.n > 0.f) or_add<N>(nh, nl, uh, ul, w.n, sh, sl);
+      if (w.s > 0.f) or_add<N>(ph, pl, uh, ul, w.s, sh, sl);
+    }
+  }
+  const int64_t n = (int64_t)y * g.Wn + x;
+  const int cls = node_class(g, x, y);
+  const float m0h = g.m0h[cls], m0l = g.m0l[cls];
+  // r_i = rh_i + rl_i, not renormalised: rh_i the rounded sum of the heads
+  float rh[N], rl[N], mu = -INFINITY;
+  {
+    float bh[N], bl[N];  // b as k_rhs_df stores it
+    ldn<float, N>(b + n * 2 * N, bh);
+    ldn<float, N>(b + n * 2 * N + N, bl);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const f2 p = mul_f2(g.teh, g.tel, sh[i], sl[i]);  // tau eps sum_m w_nm (u_m - u)
+      const f2 q = mul_f2(m0h, m0l, uh[i], ul[i]);      // Mhat u
+      const f2 s1 = two_sum(bh[i], -q.h);
+      const f2 s2 = two_sum(s1.h, p.h);
+      rh[i] = s2.h;
+      rl[i] = s1.l + s2.l + ((bl[i] - q.l) + p.l);
+      mu = fmaxf(mu, rh[i]);
+    }
+  }
+  // shift by the largest head (any per-node constant serves, see above)
+  float rf[N], zf[N], of[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const f2 a = two_sum(rh[i], -mu);
+    rf[i] = a.h + (a.l + rl[i]);
+    of[i] = uf[i];
+  }
+  const int64_t slot = fslot<float>(g, x, y);
+  stn<float, N>(r32 + slot * N, rf);
+  stn<float, N>(u32 + slot * N, of);
+  const float invDf = g.invDf[cls];
+#pragma unroll
+  for (int i = 0; i < N; ++i) zf[i] = rf[i] * invDf;
+  proj_box<float, N, kShifted>(zf, of);
+  float e = 0.f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) e = nanmax<float>(e, fabsf(zf[i]));
+  return uf[0] == uf[0] ? e : __int_as_float(0x7fc00000);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kOrThreads) k_outer_resid_df(const double *__restrict__ u,
+                                                               const float *__restrict__ b, Geo g,
+                                                               float *__restrict__ r32, float *__restrict__ u32,
+                                                               double *__restrict__ rho) {
+  __shared__ float s_h[2][N][kOrThreads], s_l[2][N][kOrThreads];
+  const int tx = threadIdx.x;
+  const int x = blockIdx.x * (kOrThreads - 2) - 1 + tx;
+  const int y0 = blockIdx.y * kOrRows;
+  const bool col = x >= 0 && x <= g.W;
+  const bool out = col && tx >= 1 && tx <= kOrThreads - 2;
+  float ph[N], pl[N], ch[N], cl[N], cf[N];
+  or_load_row<N>(u, g, col, x, y0 - 1, ph, pl, cf);
+  or_load_row<N>(u, g, col, x, y0, ch, cl, cf);
+  float e = 0.f;
+  for (int k = 0; k < kOrRows; ++k) {
+    const int y = y0 + k;
+    if (y > g.H) break;  // the same for every thread of the block
+    float nh[N], nl[N], nf[N];
+    or_load_row<N>(u, g, col, x, y + 1, nh, nl, nf);
+    const int buf = k & 1;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      s_h[buf][i][tx] = ch[i];
+      s_l[buf][i][tx] = cl[i];
+    }
+    __syncthreads();  // with two buffers, one barrier per row
+    if (out) e = nanmax<float>(e, or_node<N>(b, g, x, y, s_h[buf], s_l[buf], tx, ph, pl, ch, cl, cf, nh, nl, r32,
+                                             u32));
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      ph[i] = ch[i];
+      pl[i] = cl[i];
+      ch[i] = nh[i];
+      cl[i] = nl[i];
+      cf[i] = nf[i];
+    }
   }
   block_max_atomic(e, rho);
 }
@@ -1118,7 +1183,8 @@ __device__ __forceinline__ T op_offdiag(const T *op, const T *v, const Geo &g, i
 // the tile, which is then written once.  Each node's sums run in the fixed
 // order C, E, W, N, S, NE, SW, so the halo nodes recomputed by neighbouring
 // tiles agree bit for bit; one read and one write of the level per pair of
-// sweeps, and no neighbour loads through L1/L2.  vout must not alias vin
+// sweeps, and no neighbour loads through L1/L2.  The first sweep keeps each
+// node's 1 / l1 in shared memory for the second.  vout must not alias vin
 // unless ZERO_IN (vin unread).
 constexpr int kJ2X = 32, kJ2Y = 16, kJ2Threads = 256;
 template <typename T, int N, bool ZERO_IN>
@@ -1127,7 +1193,7 @@ __global__ void __launch_bounds__(kJ2Threads) k_coarse_jacobi2(const T *__restri
   constexpr int AX = kJ2X + 4, AY = kJ2Y + 4;  // tile + halo 2
   constexpr int BX = kJ2X + 2, BY = kJ2Y + 2;  // tile + halo 1
   __shared__ T sC[AY][AX], sE[AY][AX], sN[AY][AX], sNE[AY][AX], sV[AY][AX];
-  __shared__ T sR[BY][BX], sV1[BY][BX];
+  __shared__ T sR[BY][BX], sV1[BY][BX], sI[BY][BX];
   const int i = blockIdx.z;
   const int64_t nc = (int64_t)g.Wn * (g.H + 1);
   const T *C = op + (0 * N + i) * nc, *E = op + (1 * N + i) * nc, *Nn = op + (2 * N + i) * nc,
@@ -1179,7 +1245,9 @@ __global__ void __launch_bounds__(kJ2Threads) k_coarse_jacobi2(const T *__restri
     c = sNE[ay][ax]; if (!ZERO_IN) sv += c * sV[ay + 1][ax + 1]; l1 += fabs(c);
     c = sNE[ay - 1][ax - 1]; if (!ZERO_IN) sv += c * sV[ay - 1][ax - 1]; l1 += fabs(c);
     const T v0 = ZERO_IN ? T(0) : sV[ay][ax];
-    sV1[by][bx] = d > T(0) ? v0 + (sR[by][bx] - sv) / l1 : T(0);
+    const T inv = d > T(0) ? T(1) / l1 : T(0);  // 1 / l1, kept for the second sweep
+    sI[by][bx] = inv;
+    sV1[by][bx] = d > T(0) ? v0 + (sR[by][bx] - sv) * inv : T(0);
   }
   __syncthreads();
   // second sweep on the tile: tile (tx, ty) is B (tx + 1, ty + 1), A (tx + 2, ty + 2)
@@ -1187,15 +1255,14 @@ __global__ void __launch_bounds__(kJ2Threads) k_coarse_jacobi2(const T *__restri
     const int tx = t % kJ2X, ty = t / kJ2X, x = x0 + 2 + tx, y = y0 + 2 + ty;
     if (x > g.W || y > g.H) continue;
     const int bx = tx + 1, by = ty + 1, ax = tx + 2, ay = ty + 2;
-    const T d = sC[ay][ax];
-    T sv = d * sV1[by][bx], l1 = fabs(d), c;
-    c = sE[ay][ax]; sv += c * sV1[by][bx + 1]; l1 += fabs(c);
-    c = sE[ay][ax - 1]; sv += c * sV1[by][bx - 1]; l1 += fabs(c);
-    c = sN[ay][ax]; sv += c * sV1[by + 1][bx]; l1 += fabs(c);
-    c = sN[ay - 1][ax]; sv += c * sV1[by - 1][bx]; l1 += fabs(c);
-    c = sNE[ay][ax]; sv += c * sV1[by + 1][bx + 1]; l1 += fabs(c);
-    c = sNE[ay - 1][ax - 1]; sv += c * sV1[by - 1][bx - 1]; l1 += fabs(c);
-    vo[(int64_t)y * g.Wn + x] = d > T(0) ? sV1[by][bx] + (sR[by][bx] - sv) / l1 : T(0);
+    T sv = sC[ay][ax] * sV1[by][bx];
+    sv += sE[ay][ax] * sV1[by][bx + 1];
+    sv += sE[ay][ax - 1] * sV1[by][bx - 1];
+    sv += sN[ay][ax] * sV1[by + 1][bx];
+    sv += sN[ay - 1][ax] * sV1[by - 1][bx];
+    sv += sNE[ay][ax] * sV1[by + 1][bx + 1];
+    sv += sNE[ay - 1][ax - 1] * sV1[by - 1][bx - 1];
+    vo[(int64_t)y * g.Wn + x] = sV1[by][bx] + (sR[by][bx] - sv) * sI[by][bx];
   }
 }
 

@@ -199,7 +199,8 @@ struct Launch {
   static int outer_resid(const double *u, const float *b, const Geo &g, float *r32, float *u32, double *rho,
                          bool rho32, cudaStream_t s) {
     if (rho32)
-      k_outer_resid_df<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, b, g, r32, u32, rho);
+      k_outer_resid_df<N><<<dim3((g.W + 1 + kOrThreads - 3) / (kOrThreads - 2), (g.H + kOrRows) / kOrRows),
+                            kOrThreads, 0, s>>>(u, b, g, r32, u32, rho);
     else
       k_outer_resid<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, b, g, r32, u32, rho);
     return 1;
