@@ -255,10 +255,12 @@ def forward_states(img, u0, eps, lam, tau, steps, tol=1e-15, **kw):
     return states
 
 
-def adjoint(img, states, eps, lam, tau, gT, cg_rtol=1e-15):
+def adjoint(img, states, eps, lam, tau, gT, cg_rtol=1e-13):
     """Gradients of a loss on u^T (gT = dL/du^T) through the steps that
     produced `states`: returns (dL/dlambda, dL/deps with tau fixed,
-    dL/dI (H, W, 3), dL/du^0 (n, N))."""
+    dL/dI (H, W, 3), dL/du^0 (n, N)).  Each step's tangent system is solved
+    by CG to cg_rtol relative residual (1e-13: above the rounding floor of
+    the system, below which CG loses conjugacy)."""
     H, W, _ = img.shape
     T = len(states) - 1
     N = states[0].shape[1]

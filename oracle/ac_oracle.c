@@ -591,7 +591,10 @@ static double dotv(int64_t m, const double *a, const double *b) {
 }
 
 /* Conjugate gradients for (Pi S Pi) w = Pi g in V, from w = 0, until the
- * residual norm is below rtol times that of Pi g. */
+ * residual norm is below rtol times that of Pi g, or p'q <= 0: in exact
+ * arithmetic that means p = 0 (converged); in floating point it is CG past
+ * its rounding floor, where conjugacy is lost and further steps can grow the
+ * iterate without bound. */
 static int tangent_cg(const or_mesh *m, double te, int N, const double *up, const double *g, double *w, double rtol) {
   int64_t nn = m->n * N;
   double *r = calloc(nn, sizeof(double)), *p = calloc(nn, sizeof(double)), *q = calloc(nn, sizeof(double)),
@@ -606,7 +609,9 @@ static int tangent_cg(const or_mesh *m, double te, int N, const double *up, cons
     for (int64_t k = 0; k < m->n; ++k)
       for (int i = 0; i < N; ++i) t[k * N + i] = S_row(m, te, k, p, N, i);
     tangent_project(m->n, N, up, t, q);
-    double a = rr / dotv(nn, p, q);
+    const double pq = dotv(nn, p, q);
+    if (!(pq > 0)) break;
+    double a = rr / pq;
     for (int64_t k = 0; k < nn; ++k) {
       w[k] += a * p[k];
       r[k] -= a * q[k];
