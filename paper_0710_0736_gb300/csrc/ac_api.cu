@@ -160,6 +160,7 @@ struct Solve {
 constexpr int kCoarseSweeps = AC_COARSE_SWEEPS;
 static_assert(kCoarseSweeps >= 2 && kCoarseSweeps % 2 == 0, "coarse sweeps: an even count >= 2");
 constexpr int kCoarsestSweeps = 20;  // sweeps of the one-block coarsest solve
+constexpr size_t kTailSmemBytes = 200 * 1024;  // shared memory of k_coarse_tail per block
 constexpr int64_t kCoarsestBlockNodes = 1 << 14;
 // AC_MIXED: inner FP32 solve to max(0.9 tol, 1e-5 rho_outer) ...  The inner
 // natural residual and the outer one agree to about 0.1% at tol 1e-6 (float
@@ -425,9 +426,39 @@ int read_rho(ac_ctx *ctx, double *out) {
 // built), zero initial guess.  Smoothing runs in fused pairs of l1-Jacobi
 // sweeps that cannot work in place, so a level's two buffers v and t swap
 // roles: *res returns the one that holds v_k.
+// First level k0 >= 1 from which the rest of the hierarchy (operators and
+// the k0 iterate, right-hand side and residual, kTailArrays values per node)
+// fits in one block's shared memory: below it the whole cycle is one launch
+// of k_coarse_tail.  S.depth when none does.
+int tail_level(const Solve &S, size_t *smem) {
+  size_t bytes = 0;
+  int k0 = S.depth;
+  for (int k = S.depth - 1; k >= 1; --k) {
+    const size_t b = bytes + (size_t)ac::kTailArrays * (size_t)S.lv[k].n * (size_t)S.o->elem;
+    if (b > kTailSmemBytes || S.depth - k > ac::kTailMaxLevels) break;
+    bytes = b;
+    k0 = k;
+  }
+  *smem = bytes;
+  return k0;
+}
+
 int coarse_vcycle(ac_ctx *ctx, Solve &S, int k, void **res) {
   Level &L = S.lv[k];
   const ac::SolverOps *o = S.o;
+  size_t smem = 0;
+  if (k == tail_level(S, &smem)) {
+    ac::TailArgs a{};
+    a.levels = S.depth - k;
+    for (int l = 0; l < a.levels; ++l) {
+      a.W[l] = S.lv[k + l].g.W;
+      a.H[l] = S.lv[k + l].g.H;
+      a.op[l] = S.lv[k + l].op;
+    }
+    AC_RUN(AC_PROF_COARSE, o->coarse_tail(a, L.r, L.v, kCoarseSweeps, kCoarsestSweeps, smem, ctx->s));
+    *res = L.v;
+    return AC_OK;
+  }
   if (k == S.depth - 1) {
     if (L.n <= kCoarsestBlockNodes) {
       AC_CUDA(cudaMemsetAsync(L.v, 0, (size_t)L.n * ctx->N * o->elem, ctx->s));

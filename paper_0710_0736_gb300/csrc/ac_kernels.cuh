@@ -1319,6 +1319,201 @@ __global__ void __launch_bounds__(1024) k_coarse_solve_smem(const T *__restrict_
   for (int t = threadIdx.x; t < N * nc; t += blockDim.x) v[t] = sv[t];
 }
 
+// ---------------------------------------------------------------------------
+// The bottom of the coarse V-cycle in one launch.  Below some level k0 the
+// levels are small (at most a few thousand nodes) and each of their kernels
+// is latency-bound, about 7 us for tiny grids.  One block per phase stages
+// the operators of levels k0 .. depth-1 and r of level k0 in shared memory
+// and runs the same cycle there: kCoarseSweeps l1-Jacobi sweeps from zero,
+// residual, restriction, ..., Gauss-Seidel on the coarsest level,
+// prolongation and kCoarseSweeps l1-Jacobi sweeps back up.  v of level k0
+// is written once.  Only W, H of each level and its operator are needed.
+// ---------------------------------------------------------------------------
+constexpr int kTailThreads = 1024;
+
+// Shared-memory view of one level of one phase.
+template <typename T>
+struct TailLevel {
+  int W, H, Wn, n;
+  T *C, *E, *Nn, *NE, *r, *v, *t;
+};
+
+// sum over the six off-diagonal neighbours (E, W, N, S, NE, SW) of S_Km v_m
+template <typename T>
+__device__ __forceinline__ T tail_offdiag(const TailLevel<T> &L, const T *v, int k, int x, int y, T &l1) {
+  T s = T(0), c;
+  if (x < L.W) { c = L.E[k]; s += c * v[k + 1]; l1 += fabs(c); }
+  if (x > 0) { c = L.E[k - 1]; s += c * v[k - 1]; l1 += fabs(c); }
+  if (y < L.H) { c = L.Nn[k]; s += c * v[k + L.Wn]; l1 += fabs(c); }
+  if (y > 0) { c = L.Nn[k - L.Wn]; s += c * v[k - L.Wn]; l1 += fabs(c); }
+  if (x < L.W && y < L.H) { c = L.NE[k]; s += c * v[k + L.Wn + 1]; l1 += fabs(c); }
+  if (x > 0 && y > 0) { c = L.NE[k - L.Wn - 1]; s += c * v[k - L.Wn - 1]; l1 += fabs(c); }
+  return s;
+}
+
+// one l1-Jacobi sweep vout = vin + (r - S vin) / l1 (vin = 0 when null);
+// rows with a zero diagonal give 0
+template <typename T>
+__device__ __forceinline__ void tail_jacobi(const TailLevel<T> &L, const T *vin, T *vout) {
+  for (int k = threadIdx.x; k < L.n; k += blockDim.x) {
+    const T d = L.C[k];
+    if (!(d > T(0))) {
+      vout[k] = T(0);
+      continue;
+    }
+    const int x = k % L.Wn, y = k / L.Wn;
+    T l1 = fabs(d), sv = T(0);
+    if (vin) {
+      sv = d * vin[k] + tail_offdiag(L, vin, k, x, y, l1);
+    } else {
+      if (x < L.W) l1 += fabs(L.E[k]);
+      if (x > 0) l1 += fabs(L.E[k - 1]);
+      if (y < L.H) l1 += fabs(L.Nn[k]);
+      if (y > 0) l1 += fabs(L.Nn[k - L.Wn]);
+      if (x < L.W && y < L.H) l1 += fabs(L.NE[k]);
+      if (x > 0 && y > 0) l1 += fabs(L.NE[k - L.Wn - 1]);
+    }
+    vout[k] = (vin ? vin[k] : T(0)) + (L.r[k] - sv) / l1;
+  }
+}
+
+// t = r - S v (0 on rows with a zero diagonal)
+template <typename T>
+__device__ __forceinline__ void tail_resid(const TailLevel<T> &L) {
+  for (int k = threadIdx.x; k < L.n; k += blockDim.x) {
+    const T d = L.C[k];
+    if (!(d > T(0))) {
+      L.t[k] = T(0);
+      continue;
+    }
+    const int x = k % L.Wn, y = k / L.Wn;
+    T l1 = T(0);
+    L.t[k] = L.r[k] - d * L.v[k] - tail_offdiag(L, L.v, k, x, y, l1);
+  }
+}
+
+// r_c = P' t (weights 1 at 2K, 1/2 at its E, W, N, S, NE, SW fine
+// neighbours; 0 on coarse rows with a zero diagonal)
+template <typename T>
+__device__ __forceinline__ void tail_restrict(const TailLevel<T> &F, const TailLevel<T> &Cc) {
+  constexpr int dx[7] = {0, 1, -1, 0, 0, 1, -1};
+  constexpr int dy[7] = {0, 0, 0, 1, -1, 1, -1};
+  for (int K = threadIdx.x; K < Cc.n; K += blockDim.x) {
+    if (!(Cc.C[K] > T(0))) {
+      Cc.r[K] = T(0);
+      continue;
+    }
+    const int X = K % Cc.Wn, Y = K / Cc.Wn;
+    T acc = T(0);
+#pragma unroll
+    for (int s = 0; s < 7; ++s) {
+      const int ax = 2 * X + dx[s], ay = 2 * Y + dy[s];
+      if (ax < 0 || ax > F.W || ay < 0 || ay > F.H) continue;
+      acc += (s == 0 ? T(1) : T(0.5)) * F.t[ay * F.Wn + ax];
+    }
+    Cc.r[K] = acc;
+  }
+}
+
+// v_f += P v_c on rows with a nonzero diagonal (odd-odd fine nodes sit on
+// the coarse SW-NE diagonal)
+template <typename T>
+__device__ __forceinline__ void tail_prolong(const TailLevel<T> &F, const TailLevel<T> &Cc) {
+  for (int k = threadIdx.x; k < F.n; k += blockDim.x) {
+    if (!(F.C[k] > T(0))) continue;
+    const int x = k % F.Wn, y = k / F.Wn;
+    const int K0 = (y >> 1) * Cc.Wn + (x >> 1);
+    T p = Cc.v[K0];
+    if ((x & 1) || (y & 1)) p = T(0.5) * (p + Cc.v[K0 + (x & 1) + (y & 1) * Cc.Wn]);
+    F.v[k] += p;
+  }
+}
+
+// Gauss-Seidel in three colours ((x + y) % 3 colours the 7-point pattern)
+// from v = 0 on the coarsest level
+template <typename T>
+__device__ __forceinline__ void tail_gs(const TailLevel<T> &L, int sweeps) {
+  for (int k = threadIdx.x; k < L.n; k += blockDim.x) L.v[k] = T(0);
+  __syncthreads();
+  for (int s = 0; s < sweeps; ++s)
+    for (int color = 0; color < 3; ++color) {
+      for (int k = threadIdx.x; k < L.n; k += blockDim.x) {
+        const int x = k % L.Wn, y = k / L.Wn;
+        if ((x + y) % 3 != color) continue;
+        const T d = L.C[k];
+        T l1 = T(0);
+        L.v[k] = d > T(0) ? (L.r[k] - tail_offdiag(L, L.v, k, x, y, l1)) / d : T(0);
+      }
+      __syncthreads();
+    }
+}
+
+// one block per phase (blockIdx.x); dynamic shared memory
+// kTailArrays * sum_l n_l values of T
+template <typename T, int N>
+__global__ void __launch_bounds__(kTailThreads) k_coarse_tail(TailArgs a, const T *__restrict__ r0, T *__restrict__ v0,
+                                                              int coarse_sweeps, int coarsest_sweeps) {
+  extern __shared__ unsigned char smem_raw[];
+  T *base = reinterpret_cast<T *>(smem_raw);
+  const int i = blockIdx.x;
+  TailLevel<T> lv[kTailMaxLevels];
+  int off = 0;
+  for (int l = 0; l < a.levels; ++l) {
+    TailLevel<T> &L = lv[l];
+    L.W = a.W[l];
+    L.H = a.H[l];
+    L.Wn = L.W + 1;
+    L.n = L.Wn * (L.H + 1);
+    L.C = base + off;
+    L.E = L.C + L.n;
+    L.Nn = L.E + L.n;
+    L.NE = L.Nn + L.n;
+    L.r = L.NE + L.n;
+    L.v = L.r + L.n;
+    L.t = L.v + L.n;
+    off += kTailArrays * L.n;
+    const T *op = static_cast<const T *>(a.op[l]);
+    for (int k = threadIdx.x; k < L.n; k += blockDim.x) {
+      L.C[k] = op[(0 * N + i) * L.n + k];
+      L.E[k] = op[(1 * N + i) * L.n + k];
+      L.Nn[k] = op[(2 * N + i) * L.n + k];
+      L.NE[k] = op[(3 * N + i) * L.n + k];
+    }
+  }
+  for (int k = threadIdx.x; k < lv[0].n; k += blockDim.x) lv[0].r[k] = r0[(int64_t)i * lv[0].n + k];
+  __syncthreads();
+  const int last = a.levels - 1;
+  for (int l = 0; l < last; ++l) {
+    const TailLevel<T> &L = lv[l];
+    // coarse_sweeps (even) sweeps from zero, alternating t and v, ending in v
+    for (int s = 0; s < coarse_sweeps; ++s) {
+      if (s & 1)
+        tail_jacobi(L, L.t, L.v);
+      else
+        tail_jacobi(L, s == 0 ? (const T *)nullptr : L.v, L.t);
+      __syncthreads();
+    }
+    tail_resid(L);
+    __syncthreads();
+    tail_restrict(L, lv[l + 1]);
+    __syncthreads();
+  }
+  tail_gs(lv[last], coarsest_sweeps);
+  for (int l = last - 1; l >= 0; --l) {
+    const TailLevel<T> &L = lv[l];
+    tail_prolong(L, lv[l + 1]);
+    __syncthreads();
+    for (int s = 0; s < coarse_sweeps; ++s) {
+      if (s & 1)
+        tail_jacobi(L, L.t, L.v);
+      else
+        tail_jacobi(L, L.v, L.t);
+      __syncthreads();
+    }
+  }
+  for (int k = threadIdx.x; k < lv[0].n; k += blockDim.x) v0[(int64_t)i * lv[0].n + k] = lv[0].v[k];
+}
+
 // t = r - S v on a coarse level, one thread per (node, phase) (interior
 // nodes branch-free, as in k_coarse_jacobi; the same arithmetic and order as
 // op_offdiag).

@@ -121,6 +121,12 @@ struct SolverLaunch {
     }
     return 1;
   }
+  static int coarse_tail(const TailArgs &a, const void *r0, void *v0, int coarse_sweeps, int coarsest_sweeps,
+                         size_t smem, cudaStream_t s) {
+    cudaFuncSetAttribute(k_coarse_tail<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_coarse_tail<T, N><<<N, kTailThreads, smem, s>>>(a, (const T *)r0, (T *)v0, coarse_sweeps, coarsest_sweeps);
+    return 1;
+  }
   static int line_search(const void *x, const void *ob, const void *rt, const void *v1, const uint8_t *mask,
                          const Geo &gf, const Geo &gc, void *d, double *part, double *tot, double *omega,
                          cudaStream_t s) {
@@ -136,7 +142,7 @@ struct SolverLaunch {
   }
   static SolverOps table() {
     return SolverOps{(int)sizeof(T), smooth,       resid,        restrict0,   galerkin0,   galerkin,   coarse_smooth,
-                     coarse_solve,   coarse_resid, restrict_,    prolong_add, line_search};
+                     coarse_solve,   coarse_resid, restrict_,    prolong_add, coarse_tail, line_search};
   }
 };
 

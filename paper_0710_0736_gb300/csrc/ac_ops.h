@@ -12,6 +12,17 @@ struct Galerkin0Table;
 // Scratch of the block-partial reductions: at most kMaxPartBlocks rows.
 constexpr int kMaxPartBlocks = 1024;
 
+// The bottom levels k0 .. k0 + levels - 1 of a coarse V-cycle, run by one
+// block per phase in shared memory (kTailArrays values per node: C, E, N,
+// NE, r, v, t); the last level is the coarsest.
+constexpr int kTailMaxLevels = 8;
+constexpr int kTailArrays = 7;
+struct TailArgs {
+  int levels;
+  int W[kTailMaxLevels], H[kTailMaxLevels];
+  const void *op[kTailMaxLevels];  // phase-major C, E, N, NE planes of each level
+};
+
 // One multigrid solve instantiation (scalar type and constraint form); array
 // arguments are typed by that instantiation (double or float).
 struct SolverOps {
@@ -40,6 +51,10 @@ struct SolverOps {
   int (*coarse_resid)(const void *op, const void *r, const void *v, const Geo &g, void *t, cudaStream_t s);
   int (*restrict_)(const void *t, const Geo &gf, const Geo &gc, const void *opc, void *rc, cudaStream_t s);
   int (*prolong_add)(const void *vc, const Geo &gf, const Geo &gc, const void *opf, void *vf, cudaStream_t s);
+  // v of level k0 from r of level k0 by the whole cycle below it (see
+  // TailArgs); smem bytes of dynamic shared memory per block
+  int (*coarse_tail)(const TailArgs &a, const void *r0, void *v0, int coarse_sweeps, int coarsest_sweeps,
+                     size_t smem, cudaStream_t s);
   // line search: part needs 2 x (blocks of the fine grid) doubles, tot 2 doubles
   int (*line_search)(const void *x, const void *ob, const void *rt, const void *v1, const uint8_t *mask,
                      const Geo &gf, const Geo &gc, void *d, double *part, double *tot, double *omega, cudaStream_t s);
