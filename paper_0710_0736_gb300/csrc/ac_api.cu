@@ -160,7 +160,6 @@ struct Solve {
 constexpr int kCoarseSweeps = AC_COARSE_SWEEPS;
 static_assert(kCoarseSweeps >= 2 && kCoarseSweeps % 2 == 0, "coarse sweeps: an even count >= 2");
 constexpr int kCoarsestSweeps = 20;  // sweeps of the one-block coarsest solve
-constexpr size_t kTailSmemBytes = 200 * 1024;  // shared memory of k_coarse_tail per block
 constexpr int64_t kCoarsestBlockNodes = 1 << 14;
 // AC_MIXED: inner FP32 solve to max(0.9 tol, 1e-5 rho_outer) ...  The inner
 // natural residual and the outer one agree to about 0.1% at tol 1e-6 (float
@@ -435,7 +434,7 @@ int tail_level(const Solve &S, size_t *smem) {
   int k0 = S.depth;
   for (int k = S.depth - 1; k >= 1; --k) {
     const size_t b = bytes + (size_t)ac::kTailArrays * (size_t)S.lv[k].n * (size_t)S.o->elem;
-    if (b > kTailSmemBytes || S.depth - k > ac::kTailMaxLevels) break;
+    if (b > ac::kTailSmemBytes || S.depth - k > ac::kTailMaxLevels) break;
     bytes = b;
     k0 = k;
   }

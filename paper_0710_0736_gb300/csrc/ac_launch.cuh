@@ -123,7 +123,11 @@ struct SolverLaunch {
   }
   static int coarse_tail(const TailArgs &a, const void *r0, void *v0, int coarse_sweeps, int coarsest_sweeps,
                          size_t smem, cudaStream_t s) {
-    cudaFuncSetAttribute(k_coarse_tail<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the cap, not this launch's size: the attribute is process-wide and
+    // graphs captured for other grids replay launches of other sizes
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(k_coarse_tail<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemBytes);
+    (void)attr;
     k_coarse_tail<T, N><<<N, kTailThreads, smem, s>>>(a, (const T *)r0, (T *)v0, coarse_sweeps, coarsest_sweeps);
     return 1;
   }

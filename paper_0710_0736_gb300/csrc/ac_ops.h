@@ -1,6 +1,7 @@
 // ac_ops.h -- host-side launch table of the per-N kernel instantiations.
 // Every launcher returns the number of kernels it launched.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -17,6 +18,7 @@ constexpr int kMaxPartBlocks = 1024;
 // NE, r, v, t); the last level is the coarsest.
 constexpr int kTailMaxLevels = 8;
 constexpr int kTailArrays = 7;
+constexpr size_t kTailSmemBytes = 200 * 1024;  // shared memory cap of one block
 struct TailArgs {
   int levels;
   int W[kTailMaxLevels], H[kTailMaxLevels];
