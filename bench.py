@@ -171,6 +171,16 @@ def smooth_source_digest():
     return hashlib.sha256(text.encode()).hexdigest()
 
 
+def smooth_bytes(prof):
+    """Algorithmic bytes of all timed smoother launches: each launch moves the
+    library's per-launch bytes (one colour's right-hand side and obstacle and
+    the other colour's iterate read, its own colour written); a launch that
+    also applies the pending coarse correction reads the other colour's
+    correction d as well."""
+    return (prof.launches[ac.PROF_CLASSES.index("smooth")] * prof.smooth_bytes_per_launch
+            + prof.smooth_corr_launches * prof.smooth_corr_extra_bytes)
+
+
 def smooth_traffic(n_nodes, n_phases, precision):
     """Measured DRAM bytes of one smoother launch, or None when no capture of
     the current kernel source exists for this configuration."""
@@ -454,7 +464,7 @@ def run_refine(args):
     peaks, peak_kind = measured_peaks()
     sm_launches = prof.launches[ac.PROF_CLASSES.index("smooth")]
     sm_ms = prof.ms[ac.PROF_CLASSES.index("smooth")]
-    achieved = prof.smooth_bytes_per_launch / (sm_ms / 1e3 / max(1, sm_launches)) / 1e9
+    achieved = smooth_bytes(prof) / max(1, sm_launches) / (sm_ms / 1e3 / max(1, sm_launches)) / 1e9
     cpu = None
     if not args.no_cpu:
         # the oracle on a 64 x 64 corner of the image, refined the same way
@@ -556,14 +566,17 @@ def main():
     sm_launches = prof.launches[ac.PROF_CLASSES.index("smooth")]
     sm_ms = prof.ms[ac.PROF_CLASSES.index("smooth")]
     avg_launch_s = sm_ms / 1e3 / max(1, sm_launches)
-    achieved = prof.smooth_bytes_per_launch / avg_launch_s / 1e9
+    bytes_avg = smooth_bytes(prof) / max(1, sm_launches)
+    achieved = bytes_avg / avg_launch_s / 1e9
     kname = "k_smooth_fine<float,N,shifted>" if args.precision == "mixed" else "k_smooth_fine<double,N,direct>"
     roofline = {"bound": "hbm", "kernel": kname + " (one colour of a red-black projected sweep)",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                 "peak_kind": f"{peak_kind} hbm_gbs", "traffic": smooth_traffic(n_nodes, N, args.precision),
-                "traffic_unit": "bytes per launch (ncu capture at 2048^2 scaled by nodes)",
-                "bytes_per_launch": prof.smooth_bytes_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
-                "share_of_step_time": sm_ms / max(1e-9, ms)}
+                "traffic_unit": "bytes per plain launch (ncu capture at 2048^2 of launches without a pending "
+                                "correction, scaled by nodes); compare plain_launch_bytes",
+                "bytes_per_launch": bytes_avg, "plain_launch_bytes": prof.smooth_bytes_per_launch,
+                "correction_launches": prof.smooth_corr_launches, "launches": sm_launches,
+                "avg_launch_ms": avg_launch_s * 1e3, "share_of_step_time": sm_ms / max(1e-9, ms)}
 
     # end to end through the public API with host buffers
     e2e = None

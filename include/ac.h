@@ -119,6 +119,10 @@ typedef struct {
                                       colour written), AC_MIXED 2 n N 4 (r and obstacle of the colour,
                                       delta of the other colour read, delta of the colour written) */
   int64_t total_launches;          /* every kernel launched by this context since creation */
+  int64_t smooth_corr_launches;    /* smoother launches that also applied a pending coarse correction
+                                      x += omega d: they read d of the other colour as well */
+  double smooth_corr_extra_bytes;  /* the extra algorithmic bytes of such a launch: 0.5 n N 8 (AC_FP64),
+                                      0.5 n N 4 (AC_MIXED) */
 } ac_profile;
 
 /* Defaults: tol 1e-10, nu1 = nu2 = 2, max_cycles 200, coarse_min 4, AC_FP64,

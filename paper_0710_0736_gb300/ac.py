@@ -47,13 +47,16 @@ class ac_stats(C.Structure):
 
 class ac_profile(C.Structure):
     _fields_ = [("ms", C.c_double * 7), ("launches", C.c_int64 * 7), ("smooth_bytes_per_launch", C.c_double),
-                ("total_launches", C.c_int64)]
+                ("total_launches", C.c_int64), ("smooth_corr_launches", C.c_int64),
+                ("smooth_corr_extra_bytes", C.c_double)]
 
     def as_dict(self):
         return {"ms": dict(zip(PROF_CLASSES, list(self.ms))),
                 "launches": dict(zip(PROF_CLASSES, list(self.launches))),
                 "smooth_bytes_per_launch": self.smooth_bytes_per_launch,
-                "total_launches": self.total_launches}
+                "total_launches": self.total_launches,
+                "smooth_corr_launches": self.smooth_corr_launches,
+                "smooth_corr_extra_bytes": self.smooth_corr_extra_bytes}
 
 
 class ac_batch_stats(C.Structure):

@@ -237,6 +237,7 @@ struct ac_ctx {
   std::vector<Pending> pending;
   double prof_ms[AC_PROF_COUNT] = {};
   int64_t prof_launches[AC_PROF_COUNT] = {};
+  int64_t prof_corr_launches = 0;  // smoother launches that applied a pending correction
   // CUDA graphs (off on the legacy default stream, which cannot be captured)
   bool use_graphs = false;
   GraphSlot *capturing = nullptr;
@@ -521,6 +522,7 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
       return AC_OK;
     });
     if (rc) return rc;
+    if (ctx->profiling && corr && nsw > 0) ++ctx->prof_corr_launches;
     sweeps += nsw;
     ++cyc;
     rc = read_rho(ctx, &rho);
@@ -1154,6 +1156,7 @@ int ac_set_profiling(ac_ctx *ctx, int enable) {
     ctx->prof_ms[k] = 0;
     ctx->prof_launches[k] = 0;
   }
+  ctx->prof_corr_launches = 0;
   ctx->profiling = enable != 0;
   return AC_OK;
 }
@@ -1169,6 +1172,9 @@ int ac_get_profile(ac_ctx *ctx, ac_profile *out) {
   out->smooth_bytes_per_launch = ctx->p.precision == AC_MIXED ? 2.0 * (double)ctx->n * ctx->N * sizeof(float)
                                                                : 1.5 * (double)ctx->n * ctx->N * sizeof(double);
   out->total_launches = ctx->total_launches;
+  out->smooth_corr_launches = ctx->prof_corr_launches;
+  out->smooth_corr_extra_bytes = 0.5 * (double)ctx->n * ctx->N * (ctx->p.precision == AC_MIXED ? sizeof(float)
+                                                                                                 : sizeof(double));
   return AC_OK;
 }
 
