@@ -177,6 +177,7 @@ def smooth_bytes(prof):
     the other colour's iterate read, its own colour written); a launch that
     also applies the pending coarse correction reads the other colour's
     correction d as well."""
+    from paper_0710_0736_gb300 import ac
     return (prof.launches[ac.PROF_CLASSES.index("smooth")] * prof.smooth_bytes_per_launch
             + prof.smooth_corr_launches * prof.smooth_corr_extra_bytes)
 

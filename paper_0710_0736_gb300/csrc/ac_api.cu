@@ -471,10 +471,16 @@ int coarse_vcycle(ac_ctx *ctx, Solve &S, int k, void **res) {
   }
   Level &C = S.lv[k + 1];
   // v starts at 0: the first pair of sweeps writes every node without reading v
-  void *v = nullptr;
-  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, true, &v, ctx->s));
-  void *other = v == L.v ? L.t : L.v;
-  AC_RUN(AC_PROF_COARSE, o->coarse_resid(L.op, L.r, v, L.g, other, ctx->s));
+  void *v = nullptr, *other = nullptr;
+  if (kCoarseSweeps == 2) {
+    AC_RUN(AC_PROF_COARSE, o->coarse_pre_resid(L.op, L.r, L.v, L.t, L.g, ctx->s));
+    v = L.v;
+    other = L.t;
+  } else {
+    AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, true, &v, ctx->s));
+    other = v == L.v ? L.t : L.v;
+    AC_RUN(AC_PROF_COARSE, o->coarse_resid(L.op, L.r, v, L.g, other, ctx->s));
+  }
   AC_RUN(AC_PROF_TRANSFER, o->restrict_(other, L.g, C.g, C.op, C.r, ctx->s));
   void *cv = nullptr;
   int rc = coarse_vcycle(ctx, S, k + 1, &cv);

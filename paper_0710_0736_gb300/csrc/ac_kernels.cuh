@@ -573,10 +573,17 @@ __device__ __forceinline__ float or_node(const float *__restrict__ b, const Geo 
       sl[i] = 0.f;
     }
     if (x > 0 && x < g.W && y > 0 && y < g.H) {
-      or_add<N>(eh, el, uh, ul, 1.f, sh, sl);
-      or_add<N>(wh, wl, uh, ul, 1.f, sh, sl);
-      or_add<N>(nh, nl, uh, ul, 1.f, sh, sl);
-      or_add<N>(ph, pl, uh, ul, 1.f, sh, sl);
+      // (u_E + u_W + u_N + u_S) - 4 u: the heads summed by two-sums, 4 u_h
+      // exactly, the tails and the two-sum errors in float
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const f2 a = two_sum(eh[i], wh[i]);
+        const f2 b = two_sum(nh[i], ph[i]);
+        const f2 c = two_sum(a.h, b.h);
+        const f2 d = two_sum(c.h, -4.f * uh[i]);
+        sh[i] = d.h;
+        sl[i] = d.l + (c.l + (a.l + b.l)) + (((el[i] + wl[i]) + (nl[i] + pl[i])) - 4.f * ul[i]);
+      }
     } else {
       const Weights w = edge_weights(g, x, y);
       if (w.e > 0.f) or_add<N>(eh, el, uh, ul, w.e, sh, sl);
@@ -1263,6 +1270,107 @@ __global__ void __launch_bounds__(kJ2Threads) k_coarse_jacobi2(const T *__restri
     sv += sNE[ay][ax] * sV1[by + 1][bx + 1];
     sv += sNE[ay - 1][ax - 1] * sV1[by - 1][bx - 1];
     vo[(int64_t)y * g.Wn + x] = sV1[by][bx] + (sR[by][bx] - sv) * sI[by][bx];
+  }
+}
+
+// The pre-smoothing pair of a coarse level (two l1-Jacobi sweeps from v = 0)
+// fused with the level's residual t = r - S v: the operator is staged on the
+// tile plus a halo of 3 and r on the tile plus a halo of 2, the first sweep
+// runs on the tile plus 2, the second on the tile plus 1, and the residual
+// on the tile, so one launch writes v and t of the tile (k_coarse_resid's
+// arithmetic and order; rows with a zero diagonal give 0 for both).
+template <typename T, int N>
+__global__ void __launch_bounds__(kJ2Threads) k_coarse_jacobi2_resid(const T *__restrict__ op,
+                                                                     const T *__restrict__ r, T *__restrict__ vout,
+                                                                     T *__restrict__ tout, Geo g) {
+  constexpr int AX = kJ2X + 6, AY = kJ2Y + 6;  // tile + halo 3 (operator)
+  constexpr int BX = kJ2X + 4, BY = kJ2Y + 4;  // tile + halo 2 (r, first sweep)
+  constexpr int CX = kJ2X + 2, CY = kJ2Y + 2;  // tile + halo 1 (second sweep)
+  __shared__ T sC[AY][AX], sE[AY][AX], sN[AY][AX], sNE[AY][AX];
+  __shared__ T sR[BY][BX], sV1[BY][BX], sI[BY][BX], sV2[CY][CX];
+  const int i = blockIdx.z;
+  const int64_t nc = (int64_t)g.Wn * (g.H + 1);
+  const T *C = op + (0 * N + i) * nc, *E = op + (1 * N + i) * nc, *Nn = op + (2 * N + i) * nc,
+          *NE = op + (3 * N + i) * nc, *ri = r + i * nc;
+  T *vo = vout + i * nc, *to = tout + i * nc;
+  const int x0 = blockIdx.x * kJ2X - 3, y0 = blockIdx.y * kJ2Y - 3;  // grid position of [0][0] of the A arrays
+  int live = 0;
+  for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
+    const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
+    const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
+    const T c = in ? C[in ? (int64_t)y * g.Wn + x : 0] : T(0);
+    sC[ay][ax] = c;
+    live |= (ax >= 3 && ax < 3 + kJ2X && ay >= 3 && ay < 3 + kJ2Y && c > T(0)) ? 1 : 0;
+  }
+  if (!__syncthreads_or(live)) {
+    for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
+      const int x = x0 + 3 + t % kJ2X, y = y0 + 3 + t / kJ2X;
+      if (x <= g.W && y <= g.H) {
+        vo[(int64_t)y * g.Wn + x] = T(0);
+        to[(int64_t)y * g.Wn + x] = T(0);
+      }
+    }
+    return;
+  }
+  for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
+    const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
+    const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
+    const int64_t K = in ? (int64_t)y * g.Wn + x : 0;
+    sE[ay][ax] = in ? E[K] : T(0);
+    sN[ay][ax] = in ? Nn[K] : T(0);
+    sNE[ay][ax] = in ? NE[K] : T(0);
+  }
+  for (int t = threadIdx.x; t < BX * BY; t += kJ2Threads) {
+    const int bx = t % BX, by = t / BX, x = x0 + 1 + bx, y = y0 + 1 + by;
+    const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
+    sR[by][bx] = in ? ri[(int64_t)y * g.Wn + x] : T(0);
+  }
+  __syncthreads();
+  // first sweep from zero on the tile + 2: B (bx, by) is A (bx + 1, by + 1)
+  for (int t = threadIdx.x; t < BX * BY; t += kJ2Threads) {
+    const int bx = t % BX, by = t / BX, ax = bx + 1, ay = by + 1;
+    const T d = sC[ay][ax];
+    T l1 = fabs(d);
+    l1 += fabs(sE[ay][ax]);
+    l1 += fabs(sE[ay][ax - 1]);
+    l1 += fabs(sN[ay][ax]);
+    l1 += fabs(sN[ay - 1][ax]);
+    l1 += fabs(sNE[ay][ax]);
+    l1 += fabs(sNE[ay - 1][ax - 1]);
+    const T inv = d > T(0) ? T(1) / l1 : T(0);
+    sI[by][bx] = inv;
+    sV1[by][bx] = d > T(0) ? (sR[by][bx] - T(0)) * inv : T(0);
+  }
+  __syncthreads();
+  // second sweep on the tile + 1: C (cx, cy) is B (cx + 1, cy + 1), A (cx + 2, cy + 2)
+  for (int t = threadIdx.x; t < CX * CY; t += kJ2Threads) {
+    const int cx = t % CX, cy = t / CX, bx = cx + 1, by = cy + 1, ax = cx + 2, ay = cy + 2;
+    T sv = sC[ay][ax] * sV1[by][bx];
+    sv += sE[ay][ax] * sV1[by][bx + 1];
+    sv += sE[ay][ax - 1] * sV1[by][bx - 1];
+    sv += sN[ay][ax] * sV1[by + 1][bx];
+    sv += sN[ay - 1][ax] * sV1[by - 1][bx];
+    sv += sNE[ay][ax] * sV1[by + 1][bx + 1];
+    sv += sNE[ay - 1][ax - 1] * sV1[by - 1][bx - 1];
+    sV2[cy][cx] = sV1[by][bx] + (sR[by][bx] - sv) * sI[by][bx];
+  }
+  __syncthreads();
+  // v and the residual on the tile: C (tx + 1, ty + 1), B (tx + 2, ty + 2), A (tx + 3, ty + 3)
+  for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
+    const int tx = t % kJ2X, ty = t / kJ2X, x = x0 + 3 + tx, y = y0 + 3 + ty;
+    if (x > g.W || y > g.H) continue;
+    const int cx = tx + 1, cy = ty + 1, bx = tx + 2, by = ty + 2, ax = tx + 3, ay = ty + 3;
+    const T d = sC[ay][ax], vk = sV2[cy][cx];
+    T s = T(0);
+    s += sE[ay][ax] * sV2[cy][cx + 1];
+    s += sE[ay][ax - 1] * sV2[cy][cx - 1];
+    s += sN[ay][ax] * sV2[cy + 1][cx];
+    s += sN[ay - 1][ax] * sV2[cy - 1][cx];
+    s += sNE[ay][ax] * sV2[cy + 1][cx + 1];
+    s += sNE[ay - 1][ax - 1] * sV2[cy - 1][cx - 1];
+    const int64_t K = (int64_t)y * g.Wn + x;
+    vo[K] = vk;
+    to[K] = d > T(0) ? sR[by][bx] - d * vk - s : T(0);
   }
 }
 

@@ -90,6 +90,18 @@ struct SolverLaunch {
     *out = cur;
     return k;
   }
+  // two l1-Jacobi sweeps from v = 0, then t = r - S v; float: one fused
+  // launch (its shared memory is over the static limit in double)
+  static int coarse_pre_resid(const void *op, const void *r, void *v, void *t, const Geo &g, cudaStream_t s) {
+    const dim3 grid((unsigned)((g.W + kJ2X) / kJ2X), (unsigned)((g.H + kJ2Y) / kJ2Y), (unsigned)N);
+    if constexpr (sizeof(T) == 4) {
+      k_coarse_jacobi2_resid<T, N><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (T *)v, (T *)t, g);
+      return 1;
+    } else {
+      k_coarse_jacobi2<T, N, true><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)v, (T *)v, g);
+      return 1 + coarse_resid(op, r, v, g, t, s);
+    }
+  }
   static int coarse_solve(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s) {
     const int64_t nc = (int64_t)g.Wn * (g.H + 1);
     const size_t smem = (size_t)6 * N * nc * sizeof(T);
@@ -146,7 +158,8 @@ struct SolverLaunch {
   }
   static SolverOps table() {
     return SolverOps{(int)sizeof(T), smooth,       resid,        restrict0,   galerkin0,   galerkin,   coarse_smooth,
-                     coarse_solve,   coarse_resid, restrict_,    prolong_add, coarse_tail, line_search};
+                     coarse_solve,   coarse_resid, coarse_pre_resid, restrict_, prolong_add, coarse_tail,
+                     line_search};
   }
 };
 

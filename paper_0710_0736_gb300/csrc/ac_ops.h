@@ -51,6 +51,8 @@ struct SolverOps {
                        void **out, cudaStream_t s);
   int (*coarse_solve)(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s);
   int (*coarse_resid)(const void *op, const void *r, const void *v, const Geo &g, void *t, cudaStream_t s);
+  // one pair of l1-Jacobi sweeps from v = 0, then t = r - S v
+  int (*coarse_pre_resid)(const void *op, const void *r, void *v, void *t, const Geo &g, cudaStream_t s);
   int (*restrict_)(const void *t, const Geo &gf, const Geo &gc, const void *opc, void *rc, cudaStream_t s);
   int (*prolong_add)(const void *vc, const Geo &gf, const Geo &gc, const void *opf, void *vf, cudaStream_t s);
   // v of level k0 from r of level k0 by the whole cycle below it (see
