@@ -300,10 +300,12 @@ template <int N, bool ENERGY>
 __global__ void __launch_bounds__(kBlock) k_means_partial_df(const double *__restrict__ u,
                                                              const double *__restrict__ mom, Geo g,
                                                              double *__restrict__ part) {
-  constexpr int Q = ENERGY ? 7 : 4;
-  f2 acc[Q * N];
+  // 4N sums per phase (k_means_partial's q = 0..3), and with ENERGY three
+  // sums over all phases: u m2, m0 u (1 - u), w (u_a - u_b)^2
+  constexpr int QN = ENERGY ? 4 * N + 3 : 4 * N;
+  f2 acc[QN];
 #pragma unroll
-  for (int k = 0; k < Q * N; ++k) acc[k] = {0.f, 0.f};
+  for (int k = 0; k < QN; ++k) acc[k] = {0.f, 0.f};
   const int64_t n = (int64_t)g.Wn * (g.H + 1);
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     const unsigned k32 = (unsigned)k;  // n <= 2^31: 32-bit division suffices
@@ -336,13 +338,13 @@ __global__ void __launch_bounds__(kBlock) k_means_partial_df(const double *__res
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         f2 p = mul_f2(uh[i], ul[i], mh[4], ml[4]);  // u m2
-        acc[4 * N + i] = add_f2(acc[4 * N + i], p.h, p.l);
+        acc[4 * N] = add_f2(acc[4 * N], p.h, p.l);
         f2 v = two_sum(1.f, -uh[i]);  // 1 - u
         v.l -= ul[i];
         p = mul_f2(uh[i], ul[i], v.h, v.l);
         p = fast_two_sum(p.h, p.l);
         p = mul_f2(mh[0], ml[0], p.h, p.l);  // m0 u (1 - u)
-        acc[5 * N + i] = add_f2(acc[5 * N + i], p.h, p.l);
+        acc[4 * N + 1] = add_f2(acc[4 * N + 1], p.h, p.l);
       }
       // w (u_a - u_b)^2 over the east and north axis edges of the node
       const Weights w = edge_weights(g, x, y);
@@ -356,17 +358,39 @@ __global__ void __launch_bounds__(kBlock) k_means_partial_df(const double *__res
           f2 d = two_sum(uh[i], -h);
           d = fast_two_sum(d.h, d.l + (ul[i] - l));
           const f2 p = mul_f2(d.h, d.l, d.h, d.l);
-          acc[6 * N + i] = add_f2(acc[6 * N + i], we * p.h, we * p.l);
+          acc[4 * N + 2] = add_f2(acc[4 * N + 2], we * p.h, we * p.l);
         }
       };
       if (x < g.W) edge(k + 1, w.e);
       if (y < g.H) edge(k + g.Wn, w.n);
     }
   }
-  double v[Q * N];
+  double v[QN];
 #pragma unroll
-  for (int k = 0; k < Q * N; ++k) v[k] = f32_to_f64(acc[k].h) + f32_to_f64(acc[k].l);
-  block_sum_store<Q * N>(v, part + (int64_t)blockIdx.x * Q * N);
+  for (int k = 0; k < QN; ++k) v[k] = f32_to_f64(acc[k].h) + f32_to_f64(acc[k].l);
+  block_sum_store<QN>(v, part + (int64_t)blockIdx.x * QN);
+}
+
+// c_i as k_means_finish; with energy the discrete Eq. (E) from the 4N + 3
+// totals of k_means_partial_df<N, true>: lambda (sum u m2 - sum_i |s_i|^2 /
+// mass_i) + (1/eps) sum m0 u (1 - u) + eps/2 sum u'Au (a phase of zero mass
+// is 0 everywhere, so its u m2 term is 0 as in k_means_finish).
+template <int N>
+__global__ void k_means_finish_df(const double *__restrict__ tot, double *__restrict__ c, double *__restrict__ energy,
+                                  double eps, double lam) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double fit = 0.0;
+  for (int i = 0; i < N; ++i) {
+    const double mass = tot[0 * N + i];
+    const double s0 = tot[1 * N + i], s1 = tot[2 * N + i], s2 = tot[3 * N + i];
+    if (mass != 0.0) {
+      c[i * 3 + 0] = s0 / mass;
+      c[i * 3 + 1] = s1 / mass;
+      c[i * 3 + 2] = s2 / mass;
+      fit += (s0 * s0 + s1 * s1 + s2 * s2) / mass;
+    }
+  }
+  if (energy) *energy = lam * (tot[4 * N] - fit) + tot[4 * N + 1] / eps + 0.5 * eps * tot[4 * N + 2];
 }
 
 template <int N>

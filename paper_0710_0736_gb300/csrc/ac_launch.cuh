@@ -205,8 +205,8 @@ struct Launch {
     const int blocks = (int)(b < kMaxPartBlocks ? b : kMaxPartBlocks);
     if (energy) {
       k_means_partial_df<N, true><<<blocks, kBlock, 0, s>>>(u, mom, g, part);
-      k_colsum<<<7 * N, 1024, 0, s>>>(part, blocks, 7 * N, tot);
-      k_means_finish<N, true><<<1, 32, 0, s>>>(tot, c, energy, eps, lam);
+      k_colsum<<<4 * N + 3, 1024, 0, s>>>(part, blocks, 4 * N + 3, tot);
+      k_means_finish_df<N><<<1, 32, 0, s>>>(tot, c, energy, eps, lam);
     } else {
       k_means_partial_df<N, false><<<blocks, kBlock, 0, s>>>(u, mom, g, part);
       k_colsum<<<4 * N, 1024, 0, s>>>(part, blocks, 4 * N, tot);
