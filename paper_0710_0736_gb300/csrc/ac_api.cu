@@ -2,7 +2,7 @@
 // the time step (Sec. 3.2 of Kay & Tomasi): colour means and right-hand side,
 // then truncated monotone multigrid V-cycles until the natural residual
 // reaches tol.  The cycle is described at solve_mg; the mixed-precision form
-// wraps it in an FP64 defect correction (solve_mixed).
+// wraps an FP32 solve in a defect correction on the FP64 state (solve_mixed).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -566,8 +566,9 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
   return status;
 }
 
-// AC_MIXED: FP64 defect correction around the FP32 multigrid.  Each pass
-// forms r = b - S u and the natural residual in FP64; if rho > tol the
+// AC_MIXED: defect correction on the FP64 state around the FP32 multigrid.
+// Each pass forms r = b - S u in double-float arithmetic (k_outer_resid_df,
+// about 2^-46 of the terms) and the natural residual; if rho > tol the
 // correction problem min 1/2 d'Sd - r'd, u + d on the simplices, is solved in
 // FP32 to max(0.9 tol, 1e-5 rho) or kInnerMaxCycles V-cycles (FP32 keeps the
 // correction's own relative precision, except for components driven onto
