@@ -70,12 +70,13 @@ typedef struct {
   int max_cycles;      /* V-cycle cap per step, >= 1 */
   int coarse_min;      /* coarsen while both cell counts are even and min/2 >= coarse_min (>= 1) */
   int precision;       /* AC_FP64: every array and operation of the solve in FP64.
-                          AC_MIXED: FP64 state u, right-hand side, colour means, energy and
-                          residual r = b - S u (defect correction); the correction delta is
-                          solved by the same multigrid in FP32 with obstacle -u and the
-                          natural residual is checked in float on the FP64 residual
-                          shifted per node by its maximum; the image is rounded to
-                          bfloat16 on input (ac_set_image only). */
+                          AC_MIXED: FP64 state u and its update; right-hand side, colour
+                          means, energy and residual r = b - S u of the defect correction in
+                          double-float arithmetic (about 2^-46 of the terms: GB300 runs FP64
+                          at 1/64 of its FP32 rate); the correction delta is solved by the
+                          same multigrid in FP32 with obstacle -u and the natural residual is
+                          checked in float on that residual shifted per node by its maximum;
+                          the image is rounded to bfloat16 on input (ac_set_image only). */
   uint64_t seed;       /* seed of the random simplex initialisation in ac_set_image */
   int refine;          /* r in [0, 4]: solve on the pixel grid refined r times (Sec. 4.1, "at least four
                           nodes per interface"): every pixel becomes 2^r x 2^r cells carrying the pixel's
@@ -96,7 +97,7 @@ typedef struct {
   int steps;           /* time steps done by the call */
   int converged;       /* 1 if every step of the call reached tol */
   int64_t fine_sweeps; /* red-black projected sweeps on the fine level over the call */
-  int outer;           /* AC_MIXED: FP64 defect-correction passes over the call (0 for AC_FP64) */
+  int outer;           /* AC_MIXED: defect-correction passes over the call (0 for AC_FP64) */
 } ac_stats;
 
 /* Kernel classes of the profile (no counterpart in the paper: instrumentation). */
@@ -107,7 +108,7 @@ enum {
   AC_PROF_TRANSFER,    /* truncated Galerkin operators, restriction, prolongation */
   AC_PROF_LINESEARCH,  /* coarse-correction direction, line search, update */
   AC_PROF_SETUP,       /* colour means, energy and right-hand side of a step */
-  AC_PROF_OUTER,       /* AC_MIXED: FP64 residual and update of the defect correction */
+  AC_PROF_OUTER,       /* AC_MIXED: residual and update of the defect correction */
   AC_PROF_COUNT
 };
 
