@@ -206,6 +206,13 @@ int ac_project_simplex(const double *y, double *x, int64_t count, int n_phases, 
  * profile.  While on, every kernel group is bracketed by CUDA events on the
  * context's stream. */
 int ac_set_profiling(ac_ctx *ctx, int enable);
+/* Like ac_set_profiling(ctx, class_mask != 0), but only the classes whose bit
+ * (1 << AC_PROF_*) is set are bracketed by events; every class's launches are
+ * still counted.  Events cost host time after each V-cycle (a replayed graph's
+ * events are read back before it runs again), so a timing run that needs one
+ * class can ask for that class alone.  Changing the mask re-captures the
+ * context's profiled graphs. */
+int ac_set_profiling_mask(ac_ctx *ctx, unsigned class_mask);
 /* Synchronise the stream and return the profile accumulated since the last
  * ac_set_profiling call (total_launches counts from creation). */
 int ac_get_profile(ac_ctx *ctx, ac_profile *out);

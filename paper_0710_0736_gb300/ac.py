@@ -21,7 +21,7 @@ AC_MAX_PHASES = 8
 EXPORTS = [
     "ac_default_params", "ac_create", "ac_set_image", "ac_set_image_f64", "ac_step", "ac_segment", "ac_destroy",
     "ac_set_phase", "ac_get_phase", "ac_get_means", "ac_get_moments", "ac_get_rhs", "ac_get_node_labels",
-    "ac_get_composite", "ac_energy", "ac_residual", "ac_project_simplex", "ac_set_profiling", "ac_get_profile", "ac_colour_means_static",
+    "ac_get_composite", "ac_energy", "ac_residual", "ac_project_simplex", "ac_set_profiling", "ac_set_profiling_mask", "ac_get_profile", "ac_colour_means_static",
     "ac_batch_create", "ac_batch_set_image", "ac_batch_set_phase", "ac_batch_get_phase", "ac_batch_segment",
     "ac_batch_step", "ac_batch_tune", "ac_batch_destroy", "ac_adjoint_forward", "ac_adjoint_backward",
     "ac_last_error",
@@ -99,6 +99,7 @@ def _load():
         "ac_residual": ([vp, P(d)], i),
         "ac_project_simplex": ([vp, vp, i64, i, vp], i),
         "ac_set_profiling": ([vp, i], i),
+        "ac_set_profiling_mask": ([vp, C.c_uint], i),
         "ac_get_profile": ([vp, P(ac_profile)], i),
         "ac_colour_means_static": ([vp, vp, i, i, i, vp, vp], i),
         "ac_batch_create": ([P(vp), P(ac_params), i, i], i),
@@ -266,6 +267,14 @@ def ac_project_simplex(y, x, count, N, stream=None):
 
 def ac_set_profiling(ctx, enable=True):
     return _check(lib.ac_set_profiling(ctx, int(bool(enable))))
+
+
+def ac_set_profiling_mask(ctx, classes):
+    """Profile only the named classes (see PROF_CLASSES); an empty list turns profiling off."""
+    mask = 0
+    for c in classes:
+        mask |= 1 << PROF_CLASSES.index(c)
+    return _check(lib.ac_set_profiling_mask(ctx, mask))
 
 
 def ac_get_profile(ctx) -> ac_profile:

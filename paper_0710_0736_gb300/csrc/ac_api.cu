@@ -228,6 +228,8 @@ struct ac_ctx {
   // instrumentation
   int64_t total_launches = 0;
   bool profiling = false;
+  unsigned prof_mask = (1u << AC_PROF_COUNT) - 1u;  // classes bracketed by events while profiling
+  unsigned prof_graph_mask = (1u << AC_PROF_COUNT) - 1u;  // the mask the profiled graphs were captured with
   struct Pending {
     cudaEvent_t a, b;
     int cls;
@@ -319,7 +321,8 @@ template <class F>
 int timed(ac_ctx *ctx, int cls, F &&f) {
   cudaEvent_t a = nullptr, b = nullptr;
   GraphSlot *cap = ctx->capturing;
-  if (ctx->profiling) {
+  const bool ev = ctx->profiling && ((ctx->prof_mask >> cls) & 1u);
+  if (ev) {
     if (cap) {
       AC_CUDA(cudaEventCreate(&a));
       cap->evs.push_back({a, nullptr, cls});
@@ -343,14 +346,16 @@ int timed(ac_ctx *ctx, int cls, F &&f) {
   if (cap) {
     cap->total += k;
     cap->launches[cls] += k;
-    if (ctx->profiling) AC_CUDA(cudaEventRecordWithFlags(b, ctx->s, cudaEventRecordExternal));
+    if (ev) AC_CUDA(cudaEventRecordWithFlags(b, ctx->s, cudaEventRecordExternal));
     return AC_OK;
   }
   ctx->total_launches += k;
   if (ctx->profiling) {
-    AC_CUDA(cudaEventRecord(b, ctx->s));
-    ctx->pending.push_back({a, b, cls});
     ctx->prof_launches[cls] += k;
+    if (ev) {
+      AC_CUDA(cudaEventRecord(b, ctx->s));
+      ctx->pending.push_back({a, b, cls});
+    }
   }
   return AC_OK;
 }
@@ -1155,7 +1160,7 @@ int ac_project_simplex(const double *y, double *x, int64_t count, int n_phases, 
   return AC_OK;
 }
 
-int ac_set_profiling(ac_ctx *ctx, int enable) {
+int ac_set_profiling_mask(ac_ctx *ctx, unsigned class_mask) {
   if (!ctx) return fail(AC_ERR_ARG, "ctx is NULL");
   int rc = prof_harvest(ctx);
   if (rc) return rc;
@@ -1164,8 +1169,23 @@ int ac_set_profiling(ac_ctx *ctx, int enable) {
     ctx->prof_launches[k] = 0;
   }
   ctx->prof_corr_launches = 0;
-  ctx->profiling = enable != 0;
+  class_mask &= (1u << AC_PROF_COUNT) - 1u;
+  ctx->profiling = class_mask != 0;
+  ctx->prof_mask = class_mask ? class_mask : (1u << AC_PROF_COUNT) - 1u;
+  if (ctx->profiling && ctx->prof_mask != ctx->prof_graph_mask) {
+    // the profiled graphs carry the events of the old mask: capture them again
+    if (ctx->s) cudaStreamSynchronize(ctx->s);
+    for (Solve *S : {&ctx->sv, &ctx->adj.sv}) {
+      for (int b = 0; b < 2; ++b) slot_release(S->smooth_resid[1][b]);
+      slot_release(S->correction[1]);
+    }
+    ctx->prof_graph_mask = ctx->prof_mask;
+  }
   return AC_OK;
+}
+
+int ac_set_profiling(ac_ctx *ctx, int enable) {
+  return ac_set_profiling_mask(ctx, enable ? (1u << AC_PROF_COUNT) - 1u : 0u);
 }
 
 int ac_get_profile(ac_ctx *ctx, ac_profile *out) {
