@@ -276,6 +276,37 @@ def test_graphs_match_direct_launches(ac, precision):
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
 
 
+def test_profiling_mask(ac):
+    """ac_set_profiling_mask: events (time) only around the chosen classes,
+    every class's launches still counted; switching back to all classes
+    re-captures the graphs with every event.  The arithmetic is unchanged."""
+    W, H, N = 96, 64, 5
+    img = synth.shapes_image(11, W, H, rect_side=(4, 30), disk_r=(3, 12))
+    u0 = synth.dirichlet_init(12, (W + 1) * (H + 1), N)
+    outs = []
+    for mode in ("all", "smooth", "off"):
+        seg = ac.Segmenter(W, H, N, 2.0, 1.0, 4.0, tol=1e-9, precision=ac.AC_MIXED)
+        seg.set_image(img)
+        seg.set_phase(u0)
+        if mode == "all":
+            ac.ac_set_profiling(seg.ctx, True)
+        elif mode == "smooth":
+            ac.ac_set_profiling_mask(seg.ctx, ["smooth"])
+        seg.step(3)
+        outs.append(seg.phase())
+        if mode == "smooth":
+            p = ac.ac_get_profile(seg.ctx).as_dict()
+            assert p["ms"]["smooth"] > 0 and p["launches"]["smooth"] > 0
+            assert all(p["ms"][c] == 0 for c in ac.PROF_CLASSES if c != "smooth")
+            assert p["launches"]["resid"] > 0 and p["launches"]["coarse"] > 0
+            ac.ac_set_profiling(seg.ctx, True)
+            seg.step(1)
+            p = ac.ac_get_profile(seg.ctx).as_dict()
+            assert p["ms"]["smooth"] > 0 and p["ms"]["resid"] > 0 and p["ms"]["coarse"] > 0
+        seg.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
 # --------------------------------------------------------------------------
 # full sizes: properties that hold at any size, checked by the oracle
 # --------------------------------------------------------------------------
