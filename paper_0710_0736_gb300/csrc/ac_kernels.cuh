@@ -297,7 +297,7 @@ __global__ void k_rhs(const double *__restrict__ u, const double *__restrict__ m
 // Both err by about 2^-46 of the terms' magnitudes.
 // ---------------------------------------------------------------------------
 template <int N, bool ENERGY>
-__global__ void __launch_bounds__(kBlock) k_means_partial_df(const double *__restrict__ u,
+__global__ void __launch_bounds__(kBlock, 2) k_means_partial_df(const double *__restrict__ u,
                                                              const double *__restrict__ mom, Geo g,
                                                              double *__restrict__ part) {
   // 4N sums per phase (k_means_partial's q = 0..3), and with ENERGY three
