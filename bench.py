@@ -147,6 +147,22 @@ class Clocks:
 # digest covers the kernel's text and that of the device helpers it calls.
 BREAKDOWN_STEPS = 5  # profiled steps after the timed region, for the per-class breakdown
 
+
+def job_rate(local_ms, local_units, world, device):
+    """Whole-job rate over `world` replicas: the work units of every rank
+    summed, divided by the slowest rank's time (the maximum over ranks).
+    Returns (units per second, maximum ms).  With world > 1 a process group
+    must be initialised (NCCL on the GPUs; gloo in the CPU tests)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    return float(u.item()) / (ms_max / 1e3), ms_max
+
 SMOOTH_TRAFFIC = {"sha256": "318a4651c615373ac2df954c0c3827a00bc82a0795abac18fe55f2b9d398ed73",
                   "bytes_per_node": (201.545e6 + 47.03e6) / 4198401, "n_phases": 8, "precision": "mixed"}
 SMOOTH_HELPERS = ("node_class", "edge_weights", "fslot", "geo_te", "geo_invD", "omega_t", "rcp_small", "proj_box",
@@ -561,14 +577,8 @@ def main():
     breakdown = ac.ac_get_profile(seg.ctx)
     ac.ac_set_profiling(seg.ctx, False)
 
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    sw = torch.tensor([float(st.fine_sweeps)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(sw, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    value = world * args.steps / (ms_max / 1e3)
-    gdof = N * n_nodes * float(sw.item()) / (ms_max / 1e3) / 1e9
+    value, ms_max = job_rate(ms, args.steps, world, "cuda")
+    gdof = job_rate(ms, N * n_nodes * float(st.fine_sweeps), world, "cuda")[0] / 1e9
 
     # roofline of the dominant kernel: the fine red-black smoother
     peaks, peak_kind = measured_peaks()
@@ -599,10 +609,8 @@ def main():
         for _ in range(args.steps):
             ac.ac_segment(seg.ctx, 1, labels, W, H, allow_not_converged=True)
         torch.cuda.synchronize()
-        el = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(el, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * args.steps / float(el.item()), "unit": "steps/s",
+        e2e_value, _ = job_rate((time.perf_counter() - t0) * 1e3, args.steps, world, "cuda")
+        e2e = {"value": e2e_value, "unit": "steps/s",
                "h2d_bytes_per_step": host_img.numel() * 4 / args.steps, "d2h_bytes_per_step": labels.numel(),
                "path": "ac_set_image from pinned host memory once, then per step ac_segment(1 step) with the "
                        "pixel labels read back to pinned host memory"}
@@ -622,10 +630,7 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        t64 = torch.tensor([ev0.elapsed_time(ev1)], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(t64, op=dist.ReduceOp.MAX)
-        v64 = world * args.fp64_steps / (float(t64.item()) / 1e3)
+        v64, _ = job_rate(ev0.elapsed_time(ev1), args.fp64_steps, world, "cuda")
         fp64 = {"value": v64, "unit": "steps/s", "steps": args.fp64_steps,
                 "vcycles_per_step": st64.total_cycles / max(1, st64.steps), "ratio_mixed_over_fp64": value / v64}
         seg = seg64

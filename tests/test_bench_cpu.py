@@ -40,3 +40,50 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["nodes"] == 4097 * 4097
+
+
+RANK_SCRIPT = r"""
+import os, sys
+sys.path.insert(0, sys.argv[1])
+import torch.distributed as dist
+import bench
+rank = int(os.environ["RANK"])
+dist.init_process_group("gloo", rank=rank, world_size=2)
+rate, ms_max = bench.job_rate([100.0, 250.0][rank], [3, 5][rank], 2, "cpu")
+dist.barrier()
+dist.destroy_process_group()
+print(f"RESULT {rank} {rate!r} {ms_max!r}", flush=True)
+"""
+
+
+def _free_port():
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_job_rate_over_two_gloo_ranks():
+    """The replicas' whole-job rate: units summed over the ranks, divided by the
+    slowest rank's time (bench.py's aggregation, here over two gloo ranks)."""
+    port = _free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE="2")
+        procs.append(subprocess.Popen([sys.executable, "-c", RANK_SCRIPT, ROOT], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True, cwd=ROOT))
+    outs = []
+    try:
+        for p in procs:
+            out, err = p.communicate(timeout=300)
+            assert p.returncode == 0, err[-2000:]
+            outs.append(out)
+    finally:
+        for p in procs:
+            if p.poll() is None:
+                p.kill()
+    for out in outs:
+        line = [l for l in out.splitlines() if l.startswith("RESULT")][0].split()
+        rate, ms_max = float(line[2]), float(line[3])
+        assert ms_max == 250.0
+        assert rate == pytest.approx((3 + 5) / 0.25)  # 8 units in the slowest rank's 250 ms
