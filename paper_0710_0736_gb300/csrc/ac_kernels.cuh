@@ -1647,8 +1647,8 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(TailArgs a, const 
 }
 
 // t = r - S v on a coarse level, one thread per (node, phase) (interior
-// nodes branch-free, as in k_coarse_jacobi; the same arithmetic and order as
-// op_offdiag).
+// nodes branch-free; the same arithmetic and order as op_offdiag).  The
+// float forms fuse it into the pre-smoothing pair (k_coarse_jacobi2_resid).
 template <typename T, int N>
 __global__ void k_coarse_resid(const T *__restrict__ op, const T *__restrict__ r, const T *__restrict__ v, Geo g,
                                T *__restrict__ t) {
