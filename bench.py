@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
-    ap.add_argument("--fp64-steps", type=int, default=3,
-                    help="steps of the plain FP64 form timed for the vs-FP64 ratio (0: skip)")
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="steps of the plain FP64 form timed for the vs-FP64 ratio (default: --steps, the same "
+                         "steps as the mixed form; 0: skip)")
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--nu1", type=int, default=2, help="pre-smoothing red-black sweeps per V-cycle")
@@ -66,9 +67,15 @@ def parse():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batch sub-line of the default workload")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint sub-line of the default workload")
+    ap.add_argument("--batch-steps", type=int, default=30, help="image steps of the batch sub-line (the workload's 30)")
+    ap.add_argument("--adjoint-evals", type=int, default=2, help="gradient evaluations of the adjoint sub-line")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = {"single": 100, "batch": 30, "adjoint": 4, "refine": 20}[args.workload]
+    if args.fp64_steps is None:
+        args.fp64_steps = args.steps if args.workload == "single" else 3
     return args
 
 
@@ -209,6 +216,28 @@ def smooth_traffic(n_nodes, n_phases, precision):
     return t["bytes_per_node"] * n_nodes
 
 
+def step_roofline(prof, breakdown, steps, ms, peak):
+    """The whole step against the HBM roofline: the algorithmic bytes of every
+    kernel class over the timed steps (the library's per-launch counts:
+    every array element a launch is defined on read and written once, the
+    coarse levels counted dense) per step, over the measured ms per step;
+    per class, the bytes and event times of the profiled sample after the
+    timed region."""
+    from paper_0710_0736_gb300 import ac
+    per_step = sum(prof.bytes) / steps
+    achieved = per_step / (ms / steps / 1e3) / 1e9
+    classes = {}
+    for k, c in enumerate(ac.PROF_CLASSES):
+        b, t = breakdown.bytes[k], breakdown.ms[k]
+        if b <= 0 and t <= 0:
+            continue
+        classes[c] = {"gb_per_step": b / BREAKDOWN_STEPS / 1e9, "ms_per_step": t / BREAKDOWN_STEPS,
+                      "achieved": (b / (t / 1e3) / 1e9) if t > 0 else None,
+                      "frac": (b / (t / 1e3) / 1e9 / peak) if t > 0 else None}
+    return {"alg_bytes_per_step": per_step, "achieved": achieved, "frac": achieved / peak, "unit": "GB/s",
+            "target_frac": 0.6, "by_class_sample": classes}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -272,11 +301,15 @@ def run_reference(args):
 # our arm
 # --------------------------------------------------------------------------
 
-def run_batch(args):
+def batch_leg(args, steps, warmup, fp64_steps):
     """The uneven batch: 256 shape images (as the 64x64 workload, scaled) of
     sizes 128^2..1024^2 and 768x512, N in {2,4,6}, noise sigma U[0.02,0.15],
-    eps 2, lambda 1, tau 4, mixed precision to tol 1e-6.  value = image time
-    steps per second (each timed step advances all images once)."""
+    eps 2, lambda 1, tau 4, mixed precision to tol 1e-6, `steps` time steps
+    per image timed after `warmup`.  value = image time steps per second
+    (each timed step advances all images once).  The plain FP64 form is timed
+    for fp64_steps steps twice: on the same stream pool as the mixed form
+    (the precision's gain alone) and image after image on one stream (the
+    unbatched form).  Returns the line as a dict."""
     import torch
     from paper_0710_0736_gb300 import ac, synth
     specs = synth.batch_specs(0, args.batch_images)
@@ -297,53 +330,68 @@ def run_batch(args):
         return b
 
     b = make(ac.AC_MIXED, args.streams)
-    chosen = None
     t_tune = 0.0
     if not args.no_tune:
         t0 = time.perf_counter()
-        chosen = b.tune(trial_steps=2)
+        b.tune(trial_steps=2)
         t_tune = time.perf_counter() - t0
-    b.step(args.warmup, allow_not_converged=True)
+    b.step(warmup, allow_not_converged=True)
     torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
     t0 = time.perf_counter()
-    st = b.step(args.steps, allow_not_converged=True)
+    st = b.step(steps, allow_not_converged=True)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
+    clk = clocks.stop()
     b.close()
-    # the plain FP64 form, one image after another on one stream
-    b64 = make(ac.AC_FP64, 1)
-    b64.step(1, allow_not_converged=True)
-    k64 = max(1, min(args.steps, args.fp64_steps or 1))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st64 = b64.step(k64, allow_not_converged=True)
-    torch.cuda.synchronize()
-    el64 = time.perf_counter() - t0
-    b64.close()
-    value = st.images * args.steps / el
-    v64 = st64.images * k64 / el64
+    value = st.images * steps / el
+
+    def fp64_rate(streams):
+        b64 = make(ac.AC_FP64, streams)
+        b64.step(1, allow_not_converged=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s64 = b64.step(fp64_steps, allow_not_converged=True)
+        torch.cuda.synchronize()
+        el64 = time.perf_counter() - t0
+        b64.close()
+        return {"value": s64.images * fp64_steps / el64, "unit": "image-steps/s", "steps": fp64_steps,
+                "streams": streams, "vcycles_per_image_step": s64.total_cycles / (s64.images * fp64_steps),
+                "all_converged": s64.converged_images == s64.images}
+
+    pooled = fp64_rate(args.streams)
+    unbatched = fp64_rate(1)
+    pooled["ratio_batched_mixed_over_this"] = value / pooled["value"]
+    unbatched["ratio_batched_mixed_over_this"] = value / unbatched["value"]
     sizes = {}
     for sp in specs:
         key = f"{sp['W']}x{sp['H']}/N{sp['N']}"
         sizes[key] = sizes.get(key, 0) + 1
-    line = {"metric": "batched Allen-Cahn image time steps/s (256 uneven images)", "value": value,
-            "unit": "image-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64", "data": "synthetic",
+    return {"metric": "batched Allen-Cahn image time steps/s (256 uneven images)", "value": value,
+            "unit": "image-steps/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
+            "ms_per_step": el / steps * 1e3, "higher_is_better": True,
+            "dtype": "f32 + double-float residual/means/rhs + f64 state",
             "config": {"workload": f"{st.images} images, sizes 128^2/256^2/512^2/1024^2/768x512, N in 2/4/6, "
-                                   f"tol {tol:g}, mixed precision, {args.streams} streams, autotuned "
-                                   f"{'no' if args.no_tune else 'yes'}", "nodes": st.nodes, "dof": st.dof,
-                       "groups": sizes},
+                                   f"noise U[0.02,0.15], eps 2, lambda 1, tau 4, tol {tol:g}, mixed precision, "
+                                   f"{args.streams} streams, autotuned {'no' if args.no_tune else 'yes'}",
+                       "nodes": st.nodes, "dof": st.dof, "groups": sizes,
+                       "l2": "no flush: the batch's fields (92 M nodes) exceed the 129 MB L2"},
             "gdof_per_s": st.dof_sweeps / el / 1e9,
-            "vcycles_per_image_step": st.total_cycles / (st.images * args.steps),
-            "all_converged": st.converged_images == st.images, "tune_seconds": t_tune,
-            "plain_fp64_gpu": {"value": v64, "unit": "image-steps/s", "steps": k64, "streams": 1,
-                               "ratio_batched_mixed_over_fp64": value / v64}}
+            "vcycles_per_image_step": st.total_cycles / (st.images * steps),
+            "all_converged": st.converged_images == st.images, "tune_seconds": t_tune, "clocks": clk,
+            "plain_fp64_gpu_same_pool": pooled, "plain_fp64_gpu_unbatched": unbatched,
+            "ratio_mixed_over_fp64": value / unbatched["value"]}
+
+
+def run_batch(args):
+    line = batch_leg(args, args.steps, args.warmup, max(1, min(args.steps, args.fp64_steps or 1)))
+    line.update({"scaling": "weak", "vs_baseline": None, "data": "synthetic"})
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_adjoint(args):
+def adjoint_leg(args, steps, warmup, with_cpu):
     """Gradients through T = 64 time steps of the 512 x 512, N = 4 disks image
     (12 disks, noise 0.08; eps 2, lambda 1, tau 4, each step solved to 1e-10)
     of the misfit L = 1/2 sum Mhat |u^T - onehot(target)|^2 to a 6-seed Voronoi
@@ -351,7 +399,7 @@ def run_adjoint(args):
     is one gradient evaluation: the forward with checkpoints every 8 steps
     (ac_adjoint_forward), then the backward sweep (ac_adjoint_backward),
     which recomputes each segment from its checkpoint.  value = gradient
-    evaluations per second."""
+    evaluations per second.  Returns the line as a dict."""
     import torch
     import oracle
     from paper_0710_0736_gb300 import ac, synth
@@ -406,15 +454,15 @@ def run_adjoint(args):
 
     clocks = Clocks(0)
     clocks.start()
-    fwd_ms, bwd_ms, gl, ge = measure(ac.AC_FP64, args.steps, args.warmup)
+    fwd_ms, bwd_ms, gl, ge = measure(ac.AC_FP64, steps, warmup)
     clk = clocks.stop()
     # the mixed-precision forward (FP32 sweeps, FP64 defect correction) with the same FP64 adjoint
-    mfwd_ms, mbwd_ms, mgl, mge = measure(ac.AC_MIXED, max(1, args.steps // 2), args.warmup)
+    mfwd_ms, mbwd_ms, mgl, mge = measure(ac.AC_MIXED, max(1, steps // 2), warmup)
     ms = fwd_ms + bwd_ms
     value = 1e3 / ms
 
     cpu = None
-    if not args.no_cpu:
+    if with_cpu:
         crop, Tc = 128, 8
         ic = img[:crop, :crop]
         uc = synth.dirichlet_init(1, (crop + 1) ** 2, N)
@@ -428,10 +476,9 @@ def run_adjoint(args):
         cpu = {"value": 1.0 / (sec * scale), "unit": "gradient evaluations/s", "cores": 1, "kind": "oracle",
                "sample": f"oracle forward ({Tc} steps, SSC to {tol:g}) + FP64 adjoint (tangent CG to 1e-12) on "
                          f"the {crop}x{crop} corner, {sec:.1f} s, scaled by nodes and steps x{scale:.0f}"}
-    line = {"metric": "adjoint gradient evaluations/s (64 steps, 512^2 N=4)", "value": value,
-            "unit": "gradient evaluations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
+    return {"metric": "adjoint gradient evaluations/s (64 steps, 512^2 N=4)", "value": value,
+            "unit": "gradient evaluations/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms, "higher_is_better": True, "dtype": "f64",
             "config": {"workload": f"{W}x{H} disks image (12 disks, noise 0.08), N={N}, eps={cfg['eps']}, "
                                    f"lambda={cfg['lam']}, tau={cfg['tau']}, {T} steps to tol {tol:g}, "
                                    f"checkpoints every {every}, misfit to a 6-seed Voronoi target",
@@ -441,6 +488,11 @@ def run_adjoint(args):
             "mixed_forward": {"forward_ms": mfwd_ms, "backward_ms": mbwd_ms, "grad_lambda": mgl, "grad_eps": mge,
                               "value": 1e3 / (mfwd_ms + mbwd_ms)},
             "cpu_baseline": cpu, "clocks": clk}
+
+
+def run_adjoint(args):
+    line = adjoint_leg(args, args.steps, args.warmup, not args.no_cpu)
+    line.update({"scaling": "weak", "vs_baseline": None, "data": "synthetic"})
     print(json.dumps(line), flush=True)
     return 0
 
@@ -551,8 +603,14 @@ def main():
     stream = torch.cuda.current_stream()
     seg = ac.Segmenter(W, H, N, cfg["eps"], cfg["lam"], cfg["tau"], tol=cfg["tol"], max_cycles=1000, seed=rank,
                        precision=prec, stream=stream.cuda_stream, nu1=args.nu1, nu2=args.nu2)
-    seg.set_image(torch.from_numpy(img).cuda())
+    dev_img = torch.from_numpy(img).cuda()
+    seg.set_image(dev_img)
     seg.step(args.warmup, allow_not_converged=True)
+    # back to the seeded start: the timed steps are the workload's first K
+    # time steps (as the end-to-end leg below times them); the warm-up has
+    # captured the graphs and loaded the kernels
+    seg.set_image(dev_img)
+    torch.cuda.synchronize()
 
     # events around the smoother only (its launch times give the roofline); the
     # per-class breakdown comes from a few profiled steps after the timed region
@@ -595,9 +653,11 @@ def main():
                                 "correction, scaled by nodes); compare plain_launch_bytes",
                 "bytes_per_launch": bytes_avg, "plain_launch_bytes": prof.smooth_bytes_per_launch,
                 "correction_launches": prof.smooth_corr_launches, "launches": sm_launches,
-                "avg_launch_ms": avg_launch_s * 1e3, "share_of_step_time": sm_ms / max(1e-9, ms)}
+                "avg_launch_ms": avg_launch_s * 1e3, "share_of_step_time": sm_ms / max(1e-9, ms),
+                "step": step_roofline(prof, breakdown, args.steps, ms, peaks["hbm_gbs"])}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: the same K steps
+    # from the seeded start, the image copied in from pinned host memory
     e2e = None
     if not args.no_e2e:
         host_img = torch.from_numpy(img).pin_memory()
@@ -612,8 +672,9 @@ def main():
         e2e_value, _ = job_rate((time.perf_counter() - t0) * 1e3, args.steps, world, "cuda")
         e2e = {"value": e2e_value, "unit": "steps/s",
                "h2d_bytes_per_step": host_img.numel() * 4 / args.steps, "d2h_bytes_per_step": labels.numel(),
-               "path": "ac_set_image from pinned host memory once, then per step ac_segment(1 step) with the "
-                       "pixel labels read back to pinned host memory"}
+               "path": "ac_set_image from pinned host memory once (it resets u to the seeded start, as before "
+                       "the device-timed steps), then per step ac_segment(1 step) with the pixel labels read back "
+                       "to pinned host memory: the same K time steps as value"}
 
     # the plain FP64 form on the same workload, for the mixed/FP64 ratio
     fp64 = None
@@ -621,8 +682,9 @@ def main():
         seg.close()
         seg64 = ac.Segmenter(W, H, N, cfg["eps"], cfg["lam"], cfg["tau"], tol=cfg["tol"], max_cycles=1000, seed=rank,
                              precision=ac.AC_FP64, stream=stream.cuda_stream, nu1=args.nu1, nu2=args.nu2)
-        seg64.set_image(torch.from_numpy(img).cuda())
+        seg64.set_image(dev_img)
         seg64.step(args.warmup, allow_not_converged=True)
+        seg64.set_image(dev_img)  # the same time steps from the seeded start as the mixed form
         barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -631,7 +693,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
         v64, _ = job_rate(ev0.elapsed_time(ev1), args.fp64_steps, world, "cuda")
-        fp64 = {"value": v64, "unit": "steps/s", "steps": args.fp64_steps,
+        fp64 = {"value": v64, "unit": "steps/s", "steps": args.fp64_steps, "from": "the seeded start",
                 "vcycles_per_step": st64.total_cycles / max(1, st64.steps), "ratio_mixed_over_fp64": value / v64}
         seg = seg64
 
@@ -643,12 +705,23 @@ def main():
                "kind": "oracle",
                "sample": f"{args.cpu_steps} oracle steps (SSC, V(2,2), tol {cfg['tol']:g}) on the {args.crop}x"
                          f"{args.crop} corner of the workload image, {sum(times):.1f} s, scaled by nodes "
-                         f"{full_nodes}/{crop_nodes}"}
+                         f"{full_nodes}/{crop_nodes}; an upper bound on the oracle's rate at full size (its "
+                         f"per-node cost grows with the number of levels)"}
+
+    # the other two workloads, bounded, each as a sub-line with its own config
+    batch = adjoint = None
+    if rank == 0 and world == 1:
+        seg.close()
+        if not args.no_batch:
+            batch = batch_leg(args, args.batch_steps, args.warmup, 3)
+        if not args.no_adjoint:
+            adjoint = adjoint_leg(args, args.adjoint_evals, 1, False)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32 + double-float residual/means/rhs + f64 state",
                 "data": "synthetic",
                 "config": workload_config(cfg, args, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                                                       "solver": f"truncated monotone multigrid V({args.nu1},{args.nu2})"}),
@@ -658,7 +731,8 @@ def main():
                 "all_converged": bool(st.converged), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk,
                 "profile_ms_sample": {"steps": BREAKDOWN_STEPS, "after": "the timed region, every class profiled",
-                                      "ms": dict(zip(ac.PROF_CLASSES, [round(v, 3) for v in breakdown.ms]))}}
+                                      "ms": dict(zip(ac.PROF_CLASSES, [round(v, 3) for v in breakdown.ms]))},
+                "batch": batch, "adjoint": adjoint}
         print(json.dumps(line), flush=True)
     seg.close()
     if world > 1:

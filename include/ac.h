@@ -124,6 +124,9 @@ typedef struct {
                                       x += omega d: they read d of the other colour as well */
   double smooth_corr_extra_bytes;  /* the extra algorithmic bytes of such a launch: 0.5 n N 8 (AC_FP64),
                                       0.5 n N 4 (AC_MIXED) */
+  double bytes[AC_PROF_COUNT];     /* algorithmic HBM bytes of the class's launches while profiling was on:
+                                      every array element a launch is defined on read once and written once
+                                      (dense counts: rows the coarse kernels skip are still counted) */
 } ac_profile;
 
 /* Defaults: tol 1e-10, nu1 = nu2 = 2, max_cycles 200, coarse_min 4, AC_FP64,
@@ -238,6 +241,17 @@ int ac_adjoint_forward(ac_ctx *ctx, int n_steps, int checkpoint_every);
  * its checkpoint.  Leaves u = u^T.  AC_ERR_STATE without a forward. */
 int ac_adjoint_backward(ac_ctx *ctx, const double *grad_u, double *grad_lambda, double *grad_eps, double *grad_image,
                         double *grad_u0);
+
+/* Check of the checkpointing (no counterpart in the paper): *count receives
+ * the number of components at which a segment recomputed by the last
+ * ac_adjoint_backward ended on a state that differs, bit for bit, from the
+ * forward's own state there (the next checkpoint, or u^T for the last
+ * segment), summed over the segments.  Each segment's first step starts its
+ * correction from zero in both passes (AC_MIXED), so the recomputation repeats
+ * the forward's arithmetic and the count is 0; a nonzero count means that the
+ * backward pass differentiated states other than those the forward visited.
+ * 0 before any backward pass.  AC_ERR_ARG for NULL arguments. */
+int ac_adjoint_recompute_diff(ac_ctx *ctx, int64_t *count);
 
 /* ---- batches of independent images (no counterpart in the paper) -------- */
 

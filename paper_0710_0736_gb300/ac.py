@@ -24,7 +24,7 @@ EXPORTS = [
     "ac_get_composite", "ac_energy", "ac_residual", "ac_project_simplex", "ac_set_profiling", "ac_set_profiling_mask", "ac_get_profile", "ac_colour_means_static",
     "ac_batch_create", "ac_batch_set_image", "ac_batch_set_phase", "ac_batch_get_phase", "ac_batch_segment",
     "ac_batch_step", "ac_batch_tune", "ac_batch_destroy", "ac_adjoint_forward", "ac_adjoint_backward",
-    "ac_last_error",
+    "ac_adjoint_recompute_diff", "ac_last_error",
 ]
 PROF_CLASSES = ["smooth", "resid", "coarse", "transfer", "linesearch", "setup", "outer"]
 
@@ -48,7 +48,7 @@ class ac_stats(C.Structure):
 class ac_profile(C.Structure):
     _fields_ = [("ms", C.c_double * 7), ("launches", C.c_int64 * 7), ("smooth_bytes_per_launch", C.c_double),
                 ("total_launches", C.c_int64), ("smooth_corr_launches", C.c_int64),
-                ("smooth_corr_extra_bytes", C.c_double)]
+                ("smooth_corr_extra_bytes", C.c_double), ("bytes", C.c_double * 7)]
 
     def as_dict(self):
         return {"ms": dict(zip(PROF_CLASSES, list(self.ms))),
@@ -56,7 +56,8 @@ class ac_profile(C.Structure):
                 "smooth_bytes_per_launch": self.smooth_bytes_per_launch,
                 "total_launches": self.total_launches,
                 "smooth_corr_launches": self.smooth_corr_launches,
-                "smooth_corr_extra_bytes": self.smooth_corr_extra_bytes}
+                "smooth_corr_extra_bytes": self.smooth_corr_extra_bytes,
+                "bytes": dict(zip(PROF_CLASSES, list(self.bytes)))}
 
 
 class ac_batch_stats(C.Structure):
@@ -112,6 +113,7 @@ def _load():
         "ac_batch_destroy": ([vp], None),
         "ac_adjoint_forward": ([vp, i, i], i),
         "ac_adjoint_backward": ([vp, vp, P(d), P(d), vp, vp], i),
+        "ac_adjoint_recompute_diff": ([vp, P(i64)], i),
         "ac_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -330,6 +332,15 @@ def ac_adjoint_backward(ctx, grad_u, grad_image, grad_u0=None, allow_not_converg
     _check(lib.ac_adjoint_backward(ctx, grad_u.data_ptr(), C.byref(gl), C.byref(ge), grad_image.data_ptr(),
                                    None if grad_u0 is None else grad_u0.data_ptr()), ok)
     return gl.value, ge.value
+
+
+def ac_adjoint_recompute_diff(ctx) -> int:
+    """Components at which the last backward pass's recomputed segment ends
+    differed from the forward's states (0 when the recomputation repeated the
+    forward exactly)."""
+    k = C.c_int64()
+    _check(lib.ac_adjoint_recompute_diff(ctx, C.byref(k)))
+    return k.value
 
 
 def ac_last_error() -> str:

@@ -130,6 +130,7 @@ ac::Galerkin0Table galerkin0_table(const ac::Geo &gf, const ac::Geo &gc) {
 struct GraphSlot {
   cudaGraphExec_t exec = nullptr;
   int64_t launches[AC_PROF_COUNT] = {};
+  double bytes[AC_PROF_COUNT] = {};  // algorithmic HBM bytes of the launches per class
   int64_t total = 0;
   struct Ev {
     cudaEvent_t a, b;
@@ -195,6 +196,8 @@ struct AdjState {
   double *kw = nullptr, *kr = nullptr, *kp = nullptr, *kq = nullptr, *kq_prev = nullptr;  // flexible CG vectors
   double *kpart = nullptr, *ktot = nullptr;  // its dot products
   double *gimg = nullptr;   // dL/dI on the refined grid (refine > 0)
+  unsigned long long *ndiff = nullptr;  // components where a recomputed segment end differed from the forward
+  int64_t recompute_diff = 0;           // its value after the last backward pass
   Solve sv;                 // FP64 tangent-form solve
   std::vector<void *> allocs;
 };
@@ -239,6 +242,7 @@ struct ac_ctx {
   std::vector<Pending> pending;
   double prof_ms[AC_PROF_COUNT] = {};
   int64_t prof_launches[AC_PROF_COUNT] = {};
+  double prof_bytes[AC_PROF_COUNT] = {};
   int64_t prof_corr_launches = 0;  // smoother launches that applied a pending correction
   // CUDA graphs (off on the legacy default stream, which cannot be captured)
   bool use_graphs = false;
@@ -246,6 +250,28 @@ struct ac_ctx {
 };
 
 namespace {
+
+// Algorithmic HBM bytes of the solve's kernels, for the profile: every array
+// element a launch is defined on, read once and written once (dense: the
+// coarse kernels' skipping of rows with a zero diagonal is not credited, so
+// their DRAM traffic can be lower).  ns = N values of one node of a level in
+// the solve's scalar type (N * elem bytes).
+struct ByteModel {
+  double ns;   // N * sizeof(scalar)
+  double ob;   // 1 when the fine level has an obstacle array (shifted and tangent forms)
+  double n;    // fine nodes
+  // one launch of the fine smoother (one colour): the colour's rhs (and
+  // obstacle) and the other colour's iterate read, the colour's iterate written
+  double smooth_launch() const { return 0.5 * n * ns * (3 + ob); }
+};
+
+ByteModel byte_model(const ac_ctx *ctx, const Solve &S) {
+  ByteModel b;
+  b.ns = (double)ctx->N * S.o->elem;
+  b.ob = S.ob ? 1.0 : 0.0;
+  b.n = (double)S.lv[0].n;
+  return b;
+}
 
 int dev_alloc(ac_ctx *ctx, void **p, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -313,12 +339,14 @@ int prof_event(ac_ctx *ctx, cudaEvent_t *e) {
   return AC_OK;
 }
 
-// Run one launcher call: count its kernels, check the launch, and bracket it
-// with events on the context's stream while profiling.
-// While a graph is being captured the launches and event pairs are booked to
-// that graph (and counted each time it is replayed) instead.
+// Run one launcher call: count its kernels and their algorithmic HBM bytes
+// (`bytes`, the caller's count of what the launches must read and write),
+// check the launch, and bracket it with events on the context's stream while
+// profiling.  While a graph is being captured the launches, bytes and event
+// pairs are booked to that graph (and counted each time it is replayed)
+// instead.
 template <class F>
-int timed(ac_ctx *ctx, int cls, F &&f) {
+int timed(ac_ctx *ctx, int cls, double bytes, F &&f) {
   cudaEvent_t a = nullptr, b = nullptr;
   GraphSlot *cap = ctx->capturing;
   const bool ev = ctx->profiling && ((ctx->prof_mask >> cls) & 1u);
@@ -346,12 +374,14 @@ int timed(ac_ctx *ctx, int cls, F &&f) {
   if (cap) {
     cap->total += k;
     cap->launches[cls] += k;
+    cap->bytes[cls] += bytes;
     if (ev) AC_CUDA(cudaEventRecordWithFlags(b, ctx->s, cudaEventRecordExternal));
     return AC_OK;
   }
   ctx->total_launches += k;
   if (ctx->profiling) {
     ctx->prof_launches[cls] += k;
+    ctx->prof_bytes[cls] += bytes;
     if (ev) {
       AC_CUDA(cudaEventRecord(b, ctx->s));
       ctx->pending.push_back({a, b, cls});
@@ -402,16 +432,26 @@ int run_graph(ac_ctx *ctx, GraphSlot &slot, F &&enqueue) {
   AC_CUDA(cudaGraphLaunch(slot.exec, ctx->s));
   ctx->total_launches += slot.total;
   if (ctx->profiling) {
-    for (int k = 0; k < AC_PROF_COUNT; ++k) ctx->prof_launches[k] += slot.launches[k];
+    for (int k = 0; k < AC_PROF_COUNT; ++k) {
+      ctx->prof_launches[k] += slot.launches[k];
+      ctx->prof_bytes[k] += slot.bytes[k];
+    }
     for (const auto &ev : slot.evs) ctx->pending.push_back({ev.a, ev.b, ev.cls});
   }
   return AC_OK;
 }
 
-#define AC_RUN(cls, expr)                                  \
-  do {                                                     \
-    int rc_ = timed(ctx, (cls), [&]() { return (expr); }); \
-    if (rc_) return rc_;                                   \
+#define AC_RUN(cls, expr)                                       \
+  do {                                                          \
+    int rc_ = timed(ctx, (cls), 0.0, [&]() { return (expr); }); \
+    if (rc_) return rc_;                                        \
+  } while (0)
+
+// The same, booking `bytes` algorithmic HBM bytes to the class.
+#define AC_RUNB(cls, bytes, expr)                                       \
+  do {                                                                  \
+    int rc_ = timed(ctx, (cls), (double)(bytes), [&]() { return (expr); }); \
+    if (rc_) return rc_;                                                \
   } while (0)
 
 // Reads rho back (the one device-to-host dependency of a cycle).  While
@@ -451,47 +491,63 @@ int tail_level(const Solve &S, size_t *smem) {
 int coarse_vcycle(ac_ctx *ctx, Solve &S, int k, void **res) {
   Level &L = S.lv[k];
   const ac::SolverOps *o = S.o;
+  // level arrays: the operator is 4 values (C, E, N, NE) per node and phase,
+  // r, v, t one; pair = one fused pair of l1-Jacobi sweeps from v (7 values:
+  // operator, r and v read, the result written), from zero 6
+  const double ns = (double)ctx->N * o->elem, lk = (double)L.n * ns;
+  const double pair = 7 * lk, pair0 = 6 * lk;
   size_t smem = 0;
   if (k == tail_level(S, &smem)) {
     ac::TailArgs a{};
     a.levels = S.depth - k;
+    double ops = 0;
     for (int l = 0; l < a.levels; ++l) {
       a.W[l] = S.lv[k + l].g.W;
       a.H[l] = S.lv[k + l].g.H;
       a.op[l] = S.lv[k + l].op;
+      ops += 4.0 * (double)S.lv[k + l].n * ns;
     }
-    AC_RUN(AC_PROF_COARSE, o->coarse_tail(a, L.r, L.v, kCoarseSweeps, kCoarsestSweeps, smem, ctx->s));
+    AC_RUNB(AC_PROF_COARSE, ops + 2 * lk, o->coarse_tail(a, L.r, L.v, kCoarseSweeps, kCoarsestSweeps, smem, ctx->s));
     *res = L.v;
     return AC_OK;
   }
   if (k == S.depth - 1) {
     if (L.n <= kCoarsestBlockNodes) {
       AC_CUDA(cudaMemsetAsync(L.v, 0, (size_t)L.n * ctx->N * o->elem, ctx->s));
-      AC_RUN(AC_PROF_COARSE, o->coarse_solve(L.op, L.r, L.v, L.g, kCoarsestSweeps, ctx->s));
+      AC_RUNB(AC_PROF_COARSE, 6 * lk, o->coarse_solve(L.op, L.r, L.v, L.g, kCoarsestSweeps, ctx->s));
       *res = L.v;
     } else {
-      AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, 2 * kCoarseSweeps, true, res, ctx->s));
+      AC_RUNB(AC_PROF_COARSE, pair0 + (kCoarseSweeps - 1) * pair,
+              o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, 2 * kCoarseSweeps, true, res, ctx->s));
     }
     return AC_OK;
   }
   Level &C = S.lv[k + 1];
+  const double lc = (double)C.n * ns;
   // v starts at 0: the first pair of sweeps writes every node without reading v
   void *v = nullptr, *other = nullptr;
   if (kCoarseSweeps == 2) {
-    AC_RUN(AC_PROF_COARSE, o->coarse_pre_resid(L.op, L.r, L.v, L.t, L.g, ctx->s));
+    // float: one launch reads the operator and r and writes v and t; double:
+    // the pair, then the residual (operator, r, v read, t written)
+    AC_RUNB(AC_PROF_COARSE, o->elem == 4 ? 7 * lk : pair0 + 7 * lk,
+            o->coarse_pre_resid(L.op, L.r, L.v, L.t, L.g, ctx->s));
     v = L.v;
     other = L.t;
   } else {
-    AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, true, &v, ctx->s));
+    AC_RUNB(AC_PROF_COARSE, pair0 + (kCoarseSweeps / 2 - 1) * pair,
+            o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, true, &v, ctx->s));
     other = v == L.v ? L.t : L.v;
-    AC_RUN(AC_PROF_COARSE, o->coarse_resid(L.op, L.r, v, L.g, other, ctx->s));
+    AC_RUNB(AC_PROF_COARSE, 7 * lk, o->coarse_resid(L.op, L.r, v, L.g, other, ctx->s));
   }
-  AC_RUN(AC_PROF_TRANSFER, o->restrict_(other, L.g, C.g, C.op, C.r, ctx->s));
+  // restriction: t read, the coarse diagonal read, r written
+  AC_RUNB(AC_PROF_TRANSFER, lk + 2 * lc, o->restrict_(other, L.g, C.g, C.op, C.r, ctx->s));
   void *cv = nullptr;
   int rc = coarse_vcycle(ctx, S, k + 1, &cv);
   if (rc) return rc;
-  AC_RUN(AC_PROF_TRANSFER, o->prolong_add(cv, L.g, C.g, L.op, v, ctx->s));
-  AC_RUN(AC_PROF_COARSE, o->coarse_smooth(L.op, L.r, v, other, L.g, kCoarseSweeps, false, res, ctx->s));
+  // prolongation: coarse v and this level's diagonal read, v read and written
+  AC_RUNB(AC_PROF_TRANSFER, lc + 3 * lk, o->prolong_add(cv, L.g, C.g, L.op, v, ctx->s));
+  AC_RUNB(AC_PROF_COARSE, (kCoarseSweeps / 2) * pair,
+          o->coarse_smooth(L.op, L.r, v, other, L.g, kCoarseSweeps, false, res, ctx->s));
   return AC_OK;
 }
 
@@ -510,6 +566,7 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
   const ac::SolverOps *o = S.o;
   const ac::Geo &g0 = S.lv[0].g;
   const bool coarse = S.depth > 1;
+  const ByteModel bm = byte_model(ctx, S);
   double rho = 0;
   int cyc = 0, status = AC_ERR_NOT_CONVERGED;
   int64_t sweeps = 0;
@@ -526,10 +583,19 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
       // every-node residual, in which case the last pass re-zeroes them.
       const bool fused = nsw >= 1;
       void *rt_zero = (fused && ctx->p.nu1 == 0) ? S.rt : nullptr;
-      AC_RUN(AC_PROF_SMOOTH, o->smooth(S.x, S.rhs, S.ob, corr, ctx->omega, g0, nsw, rt_zero,
-                                       fused ? S.mask : nullptr, ctx->s));
+      // 2 nsw colour passes; the first also reads the other colour's pending
+      // correction; the last writes its colour's mask (and rt = 0)
+      const double sm_bytes = 2.0 * nsw * bm.smooth_launch() + (corr && nsw > 0 ? 0.5 * bm.n * bm.ns : 0.0) +
+                              (fused ? 0.5 * bm.n * (1.0 + (rt_zero ? bm.ns : 0.0)) : 0.0);
+      AC_RUNB(AC_PROF_SMOOTH, sm_bytes, o->smooth(S.x, S.rhs, S.ob, corr, ctx->omega, g0, nsw, rt_zero,
+                                                  fused ? S.mask : nullptr, ctx->s));
       AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
-      AC_RUN(AC_PROF_RESID, o->resid(S.x, S.rhs, S.ob, g0, S.rt, S.mask, ctx->rho, fused ? 0 : -1, ctx->s));
+      // residual at the visited nodes: x (their own and, for one colour, the
+      // other colour's as neighbours), rhs, obstacle read, rt and the mask
+      // byte written
+      const double rs_bytes = fused ? 0.5 * bm.n * (bm.ns * (4 + bm.ob) + 1) : bm.n * (bm.ns * (3 + bm.ob) + 1);
+      AC_RUNB(AC_PROF_RESID, rs_bytes,
+              o->resid(S.x, S.rhs, S.ob, g0, S.rt, S.mask, ctx->rho, fused ? 0 : -1, ctx->s));
       return AC_OK;
     });
     if (rc) return rc;
@@ -550,15 +616,23 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
     if (!coarse) continue;
     rc = run_graph(ctx, S.correction[prof], [&]() -> int {
       Level &L1 = S.lv[1];
-      AC_RUN(AC_PROF_TRANSFER, o->galerkin0(S.mask, g0, L1.g, S.tab0, L1.op, ctx->s));
+      const double l1 = (double)L1.n * bm.ns;
+      // first-level operator from the fine mask; each coarser one from the
+      // level above (4 values per node and phase read and written)
+      AC_RUNB(AC_PROF_TRANSFER, bm.n + 4 * l1, o->galerkin0(S.mask, g0, L1.g, S.tab0, L1.op, ctx->s));
       for (int k = 1; k + 1 < S.depth; ++k)
-        AC_RUN(AC_PROF_TRANSFER, o->galerkin(S.lv[k].op, S.lv[k].g, S.lv[k + 1].g, S.lv[k + 1].op, ctx->s));
-      AC_RUN(AC_PROF_TRANSFER, o->restrict0(S.rt, g0, L1.g, L1.op, L1.r, ctx->s));
+        AC_RUNB(AC_PROF_TRANSFER, 4.0 * (double)(S.lv[k].n + S.lv[k + 1].n) * bm.ns,
+                o->galerkin(S.lv[k].op, S.lv[k].g, S.lv[k + 1].g, S.lv[k + 1].op, ctx->s));
+      // rt read, the first level's diagonal read and its r written
+      AC_RUNB(AC_PROF_TRANSFER, bm.n * bm.ns + 2 * l1, o->restrict0(S.rt, g0, L1.g, L1.op, L1.r, ctx->s));
       void *v1 = nullptr;
       int rc2 = coarse_vcycle(ctx, S, 1, &v1);
       if (rc2) return rc2;
-      AC_RUN(AC_PROF_LINESEARCH, o->line_search(S.x, S.ob, S.rt, v1, S.mask, g0, L1.g, S.d, ctx->ls_part,
-                                                ctx->ls_tot, ctx->omega, ctx->s));
+      // direction: x, obstacle, rt, mask and the first level's v read, d
+      // written; curvature: d and the mask read
+      const double ls_bytes = bm.n * (bm.ns * (3 + bm.ob) + 1) + l1 + bm.n * (bm.ns + 1);
+      AC_RUNB(AC_PROF_LINESEARCH, ls_bytes, o->line_search(S.x, S.ob, S.rt, v1, S.mask, g0, L1.g, S.d, ctx->ls_part,
+                                                           ctx->ls_tot, ctx->omega, ctx->s));
       return AC_OK;
     });
     if (rc) return rc;
@@ -588,7 +662,9 @@ int solve_mixed(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_o
   const double accept = ctx->p.tol * (1.0 - kRho32Rel);
   for (;;) {
     AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
-    AC_RUN(AC_PROF_OUTER, o->outer_resid(ctx->u, (const float *)ctx->b, ctx->g0, ctx->r32, ctx->u32, ctx->rho, rho32, ctx->s));
+    // u (binary64) and b (double-float pairs) read, r32 and u32 written
+    AC_RUNB(AC_PROF_OUTER, (double)ctx->n * ctx->N * 24,
+            o->outer_resid(ctx->u, (const float *)ctx->b, ctx->g0, ctx->r32, ctx->u32, ctx->rho, rho32, ctx->s));
     int rc = read_rho(ctx, &rho);
     if (rc) return rc;
     if (std::isnan(rho) || std::isinf(rho)) {
@@ -617,7 +693,9 @@ int solve_mixed(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_o
     cycles += c;
     sweeps += sw;
     if (rc && rc != AC_ERR_NOT_CONVERGED) return rc;
-    AC_RUN(AC_PROF_OUTER, o->outer_update(ctx->u, (const float *)ctx->sv.x, ctx->g0, ctx->s));
+    // u read and written, delta read
+    AC_RUNB(AC_PROF_OUTER, (double)ctx->n * ctx->N * 20,
+            o->outer_update(ctx->u, (const float *)ctx->sv.x, ctx->g0, ctx->s));
     ++outer;
     ctx->delta_warm = rc == AC_OK && outer == 1;
   }
@@ -957,6 +1035,7 @@ static int set_image_impl(ac_ctx *ctx, const void *rgb, int is_device, bool f64)
   ctx->adj.ready = false;
   ctx->have_image = true;
   ctx->have_rhs = false;
+  ctx->delta_warm = false;
   return AC_OK;
 }
 
@@ -972,19 +1051,23 @@ int ac_step(ac_ctx *ctx, int n_steps, ac_stats *out) {
   int status = AC_OK;
   const double a1 = 1.0 + 2.0 * ctx->p.tau / ctx->p.eps, tl = ctx->p.tau * ctx->p.lambda;
   const bool mixed = ctx->p.precision == AC_MIXED;
+  // means (and energy): u (binary64) and the moments (4 doubles) read per
+  // node; right-hand side: the same read and b (8 bytes per phase) written
+  const double mean_bytes = (double)ctx->n * (8.0 * ctx->N + 32), rhs_bytes = mean_bytes + (double)ctx->n * 8.0 * ctx->N;
   for (int t = 0; t < n_steps; ++t) {
     // the energy is only evaluated for the statistics of the last step
     double *energy = (out && t == n_steps - 1) ? ctx->energy : nullptr;
     if (mixed)
-      AC_RUN(AC_PROF_SETUP, ctx->ops->means_df(ctx->u, ctx->mom, ctx->g0, ctx->part, ctx->tot, ctx->c, energy,
-                                               ctx->p.eps, ctx->p.lambda, ctx->s));
+      AC_RUNB(AC_PROF_SETUP, mean_bytes, ctx->ops->means_df(ctx->u, ctx->mom, ctx->g0, ctx->part, ctx->tot, ctx->c,
+                                                            energy, ctx->p.eps, ctx->p.lambda, ctx->s));
     else
-      AC_RUN(AC_PROF_SETUP, ctx->ops->means(ctx->u, ctx->mom, ctx->g0, ctx->part, ctx->tot, ctx->c, energy,
-                                            ctx->p.eps, ctx->p.lambda, ctx->s));
+      AC_RUNB(AC_PROF_SETUP, mean_bytes, ctx->ops->means(ctx->u, ctx->mom, ctx->g0, ctx->part, ctx->tot, ctx->c,
+                                                         energy, ctx->p.eps, ctx->p.lambda, ctx->s));
     if (mixed)
-      AC_RUN(AC_PROF_SETUP, ctx->ops->rhs_df(ctx->u, ctx->mom, ctx->c, ctx->g0, a1, tl, (float *)ctx->b, ctx->s));
+      AC_RUNB(AC_PROF_SETUP, rhs_bytes,
+              ctx->ops->rhs_df(ctx->u, ctx->mom, ctx->c, ctx->g0, a1, tl, (float *)ctx->b, ctx->s));
     else
-      AC_RUN(AC_PROF_SETUP, ctx->ops->rhs(ctx->u, ctx->mom, ctx->c, ctx->g0, a1, tl, ctx->b, ctx->s));
+      AC_RUNB(AC_PROF_SETUP, rhs_bytes, ctx->ops->rhs(ctx->u, ctx->mom, ctx->c, ctx->g0, a1, tl, ctx->b, ctx->s));
     ctx->have_rhs = true;
     int cycles = 0, outer = 0;
     double rho = 0;
@@ -1039,6 +1122,7 @@ int ac_set_phase(ac_ctx *ctx, const double *u, int is_device) {
   AC_CUDA(cudaMemcpyAsync(ctx->u, u, (size_t)ctx->n * ctx->N * sizeof(double),
                           is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->s));
   AC_CUDA(cudaMemsetAsync(ctx->c, 0, (size_t)3 * ctx->N * sizeof(double), ctx->s));
+  ctx->delta_warm = false;  // a new state: the next step's correction starts from zero
   if (!is_device) AC_CUDA(cudaStreamSynchronize(ctx->s));
   return AC_OK;
 }
@@ -1167,6 +1251,7 @@ int ac_set_profiling_mask(ac_ctx *ctx, unsigned class_mask) {
   for (int k = 0; k < AC_PROF_COUNT; ++k) {
     ctx->prof_ms[k] = 0;
     ctx->prof_launches[k] = 0;
+    ctx->prof_bytes[k] = 0;
   }
   ctx->prof_corr_launches = 0;
   class_mask &= (1u << AC_PROF_COUNT) - 1u;
@@ -1195,6 +1280,7 @@ int ac_get_profile(ac_ctx *ctx, ac_profile *out) {
   for (int k = 0; k < AC_PROF_COUNT; ++k) {
     out->ms[k] = ctx->prof_ms[k];
     out->launches[k] = ctx->prof_launches[k];
+    out->bytes[k] = ctx->prof_bytes[k];
   }
   out->smooth_bytes_per_launch = ctx->p.precision == AC_MIXED ? 2.0 * (double)ctx->n * ctx->N * sizeof(float)
                                                                : 1.5 * (double)ctx->n * ctx->N * sizeof(double);
@@ -1276,6 +1362,7 @@ int adj_setup(ac_ctx *ctx, int T, int every) {
   ADJ_ALLOC(A.kpart, (size_t)ac::kMaxPartBlocks * 2 * sizeof(double));
   if (ctx->r > 0) ADJ_ALLOC(A.gimg, (size_t)ctx->g0.W * ctx->g0.H * 3 * sizeof(double));
   ADJ_ALLOC(A.ktot, 2 * sizeof(double));
+  ADJ_ALLOC(A.ndiff, sizeof(unsigned long long));
   Solve &S = A.sv;
   S.o = &ctx->ops->adjoint;
   S.lv = ctx->sv.lv;
@@ -1296,6 +1383,17 @@ int adj_setup(ac_ctx *ctx, int T, int every) {
   ADJ_ALLOC(S.mask, (size_t)ctx->n);
   AC_CUDA(cudaMemsetAsync(S.rt, 0, fN, ctx->s));  // second-colour slots stay 0 (see solve_mg)
   return AC_OK;
+}
+
+// Components where a and b differ (bit patterns compared: a recomputation
+// either repeats the forward's arithmetic exactly or it does not).
+__global__ void k_count_diff(const double *__restrict__ a, const double *__restrict__ b, int64_t count,
+                             unsigned long long *out) {
+  unsigned long long k = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    k += __double_as_longlong(a[i]) != __double_as_longlong(b[i]);
+  k = ac::warp_sum<unsigned long long>(k);
+  if ((threadIdx.x & 31) == 0 && k) atomicAdd(out, k);
 }
 
 }  // namespace
@@ -1380,6 +1478,9 @@ int ac_adjoint_forward(ac_ctx *ctx, int n_steps, int checkpoint_every) {
       const int j = t / checkpoint_every;
       AC_CUDA(cudaMemcpyAsync(A.cp_u + (size_t)j * ctx->n * ctx->N, ctx->u, fN, cudaMemcpyDeviceToDevice, ctx->s));
       AC_CUDA(cudaMemcpyAsync(A.cp_c + (size_t)j * ctx->N * 3, ctx->c, cN, cudaMemcpyDeviceToDevice, ctx->s));
+      // each segment starts its first correction from zero (AC_MIXED), as its
+      // recomputation from this checkpoint in ac_adjoint_backward will
+      ctx->delta_warm = false;
     }
     rc = ac_step(ctx, 1, nullptr);
     if (rc == AC_ERR_NOT_CONVERGED)
@@ -1405,14 +1506,18 @@ int ac_adjoint_backward(ac_ctx *ctx, const double *grad_u, double *grad_lambda, 
   AC_CUDA(cudaMemcpyAsync(A.g, grad_u, fN, cudaMemcpyDeviceToDevice, ctx->s));
   AC_CUDA(cudaMemsetAsync(A.gm, 0, (size_t)ctx->n * 4 * sizeof(double), ctx->s));
   AC_CUDA(cudaMemsetAsync(A.scal, 0, 2 * sizeof(double), ctx->s));
+  AC_CUDA(cudaMemsetAsync(A.ndiff, 0, sizeof(unsigned long long), ctx->s));
   int status = AC_OK;
   for (int j = A.ncp - 1; j >= 0; --j) {
     const int t0 = j * A.every, t1 = std::min(t0 + A.every, A.T), len = t1 - t0;
-    // recompute the segment's states from its checkpoint (deterministic: the
-    // same arithmetic as the forward)
+    // recompute the segment's states from its checkpoint with the forward's
+    // arithmetic: like the forward, the segment's first step starts its
+    // correction from zero (AC_MIXED), and the later ones from the previous
+    // step's, which the recomputation has just produced
     AC_CUDA(cudaMemcpyAsync(ctx->u, A.cp_u + (size_t)j * nN, fN, cudaMemcpyDeviceToDevice, ctx->s));
     AC_CUDA(cudaMemcpyAsync(ctx->c, A.cp_c + (size_t)j * N * 3, cN, cudaMemcpyDeviceToDevice, ctx->s));
     AC_CUDA(cudaMemcpyAsync(A.seg_u, ctx->u, fN, cudaMemcpyDeviceToDevice, ctx->s));
+    ctx->delta_warm = false;
     for (int k = 0; k < len; ++k) {
       int rc = ac_step(ctx, 1, nullptr);
       if (rc && rc != AC_ERR_NOT_CONVERGED) return rc;
@@ -1421,6 +1526,10 @@ int ac_adjoint_backward(ac_ctx *ctx, const double *grad_u, double *grad_lambda, 
       AC_CUDA(cudaMemcpyAsync(A.seg_M + (size_t)k * N, ctx->tot, N * sizeof(double), cudaMemcpyDeviceToDevice,
                               ctx->s));
     }
+    // the segment's end against the forward's own state there
+    const double *fwd_end = j + 1 < A.ncp ? A.cp_u + (size_t)(j + 1) * nN : A.uT;
+    AC_RUN(AC_PROF_SETUP, (k_count_diff<<<(unsigned)std::min<int64_t>((nN + 255) / 256, 4 * 152), 256, 0, ctx->s>>>(
+                               A.seg_u + (size_t)len * nN, fwd_end, nN, A.ndiff), 1));
     for (int k = len - 1; k >= 0; --k) {
       const double *u = A.seg_u + (size_t)k * nN, *up = A.seg_u + (size_t)(k + 1) * nN;
       const double *c = A.seg_c + (size_t)k * N * 3, *M = A.seg_M + (size_t)k * N;
@@ -1466,12 +1575,24 @@ int ac_adjoint_backward(ac_ctx *ctx, const double *grad_u, double *grad_lambda, 
     AC_RUN(AC_PROF_SETUP, o->adj_image(A.gm, ctx->img64, ctx->g0, grad_image, ctx->s));
   }
   AC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 2, A.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+  AC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 1, A.ndiff, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->s));
   AC_CUDA(cudaMemcpyAsync(ctx->u, A.uT, fN, cudaMemcpyDeviceToDevice, ctx->s));  // leave u = u^T
   AC_CUDA(cudaStreamSynchronize(ctx->s));
   *grad_lambda = std::ldexp(ctx->h_scalars[2], -ctx->r);
   *grad_eps = std::ldexp(ctx->h_scalars[3], ctx->r);
+  {
+    unsigned long long nd = 0;
+    std::memcpy(&nd, ctx->h_scalars + 1, sizeof nd);
+    A.recompute_diff = (int64_t)nd;
+  }
   if (status) fail(status, "an adjoint solve did not reach its tolerance");
   return status;
+}
+
+int ac_adjoint_recompute_diff(ac_ctx *ctx, int64_t *count) {
+  if (!ctx || !count) return fail(AC_ERR_ARG, "NULL argument");
+  *count = ctx->adj.recompute_diff;
+  return AC_OK;
 }
 
 }  // extern "C"
@@ -1506,6 +1627,7 @@ void set_schedule(ac_ctx *ctx, int nu1, int nu2, int depth) {
   ctx->p.nu2 = nu2;
   const int L = (int)ctx->sv.lv.size();
   ctx->sv.depth = depth < 1 ? 1 : (depth > L ? L : depth);
+  ctx->delta_warm = false;  // the next step starts its correction from zero
 }
 
 }  // namespace
@@ -1651,25 +1773,37 @@ int ac_batch_tune(ac_batch *b, int trial_steps, int *chosen) {
   for (auto &kv : groups) {
     ac_ctx *c = b->ctx[kv.second.front()];
     const int L = (int)c->sv.lv.size();
+    // the state a trial starts from and is restored to: u and the colour
+    // means of the last step (the empty-phase fallback)
     void *snap = nullptr;
-    const size_t bytes = (size_t)c->n * c->N * sizeof(double);
-    AC_CUDA(cudaMalloc(&snap, bytes));
-    AC_CUDA(cudaMemcpyAsync(snap, c->u, bytes, cudaMemcpyDeviceToDevice, c->s));
+    const size_t bytes = (size_t)c->n * c->N * sizeof(double), cbytes = (size_t)3 * c->N * sizeof(double);
+    double c_snap[3 * AC_MAX_PHASES];
+    cudaError_t e = cudaMalloc(&snap, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AC_ERR_NOMEM, "cudaMalloc(%zu) for the tuning snapshot: %s", bytes, cudaGetErrorString(e));
+    }
+    auto restore = [&]() -> int {
+      int r = ac_set_phase(c, (const double *)snap, 1);
+      if (r) return r;
+      cudaError_t e2 = cudaMemcpyAsync(c->c, c_snap, cbytes, cudaMemcpyHostToDevice, c->s);
+      if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(c->s);
+      return e2 == cudaSuccess ? AC_OK : fail(AC_ERR_CUDA, "restoring the tuning snapshot: %s", cudaGetErrorString(e2));
+    };
+    int rc = AC_OK;
+    e = cudaMemcpyAsync(snap, c->u, bytes, cudaMemcpyDeviceToDevice, c->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c_snap, c->c, cbytes, cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) rc = fail(AC_ERR_CUDA, "tuning snapshot: %s", cudaGetErrorString(e));
     double best_t = 1e300;
     int best[3] = {c->p.nu1, c->p.nu2, L};
-    int rc = AC_OK;
     for (int nu = 0; nu < 4 && !rc; ++nu)
       for (int dd = 0; dd < 2 && !rc; ++dd) {
         const int depth = dd == 0 ? L : (L < 5 ? L : 5);
         if (dd == 1 && depth == L) continue;
         set_schedule(c, nus[nu][0], nus[nu][1], depth);
-        rc = ac_set_phase(c, (const double *)snap, 1);
+        rc = restore();
         if (rc) break;
-        cudaError_t e = cudaStreamSynchronize(c->s);
-        if (e != cudaSuccess) {
-          rc = fail(AC_ERR_CUDA, "%s", cudaGetErrorString(e));
-          break;
-        }
         ac_stats st{};
         auto t0 = std::chrono::steady_clock::now();
         int r = ac_step(c, trial_steps, &st);
@@ -1685,7 +1819,7 @@ int ac_batch_tune(ac_batch *b, int trial_steps, int *chosen) {
           best[2] = depth;
         }
       }
-    int rc2 = rc ? rc : ac_set_phase(c, (const double *)snap, 1);
+    int rc2 = rc ? rc : restore();
     cudaStreamSynchronize(c->s);
     cudaFree(snap);
     if (rc2) return rc2;

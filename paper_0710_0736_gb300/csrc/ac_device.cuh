@@ -219,7 +219,9 @@ __device__ __forceinline__ void proj_box(T (&z)[N], const T (&ob)[N]) {
         const T lo = SH ? -ob[i] : T(0);
         if (((keep >> i) & 1u) && z[i] - theta <= lo) drop |= 1u << i;
       }
-      if (!drop) break;
+      // in exact arithmetic some kept component stays above its bound; if
+      // rounding drops them all, keep the last set and its theta
+      if (!drop || drop == keep) break;
       keep &= ~drop;
       s = T(0);
       T L = T(0);
