@@ -6,7 +6,7 @@ lives in ``ac_oracle.c`` (plain sequential FP64 C); this module compiles it
 with gcc and marshals numpy arrays through ctypes.
 
 Every function follows a passage of Kay & Tomasi: the P1 matrices (Sec. 3.1),
-projection by simplex (Sec. 4.2), colour means and fitting terms (Eq.
+projection by simplex and by node (Sec. 4.2), colour means and fitting terms (Eq.
 VV_fidelity, Sec. 4.4), the step problem (Sec. 3.2, Eq. alpha), the Gibbs
 clamp-and-redistribute loop (Sec. 3.3), SSC over all levels (Sec. 3.2) and the
 rounded composite (Sec. 4.3).
@@ -50,6 +50,7 @@ def lib():
         i, i64, d = C.c_int, C.c_int64, C.c_double
         L.or_assemble.argtypes = [i, i, _dp, _ip, _dp, _ip]
         L.or_moments.argtypes = [i, i, _dp, _dp]
+        L.or_moments_node.argtypes = [i, i, _dp, _dp]
         L.or_means.argtypes = [i, i, i, _dp, _dp, C.c_void_p, _dp, C.c_void_p]
         L.or_rhs.argtypes = [i, i, i, _dp, _dp, _dp, d, d, d, _dp]
         L.or_energy.argtypes = [i, i, i, _dp, _dp, d, d]
@@ -64,7 +65,7 @@ def lib():
         L.or_pgs_solve.argtypes = [i, i, i, _dp, _dp, d, d, d, i, ip, dpp]
         L.or_step.argtypes = [i, i, i, _dp, _dp, _dp, d, d, d, d, i, i, i, i, i, ip, dpp]
         L.or_labels.argtypes = [i, i, i, _dp, _bp, _bp]
-        L.or_adjoint.argtypes = [i, i, i, _dp, _dp, i, d, d, d, _dp, dpp, dpp, _dp, C.c_void_p, d]
+        L.or_adjoint.argtypes = [i, i, i, _dp, _dp, i, d, d, d, _dp, dpp, dpp, _dp, C.c_void_p, d, i]
         _lib = L
     return _lib
 
@@ -90,11 +91,23 @@ def assemble(W: int, H: int):
     return mhat, col, val, cnt
 
 
-def moments(img: np.ndarray) -> np.ndarray:
-    """Projection by simplex: (n, 5) array of m0, m1 (RGB), m2 per node."""
+PROJECTIONS = {"simplex": 0, "node": 1}
+
+
+def moments(img: np.ndarray, projection: str = "simplex") -> np.ndarray:
+    """Per-node image moments (n, 5): m0, m1 (RGB), m2 (Sec. 4.2).
+    projection="simplex": exact integrals of the pixelwise-constant image
+    against each hat function, triangle by triangle; "node": one image value
+    per node (the pixel whose lower-left corner the node is, clamped to the
+    last column and row) and the consistent mass matrix, m1 = M I, m2 = M |I|^2."""
     H, W, _ = img.shape
     m = np.zeros((n_nodes(W, H), 5))
-    lib().or_moments(W, H, _f64(img), m)
+    if projection == "node":
+        lib().or_moments_node(W, H, _f64(img), m)
+    elif projection == "simplex":
+        lib().or_moments(W, H, _f64(img), m)
+    else:
+        raise ValueError(projection)
     return m
 
 
@@ -229,10 +242,11 @@ def refined_params(eps, lam, tau, r):
     return eps * 2.0 ** r, lam * 2.0 ** -r, tau * 2.0 ** r
 
 
-def run(img, u0, eps, lam, tau, steps, tol=1e-13, method="ssc", **kw):
-    """T steps from u0 on img. Returns (u_T, c_last, per-step stats list)."""
+def run(img, u0, eps, lam, tau, steps, tol=1e-13, method="ssc", projection="simplex", **kw):
+    """T steps from u0 on img (data projection by simplex or by node, Sec.
+    4.2). Returns (u_T, c_last, per-step stats list)."""
     H, W, _ = img.shape
-    m = moments(img)
+    m = moments(img, projection)
     u = _f64(u0)
     c = np.zeros((u.shape[1], 3))
     stats = []
@@ -242,10 +256,10 @@ def run(img, u0, eps, lam, tau, steps, tol=1e-13, method="ssc", **kw):
     return u, c, stats
 
 
-def forward_states(img, u0, eps, lam, tau, steps, tol=1e-15, **kw):
+def forward_states(img, u0, eps, lam, tau, steps, tol=1e-15, projection="simplex", **kw):
     """u^0..u^T of the oracle's time stepping (list of (n, N) arrays)."""
     H, W, _ = img.shape
-    m = moments(img)
+    m = moments(img, projection)
     u = _f64(u0)
     c = np.zeros((u.shape[1], 3))
     states = [u.copy()]
@@ -255,7 +269,7 @@ def forward_states(img, u0, eps, lam, tau, steps, tol=1e-15, **kw):
     return states
 
 
-def adjoint(img, states, eps, lam, tau, gT, cg_rtol=1e-13):
+def adjoint(img, states, eps, lam, tau, gT, cg_rtol=1e-13, projection="simplex"):
     """Gradients of a loss on u^T (gT = dL/du^T) through the steps that
     produced `states`: returns (dL/dlambda, dL/deps with tau fixed,
     dL/dI (H, W, 3), dL/du^0 (n, N)).  Each step's tangent system is solved
@@ -269,7 +283,7 @@ def adjoint(img, states, eps, lam, tau, gT, cg_rtol=1e-13):
     g_u0 = np.zeros_like(st[0])
     gl, ge = C.c_double(0), C.c_double(0)
     if lib().or_adjoint(W, H, N, _f64(img), st, T, eps, lam, tau, _f64(gT), C.byref(gl), C.byref(ge), g_img,
-                        g_u0.ctypes.data, cg_rtol):
+                        g_u0.ctypes.data, cg_rtol, PROJECTIONS[projection]):
         raise ValueError("or_adjoint failed")
     return gl.value, ge.value, g_img, g_u0
 

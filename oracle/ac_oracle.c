@@ -180,6 +180,56 @@ int or_moments(int W, int H, const double *img, double *m) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Data projection by node (Sec. 4.2)                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Projection by node takes one image value I_n per node and the standard
+ * (consistent) mass matrix M_nm = <eta_n, eta_m>: the fitting term of phase i
+ * at node n is sum_m M_nm |I_m - c_i|^2 and c_i = (M I . u_i) / (M 1 . u_i),
+ * i.e. the moments of the P1 interpolant I_h = sum_m I_m eta_m:
+ *     m0_n = sum_m M_nm, m1_n = sum_m M_nm I_m, m2_n = sum_m M_nm |I_m|^2.
+ * The nodes sit at pixel corners, where a pixelwise-constant image has no
+ * value; following the paper's rule for nodes without data (each takes the
+ * value of a neighbour, never an interpolated one), node (x, y) takes the
+ * value of pixel (min(x, W-1), min(y, H-1)), the pixel whose lower-left
+ * corner it is (the last column and row of nodes take the last pixels). */
+static const double *node_value(int W, int H, const double *img, int x, int y) {
+  int px = x < W ? x : W - 1, py = y < H ? y : H - 1;
+  return img + ((int64_t)py * W + px) * 3;
+}
+
+/* M assembled triangle by triangle: on a triangle of area |t| the P1 basis
+ * functions give <eta_a, eta_b>_t = |t| (1 + delta_ab) / 12. */
+int or_moments_node(int W, int H, const double *img, double *m) {
+  int64_t n = (int64_t)(W + 1) * (H + 1);
+  memset(m, 0, n * 5 * sizeof(double));
+  for (int py = 0; py < H; ++py)
+    for (int px = 0; px < W; ++px) {
+      int tri[2][3][2];
+      pixel_triangles(px, py, tri);
+      for (int t = 0; t < 2; ++t)
+        for (int a = 0; a < 3; ++a) {
+          double *ma = m + nid(W, tri[t][a][0], tri[t][a][1]) * 5;
+          for (int b = 0; b < 3; ++b) {
+            const double *I = node_value(W, H, img, tri[t][b][0], tri[t][b][1]);
+            double w = 0.5 * (a == b ? 2.0 : 1.0) / 12.0;
+            ma[0] += w;
+            ma[1] += w * I[0];
+            ma[2] += w * I[1];
+            ma[3] += w * I[2];
+            ma[4] += w * (I[0] * I[0] + I[1] * I[1] + I[2] * I[2]);
+          }
+        }
+    }
+  return 0;
+}
+
+/* The moments of either projection: 0 by simplex, 1 by node. */
+static int moments_of(int W, int H, const double *img, int projection, double *m) {
+  return projection == 1 ? or_moments_node(W, H, img, m) : or_moments(W, H, img, m);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Colour means, fitting term, right-hand side, energy (Sec. 2.3, 4.4)       */
 /* ------------------------------------------------------------------------ */
 
@@ -632,7 +682,8 @@ static int tangent_cg(const or_mesh *m, double te, int N, const double *up, cons
  * same parameters; gT = dL/du^T.  Outputs dL/dlambda, dL/deps (tau fixed),
  * dL/dI (H x W x 3) and dL/du^0 (n x N, nullable). */
 int or_adjoint(int W, int H, int N, const double *img, const double *states, int T, double eps, double lam, double tau,
-               const double *gT, double *g_lam, double *g_eps, double *g_img, double *g_u0, double cg_rtol) {
+               const double *gT, double *g_lam, double *g_eps, double *g_img, double *g_u0, double cg_rtol,
+               int projection) {
   or_mesh mesh;
   if (N < 2 || N > OR_MAXN || T < 0 || mesh_build(&mesh, W, H)) return -1;
   const int64_t n = mesh.n, nn = n * N;
@@ -641,7 +692,7 @@ int or_adjoint(int W, int H, int N, const double *img, const double *states, int
   double *g = malloc(nn * sizeof(double)), *gn = malloc(nn * sizeof(double)), *w = malloc(nn * sizeof(double));
   double *gm = calloc(n * 4, sizeof(double)); /* dL/dm1 (3), dL/dm2 */
   if (!m || !c || !g || !gn || !w || !gm) return -1;
-  or_moments(W, H, img, m);
+  moments_of(W, H, img, projection, m);
   /* the means the forward used at each step (empty phases keep the previous) */
   double cprev[OR_MAXN * 3] = {0};
   for (int t = 0; t < T; ++t) {
@@ -690,14 +741,27 @@ int or_adjoint(int W, int H, int N, const double *img, const double *states, int
   memset(g_img, 0, (size_t)W * H * 3 * sizeof(double));
   for (int py = 0; py < H; ++py)
     for (int px = 0; px < W; ++px) {
-      const double *I = img + ((int64_t)py * W + px) * 3;
-      double *gI = g_img + ((int64_t)py * W + px) * 3;
       int tri[2][3][2];
       pixel_triangles(px, py, tri);
       for (int tt = 0; tt < 2; ++tt)
         for (int a = 0; a < 3; ++a) {
           const double *gk = gm + nid(W, tri[tt][a][0], tri[tt][a][1]) * 4;
-          for (int ch = 0; ch < 3; ++ch) gI[ch] += (0.5 / 3.0) * (gk[ch] + 2.0 * I[ch] * gk[3]);
+          if (projection == 1) {
+            /* m_a gathers w_ab (I_b, |I_b|^2) from the triangle's nodes b,
+             * each carrying the value of the pixel it copies */
+            for (int b = 0; b < 3; ++b) {
+              int bx = tri[tt][b][0], by = tri[tt][b][1];
+              int sx = bx < W ? bx : W - 1, sy = by < H ? by : H - 1;
+              const double *I = img + ((int64_t)sy * W + sx) * 3;
+              double *gI = g_img + ((int64_t)sy * W + sx) * 3;
+              double w = 0.5 * (a == b ? 2.0 : 1.0) / 12.0;
+              for (int ch = 0; ch < 3; ++ch) gI[ch] += w * (gk[ch] + 2.0 * I[ch] * gk[3]);
+            }
+          } else {
+            const double *I = img + ((int64_t)py * W + px) * 3;
+            double *gI = g_img + ((int64_t)py * W + px) * 3;
+            for (int ch = 0; ch < 3; ++ch) gI[ch] += (0.5 / 3.0) * (gk[ch] + 2.0 * I[ch] * gk[3]);
+          }
         }
     }
   *g_lam = glam;

@@ -16,18 +16,21 @@ def _problem(oracle_mod, seed=0, W=10, H=8, N=3, T=3):
     return img, u0, target, m0
 
 
-def _loss(oracle_mod, img, u0, target, m0, eps, lam, tau, T):
-    uT = oracle_mod.forward_states(img, u0, eps, lam, tau, T)[-1]
+def _loss(oracle_mod, img, u0, target, m0, eps, lam, tau, T, projection="simplex"):
+    uT = oracle_mod.forward_states(img, u0, eps, lam, tau, T, projection=projection)[-1]
     return oracle_mod.misfit_loss(uT, m0, target)[0]
 
 
-@pytest.mark.parametrize("seed", [0, 1])
-def test_adjoint_matches_finite_differences(oracle_mod, seed):
+@pytest.mark.parametrize("seed,projection", [(0, "simplex"), (1, "simplex"), (2, "node")])
+def test_adjoint_matches_finite_differences(oracle_mod, seed, projection):
+    """Data projection by simplex or by node (Sec. 4.2): the image enters
+    through the moments, whose adjoint differs between the two."""
     eps, lam, tau, T = 2.0, 1.0, 4.0, 3
     img, u0, target, m0 = _problem(oracle_mod, seed)
-    states = oracle_mod.forward_states(img, u0, eps, lam, tau, T)
+    states = oracle_mod.forward_states(img, u0, eps, lam, tau, T, projection=projection)
     L, gT = oracle_mod.misfit_loss(states[-1], m0, target)
-    g_lam, g_eps, g_img, g_u0 = oracle_mod.adjoint(img, states, eps, lam, tau, gT)
+    g_lam, g_eps, g_img, g_u0 = oracle_mod.adjoint(img, states, eps, lam, tau, gT, projection=projection)
+    P = projection
     h = 1e-6
 
     def fd(f):
@@ -36,8 +39,8 @@ def test_adjoint_matches_finite_differences(oracle_mod, seed):
     def close(a, b):
         return abs(a - b) <= 1e-5 * max(abs(b), 1e-3 * abs(L))
 
-    assert close(g_lam, fd(lambda d: _loss(oracle_mod, img, u0, target, m0, eps, lam + d, tau, T)))
-    assert close(g_eps, fd(lambda d: _loss(oracle_mod, img, u0, target, m0, eps + d, lam, tau, T)))
+    assert close(g_lam, fd(lambda d: _loss(oracle_mod, img, u0, target, m0, eps, lam + d, tau, T, P)))
+    assert close(g_eps, fd(lambda d: _loss(oracle_mod, img, u0, target, m0, eps + d, lam, tau, T, P)))
     rng = np.random.default_rng(seed)
     for _ in range(6):
         py, px, ch = rng.integers(0, img.shape[0]), rng.integers(0, img.shape[1]), rng.integers(0, 3)
@@ -45,11 +48,11 @@ def test_adjoint_matches_finite_differences(oracle_mod, seed):
         def f(d, py=py, px=px, ch=ch):
             im = img.copy()
             im[py, px, ch] += d
-            return _loss(oracle_mod, im, u0, target, m0, eps, lam, tau, T)
+            return _loss(oracle_mod, im, u0, target, m0, eps, lam, tau, T, P)
         assert close(g_img[py, px, ch], fd(f))
     for _ in range(2):  # a random direction in image space and one in u0 (sum zero per node)
         v = rng.normal(size=img.shape)
-        assert close((g_img * v).sum(), fd(lambda d: _loss(oracle_mod, img + d * v, u0, target, m0, eps, lam, tau, T)))
+        assert close((g_img * v).sum(), fd(lambda d: _loss(oracle_mod, img + d * v, u0, target, m0, eps, lam, tau, T, P)))
         z = rng.normal(size=u0.shape)
         z -= z.mean(1, keepdims=True)
-        assert close((g_u0 * z).sum(), fd(lambda d: _loss(oracle_mod, img, u0 + d * z, target, m0, eps, lam, tau, T)))
+        assert close((g_u0 * z).sum(), fd(lambda d: _loss(oracle_mod, img, u0 + d * z, target, m0, eps, lam, tau, T, P)))

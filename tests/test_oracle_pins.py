@@ -524,3 +524,114 @@ def test_refined_exact_segmentation_of_stripes(oracle_mod, seed):
     assert np.array_equal(pl, truth) or np.array_equal(pl, 1 - truth)
     uc, _, _ = oracle_mod.run(img, u0, 2.0, 1.0, 4.0, 30, tol=1e-12)
     assert np.abs(u.reshape(2 * H + 1, 2 * W + 1, 2)[::2, ::2] - uc.reshape(H + 1, W + 1, 2)).max() < 0.1
+
+
+# --------------------------------------------------------------------------
+# Data projection by node (Sec. 4.2): one image value per node, the
+# consistent mass matrix
+# --------------------------------------------------------------------------
+
+def test_golden_node_moments_2x1(oracle_mod):
+    img = np.zeros((1, 2, 3))
+    img[0, 0] = (1.0, 2.0, 0.0)
+    img[0, 1] = (4.0, 8.0, 2.0)
+    m = oracle_mod.moments(img, "node")
+    rows = _read_rows("node_moments_2x1.txt")
+    assert len(rows) == 6
+    for x, y, *vals in rows:
+        n = int(y) * 3 + int(x)
+        for k, v in enumerate(vals):
+            assert m[n, k] == pytest.approx(int(v) / 24.0, abs=1e-14)
+
+
+def test_node_moments_of_a_constant_image(oracle_mod):
+    """The consistent mass matrix's rows sum to <eta_n, 1>: a constant image
+    gives m1 = m0 I and m2 = m0 |I|^2, with the lumped mass as m0."""
+    W, H = 7, 5
+    img = np.empty((H, W, 3))
+    img[:] = (0.2, 0.7, 0.4)
+    m = oracle_mod.moments(img, "node")
+    mhat, _, _, _ = oracle_mod.assemble(W, H)
+    assert np.abs(m[:, 0] - mhat).max() < 1e-15
+    assert np.abs(m[:, 1:4] - m[:, :1] * img[0, 0]).max() < 1e-15
+    assert np.abs(m[:, 4] - m[:, 0] * (img[0, 0] ** 2).sum()).max() < 1e-15
+
+
+def _node_values(img):
+    """The copy rule: node (x, y) takes pixel (min(x, W-1), min(y, H-1))."""
+    H, W, _ = img.shape
+    ys = np.minimum(np.arange(H + 1), H - 1)
+    xs = np.minimum(np.arange(W + 1), W - 1)
+    return img[ys][:, xs]
+
+
+def test_node_moments_integrate_the_interpolant(oracle_mod):
+    """sum_n m1_n = sum_n (M I)_n = int I_h, the integral of the P1
+    interpolant of the nodal values: on each triangle (area 1/2) the mean of
+    its three vertex values; likewise sum_n m2_n for |I|^2."""
+    W, H = 9, 6
+    img = synth.shapes_image(4, W, H, rect_side=(1, 4), disk_r=(1, 3), sigma=0.1).astype(np.float64)
+    m = oracle_mod.moments(img, "node")
+    V = _node_values(img)
+    V2 = (V ** 2).sum(axis=2)
+    lo = (V[:-1, :-1] + V[:-1, 1:] + V[1:, 1:]) / 3.0      # (px,py), (px+1,py), (px+1,py+1)
+    up = (V[:-1, :-1] + V[1:, :-1] + V[1:, 1:]) / 3.0      # (px,py), (px,py+1), (px+1,py+1)
+    lo2 = (V2[:-1, :-1] + V2[:-1, 1:] + V2[1:, 1:]) / 3.0
+    up2 = (V2[:-1, :-1] + V2[1:, :-1] + V2[1:, 1:]) / 3.0
+    assert np.abs(m[:, 1:4].sum(0) - 0.5 * (lo + up).sum(axis=(0, 1))).max() < 1e-12
+    assert abs(m[:, 4].sum() - 0.5 * (lo2 + up2).sum()) < 1e-12
+
+
+def test_node_moments_of_a_linear_field(oracle_mod):
+    """Pixel values linear in the pixel index give nodal values linear in
+    (x, y) away from the last column and row; an interior node's hat function
+    is point-symmetric, so its m1 is its own value (m0 = 1) exactly."""
+    W, H = 8, 7
+    py, px = np.mgrid[0:H, 0:W]
+    img = np.stack([0.1 + 0.03 * px + 0.05 * py, 0.9 - 0.02 * px, 0.4 + 0.07 * py], axis=2)
+    m = oracle_mod.moments(img, "node").reshape(H + 1, W + 1, 5)
+    V = _node_values(img)
+    inner = (slice(1, H - 1), slice(1, W - 1))
+    assert np.abs(m[inner][..., 0] - 1.0).max() < 1e-15
+    assert np.abs(m[inner][..., 1:4] - V[inner]).max() < 1e-14
+
+
+def test_node_and_simplex_projections_converge_under_refinement(oracle_mod):
+    """The paper notes that the errors of both projections decrease with
+    every mesh refinement: on the pixel grid refined r times by copy, the two
+    projections differ only in the cells along pixel edges, a band whose area
+    halves with each r: the relative error of the by-node integral of I
+    (against the exact one, sum_n m1 of the projection by simplex) halves, and the
+    node-by-node difference of m1 shrinks towards the same rate."""
+    W, H = 6, 5
+    img = synth.shapes_image(9, W, H, rect_side=(1, 3), disk_r=(1, 2), sigma=0.2).astype(np.float64)
+    total, nodewise = [], []
+    for r in range(5):
+        fine = oracle_mod.refine_image(img, r)
+        a, b = oracle_mod.moments(fine, "node"), oracle_mod.moments(fine, "simplex")
+        total.append(np.abs(a[:, 1:4].sum(0) - b[:, 1:4].sum(0)).sum() / np.abs(b[:, 1:4].sum(0)).sum())
+        nodewise.append(np.abs(a[:, 1:4] - b[:, 1:4]).sum() / np.abs(b[:, 1:4]).sum())
+    for e0, e1 in zip(total, total[1:]):
+        assert 0.45 * e0 < e1 < 0.55 * e0
+    for e0, e1 in zip(nodewise, nodewise[1:]):
+        assert e1 < 0.8 * e0
+    assert 0.45 * nodewise[-2] < nodewise[-1] < 0.55 * nodewise[-2]
+
+
+def test_node_projection_step_kkt_and_fixed_point(oracle_mod):
+    """A step with the by-node fitting terms: SSC and plain projected
+    Gauss-Seidel reach the same minimiser, and it satisfies the KKT
+    conditions of the step problem (Sec. 3.2) to 1e-12."""
+    W, H, N = 12, 10, 3
+    img = synth.shapes_image(5, W, H, rect_side=(2, 6), disk_r=(1, 3), sigma=0.05).astype(np.float64)
+    u0 = synth.dirichlet_init(6, (W + 1) * (H + 1), N)
+    m = oracle_mod.moments(img, "node")
+    c, _ = oracle_mod.means(u0, m, W, H)
+    b = oracle_mod.rhs(u0, m, c, W, H, 2.0, 1.0, 4.0)
+    u1, _, rho1, st1 = oracle_mod.ssc_solve(u0, b, W, H, 2.0, 4.0, tol=1e-14, nu1=2, nu2=2)
+    u2, _, rho2, st2 = oracle_mod.pgs_solve(u0, b, W, H, 2.0, 4.0, tol=1e-14)
+    assert st1 == 0 and st2 == 0
+    assert np.abs(u1 - u2).max() < 1e-11
+    mhat, A = BF.assemble_dense(W, H)
+    spread, below = BF.kkt_violation(np.diag(mhat) + 4.0 * 2.0 * A, b, u1)
+    assert spread < 1e-12 and below < 1e-12
