@@ -50,6 +50,9 @@ def parse():
                     help="steps of the plain FP64 form timed for the vs-FP64 ratio (default: --steps, the same "
                          "steps as the mixed form; 0: skip)")
     ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--projection", choices=["simplex", "node"], default="simplex",
+                    help="data projection of the image (Sec. 4.2): exact moments by simplex, or nodal values with "
+                         "the consistent mass matrix")
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--nu1", type=int, default=2, help="pre-smoothing red-black sweeps per V-cycle")
     ap.add_argument("--nu2", type=int, default=1, help="post-smoothing red-black sweeps per V-cycle")
@@ -96,6 +99,7 @@ def workload_config(cfg, args, extra=None):
         "nodes": (cfg["W"] + 1) * (cfg["H"] + 1),
         "n_phases": cfg["N"],
         "precision": args.precision,
+        "projection": args.projection,
         "tol": cfg["tol"],
         "l2": "no flush: the phase field and right-hand side (1.07 GB each in FP64) exceed the 129 MB L2",
     }
@@ -601,8 +605,9 @@ def main():
     prec = ac.AC_FP64 if args.precision == "fp64" else ac.AC_MIXED
     img = synth.config_image(WORKLOAD, rank, W, H)
     stream = torch.cuda.current_stream()
+    proj = ac.AC_PROJ_NODE if args.projection == "node" else ac.AC_PROJ_SIMPLEX
     seg = ac.Segmenter(W, H, N, cfg["eps"], cfg["lam"], cfg["tau"], tol=cfg["tol"], max_cycles=1000, seed=rank,
-                       precision=prec, stream=stream.cuda_stream, nu1=args.nu1, nu2=args.nu2)
+                       precision=prec, stream=stream.cuda_stream, nu1=args.nu1, nu2=args.nu2, projection=proj)
     dev_img = torch.from_numpy(img).cuda()
     seg.set_image(dev_img)
     seg.step(args.warmup, allow_not_converged=True)
@@ -681,7 +686,8 @@ def main():
     if args.precision == "mixed" and args.fp64_steps > 0:
         seg.close()
         seg64 = ac.Segmenter(W, H, N, cfg["eps"], cfg["lam"], cfg["tau"], tol=cfg["tol"], max_cycles=1000, seed=rank,
-                             precision=ac.AC_FP64, stream=stream.cuda_stream, nu1=args.nu1, nu2=args.nu2)
+                             precision=ac.AC_FP64, stream=stream.cuda_stream, nu1=args.nu1, nu2=args.nu2,
+                             projection=proj)
         seg64.set_image(dev_img)
         seg64.step(args.warmup, allow_not_converged=True)
         seg64.set_image(dev_img)  # the same time steps from the seeded start as the mixed form

@@ -55,6 +55,16 @@ enum {
 
 enum { AC_FP64 = 0, AC_MIXED = 1 };
 
+/* Data projection of the image onto the finite-element space (Sec. 4.2). */
+enum {
+  AC_PROJ_SIMPLEX = 0, /* "projection by simplex": the exact integrals of the pixelwise-constant image
+                          against every hat function, m1_n = <eta_n, I>, m2_n = <eta_n, |I|^2> */
+  AC_PROJ_NODE = 1     /* "projection by node": one image value I_n per node and the standard (consistent)
+                          mass matrix M_nm = <eta_n, eta_m>, m1 = M I, m2 = M |I|^2.  Nodes sit at pixel
+                          corners; node (x, y) takes the value of pixel (min(x, W-1), min(y, H-1)) (the
+                          paper's rule for nodes without data: copy a neighbour's value, never interpolate) */
+};
+
 #define AC_MAX_PHASES 8
 
 typedef struct ac_ctx ac_ctx;
@@ -86,6 +96,8 @@ typedef struct {
                           4^r).  Images come in and pixel labels, composites and image gradients go out at
                           W x H; phase fields, node labels and moments are on the refined grid
                           ((2^r W + 1)(2^r H + 1) nodes); energies are in pixel units. */
+  int projection;      /* AC_PROJ_SIMPLEX (default) or AC_PROJ_NODE: how the image enters the fitting terms
+                          and the colour means (on the refined grid when refine > 0) */
   void *stream;        /* cudaStream_t for all work of this context */
 } ac_params;
 
@@ -141,9 +153,11 @@ int ac_default_params(ac_params *p);
 int ac_create(ac_ctx **out, const ac_params *p);
 
 /* Copy an RGB image in (H x W x 3 float32, values in [0,1]), compute the
- * per-node image moments m0 = <eta_n,1>, m1 = <eta_n,I>, m2 = <eta_n,|I|^2>
- * ("projection by simplex", Sec. 4.2; exact for a pixelwise-constant image)
- * and reset u to a seeded random point of the simplex at every node. */
+ * per-node image moments of params.projection (Sec. 4.2): by simplex m0 =
+ * <eta_n,1>, m1 = <eta_n,I>, m2 = <eta_n,|I|^2> (exact for a
+ * pixelwise-constant image); by node m1 = M I, m2 = M |I|^2 with nodal
+ * values I_n and the consistent mass matrix M (m0 = <eta_n,1> either way)
+ * -- and reset u to a seeded random point of the simplex at every node. */
 int ac_set_image(ac_ctx *ctx, const float *rgb, int is_device);
 /* The same with an FP64 image (used for parity with the FP64 oracle). */
 int ac_set_image_f64(ac_ctx *ctx, const double *rgb, int is_device);

@@ -16,6 +16,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 
 AC_OK, AC_ERR_ARG, AC_ERR_CUDA, AC_ERR_NOT_CONVERGED, AC_ERR_NUMERIC, AC_ERR_STATE, AC_ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
 AC_FP64, AC_MIXED = 0, 1
+AC_PROJ_SIMPLEX, AC_PROJ_NODE = 0, 1
 AC_MAX_PHASES = 8
 
 EXPORTS = [
@@ -33,7 +34,8 @@ class ac_params(C.Structure):
     _fields_ = [("width", C.c_int), ("height", C.c_int), ("n_phases", C.c_int),
                 ("eps", C.c_double), ("lambda_", C.c_double), ("tau", C.c_double), ("tol", C.c_double),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("max_cycles", C.c_int), ("coarse_min", C.c_int),
-                ("precision", C.c_int), ("seed", C.c_uint64), ("refine", C.c_int), ("stream", C.c_void_p)]
+                ("precision", C.c_int), ("seed", C.c_uint64), ("refine", C.c_int), ("projection", C.c_int),
+                ("stream", C.c_void_p)]
 
 
 class ac_stats(C.Structure):
@@ -430,7 +432,8 @@ class Batch:
         self.specs = [dict(s) for s in specs]
         plist = []
         for sp in self.specs:
-            kw = {k: sp[k] for k in ("tol", "precision", "seed", "nu1", "nu2", "coarse_min", "max_cycles") if k in sp}
+            kw = {k: sp[k] for k in ("tol", "precision", "seed", "nu1", "nu2", "coarse_min", "max_cycles", "projection")
+                  if k in sp}
             plist.append(ac_default_params(width=sp["W"], height=sp["H"], n_phases=sp["N"], eps=sp.get("eps", 2.0),
                                            tau=sp.get("tau", 4.0), stream=None, **{"lambda": sp.get("lam", 1.0)},
                                            **kw))

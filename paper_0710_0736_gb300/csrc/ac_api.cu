@@ -310,6 +310,8 @@ int validate(const ac_params *p) {
   if (p->coarse_min < 1) return fail(AC_ERR_ARG, "coarse_min must be >= 1");
   if (p->precision != AC_FP64 && p->precision != AC_MIXED)
     return fail(AC_ERR_ARG, "precision must be AC_FP64 or AC_MIXED");
+  if (p->projection != AC_PROJ_SIMPLEX && p->projection != AC_PROJ_NODE)
+    return fail(AC_ERR_ARG, "projection must be AC_PROJ_SIMPLEX or AC_PROJ_NODE");
   return AC_OK;
 }
 
@@ -806,6 +808,99 @@ __global__ void k_moments_bf16(const __nv_bfloat16 *__restrict__ img, ac::Geo g,
   m[3] = s2 / 6.0;
 }
 
+// ---- data projection by node (Sec. 4.2) ------------------------------------
+// One image value per node, I_n = pixel (min(x, W-1), min(y, H-1)) (a copy of
+// a neighbouring pixel, never an interpolated value), and the standard mass
+// matrix M_nm = <eta_n, eta_m>.  On the right-diagonal triangulation a
+// triangle of area 1/2 contributes (1 + delta_ab)/24 to M_ab, so M is a
+// 7-point stencil: M_nn = (incident triangles)/12 = Mhat_n / 2, and an edge
+// to E, W, N, S, NE or SW carries (triangles sharing it)/24.  The axis edges
+// are shared by 2 vy (E, W) and 2 vx (N, S) triangles -- twice the stiffness
+// edge weights of edge_weights -- and a diagonal by the two triangles of its
+// pixel.
+
+__device__ __forceinline__ double img_value(float v) { return (double)v; }
+__device__ __forceinline__ double img_value(double v) { return v; }
+__device__ __forceinline__ double img_value(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+// The seven stencil entries of row (x, y) of M: self, E, W, N, S, NE, SW.
+struct MassRow {
+  double w[7];
+};
+__device__ __forceinline__ MassRow mass_row(const ac::Geo &g, int x, int y) {
+  const ac::Weights e = ac::edge_weights(g, x, y);
+  MassRow r;
+  r.w[0] = 0.5 * g.m0[ac::node_class(g, x, y)];
+  r.w[1] = (double)e.e / 12.0;
+  r.w[2] = (double)e.w / 12.0;
+  r.w[3] = (double)e.n / 12.0;
+  r.w[4] = (double)e.s / 12.0;
+  r.w[5] = (x < g.W && y < g.H) ? 1.0 / 12.0 : 0.0;
+  r.w[6] = (x > 0 && y > 0) ? 1.0 / 12.0 : 0.0;
+  return r;
+}
+__constant__ int kMassDx[7] = {0, 1, -1, 0, 0, 1, -1};
+__constant__ int kMassDy[7] = {0, 0, 0, 1, -1, 1, -1};
+
+// m1 = M I and m2 = M |I|^2 at every node (m0 = Mhat, the rows' sums, is
+// taken from the node class as for projection by simplex).
+template <typename TI>
+__global__ void k_moments_node(const TI *__restrict__ img, ac::Geo g, double *__restrict__ mom) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x > g.W || y > g.H) return;
+  const MassRow row = mass_row(g, x, y);
+  double s[3] = {0.0, 0.0, 0.0}, s2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    if (row.w[k] == 0.0) continue;  // no such neighbour (the weight of a missing edge is 0)
+    const int mx = x + kMassDx[k], my = y + kMassDy[k];
+    const int px = mx < g.W ? mx : g.W - 1, py = my < g.H ? my : g.H - 1;
+    const TI *p = img + ((int64_t)py * g.W + px) * 3;
+    const double r = img_value(p[0]), gg = img_value(p[1]), bb = img_value(p[2]);
+    s[0] += row.w[k] * r;
+    s[1] += row.w[k] * gg;
+    s[2] += row.w[k] * bb;
+    s2 += row.w[k] * (r * r + gg * gg + bb * bb);
+  }
+  double *m = mom + ((int64_t)y * g.Wn + x) * 4;
+  m[0] = s[0];
+  m[1] = s[1];
+  m[2] = s[2];
+  m[3] = s2;
+}
+
+// The adjoint of k_moments_node: pixel p collects, over the nodes n that copy
+// it, (M dL/dm1)_n + 2 I_p (M dL/dm2)_n (M is symmetric).  A pixel is copied
+// by node (px, py), and also by the nodes of column W (row H) when it is in
+// the last column (row).
+__global__ void k_adj_image_node(const double *__restrict__ gm, const double *__restrict__ img, ac::Geo g,
+                                 double *__restrict__ gimg) {
+  const int px = blockIdx.x * blockDim.x + threadIdx.x, py = blockIdx.y;
+  if (px >= g.W || py >= g.H) return;
+  const double *I = img + ((int64_t)py * g.W + px) * 3;
+  double out[3] = {0.0, 0.0, 0.0};
+  const int nx = px == g.W - 1 ? 2 : 1, ny = py == g.H - 1 ? 2 : 1;
+  for (int b = 0; b < ny; ++b)
+    for (int a = 0; a < nx; ++a) {
+      const int x = px + a, y = py + b;
+      const MassRow row = mass_row(g, x, y);
+      double t[4] = {0.0, 0.0, 0.0, 0.0};  // (M gm)_n for the four moment entries
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        if (row.w[k] == 0.0) continue;
+        const double *gk = gm + ((int64_t)(y + kMassDy[k]) * g.Wn + (x + kMassDx[k])) * 4;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) t[j] += row.w[k] * gk[j];
+      }
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) out[ch] += t[ch] + 2.0 * I[ch] * t[3];
+    }
+  double *o = gimg + ((int64_t)py * g.W + px) * 3;
+  o[0] = out[0];
+  o[1] = out[1];
+  o[2] = out[2];
+}
+
 }  // namespace
 
 extern "C" {
@@ -819,6 +914,7 @@ int ac_default_params(ac_params *p) {
   p->max_cycles = 200;
   p->coarse_min = 4;
   p->precision = AC_FP64;
+  p->projection = AC_PROJ_SIMPLEX;
   return AC_OK;
 }
 
@@ -1005,8 +1101,17 @@ static int set_image_impl(ac_ctx *ctx, const void *rgb, int is_device, bool f64)
     }
     AC_RUN(AC_PROF_SETUP, (k_to_bf16<<<(unsigned)((count + 255) / 256), 256, 0, ctx->s>>>(
                                (const float *)src, ctx->img16, count), 1));
-    AC_RUN(AC_PROF_SETUP, (k_moments_bf16<<<dim3((unsigned)((g.W + 256) / 256), (unsigned)(g.H + 1)), 256, 0,
-                                             ctx->s>>>(ctx->img16, g, ctx->mom), 1));
+  }
+  const dim3 mgrid((unsigned)((g.W + 256) / 256), (unsigned)(g.H + 1));
+  if (ctx->p.projection == AC_PROJ_NODE) {
+    if (mixed)
+      AC_RUN(AC_PROF_SETUP, (k_moments_node<__nv_bfloat16><<<mgrid, 256, 0, ctx->s>>>(ctx->img16, g, ctx->mom), 1));
+    else if (f64)
+      AC_RUN(AC_PROF_SETUP, (k_moments_node<double><<<mgrid, 256, 0, ctx->s>>>((const double *)src, g, ctx->mom), 1));
+    else
+      AC_RUN(AC_PROF_SETUP, (k_moments_node<float><<<mgrid, 256, 0, ctx->s>>>((const float *)src, g, ctx->mom), 1));
+  } else if (mixed) {
+    AC_RUN(AC_PROF_SETUP, (k_moments_bf16<<<mgrid, 256, 0, ctx->s>>>(ctx->img16, g, ctx->mom), 1));
   } else if (f64) {
     AC_RUN(AC_PROF_SETUP, ctx->ops->moments_f64((const double *)src, g, ctx->mom, ctx->s));
   } else {
@@ -1565,14 +1670,25 @@ int ac_adjoint_backward(ac_ctx *ctx, const double *grad_u, double *grad_lambda, 
     }
   }
   if (grad_u0) AC_CUDA(cudaMemcpyAsync(grad_u0, A.g, fN, cudaMemcpyDeviceToDevice, ctx->s));
+  // dL/dI through the moments of the context's projection (Sec. 4.2)
+  const dim3 igrid((unsigned)((ctx->g0.W + 255) / 256), (unsigned)ctx->g0.H);
+  auto image_grad = [&](double *out) -> int {
+    if (ctx->p.projection == AC_PROJ_NODE)
+      AC_RUN(AC_PROF_SETUP, (k_adj_image_node<<<igrid, 256, 0, ctx->s>>>(A.gm, ctx->img64, ctx->g0, out), 1));
+    else
+      AC_RUN(AC_PROF_SETUP, o->adj_image(A.gm, ctx->img64, ctx->g0, out, ctx->s));
+    return AC_OK;
+  };
   if (ctx->r > 0) {
     // refined grid: the cells' gradients, then their sums over each pixel
     // (the adjoint of the copy); lambda' = 2^-r lambda, eps' = 2^r eps
-    AC_RUN(AC_PROF_SETUP, o->adj_image(A.gm, ctx->img64, ctx->g0, A.gimg, ctx->s));
+    int rc = image_grad(A.gimg);
+    if (rc) return rc;
     AC_RUN(AC_PROF_SETUP, (k_refine_sum<<<dim3((unsigned)((ctx->W0 + 255) / 256), (unsigned)ctx->H0), 256, 0, ctx->s>>>(
                                A.gimg, ctx->W0, ctx->H0, ctx->r, ctx->g0, grad_image), 1));
   } else {
-    AC_RUN(AC_PROF_SETUP, o->adj_image(A.gm, ctx->img64, ctx->g0, grad_image, ctx->s));
+    int rc = image_grad(grad_image);
+    if (rc) return rc;
   }
   AC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 2, A.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
   AC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 1, A.ndiff, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->s));

@@ -656,6 +656,115 @@ def test_mixed_ragged(ac, W, H, N):
 
 
 # --------------------------------------------------------------------------
+# data projection by node (Sec. 4.2)
+# --------------------------------------------------------------------------
+
+def test_node_projection_moments(ac):
+    """The by-node moments (nodal image values by the copy rule, consistent
+    mass matrix) against the oracle: the hand-derived 2x1 case, a 64x64
+    image through the float and FP64 inputs, a 1-pixel-wide image, and the
+    mixed form's bfloat16 image."""
+    def close(a, b):
+        return (np.abs(a - b) <= 2e-15 * np.maximum(1.0, np.abs(b))).all()
+
+    img = np.zeros((1, 2, 3))
+    img[0, 0] = (1.0, 2.0, 0.0)
+    img[0, 1] = (4.0, 8.0, 2.0)
+    seg = _seg(ac, 2, 1, 2, projection=ac.AC_PROJ_NODE)
+    seg.set_image(img)
+    assert close(seg.moments(), oracle.moments(img, "node"))
+    for (W, H) in [(64, 64), (1, 7), (37, 23)]:
+        img = synth.shapes_image(W + 3 * H, W, H, rect_side=(1, max(1, W // 2)), disk_r=(1, max(1.5, W / 4)))
+        ref = oracle.moments(img.astype(np.float64), "node")
+        for im in (img, img.astype(np.float64)):
+            seg = _seg(ac, W, H, 3, projection=ac.AC_PROJ_NODE)
+            seg.set_image(im)
+            assert close(seg.moments(), ref)
+        segm = _mixed(ac, W, H, 3, 1e-6, projection=ac.AC_PROJ_NODE)
+        segm.set_image(img)
+        assert close(segm.moments(), oracle.moments(synth.round_bf16(img).astype(np.float64), "node"))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("W,H,N,steps", [(64, 64, 4, 20), (96, 64, 5, 3), (256, 256, 8, 1)])
+def test_node_projection_steps(ac, precision, W, H, N, steps):
+    """Time steps with the by-node fitting terms against the oracle's:
+    phase fields to 1e-10 (FP64, both solved to 3e-15) or 1e-7 (mixed at tol
+    1e-12, against the oracle on the bfloat16-rounded image), labels bit-exact
+    from the GPU's own field and equal to the oracle's except at near-ties.
+    256^2 runs the tiled coarse kernels."""
+    img = synth.shapes_image(W * 3 + N, W, H, rect_side=(4, W // 3), disk_r=(3, W / 6))
+    u0 = synth.dirichlet_init(W + N, (W + 1) * (H + 1), N)
+    if precision == "fp64":
+        seg = _seg(ac, W, H, N, projection=ac.AC_PROJ_NODE)
+        seg.set_image(img.astype(np.float64))
+        img_used, bound = img.astype(np.float64), 1e-10
+    else:
+        seg = _mixed(ac, W, H, N, 1e-12, max_cycles=3000, projection=ac.AC_PROJ_NODE)
+        seg.set_image(img)
+        img_used, bound = synth.round_bf16(img).astype(np.float64), 1e-7
+    seg.set_phase(u0)
+    st = seg.step(steps)
+    assert st.converged
+    u_ref, c_ref, _ = oracle.run(img_used, u0, 2.0, 1.0, 4.0, steps, tol=TIGHT, nu1=2, nu2=2, projection="node")
+    u = seg.phase()
+    assert np.abs(u - u_ref).max() < bound
+    assert np.abs(seg.means() - c_ref).max() < 10 * bound
+    _check_labels(seg, u, u_ref, W, H, margin=max(1e-8, 10 * bound))
+    seg.close()
+
+
+def test_node_projection_refined(ac):
+    """Projection by node on the pixel grid refined once (Sec. 4.1): the
+    nodes of the refined grid copy the cells, which copy the pixels."""
+    W0, H0, N, r = 24, 16, 4, 1
+    s_ = 1 << r
+    img = synth.shapes_image(71, W0, H0, rect_side=(3, 10), disk_r=(2, 6)).astype(np.float64)
+    u0 = synth.dirichlet_init(72, (W0 * s_ + 1) * (H0 * s_ + 1), N)
+    seg = _seg(ac, W0, H0, N, refine=r, projection=ac.AC_PROJ_NODE)
+    seg.set_image(img)
+    seg.set_phase(u0)
+    seg.step(3)
+    fine = oracle.refine_image(img, r)
+    assert np.abs(seg.moments() - oracle.moments(fine, "node")).max() < 1e-14
+    e2, l2, t2 = oracle.refined_params(2.0, 1.0, 4.0, r)
+    u_ref, _, _ = oracle.run(fine, u0, e2, l2, t2, 3, tol=TIGHT, projection="node")
+    assert np.abs(seg.phase() - u_ref).max() < 1e-10
+    seg.close()
+
+
+@pytest.mark.parametrize("r", [0, 1])
+def test_node_projection_adjoint(ac, r):
+    """Gradients through T steps with the by-node fitting terms against the
+    FP64 oracle adjoint of the same projection: 1e-6 relative (the image
+    gradient goes through the copy rule and the consistent mass matrix)."""
+    import torch
+    W0, H0, N, T, every = (20, 14, 3, 5, 2) if r == 0 else (12, 8, 3, 4, 2)
+    s_ = 1 << r
+    img = synth.shapes_image(81 + r, W0, H0, rect_side=(2, 6), disk_r=(1.5, 4), sigma=0.08).astype(np.float64)
+    u0 = synth.dirichlet_init(82, (W0 * s_ + 1) * (H0 * s_ + 1), N)
+    target = synth.voronoi_labels(83, W0 * s_ + 1, H0 * s_ + 1, n_seeds=4, n_labels=N)
+    seg = _seg(ac, W0, H0, N, tol=1e-14, refine=r, projection=ac.AC_PROJ_NODE)
+    seg.set_image(img)
+    seg.set_phase(u0)
+    ac.ac_adjoint_forward(seg.ctx, T, every)
+    uT = seg.phase()
+    fine = oracle.refine_image(img, r)
+    m0 = oracle.moments(fine)[:, 0]
+    _, gT = oracle.misfit_loss(uT, m0, target)
+    g_img = torch.zeros((H0, W0, 3), dtype=torch.float64, device="cuda")
+    gl, ge = ac.ac_adjoint_backward(seg.ctx, torch.tensor(gT, device="cuda"), g_img)
+    seg.close()
+    e2, l2, t2 = oracle.refined_params(2.0, 1.0, 4.0, r)
+    states = oracle.forward_states(fine, u0, e2, l2, t2, T, projection="node")
+    rl, re_, rimg, _ = oracle.adjoint(fine, states, e2, l2, t2, gT, projection="node")
+    assert gl == pytest.approx(rl * 2.0 ** -r, rel=1e-6)
+    assert ge == pytest.approx(re_ * 2.0 ** r, rel=1e-6)
+    rimg0 = rimg.reshape(H0, s_, W0, s_, 3).sum(axis=(1, 3))
+    assert np.abs(g_img.cpu().numpy() - rimg0).max() <= 1e-6 * np.abs(rimg0).max()
+
+
+# --------------------------------------------------------------------------
 # a12: batches of uneven images
 # --------------------------------------------------------------------------
 
