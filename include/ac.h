@@ -217,6 +217,25 @@ int ac_residual(ac_ctx *ctx, double *rho);
  * (device, count x N) may alias y.  Ordered on stream. */
 int ac_project_simplex(const double *y, double *x, int64_t count, int n_phases, void *stream);
 
+/* ---- coarse-level tiling (no counterpart in the paper) -------------------- */
+
+/* How the coarse corrections treat their first levels.  Dense: every row of
+ * every level is visited, the rows of phases with no free fine node under
+ * them (exact zeros) at little cost.  Tiled: the large levels are split into
+ * 32 x 16-node tiles per phase; a Galerkin kernel marks the tiles with a
+ * nonzero row (live) and lists them, and the level's other kernels work on
+ * the listed tiles only (tiles that stay dead hold exact zeros and are not
+ * visited).  Both forms compute the same numbers; the tiled one pays when
+ * few tiles are live, i.e. once the phases have separated.
+ *   AC_TILES_AUTO (default): tiled for levels with at least 32 (tile, phase)
+ *     pairs per multiprocessor, chosen per V-cycle when fewer than a quarter
+ *     of the fine nodes have a free phase;
+ *   AC_TILES_NEVER: dense always;
+ *   AC_TILES_ALWAYS: tiled on every coarse level above the coarsest and the
+ *     one-launch tail, whatever its size (a check of the tiled kernels). */
+enum { AC_TILES_AUTO = 0, AC_TILES_NEVER = 1, AC_TILES_ALWAYS = 2 };
+int ac_set_coarse_tiling(ac_ctx *ctx, int mode);
+
 /* ---- instrumentation (no counterpart in the paper) ------------------------ */
 
 /* Turn per-class kernel timing on (1) or off (0) and clear the accumulated

@@ -17,6 +17,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 AC_OK, AC_ERR_ARG, AC_ERR_CUDA, AC_ERR_NOT_CONVERGED, AC_ERR_NUMERIC, AC_ERR_STATE, AC_ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
 AC_FP64, AC_MIXED = 0, 1
 AC_PROJ_SIMPLEX, AC_PROJ_NODE = 0, 1
+AC_TILES_AUTO, AC_TILES_NEVER, AC_TILES_ALWAYS = 0, 1, 2
 AC_MAX_PHASES = 8
 
 EXPORTS = [
@@ -25,7 +26,7 @@ EXPORTS = [
     "ac_get_composite", "ac_energy", "ac_residual", "ac_project_simplex", "ac_set_profiling", "ac_set_profiling_mask", "ac_get_profile", "ac_colour_means_static",
     "ac_batch_create", "ac_batch_set_image", "ac_batch_set_phase", "ac_batch_get_phase", "ac_batch_segment",
     "ac_batch_step", "ac_batch_tune", "ac_batch_destroy", "ac_adjoint_forward", "ac_adjoint_backward",
-    "ac_adjoint_recompute_diff", "ac_last_error",
+    "ac_adjoint_recompute_diff", "ac_set_coarse_tiling", "ac_last_error",
 ]
 PROF_CLASSES = ["smooth", "resid", "coarse", "transfer", "linesearch", "setup", "outer"]
 
@@ -116,6 +117,7 @@ def _load():
         "ac_adjoint_forward": ([vp, i, i], i),
         "ac_adjoint_backward": ([vp, vp, P(d), P(d), vp, vp], i),
         "ac_adjoint_recompute_diff": ([vp, P(i64)], i),
+        "ac_set_coarse_tiling": ([vp, i], i),
         "ac_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -343,6 +345,11 @@ def ac_adjoint_recompute_diff(ctx) -> int:
     k = C.c_int64()
     _check(lib.ac_adjoint_recompute_diff(ctx, C.byref(k)))
     return k.value
+
+
+def ac_set_coarse_tiling(ctx, mode):
+    """AC_TILES_AUTO, AC_TILES_NEVER or AC_TILES_ALWAYS (see include/ac.h)."""
+    return _check(lib.ac_set_coarse_tiling(ctx, mode))
 
 
 def ac_last_error() -> str:

@@ -101,7 +101,12 @@ struct Level {
   ac::Geo g;
   int64_t n = 0;
   void *op = nullptr, *r = nullptr, *v = nullptr, *t = nullptr;  // coarse levels only
+  ac::LevelLists lists{};  // live-tile flags and work lists (coarse levels; used while the level is tiled)
 };
+
+// Bytes of a level's live flags: one per (kJ2X x kJ2Y tile, phase).
+size_t tile_flag_bytes(const ac::Geo &g, int N) { return (size_t)ac::tiles_x(g) * ac::tiles_y(g) * N; }
+
 
 // Untruncated entries of P'SP on the first coarse level, one representative
 // coarse node per boundary class.
@@ -143,15 +148,28 @@ struct GraphSlot {
 // constraint set of the instantiation (see ac_kernels.cuh).
 struct Solve {
   const ac::SolverOps *o = nullptr;
+  int *list_counts = nullptr;  // the tiled levels' list counts, two per level (cleared by one memset per cycle)
   void *x = nullptr, *rhs = nullptr, *ob = nullptr, *rt = nullptr, *d = nullptr;
   uint8_t *mask = nullptr;
   std::vector<Level> lv;  // lv[0]: fine level geometry
   int depth = 0;          // levels in use (<= lv.size()); a schedule can cut the hierarchy short
   ac::Galerkin0Table tab0{};
   // graphs [profiling][variant]: smoothing + residual of the first / a later
-  // cycle, and the coarse correction with its line search
-  GraphSlot smooth_resid[2][2], correction[2];
+  // cycle, and the coarse correction with its line search [profiling][form:
+  // dense levels / tiled levels with live flags and work lists]
+  GraphSlot smooth_resid[2][2], correction[2][2];
+  // the form of the next coarse correction: tiled while few fine nodes are
+  // free (its kernels then skip the dead tiles), dense otherwise (when most
+  // tiles are live the work lists cost more than they skip); was_tiled: the
+  // last correction ran tiled, so the flags describe its tiles
+  bool tiled = false, was_tiled = false;
+  int tiling = AC_TILES_AUTO;  // ac_set_coarse_tiling
 };
+
+// A coarse correction runs tiled when fewer than this fraction of the fine
+// nodes have a free phase (about 45% of the first level's tiles are then
+// live at 4096^2, N = 8, where both forms take the same time).
+constexpr double kTiledFreeFraction = 0.25;
 
 // Pre/post l1-Jacobi sweeps on coarse levels (even); a build option
 // (-DAC_COARSE_SWEEPS=k) for tuning.
@@ -211,6 +229,7 @@ struct ac_ctx {
   int8_t *lab = nullptr;  // device staging of labels for host copies (nodes of the solve grid)
   int N = 0;
   int64_t n = 0;
+  int sms = 1;  // multiprocessors of the device
   const ac::Ops *ops = nullptr;
   cudaStream_t s = nullptr;
   ac::Geo g0{};
@@ -456,13 +475,19 @@ int run_graph(ac_ctx *ctx, GraphSlot &slot, F &&enqueue) {
     if (rc_) return rc_;                                                \
   } while (0)
 
-// Reads rho back (the one device-to-host dependency of a cycle).  While
-// profiling, the finished event pairs are summed here: the graphs re-record
-// their events on every replay.
-int read_rho(ac_ctx *ctx, double *out) {
-  AC_CUDA(cudaMemcpyAsync(ctx->h_scalars, ctx->rho, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+// Reads rho back (the one device-to-host dependency of a cycle), and the
+// count of free nodes that the fine residual stores beside it (*nfree,
+// nullable).  While profiling, the finished event pairs are summed here: the
+// graphs re-record their events on every replay.
+int read_rho(ac_ctx *ctx, double *out, int64_t *nfree = nullptr) {
+  AC_CUDA(cudaMemcpyAsync(ctx->h_scalars, ctx->rho, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
   AC_CUDA(cudaStreamSynchronize(ctx->s));
   *out = ctx->h_scalars[0];
+  if (nfree) {
+    unsigned long long c = 0;
+    std::memcpy(&c, ctx->h_scalars + 1, sizeof c);
+    *nfree = (int64_t)c;
+  }
   if (ctx->profiling) return prof_harvest(ctx);
   return AC_OK;
 }
@@ -490,9 +515,35 @@ int tail_level(const Solve &S, size_t *smem) {
   return k0;
 }
 
+// The coarse levels worked tile by tile with live flags and work lists (see
+// kLiveNow): levels above the one-launch tail and above the coarsest that
+// have at least kTiledMinItems (tile, phase) items per multiprocessor (on
+// smaller levels the lists' bookkeeping costs more than the dead tiles
+// they skip).  They form a prefix 1 .. k1 - 1 of the hierarchy; the others
+// stay dense.
+constexpr int64_t kTiledMinItems = 32;
+int tiled_end(const Solve &S) {
+  size_t smem = 0;
+  const int k0 = tail_level(S, &smem);
+  int k1 = k0 < S.depth - 1 ? k0 : S.depth - 1;
+  if (S.tiling == AC_TILES_NEVER) return 1;
+  if (S.tiling == AC_TILES_ALWAYS) return k1;
+  for (int k = 1; k < k1; ++k)
+    if (S.lv[k].lists.cap < kTiledMinItems * S.lv[k].lists.sms) {
+      k1 = k;
+      break;
+    }
+  return k1;
+}
+
+const ac::LevelLists *level_lists(Solve &S, int k) {
+  return (S.tiled && k >= 1 && k < tiled_end(S)) ? &S.lv[k].lists : nullptr;
+}
+
 int coarse_vcycle(ac_ctx *ctx, Solve &S, int k, void **res) {
   Level &L = S.lv[k];
   const ac::SolverOps *o = S.o;
+  const ac::LevelLists *const tf = level_lists(S, k), *const tfc = level_lists(S, k + 1);
   // level arrays: the operator is 4 values (C, E, N, NE) per node and phase,
   // r, v, t one; pair = one fused pair of l1-Jacobi sweeps from v (7 values:
   // operator, r and v read, the result written), from zero 6
@@ -520,7 +571,7 @@ int coarse_vcycle(ac_ctx *ctx, Solve &S, int k, void **res) {
       *res = L.v;
     } else {
       AC_RUNB(AC_PROF_COARSE, pair0 + (kCoarseSweeps - 1) * pair,
-              o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, 2 * kCoarseSweeps, true, res, ctx->s));
+              o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, 2 * kCoarseSweeps, true, res, nullptr, ctx->s));
     }
     return AC_OK;
   }
@@ -532,24 +583,24 @@ int coarse_vcycle(ac_ctx *ctx, Solve &S, int k, void **res) {
     // float: one launch reads the operator and r and writes v and t; double:
     // the pair, then the residual (operator, r, v read, t written)
     AC_RUNB(AC_PROF_COARSE, o->elem == 4 ? 7 * lk : pair0 + 7 * lk,
-            o->coarse_pre_resid(L.op, L.r, L.v, L.t, L.g, ctx->s));
+            o->coarse_pre_resid(L.op, L.r, L.v, L.t, L.g, tf, ctx->s));
     v = L.v;
     other = L.t;
   } else {
     AC_RUNB(AC_PROF_COARSE, pair0 + (kCoarseSweeps / 2 - 1) * pair,
-            o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, true, &v, ctx->s));
+            o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, true, &v, tf, ctx->s));
     other = v == L.v ? L.t : L.v;
-    AC_RUNB(AC_PROF_COARSE, 7 * lk, o->coarse_resid(L.op, L.r, v, L.g, other, ctx->s));
+    AC_RUNB(AC_PROF_COARSE, 7 * lk, o->coarse_resid(L.op, L.r, v, L.g, other, tf, ctx->s));
   }
   // restriction: t read, the coarse diagonal read, r written
-  AC_RUNB(AC_PROF_TRANSFER, lk + 2 * lc, o->restrict_(other, L.g, C.g, C.op, C.r, ctx->s));
+  AC_RUNB(AC_PROF_TRANSFER, lk + 2 * lc, o->restrict_(other, L.g, C.g, C.op, C.r, tfc, ctx->s));
   void *cv = nullptr;
   int rc = coarse_vcycle(ctx, S, k + 1, &cv);
   if (rc) return rc;
   // prolongation: coarse v and this level's diagonal read, v read and written
-  AC_RUNB(AC_PROF_TRANSFER, lc + 3 * lk, o->prolong_add(cv, L.g, C.g, L.op, v, ctx->s));
+  AC_RUNB(AC_PROF_TRANSFER, lc + 3 * lk, o->prolong_add(cv, L.g, C.g, L.op, v, tf, ctx->s));
   AC_RUNB(AC_PROF_COARSE, (kCoarseSweeps / 2) * pair,
-          o->coarse_smooth(L.op, L.r, v, other, L.g, kCoarseSweeps, false, res, ctx->s));
+          o->coarse_smooth(L.op, L.r, v, other, L.g, kCoarseSweeps, false, res, tf, ctx->s));
   return AC_OK;
 }
 
@@ -591,7 +642,7 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
                               (fused ? 0.5 * bm.n * (1.0 + (rt_zero ? bm.ns : 0.0)) : 0.0);
       AC_RUNB(AC_PROF_SMOOTH, sm_bytes, o->smooth(S.x, S.rhs, S.ob, corr, ctx->omega, g0, nsw, rt_zero,
                                                   fused ? S.mask : nullptr, ctx->s));
-      AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
+      AC_CUDA(cudaMemsetAsync(ctx->rho, 0, 2 * sizeof(double), ctx->s));  // rho and the free-node count
       // residual at the visited nodes: x (their own and, for one colour, the
       // other colour's as neighbours), rhs, obstacle read, rt and the mask
       // byte written
@@ -604,7 +655,8 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
     if (ctx->profiling && corr && nsw > 0) ++ctx->prof_corr_launches;
     sweeps += nsw;
     ++cyc;
-    rc = read_rho(ctx, &rho);
+    int64_t nfree = 0;
+    rc = read_rho(ctx, &rho, &nfree);
     if (rc) return rc;
     if (std::isnan(rho) || std::isinf(rho)) {
       status = fail(AC_ERR_NUMERIC, "non-finite residual");
@@ -616,17 +668,32 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
     }
     if (cyc >= max_cycles) break;
     if (!coarse) continue;
-    rc = run_graph(ctx, S.correction[prof], [&]() -> int {
+    // the coarse correction's form from the free nodes (only one colour is
+    // counted after a smoothing sequence: about half of them)
+    const double free_frac = (double)nfree * (nsw >= 1 ? 2.0 : 1.0) / (double)S.lv[0].n;
+    S.tiled = tiled_end(S) > 1 && (S.tiling == AC_TILES_ALWAYS || free_frac < kTiledFreeFraction);
+    if (S.tiled && !S.was_tiled) {
+      // the flags are stale: let this correction write every tile (kLiveNow)
+      for (int k = 1; k < tiled_end(S); ++k)
+        AC_CUDA(cudaMemsetAsync(S.lv[k].lists.flags, ac::kLiveNow, tile_flag_bytes(S.lv[k].g, ctx->N), ctx->s));
+    }
+    S.was_tiled = S.tiled;
+    rc = run_graph(ctx, S.correction[prof][S.tiled ? 1 : 0], [&]() -> int {
       Level &L1 = S.lv[1];
       const double l1 = (double)L1.n * bm.ns;
       // first-level operator from the fine mask; each coarser one from the
       // level above (4 values per node and phase read and written)
-      AC_RUNB(AC_PROF_TRANSFER, bm.n + 4 * l1, o->galerkin0(S.mask, g0, L1.g, S.tab0, L1.op, ctx->s));
+      // the tiled levels' work lists are rebuilt by their Galerkin kernels
+      if (tiled_end(S) > 1) AC_CUDA(cudaMemsetAsync(S.list_counts, 0, 2 * S.lv.size() * sizeof(int), ctx->s));
+      AC_RUNB(AC_PROF_TRANSFER, bm.n + 4 * l1,
+              o->galerkin0(S.mask, g0, L1.g, S.tab0, L1.op, level_lists(S, 1), ctx->s));
       for (int k = 1; k + 1 < S.depth; ++k)
         AC_RUNB(AC_PROF_TRANSFER, 4.0 * (double)(S.lv[k].n + S.lv[k + 1].n) * bm.ns,
-                o->galerkin(S.lv[k].op, S.lv[k].g, S.lv[k + 1].g, S.lv[k + 1].op, ctx->s));
+                o->galerkin(S.lv[k].op, S.lv[k].g, S.lv[k + 1].g, S.lv[k + 1].op, level_lists(S, k),
+                            level_lists(S, k + 1), ctx->s));
       // rt read, the first level's diagonal read and its r written
-      AC_RUNB(AC_PROF_TRANSFER, bm.n * bm.ns + 2 * l1, o->restrict0(S.rt, g0, L1.g, L1.op, L1.r, ctx->s));
+      AC_RUNB(AC_PROF_TRANSFER, bm.n * bm.ns + 2 * l1,
+              o->restrict0(S.rt, g0, L1.g, L1.op, L1.r, level_lists(S, 1), ctx->s));
       void *v1 = nullptr;
       int rc2 = coarse_vcycle(ctx, S, 1, &v1);
       if (rc2) return rc2;
@@ -943,6 +1010,14 @@ int ac_create(ac_ctx **out, const ac_params *p) {
   ctx->ops = ops_for(ctx->N);
   ctx->s = (cudaStream_t)p->stream;
   ctx->use_graphs = ctx->s != nullptr;  // the legacy default stream cannot be captured
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || ctx->sms < 1) {
+      cudaGetLastError();
+      ctx->sms = 1;
+    }
+  }
   const bool mixed = p->precision == AC_MIXED;
   const double te = p->tau * p->eps;
   Solve &S = ctx->sv;
@@ -989,16 +1064,25 @@ int ac_create(ac_ctx **out, const ac_params *p) {
     AC_ALLOC(ctx->c, (size_t)3 * N * sizeof(double));
     AC_ALLOC(ctx->c_tmp, (size_t)3 * N * sizeof(double));
     AC_ALLOC(ctx->energy, sizeof(double));
-    AC_ALLOC(ctx->rho, sizeof(double));
+    AC_ALLOC(ctx->rho, 2 * sizeof(double));  // rho and the free-node count of the fine residual
     AC_ALLOC(ctx->omega, 2 * sizeof(double));  // omega and its float rounding
     AC_ALLOC(ctx->ls_part, (size_t)2 * ls_blocks * sizeof(double));
     AC_ALLOC(ctx->ls_tot, 2 * sizeof(double));
+    AC_ALLOC(S.list_counts, 2 * S.lv.size() * sizeof(int));
     for (size_t k = 1; k < S.lv.size(); ++k) {
       Level &L = S.lv[k];
       AC_ALLOC(L.op, (size_t)L.n * 4 * N * es);
       AC_ALLOC(L.r, (size_t)L.n * N * es);
       AC_ALLOC(L.v, (size_t)L.n * N * es);
       AC_ALLOC(L.t, (size_t)L.n * N * es);
+      const size_t nt = (size_t)ac::tiles_x(L.g) * ac::tiles_y(L.g);
+      AC_ALLOC(L.lists.flags, nt * N);
+      AC_ALLOC(L.lists.items, nt * N * sizeof(uint64_t));
+      AC_ALLOC(L.lists.tiles, nt * sizeof(uint64_t));
+      L.lists.count = S.list_counts + 2 * k;
+      L.lists.cap = (int64_t)nt * N;
+      L.lists.sms = ctx->sms;
+      AC_CUDA(cudaMemsetAsync(L.lists.flags, ac::kLiveNow, nt * N, ctx->s));  // the first cycle writes all tiles
     }
     AC_CUDA(cudaMallocHost(&ctx->h_scalars, 4 * sizeof(double)));
     AC_CUDA(cudaMemsetAsync(ctx->c, 0, (size_t)3 * N * sizeof(double), ctx->s));
@@ -1026,7 +1110,7 @@ void ac_destroy(ac_ctx *ctx) {
   for (Solve *S : {&ctx->sv, &ctx->adj.sv})
     for (int a = 0; a < 2; ++a) {
       for (int b = 0; b < 2; ++b) slot_release(S->smooth_resid[a][b]);
-      slot_release(S->correction[a]);
+      for (int f = 0; f < 2; ++f) slot_release(S->correction[a][f]);
     }
   for (void *p : ctx->adj.allocs) cudaFree(p);
   if (ctx->img64) cudaFree(ctx->img64);
@@ -1367,9 +1451,23 @@ int ac_set_profiling_mask(ac_ctx *ctx, unsigned class_mask) {
     if (ctx->s) cudaStreamSynchronize(ctx->s);
     for (Solve *S : {&ctx->sv, &ctx->adj.sv}) {
       for (int b = 0; b < 2; ++b) slot_release(S->smooth_resid[1][b]);
-      slot_release(S->correction[1]);
+      for (int f = 0; f < 2; ++f) slot_release(S->correction[1][f]);
     }
     ctx->prof_graph_mask = ctx->prof_mask;
+  }
+  return AC_OK;
+}
+
+int ac_set_coarse_tiling(ac_ctx *ctx, int mode) {
+  if (!ctx) return fail(AC_ERR_ARG, "ctx is NULL");
+  if (mode != AC_TILES_AUTO && mode != AC_TILES_NEVER && mode != AC_TILES_ALWAYS)
+    return fail(AC_ERR_ARG, "mode must be AC_TILES_AUTO, AC_TILES_NEVER or AC_TILES_ALWAYS");
+  if (ctx->s) cudaStreamSynchronize(ctx->s);
+  for (Solve *S : {&ctx->sv, &ctx->adj.sv}) {
+    // the tiled correction graphs depend on which levels are tiled
+    for (int a = 0; a < 2; ++a) slot_release(S->correction[a][1]);
+    S->tiling = mode;
+    S->was_tiled = false;  // the next tiled correction writes every tile
   }
   return AC_OK;
 }
@@ -1429,7 +1527,7 @@ void adj_release(ac_ctx *ctx) {
   AdjState &A = ctx->adj;
   for (int a = 0; a < 2; ++a) {
     for (int b = 0; b < 2; ++b) slot_release(A.sv.smooth_resid[a][b]);
-    slot_release(A.sv.correction[a]);
+    for (int f = 0; f < 2; ++f) slot_release(A.sv.correction[a][f]);
   }
   for (void *p : A.allocs) cudaFree(p);
   A = AdjState{};
@@ -1471,15 +1569,25 @@ int adj_setup(ac_ctx *ctx, int T, int every) {
   Solve &S = A.sv;
   S.o = &ctx->ops->adjoint;
   S.lv = ctx->sv.lv;
+  ADJ_ALLOC(S.list_counts, 2 * S.lv.size() * sizeof(int));
   for (size_t k = 1; k < S.lv.size(); ++k) {
     Level &L = S.lv[k];
     ADJ_ALLOC(L.op, (size_t)L.n * 4 * N * sizeof(double));
     ADJ_ALLOC(L.r, (size_t)L.n * N * sizeof(double));
     ADJ_ALLOC(L.v, (size_t)L.n * N * sizeof(double));
     ADJ_ALLOC(L.t, (size_t)L.n * N * sizeof(double));
+    const size_t nt = (size_t)ac::tiles_x(L.g) * ac::tiles_y(L.g);
+    ADJ_ALLOC(L.lists.flags, nt * N);
+    ADJ_ALLOC(L.lists.items, nt * N * sizeof(uint64_t));
+    ADJ_ALLOC(L.lists.tiles, nt * sizeof(uint64_t));
+    L.lists.count = S.list_counts + 2 * k;
+    L.lists.cap = (int64_t)nt * N;
+    L.lists.sms = ctx->sms;
+    AC_CUDA(cudaMemsetAsync(L.lists.flags, ac::kLiveNow, nt * N, ctx->s));
   }
   S.depth = ctx->sv.depth;
   S.tab0 = ctx->sv.tab0;
+  S.tiling = ctx->sv.tiling;
   ADJ_ALLOC(S.x, fN);
   ADJ_ALLOC(S.rhs, fN);
   ADJ_ALLOC(S.ob, fN);
@@ -1737,13 +1845,18 @@ namespace {
 void set_schedule(ac_ctx *ctx, int nu1, int nu2, int depth) {
   for (int a = 0; a < 2; ++a) {
     for (int b = 0; b < 2; ++b) slot_release(ctx->sv.smooth_resid[a][b]);
-    slot_release(ctx->sv.correction[a]);
+    for (int f = 0; f < 2; ++f) slot_release(ctx->sv.correction[a][f]);
   }
   ctx->p.nu1 = nu1;
   ctx->p.nu2 = nu2;
   const int L = (int)ctx->sv.lv.size();
   ctx->sv.depth = depth < 1 ? 1 : (depth > L ? L : depth);
   ctx->delta_warm = false;  // the next step starts its correction from zero
+  ctx->sv.was_tiled = false;
+  // the tiled levels may change with the depth: let the next cycle write
+  // every tile of every level again (see kLiveNow)
+  for (int k = 1; k < L; ++k)
+    cudaMemsetAsync(ctx->sv.lv[k].lists.flags, ac::kLiveNow, tile_flag_bytes(ctx->sv.lv[k].g, ctx->N), ctx->s);
 }
 
 }  // namespace

@@ -32,6 +32,33 @@ struct Geo {
   float teh, tel, m0h[9], m0l[9];  // te and Mhat as double-floats h + l (the defect correction's residual)
 };
 
+// Tiles of the coarse levels: kJ2X x kJ2Y nodes of one phase plane, the unit
+// of the fused l1-Jacobi kernels and of the live flags below.
+constexpr int kJ2X = 32, kJ2Y = 16;
+
+// Live flags of the tiled coarse levels (the levels above the one-launch
+// coarse tail): one byte per (tile, phase), at tf[(i * tiles_y + ty) *
+// tiles_x + tx].  Bit kLiveNow: some row of phase i in the tile has a
+// nonzero diagonal in this cycle's truncated operator; bit kLivePrev: so it
+// had in the previous cycle.  The level's producers (Galerkin product,
+// restriction, l1-Jacobi pairs, residual, prolongation) work on live tiles
+// only, write zeros into a tile once, in the cycle it stops being live
+// (kLivePrev without kLiveNow), and skip it while it stays dead.  So every
+// array of a tiled level (operator, r, v, t) holds exact zeros on tiles that
+// are not live, which is what a dense level would hold there: readers of
+// halos and neighbours need no flags.  The producer derives kLivePrev from
+// the kLiveNow it finds, so a new, re-scheduled or newly tiled level starts
+// with kLiveNow set everywhere: its first cycle then writes every tile.
+constexpr uint8_t kLiveNow = 1, kLivePrev = 2;
+
+__host__ __device__ __forceinline__ int tiles_x(const Geo &g) { return (g.W + kJ2X) / kJ2X; }
+__host__ __device__ __forceinline__ int tiles_y(const Geo &g) { return (g.H + kJ2Y) / kJ2Y; }
+
+// The flag byte of the tile holding node (x, y), phase i.
+__device__ __forceinline__ uint8_t tile_flag(const uint8_t *__restrict__ tf, const Geo &g, int x, int y, int i) {
+  return __ldg(tf + ((int64_t)i * tiles_y(g) + y / kJ2Y) * tiles_x(g) + x / kJ2X);
+}
+
 // te, S_nn, 1/S_nn in a kernel's scalar type.
 template <typename T>
 __host__ __device__ __forceinline__ T geo_te(const Geo &g) {

@@ -24,6 +24,43 @@
 namespace ac {
 
 constexpr int kBlock = 256;
+// Kernels that work on kJ2X x kJ2Y tiles of a coarse level: kTileThreads
+// threads per block, kTileRows rows of the tile per thread.
+constexpr int kTileThreads = 256, kTileRows = kJ2X * kJ2Y / kTileThreads;
+
+// A list of the (tile, phase) items of a tiled level that are live or died
+// this cycle (see kLiveNow), appended by the kernel that computes the level's
+// flags: item = tile | phase << 32 | dying << 40 (tile = ty * tiles_x + tx).
+// Kernels driven by it run a fixed grid that strides over the count; with
+// items == null they run one block per tile and phase instead (a dense
+// level).  Every item writes its own tile only, so the order of the list does
+// not change any result.
+struct TileList {
+  const uint64_t *items;
+  const int *count;
+};
+constexpr uint64_t kItemDying = 1ull << 40;
+__device__ __forceinline__ uint64_t tile_item(int64_t tile, int phase, bool dying) {
+  return (uint64_t)tile | ((uint64_t)phase << 32) | (dying ? kItemDying : 0ull);
+}
+
+// Run body(tx, ty, i, dying) for the block's tiles: the grid's tile and phase
+// (dense) or the list's items in block-strided order.
+template <class F>
+__device__ __forceinline__ void for_each_tile(const TileList &L, const Geo &g, F &&body) {
+  if (!L.items) {
+    body((int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, false);
+    return;
+  }
+  const int cnt = *L.count, ntx = tiles_x(g);
+  for (int w = blockIdx.x; w < cnt; w += gridDim.x) {
+    const uint64_t e = L.items[w];
+    const int tile = (int)(e & 0xffffffffull), i = (int)((e >> 32) & 0xffull);
+    __syncthreads();  // the previous item's shared-memory tiles are no longer read
+    body(tile % ntx, tile / ntx, i, (e & kItemDying) != 0ull);
+  }
+}
+
 
 // m1 (RGB) and m2 of one node as two 16-byte loads.
 __device__ __forceinline__ double4 ld_mom(const double *p) {
@@ -834,7 +871,9 @@ __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const
 //   rt_n,i   = r_n,i - mean_{free j} r_n,j for free i, 0 otherwise.
 // A node at a vertex of the simplex has no free phase.  rt and mask may be
 // null (residual only).  After a red-black smoothing sequence only the first
-// colour needs this kernel: see k_smooth_fine.
+// colour needs this kernel: see k_smooth_fine.  With a mask, the number of
+// visited nodes with a free phase is added to the integer that follows *rho
+// (the host picks the coarse correction's form from it).
 // ---------------------------------------------------------------------------
 template <typename T, int N, int FORM>
 __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, const T *__restrict__ rhs,
@@ -847,6 +886,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int xx = color < 0 ? t : 2 * t + ((y + color) & 1);
   T e = T(0);
+  int nfree = 0;
   if (xx <= g.W) {
     const int64_t n = (int64_t)y * g.Wn + xx, sl = fslot<T>(g, xx, y);
     T acc[N], xk[N], bk[N], r[N], o[N];
@@ -879,6 +919,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
     if (!(xk[0] == xk[0])) e = xk[0];
     if (rt) {
       const unsigned fr = cnt >= 2 ? pos : 0u;
+      nfree = fr != 0u;
       T s = T(0);
 #pragma unroll
       for (int i = 0; i < N; ++i)
@@ -889,6 +930,10 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
       stn<T, N>(rt + sl * N, r);
       mask[n] = (uint8_t)fr;
     }
+  }
+  if (rt) {
+    const int c = __syncthreads_count(nfree);
+    if (threadIdx.x == 0 && c) atomicAdd(reinterpret_cast<unsigned long long *>(rho + 1), (unsigned long long)c);
   }
   block_max_atomic<T>(e, rho);
 }
@@ -902,37 +947,115 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
 // (or active) fine node of its phase in its support, where t = 0: r_c = 0
 // without reading t.
 // ---------------------------------------------------------------------------
+// One kJ2X x kJ2Y tile of coarse nodes per block (kTileRows rows per
+// thread), all phases per node: the grid's tiles (a dense level), or the
+// first level's tile list (tile | now << 32 | written << 40): phases live
+// now are computed, the ones that just died are zeroed, and tiles dead in
+// both cycles are not in the list (see kLiveNow).
 template <typename T, int N>
-__global__ void k_restrict0(const T *__restrict__ t, Geo gf, Geo gc, const T *__restrict__ opc,
-                            T *__restrict__ rc) {
-  const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
-  if (X > gc.W) return;
-  constexpr int dx[7] = {0, 1, -1, 0, 0, 1, -1};
-  constexpr int dy[7] = {0, 0, 0, 1, -1, 1, -1};
-  const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), K = (int64_t)Y * gc.Wn + X;
-  T acc[N], v[N];
-  bool live = false;
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    acc[i] = T(0);
-    live |= opc[i * nc + K] > T(0);
-  }
-  if (!live) {
-#pragma unroll
-    for (int i = 0; i < N; ++i) rc[i * nc + K] = T(0);
+__device__ __forceinline__ void restrict0_tile(const T *__restrict__ t, const Geo &gf, const Geo &gc,
+                                               const T *__restrict__ opc, T *__restrict__ rc, int tx, int ty,
+                                               unsigned now, unsigned wr);
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kTileThreads) k_restrict0(const T *__restrict__ t, Geo gf, Geo gc,
+                                                            const T *__restrict__ opc, T *__restrict__ rc,
+                                                            const uint64_t *__restrict__ tiles,
+                                                            const int *__restrict__ count) {
+  if (!tiles) {
+    restrict0_tile<T, N>(t, gf, gc, opc, rc, (int)blockIdx.x, (int)blockIdx.y, (1u << N) - 1u, (1u << N) - 1u);
     return;
   }
+  const int cnt = *count, ntx = tiles_x(gc);
+  for (int w = blockIdx.x; w < cnt; w += gridDim.x) {
+    const uint64_t e = tiles[w];
+    const int tile = (int)(e & 0xffffffffull);
+    restrict0_tile<T, N>(t, gf, gc, opc, rc, tile % ntx, tile / ntx, (unsigned)((e >> 32) & 0xffull),
+                         (unsigned)((e >> 40) & 0xffull));
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void restrict0_tile(const T *__restrict__ t, const Geo &gf, const Geo &gc,
+                                               const T *__restrict__ opc, T *__restrict__ rc, int tx, int ty,
+                                               unsigned now, unsigned wr) {
+  constexpr int dx[7] = {0, 1, -1, 0, 0, 1, -1};
+  constexpr int dy[7] = {0, 0, 0, 1, -1, 1, -1};
+  const int64_t nc = (int64_t)gc.Wn * (gc.H + 1);
+  const int X = tx * kJ2X + (int)(threadIdx.x % kJ2X);
+#pragma unroll 1
+  for (int q = 0; q < kTileRows; ++q) {
+    const int Y = ty * kJ2Y + (int)(threadIdx.x / kJ2X) + q * (kTileThreads / kJ2X);
+    if (X > gc.W || Y > gc.H) continue;
+    const int64_t K = (int64_t)Y * gc.Wn + X;
+    unsigned live = 0u;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if ((now >> i) & 1u) live |= (opc[i * nc + K] > T(0)) ? 1u << i : 0u;
+    T acc[N], v[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] = T(0);
+    if (live) {
+#pragma unroll
+      for (int s = 0; s < 7; ++s) {
+        const int ax = 2 * X + dx[s], ay = 2 * Y + dy[s];
+        if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
+        const T p = s == 0 ? T(1) : T(0.5);
+        ldn<T, N>(t + fslot<T>(gf, ax, ay) * N, v);
+#pragma unroll
+        for (int i = 0; i < N; ++i) acc[i] += p * v[i];
+      }
+    }
+    // a row with a zero diagonal has no free fine node of its phase under it
+    // (rt = 0 there): r = 0
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if ((wr >> i) & 1u) rc[i * nc + K] = ((live >> i) & 1u) ? acc[i] : T(0);
+  }
+}
+
+// One coarse row (node, phase) of the restriction between coarse levels.
+template <typename T, int N>
+__device__ __forceinline__ void restrict_row(const T *__restrict__ t, const Geo &gf, const Geo &gc,
+                                             const T *__restrict__ opc, T *__restrict__ rc, int X, int Y, int i) {
+  constexpr int dx[7] = {0, 1, -1, 0, 0, 1, -1};
+  constexpr int dy[7] = {0, 0, 0, 1, -1, 1, -1};
+  const int64_t nf = (int64_t)gf.Wn * (gf.H + 1), nc = (int64_t)gc.Wn * (gc.H + 1);
+  if (!(opc[i * nc + (int64_t)Y * gc.Wn + X] > T(0))) {
+    rc[i * nc + (int64_t)Y * gc.Wn + X] = T(0);
+    return;
+  }
+  const T *ti = t + i * nf;
+  T acc = T(0);
 #pragma unroll
   for (int s = 0; s < 7; ++s) {
     const int ax = 2 * X + dx[s], ay = 2 * Y + dy[s];
     if (ax < 0 || ax > gf.W || ay < 0 || ay > gf.H) continue;
     const T p = s == 0 ? T(1) : T(0.5);
-    ldn<T, N>(t + fslot<T>(gf, ax, ay) * N, v);
-#pragma unroll
-    for (int i = 0; i < N; ++i) acc[i] += p * v[i];
+    acc += p * ti[(int64_t)ay * gf.Wn + ax];
   }
+  rc[i * nc + (int64_t)Y * gc.Wn + X] = acc;
+}
+
+// The restriction onto a tiled level, driven by the coarse level's list:
+// live tiles computed, dying ones zeroed (see kLiveNow).
+template <typename T, int N>
+__global__ void __launch_bounds__(kTileThreads) k_restrict_tiled(const T *__restrict__ t, Geo gf, Geo gc,
+                                                                 const T *__restrict__ opc, T *__restrict__ rc,
+                                                                 TileList L) {
+  for_each_tile(L, gc, [&](int tx, int ty, int i, bool dying) {
+    const int64_t nc = (int64_t)gc.Wn * (gc.H + 1);
+    const int X = tx * kJ2X + (int)(threadIdx.x % kJ2X);
 #pragma unroll
-  for (int i = 0; i < N; ++i) rc[i * nc + K] = acc[i];
+    for (int q = 0; q < kTileRows; ++q) {
+      const int Y = ty * kJ2Y + (int)(threadIdx.x / kJ2X) + q * (kTileThreads / kJ2X);
+      if (X > gc.W || Y > gc.H) continue;
+      if (dying)
+        rc[i * nc + (int64_t)Y * gc.Wn + X] = T(0);
+      else
+        restrict_row<T, N>(t, gf, gc, opc, rc, X, Y, i);
+    }
+  });
 }
 
 template <typename T, int N>
@@ -974,20 +1097,16 @@ __global__ void k_restrict(const T *__restrict__ t, Geo gf, Geo gc, const T *__r
 // 2 <= Y <= Hc-2): every box node is in the grid and every a, b is an interior
 // fine node (S_aa = D[interior], S_ab = -tau eps), so range tests and
 // stencil lookups drop out.
-template <typename T, int N, bool INTERIOR>
-__device__ __forceinline__ void galerkin0_node(const uint8_t *__restrict__ mask, const Geo &gf, const Geo &gc,
-                                               const Galerkin0Table &tab, int cls, int X, int Y,
-                                               T *__restrict__ op) {
-  constexpr int sx[7] = {0, 1, -1, 0, 0, 1, -1};
-  constexpr int sy[7] = {0, 0, 0, 1, -1, 1, -1};
-  constexpr int ox[5] = {0, 1, -1, 0, 0};
-  constexpr int oy[5] = {0, 0, 0, 1, -1};
-  constexpr int lx[4] = {0, 1, 0, 1};
-  constexpr int ly[4] = {0, 0, 1, 1};
-  // mask of fine node (2X - 2 + i, 2Y - 2 + j), 0 outside the grid: byte i of
-  // the packed row words pk[j][0] (i < 4) and pk[j][1] (i = 4, 5)
-  unsigned pk[6][2];
-  unsigned all = (1u << N) - 1u, any = 0u;
+// The 6x6 box of fine masks around coarse node (X, Y): the mask of fine node
+// (2X - 2 + i, 2Y - 2 + j), 0 outside the grid, is byte i of the packed row
+// words pk[j][0] (i < 4) and pk[j][1] (i = 4, 5).  all / any: the phases free
+// at every / some box node inside the grid (any is a superset of the phases
+// whose row of the truncated operator is nonzero).
+template <int N, bool INTERIOR>
+__device__ __forceinline__ void galerkin0_box(const uint8_t *__restrict__ mask, const Geo &gf, int X, int Y,
+                                              unsigned (&pk)[6][2], unsigned &all, unsigned &any) {
+  all = (1u << N) - 1u;
+  any = 0u;
   const int64_t row0 = (int64_t)(2 * Y - 2) * gf.Wn + (2 * X - 2);
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
@@ -1004,6 +1123,21 @@ __device__ __forceinline__ void galerkin0_node(const uint8_t *__restrict__ mask,
       }
     }
   }
+}
+
+// The operator entries of coarse node (X, Y) from its box, for the phases in
+// wmask (the others are not written).
+template <typename T, int N, bool INTERIOR>
+__device__ __forceinline__ void galerkin0_node(const unsigned (&pk)[6][2], unsigned all, unsigned any,
+                                               unsigned wmask, const Geo &gf, const Geo &gc,
+                                               const Galerkin0Table &tab, int cls, int X, int Y,
+                                               T *__restrict__ op) {
+  constexpr int sx[7] = {0, 1, -1, 0, 0, 1, -1};
+  constexpr int sy[7] = {0, 0, 0, 1, -1, 1, -1};
+  constexpr int ox[5] = {0, 1, -1, 0, 0};
+  constexpr int oy[5] = {0, 0, 0, 1, -1};
+  constexpr int lx[4] = {0, 1, 0, 1};
+  constexpr int ly[4] = {0, 0, 1, 1};
   auto m = [&](int j, int i) -> unsigned { return (pk[j][i >> 2] >> (8 * (i & 3))) & 0xffu; };
   const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), K = (int64_t)Y * gc.Wn + X;
   const unsigned partial = any & ~all;
@@ -1019,7 +1153,8 @@ __device__ __forceinline__ void galerkin0_node(const uint8_t *__restrict__ mask,
 #pragma unroll
     for (int l = 0; l < 4; ++l)
 #pragma unroll
-      for (int i = 0; i < N; ++i) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? tvT[l] : T(0);
+      for (int i = 0; i < N; ++i)
+        if ((wmask >> i) & 1u) op[(l * N + i) * nc + K] = ((all >> i) & 1u) ? tvT[l] : T(0);
     return;
   }
   if constexpr (INTERIOR) {
@@ -1028,6 +1163,7 @@ __device__ __forceinline__ void galerkin0_node(const uint8_t *__restrict__ mask,
     const T Daa = geo_D<T>(gf, 4), Sab = -geo_te<T>(gf);
 #pragma unroll 1
     for (int i = 0; i < N; ++i) {
+      if (!((wmask >> i) & 1u)) continue;
       T c4[4] = {T(0), T(0), T(0), T(0)};
       if ((partial >> i) & 1u) {
 #pragma unroll
@@ -1058,6 +1194,7 @@ __device__ __forceinline__ void galerkin0_node(const uint8_t *__restrict__ mask,
     for (int l = 0; l < 4; ++l) lval[l] = (lx[l] == 0 || X < gc.W) && (ly[l] == 0 || Y < gc.H);
 #pragma unroll 1
     for (int i = 0; i < N; ++i) {
+      if (!((wmask >> i) & 1u)) continue;
       T c4[4] = {T(0), T(0), T(0), T(0)};
       if (((partial >> i) & 1u)) {
 #pragma unroll
@@ -1084,15 +1221,80 @@ __device__ __forceinline__ void galerkin0_node(const uint8_t *__restrict__ mask,
   }
 }
 
+// One block per kJ2X x kJ2Y tile of coarse nodes, kTileThreads threads with
+// kTileRows rows of nodes each.  With live flags (tf != null, a tiled first
+// level) the block first ORs the fine masks over the union of its nodes' 6x6
+// boxes (the phases with a free fine node near the tile) into the tile's
+// flags, then writes the entries of the phases live now or in the previous
+// cycle only (zeros for the latter, see kLiveNow): a tile that stays dead
+// costs the OR alone.
+// The tiles of the first level are also appended to its lists: each (tile,
+// phase) live or dying to items, and each tile with phases to write to tiles
+// as tile | now << 32 | written << 40 (phase masks).
 template <typename T, int N>
-__global__ void __launch_bounds__(kBlock) k_galerkin0(const uint8_t *__restrict__ mask, Geo gf, Geo gc,
-                                                      Galerkin0Table tab, T *__restrict__ op) {
-  const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
-  if (X > gc.W) return;
-  if (X >= 2 && X <= gc.W - 2 && Y >= 2 && Y <= gc.H - 2)
-    galerkin0_node<T, N, true>(mask, gf, gc, tab, 2 * 5 + 2, X, Y, op);
-  else
-    galerkin0_node<T, N, false>(mask, gf, gc, tab, g0_class(Y, gc.H) * 5 + g0_class(X, gc.W), X, Y, op);
+__global__ void __launch_bounds__(kTileThreads) k_galerkin0(const uint8_t *__restrict__ mask, Geo gf, Geo gc,
+                                                            Galerkin0Table tab, T *__restrict__ op,
+                                                            uint8_t *__restrict__ tf, uint64_t *__restrict__ items,
+                                                            uint64_t *__restrict__ tiles, int *__restrict__ count) {
+  __shared__ unsigned s_now, s_prev;
+  __shared__ int s_base;
+  unsigned wmask = (1u << N) - 1u;
+  if (tf) {
+    if (threadIdx.x == 0) s_now = s_prev = 0u;
+    __syncthreads();
+    // fine nodes 2X - 2 .. 2X + 3 over the tile's X range (rows alike), a
+    // (2 kJ2X + 4) x (2 kJ2Y + 4) box clamped to the grid; the loops have
+    // compile-time trip counts, so every load issues before the first OR
+    constexpr int BX = 2 * kJ2X + 4, BY = 2 * kJ2Y + 4, WARPS = kTileThreads / 32;
+    const int fx0 = 2 * (int)blockIdx.x * kJ2X - 2, fy0 = 2 * (int)blockIdx.y * kJ2Y - 2;
+    unsigned a = 0u;
+#pragma unroll
+    for (int j = 0; j < (BY + WARPS - 1) / WARPS; ++j)
+#pragma unroll
+      for (int c = 0; c < (BX + 31) / 32; ++c) {
+        const int by = j * WARPS + (int)(threadIdx.x / 32u), bx = c * 32 + (int)(threadIdx.x & 31u);
+        const int fx = fx0 + bx, fy = fy0 + by;
+        if (by < BY && bx < BX && fx >= 0 && fx <= gf.W && fy >= 0 && fy <= gf.H)
+          a |= mask[(int64_t)fy * gf.Wn + fx];
+      }
+    a = __reduce_or_sync(0xffffffffu, a);
+    if ((threadIdx.x & 31u) == 0u && a) atomicOr(&s_now, a);
+    __syncthreads();
+    const int64_t tile = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    if (threadIdx.x < (unsigned)N) {
+      uint8_t *f = tf + ((int64_t)threadIdx.x * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      const unsigned old = *f, now = (s_now >> threadIdx.x) & 1u;
+      *f = (uint8_t)(now | ((old & kLiveNow) ? kLivePrev : 0u));
+      if (old & kLiveNow) atomicOr(&s_prev, 1u << threadIdx.x);
+    }
+    __syncthreads();
+    wmask = s_now | s_prev;
+    // one atomic per list and block: the block's items go to consecutive slots
+    if (threadIdx.x == 0 && wmask) {
+      s_base = atomicAdd(count, __popc(wmask));
+      tiles[atomicAdd(count + 1, 1)] = (uint64_t)tile | ((uint64_t)s_now << 32) | ((uint64_t)wmask << 40);
+    }
+    __syncthreads();
+    if (threadIdx.x < (unsigned)N && ((wmask >> threadIdx.x) & 1u))
+      items[s_base + __popc(wmask & ((1u << threadIdx.x) - 1u))] =
+          tile_item(tile, (int)threadIdx.x, !((s_now >> threadIdx.x) & 1u));
+  }
+  if (!wmask) return;
+#pragma unroll 1
+  for (int q = 0; q < kTileRows; ++q) {
+    const int X = blockIdx.x * kJ2X + (int)(threadIdx.x % kJ2X);
+    const int Y = blockIdx.y * kJ2Y + (int)(threadIdx.x / kJ2X) + q * (kTileThreads / kJ2X);
+    if (X > gc.W || Y > gc.H) continue;
+    unsigned pk[6][2], all, any;
+    if (X >= 2 && X <= gc.W - 2 && Y >= 2 && Y <= gc.H - 2) {
+      galerkin0_box<N, true>(mask, gf, X, Y, pk, all, any);
+      galerkin0_node<T, N, true>(pk, all, any, wmask, gf, gc, tab, 2 * 5 + 2, X, Y, op);
+    } else {
+      galerkin0_box<N, false>(mask, gf, X, Y, pk, all, any);
+      galerkin0_node<T, N, false>(pk, all, any, wmask, gf, gc, tab, g0_class(Y, gc.H) * 5 + g0_class(X, gc.W), X,
+                                  Y, op);
+    }
+  }
 }
 
 
@@ -1185,6 +1387,79 @@ __global__ void __launch_bounds__(kBlock) k_galerkin(const T *__restrict__ opf, 
   for (int l = 0; l < 4; ++l) opc[(l * N + i) * nc + K] = c4[l];
 }
 
+// The same product onto a tiled level (live flags tfc) from a tiled level
+// (flags tff): one block per (kJ2X x kJ2Y tile, phase), one thread per node.
+// The fine tiles under the coarse tile and its one-node halo are looked up
+// first: if none is live for the phase, no coarse row of the tile can be
+// nonzero and no fine operator entry is read.
+template <typename T, int N>
+__global__ void __launch_bounds__(kTileThreads) k_galerkin_tiled(const T *__restrict__ opf, Geo gf, Geo gc,
+                                                                 T *__restrict__ opc, const uint8_t *__restrict__ tff,
+                                                                 uint8_t *__restrict__ tfc, uint64_t *__restrict__ items,
+                                                                 int *__restrict__ count) {
+  __shared__ int s_fine;
+  __shared__ unsigned s_prev;
+  const int i = blockIdx.z;
+  const int64_t nf = (int64_t)gf.Wn * (gf.H + 1), nc = (int64_t)gc.Wn * (gc.H + 1);
+  {
+    // fine nodes 2X - 1 .. 2X + 1 over the tile's X range (rows alike): fine
+    // tiles 2 tx - 1 .. 2 tx + 1 (ty alike), one flag per thread of the first 9
+    bool f = false;
+    if (threadIdx.x < 9u) {
+      const int fx = 2 * (int)blockIdx.x - 1 + (int)(threadIdx.x % 3u), fy = 2 * (int)blockIdx.y - 1 + (int)(threadIdx.x / 3u);
+      if (fx >= 0 && fx < tiles_x(gf) && fy >= 0 && fy < tiles_y(gf))
+        f = (tff[((int64_t)i * tiles_y(gf) + fy) * tiles_x(gf) + fx] & kLiveNow) != 0;
+    }
+    const int any = __syncthreads_or(f);
+    if (threadIdx.x == 0) s_fine = any;
+  }
+  __syncthreads();
+  // the rows of this thread: a row is live when a fine row under its hat is
+  unsigned live = 0u;
+  const int X = blockIdx.x * kJ2X + (int)(threadIdx.x % kJ2X);
+  if (s_fine) {
+#pragma unroll
+    for (int q = 0; q < kTileRows; ++q) {
+      const int Y = blockIdx.y * kJ2Y + (int)(threadIdx.x / kJ2X) + q * (kTileThreads / kJ2X);
+      if (X > gc.W || Y > gc.H) continue;
+      constexpr int sx[7] = {0, 1, -1, 0, 0, 1, -1};
+      constexpr int sy[7] = {0, 0, 0, 1, -1, 1, -1};
+      bool lq = false;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const int ax = 2 * X + sx[k], ay = 2 * Y + sy[k];
+        if (ax >= 0 && ax <= gf.W && ay >= 0 && ay <= gf.H) lq |= opf[i * nf + (int64_t)ay * gf.Wn + ax] > T(0);
+      }
+      live |= lq ? 1u << q : 0u;
+    }
+  }
+  const int now = __syncthreads_or(live != 0u);
+  if (threadIdx.x == 0) {
+    uint8_t *f = tfc + ((int64_t)i * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const unsigned old = *f;
+    s_prev = old & kLiveNow;
+    *f = (uint8_t)((now ? kLiveNow : 0u) | (s_prev ? kLivePrev : 0u));
+    if (now || s_prev) items[atomicAdd(count, 1)] = tile_item((int64_t)blockIdx.y * gridDim.x + blockIdx.x, i, !now);
+  }
+  __syncthreads();
+  if (!now && !s_prev) return;
+#pragma unroll 1
+  for (int q = 0; q < kTileRows; ++q) {
+    const int Y = blockIdx.y * kJ2Y + (int)(threadIdx.x / kJ2X) + q * (kTileThreads / kJ2X);
+    if (X > gc.W || Y > gc.H) continue;
+    const int64_t K = (int64_t)Y * gc.Wn + X;
+    T c4[4] = {T(0), T(0), T(0), T(0)};
+    if ((live >> q) & 1u) {
+      if (X >= 1 && X <= gc.W - 1 && Y >= 1 && Y <= gc.H - 1)
+        galerkin_phase<T, N, true>(opf, gf, gc, nf, X, Y, i, c4);
+      else
+        galerkin_phase<T, N, false>(opf, gf, gc, nf, X, Y, i, c4);
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) opc[(l * N + i) * nc + K] = c4[l];
+  }
+}
+
 // (S v)_K - S_KK v_K for phase i of a stored operator (phase-major arrays).
 template <typename T, int N>
 __device__ __forceinline__ T op_offdiag(const T *op, const T *v, const Geo &g, int64_t nc, int x, int y, int i) {
@@ -1217,20 +1492,33 @@ __device__ __forceinline__ T op_offdiag(const T *op, const T *v, const Geo &g, i
 // sweeps, and no neighbour loads through L1/L2.  The first sweep keeps each
 // node's 1 / l1 in shared memory for the second.  vout must not alias vin
 // unless ZERO_IN (vin unread).
-constexpr int kJ2X = 32, kJ2Y = 16, kJ2Threads = 256;
+constexpr int kJ2Threads = 256;
+
+// Zeros into the tile (tx, ty) of phase plane a (and b when not null): a tile
+// that stopped being live this cycle (see kLiveNow).
+template <typename T>
+__device__ __forceinline__ void tile_zero(const Geo &g, int tx, int ty, T *__restrict__ a, T *__restrict__ b) {
+  for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += blockDim.x) {
+    const int x = tx * kJ2X + t % kJ2X, y = ty * kJ2Y + t / kJ2X;
+    if (x <= g.W && y <= g.H) {
+      a[(int64_t)y * g.Wn + x] = T(0);
+      if (b) b[(int64_t)y * g.Wn + x] = T(0);
+    }
+  }
+}
+
 template <typename T, int N, bool ZERO_IN>
-__global__ void __launch_bounds__(kJ2Threads) k_coarse_jacobi2(const T *__restrict__ op, const T *__restrict__ r,
-                                                               const T *vin, T *vout, Geo g) {
+__device__ __forceinline__ void jacobi2_tile(const T *__restrict__ op, const T *__restrict__ r, const T *vin,
+                                             T *vout, const Geo &g, int bxt, int byt, int i) {
   constexpr int AX = kJ2X + 4, AY = kJ2Y + 4;  // tile + halo 2
   constexpr int BX = kJ2X + 2, BY = kJ2Y + 2;  // tile + halo 1
   __shared__ T sC[AY][AX], sE[AY][AX], sN[AY][AX], sNE[AY][AX], sV[AY][AX];
   __shared__ T sR[BY][BX], sV1[BY][BX], sI[BY][BX];
-  const int i = blockIdx.z;
   const int64_t nc = (int64_t)g.Wn * (g.H + 1);
   const T *C = op + (0 * N + i) * nc, *E = op + (1 * N + i) * nc, *Nn = op + (2 * N + i) * nc,
           *NE = op + (3 * N + i) * nc, *ri = r + i * nc, *vi = vin + i * nc;
   T *vo = vout + i * nc;
-  const int x0 = blockIdx.x * kJ2X - 2, y0 = blockIdx.y * kJ2Y - 2;  // grid position of [0][0] of the A arrays
+  const int x0 = bxt * kJ2X - 2, y0 = byt * kJ2Y - 2;  // grid position of [0][0] of the A arrays
   // A tile whose rows all have a zero diagonal (no free fine node of this
   // phase under any of them) has vout = 0 whatever vin: write the zeros and
   // stop.  After phase separation most tiles of a phase are like that.
@@ -1297,6 +1585,21 @@ __global__ void __launch_bounds__(kJ2Threads) k_coarse_jacobi2(const T *__restri
   }
 }
 
+// (the register bound keeps as many blocks per SM as the shared memory
+// allows: eight in float, five in double)
+constexpr int j2_min_blocks(int elem) { return elem == 4 ? 8 : 5; }
+template <typename T, int N, bool ZERO_IN>
+__global__ void __launch_bounds__(kJ2Threads, j2_min_blocks(sizeof(T))) k_coarse_jacobi2(const T *__restrict__ op, const T *__restrict__ r,
+                                                                  const T *vin, T *vout, Geo g, TileList L) {
+  for_each_tile(L, g, [&](int tx, int ty, int i, bool dying) {
+    const int64_t nc = (int64_t)g.Wn * (g.H + 1);
+    if (dying)
+      tile_zero<T>(g, tx, ty, vout + i * nc, (T *)nullptr);
+    else
+      jacobi2_tile<T, N, ZERO_IN>(op, r, vin, vout, g, tx, ty, i);
+  });
+}
+
 // The pre-smoothing pair of a coarse level (two l1-Jacobi sweeps from v = 0)
 // fused with the level's residual t = r - S v: the operator is staged on the
 // tile plus a halo of 3 and r on the tile plus a halo of 2, the first sweep
@@ -1304,20 +1607,19 @@ __global__ void __launch_bounds__(kJ2Threads) k_coarse_jacobi2(const T *__restri
 // on the tile, so one launch writes v and t of the tile (k_coarse_resid's
 // arithmetic and order; rows with a zero diagonal give 0 for both).
 template <typename T, int N>
-__global__ void __launch_bounds__(kJ2Threads) k_coarse_jacobi2_resid(const T *__restrict__ op,
-                                                                     const T *__restrict__ r, T *__restrict__ vout,
-                                                                     T *__restrict__ tout, Geo g) {
+__device__ __forceinline__ void jacobi2_resid_tile(const T *__restrict__ op, const T *__restrict__ r,
+                                                   T *__restrict__ vout, T *__restrict__ tout, const Geo &g, int bxt,
+                                                   int byt, int i) {
   constexpr int AX = kJ2X + 6, AY = kJ2Y + 6;  // tile + halo 3 (operator)
   constexpr int BX = kJ2X + 4, BY = kJ2Y + 4;  // tile + halo 2 (r, first sweep)
   constexpr int CX = kJ2X + 2, CY = kJ2Y + 2;  // tile + halo 1 (second sweep)
   __shared__ T sC[AY][AX], sE[AY][AX], sN[AY][AX], sNE[AY][AX];
   __shared__ T sR[BY][BX], sV1[BY][BX], sI[BY][BX], sV2[CY][CX];
-  const int i = blockIdx.z;
   const int64_t nc = (int64_t)g.Wn * (g.H + 1);
   const T *C = op + (0 * N + i) * nc, *E = op + (1 * N + i) * nc, *Nn = op + (2 * N + i) * nc,
           *NE = op + (3 * N + i) * nc, *ri = r + i * nc;
   T *vo = vout + i * nc, *to = tout + i * nc;
-  const int x0 = blockIdx.x * kJ2X - 3, y0 = blockIdx.y * kJ2Y - 3;  // grid position of [0][0] of the A arrays
+  const int x0 = bxt * kJ2X - 3, y0 = byt * kJ2Y - 3;  // grid position of [0][0] of the A arrays
   int live = 0;
   for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
     const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
@@ -1396,6 +1698,19 @@ __global__ void __launch_bounds__(kJ2Threads) k_coarse_jacobi2_resid(const T *__
     vo[K] = vk;
     to[K] = d > T(0) ? sR[by][bx] - d * vk - s : T(0);
   }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kJ2Threads, j2_min_blocks(sizeof(T))) k_coarse_jacobi2_resid(const T *__restrict__ op,
+                                                                        const T *__restrict__ r, T *__restrict__ vout,
+                                                                        T *__restrict__ tout, Geo g, TileList L) {
+  for_each_tile(L, g, [&](int tx, int ty, int i, bool dying) {
+    const int64_t nc = (int64_t)g.Wn * (g.H + 1);
+    if (dying)
+      tile_zero<T>(g, tx, ty, vout + i * nc, tout + i * nc);
+    else
+      jacobi2_resid_tile<T, N>(op, r, vout, tout, g, tx, ty, i);
+  });
 }
 
 // Whole-level Gauss-Seidel in one block for small coarsest grids: `sweeps`
@@ -1650,10 +1965,41 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(TailArgs a, const 
 // nodes branch-free; the same arithmetic and order as op_offdiag).  The
 // float forms fuse it into the pre-smoothing pair (k_coarse_jacobi2_resid).
 template <typename T, int N>
+__device__ __forceinline__ void coarse_resid_row(const T *__restrict__ op, const T *__restrict__ r,
+                                                 const T *__restrict__ v, const Geo &g, T *__restrict__ t, int x, int y,
+                                                 int i);
+
+template <typename T, int N>
 __global__ void k_coarse_resid(const T *__restrict__ op, const T *__restrict__ r, const T *__restrict__ v, Geo g,
                                T *__restrict__ t) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, i = blockIdx.z;
   if (x > g.W) return;
+  coarse_resid_row<T, N>(op, r, v, g, t, x, y, i);
+}
+
+// The same on a tiled level, driven by its list (dying tiles zeroed).
+template <typename T, int N>
+__global__ void __launch_bounds__(kTileThreads) k_coarse_resid_tiled(const T *__restrict__ op, const T *__restrict__ r,
+                                                                     const T *__restrict__ v, Geo g, T *__restrict__ t,
+                                                                     TileList L) {
+  for_each_tile(L, g, [&](int tx, int ty, int i, bool dying) {
+    const int x = tx * kJ2X + (int)(threadIdx.x % kJ2X);
+#pragma unroll
+    for (int q = 0; q < kTileRows; ++q) {
+      const int y = ty * kJ2Y + (int)(threadIdx.x / kJ2X) + q * (kTileThreads / kJ2X);
+      if (x > g.W || y > g.H) continue;
+      if (dying)
+        t[i * ((int64_t)g.Wn * (g.H + 1)) + (int64_t)y * g.Wn + x] = T(0);
+      else
+        coarse_resid_row<T, N>(op, r, v, g, t, x, y, i);
+    }
+  });
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void coarse_resid_row(const T *__restrict__ op, const T *__restrict__ r,
+                                                 const T *__restrict__ v, const Geo &g, T *__restrict__ t, int x, int y,
+                                                 int i) {
   const int64_t nc = (int64_t)g.Wn * (g.H + 1), K = (int64_t)y * g.Wn + x;
   // a row with a zero diagonal is zero, and so is its r (no free fine node of
   // the phase under it): t = 0 without reading the row
@@ -1717,6 +2063,31 @@ __global__ void k_prolong_add(const T *__restrict__ vc, Geo gf, Geo gc, const T 
     if (mid) p = T(0.5) * (p + vi[K1]);
     vf[i * nf + a] += p;
   }
+}
+
+// The same onto a tiled level, driven by that level's list: the live tiles
+// only (a dying tile's v is 0 and stays 0, see kLiveNow).
+template <typename T, int N>
+__global__ void __launch_bounds__(kTileThreads) k_prolong_add_tiled(const T *__restrict__ vc, Geo gf, Geo gc,
+                                                                    const T *__restrict__ opf, T *__restrict__ vf,
+                                                                    TileList L) {
+  for_each_tile(L, gf, [&](int tx, int ty, int i, bool dying) {
+    if (dying) return;
+    const int64_t nc = (int64_t)gc.Wn * (gc.H + 1), nf = (int64_t)gf.Wn * (gf.H + 1);
+    const int x = tx * kJ2X + (int)(threadIdx.x % kJ2X);
+    const T *vi = vc + i * nc;
+#pragma unroll
+    for (int q = 0; q < kTileRows; ++q) {
+      const int y = ty * kJ2Y + (int)(threadIdx.x / kJ2X) + q * (kTileThreads / kJ2X);
+      if (x > gf.W || y > gf.H) continue;
+      const int64_t a = (int64_t)y * gf.Wn + x;
+      if (!(opf[i * nf + a] > T(0))) continue;
+      const int64_t K0 = (int64_t)(y >> 1) * gc.Wn + (x >> 1);
+      T p = vi[K0];
+      if ((x & 1) || (y & 1)) p = T(0.5) * (p + vi[K0 + (x & 1) + (int64_t)(y & 1) * gc.Wn]);
+      vf[i * nf + a] += p;
+    }
+  });
 }
 
 // ---------------------------------------------------------------------------

@@ -26,6 +26,34 @@ inline PhaseLaunch phase_grid(int count_per_row, int rows, int phases) {
   return {dim3((unsigned)((count_per_row + (int)b - 1) / (int)b), (unsigned)rows, (unsigned)phases), b};
 }
 
+// The TileList view of a level's items (dense: null) and the grid that
+// strides over it (dense: the level's tiles x phases).
+inline TileList item_list(const LevelLists *L) {
+  return L ? TileList{L->items, L->count} : TileList{nullptr, nullptr};
+}
+// Blocks of kernel k with `threads` threads resident on one SM (at least 1).
+template <class K>
+inline int resident_blocks(K k, int threads) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, threads, 0) != cudaSuccess || b < 1) {
+    cudaGetLastError();
+    b = 1;
+  }
+  return b;
+}
+// The grid of a launch of kernel k over a level's lists: every block
+// resident at once, no more blocks than list entries can exist.
+template <class K>
+inline dim3 list_grid(const LevelLists *L, int64_t entries, K k, int threads) {
+  static const int per_sm = resident_blocks(k, threads);
+  const int64_t b = (int64_t)L->sms * per_sm;
+  return dim3((unsigned)(b < entries ? b : (entries > 0 ? entries : 1)));
+}
+template <class K>
+inline dim3 tile_grid(const Geo &g, const LevelLists *L, int N, K k, int threads) {
+  return L ? list_grid(L, L->cap, k, threads) : dim3((unsigned)tiles_x(g), (unsigned)tiles_y(g), (unsigned)N);
+}
+
 template <typename T, int N, int FORM>
 struct SolverLaunch {
   // `sweeps` red-black sweeps in place, one launch per colour; the pending
@@ -55,34 +83,50 @@ struct SolverLaunch {
                                                    rho, color);
     return 1;
   }
-  static int restrict0(const void *rt, const Geo &gf, const Geo &gc, const void *op1, void *r1, cudaStream_t s) {
-    k_restrict0<T, N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>((const T *)rt, gf, gc, (const T *)op1,
-                                                                        (T *)r1);
+  static int restrict0(const void *rt, const Geo &gf, const Geo &gc, const void *op1, void *r1, const LevelLists *L1,
+                       cudaStream_t s) {
+    const dim3 grid = L1 ? list_grid(L1, L1->cap / N, k_restrict0<T, N>, kTileThreads)
+                         : dim3((unsigned)tiles_x(gc), (unsigned)tiles_y(gc));
+    k_restrict0<T, N><<<grid, kTileThreads, 0, s>>>((const T *)rt, gf, gc, (const T *)op1, (T *)r1,
+                                                  L1 ? L1->tiles : nullptr, L1 ? L1->count + 1 : nullptr);
     return 1;
   }
   static int galerkin0(const uint8_t *mask, const Geo &gf, const Geo &gc, const Galerkin0Table &tab, void *op,
-                       cudaStream_t s) {
-    k_galerkin0<T, N><<<row_grid(gc.W + 1, gc.H + 1), kBlock, 0, s>>>(mask, gf, gc, tab, (T *)op);
+                       const LevelLists *L1, cudaStream_t s) {
+    const dim3 grid((unsigned)tiles_x(gc), (unsigned)tiles_y(gc));
+    k_galerkin0<T, N><<<grid, kTileThreads, 0, s>>>(mask, gf, gc, tab, (T *)op, L1 ? L1->flags : nullptr,
+                                                  L1 ? L1->items : nullptr, L1 ? L1->tiles : nullptr,
+                                                  L1 ? L1->count : nullptr);
     return 1;
   }
-  static int galerkin(const void *opf, const Geo &gf, const Geo &gc, void *opc, cudaStream_t s) {
-    const PhaseLaunch L = phase_grid(gc.W + 1, gc.H + 1, N);
-    k_galerkin<T, N><<<L.grid, L.block, 0, s>>>((const T *)opf, gf, gc, (T *)opc);
+  static int galerkin(const void *opf, const Geo &gf, const Geo &gc, void *opc, const LevelLists *Lf,
+                      const LevelLists *Lc, cudaStream_t s) {
+    if (Lc) {
+      const dim3 grid((unsigned)tiles_x(gc), (unsigned)tiles_y(gc), (unsigned)N);
+      k_galerkin_tiled<T, N><<<grid, kTileThreads, 0, s>>>((const T *)opf, gf, gc, (T *)opc, Lf->flags, Lc->flags,
+                                                         Lc->items, Lc->count);
+    } else {
+      const PhaseLaunch L = phase_grid(gc.W + 1, gc.H + 1, N);
+      k_galerkin<T, N><<<L.grid, L.block, 0, s>>>((const T *)opf, gf, gc, (T *)opc);
+    }
     return 1;
   }
   static int coarse_smooth(const void *op, const void *r, void *v, void *tmp, const Geo &g, int sweeps,
-                           bool zero_start, void **out, cudaStream_t s) {
-    const dim3 grid((unsigned)((g.W + kJ2X) / kJ2X), (unsigned)((g.H + kJ2Y) / kJ2Y), (unsigned)N);
+                           bool zero_start, void **out, const LevelLists *L, cudaStream_t s) {
+    const TileList tf = item_list(L);
     void *cur = v;
     int k = 0;
     for (int p = 0; p < sweeps / 2; ++p) {
       if (p == 0 && zero_start) {
         // v is not read: the pair can write it
-        k_coarse_jacobi2<T, N, true><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)v, (T *)v, g);
+        const dim3 grid = tile_grid(g, L, N, k_coarse_jacobi2<T, N, true>, kJ2Threads);
+        k_coarse_jacobi2<T, N, true><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)v, (T *)v, g,
+                                                                tf);
       } else {
         void *nxt = cur == v ? tmp : v;
+        const dim3 grid = tile_grid(g, L, N, k_coarse_jacobi2<T, N, false>, kJ2Threads);
         k_coarse_jacobi2<T, N, false><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)cur,
-                                                                 (T *)nxt, g);
+                                                                 (T *)nxt, g, tf);
         cur = nxt;
       }
       ++k;
@@ -92,14 +136,18 @@ struct SolverLaunch {
   }
   // two l1-Jacobi sweeps from v = 0, then t = r - S v; float: one fused
   // launch (its shared memory is over the static limit in double)
-  static int coarse_pre_resid(const void *op, const void *r, void *v, void *t, const Geo &g, cudaStream_t s) {
-    const dim3 grid((unsigned)((g.W + kJ2X) / kJ2X), (unsigned)((g.H + kJ2Y) / kJ2Y), (unsigned)N);
+  static int coarse_pre_resid(const void *op, const void *r, void *v, void *t, const Geo &g, const LevelLists *L,
+                              cudaStream_t s) {
+    const TileList tf = item_list(L);
     if constexpr (sizeof(T) == 4) {
-      k_coarse_jacobi2_resid<T, N><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (T *)v, (T *)t, g);
+      const dim3 grid = tile_grid(g, L, N, k_coarse_jacobi2_resid<T, N>, kJ2Threads);
+      k_coarse_jacobi2_resid<T, N><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (T *)v, (T *)t, g, tf);
       return 1;
     } else {
-      k_coarse_jacobi2<T, N, true><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)v, (T *)v, g);
-      return 1 + coarse_resid(op, r, v, g, t, s);
+      const dim3 grid = tile_grid(g, L, N, k_coarse_jacobi2<T, N, true>, kJ2Threads);
+      k_coarse_jacobi2<T, N, true><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)v, (T *)v, g,
+                                                              tf);
+      return 1 + coarse_resid(op, r, v, g, t, L, s);
     }
   }
   static int coarse_solve(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s) {
@@ -113,18 +161,36 @@ struct SolverLaunch {
     }
     return 1;
   }
-  static int coarse_resid(const void *op, const void *r, const void *v, const Geo &g, void *t, cudaStream_t s) {
-    const PhaseLaunch L = phase_grid(g.W + 1, g.H + 1, N);
-    k_coarse_resid<T, N><<<L.grid, L.block, 0, s>>>((const T *)op, (const T *)r, (const T *)v, g, (T *)t);
+  static int coarse_resid(const void *op, const void *r, const void *v, const Geo &g, void *t, const LevelLists *Lv,
+                          cudaStream_t s) {
+    if (Lv) {
+      k_coarse_resid_tiled<T, N><<<list_grid(Lv, Lv->cap, k_coarse_resid_tiled<T, N>, kTileThreads), kTileThreads, 0,
+                                   s>>>((const T *)op, (const T *)r, (const T *)v, g,
+                                                                    (T *)t, item_list(Lv));
+    } else {
+      const PhaseLaunch L = phase_grid(g.W + 1, g.H + 1, N);
+      k_coarse_resid<T, N><<<L.grid, L.block, 0, s>>>((const T *)op, (const T *)r, (const T *)v, g, (T *)t);
+    }
     return 1;
   }
-  static int restrict_(const void *t, const Geo &gf, const Geo &gc, const void *opc, void *rc, cudaStream_t s) {
-    const PhaseLaunch L = phase_grid(gc.W + 1, gc.H + 1, N);
-    k_restrict<T, N><<<L.grid, L.block, 0, s>>>((const T *)t, gf, gc, (const T *)opc, (T *)rc);
+  static int restrict_(const void *t, const Geo &gf, const Geo &gc, const void *opc, void *rc, const LevelLists *Lc,
+                       cudaStream_t s) {
+    if (Lc) {
+      k_restrict_tiled<T, N><<<list_grid(Lc, Lc->cap, k_restrict_tiled<T, N>, kTileThreads), kTileThreads, 0, s>>>((const T *)t, gf, gc, (const T *)opc, (T *)rc,
+                                                               item_list(Lc));
+    } else {
+      const PhaseLaunch L = phase_grid(gc.W + 1, gc.H + 1, N);
+      k_restrict<T, N><<<L.grid, L.block, 0, s>>>((const T *)t, gf, gc, (const T *)opc, (T *)rc);
+    }
     return 1;
   }
-  static int prolong_add(const void *vc, const Geo &gf, const Geo &gc, const void *opf, void *vf, cudaStream_t s) {
-    if ((int64_t)(gf.W + 1) * (gf.H + 1) >= kWideLevelNodes) {
+  static int prolong_add(const void *vc, const Geo &gf, const Geo &gc, const void *opf, void *vf, const LevelLists *Lf,
+                         cudaStream_t s) {
+    if (Lf) {
+      k_prolong_add_tiled<T, N><<<list_grid(Lf, Lf->cap, k_prolong_add_tiled<T, N>, kTileThreads), kTileThreads, 0,
+                                  s>>>((const T *)vc, gf, gc, (const T *)opf, (T *)vf,
+                                                                  item_list(Lf));
+    } else if ((int64_t)(gf.W + 1) * (gf.H + 1) >= kWideLevelNodes) {
       k_prolong_add<T, N, false><<<row_grid(gf.W + 1, gf.H + 1), kBlock, 0, s>>>((const T *)vc, gf, gc,
                                                                                  (const T *)opf, (T *)vf);
     } else {

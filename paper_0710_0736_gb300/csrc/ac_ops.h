@@ -25,6 +25,23 @@ struct TailArgs {
   const void *op[kTailMaxLevels];  // phase-major C, E, N, NE planes of each level
 };
 
+// The live-tile state of a tiled coarse level (see kLiveNow in
+// ac_device.cuh): its flags, the work lists its Galerkin kernel appends --
+// (tile, phase) items and, on the first level, tiles with their phase masks --
+// with their two counts (cleared before each coarse correction), the lists'
+// capacity and the device's multiprocessors.  A launch that strides over a
+// list runs as many blocks as can be resident at once (at most the
+// capacity), so that no block waits for another to finish its share.  Null
+// for a dense level.
+struct LevelLists {
+  uint8_t *flags;
+  uint64_t *items;
+  uint64_t *tiles;
+  int *count;  // [0] items, [1] tiles
+  int64_t cap; // tiles x phases
+  int sms;
+};
+
 // One multigrid solve instantiation (scalar type and constraint form); array
 // arguments are typed by that instantiation (double or float).
 struct SolverOps {
@@ -39,22 +56,31 @@ struct SolverOps {
   int (*resid)(const void *x, const void *rhs, const void *ob, const Geo &g, void *rt, uint8_t *mask, double *rho,
                int color, cudaStream_t s);
   // transfers skip the rows whose diagonal in the (coarse or fine) level's
-  // operator is 0: those rows and their residuals are exactly 0
-  int (*restrict0)(const void *rt, const Geo &gf, const Geo &gc, const void *op1, void *r1, cudaStream_t s);
-  int (*galerkin0)(const uint8_t *mask, const Geo &gf, const Geo &gc, const Galerkin0Table &tab, void *op,
+  // operator is 0: those rows and their residuals are exactly 0.  LevelLists
+  // arguments: the live-tile state of a tiled level, or null for a level
+  // kept dense
+  int (*restrict0)(const void *rt, const Geo &gf, const Geo &gc, const void *op1, void *r1, const LevelLists *L1,
                    cudaStream_t s);
-  int (*galerkin)(const void *opf, const Geo &gf, const Geo &gc, void *opc, cudaStream_t s);
+  int (*galerkin0)(const uint8_t *mask, const Geo &gf, const Geo &gc, const Galerkin0Table &tab, void *op,
+                   const LevelLists *L1, cudaStream_t s);
+  // Lc != null: a tiled coarse level from a tiled fine level (Lf)
+  int (*galerkin)(const void *opf, const Geo &gf, const Geo &gc, void *opc, const LevelLists *Lf,
+                  const LevelLists *Lc, cudaStream_t s);
   // `sweeps` (even) l1-Jacobi sweeps in fused pairs starting from v, using v
   // and tmp in turn; *out returns the buffer holding the result.  zero_start:
   // v = 0 on entry (it is then neither read nor needs clearing)
   int (*coarse_smooth)(const void *op, const void *r, void *v, void *tmp, const Geo &g, int sweeps, bool zero_start,
-                       void **out, cudaStream_t s);
+                       void **out, const LevelLists *L, cudaStream_t s);
   int (*coarse_solve)(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s);
-  int (*coarse_resid)(const void *op, const void *r, const void *v, const Geo &g, void *t, cudaStream_t s);
+  int (*coarse_resid)(const void *op, const void *r, const void *v, const Geo &g, void *t, const LevelLists *L,
+                      cudaStream_t s);
   // one pair of l1-Jacobi sweeps from v = 0, then t = r - S v
-  int (*coarse_pre_resid)(const void *op, const void *r, void *v, void *t, const Geo &g, cudaStream_t s);
-  int (*restrict_)(const void *t, const Geo &gf, const Geo &gc, const void *opc, void *rc, cudaStream_t s);
-  int (*prolong_add)(const void *vc, const Geo &gf, const Geo &gc, const void *opf, void *vf, cudaStream_t s);
+  int (*coarse_pre_resid)(const void *op, const void *r, void *v, void *t, const Geo &g, const LevelLists *L,
+                          cudaStream_t s);
+  int (*restrict_)(const void *t, const Geo &gf, const Geo &gc, const void *opc, void *rc, const LevelLists *Lc,
+                   cudaStream_t s);
+  int (*prolong_add)(const void *vc, const Geo &gf, const Geo &gc, const void *opf, void *vf, const LevelLists *Lf,
+                     cudaStream_t s);
   // v of level k0 from r of level k0 by the whole cycle below it (see
   // TailArgs); smem bytes of dynamic shared memory per block
   int (*coarse_tail)(const TailArgs &a, const void *r0, void *v0, int coarse_sweeps, int coarsest_sweeps,

@@ -376,6 +376,65 @@ def test_profiling_mask(ac):
 
 
 # --------------------------------------------------------------------------
+# coarse-level tiling: the tiled and the dense forms compute the same numbers
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("W,H,N", [(256, 256, 8), (1024, 1024, 4)])
+def test_coarse_tiling_is_bit_identical(ac, precision, W, H, N):
+    """The tiled coarse levels (live flags, work lists, zeros written once per
+    dying tile) against the dense levels: the same fields bit for bit, also
+    when a run switches between the forms every two steps (each switch into
+    the tiled form must rewrite every tile)."""
+    img = synth.shapes_image(W + N, W, H, rect_side=(8, W // 4), disk_r=(4, W / 8))
+    u0 = synth.dirichlet_init(W - N, (W + 1) * (H + 1), N)
+    prec = ac.AC_MIXED if precision == "mixed" else ac.AC_FP64
+    tol = 1e-6 if precision == "mixed" else 1e-8
+
+    def run(modes):
+        seg = ac.Segmenter(W, H, N, 2.0, 1.0, 4.0, tol=tol, max_cycles=2000, precision=prec)
+        seg.set_image(img)
+        seg.set_phase(u0)
+        cycles = 0
+        for m in modes:
+            ac.ac_set_coarse_tiling(seg.ctx, m)
+            cycles += seg.step(2).total_cycles
+        u = seg.phase()
+        seg.close()
+        return u, cycles
+
+    NEVER, ALWAYS, AUTO = ac.AC_TILES_NEVER, ac.AC_TILES_ALWAYS, ac.AC_TILES_AUTO
+    u_ref, c_ref = run([NEVER] * 4)
+    for modes in ([ALWAYS] * 4, [ALWAYS, NEVER, ALWAYS, NEVER], [AUTO] * 4):
+        u, c = run(modes)
+        assert c == c_ref and np.array_equal(u, u_ref), modes
+
+
+def test_coarse_tiling_adjoint_is_bit_identical(ac):
+    """The adjoint's tangent solve (FP64) runs the same coarse levels: tiled
+    and dense give the same gradients bit for bit."""
+    import torch
+    W, H, N, T, every = 256, 256, 4, 4, 2
+    img = synth.shapes_image(91, W, H, rect_side=(8, 64), disk_r=(4, 32)).astype(np.float64)
+    u0 = synth.dirichlet_init(92, (W + 1) * (H + 1), N)
+    target = synth.voronoi_labels(93, W + 1, H + 1, n_seeds=6, n_labels=N)
+    m0 = oracle.moments(img)[:, 0]
+    out = []
+    for mode in (ac.AC_TILES_NEVER, ac.AC_TILES_ALWAYS):
+        seg = _seg(ac, W, H, N, tol=1e-10)
+        ac.ac_set_coarse_tiling(seg.ctx, mode)
+        seg.set_image(img)
+        seg.set_phase(u0)
+        ac.ac_adjoint_forward(seg.ctx, T, every)
+        _, gT = oracle.misfit_loss(seg.phase(), m0, target)
+        g_img = torch.zeros((H, W, 3), dtype=torch.float64, device="cuda")
+        gl, ge = ac.ac_adjoint_backward(seg.ctx, torch.tensor(gT, device="cuda"), g_img)
+        out.append((gl, ge, g_img.cpu().numpy()))
+        seg.close()
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1] and np.array_equal(out[0][2], out[1][2])
+
+
+# --------------------------------------------------------------------------
 # full sizes: properties that hold at any size, checked by the oracle
 # --------------------------------------------------------------------------
 
