@@ -672,14 +672,14 @@ def main():
         t0 = time.perf_counter()
         ac.ac_set_image(seg.ctx, host_img, W, H)
         for _ in range(args.steps):
-            ac.ac_segment(seg.ctx, 1, labels, W, H, allow_not_converged=True)
+            ac.ac_segment(seg.ctx, 1, labels, W, H, allow_not_converged=True, stats=False)
         torch.cuda.synchronize()
         e2e_value, _ = job_rate((time.perf_counter() - t0) * 1e3, args.steps, world, "cuda")
         e2e = {"value": e2e_value, "unit": "steps/s",
                "h2d_bytes_per_step": host_img.numel() * 4 / args.steps, "d2h_bytes_per_step": labels.numel(),
                "path": "ac_set_image from pinned host memory once (it resets u to the seeded start, as before "
-                       "the device-timed steps), then per step ac_segment(1 step) with the pixel labels read back "
-                       "to pinned host memory: the same K time steps as value"}
+                       "the device-timed steps), then per step ac_segment(1 step, no statistics) with the pixel "
+                       "labels read back to pinned host memory: the same K time steps as value"}
 
     # the plain FP64 form on the same workload, for the mixed/FP64 ratio
     fp64 = None

@@ -163,8 +163,10 @@ int ac_set_image(ac_ctx *ctx, const float *rgb, int is_device);
 int ac_set_image_f64(ac_ctx *ctx, const double *rgb, int is_device);
 
 /* Advance n_steps >= 0 time steps (Sec. 3.2).  out (nullable) receives the
- * statistics of the call.  Returns AC_ERR_NOT_CONVERGED if some step hit
- * max_cycles (all steps are still taken), AC_ERR_NUMERIC on NaN/Inf. */
+ * statistics of the call; the energy it reports is evaluated for the last
+ * step only when out is not NULL (about one extra read of u and the
+ * moments).  Returns AC_ERR_NOT_CONVERGED if some step hit max_cycles (all
+ * steps are still taken), AC_ERR_NUMERIC on NaN/Inf. */
 int ac_step(ac_ctx *ctx, int n_steps, ac_stats *out);
 
 /* ac_step(n_steps), then write the rounded composite (Sec. 4.3): the pixel

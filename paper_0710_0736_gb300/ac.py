@@ -203,11 +203,13 @@ def ac_step(ctx, n_steps, allow_not_converged=False):
     return rc, st
 
 
-def ac_segment(ctx, n_steps, labels, W, H, allow_not_converged=False):
+def ac_segment(ctx, n_steps, labels, W, H, allow_not_converged=False, stats=True):
+    """stats=False passes no statistics struct: the library then skips the
+    energy evaluation of the last step (st is returned as None)."""
     ptr, dev = _buf(labels, np.int8, W * H, writable=True)
-    st = ac_stats()
+    st = ac_stats() if stats else None
     ok = (AC_OK, AC_ERR_NOT_CONVERGED) if allow_not_converged else (AC_OK,)
-    rc = _check(lib.ac_segment(ctx, n_steps, ptr, dev, C.byref(st)), ok)
+    rc = _check(lib.ac_segment(ctx, n_steps, ptr, dev, C.byref(st) if stats else None), ok)
     return rc, st
 
 

@@ -640,15 +640,19 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
       // correction; the last writes its colour's mask (and rt = 0)
       const double sm_bytes = 2.0 * nsw * bm.smooth_launch() + (corr && nsw > 0 ? 0.5 * bm.n * bm.ns : 0.0) +
                               (fused ? 0.5 * bm.n * (1.0 + (rt_zero ? bm.ns : 0.0)) : 0.0);
+      // mask changes mark the first coarse level's tiles (whatever its form)
+      const ac::MaskDirty dirty = S.lv.size() > 1
+                                      ? ac::MaskDirty{S.lv[1].lists.dirty, ac::tiles_x(S.lv[1].g), ac::tiles_y(S.lv[1].g)}
+                                      : ac::MaskDirty{nullptr, 0, 0};
       AC_RUNB(AC_PROF_SMOOTH, sm_bytes, o->smooth(S.x, S.rhs, S.ob, corr, ctx->omega, g0, nsw, rt_zero,
-                                                  fused ? S.mask : nullptr, ctx->s));
+                                                  fused ? S.mask : nullptr, dirty, ctx->s));
       AC_CUDA(cudaMemsetAsync(ctx->rho, 0, 2 * sizeof(double), ctx->s));  // rho and the free-node count
       // residual at the visited nodes: x (their own and, for one colour, the
       // other colour's as neighbours), rhs, obstacle read, rt and the mask
       // byte written
       const double rs_bytes = fused ? 0.5 * bm.n * (bm.ns * (4 + bm.ob) + 1) : bm.n * (bm.ns * (3 + bm.ob) + 1);
       AC_RUNB(AC_PROF_RESID, rs_bytes,
-              o->resid(S.x, S.rhs, S.ob, g0, S.rt, S.mask, ctx->rho, fused ? 0 : -1, ctx->s));
+              o->resid(S.x, S.rhs, S.ob, g0, S.rt, S.mask, ctx->rho, fused ? 0 : -1, dirty, ctx->s));
       return AC_OK;
     });
     if (rc) return rc;
@@ -673,9 +677,12 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
     const double free_frac = (double)nfree * (nsw >= 1 ? 2.0 : 1.0) / (double)S.lv[0].n;
     S.tiled = tiled_end(S) > 1 && (S.tiling == AC_TILES_ALWAYS || free_frac < kTiledFreeFraction);
     if (S.tiled && !S.was_tiled) {
-      // the flags are stale: let this correction write every tile (kLiveNow)
-      for (int k = 1; k < tiled_end(S); ++k)
+      // the flags are stale: let this correction compute and write every
+      // tile (kLiveNow), whatever the mask changes since the last one
+      for (int k = 1; k < tiled_end(S); ++k) {
         AC_CUDA(cudaMemsetAsync(S.lv[k].lists.flags, ac::kLiveNow, tile_flag_bytes(S.lv[k].g, ctx->N), ctx->s));
+        AC_CUDA(cudaMemsetAsync(S.lv[k].lists.dirty, 1, tile_flag_bytes(S.lv[k].g, 1), ctx->s));
+      }
     }
     S.was_tiled = S.tiled;
     rc = run_graph(ctx, S.correction[prof][S.tiled ? 1 : 0], [&]() -> int {
@@ -1079,6 +1086,9 @@ int ac_create(ac_ctx **out, const ac_params *p) {
       AC_ALLOC(L.lists.flags, nt * N);
       AC_ALLOC(L.lists.items, nt * N * sizeof(uint64_t));
       AC_ALLOC(L.lists.tiles, nt * sizeof(uint64_t));
+      AC_ALLOC(L.lists.dirty, nt);
+      AC_ALLOC(L.lists.changed, nt);
+      AC_CUDA(cudaMemsetAsync(L.lists.dirty, 1, nt, ctx->s));
       L.lists.count = S.list_counts + 2 * k;
       L.lists.cap = (int64_t)nt * N;
       L.lists.sms = ctx->sms;
@@ -1419,7 +1429,8 @@ int ac_residual(ac_ctx *ctx, double *rho) {
            ctx->ops->outer_resid(ctx->u, (const float *)ctx->b, ctx->g0, ctx->r32, ctx->u32, ctx->rho, false, ctx->s));
   else
     AC_RUN(AC_PROF_RESID,
-           ctx->ops->fp64.resid(ctx->u, ctx->b, nullptr, ctx->g0, nullptr, nullptr, ctx->rho, -1, ctx->s));
+           ctx->ops->fp64.resid(ctx->u, ctx->b, nullptr, ctx->g0, nullptr, nullptr, ctx->rho, -1,
+                                ac::MaskDirty{nullptr, 0, 0}, ctx->s));
   return read_rho(ctx, rho);
 }
 
@@ -1580,6 +1591,9 @@ int adj_setup(ac_ctx *ctx, int T, int every) {
     ADJ_ALLOC(L.lists.flags, nt * N);
     ADJ_ALLOC(L.lists.items, nt * N * sizeof(uint64_t));
     ADJ_ALLOC(L.lists.tiles, nt * sizeof(uint64_t));
+    ADJ_ALLOC(L.lists.dirty, nt);
+    ADJ_ALLOC(L.lists.changed, nt);
+    AC_CUDA(cudaMemsetAsync(L.lists.dirty, 1, nt, ctx->s));
     L.lists.count = S.list_counts + 2 * k;
     L.lists.cap = (int64_t)nt * N;
     L.lists.sms = ctx->sms;
@@ -1855,8 +1869,10 @@ void set_schedule(ac_ctx *ctx, int nu1, int nu2, int depth) {
   ctx->sv.was_tiled = false;
   // the tiled levels may change with the depth: let the next cycle write
   // every tile of every level again (see kLiveNow)
-  for (int k = 1; k < L; ++k)
+  for (int k = 1; k < L; ++k) {
     cudaMemsetAsync(ctx->sv.lv[k].lists.flags, ac::kLiveNow, tile_flag_bytes(ctx->sv.lv[k].g, ctx->N), ctx->s);
+    cudaMemsetAsync(ctx->sv.lv[k].lists.dirty, 1, tile_flag_bytes(ctx->sv.lv[k].g, 1), ctx->s);
+  }
 }
 
 }  // namespace

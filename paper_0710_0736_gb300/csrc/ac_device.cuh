@@ -59,6 +59,26 @@ __device__ __forceinline__ uint8_t tile_flag(const uint8_t *__restrict__ tf, con
   return __ldg(tf + ((int64_t)i * tiles_y(g) + y / kJ2Y) * tiles_x(g) + x / kJ2X);
 }
 
+// Changes of the fine free mask, for the first coarse level's operator: it
+// depends on the fine masks in the 6x6-node boxes of its nodes only, so a
+// first-level tile whose boxes saw no change keeps its operator.  The kernels
+// that write the mask set p[ty * tx + tx'] for every first-level tile whose
+// boxes hold a node whose mask byte changed (fine x in [2 kJ2X tx - 2,
+// 2 kJ2X tx + 2 kJ2X + 1], y alike); the first level's Galerkin kernel
+// clears them.  p == null: no tracking.
+struct MaskDirty {
+  uint8_t *p;
+  int tx, ty;  // tiles of the first coarse level
+};
+
+__device__ __forceinline__ void mark_dirty(const MaskDirty &d, int x, int y) {
+  constexpr int SX = 2 * kJ2X, SY = 2 * kJ2Y;  // fine nodes per tile
+  const int x0 = x - (SX + 1) <= 0 ? 0 : (x - (SX + 1) + SX - 1) / SX, x1 = min(d.tx - 1, (x + 2) / SX);
+  const int y0 = y - (SY + 1) <= 0 ? 0 : (y - (SY + 1) + SY - 1) / SY, y1 = min(d.ty - 1, (y + 2) / SY);
+  for (int ty = y0; ty <= y1; ++ty)
+    for (int tx = x0; tx <= x1; ++tx) d.p[(int64_t)ty * d.tx + tx] = 1;
+}
+
 // te, S_nn, 1/S_nn in a kernel's scalar type.
 template <typename T>
 __host__ __device__ __forceinline__ T geo_te(const Geo &g) {

@@ -816,11 +816,14 @@ template <typename T, int N, int FORM, bool MASK>
 __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const T *__restrict__ rhs,
                                                         const T *__restrict__ ob, const T *__restrict__ corr,
                                                         const double *__restrict__ omega, Geo g, int color,
-                                                        T *__restrict__ rt, uint8_t *__restrict__ mask) {
+                                                        T *__restrict__ rt, uint8_t *__restrict__ mask,
+                                                        MaskDirty dirty) {
   const int y = blockIdx.y;
   const int xx = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((y + color) & 1);
   if (xx > g.W) return;
   const int64_t n = fslot<T>(g, xx, y);
+  // the mask byte this pass replaces, loaded first so its latency overlaps
+  const uint8_t old_mask = (MASK && dirty.p) ? mask[(int64_t)y * g.Wn + xx] : (uint8_t)0;
   T acc[N], bk[N], o[N];
   nbr_sum<T, N>(x, g, xx, y, acc);
   if (corr) {
@@ -855,7 +858,9 @@ __global__ void __launch_bounds__(kBlock) k_smooth_fine(T *__restrict__ x, const
         ++cnt;
       }
     }
-    mask[(int64_t)y * g.Wn + xx] = (uint8_t)(cnt >= 2 ? pos : 0u);
+    const uint8_t nm = (uint8_t)(cnt >= 2 ? pos : 0u);
+    if (dirty.p && old_mask != nm) mark_dirty(dirty, xx, y);
+    mask[(int64_t)y * g.Wn + xx] = nm;
     if (rt) {
       T z[N];
 #pragma unroll
@@ -879,7 +884,7 @@ template <typename T, int N, int FORM>
 __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, const T *__restrict__ rhs,
                                                        const T *__restrict__ ob, Geo g, T *__restrict__ rt,
                                                        uint8_t *__restrict__ mask, double *__restrict__ rho,
-                                                       int color) {
+                                                       int color, MaskDirty dirty) {
   // color < 0: every node; color 0 or 1: the nodes of that colour only (the
   // other colour's share was stored by the last smoothing pass)
   const int y = blockIdx.y;
@@ -889,6 +894,8 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
   int nfree = 0;
   if (xx <= g.W) {
     const int64_t n = (int64_t)y * g.Wn + xx, sl = fslot<T>(g, xx, y);
+    // the mask byte this kernel replaces, loaded first so its latency overlaps
+    const uint8_t old_mask = (rt && dirty.p) ? mask[n] : (uint8_t)0;
     T acc[N], xk[N], bk[N], r[N], o[N];
     nbr_sum<T, N>(x, g, xx, y, acc);
     ldn<T, N>(x + sl * N, xk);
@@ -928,6 +935,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_resid(const T *__restrict__ x, 
 #pragma unroll
       for (int i = 0; i < N; ++i) r[i] = ((fr >> i) & 1u) ? r[i] - mean : T(0);
       stn<T, N>(rt + sl * N, r);
+      if (dirty.p && old_mask != (uint8_t)fr) mark_dirty(dirty, xx, y);
       mask[n] = (uint8_t)fr;
     }
   }
@@ -1231,15 +1239,53 @@ __device__ __forceinline__ void galerkin0_node(const unsigned (&pk)[6][2], unsig
 // The tiles of the first level are also appended to its lists: each (tile,
 // phase) live or dying to items, and each tile with phases to write to tiles
 // as tile | now << 32 | written << 40 (phase masks).
+// A tile whose boxes saw no mask change since its last computation (dirty
+// byte clear) keeps its operator and its live phases: only its flags and list
+// entries are renewed.  changed[tile] tells the next level whether the
+// tile's operator was rewritten this cycle.
 template <typename T, int N>
 __global__ void __launch_bounds__(kTileThreads) k_galerkin0(const uint8_t *__restrict__ mask, Geo gf, Geo gc,
                                                             Galerkin0Table tab, T *__restrict__ op,
                                                             uint8_t *__restrict__ tf, uint64_t *__restrict__ items,
-                                                            uint64_t *__restrict__ tiles, int *__restrict__ count) {
+                                                            uint64_t *__restrict__ tiles, int *__restrict__ count,
+                                                            uint8_t *__restrict__ dirty,
+                                                            uint8_t *__restrict__ changed) {
   __shared__ unsigned s_now, s_prev;
-  __shared__ int s_base;
+  __shared__ int s_base, s_dirty;
   unsigned wmask = (1u << N) - 1u;
   if (tf) {
+    const int64_t tile = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    if (threadIdx.x == 0) s_dirty = dirty[tile];
+    __syncthreads();
+    if (!s_dirty) {
+      // the operator stands: the phases live before stay live (one lane per
+      // phase of the first warp)
+      if (threadIdx.x < 32u) {
+        const unsigned lane = threadIdx.x;
+        unsigned live = 0u;
+        uint8_t *f = tf + ((int64_t)lane * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        if (lane < (unsigned)N) {
+          live = *f & kLiveNow;
+          *f = (uint8_t)(live ? (kLiveNow | kLivePrev) : 0u);
+        }
+        const unsigned now = __ballot_sync(0xffffffffu, live != 0u);
+        if (now) {
+          int base = 0;
+          if (lane == 0) {
+            base = atomicAdd(count, __popc(now));
+            tiles[atomicAdd(count + 1, 1)] = (uint64_t)tile | ((uint64_t)now << 32) | ((uint64_t)now << 40);
+          }
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (live) items[base + __popc(now & ((1u << lane) - 1u))] = tile_item(tile, (int)lane, false);
+        }
+        if (lane == 0) changed[tile] = 0;
+      }
+      return;
+    }
+    if (threadIdx.x == 0) {
+      dirty[tile] = 0;
+      changed[tile] = 1;
+    }
     if (threadIdx.x == 0) s_now = s_prev = 0u;
     __syncthreads();
     // fine nodes 2X - 2 .. 2X + 3 over the tile's X range (rows alike), a
@@ -1260,7 +1306,6 @@ __global__ void __launch_bounds__(kTileThreads) k_galerkin0(const uint8_t *__res
     a = __reduce_or_sync(0xffffffffu, a);
     if ((threadIdx.x & 31u) == 0u && a) atomicOr(&s_now, a);
     __syncthreads();
-    const int64_t tile = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
     if (threadIdx.x < (unsigned)N) {
       uint8_t *f = tf + ((int64_t)threadIdx.x * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
       const unsigned old = *f, now = (s_now >> threadIdx.x) & 1u;
@@ -1392,28 +1437,52 @@ __global__ void __launch_bounds__(kBlock) k_galerkin(const T *__restrict__ opf, 
 // The fine tiles under the coarse tile and its one-node halo are looked up
 // first: if none is live for the phase, no coarse row of the tile can be
 // nonzero and no fine operator entry is read.
+// With changed_f (whether each fine tile's operator was rewritten this
+// cycle) a coarse tile over fine tiles that all kept theirs keeps its own
+// operator and live phases; changed_c records the same for this level.
 template <typename T, int N>
 __global__ void __launch_bounds__(kTileThreads) k_galerkin_tiled(const T *__restrict__ opf, Geo gf, Geo gc,
                                                                  T *__restrict__ opc, const uint8_t *__restrict__ tff,
                                                                  uint8_t *__restrict__ tfc, uint64_t *__restrict__ items,
-                                                                 int *__restrict__ count) {
-  __shared__ int s_fine;
+                                                                 int *__restrict__ count,
+                                                                 const uint8_t *__restrict__ changed_f,
+                                                                 uint8_t *__restrict__ changed_c) {
+  __shared__ int s_fine, s_changed;
   __shared__ unsigned s_prev;
   const int i = blockIdx.z;
   const int64_t nf = (int64_t)gf.Wn * (gf.H + 1), nc = (int64_t)gc.Wn * (gc.H + 1);
   {
     // fine nodes 2X - 1 .. 2X + 1 over the tile's X range (rows alike): fine
     // tiles 2 tx - 1 .. 2 tx + 1 (ty alike), one flag per thread of the first 9
-    bool f = false;
+    bool f = false, c = false;
     if (threadIdx.x < 9u) {
       const int fx = 2 * (int)blockIdx.x - 1 + (int)(threadIdx.x % 3u), fy = 2 * (int)blockIdx.y - 1 + (int)(threadIdx.x / 3u);
-      if (fx >= 0 && fx < tiles_x(gf) && fy >= 0 && fy < tiles_y(gf))
+      if (fx >= 0 && fx < tiles_x(gf) && fy >= 0 && fy < tiles_y(gf)) {
         f = (tff[((int64_t)i * tiles_y(gf) + fy) * tiles_x(gf) + fx] & kLiveNow) != 0;
+        c = changed_f[(int64_t)fy * tiles_x(gf) + fx] != 0;
+      }
     }
     const int any = __syncthreads_or(f);
-    if (threadIdx.x == 0) s_fine = any;
+    const int chg = __syncthreads_or(c);
+    if (threadIdx.x == 0) {
+      s_fine = any;
+      s_changed = chg;
+    }
   }
   __syncthreads();
+  const int64_t tile = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+  if (!s_changed) {
+    // the fine operator under the tile stands, and so does this one
+    if (threadIdx.x == 0) {
+      uint8_t *f = tfc + ((int64_t)i * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      const unsigned live = *f & kLiveNow;
+      *f = (uint8_t)(live ? (kLiveNow | kLivePrev) : 0u);
+      if (live) items[atomicAdd(count, 1)] = tile_item(tile, i, false);
+      if (changed_c && i == 0) changed_c[tile] = 0;
+    }
+    return;
+  }
+  if (changed_c && threadIdx.x == 0 && i == 0) changed_c[tile] = 1;
   // the rows of this thread: a row is live when a fine row under its hat is
   unsigned live = 0u;
   const int X = blockIdx.x * kJ2X + (int)(threadIdx.x % kJ2X);

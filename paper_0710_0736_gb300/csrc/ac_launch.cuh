@@ -61,26 +61,26 @@ struct SolverLaunch {
   // With mask != null the last launch (colour 1) also stores its nodes' free
   // mask (and rt = 0 if rt != null), so that resid(color = 0) completes them.
   static int smooth(void *x, const void *rhs, const void *ob, const void *corr, const double *omega, const Geo &g,
-                    int sweeps, void *rt, uint8_t *mask, cudaStream_t s) {
+                    int sweeps, void *rt, uint8_t *mask, const MaskDirty &dirty, cudaStream_t s) {
     const dim3 grid = row_grid((g.W + 2) / 2, g.H + 1);
     for (int k = 0; k < sweeps; ++k)
       for (int c = 0; c < 2; ++c) {
         const T *cr = k == 0 && c == 0 ? (const T *)corr : nullptr;
         if (mask && k == sweeps - 1 && c == 1)
           k_smooth_fine<T, N, FORM, true><<<grid, kBlock, 0, s>>>((T *)x, (const T *)rhs, (const T *)ob, cr, omega,
-                                                                g, c, (T *)rt, mask);
+                                                                g, c, (T *)rt, mask, dirty);
         else
           k_smooth_fine<T, N, FORM, false><<<grid, kBlock, 0, s>>>((T *)x, (const T *)rhs, (const T *)ob, cr, omega,
-                                                                 g, c, nullptr, nullptr);
+                                                                 g, c, nullptr, nullptr, MaskDirty{nullptr, 0, 0});
       }
     return 2 * sweeps;
   }
   // color < 0: every node; 0: the first colour only (after smooth() with a mask)
   static int resid(const void *x, const void *rhs, const void *ob, const Geo &g, void *rt, uint8_t *mask,
-                   double *rho, int color, cudaStream_t s) {
+                   double *rho, int color, const MaskDirty &dirty, cudaStream_t s) {
     const dim3 grid = color < 0 ? row_grid(g.W + 1, g.H + 1) : row_grid((g.W + 2) / 2, g.H + 1);
     k_fine_resid<T, N, FORM><<<grid, kBlock, 0, s>>>((const T *)x, (const T *)rhs, (const T *)ob, g, (T *)rt, mask,
-                                                   rho, color);
+                                                   rho, color, dirty);
     return 1;
   }
   static int restrict0(const void *rt, const Geo &gf, const Geo &gc, const void *op1, void *r1, const LevelLists *L1,
@@ -96,7 +96,8 @@ struct SolverLaunch {
     const dim3 grid((unsigned)tiles_x(gc), (unsigned)tiles_y(gc));
     k_galerkin0<T, N><<<grid, kTileThreads, 0, s>>>(mask, gf, gc, tab, (T *)op, L1 ? L1->flags : nullptr,
                                                   L1 ? L1->items : nullptr, L1 ? L1->tiles : nullptr,
-                                                  L1 ? L1->count : nullptr);
+                                                  L1 ? L1->count : nullptr, L1 ? L1->dirty : nullptr,
+                                                  L1 ? L1->changed : nullptr);
     return 1;
   }
   static int galerkin(const void *opf, const Geo &gf, const Geo &gc, void *opc, const LevelLists *Lf,
@@ -104,7 +105,7 @@ struct SolverLaunch {
     if (Lc) {
       const dim3 grid((unsigned)tiles_x(gc), (unsigned)tiles_y(gc), (unsigned)N);
       k_galerkin_tiled<T, N><<<grid, kTileThreads, 0, s>>>((const T *)opf, gf, gc, (T *)opc, Lf->flags, Lc->flags,
-                                                         Lc->items, Lc->count);
+                                                         Lc->items, Lc->count, Lf->changed, Lc->changed);
     } else {
       const PhaseLaunch L = phase_grid(gc.W + 1, gc.H + 1, N);
       k_galerkin<T, N><<<L.grid, L.block, 0, s>>>((const T *)opf, gf, gc, (T *)opc);

@@ -9,6 +9,7 @@ namespace ac {
 
 struct Geo;
 struct Galerkin0Table;
+struct MaskDirty;
 
 // Scratch of the block-partial reductions: at most kMaxPartBlocks rows.
 constexpr int kMaxPartBlocks = 1024;
@@ -37,6 +38,8 @@ struct LevelLists {
   uint8_t *flags;
   uint64_t *items;
   uint64_t *tiles;
+  uint8_t *dirty;    // per tile: the fine mask under it changed since its operator was computed (first level)
+  uint8_t *changed;  // per tile: its operator was rewritten in this cycle's correction
   int *count;  // [0] items, [1] tiles
   int64_t cap; // tiles x phases
   int sms;
@@ -50,11 +53,12 @@ struct SolverOps {
   // correction x += (*omega) corr is applied inside the first launch; with
   // mask != null the last launch stores its colour's free mask (and rt = 0
   // for that colour if rt != null)
+  // (dirty: the first coarse level's tiles to mark where the mask changes)
   int (*smooth)(void *x, const void *rhs, const void *ob, const void *corr, const double *omega, const Geo &g,
-                int sweeps, void *rt, uint8_t *mask, cudaStream_t s);
+                int sweeps, void *rt, uint8_t *mask, const MaskDirty &dirty, cudaStream_t s);
   // color < 0: every node; 0: the first colour only (completes a masked smooth)
   int (*resid)(const void *x, const void *rhs, const void *ob, const Geo &g, void *rt, uint8_t *mask, double *rho,
-               int color, cudaStream_t s);
+               int color, const MaskDirty &dirty, cudaStream_t s);
   // transfers skip the rows whose diagonal in the (coarse or fine) level's
   // operator is 0: those rows and their residuals are exactly 0.  LevelLists
   // arguments: the live-tile state of a tiled level, or null for a level
