@@ -368,6 +368,26 @@ def batch_leg(args, steps, warmup, fp64_steps):
                 "streams": streams, "vcycles_per_image_step": s64.total_cycles / (s64.images * fp64_steps),
                 "all_converged": s64.converged_images == s64.images}
 
+    # the same batch with one graph launch per time step: every image's step
+    # (its V-cycle loop on the device) in one CUDA graph
+    b = make(ac.AC_MIXED, args.streams)
+    if not args.no_tune:
+        b.tune(trial_steps=2)
+    b.set_launch(ac.AC_BATCH_ONE_GRAPH)
+    b.step(warmup, allow_not_converged=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sg = b.step(steps, allow_not_converged=True)
+    torch.cuda.synchronize()
+    el_g = time.perf_counter() - t0
+    b.close()
+    one_graph = {"value": sg.images * steps / el_g, "unit": "image-steps/s", "steps": steps,
+                 "ms_per_step": el_g / steps * 1e3,
+                 "vcycles_per_image_step": sg.total_cycles / (sg.images * steps),
+                 "all_converged": sg.converged_images == sg.images,
+                 "launch": "one CUDA graph per time step holding every image's step, each image's V-cycle and "
+                           "defect-correction loops under device-side WHILE nodes (AC_BATCH_ONE_GRAPH)",
+                 "ratio_over_stream_pool": (sg.images * steps / el_g) / value}
     pooled = fp64_rate(args.streams)
     unbatched = fp64_rate(1)
     pooled["ratio_batched_mixed_over_this"] = value / pooled["value"]
@@ -388,6 +408,9 @@ def batch_leg(args, steps, warmup, fp64_steps):
             "gdof_per_s": st.dof_sweeps / el / 1e9,
             "vcycles_per_image_step": st.total_cycles / (st.images * steps),
             "all_converged": st.converged_images == st.images, "tune_seconds": t_tune, "clocks": clk,
+            "launch": f"stream pool: {args.streams} streams, one host worker thread per stream, each image's "
+                      "V-cycle loop on the host (AC_BATCH_STREAMS)",
+            "one_graph": one_graph,
             "plain_fp64_gpu_same_pool": pooled, "plain_fp64_gpu_unbatched": unbatched,
             "ratio_mixed_over_fp64": value / unbatched["value"]}
 

@@ -238,6 +238,30 @@ int ac_project_simplex(const double *y, double *x, int64_t count, int n_phases, 
 enum { AC_TILES_AUTO = 0, AC_TILES_NEVER = 1, AC_TILES_ALWAYS = 2 };
 int ac_set_coarse_tiling(ac_ctx *ctx, int mode);
 
+/* ---- where the V-cycle loop runs (no counterpart in the paper) ----------- */
+
+/* The cycles of a time step repeat until the natural residual reaches tol
+ * (Sec. 3.2); a defect-correction pass (AC_MIXED) repeats until the outer
+ * residual does.  Those tests can run on the host, which reads rho back
+ * after every cycle, or on the device: the whole time step is then one CUDA
+ * graph whose WHILE nodes loop over the cycles and passes, with their
+ * conditions set by one-thread kernels from rho, and ac_step synchronises
+ * once per call.  Both run the same kernels with the same arguments, so the
+ * results are bit-identical.
+ *   AC_LOOP_AUTO (default): on the device whenever the context can -- it
+ *     has a stream (the legacy default stream cannot be captured), profiling
+ *     is off (a profiled cycle brackets its kernels with events, which a
+ *     conditional body cannot hold), and no coarse level can run tiled
+ *     (ac_set_coarse_tiling; with AC_TILES_AUTO that is every image whose
+ *     coarse levels are too small for tiles, e.g. 1024^2 and below at N <= 8)
+ *     -- and on the host otherwise;
+ *   AC_LOOP_HOST: always on the host.
+ * ac_get_cycle_loop sets *on_device to 1 if the next ac_step runs the loop on
+ * the device.  AC_ERR_ARG for a NULL context or an unknown mode. */
+enum { AC_LOOP_AUTO = 0, AC_LOOP_HOST = 1 };
+int ac_set_cycle_loop(ac_ctx *ctx, int mode);
+int ac_get_cycle_loop(ac_ctx *ctx, int *on_device);
+
 /* ---- instrumentation (no counterpart in the paper) ------------------------ */
 
 /* Turn per-class kernel timing on (1) or off (0) and clear the accumulated
@@ -329,6 +353,25 @@ int ac_batch_step(ac_batch *b, int n_steps, ac_batch_stats *out);
  * count x 3 ints) receives nu1, nu2 and depth per image.  Every image needs
  * its image set first. */
 int ac_batch_tune(ac_batch *b, int trial_steps, int *chosen);
+/* How ac_batch_step launches the images' work.
+ *   AC_BATCH_STREAMS (default): one host worker thread per stream advances
+ *     its images one after the other (ac_step on each image's own stream);
+ *   AC_BATCH_ONE_GRAPH: one CUDA graph holds a time step of every image --
+ *     each image an independent chain with its V-cycle loop on the device
+ *     (see ac_set_cycle_loop), whatever the images' own loop setting -- and
+ *     is launched once per time step on the first stream, with one
+ *     synchronisation per call.  Needs every image able to run its loop on
+ *     the device: no coarse level that can run tiled (AC_ERR_STATE from
+ *     ac_batch_step otherwise).  The graph is captured on the first
+ *     ac_batch_step and again after ac_batch_tune.
+ * Both give every image the results of a single-image context, bit for bit.
+ * The images of a batch start with AC_LOOP_HOST (ac_batch_set_cycle_loop
+ * changes it): in the stream pool the host loop measured faster.
+ * AC_ERR_ARG for a NULL batch or an unknown mode. */
+enum { AC_BATCH_STREAMS = 0, AC_BATCH_ONE_GRAPH = 1 };
+int ac_batch_set_launch(ac_batch *b, int mode);
+/* ac_set_cycle_loop on every image of the batch. */
+int ac_batch_set_cycle_loop(ac_batch *b, int mode);
 /* Free the batch (NULL is accepted). */
 void ac_batch_destroy(ac_batch *b);
 

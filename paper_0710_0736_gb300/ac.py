@@ -18,6 +18,8 @@ AC_OK, AC_ERR_ARG, AC_ERR_CUDA, AC_ERR_NOT_CONVERGED, AC_ERR_NUMERIC, AC_ERR_STA
 AC_FP64, AC_MIXED = 0, 1
 AC_PROJ_SIMPLEX, AC_PROJ_NODE = 0, 1
 AC_TILES_AUTO, AC_TILES_NEVER, AC_TILES_ALWAYS = 0, 1, 2
+AC_LOOP_AUTO, AC_LOOP_HOST = 0, 1
+AC_BATCH_STREAMS, AC_BATCH_ONE_GRAPH = 0, 1
 AC_MAX_PHASES = 8
 
 EXPORTS = [
@@ -26,7 +28,8 @@ EXPORTS = [
     "ac_get_composite", "ac_energy", "ac_residual", "ac_project_simplex", "ac_set_profiling", "ac_set_profiling_mask", "ac_get_profile", "ac_colour_means_static",
     "ac_batch_create", "ac_batch_set_image", "ac_batch_set_phase", "ac_batch_get_phase", "ac_batch_segment",
     "ac_batch_step", "ac_batch_tune", "ac_batch_destroy", "ac_adjoint_forward", "ac_adjoint_backward",
-    "ac_adjoint_recompute_diff", "ac_set_coarse_tiling", "ac_last_error",
+    "ac_adjoint_recompute_diff", "ac_set_coarse_tiling", "ac_set_cycle_loop", "ac_get_cycle_loop",
+    "ac_batch_set_launch", "ac_batch_set_cycle_loop", "ac_last_error",
 ]
 PROF_CLASSES = ["smooth", "resid", "coarse", "transfer", "linesearch", "setup", "outer"]
 
@@ -118,6 +121,10 @@ def _load():
         "ac_adjoint_backward": ([vp, vp, P(d), P(d), vp, vp], i),
         "ac_adjoint_recompute_diff": ([vp, P(i64)], i),
         "ac_set_coarse_tiling": ([vp, i], i),
+        "ac_set_cycle_loop": ([vp, i], i),
+        "ac_get_cycle_loop": ([vp, P(i)], i),
+        "ac_batch_set_launch": ([vp, i], i),
+        "ac_batch_set_cycle_loop": ([vp, i], i),
         "ac_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -354,6 +361,19 @@ def ac_set_coarse_tiling(ctx, mode):
     return _check(lib.ac_set_coarse_tiling(ctx, mode))
 
 
+def ac_set_cycle_loop(ctx, mode):
+    """AC_LOOP_AUTO (the V-cycle loop on the device where the context allows)
+    or AC_LOOP_HOST (see include/ac.h)."""
+    return _check(lib.ac_set_cycle_loop(ctx, mode))
+
+
+def ac_get_cycle_loop(ctx) -> bool:
+    """True if the next ac_step runs its cycle loop on the device."""
+    k = C.c_int()
+    _check(lib.ac_get_cycle_loop(ctx, C.byref(k)))
+    return bool(k.value)
+
+
 def ac_last_error() -> str:
     return lib.ac_last_error().decode()
 
@@ -424,6 +444,12 @@ class Segmenter:
         ac_get_composite(self.ctx, out, self.W, self.H, rounded)
         return out
 
+    def set_cycle_loop(self, mode):
+        return ac_set_cycle_loop(self.ctx, mode)
+
+    def loop_on_device(self):
+        return ac_get_cycle_loop(self.ctx)
+
     def energy(self):
         return ac_energy(self.ctx)
 
@@ -486,3 +512,10 @@ class Batch:
 
     def tune(self, trial_steps=2):
         return ac_batch_tune(self.b, len(self.specs), trial_steps)
+
+    def set_launch(self, mode):
+        """AC_BATCH_STREAMS or AC_BATCH_ONE_GRAPH (see include/ac.h)."""
+        return _check(lib.ac_batch_set_launch(self.b, mode))
+
+    def set_cycle_loop(self, mode):
+        return _check(lib.ac_batch_set_cycle_loop(self.b, mode))

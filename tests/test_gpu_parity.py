@@ -327,14 +327,20 @@ def test_graphs_match_direct_launches(ac, precision):
     W, H, N = 96, 64, 5
     img = synth.shapes_image(11, W, H, rect_side=(4, 30), disk_r=(3, 12))
     u0 = synth.dirichlet_init(12, (W + 1) * (H + 1), N)
+    import torch
     prec = ac.AC_MIXED if precision == "mixed" else ac.AC_FP64
     outs = []
-    for stream, prof in [(None, False), ("torch", False), ("torch", True)]:
-        kw = {} if stream == "torch" else {"stream": None}
+    side = torch.cuda.Stream()
+    for stream, prof in [(None, False), ("side", False), ("side", True)]:
+        kw = {"stream": side.cuda_stream if stream == "side" else None}
         seg = ac.Segmenter(W, H, N, 2.0, 1.0, 4.0, tol=1e-9, precision=prec, **kw)
         seg.set_image(img)
         seg.set_phase(u0)
         ac.ac_set_profiling(seg.ctx, prof)
+        # the V-cycle halves as graphs, with the host loop (the device-side
+        # loop has its own test)
+        ac.ac_set_cycle_loop(seg.ctx, ac.AC_LOOP_HOST)
+        assert not seg.loop_on_device()
         st = seg.step(4)
         outs.append(seg.phase())
         if prof:
@@ -342,6 +348,71 @@ def test_graphs_match_direct_launches(ac, precision):
             assert p["launches"]["smooth"] > 0 and p["ms"]["smooth"] > 0 and st.fine_sweeps > 0
         seg.close()
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+def _stream_seg(ac, W, H, N, stream, **kw):
+    return ac.Segmenter(W, H, N, 2.0, 1.0, 4.0, stream=stream.cuda_stream, **kw)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("W,H,N,nu1,nu2,max_cycles", [(96, 64, 5, 2, 1, 200), (37, 23, 3, 2, 2, 200),
+                                                      (1, 1, 2, 1, 1, 200), (64, 48, 4, 0, 2, 200),
+                                                      (128, 128, 8, 2, 1, 3)])
+def test_device_loop_matches_host_loop(ac, precision, W, H, N, nu1, nu2, max_cycles):
+    """The V-cycle loop run on the device (graph WHILE nodes, conditions set
+    from rho by one-thread kernels) takes the decisions of the host loop:
+    bit-identical fields, the same statistics and return codes -- also with
+    no coarse level (1 x 1), no pre-smoothing (no warm start), and a cycle
+    cap that stops every step unconverged."""
+    import torch
+    prec = ac.AC_MIXED if precision == "mixed" else ac.AC_FP64
+    img = synth.shapes_image(21, W, H, rect_side=(1, max(1, W // 3)), disk_r=(1, max(1.5, W / 5)))
+    u0 = synth.dirichlet_init(22, (W + 1) * (H + 1), N)
+    st = torch.cuda.Stream()
+    res = []
+    for mode in (ac.AC_LOOP_HOST, ac.AC_LOOP_AUTO):
+        seg = _stream_seg(ac, W, H, N, st, tol=1e-9, precision=prec, nu1=nu1, nu2=nu2, max_cycles=max_cycles)
+        seg.set_cycle_loop(mode)
+        assert seg.loop_on_device() == (mode == ac.AC_LOOP_AUTO)
+        seg.set_image(img)
+        seg.set_phase(u0)
+        stats = []
+        for n in (1, 3, 2):  # several calls: the warm start carries across them
+            rc, s = ac.ac_step(seg.ctx, n, allow_not_converged=True)
+            stats.append((rc, s.as_dict()))
+        res.append((seg.phase(), stats, seg.node_labels()))
+        seg.close()
+    (u_h, st_h, nl_h), (u_d, st_d, nl_d) = res
+    assert np.array_equal(u_h, u_d)
+    assert np.array_equal(nl_h, nl_d)
+    assert st_h == st_d
+    if max_cycles == 3:
+        assert all(rc == ac.AC_ERR_NOT_CONVERGED and s["converged"] == 0 for rc, s in st_d)
+
+
+def test_device_loop_eligibility(ac):
+    """The loop runs on the device only with a stream, profiling off and no
+    coarse level that can run tiled; the legacy default stream, profiling and
+    a tiled hierarchy keep it on the host."""
+    import torch
+    st = torch.cuda.Stream()
+    seg = _stream_seg(ac, 64, 64, 4, st)
+    assert seg.loop_on_device()
+    ac.ac_set_profiling(seg.ctx, True)
+    assert not seg.loop_on_device()
+    ac.ac_set_profiling(seg.ctx, False)
+    assert seg.loop_on_device()
+    seg.close()
+    seg = ac.Segmenter(64, 64, 4, 2.0, 1.0, 4.0, stream=None)
+    assert not seg.loop_on_device()
+    seg.close()
+    seg = _stream_seg(ac, 256, 256, 8, st)
+    assert seg.loop_on_device()  # AUTO: level 1 too small for tiles
+    ac.ac_set_coarse_tiling(seg.ctx, ac.AC_TILES_ALWAYS)
+    assert not seg.loop_on_device()
+    seg.close()
+    with pytest.raises(ac.AcError):
+        ac.ac_set_cycle_loop(None, ac.AC_LOOP_AUTO)
 
 
 def test_profiling_mask(ac):
@@ -857,6 +928,69 @@ def test_batch_matches_single_images(ac, precision):
         assert np.array_equal(b.phase(k), seg.phase()), f"image {k}"
         assert np.array_equal(b.labels(k), seg.segment(0))
         seg.close()
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_one_graph_matches_single_images(ac, precision):
+    """AC_BATCH_ONE_GRAPH: one graph launch per time step runs every image's
+    step with its cycle loop on the device.  Every image ends bit-identical to
+    the same image solved alone with the host loop, over two calls (the second
+    replays the captured graph and carries the warm start), after a retune
+    (the graph is captured again), and the statistics agree with the stream
+    pool's."""
+    specs = _batch_specs()
+    prec = ac.AC_MIXED if precision == "mixed" else ac.AC_FP64
+    for sp in specs:
+        sp.update(tol=1e-9, precision=prec)
+    imgs = [synth.shapes_image(7 + k, sp["W"], sp["H"], rect_side=(2, max(2, sp["W"] // 3)),
+                               disk_r=(1, max(1.5, sp["W"] / 5))) for k, sp in enumerate(specs)]
+    u0s = [synth.dirichlet_init(50 + k, (sp["W"] + 1) * (sp["H"] + 1), sp["N"]) for k, sp in enumerate(specs)]
+    runs = {}
+    for mode, loop in [("pool_host", ac.AC_LOOP_HOST), ("pool_dev", ac.AC_LOOP_AUTO), ("graph", ac.AC_LOOP_AUTO)]:
+        b = ac.Batch(specs, n_streams=3)
+        b.set_cycle_loop(loop)
+        if mode == "graph":
+            b.set_launch(ac.AC_BATCH_ONE_GRAPH)
+        for k in range(len(specs)):
+            b.set_image(k, imgs[k])
+            b.set_phase(k, u0s[k])
+        s1 = b.step(2).as_dict()
+        s2 = b.step(1).as_dict()
+        runs[mode] = ([b.phase(k) for k in range(len(specs))], s1, s2)
+        if mode == "graph":
+            b.tune(trial_steps=1)
+            assert b.step(1).converged_images == len(specs)
+        b.close()
+    for k, sp in enumerate(specs):
+        seg = ac.Segmenter(sp["W"], sp["H"], sp["N"], 2.0, 1.0, 4.0, tol=1e-9, precision=prec)
+        seg.set_image(imgs[k])
+        seg.set_phase(u0s[k])
+        seg.step(2)
+        seg.step(1)
+        for mode in runs:
+            assert np.array_equal(runs[mode][0][k], seg.phase()), f"{mode}, image {k}"
+        seg.close()
+    assert runs["graph"][1] == runs["pool_host"][1] == runs["pool_dev"][1]
+    assert runs["graph"][2] == runs["pool_host"][2] == runs["pool_dev"][2]
+    assert runs["graph"][1]["converged_images"] == len(specs)
+
+
+def test_batch_one_graph_rejects_tiled_images(ac):
+    """A 2048 x 1024, N = 8 image has a first coarse level large enough for
+    tiles, so its loop stays on the host and the one-graph launch refuses the
+    batch with AC_ERR_STATE; the stream pool still runs it."""
+    specs = [dict(W=64, H=64, N=4, tol=1e-6, precision=ac.AC_MIXED),
+             dict(W=2048, H=1024, N=8, tol=1e-6, precision=ac.AC_MIXED)]
+    b = ac.Batch(specs, n_streams=2)
+    for k, sp in enumerate(specs):
+        b.set_image(k, synth.shapes_image(k, sp["W"], sp["H"]))
+    b.set_launch(ac.AC_BATCH_ONE_GRAPH)
+    with pytest.raises(ac.AcError) as e:
+        b.step(1)
+    assert "-5" in str(e.value)
+    b.set_launch(ac.AC_BATCH_STREAMS)
+    assert b.step(1).converged_images == 2
     b.close()
 
 
