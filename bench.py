@@ -442,7 +442,10 @@ def adjoint_leg(args, steps, warmup, with_cpu):
     u0 = synth.dirichlet_init(1, (W + 1) * (H + 1), N)
     target = synth.voronoi_labels(2, W + 1, H + 1, n_seeds=6, n_labels=N)
     torch.cuda.set_device(0)
-    stream = torch.cuda.current_stream()
+    # a stream of its own: torch's default stream is the legacy stream (handle 0),
+    # on which the library cannot capture its CUDA graphs
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)  # torch's own work of this leg goes on the same stream
     dev = torch.device("cuda", 0)
     onehot = np.eye(N)[target.ravel().astype(int)]
     m0 = None
@@ -543,7 +546,10 @@ def run_refine(args):
     tol = args.tol if args.tol is not None else cfg["tol_mixed"]
     img = synth.config_image(name, 0)
     torch.cuda.set_device(0)
-    stream = torch.cuda.current_stream()
+    # a stream of its own: torch's default stream is the legacy stream (handle 0),
+    # on which the library cannot capture its CUDA graphs
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)  # torch's own work of this leg goes on the same stream
     seg = ac.Segmenter(W, H, N, cfg["eps"], cfg["lam"], cfg["tau"], tol=tol, max_cycles=1000, precision=ac.AC_MIXED,
                        refine=r, nu1=args.nu1, nu2=args.nu2, stream=stream.cuda_stream)
     seg.set_image(torch.from_numpy(img).cuda())
@@ -631,7 +637,10 @@ def main():
     n_nodes = (W + 1) * (H + 1)
     prec = ac.AC_FP64 if args.precision == "fp64" else ac.AC_MIXED
     img = synth.config_image(WORKLOAD, rank, W, H)
-    stream = torch.cuda.current_stream()
+    # a stream of its own: torch's default stream is the legacy stream (handle 0),
+    # on which the library cannot capture its CUDA graphs
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)  # torch's own work of this leg goes on the same stream
     proj = ac.AC_PROJ_NODE if args.projection == "node" else ac.AC_PROJ_SIMPLEX
     seg = ac.Segmenter(W, H, N, cfg["eps"], cfg["lam"], cfg["tau"], tol=cfg["tol"], max_cycles=1000, seed=rank,
                        precision=prec, stream=stream.cuda_stream, nu1=args.nu1, nu2=args.nu2, projection=proj)

@@ -238,6 +238,28 @@ int ac_project_simplex(const double *y, double *x, int64_t count, int n_phases, 
 enum { AC_TILES_AUTO = 0, AC_TILES_NEVER = 1, AC_TILES_ALWAYS = 2 };
 int ac_set_coarse_tiling(ac_ctx *ctx, int mode);
 
+/* ---- the coarse levels' smoother --------------------------------------- */
+
+/* The linear V-cycle on the coarse levels (Sec. 3.2: the coarse corrections
+ * of the multigrid) smooths each level twice before and twice after its
+ * coarse correction, in one launch per pair of sweeps over 32 x 16-node
+ * tiles staged in shared memory.
+ *   AC_SMOOTH_GS3 (default): Gauss-Seidel in three colours ((x + y) mod 3
+ *     colours the 7-point pattern of the coarse operators), forward then
+ *     backward; within a tile each update sees its neighbours' newest values,
+ *     across tiles the values at the launch (overlapping blocks);
+ *   AC_SMOOTH_JACOBI: l1-Jacobi, x += (r - S x) / sum_m |S_nm|, which
+ *     converges for any symmetric positive definite operator.
+ * The one-block bottom of the cycle runs the same kind of sweeps, and the
+ * coarsest level always takes Gauss-Seidel.  Every coarse correction goes
+ * through the feasible direction and the exact line search, so either
+ * smoother reaches the same minimiser; at 4096^2, N = 8 (mixed, tol 1e-6)
+ * Gauss-Seidel needs 8.65 V-cycles per step over the first 20 steps against
+ * 9.6, and 7.2 against 8.8 once the phases have separated.
+ * AC_ERR_ARG for a NULL context or an unknown mode. */
+enum { AC_SMOOTH_GS3 = 0, AC_SMOOTH_JACOBI = 1 };
+int ac_set_coarse_smoother(ac_ctx *ctx, int mode);
+
 /* ---- where the V-cycle loop runs (no counterpart in the paper) ----------- */
 
 /* The cycles of a time step repeat until the natural residual reaches tol
@@ -346,12 +368,13 @@ int ac_batch_segment(ac_batch *b, int k, int8_t *labels, int is_device);
  * error of any image (AC_ERR_NOT_CONVERGED only if nothing worse happened). */
 int ac_batch_step(ac_batch *b, int n_steps, ac_batch_stats *out);
 /* Autotuner: per group of images with equal size, N and model parameters,
- * time trial_steps steps of every candidate schedule -- (nu1, nu2) in
- * {(1,1),(2,1),(1,2),(2,2)} and multigrid depth in {all levels, 5} -- on the
- * group's first image (its state is restored after each trial) and give the
- * whole group the fastest candidate that converged.  chosen (nullable,
- * count x 3 ints) receives nu1, nu2 and depth per image.  Every image needs
- * its image set first. */
+ * time trial_steps steps of every candidate schedule -- the coarse smoother
+ * (AC_SMOOTH_GS3, AC_SMOOTH_JACOBI: the colouring of the coarse sweeps),
+ * (nu1, nu2) in {(1,1),(2,1),(1,2),(2,2)} and multigrid depth in {all levels,
+ * 5} -- on the group's first image (its state is restored after each trial)
+ * and give the whole group the fastest candidate that converged.  chosen
+ * (nullable, count x 4 ints) receives nu1, nu2, depth and the coarse smoother
+ * per image.  Every image needs its image set first. */
 int ac_batch_tune(ac_batch *b, int trial_steps, int *chosen);
 /* How ac_batch_step launches the images' work.
  *   AC_BATCH_STREAMS (default): one host worker thread per stream advances

@@ -19,6 +19,7 @@ AC_FP64, AC_MIXED = 0, 1
 AC_PROJ_SIMPLEX, AC_PROJ_NODE = 0, 1
 AC_TILES_AUTO, AC_TILES_NEVER, AC_TILES_ALWAYS = 0, 1, 2
 AC_LOOP_AUTO, AC_LOOP_HOST = 0, 1
+AC_SMOOTH_GS3, AC_SMOOTH_JACOBI = 0, 1
 AC_BATCH_STREAMS, AC_BATCH_ONE_GRAPH = 0, 1
 AC_MAX_PHASES = 8
 
@@ -28,7 +29,7 @@ EXPORTS = [
     "ac_get_composite", "ac_energy", "ac_residual", "ac_project_simplex", "ac_set_profiling", "ac_set_profiling_mask", "ac_get_profile", "ac_colour_means_static",
     "ac_batch_create", "ac_batch_set_image", "ac_batch_set_phase", "ac_batch_get_phase", "ac_batch_segment",
     "ac_batch_step", "ac_batch_tune", "ac_batch_destroy", "ac_adjoint_forward", "ac_adjoint_backward",
-    "ac_adjoint_recompute_diff", "ac_set_coarse_tiling", "ac_set_cycle_loop", "ac_get_cycle_loop",
+    "ac_adjoint_recompute_diff", "ac_set_coarse_tiling", "ac_set_cycle_loop", "ac_get_cycle_loop", "ac_set_coarse_smoother",
     "ac_batch_set_launch", "ac_batch_set_cycle_loop", "ac_last_error",
 ]
 PROF_CLASSES = ["smooth", "resid", "coarse", "transfer", "linesearch", "setup", "outer"]
@@ -122,6 +123,7 @@ def _load():
         "ac_adjoint_recompute_diff": ([vp, P(i64)], i),
         "ac_set_coarse_tiling": ([vp, i], i),
         "ac_set_cycle_loop": ([vp, i], i),
+        "ac_set_coarse_smoother": ([vp, i], i),
         "ac_get_cycle_loop": ([vp, P(i)], i),
         "ac_batch_set_launch": ([vp, i], i),
         "ac_batch_set_cycle_loop": ([vp, i], i),
@@ -324,7 +326,8 @@ def ac_batch_step(b, n_steps, allow_not_converged=False):
 
 
 def ac_batch_tune(b, count, trial_steps=2):
-    chosen = np.zeros((count, 3), np.int32)
+    """Per image: nu1, nu2, depth and the coarse smoother the tuner chose."""
+    chosen = np.zeros((count, 4), np.int32)
     _check(lib.ac_batch_tune(b, trial_steps, chosen.ctypes.data))
     return chosen
 
@@ -365,6 +368,11 @@ def ac_set_cycle_loop(ctx, mode):
     """AC_LOOP_AUTO (the V-cycle loop on the device where the context allows)
     or AC_LOOP_HOST (see include/ac.h)."""
     return _check(lib.ac_set_cycle_loop(ctx, mode))
+
+
+def ac_set_coarse_smoother(ctx, mode):
+    """AC_SMOOTH_GS3 (default) or AC_SMOOTH_JACOBI (see include/ac.h)."""
+    return _check(lib.ac_set_coarse_smoother(ctx, mode))
 
 
 def ac_get_cycle_loop(ctx) -> bool:

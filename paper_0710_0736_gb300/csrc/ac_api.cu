@@ -194,6 +194,7 @@ struct Solve {
   // last correction ran tiled, so the flags describe its tiles
   bool tiled = false, was_tiled = false;
   int tiling = AC_TILES_AUTO;  // ac_set_coarse_tiling
+  bool coarse_gs = true;       // ac_set_coarse_smoother: 3-colour Gauss-Seidel (else l1-Jacobi)
 };
 
 // A coarse correction runs tiled when fewer than this fraction of the fine
@@ -597,7 +598,7 @@ int coarse_vcycle(ac_ctx *ctx, Solve &S, int k, void **res) {
       a.op[l] = S.lv[k + l].op;
       ops += 4.0 * (double)S.lv[k + l].n * ns;
     }
-    AC_RUNB(AC_PROF_COARSE, ops + 2 * lk, o->coarse_tail(a, L.r, L.v, kCoarseSweeps, kCoarsestSweeps, smem, ctx->s));
+    AC_RUNB(AC_PROF_COARSE, ops + 2 * lk, o->coarse_tail(a, L.r, L.v, kCoarseSweeps, kCoarsestSweeps, smem, S.coarse_gs, ctx->s));
     *res = L.v;
     return AC_OK;
   }
@@ -608,7 +609,7 @@ int coarse_vcycle(ac_ctx *ctx, Solve &S, int k, void **res) {
       *res = L.v;
     } else {
       AC_RUNB(AC_PROF_COARSE, pair0 + (kCoarseSweeps - 1) * pair,
-              o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, 2 * kCoarseSweeps, true, res, nullptr, ctx->s));
+              o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, 2 * kCoarseSweeps, true, res, nullptr, S.coarse_gs, ctx->s));
     }
     return AC_OK;
   }
@@ -620,12 +621,12 @@ int coarse_vcycle(ac_ctx *ctx, Solve &S, int k, void **res) {
     // float: one launch reads the operator and r and writes v and t; double:
     // the pair, then the residual (operator, r, v read, t written)
     AC_RUNB(AC_PROF_COARSE, o->elem == 4 ? 7 * lk : pair0 + 7 * lk,
-            o->coarse_pre_resid(L.op, L.r, L.v, L.t, L.g, tf, ctx->s));
+            o->coarse_pre_resid(L.op, L.r, L.v, L.t, L.g, tf, S.coarse_gs, ctx->s));
     v = L.v;
     other = L.t;
   } else {
     AC_RUNB(AC_PROF_COARSE, pair0 + (kCoarseSweeps / 2 - 1) * pair,
-            o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, true, &v, tf, ctx->s));
+            o->coarse_smooth(L.op, L.r, L.v, L.t, L.g, kCoarseSweeps, true, &v, tf, S.coarse_gs, ctx->s));
     other = v == L.v ? L.t : L.v;
     AC_RUNB(AC_PROF_COARSE, 7 * lk, o->coarse_resid(L.op, L.r, v, L.g, other, tf, ctx->s));
   }
@@ -637,7 +638,7 @@ int coarse_vcycle(ac_ctx *ctx, Solve &S, int k, void **res) {
   // prolongation: coarse v and this level's diagonal read, v read and written
   AC_RUNB(AC_PROF_TRANSFER, lc + 3 * lk, o->prolong_add(cv, L.g, C.g, L.op, v, tf, ctx->s));
   AC_RUNB(AC_PROF_COARSE, (kCoarseSweeps / 2) * pair,
-          o->coarse_smooth(L.op, L.r, v, other, L.g, kCoarseSweeps, false, res, tf, ctx->s));
+          o->coarse_smooth(L.op, L.r, v, other, L.g, kCoarseSweeps, false, res, tf, S.coarse_gs, ctx->s));
   return AC_OK;
 }
 
@@ -742,6 +743,14 @@ int solve_mg(ac_ctx *ctx, Solve &S, double tol, int max_cycles, int *cycles_out,
     int64_t nfree = 0;
     rc = read_rho(ctx, &rho, &nfree);
     if (rc) return rc;
+#ifdef AC_TRACE_CYCLES
+    {  // build option: one line per cycle (rho, the omega the cycle applied, free nodes, form)
+      double om[2] = {0, 0};
+      cudaMemcpy(om, ctx->omega, sizeof om, cudaMemcpyDeviceToHost);
+      std::fprintf(stderr, "cycle %d rho %.3e omega %.4f free %lld tiled %d elem %d\n", cyc, rho, later ? om[0] : 0.0,
+                   (long long)nfree, S.tiled ? 1 : 0, S.o->elem);
+    }
+#endif
     if (std::isnan(rho) || std::isinf(rho)) {
       status = fail(AC_ERR_NUMERIC, "non-finite residual");
       break;
@@ -798,6 +807,9 @@ int solve_mixed(ac_ctx *ctx, int *cycles_out, double *rho_out, int64_t *sweeps_o
             o->outer_resid(ctx->u, (const float *)ctx->b, ctx->g0, ctx->r32, ctx->u32, ctx->rho, rho32, ctx->s));
     int rc = read_rho(ctx, &rho);
     if (rc) return rc;
+#ifdef AC_TRACE_CYCLES
+    std::fprintf(stderr, "outer %d rho %.3e\n", outer, rho);
+#endif
     if (std::isnan(rho) || std::isinf(rho)) {
       status = fail(AC_ERR_NUMERIC, "non-finite residual");
       break;
@@ -1927,6 +1939,21 @@ int ac_get_cycle_loop(ac_ctx *ctx, int *on_device) {
   return AC_OK;
 }
 
+int ac_set_coarse_smoother(ac_ctx *ctx, int mode) {
+  if (!ctx) return fail(AC_ERR_ARG, "ctx is NULL");
+  if (mode != AC_SMOOTH_GS3 && mode != AC_SMOOTH_JACOBI)
+    return fail(AC_ERR_ARG, "mode must be AC_SMOOTH_GS3 or AC_SMOOTH_JACOBI");
+  if (ctx->s) cudaStreamSynchronize(ctx->s);
+  release_step_graphs(ctx);
+  for (Solve *S : {&ctx->sv, &ctx->adj.sv}) {
+    // the correction graphs hold the smoother's kernels
+    for (int a = 0; a < 2; ++a)
+      for (int f = 0; f < 2; ++f) slot_release(S->correction[a][f]);
+    S->coarse_gs = mode == AC_SMOOTH_GS3;
+  }
+  return AC_OK;
+}
+
 int ac_set_profiling(ac_ctx *ctx, int enable) {
   return ac_set_profiling_mask(ctx, enable ? (1u << AC_PROF_COUNT) - 1u : 0u);
 }
@@ -2304,9 +2331,10 @@ struct ac_batch {
 
 namespace {
 
-// Change a context's schedule: pre/post sweeps and the number of multigrid
-// levels in use.  The captured graphs depend on both, so they are dropped.
-void set_schedule(ac_ctx *ctx, int nu1, int nu2, int depth) {
+// Change a context's schedule: pre/post sweeps, the number of multigrid
+// levels in use and the coarse smoother (gs: 3-colour Gauss-Seidel, else
+// l1-Jacobi).  The captured graphs depend on them, so they are dropped.
+void set_schedule(ac_ctx *ctx, int nu1, int nu2, int depth, bool gs) {
   release_step_graphs(ctx);
   for (int a = 0; a < 2; ++a) {
     for (int b = 0; b < 2; ++b) slot_release(ctx->sv.smooth_resid[a][b]);
@@ -2314,6 +2342,7 @@ void set_schedule(ac_ctx *ctx, int nu1, int nu2, int depth) {
   }
   ctx->p.nu1 = nu1;
   ctx->p.nu2 = nu2;
+  ctx->sv.coarse_gs = gs;
   const int L = (int)ctx->sv.lv.size();
   ctx->sv.depth = depth < 1 ? 1 : (depth > L ? L : depth);
   ctx->delta_warm = false;  // the next step starts its correction from zero
@@ -2553,10 +2582,10 @@ int ac_batch_step(ac_batch *b, int n_steps, ac_batch_stats *out) {
 
 // Empirical schedule search.  Images with the same size, phase count and
 // model parameters form a group; on the group's first image every candidate
-// (nu1, nu2) in {(1,1), (2,1), (1,2), (2,2)} x depth in {all levels, 5} is run
-// for trial_steps steps from the image's current state (restored after each
-// trial) and timed; the fastest candidate whose steps all converged is applied
-// to the whole group.
+// coarse smoother (3-colour Gauss-Seidel, l1-Jacobi) x (nu1, nu2) in {(1,1),
+// (2,1), (1,2), (2,2)} x depth in {all levels, 5} is run for trial_steps steps
+// from the image's current state (restored after each trial) and timed; the
+// fastest candidate whose steps all converged is applied to the whole group.
 int ac_batch_tune(ac_batch *b, int trial_steps, int *chosen) {
   if (!b || trial_steps < 1) return fail(AC_ERR_ARG, "bad tune arguments");
   if (b->group) {
@@ -2599,12 +2628,14 @@ int ac_batch_tune(ac_batch *b, int trial_steps, int *chosen) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
     if (e != cudaSuccess) rc = fail(AC_ERR_CUDA, "tuning snapshot: %s", cudaGetErrorString(e));
     double best_t = 1e300;
-    int best[3] = {c->p.nu1, c->p.nu2, L};
+    int best[4] = {c->p.nu1, c->p.nu2, L, c->sv.coarse_gs ? AC_SMOOTH_GS3 : AC_SMOOTH_JACOBI};
+    for (int sm = 0; sm < 2 && !rc; ++sm)
     for (int nu = 0; nu < 4 && !rc; ++nu)
       for (int dd = 0; dd < 2 && !rc; ++dd) {
         const int depth = dd == 0 ? L : (L < 5 ? L : 5);
         if (dd == 1 && depth == L) continue;
-        set_schedule(c, nus[nu][0], nus[nu][1], depth);
+        const int smoother = sm == 0 ? AC_SMOOTH_GS3 : AC_SMOOTH_JACOBI;
+        set_schedule(c, nus[nu][0], nus[nu][1], depth, smoother == AC_SMOOTH_GS3);
         rc = restore();
         if (rc) break;
         ac_stats st{};
@@ -2620,6 +2651,7 @@ int ac_batch_tune(ac_batch *b, int trial_steps, int *chosen) {
           best[0] = nus[nu][0];
           best[1] = nus[nu][1];
           best[2] = depth;
+          best[3] = smoother;
         }
       }
     int rc2 = rc ? rc : restore();
@@ -2627,12 +2659,9 @@ int ac_batch_tune(ac_batch *b, int trial_steps, int *chosen) {
     cudaFree(snap);
     if (rc2) return rc2;
     for (int k : kv.second) {
-      set_schedule(b->ctx[k], best[0], best[1], best[2]);
-      if (chosen) {
-        chosen[3 * k + 0] = best[0];
-        chosen[3 * k + 1] = best[1];
-        chosen[3 * k + 2] = best[2];
-      }
+      set_schedule(b->ctx[k], best[0], best[1], best[2], best[3] == AC_SMOOTH_GS3);
+      if (chosen)
+        for (int q = 0; q < 4; ++q) chosen[4 * k + q] = best[q];
     }
   }
   return AC_OK;

@@ -1654,16 +1654,183 @@ __device__ __forceinline__ void jacobi2_tile(const T *__restrict__ op, const T *
   }
 }
 
+// ---- 3-colour Gauss-Seidel on a tile (coarse levels) -------------------------
+// The 7-point pattern (E, W, N, S, NE, SW) is 3-coloured by (x + y) mod 3:
+// every neighbour of a node differs from it by +-1 or +-2 in x + y.  A block
+// stages its tile with a halo in shared memory and sweeps it colour by
+// colour, so each update sees the newest values of its neighbours inside the
+// block; values outside the block's region are those at the launch.  The
+// first sweep covers the tile and a ring, the second the tile (and, for the
+// pre-smoothing, a ring for the residual), so one launch does two sweeps,
+// and blocks agree wherever their regions overlap only up to that boundary
+// information -- a smoother with overlapping blocks (every block's sweep is
+// Gauss-Seidel on its own region).  The second sweep runs the colours in
+// reverse (symmetric Gauss-Seidel).  Rows with a zero diagonal (no free fine
+// node of the phase under them) keep 0.
+
+// One pass of colour c over the region [lo, hx] x [lo, hy] of the staged
+// arrays (array index a <-> grid x0 + a, y0 + a).
+template <typename T, int AX, int AY>
+__device__ __forceinline__ void gs_colour_pass(const T (&sC)[AY][AX], const T (&sE)[AY][AX], const T (&sN)[AY][AX],
+                                               const T (&sNE)[AY][AX], const T (&sR)[AY][AX], T (&sV)[AY][AX],
+                                               int x0, int y0, int lo, int hx, int hy, int c) {
+  const int wr = hx - lo + 1, hr = hy - lo + 1, per_row = (wr + 2) / 3;
+  for (int t = threadIdx.x; t < hr * per_row; t += blockDim.x) {
+    const int row = t / per_row, k = t - row * per_row;
+    const int ay = lo + row;
+    const int ph = (((c - (x0 + lo + y0 + ay)) % 3) + 3) % 3;  // first column of colour c in this row
+    const int ax = lo + ph + 3 * k;
+    if (ax > hx) continue;
+    const T d = sC[ay][ax];
+    if (!(d > T(0))) continue;
+    T s = sE[ay][ax] * sV[ay][ax + 1];
+    s += sE[ay][ax - 1] * sV[ay][ax - 1];
+    s += sN[ay][ax] * sV[ay + 1][ax];
+    s += sN[ay - 1][ax] * sV[ay - 1][ax];
+    s += sNE[ay][ax] * sV[ay + 1][ax + 1];
+    s += sNE[ay - 1][ax - 1] * sV[ay - 1][ax - 1];
+    sV[ay][ax] = (sR[ay][ax] - s) / d;
+  }
+}
+
+// A pair of sweeps from vin (from 0 if ZERO_IN: vin is not read): the
+// operator and vin on the tile + 2, r on the tile + 1; sweep 1 on the
+// tile + 1, sweep 2 on the tile.
+template <typename T, int N, bool ZERO_IN>
+__device__ __forceinline__ void gs2_tile(const T *__restrict__ op, const T *__restrict__ r, const T *vin, T *vout,
+                                         const Geo &g, int bxt, int byt, int i) {
+  constexpr int AX = kJ2X + 4, AY = kJ2Y + 4;
+  __shared__ T sC[AY][AX], sE[AY][AX], sN[AY][AX], sNE[AY][AX], sV[AY][AX], sR[AY][AX];
+  const int64_t nc = (int64_t)g.Wn * (g.H + 1);
+  const T *C = op + (0 * N + i) * nc, *E = op + (1 * N + i) * nc, *Nn = op + (2 * N + i) * nc,
+          *NE = op + (3 * N + i) * nc, *ri = r + i * nc, *vi = vin + i * nc;
+  T *vo = vout + i * nc;
+  const int x0 = bxt * kJ2X - 2, y0 = byt * kJ2Y - 2;
+  int live = 0;
+  for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
+    const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
+    const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
+    const T c = in ? C[in ? (int64_t)y * g.Wn + x : 0] : T(0);
+    sC[ay][ax] = c;
+    live |= (ax >= 2 && ax < 2 + kJ2X && ay >= 2 && ay < 2 + kJ2Y && c > T(0)) ? 1 : 0;
+  }
+  if (!__syncthreads_or(live)) {
+    for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
+      const int x = x0 + 2 + t % kJ2X, y = y0 + 2 + t / kJ2X;
+      if (x <= g.W && y <= g.H) vo[(int64_t)y * g.Wn + x] = T(0);
+    }
+    return;
+  }
+  for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
+    const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
+    const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
+    const int64_t K = in ? (int64_t)y * g.Wn + x : 0;
+    sE[ay][ax] = in ? E[K] : T(0);
+    sN[ay][ax] = in ? Nn[K] : T(0);
+    sNE[ay][ax] = in ? NE[K] : T(0);
+    sV[ay][ax] = (!ZERO_IN && in) ? vi[K] : T(0);
+    const bool rin = in && ax >= 1 && ax <= AX - 2 && ay >= 1 && ay <= AY - 2;
+    sR[ay][ax] = rin ? ri[K] : T(0);
+  }
+  __syncthreads();
+  for (int c = 0; c < 3; ++c) {
+    gs_colour_pass<T, AX, AY>(sC, sE, sN, sNE, sR, sV, x0, y0, 1, AX - 2, AY - 2, c);
+    __syncthreads();
+  }
+  for (int c = 2; c >= 0; --c) {
+    gs_colour_pass<T, AX, AY>(sC, sE, sN, sNE, sR, sV, x0, y0, 2, AX - 3, AY - 3, c);
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
+    const int tx = t % kJ2X, ty = t / kJ2X, x = x0 + 2 + tx, y = y0 + 2 + ty;
+    if (x <= g.W && y <= g.H) vo[(int64_t)y * g.Wn + x] = sV[ty + 2][tx + 2];
+  }
+}
+
+// Pre-smoothing pair from v = 0 fused with the level's residual t = r - S v:
+// the operator on the tile + 3, r on the tile + 2; sweep 1 on the tile + 2,
+// sweep 2 on the tile + 1, the residual on the tile.
+template <typename T, int N>
+__device__ __forceinline__ void gs2_resid_tile(const T *__restrict__ op, const T *__restrict__ r,
+                                               T *__restrict__ vout, T *__restrict__ tout, const Geo &g, int bxt,
+                                               int byt, int i) {
+  constexpr int AX = kJ2X + 6, AY = kJ2Y + 6;
+  __shared__ T sC[AY][AX], sE[AY][AX], sN[AY][AX], sNE[AY][AX], sV[AY][AX], sR[AY][AX];
+  const int64_t nc = (int64_t)g.Wn * (g.H + 1);
+  const T *C = op + (0 * N + i) * nc, *E = op + (1 * N + i) * nc, *Nn = op + (2 * N + i) * nc,
+          *NE = op + (3 * N + i) * nc, *ri = r + i * nc;
+  T *vo = vout + i * nc, *to = tout + i * nc;
+  const int x0 = bxt * kJ2X - 3, y0 = byt * kJ2Y - 3;
+  int live = 0;
+  for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
+    const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
+    const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
+    const T c = in ? C[in ? (int64_t)y * g.Wn + x : 0] : T(0);
+    sC[ay][ax] = c;
+    live |= (ax >= 3 && ax < 3 + kJ2X && ay >= 3 && ay < 3 + kJ2Y && c > T(0)) ? 1 : 0;
+  }
+  if (!__syncthreads_or(live)) {
+    for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
+      const int x = x0 + 3 + t % kJ2X, y = y0 + 3 + t / kJ2X;
+      if (x <= g.W && y <= g.H) {
+        vo[(int64_t)y * g.Wn + x] = T(0);
+        to[(int64_t)y * g.Wn + x] = T(0);
+      }
+    }
+    return;
+  }
+  for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
+    const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
+    const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
+    const int64_t K = in ? (int64_t)y * g.Wn + x : 0;
+    sE[ay][ax] = in ? E[K] : T(0);
+    sN[ay][ax] = in ? Nn[K] : T(0);
+    sNE[ay][ax] = in ? NE[K] : T(0);
+    sV[ay][ax] = T(0);
+    const bool rin = in && ax >= 1 && ax <= AX - 2 && ay >= 1 && ay <= AY - 2;
+    sR[ay][ax] = rin ? ri[K] : T(0);
+  }
+  __syncthreads();
+  for (int c = 0; c < 3; ++c) {
+    gs_colour_pass<T, AX, AY>(sC, sE, sN, sNE, sR, sV, x0, y0, 1, AX - 2, AY - 2, c);
+    __syncthreads();
+  }
+  for (int c = 2; c >= 0; --c) {
+    gs_colour_pass<T, AX, AY>(sC, sE, sN, sNE, sR, sV, x0, y0, 2, AX - 3, AY - 3, c);
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
+    const int tx = t % kJ2X, ty = t / kJ2X, x = x0 + 3 + tx, y = y0 + 3 + ty;
+    if (x > g.W || y > g.H) continue;
+    const int ax = tx + 3, ay = ty + 3;
+    const T d = sC[ay][ax], vk = sV[ay][ax];
+    T s = T(0);
+    s += sE[ay][ax] * sV[ay][ax + 1];
+    s += sE[ay][ax - 1] * sV[ay][ax - 1];
+    s += sN[ay][ax] * sV[ay + 1][ax];
+    s += sN[ay - 1][ax] * sV[ay - 1][ax];
+    s += sNE[ay][ax] * sV[ay + 1][ax + 1];
+    s += sNE[ay - 1][ax - 1] * sV[ay - 1][ax - 1];
+    const int64_t K = (int64_t)y * g.Wn + x;
+    vo[K] = vk;
+    to[K] = d > T(0) ? sR[ay][ax] - d * vk - s : T(0);
+  }
+}
+
 // (the register bound keeps as many blocks per SM as the shared memory
 // allows: eight in float, five in double)
 constexpr int j2_min_blocks(int elem) { return elem == 4 ? 8 : 5; }
-template <typename T, int N, bool ZERO_IN>
-__global__ void __launch_bounds__(kJ2Threads, j2_min_blocks(sizeof(T))) k_coarse_jacobi2(const T *__restrict__ op, const T *__restrict__ r,
+// Two smoothing sweeps per tile of a coarse level: 3-colour Gauss-Seidel
+// (GS) or l1-Jacobi.
+template <typename T, int N, bool ZERO_IN, bool GS>
+__global__ void __launch_bounds__(kJ2Threads, j2_min_blocks(sizeof(T))) k_coarse_pair(const T *__restrict__ op, const T *__restrict__ r,
                                                                   const T *vin, T *vout, Geo g, TileList L) {
   for_each_tile(L, g, [&](int tx, int ty, int i, bool dying) {
     const int64_t nc = (int64_t)g.Wn * (g.H + 1);
     if (dying)
       tile_zero<T>(g, tx, ty, vout + i * nc, (T *)nullptr);
+    else if constexpr (GS)
+      gs2_tile<T, N, ZERO_IN>(op, r, vin, vout, g, tx, ty, i);
     else
       jacobi2_tile<T, N, ZERO_IN>(op, r, vin, vout, g, tx, ty, i);
   });
@@ -1769,14 +1936,16 @@ __device__ __forceinline__ void jacobi2_resid_tile(const T *__restrict__ op, con
   }
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(kJ2Threads, j2_min_blocks(sizeof(T))) k_coarse_jacobi2_resid(const T *__restrict__ op,
+template <typename T, int N, bool GS>
+__global__ void __launch_bounds__(kJ2Threads, j2_min_blocks(sizeof(T))) k_coarse_pair_resid(const T *__restrict__ op,
                                                                         const T *__restrict__ r, T *__restrict__ vout,
                                                                         T *__restrict__ tout, Geo g, TileList L) {
   for_each_tile(L, g, [&](int tx, int ty, int i, bool dying) {
     const int64_t nc = (int64_t)g.Wn * (g.H + 1);
     if (dying)
       tile_zero<T>(g, tx, ty, vout + i * nc, tout + i * nc);
+    else if constexpr (GS)
+      gs2_resid_tile<T, N>(op, r, vout, tout, g, tx, ty, i);
     else
       jacobi2_resid_tile<T, N>(op, r, vout, tout, g, tx, ty, i);
   });
@@ -1964,9 +2133,29 @@ __device__ __forceinline__ void tail_gs(const TailLevel<T> &L, int sweeps) {
     }
 }
 
+// `sweeps` Gauss-Seidel sweeps on v in place, the colours forward (0, 1, 2)
+// in even sweeps and backward in odd ones (as the tiles of k_coarse_pair)
+template <typename T>
+__device__ __forceinline__ void tail_sgs(const TailLevel<T> &L, int sweeps) {
+  for (int s = 0; s < sweeps; ++s)
+    for (int q = 0; q < 3; ++q) {
+      const int color = (s & 1) ? 2 - q : q;
+      for (int k = threadIdx.x; k < L.n; k += blockDim.x) {
+        const int x = k % L.Wn, y = k / L.Wn;
+        if ((x + y) % 3 != color) continue;
+        const T d = L.C[k];
+        if (!(d > T(0))) continue;
+        T l1 = T(0);
+        L.v[k] = (L.r[k] - tail_offdiag(L, L.v, k, x, y, l1)) / d;
+      }
+      __syncthreads();
+    }
+}
+
 // one block per phase (blockIdx.x); dynamic shared memory
-// kTailArrays * sum_l n_l values of T
-template <typename T, int N>
+// kTailArrays * sum_l n_l values of T.  GS: the levels' smoothing sweeps are
+// Gauss-Seidel (tail_sgs), else l1-Jacobi.
+template <typename T, int N, bool GS>
 __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(TailArgs a, const T *__restrict__ r0, T *__restrict__ v0,
                                                               int coarse_sweeps, int coarsest_sweeps) {
   extern __shared__ unsigned char smem_raw[];
@@ -2001,13 +2190,19 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(TailArgs a, const 
   const int last = a.levels - 1;
   for (int l = 0; l < last; ++l) {
     const TailLevel<T> &L = lv[l];
-    // coarse_sweeps (even) sweeps from zero, alternating t and v, ending in v
-    for (int s = 0; s < coarse_sweeps; ++s) {
-      if (s & 1)
-        tail_jacobi(L, L.t, L.v);
-      else
-        tail_jacobi(L, s == 0 ? (const T *)nullptr : L.v, L.t);
+    if constexpr (GS) {
+      for (int k = threadIdx.x; k < L.n; k += blockDim.x) L.v[k] = T(0);
       __syncthreads();
+      tail_sgs(L, coarse_sweeps);
+    } else {
+      // coarse_sweeps (even) sweeps from zero, alternating t and v, ending in v
+      for (int s = 0; s < coarse_sweeps; ++s) {
+        if (s & 1)
+          tail_jacobi(L, L.t, L.v);
+        else
+          tail_jacobi(L, s == 0 ? (const T *)nullptr : L.v, L.t);
+        __syncthreads();
+      }
     }
     tail_resid(L);
     __syncthreads();
@@ -2019,12 +2214,16 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(TailArgs a, const 
     const TailLevel<T> &L = lv[l];
     tail_prolong(L, lv[l + 1]);
     __syncthreads();
-    for (int s = 0; s < coarse_sweeps; ++s) {
-      if (s & 1)
-        tail_jacobi(L, L.t, L.v);
-      else
-        tail_jacobi(L, L.v, L.t);
-      __syncthreads();
+    if constexpr (GS) {
+      tail_sgs(L, coarse_sweeps);
+    } else {
+      for (int s = 0; s < coarse_sweeps; ++s) {
+        if (s & 1)
+          tail_jacobi(L, L.t, L.v);
+        else
+          tail_jacobi(L, L.v, L.t);
+        __syncthreads();
+      }
     }
   }
   for (int k = threadIdx.x; k < lv[0].n; k += blockDim.x) v0[(int64_t)i * lv[0].n + k] = lv[0].v[k];
@@ -2032,7 +2231,7 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(TailArgs a, const 
 
 // t = r - S v on a coarse level, one thread per (node, phase) (interior
 // nodes branch-free; the same arithmetic and order as op_offdiag).  The
-// float forms fuse it into the pre-smoothing pair (k_coarse_jacobi2_resid).
+// float forms fuse it into the pre-smoothing pair (k_coarse_pair_resid).
 template <typename T, int N>
 __device__ __forceinline__ void coarse_resid_row(const T *__restrict__ op, const T *__restrict__ r,
                                                  const T *__restrict__ v, const Geo &g, T *__restrict__ t, int x, int y,

@@ -112,22 +112,23 @@ struct SolverLaunch {
     }
     return 1;
   }
-  static int coarse_smooth(const void *op, const void *r, void *v, void *tmp, const Geo &g, int sweeps,
-                           bool zero_start, void **out, const LevelLists *L, cudaStream_t s) {
+  template <bool GS>
+  static int coarse_smooth_t(const void *op, const void *r, void *v, void *tmp, const Geo &g, int sweeps,
+                             bool zero_start, void **out, const LevelLists *L, cudaStream_t s) {
     const TileList tf = item_list(L);
     void *cur = v;
     int k = 0;
     for (int p = 0; p < sweeps / 2; ++p) {
       if (p == 0 && zero_start) {
         // v is not read: the pair can write it
-        const dim3 grid = tile_grid(g, L, N, k_coarse_jacobi2<T, N, true>, kJ2Threads);
-        k_coarse_jacobi2<T, N, true><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)v, (T *)v, g,
-                                                                tf);
+        const dim3 grid = tile_grid(g, L, N, k_coarse_pair<T, N, true, GS>, kJ2Threads);
+        k_coarse_pair<T, N, true, GS><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)v, (T *)v,
+                                                                   g, tf);
       } else {
         void *nxt = cur == v ? tmp : v;
-        const dim3 grid = tile_grid(g, L, N, k_coarse_jacobi2<T, N, false>, kJ2Threads);
-        k_coarse_jacobi2<T, N, false><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)cur,
-                                                                 (T *)nxt, g, tf);
+        const dim3 grid = tile_grid(g, L, N, k_coarse_pair<T, N, false, GS>, kJ2Threads);
+        k_coarse_pair<T, N, false, GS><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)cur,
+                                                                    (T *)nxt, g, tf);
         cur = nxt;
       }
       ++k;
@@ -135,21 +136,31 @@ struct SolverLaunch {
     *out = cur;
     return k;
   }
-  // two l1-Jacobi sweeps from v = 0, then t = r - S v; float: one fused
-  // launch (its shared memory is over the static limit in double)
-  static int coarse_pre_resid(const void *op, const void *r, void *v, void *t, const Geo &g, const LevelLists *L,
-                              cudaStream_t s) {
+  static int coarse_smooth(const void *op, const void *r, void *v, void *tmp, const Geo &g, int sweeps,
+                           bool zero_start, void **out, const LevelLists *L, bool gs, cudaStream_t s) {
+    return gs ? coarse_smooth_t<true>(op, r, v, tmp, g, sweeps, zero_start, out, L, s)
+              : coarse_smooth_t<false>(op, r, v, tmp, g, sweeps, zero_start, out, L, s);
+  }
+  // two sweeps from v = 0, then t = r - S v; float: one fused launch (its
+  // shared memory is over the static limit in double)
+  template <bool GS>
+  static int coarse_pre_resid_t(const void *op, const void *r, void *v, void *t, const Geo &g, const LevelLists *L,
+                                cudaStream_t s) {
     const TileList tf = item_list(L);
     if constexpr (sizeof(T) == 4) {
-      const dim3 grid = tile_grid(g, L, N, k_coarse_jacobi2_resid<T, N>, kJ2Threads);
-      k_coarse_jacobi2_resid<T, N><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (T *)v, (T *)t, g, tf);
+      const dim3 grid = tile_grid(g, L, N, k_coarse_pair_resid<T, N, GS>, kJ2Threads);
+      k_coarse_pair_resid<T, N, GS><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (T *)v, (T *)t, g, tf);
       return 1;
     } else {
-      const dim3 grid = tile_grid(g, L, N, k_coarse_jacobi2<T, N, true>, kJ2Threads);
-      k_coarse_jacobi2<T, N, true><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)v, (T *)v, g,
-                                                              tf);
+      const dim3 grid = tile_grid(g, L, N, k_coarse_pair<T, N, true, GS>, kJ2Threads);
+      k_coarse_pair<T, N, true, GS><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)v, (T *)v, g,
+                                                                 tf);
       return 1 + coarse_resid(op, r, v, g, t, L, s);
     }
+  }
+  static int coarse_pre_resid(const void *op, const void *r, void *v, void *t, const Geo &g, const LevelLists *L,
+                              bool gs, cudaStream_t s) {
+    return gs ? coarse_pre_resid_t<true>(op, r, v, t, g, L, s) : coarse_pre_resid_t<false>(op, r, v, t, g, L, s);
   }
   static int coarse_solve(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s) {
     const int64_t nc = (int64_t)g.Wn * (g.H + 1);
@@ -200,15 +211,21 @@ struct SolverLaunch {
     }
     return 1;
   }
-  static int coarse_tail(const TailArgs &a, const void *r0, void *v0, int coarse_sweeps, int coarsest_sweeps,
-                         size_t smem, cudaStream_t s) {
+  template <bool GS>
+  static int coarse_tail_t(const TailArgs &a, const void *r0, void *v0, int coarse_sweeps, int coarsest_sweeps,
+                           size_t smem, cudaStream_t s) {
     // the cap, not this launch's size: the attribute is process-wide and
     // graphs captured for other grids replay launches of other sizes
-    static const cudaError_t attr =
-        cudaFuncSetAttribute(k_coarse_tail<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemBytes);
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_coarse_tail<T, N, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemBytes);
     (void)attr;
-    k_coarse_tail<T, N><<<N, kTailThreads, smem, s>>>(a, (const T *)r0, (T *)v0, coarse_sweeps, coarsest_sweeps);
+    k_coarse_tail<T, N, GS><<<N, kTailThreads, smem, s>>>(a, (const T *)r0, (T *)v0, coarse_sweeps, coarsest_sweeps);
     return 1;
+  }
+  static int coarse_tail(const TailArgs &a, const void *r0, void *v0, int coarse_sweeps, int coarsest_sweeps,
+                         size_t smem, bool gs, cudaStream_t s) {
+    return gs ? coarse_tail_t<true>(a, r0, v0, coarse_sweeps, coarsest_sweeps, smem, s)
+              : coarse_tail_t<false>(a, r0, v0, coarse_sweeps, coarsest_sweeps, smem, s);
   }
   static int line_search(const void *x, const void *ob, const void *rt, const void *v1, const uint8_t *mask,
                          const Geo &gf, const Geo &gc, void *d, double *part, double *tot, double *omega,

@@ -70,17 +70,18 @@ struct SolverOps {
   // Lc != null: a tiled coarse level from a tiled fine level (Lf)
   int (*galerkin)(const void *opf, const Geo &gf, const Geo &gc, void *opc, const LevelLists *Lf,
                   const LevelLists *Lc, cudaStream_t s);
-  // `sweeps` (even) l1-Jacobi sweeps in fused pairs starting from v, using v
+  // `sweeps` (even) smoothing sweeps in fused pairs starting from v, using v
   // and tmp in turn; *out returns the buffer holding the result.  zero_start:
-  // v = 0 on entry (it is then neither read nor needs clearing)
+  // v = 0 on entry (it is then neither read nor needs clearing).  gs:
+  // 3-colour Gauss-Seidel on shared-memory tiles, else l1-Jacobi
   int (*coarse_smooth)(const void *op, const void *r, void *v, void *tmp, const Geo &g, int sweeps, bool zero_start,
-                       void **out, const LevelLists *L, cudaStream_t s);
+                       void **out, const LevelLists *L, bool gs, cudaStream_t s);
   int (*coarse_solve)(const void *op, const void *r, void *v, const Geo &g, int sweeps, cudaStream_t s);
   int (*coarse_resid)(const void *op, const void *r, const void *v, const Geo &g, void *t, const LevelLists *L,
                       cudaStream_t s);
-  // one pair of l1-Jacobi sweeps from v = 0, then t = r - S v
+  // one pair of smoothing sweeps from v = 0, then t = r - S v
   int (*coarse_pre_resid)(const void *op, const void *r, void *v, void *t, const Geo &g, const LevelLists *L,
-                          cudaStream_t s);
+                          bool gs, cudaStream_t s);
   int (*restrict_)(const void *t, const Geo &gf, const Geo &gc, const void *opc, void *rc, const LevelLists *Lc,
                    cudaStream_t s);
   int (*prolong_add)(const void *vc, const Geo &gf, const Geo &gc, const void *opf, void *vf, const LevelLists *Lf,
@@ -88,7 +89,7 @@ struct SolverOps {
   // v of level k0 from r of level k0 by the whole cycle below it (see
   // TailArgs); smem bytes of dynamic shared memory per block
   int (*coarse_tail)(const TailArgs &a, const void *r0, void *v0, int coarse_sweeps, int coarsest_sweeps,
-                     size_t smem, cudaStream_t s);
+                     size_t smem, bool gs, cudaStream_t s);
   // line search: part needs 2 x (blocks of the fine grid) doubles, tot 2 doubles
   int (*line_search)(const void *x, const void *ob, const void *rt, const void *v1, const uint8_t *mask,
                      const Geo &gf, const Geo &gc, void *d, double *part, double *tot, double *omega, cudaStream_t s);

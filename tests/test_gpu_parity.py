@@ -390,6 +390,36 @@ def test_device_loop_matches_host_loop(ac, precision, W, H, N, nu1, nu2, max_cyc
         assert all(rc == ac.AC_ERR_NOT_CONVERGED and s["converged"] == 0 for rc, s in st_d)
 
 
+@pytest.mark.parametrize("W,H,N", [(256, 256, 8), (320, 192, 5)])
+@pytest.mark.parametrize("form,tol,bound", [("fp64", TIGHT, 1e-10), ("mixed", 1e-12, 1e-10)])
+@pytest.mark.parametrize("tiling", ["auto", "always"])
+def test_coarse_smoothers_reach_the_same_minimiser(ac, tiled_coarse_cases, W, H, N, form, tol, bound, tiling):
+    """The coarse levels' 3-colour Gauss-Seidel and l1-Jacobi take different
+    cycles to the same step minimiser (Sec. 3.2): one step from the oracle's
+    phase-separated u1 matches the oracle's u2 element by element with either
+    smoother, with dense coarse levels and with AC_TILES_ALWAYS (the live-tile
+    lists), and Gauss-Seidel needs no more V-cycles than Jacobi."""
+    import torch
+    case = tiled_coarse_cases[(W, H, N, form)]
+    prec = ac.AC_MIXED if form == "mixed" else ac.AC_FP64
+    st = torch.cuda.Stream()
+    cyc = {}
+    for mode in (ac.AC_SMOOTH_GS3, ac.AC_SMOOTH_JACOBI):
+        seg = _stream_seg(ac, W, H, N, st, tol=tol, precision=prec, max_cycles=3000)
+        ac.ac_set_coarse_smoother(seg.ctx, mode)
+        if tiling == "always":
+            ac.ac_set_coarse_tiling(seg.ctx, ac.AC_TILES_ALWAYS)
+        seg.set_image(case["img"] if form == "mixed" else case["img"].astype(np.float64))
+        seg.set_phase(case["u1"])
+        cyc[mode] = seg.step(1).total_cycles
+        err = np.abs(seg.phase() - case["u2"]).max()
+        assert err < bound, f"smoother {mode}: {err:.3e}"
+        seg.close()
+    assert cyc[ac.AC_SMOOTH_GS3] <= cyc[ac.AC_SMOOTH_JACOBI]
+    with pytest.raises(ac.AcError):
+        ac.ac_set_coarse_smoother(None, ac.AC_SMOOTH_GS3)
+
+
 def test_device_loop_eligibility(ac):
     """The loop runs on the device only with a stream, profiling off and no
     coarse level that can run tiled; the legacy default stream, profiling and
@@ -1011,6 +1041,7 @@ def test_batch_autotuner(ac):
         assert np.array_equal(b.phase(k), u_before[k])
     assert ((chosen[:, 0] >= 1) & (chosen[:, 0] <= 2) & (chosen[:, 1] >= 1) & (chosen[:, 1] <= 2)).all()
     assert (chosen[:, 2] >= 1).all()
+    assert np.isin(chosen[:, 3], [ac.AC_SMOOTH_GS3, ac.AC_SMOOTH_JACOBI]).all()
     assert b.step(1).converged_images == len(specs)
     u_prev = [b.phase(k) for k in range(len(specs))]
     assert b.step(1).converged_images == len(specs)
