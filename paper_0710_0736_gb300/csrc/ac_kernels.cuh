@@ -1668,55 +1668,72 @@ __device__ __forceinline__ void jacobi2_tile(const T *__restrict__ op, const T *
 // reverse (symmetric Gauss-Seidel).  Rows with a zero diagonal (no free fine
 // node of the phase under them) keep 0.
 
-// One pass of colour c over the region [lo, hx] x [lo, hy] of the staged
-// arrays (array index a <-> grid x0 + a, y0 + a).
-template <typename T, int AX, int AY>
-__device__ __forceinline__ void gs_colour_pass(const T (&sC)[AY][AX], const T (&sE)[AY][AX], const T (&sN)[AY][AX],
-                                               const T (&sNE)[AY][AX], const T (&sR)[AY][AX], T (&sV)[AY][AX],
-                                               int x0, int y0, int lo, int hx, int hy, int c) {
-  const int wr = hx - lo + 1, hr = hy - lo + 1, per_row = (wr + 2) / 3;
-  for (int t = threadIdx.x; t < hr * per_row; t += blockDim.x) {
-    const int row = t / per_row, k = t - row * per_row;
-    const int ay = lo + row;
-    const int ph = (((c - (x0 + lo + y0 + ay)) % 3) + 3) % 3;  // first column of colour c in this row
-    const int ax = lo + ph + 3 * k;
-    if (ax > hx) continue;
-    const T d = sC[ay][ax];
-    if (!(d > T(0))) continue;
-    T s = sE[ay][ax] * sV[ay][ax + 1];
-    s += sE[ay][ax - 1] * sV[ay][ax - 1];
-    s += sN[ay][ax] * sV[ay + 1][ax];
-    s += sN[ay - 1][ax] * sV[ay - 1][ax];
-    s += sNE[ay][ax] * sV[ay + 1][ax + 1];
-    s += sNE[ay - 1][ax - 1] * sV[ay - 1][ax - 1];
-    sV[ay][ax] = (sR[ay][ax] - s) / d;
-  }
+// A colour pass gives each thread at most one node: thread t takes row
+// t / kGsPerRow of the region and the (t % kGsPerRow)-th node of the colour in
+// that row (regions are at most 3 kGsPerRow wide and their rows x kGsPerRow
+// at most kJ2Threads).  The row's first column of a colour follows from the
+// row's colour offset, which each thread computes once per region.
+constexpr int kGsPerRow = 12;
+
+// (x0 + y0 + 2 lo + row) mod 3: the colour of the region's first node in the
+// thread's row (x0, y0: grid position of array index 0; may be negative)
+__device__ __forceinline__ int gs_row_base(int x0, int y0, int lo) {
+  const int v = (x0 + y0 + 2 * lo + (int)threadIdx.x / kGsPerRow) % 3;
+  return v < 0 ? v + 3 : v;
 }
 
-// A pair of sweeps from vin (from 0 if ZERO_IN: vin is not read): the
-// operator and vin on the tile + 2, r on the tile + 1; sweep 1 on the
-// tile + 1, sweep 2 on the tile.
-template <typename T, int N, bool ZERO_IN>
-__device__ __forceinline__ void gs2_tile(const T *__restrict__ op, const T *__restrict__ r, const T *vin, T *vout,
-                                         const Geo &g, int bxt, int byt, int i) {
-  constexpr int AX = kJ2X + 4, AY = kJ2Y + 4;
-  __shared__ T sC[AY][AX], sE[AY][AX], sN[AY][AX], sNE[AY][AX], sV[AY][AX], sR[AY][AX];
+// The thread's update in the pass of colour c over the region [LO, HX] x
+// [LO, HY] of the staged arrays: v = (r - sum of the off-diagonal terms) / d
+// with the reciprocal of d staged in sI (0 on rows with a zero diagonal,
+// whose entries and r are 0 as well, and outside the grid).
+template <typename T, int AX, int AY, int LO, int HX, int HY>
+__device__ __forceinline__ void gs_colour_pass(const T (&sE)[AY][AX], const T (&sN)[AY][AX], const T (&sNE)[AY][AX],
+                                               const T (&sR)[AY][AX], const T (&sI)[AY][AX], T (&sV)[AY][AX], int base,
+                                               int c) {
+  static_assert(HX - LO + 1 <= 3 * kGsPerRow && (HY - LO + 1) * kGsPerRow <= kJ2Threads, "colour pass region");
+  const int row = (int)threadIdx.x / kGsPerRow, k = (int)threadIdx.x - row * kGsPerRow;
+  if (row > HY - LO) return;
+  int ph = c - base;
+  ph += ph < 0 ? 3 : 0;
+  const int ay = LO + row, ax = LO + ph + 3 * k;
+  if (ax > HX) return;
+  T s = sE[ay][ax] * sV[ay][ax + 1];
+  s += sE[ay][ax - 1] * sV[ay][ax - 1];
+  s += sN[ay][ax] * sV[ay + 1][ax];
+  s += sN[ay - 1][ax] * sV[ay - 1][ax];
+  s += sNE[ay][ax] * sV[ay + 1][ax + 1];
+  s += sNE[ay - 1][ax - 1] * sV[ay - 1][ax - 1];
+  sV[ay][ax] = (sR[ay][ax] - s) * sI[ay][ax];
+}
+
+__device__ __forceinline__ float rcp_t(float d) { return __frcp_rn(d); }
+__device__ __forceinline__ double rcp_t(double d) { return __drcp_rn(d); }
+
+// SW (1 or 2) sweeps from vin (from 0 if ZERO_IN: vin is not read): the
+// operator and vin on the tile + SW, r on the tile + SW - 1; sweep s (1 ..
+// SW) on the tile + SW - s.  Two sweeps run the colours forward, then
+// backward; a single sweep runs them in the order `FWD` asks.
+template <typename T, int N, bool ZERO_IN, int SW, bool FWD>
+__device__ __forceinline__ void gs_tile(const T *__restrict__ op, const T *__restrict__ r, const T *vin, T *vout,
+                                        const Geo &g, int bxt, int byt, int i) {
+  constexpr int AX = kJ2X + 2 * SW, AY = kJ2Y + 2 * SW;
+  __shared__ T sC[AY][AX], sE[AY][AX], sN[AY][AX], sNE[AY][AX], sV[AY][AX], sR[AY][AX], sI[AY][AX];
   const int64_t nc = (int64_t)g.Wn * (g.H + 1);
   const T *C = op + (0 * N + i) * nc, *E = op + (1 * N + i) * nc, *Nn = op + (2 * N + i) * nc,
           *NE = op + (3 * N + i) * nc, *ri = r + i * nc, *vi = vin + i * nc;
   T *vo = vout + i * nc;
-  const int x0 = bxt * kJ2X - 2, y0 = byt * kJ2Y - 2;
+  const int x0 = bxt * kJ2X - SW, y0 = byt * kJ2Y - SW;
   int live = 0;
   for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
     const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
     const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
     const T c = in ? C[in ? (int64_t)y * g.Wn + x : 0] : T(0);
     sC[ay][ax] = c;
-    live |= (ax >= 2 && ax < 2 + kJ2X && ay >= 2 && ay < 2 + kJ2Y && c > T(0)) ? 1 : 0;
+    live |= (ax >= SW && ax < SW + kJ2X && ay >= SW && ay < SW + kJ2Y && c > T(0)) ? 1 : 0;
   }
   if (!__syncthreads_or(live)) {
     for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
-      const int x = x0 + 2 + t % kJ2X, y = y0 + 2 + t / kJ2X;
+      const int x = x0 + SW + t % kJ2X, y = y0 + SW + t / kJ2X;
       if (x <= g.W && y <= g.H) vo[(int64_t)y * g.Wn + x] = T(0);
     }
     return;
@@ -1731,47 +1748,57 @@ __device__ __forceinline__ void gs2_tile(const T *__restrict__ op, const T *__re
     sV[ay][ax] = (!ZERO_IN && in) ? vi[K] : T(0);
     const bool rin = in && ax >= 1 && ax <= AX - 2 && ay >= 1 && ay <= AY - 2;
     sR[ay][ax] = rin ? ri[K] : T(0);
+    const T c = sC[ay][ax];
+    sI[ay][ax] = c > T(0) ? rcp_t(c) : T(0);
   }
+  const int b1 = gs_row_base(x0, y0, 1);
   __syncthreads();
-  for (int c = 0; c < 3; ++c) {
-    gs_colour_pass<T, AX, AY>(sC, sE, sN, sNE, sR, sV, x0, y0, 1, AX - 2, AY - 2, c);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    gs_colour_pass<T, AX, AY, 1, AX - 2, AY - 2>(sE, sN, sNE, sR, sI, sV, b1, (SW == 2 || FWD) ? q : 2 - q);
     __syncthreads();
   }
-  for (int c = 2; c >= 0; --c) {
-    gs_colour_pass<T, AX, AY>(sC, sE, sN, sNE, sR, sV, x0, y0, 2, AX - 3, AY - 3, c);
-    __syncthreads();
+  if constexpr (SW == 2) {
+    const int b2 = gs_row_base(x0, y0, 2);
+#pragma unroll
+    for (int c = 2; c >= 0; --c) {
+      gs_colour_pass<T, AX, AY, 2, AX - 3, AY - 3>(sE, sN, sNE, sR, sI, sV, b2, c);
+      __syncthreads();
+    }
   }
   for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
-    const int tx = t % kJ2X, ty = t / kJ2X, x = x0 + 2 + tx, y = y0 + 2 + ty;
-    if (x <= g.W && y <= g.H) vo[(int64_t)y * g.Wn + x] = sV[ty + 2][tx + 2];
+    const int tx = t % kJ2X, ty = t / kJ2X, x = x0 + SW + tx, y = y0 + SW + ty;
+    if (x <= g.W && y <= g.H) vo[(int64_t)y * g.Wn + x] = sV[ty + SW][tx + SW];
   }
 }
 
-// Pre-smoothing pair from v = 0 fused with the level's residual t = r - S v:
-// the operator on the tile + 3, r on the tile + 2; sweep 1 on the tile + 2,
-// sweep 2 on the tile + 1, the residual on the tile.
-template <typename T, int N>
-__device__ __forceinline__ void gs2_resid_tile(const T *__restrict__ op, const T *__restrict__ r,
-                                               T *__restrict__ vout, T *__restrict__ tout, const Geo &g, int bxt,
-                                               int byt, int i) {
-  constexpr int AX = kJ2X + 6, AY = kJ2Y + 6;
-  __shared__ T sC[AY][AX], sE[AY][AX], sN[AY][AX], sNE[AY][AX], sV[AY][AX], sR[AY][AX];
+// Pre-smoothing from v = 0 (SW sweeps, colours forward then backward)
+// fused with the level's residual t = r - S v: the operator on the tile +
+// SW + 1, r on the tile + SW; sweep s on the tile + SW + 1 - s, the residual
+// on the tile.
+template <typename T, int N, int SW>
+__device__ __forceinline__ void gs_resid_tile(const T *__restrict__ op, const T *__restrict__ r,
+                                              T *__restrict__ vout, T *__restrict__ tout, const Geo &g, int bxt,
+                                              int byt, int i) {
+  constexpr int H0 = SW + 1;  // halo of the staged operator
+  constexpr int AX = kJ2X + 2 * H0, AY = kJ2Y + 2 * H0;
+  __shared__ T sC[AY][AX], sE[AY][AX], sN[AY][AX], sNE[AY][AX], sV[AY][AX], sR[AY][AX], sI[AY][AX];
   const int64_t nc = (int64_t)g.Wn * (g.H + 1);
   const T *C = op + (0 * N + i) * nc, *E = op + (1 * N + i) * nc, *Nn = op + (2 * N + i) * nc,
           *NE = op + (3 * N + i) * nc, *ri = r + i * nc;
   T *vo = vout + i * nc, *to = tout + i * nc;
-  const int x0 = bxt * kJ2X - 3, y0 = byt * kJ2Y - 3;
+  const int x0 = bxt * kJ2X - H0, y0 = byt * kJ2Y - H0;
   int live = 0;
   for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
     const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
     const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
     const T c = in ? C[in ? (int64_t)y * g.Wn + x : 0] : T(0);
     sC[ay][ax] = c;
-    live |= (ax >= 3 && ax < 3 + kJ2X && ay >= 3 && ay < 3 + kJ2Y && c > T(0)) ? 1 : 0;
+    live |= (ax >= H0 && ax < H0 + kJ2X && ay >= H0 && ay < H0 + kJ2Y && c > T(0)) ? 1 : 0;
   }
   if (!__syncthreads_or(live)) {
     for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
-      const int x = x0 + 3 + t % kJ2X, y = y0 + 3 + t / kJ2X;
+      const int x = x0 + H0 + t % kJ2X, y = y0 + H0 + t / kJ2X;
       if (x <= g.W && y <= g.H) {
         vo[(int64_t)y * g.Wn + x] = T(0);
         to[(int64_t)y * g.Wn + x] = T(0);
@@ -1789,20 +1816,28 @@ __device__ __forceinline__ void gs2_resid_tile(const T *__restrict__ op, const T
     sV[ay][ax] = T(0);
     const bool rin = in && ax >= 1 && ax <= AX - 2 && ay >= 1 && ay <= AY - 2;
     sR[ay][ax] = rin ? ri[K] : T(0);
+    const T c = sC[ay][ax];
+    sI[ay][ax] = c > T(0) ? rcp_t(c) : T(0);
   }
+  const int b1 = gs_row_base(x0, y0, 1);
   __syncthreads();
+#pragma unroll
   for (int c = 0; c < 3; ++c) {
-    gs_colour_pass<T, AX, AY>(sC, sE, sN, sNE, sR, sV, x0, y0, 1, AX - 2, AY - 2, c);
+    gs_colour_pass<T, AX, AY, 1, AX - 2, AY - 2>(sE, sN, sNE, sR, sI, sV, b1, c);
     __syncthreads();
   }
-  for (int c = 2; c >= 0; --c) {
-    gs_colour_pass<T, AX, AY>(sC, sE, sN, sNE, sR, sV, x0, y0, 2, AX - 3, AY - 3, c);
-    __syncthreads();
+  if constexpr (SW == 2) {
+    const int b2 = gs_row_base(x0, y0, 2);
+#pragma unroll
+    for (int c = 2; c >= 0; --c) {
+      gs_colour_pass<T, AX, AY, 2, AX - 3, AY - 3>(sE, sN, sNE, sR, sI, sV, b2, c);
+      __syncthreads();
+    }
   }
   for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
-    const int tx = t % kJ2X, ty = t / kJ2X, x = x0 + 3 + tx, y = y0 + 3 + ty;
+    const int tx = t % kJ2X, ty = t / kJ2X, x = x0 + H0 + tx, y = y0 + H0 + ty;
     if (x > g.W || y > g.H) continue;
-    const int ax = tx + 3, ay = ty + 3;
+    const int ax = tx + H0, ay = ty + H0;
     const T d = sC[ay][ax], vk = sV[ay][ax];
     T s = T(0);
     s += sE[ay][ax] * sV[ay][ax + 1];
@@ -1830,7 +1865,7 @@ __global__ void __launch_bounds__(kJ2Threads, j2_min_blocks(sizeof(T))) k_coarse
     if (dying)
       tile_zero<T>(g, tx, ty, vout + i * nc, (T *)nullptr);
     else if constexpr (GS)
-      gs2_tile<T, N, ZERO_IN>(op, r, vin, vout, g, tx, ty, i);
+      gs_tile<T, N, ZERO_IN, kGsSweeps, ZERO_IN>(op, r, vin, vout, g, tx, ty, i);
     else
       jacobi2_tile<T, N, ZERO_IN>(op, r, vin, vout, g, tx, ty, i);
   });
@@ -1945,7 +1980,7 @@ __global__ void __launch_bounds__(kJ2Threads, j2_min_blocks(sizeof(T))) k_coarse
     if (dying)
       tile_zero<T>(g, tx, ty, vout + i * nc, tout + i * nc);
     else if constexpr (GS)
-      gs2_resid_tile<T, N>(op, r, vout, tout, g, tx, ty, i);
+      gs_resid_tile<T, N, kGsSweeps>(op, r, vout, tout, g, tx, ty, i);
     else
       jacobi2_resid_tile<T, N>(op, r, vout, tout, g, tx, ty, i);
   });
