@@ -135,6 +135,22 @@ __host__ __device__ __forceinline__ Weights edge_weights(const Geo &g, int x, in
   return w;
 }
 
+// ---- asynchronous global -> shared copies (cp.async) ------------------------
+// B bytes (4, 8 or 16; both addresses B-aligned) from global to shared memory
+// without passing through registers, cached in L1; completion is awaited per
+// commit group with cp_async_wait<K>() (all but the K most recent groups).
+template <int B>
+__device__ __forceinline__ void cp_async(void *sdst, const void *gsrc) {
+  static_assert(B == 4 || B == 8 || B == 16, "cp.async copies 4, 8 or 16 bytes");
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gsrc), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
+}
+
 // ---- vector loads / stores of one node's N values ------------------------
 
 template <typename T, int N>

@@ -615,8 +615,16 @@ __device__ __forceinline__ void or_add(const float (&mh)[N], const float (&ml)[N
 // and east neighbours from the shared row, north and south from the thread's
 // own registers), r32 and u32 stored, and the node's natural-residual term
 // returned (NaN if u is).
+// Float j (0 .. 2N - 1) of this thread's node in a b slot of
+// k_outer_resid_df (read when it is used, to spare registers).
 template <int N>
-__device__ __forceinline__ float or_node(const float *__restrict__ b, const Geo &g, int x, int y,
+__device__ __forceinline__ float or_bval(const unsigned char *slot, int tx, int j) {
+  constexpr int B = (N % 2 == 0) ? 16 : 8, K = B / 4;
+  return reinterpret_cast<const float *>(slot + ((size_t)(j / K) * kOrThreads + tx) * B)[j % K];
+}
+
+template <int N>
+__device__ __forceinline__ float or_node(const unsigned char *bslot, const Geo &g, int x, int y,
                                          const float (&rh_s)[N][kOrThreads], const float (&rl_s)[N][kOrThreads],
                                          int tx, const float (&ph)[N], const float (&pl)[N], const float (&uh)[N],
                                          const float (&ul)[N], const float (&uf)[N], const float (&nh)[N],
@@ -659,17 +667,15 @@ __device__ __forceinline__ float or_node(const float *__restrict__ b, const Geo 
   // r_i = rh_i + rl_i, not renormalised: rh_i the rounded sum of the heads
   float rh[N], rl[N], mu = -INFINITY;
   {
-    float bh[N], bl[N];  // b as k_rhs_df stores it
-    ldn<float, N>(b + n * 2 * N, bh);
-    ldn<float, N>(b + n * 2 * N + N, bl);
+    // b as k_rhs_df stores it: N heads, then N tails
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const f2 p = mul_f2(g.teh, g.tel, sh[i], sl[i]);  // tau eps sum_m w_nm (u_m - u)
       const f2 q = mul_f2(m0h, m0l, uh[i], ul[i]);      // Mhat u
-      const f2 s1 = two_sum(bh[i], -q.h);
+      const f2 s1 = two_sum(or_bval<N>(bslot, tx, i), -q.h);
       const f2 s2 = two_sum(s1.h, p.h);
       rh[i] = s2.h;
-      rl[i] = s1.l + s2.l + ((bl[i] - q.l) + p.l);
+      rl[i] = s1.l + s2.l + ((or_bval<N>(bslot, tx, N + i) - q.l) + p.l);
       mu = fmaxf(mu, rh[i]);
     }
   }
@@ -694,26 +700,101 @@ __device__ __forceinline__ float or_node(const float *__restrict__ b, const Geo 
   return uf[0] == uf[0] ? e : __int_as_float(0x7fc00000);
 }
 
+// The rows of u a thread needs next (two ahead) and the b of its next node
+// are copied to shared memory with cp.async while the thread works on the
+// current row, so the loads' latency overlaps the double-float arithmetic.
+// A node's 8N bytes (N doubles of u, or the 2N floats of b) go as OrCopy<N>::C
+// pieces of B bytes, stored piece-major ([piece][thread]) so that a warp's
+// shared-memory reads are conflict-free.
 template <int N>
-__global__ void __launch_bounds__(kOrThreads) k_outer_resid_df(const double *__restrict__ u,
+struct OrCopy {
+  static constexpr int B = (N % 2 == 0) ? 16 : 8, C = 8 * N / B;
+  static constexpr int kSlotBytes = 8 * N * kOrThreads;  // one row of the strip
+};
+// Shared memory of k_outer_resid_df beyond its static arrays: two u slots and
+// two b slots.
+template <int N>
+constexpr size_t outer_resid_smem() { return 4 * (size_t)OrCopy<N>::kSlotBytes; }
+
+template <int N>
+__device__ __forceinline__ void or_issue(unsigned char *slot, const void *gsrc, int tx) {
+  using O = OrCopy<N>;
+#pragma unroll
+  for (int c = 0; c < O::C; ++c)
+    cp_async<O::B>(slot + ((size_t)c * kOrThreads + tx) * O::B, static_cast<const unsigned char *>(gsrc) + c * O::B);
+}
+
+// The thread's 8N bytes back from its slot, as T values (double: u, float: b).
+template <int N, typename T, int M>
+__device__ __forceinline__ void or_read(const unsigned char *slot, int tx, T (&v)[M]) {
+  using O = OrCopy<N>;
+  static_assert(M * sizeof(T) == 8 * N, "one node's bytes");
+#pragma unroll
+  for (int c = 0; c < O::C; ++c) {
+    const unsigned char *q = slot + ((size_t)c * kOrThreads + tx) * O::B;
+    constexpr int K = O::B / sizeof(T);
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[c * K + j] = reinterpret_cast<const T *>(q)[j];
+  }
+}
+
+// Split a node's u (binary64) into heads, tails and the float rounding.
+template <int N>
+__device__ __forceinline__ void or_split(const double (&t)[N], float (&h)[N], float (&l)[N], float (&f)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    split_f64(t[i], h[i], l[i]);
+    f[i] = f64_to_f32_rn(t[i]);  // the rounding k_outer_update tests against
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kOrThreads, 2) k_outer_resid_df(const double *__restrict__ u,
                                                                const float *__restrict__ b, Geo g,
                                                                float *__restrict__ r32, float *__restrict__ u32,
                                                                double *__restrict__ rho) {
   __shared__ float s_h[2][N][kOrThreads], s_l[2][N][kOrThreads];
+  extern __shared__ __align__(16) unsigned char or_ring[];
+  // slots: u of rows in flight at [0, 2), b at [2, 4)
+  auto uslot = [&](int q) { return or_ring + q * OrCopy<N>::kSlotBytes; };
+  auto bslot = [&](int q) { return or_ring + (2 + q) * OrCopy<N>::kSlotBytes; };
   const int tx = threadIdx.x;
   const int x = blockIdx.x * (kOrThreads - 2) - 1 + tx;
   const int y0 = blockIdx.y * kOrRows;
   const bool col = x >= 0 && x <= g.W;
   const bool out = col && tx >= 1 && tx <= kOrThreads - 2;
+  auto u_ok = [&](int y) { return col && y >= 0 && y <= g.H; };
+  auto u_row = [&](int y) { return u + ((int64_t)y * g.Wn + x) * N; };
+  auto b_row = [&](int y) { return b + ((int64_t)y * g.Wn + x) * 2 * N; };
   float ph[N], pl[N], ch[N], cl[N], cf[N];
   or_load_row<N>(u, g, col, x, y0 - 1, ph, pl, cf);
   or_load_row<N>(u, g, col, x, y0, ch, cl, cf);
+  // the first group: u of row y0 + 1, b of row y0
+  if (u_ok(y0 + 1)) or_issue<N>(uslot(0), u_row(y0 + 1), tx);
+  if (out && y0 <= g.H) or_issue<N>(bslot(0), b_row(y0), tx);
+  cp_async_commit();
   float e = 0.f;
   for (int k = 0; k < kOrRows; ++k) {
     const int y = y0 + k;
     if (y > g.H) break;  // the same for every thread of the block
+    // the next group: u of row y + 2 (the north row of the next iteration)
+    // and b of row y + 1, into the slots this thread emptied last iteration
+    const int nxt = (k + 1) & 1, cur = k & 1;
+    if (k + 1 < kOrRows) {
+      if (u_ok(y + 2)) or_issue<N>(uslot(nxt), u_row(y + 2), tx);
+      if (out && y + 1 <= g.H) or_issue<N>(bslot(nxt), b_row(y + 1), tx);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();  // this iteration's group (u of row y + 1, b of row y) has landed
     float nh[N], nl[N], nf[N];
-    or_load_row<N>(u, g, col, x, y + 1, nh, nl, nf);
+    if (u_ok(y + 1)) {
+      double t[N];
+      or_read<N>(uslot(cur), tx, t);
+      or_split<N>(t, nh, nl, nf);
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; ++i) nh[i] = nl[i] = nf[i] = 0.f;
+    }
     const int buf = k & 1;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -721,8 +802,9 @@ __global__ void __launch_bounds__(kOrThreads) k_outer_resid_df(const double *__r
       s_l[buf][i][tx] = cl[i];
     }
     __syncthreads();  // with two buffers, one barrier per row
-    if (out) e = nanmax<float>(e, or_node<N>(b, g, x, y, s_h[buf], s_l[buf], tx, ph, pl, ch, cl, cf, nh, nl, r32,
-                                             u32));
+    if (out)
+      e = nanmax<float>(e, or_node<N>(bslot(cur), g, x, y, s_h[buf], s_l[buf], tx, ph, pl, ch, cl, cf, nh, nl, r32,
+                                      u32));
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       ph[i] = ch[i];
@@ -732,6 +814,7 @@ __global__ void __launch_bounds__(kOrThreads) k_outer_resid_df(const double *__r
       cf[i] = nf[i];
     }
   }
+  cp_async_wait<0>();
   block_max_atomic(e, rho);
 }
 

@@ -305,9 +305,13 @@ struct Launch {
   }
   static int outer_resid(const double *u, const float *b, const Geo &g, float *r32, float *u32, double *rho,
                          bool rho32, cudaStream_t s) {
-    if (rho32)
+    if (rho32) {
+      static const cudaError_t attr = cudaFuncSetAttribute(
+          k_outer_resid_df<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)outer_resid_smem<N>());
+      (void)attr;
       k_outer_resid_df<N><<<dim3((g.W + 1 + kOrThreads - 3) / (kOrThreads - 2), (g.H + kOrRows) / kOrRows),
-                            kOrThreads, 0, s>>>(u, b, g, r32, u32, rho);
+                            kOrThreads, outer_resid_smem<N>(), s>>>(u, b, g, r32, u32, rho);
+    }
     else
       k_outer_resid<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(u, b, g, r32, u32, rho);
     return 1;
