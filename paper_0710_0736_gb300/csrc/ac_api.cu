@@ -598,7 +598,7 @@ int coarse_vcycle(ac_ctx *ctx, Solve &S, int k, void **res) {
       a.op[l] = S.lv[k + l].op;
       ops += 4.0 * (double)S.lv[k + l].n * ns;
     }
-    AC_RUNB(AC_PROF_COARSE, ops + 2 * lk, o->coarse_tail(a, L.r, L.v, S.coarse_gs ? ac::kGsSweeps : kCoarseSweeps, kCoarsestSweeps, smem, S.coarse_gs, ctx->s));
+    AC_RUNB(AC_PROF_COARSE, ops + 2 * lk, o->coarse_tail(a, L.r, L.v, kCoarseSweeps, kCoarsestSweeps, smem, S.coarse_gs, ctx->s));
     *res = L.v;
     return AC_OK;
   }

@@ -1751,204 +1751,185 @@ __device__ __forceinline__ void jacobi2_tile(const T *__restrict__ op, const T *
 // reverse (symmetric Gauss-Seidel).  Rows with a zero diagonal (no free fine
 // node of the phase under them) keep 0.
 
-// A colour pass gives each thread at most one node: thread t takes row
-// t / kGsPerRow of the region and the (t % kGsPerRow)-th node of the colour in
-// that row (regions are at most 3 kGsPerRow wide and their rows x kGsPerRow
-// at most kJ2Threads).  The row's first column of a colour follows from the
-// row's colour offset, which each thread computes once per region.
-constexpr int kGsPerRow = 12;
-
-// (x0 + y0 + 2 lo + row) mod 3: the colour of the region's first node in the
-// thread's row (x0, y0: grid position of array index 0; may be negative)
-__device__ __forceinline__ int gs_row_base(int x0, int y0, int lo) {
-  const int v = (x0 + y0 + 2 * lo + (int)threadIdx.x / kGsPerRow) % 3;
-  return v < 0 ? v + 3 : v;
-}
-
-// The thread's update in the pass of colour c over the region [LO, HX] x
-// [LO, HY] of the staged arrays: v = (r - sum of the off-diagonal terms) / d
-// with the reciprocal of d staged in sI (0 on rows with a zero diagonal,
-// whose entries and r are 0 as well, and outside the grid).
-template <typename T, int AX, int AY, int LO, int HX, int HY>
-__device__ __forceinline__ void gs_colour_pass(const T (&sE)[AY][AX], const T (&sN)[AY][AX], const T (&sNE)[AY][AX],
-                                               const T (&sR)[AY][AX], const T (&sI)[AY][AX], T (&sV)[AY][AX], int base,
-                                               int c) {
-  static_assert(HX - LO + 1 <= 3 * kGsPerRow && (HY - LO + 1) * kGsPerRow <= kJ2Threads, "colour pass region");
-  const int row = (int)threadIdx.x / kGsPerRow, k = (int)threadIdx.x - row * kGsPerRow;
-  if (row > HY - LO) return;
-  int ph = c - base;
-  ph += ph < 0 ? 3 : 0;
-  const int ay = LO + row, ax = LO + ph + 3 * k;
-  if (ax > HX) return;
-  T s = sE[ay][ax] * sV[ay][ax + 1];
-  s += sE[ay][ax - 1] * sV[ay][ax - 1];
-  s += sN[ay][ax] * sV[ay + 1][ax];
-  s += sN[ay - 1][ax] * sV[ay - 1][ax];
-  s += sNE[ay][ax] * sV[ay + 1][ax + 1];
-  s += sNE[ay - 1][ax - 1] * sV[ay - 1][ax - 1];
-  sV[ay][ax] = (sR[ay][ax] - s) * sI[ay][ax];
-}
+// The blocks' work is spread over threads by horizontal triplets: a thread
+// owns three consecutive nodes of a row of the first sweep's region -- one
+// of each colour -- and keeps their operator entries, 1/d and r in registers
+// for both sweeps and the residual; only the iterate is in shared memory.
+// Each row's triplets start on a node of colour 0, so a thread's node q has
+// colour q and the pass of colour q updates node q at a compile-time offset.
+// kGsTrip triplets per row (one more than the widest region needs, for the
+// row's shift) and kGsThreads threads per block.
+constexpr int kGsTrip = 13, kGsThreads = 288;
+enum { kGsPost = 0, kGsZero = 1, kGsPreResid = 2 };
 
 __device__ __forceinline__ float rcp_t(float d) { return __frcp_rn(d); }
 __device__ __forceinline__ double rcp_t(double d) { return __drcp_rn(d); }
 
-// SW (1 or 2) sweeps from vin (from 0 if ZERO_IN: vin is not read): the
-// operator and vin on the tile + SW, r on the tile + SW - 1; sweep s (1 ..
-// SW) on the tile + SW - s.  Two sweeps run the colours forward, then
-// backward; a single sweep runs them in the order `FWD` asks.
-template <typename T, int N, bool ZERO_IN, int SW, bool FWD>
-__device__ __forceinline__ void gs_tile(const T *__restrict__ op, const T *__restrict__ r, const T *vin, T *vout,
-                                        const Geo &g, int bxt, int byt, int i) {
-  constexpr int AX = kJ2X + 2 * SW, AY = kJ2Y + 2 * SW;
-  __shared__ T sC[AY][AX], sE[AY][AX], sN[AY][AX], sNE[AY][AX], sV[AY][AX], sR[AY][AX], sI[AY][AX];
-  const int64_t nc = (int64_t)g.Wn * (g.H + 1);
-  const T *C = op + (0 * N + i) * nc, *E = op + (1 * N + i) * nc, *Nn = op + (2 * N + i) * nc,
-          *NE = op + (3 * N + i) * nc, *ri = r + i * nc, *vi = vin + i * nc;
-  T *vo = vout + i * nc;
-  const int x0 = bxt * kJ2X - SW, y0 = byt * kJ2Y - SW;
-  int live = 0;
-  for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
-    const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
-    const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
-    const T c = in ? C[in ? (int64_t)y * g.Wn + x : 0] : T(0);
-    sC[ay][ax] = c;
-    live |= (ax >= SW && ax < SW + kJ2X && ay >= SW && ay < SW + kJ2Y && c > T(0)) ? 1 : 0;
-  }
-  if (!__syncthreads_or(live)) {
-    for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
-      const int x = x0 + SW + t % kJ2X, y = y0 + SW + t / kJ2X;
-      if (x <= g.W && y <= g.H) vo[(int64_t)y * g.Wn + x] = T(0);
-    }
-    return;
-  }
-  for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
-    const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
-    const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
-    const int64_t K = in ? (int64_t)y * g.Wn + x : 0;
-    sE[ay][ax] = in ? E[K] : T(0);
-    sN[ay][ax] = in ? Nn[K] : T(0);
-    sNE[ay][ax] = in ? NE[K] : T(0);
-    sV[ay][ax] = (!ZERO_IN && in) ? vi[K] : T(0);
-    const bool rin = in && ax >= 1 && ax <= AX - 2 && ay >= 1 && ay <= AY - 2;
-    sR[ay][ax] = rin ? ri[K] : T(0);
-    const T c = sC[ay][ax];
-    sI[ay][ax] = c > T(0) ? rcp_t(c) : T(0);
-  }
-  const int b1 = gs_row_base(x0, y0, 1);
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    gs_colour_pass<T, AX, AY, 1, AX - 2, AY - 2>(sE, sN, sNE, sR, sI, sV, b1, (SW == 2 || FWD) ? q : 2 - q);
-    __syncthreads();
-  }
-  if constexpr (SW == 2) {
-    const int b2 = gs_row_base(x0, y0, 2);
-#pragma unroll
-    for (int c = 2; c >= 0; --c) {
-      gs_colour_pass<T, AX, AY, 2, AX - 3, AY - 3>(sE, sN, sNE, sR, sI, sV, b2, c);
-      __syncthreads();
-    }
-  }
-  for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
-    const int tx = t % kJ2X, ty = t / kJ2X, x = x0 + SW + tx, y = y0 + SW + ty;
-    if (x <= g.W && y <= g.H) vo[(int64_t)y * g.Wn + x] = sV[ty + SW][tx + SW];
-  }
-}
+// Two Gauss-Seidel sweeps on a tile of phase i, colours forward then
+// backward (see above).  MODE kGsPost: from vin, the first sweep on the tile
+// + 1, the second on the tile, v written.  kGsZero: the same from v = 0 (vin
+// is not read).  kGsPreResid: from v = 0, the first sweep on the tile + 2,
+// the second on the tile + 1, then v and the residual t = r - S v written on
+// the tile (k_coarse_resid's arithmetic order).  Rows with a zero diagonal
+// keep 0 in v and t.  INTERIOR: every node the block reads lies in the grid
+// (no range tests).
+template <int MODE>
+struct GsShape {
+  static constexpr int H1 = MODE == kGsPreResid ? 2 : 1;        // halo of the first sweep's region
+  static constexpr int W1 = kJ2X + 2 * H1, R1 = kJ2Y + 2 * H1;  // its width and height
+  // shared columns cx <-> grid x = xs + cx: the region is cx in [3, 2 + W1]
+  // (a ring at 2 and 3 + W1); rows cy <-> y = ys + cy: the region is [1, R1]
+  static constexpr int X1 = 3, AX = 3 * kGsTrip + 4, AY = R1 + 2;
+};
 
-// Pre-smoothing from v = 0 (SW sweeps, colours forward then backward)
-// fused with the level's residual t = r - S v: the operator on the tile +
-// SW + 1, r on the tile + SW; sweep s on the tile + SW + 1 - s, the residual
-// on the tile.
-template <typename T, int N, int SW>
-__device__ __forceinline__ void gs_resid_tile(const T *__restrict__ op, const T *__restrict__ r,
-                                              T *__restrict__ vout, T *__restrict__ tout, const Geo &g, int bxt,
-                                              int byt, int i) {
-  constexpr int H0 = SW + 1;  // halo of the staged operator
-  constexpr int AX = kJ2X + 2 * H0, AY = kJ2Y + 2 * H0;
-  __shared__ T sC[AY][AX], sE[AY][AX], sN[AY][AX], sNE[AY][AX], sV[AY][AX], sR[AY][AX], sI[AY][AX];
+template <typename T, int N, int MODE, bool INTERIOR>
+__device__ __forceinline__ void gs_tile_body(const T *__restrict__ op, const T *__restrict__ r, const T *vin, T *vout,
+                                             T *__restrict__ tout, const Geo &g, int i, int xs, int ys,
+                                             T (&sV)[GsShape<MODE>::AY][GsShape<MODE>::AX]) {
+  using S = GsShape<MODE>;
+  constexpr int H1 = S::H1, W1 = S::W1, R1 = S::R1, X1 = S::X1, AX = S::AX, AY = S::AY;
+  // rows of triplets fit the block; with the row shift sh <= 2 the triplets
+  // cover columns [1 + sh, 3 kGsTrip + sh] (a region [3, 2 + W1]) and touch
+  // [sh, 3 kGsTrip + sh + 1] < AX
+  static_assert(R1 * kGsTrip <= kGsThreads && 3 * kGsTrip >= X1 - 1 + W1 && 3 * kGsTrip + 3 < AX, "triplet grid");
   const int64_t nc = (int64_t)g.Wn * (g.H + 1);
   const T *C = op + (0 * N + i) * nc, *E = op + (1 * N + i) * nc, *Nn = op + (2 * N + i) * nc,
           *NE = op + (3 * N + i) * nc, *ri = r + i * nc;
-  T *vo = vout + i * nc, *to = tout + i * nc;
-  const int x0 = bxt * kJ2X - H0, y0 = byt * kJ2Y - H0;
+  const int row = (int)threadIdx.x / kGsTrip, trip = (int)threadIdx.x - row * kGsTrip;
+  const bool owner = row < R1;
+  const int cy = row + 1, y = ys + cy;
+  int sh = -(xs + 1 + y) % 3;  // shift so that node 0 (cx0) has colour 0
+  sh += sh < 0 ? 3 : 0;
+  const int cx0 = 1 + sh + 3 * trip, x0 = xs + cx0;
+  // node q: in the first region, the second, the tile (where v and t are
+  // written), the grid
+  unsigned in1 = 0u, in2 = 0u, inT = 0u, grid = 0u;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int cx = cx0 + q;
+    if (owner && cx >= X1 && cx <= X1 + W1 - 1) in1 |= 1u << q;
+    if (owner && cx >= X1 + 1 && cx <= X1 + W1 - 2 && cy >= 2 && cy <= R1 - 1) in2 |= 1u << q;
+    if (owner && cx >= X1 + H1 && cx <= X1 + H1 + kJ2X - 1 && cy >= 1 + H1 && cy <= H1 + kJ2Y) inT |= 1u << q;
+    if (owner && (INTERIOR || (x0 + q >= 0 && x0 + q <= g.W && y >= 0 && y <= g.H))) grid |= 1u << q;
+  }
+  const int64_t K0 = (int64_t)y * g.Wn + x0;
+  // every load of the tile first (one round trip of latency): the
+  // operator entries and r of the triplet into registers, the iterate --
+  // vin (kGsPost) or 0 -- on the region, its ring and the spare columns
+  T cD[3], cI[3], cR[3], cE[3], cW[3], cN[3], cS[3], cNE[3], cSW[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const bool on = (grid >> q) & 1u;
+    const bool w = on && (INTERIOR || x0 + q > 0), s = on && (INTERIOR || y > 0);
+    cD[q] = on ? C[K0 + q] : T(0);
+    cR[q] = on ? ri[K0 + q] : T(0);
+    cE[q] = on ? E[K0 + q] : T(0);
+    cN[q] = on ? Nn[K0 + q] : T(0);
+    cNE[q] = on ? NE[K0 + q] : T(0);
+    cW[q] = w ? E[K0 + q - 1] : T(0);
+    cS[q] = s ? Nn[K0 + q - g.Wn] : T(0);
+    cSW[q] = w && s ? NE[K0 + q - g.Wn - 1] : T(0);
+  }
+  const T *vi = MODE == kGsPost ? vin + i * nc : nullptr;
+  for (int t = threadIdx.x; t < AX * AY; t += kGsThreads) {
+    const int bx = t % AX, by = t / AX, gx = xs + bx, gy = ys + by;
+    T v = T(0);
+    if (MODE == kGsPost && (INTERIOR || (gx >= 0 && gx <= g.W && gy >= 0 && gy <= g.H)))
+      v = vi[(int64_t)gy * g.Wn + gx];
+    sV[by][bx] = v;
+  }
   int live = 0;
-  for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
-    const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
-    const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
-    const T c = in ? C[in ? (int64_t)y * g.Wn + x : 0] : T(0);
-    sC[ay][ax] = c;
-    live |= (ax >= H0 && ax < H0 + kJ2X && ay >= H0 && ay < H0 + kJ2Y && c > T(0)) ? 1 : 0;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    live |= ((inT >> q) & 1u) && cD[q] > T(0) ? 1 : 0;
+    cI[q] = cD[q] > T(0) ? rcp_t(cD[q]) : T(0);
   }
   if (!__syncthreads_or(live)) {
-    for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
-      const int x = x0 + H0 + t % kJ2X, y = y0 + H0 + t / kJ2X;
-      if (x <= g.W && y <= g.H) {
-        vo[(int64_t)y * g.Wn + x] = T(0);
-        to[(int64_t)y * g.Wn + x] = T(0);
+    // a tile with no live row: v (and t) are 0 whatever vin
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      if (((inT & grid) >> q) & 1u) {
+        vout[i * nc + K0 + q] = T(0);
+        if (MODE == kGsPreResid) tout[i * nc + K0 + q] = T(0);
       }
-    }
     return;
   }
-  for (int t = threadIdx.x; t < AX * AY; t += kJ2Threads) {
-    const int ax = t % AX, ay = t / AX, x = x0 + ax, y = y0 + ay;
-    const bool in = x >= 0 && x <= g.W && y >= 0 && y <= g.H;
-    const int64_t K = in ? (int64_t)y * g.Wn + x : 0;
-    sE[ay][ax] = in ? E[K] : T(0);
-    sN[ay][ax] = in ? Nn[K] : T(0);
-    sNE[ay][ax] = in ? NE[K] : T(0);
-    sV[ay][ax] = T(0);
-    const bool rin = in && ax >= 1 && ax <= AX - 2 && ay >= 1 && ay <= AY - 2;
-    sR[ay][ax] = rin ? ri[K] : T(0);
-    const T c = sC[ay][ax];
-    sI[ay][ax] = c > T(0) ? rcp_t(c) : T(0);
-  }
-  const int b1 = gs_row_base(x0, y0, 1);
+  T *const sv = &sV[owner ? cy : 1][cx0];  // node 0 of the thread's triplet (read only by owners)
+#define AC_GS_UPDATE(q)                                          \
+  do {                                                           \
+    T s_ = cE[q] * sv[(q) + 1];                                  \
+    s_ += cW[q] * sv[(q)-1];                                     \
+    s_ += cN[q] * sv[(q) + AX];                                  \
+    s_ += cS[q] * sv[(q)-AX];                                    \
+    s_ += cNE[q] * sv[(q) + AX + 1];                             \
+    s_ += cSW[q] * sv[(q)-AX - 1];                               \
+    sv[q] = (cR[q] - s_) * cI[q];                                \
+  } while (0)
+  if (in1 & 1u) AC_GS_UPDATE(0);
   __syncthreads();
+  if (in1 & 2u) AC_GS_UPDATE(1);
+  __syncthreads();
+  if (in1 & 4u) AC_GS_UPDATE(2);
+  __syncthreads();
+  if (in2 & 4u) AC_GS_UPDATE(2);
+  __syncthreads();
+  if (in2 & 2u) AC_GS_UPDATE(1);
+  __syncthreads();
+  if (in2 & 1u) AC_GS_UPDATE(0);
+  __syncthreads();
+#undef AC_GS_UPDATE
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    gs_colour_pass<T, AX, AY, 1, AX - 2, AY - 2>(sE, sN, sNE, sR, sI, sV, b1, c);
-    __syncthreads();
-  }
-  if constexpr (SW == 2) {
-    const int b2 = gs_row_base(x0, y0, 2);
-#pragma unroll
-    for (int c = 2; c >= 0; --c) {
-      gs_colour_pass<T, AX, AY, 2, AX - 3, AY - 3>(sE, sN, sNE, sR, sI, sV, b2, c);
-      __syncthreads();
+  for (int q = 0; q < 3; ++q) {
+    if (!(((inT & grid) >> q) & 1u)) continue;
+    const T vk = sv[q];
+    vout[i * nc + K0 + q] = vk;
+    if constexpr (MODE == kGsPreResid) {
+      T s = T(0);
+      s += cE[q] * sv[q + 1];
+      s += cW[q] * sv[q - 1];
+      s += cN[q] * sv[q + AX];
+      s += cS[q] * sv[q - AX];
+      s += cNE[q] * sv[q + AX + 1];
+      s += cSW[q] * sv[q - AX - 1];
+      tout[i * nc + K0 + q] = cD[q] > T(0) ? cR[q] - cD[q] * vk - s : T(0);
     }
-  }
-  for (int t = threadIdx.x; t < kJ2X * kJ2Y; t += kJ2Threads) {
-    const int tx = t % kJ2X, ty = t / kJ2X, x = x0 + H0 + tx, y = y0 + H0 + ty;
-    if (x > g.W || y > g.H) continue;
-    const int ax = tx + H0, ay = ty + H0;
-    const T d = sC[ay][ax], vk = sV[ay][ax];
-    T s = T(0);
-    s += sE[ay][ax] * sV[ay][ax + 1];
-    s += sE[ay][ax - 1] * sV[ay][ax - 1];
-    s += sN[ay][ax] * sV[ay + 1][ax];
-    s += sN[ay - 1][ax] * sV[ay - 1][ax];
-    s += sNE[ay][ax] * sV[ay + 1][ax + 1];
-    s += sNE[ay - 1][ax - 1] * sV[ay - 1][ax - 1];
-    const int64_t K = (int64_t)y * g.Wn + x;
-    vo[K] = vk;
-    to[K] = d > T(0) ? sR[ay][ax] - d * vk - s : T(0);
   }
 }
 
+template <typename T, int N, int MODE>
+__device__ __forceinline__ void gs_tile_rt(const T *__restrict__ op, const T *__restrict__ r, const T *vin, T *vout,
+                                           T *__restrict__ tout, const Geo &g, int bxt, int byt, int i) {
+  using S = GsShape<MODE>;
+  __shared__ T sV[S::AY][S::AX];
+  const int xs = bxt * kJ2X - S::H1 - S::X1, ys = byt * kJ2Y - S::H1 - 1;
+  // every node the block can read: columns xs - 1 .. xs + AX - 1 (a west
+  // neighbour of the first triplet), rows ys - 1 .. ys + AY - 1
+  if (xs >= 1 && xs + S::AX <= g.W && ys >= 1 && ys + S::AY <= g.H)
+    gs_tile_body<T, N, MODE, true>(op, r, vin, vout, tout, g, i, xs, ys, sV);
+  else
+    gs_tile_body<T, N, MODE, false>(op, r, vin, vout, tout, g, i, xs, ys, sV);
+}
+
 // (the register bound keeps as many blocks per SM as the shared memory
-// allows: eight in float, five in double)
+// allows: eight in float, five in double; the Gauss-Seidel tiles hold their
+// triplets' operator entries in registers: four blocks of 288 threads in
+// float, two in double, without spills)
 constexpr int j2_min_blocks(int elem) { return elem == 4 ? 8 : 5; }
+#ifndef AC_GS_BLOCKS
+#define AC_GS_BLOCKS 4
+#endif
+constexpr int pair_min_blocks(int elem, bool gs) { return gs ? (elem == 4 ? AC_GS_BLOCKS : 2) : j2_min_blocks(elem); }
 // Two smoothing sweeps per tile of a coarse level: 3-colour Gauss-Seidel
 // (GS) or l1-Jacobi.
 template <typename T, int N, bool ZERO_IN, bool GS>
-__global__ void __launch_bounds__(kJ2Threads, j2_min_blocks(sizeof(T))) k_coarse_pair(const T *__restrict__ op, const T *__restrict__ r,
+__global__ void __launch_bounds__(GS ? kGsThreads : kJ2Threads, pair_min_blocks(sizeof(T), GS)) k_coarse_pair(const T *__restrict__ op, const T *__restrict__ r,
                                                                   const T *vin, T *vout, Geo g, TileList L) {
   for_each_tile(L, g, [&](int tx, int ty, int i, bool dying) {
     const int64_t nc = (int64_t)g.Wn * (g.H + 1);
     if (dying)
       tile_zero<T>(g, tx, ty, vout + i * nc, (T *)nullptr);
     else if constexpr (GS)
-      gs_tile<T, N, ZERO_IN, kGsSweeps, ZERO_IN>(op, r, vin, vout, g, tx, ty, i);
+      gs_tile_rt<T, N, ZERO_IN ? kGsZero : kGsPost>(op, r, vin, vout, (T *)nullptr, g, tx, ty, i);
     else
       jacobi2_tile<T, N, ZERO_IN>(op, r, vin, vout, g, tx, ty, i);
   });
@@ -2055,7 +2036,7 @@ __device__ __forceinline__ void jacobi2_resid_tile(const T *__restrict__ op, con
 }
 
 template <typename T, int N, bool GS>
-__global__ void __launch_bounds__(kJ2Threads, j2_min_blocks(sizeof(T))) k_coarse_pair_resid(const T *__restrict__ op,
+__global__ void __launch_bounds__(GS ? kGsThreads : kJ2Threads, pair_min_blocks(sizeof(T), GS)) k_coarse_pair_resid(const T *__restrict__ op,
                                                                         const T *__restrict__ r, T *__restrict__ vout,
                                                                         T *__restrict__ tout, Geo g, TileList L) {
   for_each_tile(L, g, [&](int tx, int ty, int i, bool dying) {
@@ -2063,7 +2044,7 @@ __global__ void __launch_bounds__(kJ2Threads, j2_min_blocks(sizeof(T))) k_coarse
     if (dying)
       tile_zero<T>(g, tx, ty, vout + i * nc, tout + i * nc);
     else if constexpr (GS)
-      gs_resid_tile<T, N, kGsSweeps>(op, r, vout, tout, g, tx, ty, i);
+      gs_tile_rt<T, N, kGsPreResid>(op, r, (const T *)nullptr, vout, tout, g, tx, ty, i);
     else
       jacobi2_resid_tile<T, N>(op, r, vout, tout, g, tx, ty, i);
   });

@@ -121,14 +121,15 @@ struct SolverLaunch {
     for (int p = 0; p < sweeps / 2; ++p) {
       if (p == 0 && zero_start) {
         // v is not read: the pair can write it
-        const dim3 grid = tile_grid(g, L, N, k_coarse_pair<T, N, true, GS>, kJ2Threads);
-        k_coarse_pair<T, N, true, GS><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)v, (T *)v,
-                                                                   g, tf);
+        constexpr int th = GS ? kGsThreads : kJ2Threads;
+        const dim3 grid = tile_grid(g, L, N, k_coarse_pair<T, N, true, GS>, th);
+        k_coarse_pair<T, N, true, GS><<<grid, th, 0, s>>>((const T *)op, (const T *)r, (const T *)v, (T *)v, g, tf);
       } else {
         void *nxt = cur == v ? tmp : v;
-        const dim3 grid = tile_grid(g, L, N, k_coarse_pair<T, N, false, GS>, kJ2Threads);
-        k_coarse_pair<T, N, false, GS><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)cur,
-                                                                    (T *)nxt, g, tf);
+        constexpr int th = GS ? kGsThreads : kJ2Threads;
+        const dim3 grid = tile_grid(g, L, N, k_coarse_pair<T, N, false, GS>, th);
+        k_coarse_pair<T, N, false, GS><<<grid, th, 0, s>>>((const T *)op, (const T *)r, (const T *)cur, (T *)nxt, g,
+                                                            tf);
         cur = nxt;
       }
       ++k;
@@ -148,13 +149,14 @@ struct SolverLaunch {
                                 cudaStream_t s) {
     const TileList tf = item_list(L);
     if constexpr (sizeof(T) == 4) {
-      const dim3 grid = tile_grid(g, L, N, k_coarse_pair_resid<T, N, GS>, kJ2Threads);
-      k_coarse_pair_resid<T, N, GS><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (T *)v, (T *)t, g, tf);
+      constexpr int th = GS ? kGsThreads : kJ2Threads;
+      const dim3 grid = tile_grid(g, L, N, k_coarse_pair_resid<T, N, GS>, th);
+      k_coarse_pair_resid<T, N, GS><<<grid, th, 0, s>>>((const T *)op, (const T *)r, (T *)v, (T *)t, g, tf);
       return 1;
     } else {
-      const dim3 grid = tile_grid(g, L, N, k_coarse_pair<T, N, true, GS>, kJ2Threads);
-      k_coarse_pair<T, N, true, GS><<<grid, kJ2Threads, 0, s>>>((const T *)op, (const T *)r, (const T *)v, (T *)v, g,
-                                                                 tf);
+      constexpr int th = GS ? kGsThreads : kJ2Threads;
+      const dim3 grid = tile_grid(g, L, N, k_coarse_pair<T, N, true, GS>, th);
+      k_coarse_pair<T, N, true, GS><<<grid, th, 0, s>>>((const T *)op, (const T *)r, (const T *)v, (T *)v, g, tf);
       return 1 + coarse_resid(op, r, v, g, t, L, s);
     }
   }

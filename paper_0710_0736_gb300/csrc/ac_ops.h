@@ -11,14 +11,6 @@ struct Geo;
 struct Galerkin0Table;
 struct MaskDirty;
 
-// Gauss-Seidel sweeps per coarse-level smoothing launch (1 or 2; a build
-// option for tuning).
-#ifndef AC_GS_SWEEPS
-#define AC_GS_SWEEPS 2
-#endif
-constexpr int kGsSweeps = AC_GS_SWEEPS;
-static_assert(kGsSweeps == 1 || kGsSweeps == 2, "Gauss-Seidel sweeps per launch: 1 or 2");
-
 // Scratch of the block-partial reductions: at most kMaxPartBlocks rows.
 constexpr int kMaxPartBlocks = 1024;
 
