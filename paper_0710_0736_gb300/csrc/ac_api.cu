@@ -696,7 +696,8 @@ int enqueue_correction(ac_ctx *ctx, Solve &S) {
   // level above (4 values per node and phase read and written)
   // the tiled levels' work lists are rebuilt by their Galerkin kernels
   if (tiled_end(S) > 1) AC_CUDA(cudaMemsetAsync(S.list_counts, 0, 2 * S.lv.size() * sizeof(int), ctx->s));
-  AC_RUNB(AC_PROF_TRANSFER, bm.n + 4 * l1, o->galerkin0(S.mask, g0, L1.g, S.tab0, L1.op, level_lists(S, 1), ctx->s));
+  AC_RUNB(AC_PROF_TRANSFER, bm.n + 4 * l1,
+          o->galerkin0(S.mask, g0, L1.g, S.tab0, L1.op, level_lists(S, 1), L1.lists.dirty, ctx->s));
   for (int k = 1; k + 1 < S.depth; ++k)
     AC_RUNB(AC_PROF_TRANSFER, 4.0 * (double)(S.lv[k].n + S.lv[k + 1].n) * bm.ns,
             o->galerkin(S.lv[k].op, S.lv[k].g, S.lv[k + 1].g, S.lv[k + 1].op, level_lists(S, k), level_lists(S, k + 1),

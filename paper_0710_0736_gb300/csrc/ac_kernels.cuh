@@ -1325,7 +1325,8 @@ __device__ __forceinline__ void galerkin0_node(const unsigned (&pk)[6][2], unsig
 // A tile whose boxes saw no mask change since its last computation (dirty
 // byte clear) keeps its operator and its live phases: only its flags and list
 // entries are renewed.  changed[tile] tells the next level whether the
-// tile's operator was rewritten this cycle.
+// tile's operator was rewritten this cycle.  A dense first level (tf null)
+// with dirty flags skips its clean tiles the same way.
 template <typename T, int N>
 __global__ void __launch_bounds__(kTileThreads) k_galerkin0(const uint8_t *__restrict__ mask, Geo gf, Geo gc,
                                                             Galerkin0Table tab, T *__restrict__ op,
@@ -1336,6 +1337,15 @@ __global__ void __launch_bounds__(kTileThreads) k_galerkin0(const uint8_t *__res
   __shared__ unsigned s_now, s_prev;
   __shared__ int s_base, s_dirty;
   unsigned wmask = (1u << N) - 1u;
+  if (!tf && dirty) {
+    // dense level: a tile whose boxes saw no mask change keeps its operator
+    const int64_t tile = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    if (threadIdx.x == 0) s_dirty = dirty[tile];
+    __syncthreads();
+    if (!s_dirty) return;
+    __syncthreads();  // every thread has read the flag before it is cleared
+    if (threadIdx.x == 0) dirty[tile] = 0;
+  }
   if (tf) {
     const int64_t tile = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
     if (threadIdx.x == 0) s_dirty = dirty[tile];

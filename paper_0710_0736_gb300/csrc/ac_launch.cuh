@@ -92,11 +92,11 @@ struct SolverLaunch {
     return 1;
   }
   static int galerkin0(const uint8_t *mask, const Geo &gf, const Geo &gc, const Galerkin0Table &tab, void *op,
-                       const LevelLists *L1, cudaStream_t s) {
+                       const LevelLists *L1, uint8_t *dirty, cudaStream_t s) {
     const dim3 grid((unsigned)tiles_x(gc), (unsigned)tiles_y(gc));
     k_galerkin0<T, N><<<grid, kTileThreads, 0, s>>>(mask, gf, gc, tab, (T *)op, L1 ? L1->flags : nullptr,
                                                   L1 ? L1->items : nullptr, L1 ? L1->tiles : nullptr,
-                                                  L1 ? L1->count : nullptr, L1 ? L1->dirty : nullptr,
+                                                  L1 ? L1->count : nullptr, L1 ? L1->dirty : dirty,
                                                   L1 ? L1->changed : nullptr);
     return 1;
   }

@@ -65,8 +65,11 @@ struct SolverOps {
   // kept dense
   int (*restrict0)(const void *rt, const Geo &gf, const Geo &gc, const void *op1, void *r1, const LevelLists *L1,
                    cudaStream_t s);
+  // dirty (dense level, nullable): per tile, the fine mask under it changed
+  // since its operator was computed; clean tiles are skipped, dirty ones
+  // recomputed and cleared
   int (*galerkin0)(const uint8_t *mask, const Geo &gf, const Geo &gc, const Galerkin0Table &tab, void *op,
-                   const LevelLists *L1, cudaStream_t s);
+                   const LevelLists *L1, uint8_t *dirty, cudaStream_t s);
   // Lc != null: a tiled coarse level from a tiled fine level (Lf)
   int (*galerkin)(const void *opf, const Geo &gf, const Geo &gc, void *opc, const LevelLists *Lf,
                   const LevelLists *Lc, cudaStream_t s);
