@@ -776,6 +776,8 @@ def main():
                 "outer_per_step": st.outer / max(1, st.steps), "plain_fp64_gpu": fp64,
                 "all_converged": bool(st.converged), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk,
+                # the library's kernel launches before the timed region (an ncu --launch-skip for it)
+                "launches_before_timed": int(launches0),
                 "profile_ms_sample": {"steps": BREAKDOWN_STEPS, "after": "the timed region, every class profiled",
                                       "ms": dict(zip(ac.PROF_CLASSES, [round(v, 3) for v in breakdown.ms]))},
                 "batch": batch, "adjoint": adjoint}
