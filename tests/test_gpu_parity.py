@@ -258,6 +258,39 @@ def test_ragged_sizes(ac, W, H, N):
     assert np.abs(seg.phase() - u_ref).max() < 1e-11
 
 
+def test_pixel_labels_at_near_ties(ac):
+    """Pixel labels (Sec. 4.3) on a field built of near-ties: phases 0 and 1
+    at 0.4 + e and 0.4 - e per node with e >= 0 drawn from 0 to 1e-5, so the
+    two pixel sums differ by 0 (an exact tie: the lowest index) to about
+    1e-4, on both sides of the float filter's 4e-6 margin.  The labels must
+    be the oracle's rule on the same field, bit for bit, and the node labels
+    too."""
+    W, H, N = 64, 48, 4
+    rng = np.random.default_rng(5)
+    levels = np.array([0.0, 0.0, 1e-9, 1e-8, 1e-7, 3e-7, 6e-7, 1e-6, 2e-6, 3e-6, 1e-5])
+    e = levels[rng.integers(0, levels.size, (H + 1) * (W + 1))]
+    e[: 5 * (W + 1)] = 0.0  # pixel rows 0..3: exact ties
+    u = np.empty(((H + 1) * (W + 1), N))
+    u[:, 0] = 0.4 + e
+    u[:, 1] = 0.4 - e
+    u[:, 2:] = 0.1
+    seg = _seg(ac, W, H, N)
+    seg.set_image(np.zeros((H, W, 3), np.float32))
+    seg.set_phase(u)
+    u_gpu = seg.phase()
+    assert np.array_equal(u_gpu, u)
+    nl_own, lab_own = oracle.labels(u, W, H)
+    lab = seg.segment(0)
+    assert np.array_equal(lab, lab_own)
+    assert np.array_equal(seg.node_labels(), nl_own)
+    # the field holds exact ties and margins around the filter's threshold
+    U = u.reshape(H + 1, W + 1, N)
+    v = 2 * U[:-1, :-1] + U[:-1, 1:] + U[1:, :-1] + 2 * U[1:, 1:]
+    m = v[..., 0] - v[..., 1]
+    assert (m == 0).any() and ((m > 0) & (m < 4e-6)).any() and (m > 1e-5).any()
+    seg.close()
+
+
 def test_empty_phase_and_constant_state(ac):
     W, H, N = 32, 16, 4
     img = synth.config_image("c1_64_n4_fp64", 3, W, H).astype(np.float64)
