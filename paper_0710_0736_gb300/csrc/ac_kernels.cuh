@@ -197,16 +197,21 @@ template <int N>
 __global__ void k_init_random(double *__restrict__ u, int64_t n, uint64_t seed) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
+  // -log U in float for a uniform U on the 2^23 midpoints (j + 1/2) 2^-23
+  // of (0, 1), exact in float (binary64 logarithms run on GB300's slow FP64
+  // pipe), widened exactly and normalised in binary64, so that the node lies
+  // on the simplex to binary64 rounding with every component > 0
   double e[N], s = 0;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     uint64_t z = splitmix64(seed ^ splitmix64((uint64_t)(k * N + i)));
-    double U = ((double)(z >> 11) + 0.5) * 0x1.0p-53;
-    e[i] = -log(U);
+    const float U = ((float)(uint32_t)(z >> 41) + 0.5f) * 0x1.0p-23f;
+    e[i] = f32_to_f64(-logf(U));
     s += e[i];
   }
+  const double inv = 1.0 / s;
 #pragma unroll
-  for (int i = 0; i < N; ++i) e[i] /= s;
+  for (int i = 0; i < N; ++i) e[i] *= inv;
   stn<double, N>(u + k * N, e);
 }
 
