@@ -148,6 +148,19 @@ AC_HD void split_f64(double d, float &h, float &l) {
   l = bits_f32(sign | tl);
 }
 
+// The binary64 significand of d truncated to 24 bits, as a float (the head
+// of split_f64, integer pipe): |d - head| <= 2^-23 |d|; 0 (signed) for
+// |d| < 2^-126; NaN for |d| >= 2^128, infinities and NaN.  The pixel-label
+// filter sums these heads of phase values in [0, 1] in float.
+AC_HD float f64_head(double d) {
+  uint32_t hi, lo;
+  f64_words(d, hi, lo);
+  const uint32_t sign = hi & 0x80000000u, ah = hi & 0x7FFFFFFFu;
+  uint32_t t = ah < 0x38100000u ? 0u : (((ah - 0x38000000u) << 3) | (lo >> 29));
+  t = ah >= 0x47F00000u ? 0x7FC00000u : t;
+  return bits_f32(sign | t);
+}
+
 // Double-float value h + l.
 struct f2 {
   float h, l;

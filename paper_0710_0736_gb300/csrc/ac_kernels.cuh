@@ -2801,19 +2801,6 @@ __device__ __forceinline__ void pixel_integrals(const double *__restrict__ u, co
     }
 }
 
-// The binary64 significand of d truncated to 24 bits, as a float (integer
-// pipe; |d - head| <= 2^-23 |d|); 0 for |d| < 2^-126.  For the label filter,
-// where d is a phase value in [0, 1] (NaN beyond the float range, so that the
-// filter defers to the binary64 path).
-__device__ __forceinline__ float f64_head(double d) {
-  uint32_t hi, lo;
-  f64_words(d, hi, lo);
-  const uint32_t sign = hi & 0x80000000u, ah = hi & 0x7FFFFFFFu;
-  uint32_t t = ah < 0x38100000u ? 0u : (((ah - 0x38000000u) << 3) | (lo >> 29));
-  t = ah >= 0x47F00000u ? 0x7FC00000u : t;  // out of float range, infinities and NaN: NaN
-  return bits_f32(sign | t);
-}
-
 // argmax with the lowest index on ties.
 template <int N>
 __device__ __forceinline__ int argmax_low(const double (&v)[N]) {

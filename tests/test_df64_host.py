@@ -43,6 +43,14 @@ int main(int argc, char **argv) {
       double d = ac::f32_to_f64(f);
       fwrite(&d, 8, 1, stdout);
     }
+  } else if (mode == 'h') {  // doubles -> f64_head
+    size_t n = in.size() / 8;
+    for (size_t i = 0; i < n; ++i) {
+      double d;
+      std::memcpy(&d, &in[8 * i], 8);
+      float o = ac::f64_head(d);
+      fwrite(&o, 4, 1, stdout);
+    }
   } else if (mode == 'a') {  // float quadruples (ah, al, bh, bl) -> add_f2
     size_t n = in.size() / 16;
     for (size_t i = 0; i < n; ++i) {
@@ -204,3 +212,62 @@ def test_double_float_add(harness):
         assert abs(got - (a + b)) <= (abs(a) + abs(b)) / 2**46
         # renormalised: the tail is below one ulp of the head
         assert abs(float(out[i, 1])) <= abs(float(out[i, 0])) * 2.0**-23
+
+
+def test_head_is_the_truncated_significand(harness):
+    """f64_head (the pixel-label filter's conversion) is split_f64's head:
+    the significand truncated to 24 bits, 0 below 2^-126, NaN from 2^128."""
+    rng = np.random.default_rng(10)
+    d = _doubles(rng, 20000)
+    head = np.frombuffer(harness("h", d), dtype=np.float32)
+    h = np.frombuffer(harness("d", d), dtype=np.float32).reshape(-1, 3)[:, 1]
+    a = np.abs(d)
+    normal = np.isfinite(d) & (a >= 2.0**-126) & (a < 2.0**128)
+    assert (head[normal].view(np.uint32) == h[normal].view(np.uint32)).all()
+    assert (head[a < 2.0**-126] == 0).all()
+    assert np.isnan(head[~np.isfinite(d) | (a >= 2.0**128)]).all()
+    for i in np.flatnonzero(normal)[:4000]:
+        assert abs(Fraction(float(d[i])) - Fraction(float(head[i]))) <= Fraction(float(a[i])) / 2**23
+
+
+def _filter_sums(head, U):
+    """The label filter's float sums, in the kernel's order: 2 h00, + h10,
+    + h01, + 2 h11 (float32 arithmetic)."""
+    h = lambda q: np.frombuffer(head(np.ascontiguousarray(q)), dtype=np.float32).reshape(q.shape)
+    v = np.float32(2) * h(U[0])
+    v = v + h(U[1])
+    v = v + h(U[2])
+    return v + np.float32(2) * h(U[3])
+
+
+def test_pixel_label_filter_bound(harness):
+    """The pixel-label filter (Sec. 4.3 labels; k_pixel_labels): for phase
+    values in [0, 1] its float sums are within 1.5e-6 of the exact
+    2 u00 + u10 + u01 + 2 u11, so a float lead above 4e-6 fixes the argmax
+    of the binary64 sums.  Checked on random values, values just below
+    powers of two (the largest truncation errors) and exact ties."""
+    rng = np.random.default_rng(11)
+    n = 3000
+    U = rng.random((4, n))
+    # largest truncation error: significands 1.111...1 just below 1, 1/2, 1/4
+    below = np.array([np.nextafter(2.0**-k, 0) for k in range(0, 4)])
+    U[:, : 4 * 200] = np.repeat(below, 200)[None, :] * (1 - rng.random((4, 800)) * 2.0**-30)
+    U[:, 900:1000] = 1.0
+    U[:, 1000:1100] = 0.0
+    v = _filter_sums(lambda q: harness("h", q), U).astype(np.float64)
+    for i in range(n):
+        exact = 2 * Fraction(float(U[0, i])) + Fraction(float(U[1, i])) + Fraction(float(U[2, i])) \
+            + 2 * Fraction(float(U[3, i]))
+        assert abs(Fraction(float(v[i])) - exact) < Fraction(3, 2 * 10**6), (U[:, i], v[i])
+    # two phases per pixel: where the float lead exceeds 4e-6 the binary64
+    # sums order the phases the same way
+    a = rng.random((4, n))
+    b = np.clip(a + rng.choice([0.0, 1e-9, -1e-9, 3e-7, -3e-7, 1e-6, -1e-6, 5e-6, -5e-6], (4, n)), 0, 1)
+    va = _filter_sums(lambda q: harness("h", q), a)
+    vb = _filter_sums(lambda q: harness("h", q), b)
+    sa = 2 * a[0] + a[1] + a[2] + 2 * a[3]
+    sb = 2 * b[0] + b[1] + b[2] + 2 * b[3]
+    lead = (va - vb).astype(np.float64)
+    sure = np.abs(lead) > 4e-6
+    assert sure.any() and (~sure).any()
+    assert (np.sign(lead[sure]) == np.sign(sa[sure] - sb[sure])).all()
