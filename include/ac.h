@@ -323,6 +323,15 @@ int ac_adjoint_forward(ac_ctx *ctx, int n_steps, int checkpoint_every);
 int ac_adjoint_backward(ac_ctx *ctx, const double *grad_u, double *grad_lambda, double *grad_eps, double *grad_image,
                         double *grad_u0);
 
+/* The adjoint's tangent solve (ac_adjoint_backward) is flexible CG in FP64
+ * preconditioned by two truncated V-cycles from zero.  AC_ADJ_PRECOND_F32
+ * (default) runs those V-cycles in FP32 on the residual rounded to float (the
+ * CG recurrence, residual, stopping test and gradients stay FP64; GB300 runs
+ * FP64 at 1/64 of its FP32 rate), AC_ADJ_PRECOND_F64 in FP64.  Takes effect at
+ * the next ac_adjoint_forward.  AC_ERR_ARG for a NULL context or another value. */
+enum { AC_ADJ_PRECOND_F32 = 0, AC_ADJ_PRECOND_F64 = 1 };
+int ac_set_adjoint_preconditioner(ac_ctx *ctx, int precision);
+
 /* Check of the checkpointing (no counterpart in the paper): *count receives
  * the number of components at which a segment recomputed by the last
  * ac_adjoint_backward ended on a state that differs, bit for bit, from the

@@ -20,6 +20,7 @@ AC_PROJ_SIMPLEX, AC_PROJ_NODE = 0, 1
 AC_TILES_AUTO, AC_TILES_NEVER, AC_TILES_ALWAYS = 0, 1, 2
 AC_LOOP_AUTO, AC_LOOP_HOST = 0, 1
 AC_SMOOTH_GS3, AC_SMOOTH_JACOBI = 0, 1
+AC_ADJ_PRECOND_F32, AC_ADJ_PRECOND_F64 = 0, 1
 AC_BATCH_STREAMS, AC_BATCH_ONE_GRAPH = 0, 1
 AC_MAX_PHASES = 8
 
@@ -29,7 +30,7 @@ EXPORTS = [
     "ac_get_composite", "ac_energy", "ac_residual", "ac_project_simplex", "ac_set_profiling", "ac_set_profiling_mask", "ac_get_profile", "ac_colour_means_static",
     "ac_batch_create", "ac_batch_set_image", "ac_batch_set_phase", "ac_batch_get_phase", "ac_batch_segment",
     "ac_batch_step", "ac_batch_tune", "ac_batch_destroy", "ac_adjoint_forward", "ac_adjoint_backward",
-    "ac_adjoint_recompute_diff", "ac_set_coarse_tiling", "ac_set_cycle_loop", "ac_get_cycle_loop", "ac_set_coarse_smoother",
+    "ac_adjoint_recompute_diff", "ac_set_coarse_tiling", "ac_set_cycle_loop", "ac_get_cycle_loop", "ac_set_coarse_smoother", "ac_set_adjoint_preconditioner",
     "ac_batch_set_launch", "ac_batch_set_cycle_loop", "ac_last_error",
 ]
 PROF_CLASSES = ["smooth", "resid", "coarse", "transfer", "linesearch", "setup", "outer"]
@@ -124,6 +125,7 @@ def _load():
         "ac_set_coarse_tiling": ([vp, i], i),
         "ac_set_cycle_loop": ([vp, i], i),
         "ac_set_coarse_smoother": ([vp, i], i),
+        "ac_set_adjoint_preconditioner": ([vp, i], i),
         "ac_get_cycle_loop": ([vp, P(i)], i),
         "ac_batch_set_launch": ([vp, i], i),
         "ac_batch_set_cycle_loop": ([vp, i], i),
@@ -373,6 +375,11 @@ def ac_set_cycle_loop(ctx, mode):
 def ac_set_coarse_smoother(ctx, mode):
     """AC_SMOOTH_GS3 (default) or AC_SMOOTH_JACOBI (see include/ac.h)."""
     return _check(lib.ac_set_coarse_smoother(ctx, mode))
+
+
+def ac_set_adjoint_preconditioner(ctx, precision):
+    """AC_ADJ_PRECOND_F32 (default) or AC_ADJ_PRECOND_F64 (see include/ac.h)."""
+    return _check(lib.ac_set_adjoint_preconditioner(ctx, precision))
 
 
 def ac_get_cycle_loop(ctx) -> bool:

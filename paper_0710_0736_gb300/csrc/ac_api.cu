@@ -248,6 +248,7 @@ struct AdjState {
   unsigned long long *ndiff = nullptr;  // components where a recomputed segment end differed from the forward
   int64_t recompute_diff = 0;           // its value after the last backward pass
   Solve sv;                 // FP64 tangent-form solve
+  Solve sv32;               // its FP32 copy: the preconditioner of the FCG (ac_set_adjoint_preconditioner)
   std::vector<void *> allocs;
 };
 
@@ -275,6 +276,7 @@ struct ac_ctx {
   __nv_bfloat16 *img16 = nullptr;  // AC_MIXED: the image stored in bfloat16
   double *img64 = nullptr;         // the image as the moments used it, FP64 (for the adjoint)
   AdjState adj;
+  bool adj_pre32 = true;           // the adjoint's FCG preconditioned by the FP32 V-cycle (else FP64)
   double *h_scalars = nullptr;     // pinned: rho, energy
   bool have_image = false, have_rhs = false;
   std::vector<void *> allocs;
@@ -1555,7 +1557,7 @@ void ac_destroy(ac_ctx *ctx) {
     cudaStreamSynchronize(ctx->s);
   else
     cudaDeviceSynchronize();
-  for (Solve *S : {&ctx->sv, &ctx->adj.sv})
+  for (Solve *S : {&ctx->sv, &ctx->adj.sv, &ctx->adj.sv32})
     for (int a = 0; a < 2; ++a) {
       for (int b = 0; b < 2; ++b) slot_release(S->smooth_resid[a][b]);
       for (int f = 0; f < 2; ++f) slot_release(S->correction[a][f]);
@@ -1903,7 +1905,7 @@ int ac_set_profiling_mask(ac_ctx *ctx, unsigned class_mask) {
   if (ctx->profiling && ctx->prof_mask != ctx->prof_graph_mask) {
     // the profiled graphs carry the events of the old mask: capture them again
     if (ctx->s) cudaStreamSynchronize(ctx->s);
-    for (Solve *S : {&ctx->sv, &ctx->adj.sv}) {
+    for (Solve *S : {&ctx->sv, &ctx->adj.sv, &ctx->adj.sv32}) {
       for (int b = 0; b < 2; ++b) slot_release(S->smooth_resid[1][b]);
       for (int f = 0; f < 2; ++f) slot_release(S->correction[1][f]);
     }
@@ -1918,12 +1920,21 @@ int ac_set_coarse_tiling(ac_ctx *ctx, int mode) {
     return fail(AC_ERR_ARG, "mode must be AC_TILES_AUTO, AC_TILES_NEVER or AC_TILES_ALWAYS");
   if (ctx->s) cudaStreamSynchronize(ctx->s);
   release_step_graphs(ctx);
-  for (Solve *S : {&ctx->sv, &ctx->adj.sv}) {
+  for (Solve *S : {&ctx->sv, &ctx->adj.sv, &ctx->adj.sv32}) {
     // the tiled correction graphs depend on which levels are tiled
     for (int a = 0; a < 2; ++a) slot_release(S->correction[a][1]);
     S->tiling = mode;
     S->was_tiled = false;  // the next tiled correction writes every tile
   }
+  return AC_OK;
+}
+
+int ac_set_adjoint_preconditioner(ac_ctx *ctx, int precision) {
+  if (!ctx) return fail(AC_ERR_ARG, "ctx is NULL");
+  if (precision != AC_ADJ_PRECOND_F32 && precision != AC_ADJ_PRECOND_F64)
+    return fail(AC_ERR_ARG, "precision must be AC_ADJ_PRECOND_F32 or AC_ADJ_PRECOND_F64");
+  ctx->adj_pre32 = precision == AC_ADJ_PRECOND_F32;
+  ctx->adj.ready = false;  // the next ac_adjoint_forward sets up the solves again
   return AC_OK;
 }
 
@@ -1946,7 +1957,7 @@ int ac_set_coarse_smoother(ac_ctx *ctx, int mode) {
     return fail(AC_ERR_ARG, "mode must be AC_SMOOTH_GS3 or AC_SMOOTH_JACOBI");
   if (ctx->s) cudaStreamSynchronize(ctx->s);
   release_step_graphs(ctx);
-  for (Solve *S : {&ctx->sv, &ctx->adj.sv}) {
+  for (Solve *S : {&ctx->sv, &ctx->adj.sv, &ctx->adj.sv32}) {
     // the correction graphs hold the smoother's kernels
     for (int a = 0; a < 2; ++a)
       for (int f = 0; f < 2; ++f) slot_release(S->correction[a][f]);
@@ -2008,10 +2019,11 @@ int adj_alloc(ac_ctx *ctx, void **p, size_t bytes) {
 
 void adj_release(ac_ctx *ctx) {
   AdjState &A = ctx->adj;
-  for (int a = 0; a < 2; ++a) {
-    for (int b = 0; b < 2; ++b) slot_release(A.sv.smooth_resid[a][b]);
-    for (int f = 0; f < 2; ++f) slot_release(A.sv.correction[a][f]);
-  }
+  for (Solve *S : {&A.sv, &A.sv32})
+    for (int a = 0; a < 2; ++a) {
+      for (int b = 0; b < 2; ++b) slot_release(S->smooth_resid[a][b]);
+      for (int f = 0; f < 2; ++f) slot_release(S->correction[a][f]);
+    }
   for (void *p : A.allocs) cudaFree(p);
   A = AdjState{};
 }
@@ -2049,39 +2061,49 @@ int adj_setup(ac_ctx *ctx, int T, int every) {
   if (ctx->r > 0) ADJ_ALLOC(A.gimg, (size_t)ctx->g0.W * ctx->g0.H * 3 * sizeof(double));
   ADJ_ALLOC(A.ktot, 2 * sizeof(double));
   ADJ_ALLOC(A.ndiff, sizeof(unsigned long long));
-  Solve &S = A.sv;
-  S.o = &ctx->ops->adjoint;
-  S.lv = ctx->sv.lv;
-  ADJ_ALLOC(S.list_counts, 2 * S.lv.size() * sizeof(int));
-  for (size_t k = 1; k < S.lv.size(); ++k) {
-    Level &L = S.lv[k];
-    ADJ_ALLOC(L.op, (size_t)L.n * 4 * N * sizeof(double));
-    ADJ_ALLOC(L.r, (size_t)L.n * N * sizeof(double));
-    ADJ_ALLOC(L.v, (size_t)L.n * N * sizeof(double));
-    ADJ_ALLOC(L.t, (size_t)L.n * N * sizeof(double));
-    const size_t nt = (size_t)ac::tiles_x(L.g) * ac::tiles_y(L.g);
-    ADJ_ALLOC(L.lists.flags, nt * N);
-    ADJ_ALLOC(L.lists.items, nt * N * sizeof(uint64_t));
-    ADJ_ALLOC(L.lists.tiles, nt * sizeof(uint64_t));
-    ADJ_ALLOC(L.lists.dirty, nt);
-    ADJ_ALLOC(L.lists.changed, nt);
-    AC_CUDA(cudaMemsetAsync(L.lists.dirty, 1, nt, ctx->s));
-    L.lists.count = S.list_counts + 2 * k;
-    L.lists.cap = (int64_t)nt * N;
-    L.lists.sms = ctx->sms;
-    AC_CUDA(cudaMemsetAsync(L.lists.flags, ac::kLiveNow, nt * N, ctx->s));
-  }
-  S.depth = ctx->sv.depth;
-  S.tab0 = ctx->sv.tab0;
-  S.tiling = ctx->sv.tiling;
-  ADJ_ALLOC(S.x, fN);
-  ADJ_ALLOC(S.rhs, fN);
-  ADJ_ALLOC(S.ob, fN);
-  ADJ_ALLOC(S.rt, fN);
-  ADJ_ALLOC(S.d, fN);
-  ADJ_ALLOC(S.mask, (size_t)ctx->n);
-  AC_CUDA(cudaMemsetAsync(S.rt, 0, fN, ctx->s));  // second-colour slots stay 0 (see solve_mg)
-  return AC_OK;
+  // the tangent-form solves on the primary solve's level hierarchy: FP64
+  // (elem 8, node-order fine arrays) and its FP32 copy (elem 4, colour-split
+  // fine arrays), each with its own arrays, lists and graphs
+  auto setup_solve = [&](Solve &S, const ac::SolverOps *ops) -> int {
+    const size_t es = (size_t)ops->elem;
+    const size_t fS = (size_t)fine_slots(ctx->n) * N * es;
+    S.o = ops;
+    S.lv = ctx->sv.lv;
+    ADJ_ALLOC(S.list_counts, 2 * S.lv.size() * sizeof(int));
+    for (size_t k = 1; k < S.lv.size(); ++k) {
+      Level &L = S.lv[k];
+      ADJ_ALLOC(L.op, (size_t)L.n * 4 * N * es);
+      ADJ_ALLOC(L.r, (size_t)L.n * N * es);
+      ADJ_ALLOC(L.v, (size_t)L.n * N * es);
+      ADJ_ALLOC(L.t, (size_t)L.n * N * es);
+      const size_t nt = (size_t)ac::tiles_x(L.g) * ac::tiles_y(L.g);
+      ADJ_ALLOC(L.lists.flags, nt * N);
+      ADJ_ALLOC(L.lists.items, nt * N * sizeof(uint64_t));
+      ADJ_ALLOC(L.lists.tiles, nt * sizeof(uint64_t));
+      ADJ_ALLOC(L.lists.dirty, nt);
+      ADJ_ALLOC(L.lists.changed, nt);
+      AC_CUDA(cudaMemsetAsync(L.lists.dirty, 1, nt, ctx->s));
+      L.lists.count = S.list_counts + 2 * k;
+      L.lists.cap = (int64_t)nt * N;
+      L.lists.sms = ctx->sms;
+      AC_CUDA(cudaMemsetAsync(L.lists.flags, ac::kLiveNow, nt * N, ctx->s));
+    }
+    S.depth = ctx->sv.depth;
+    S.tab0 = ctx->sv.tab0;
+    S.tiling = ctx->sv.tiling;
+    S.coarse_gs = ctx->sv.coarse_gs;
+    ADJ_ALLOC(S.x, fS);
+    ADJ_ALLOC(S.rhs, fS);
+    ADJ_ALLOC(S.ob, fS);
+    ADJ_ALLOC(S.rt, fS);
+    ADJ_ALLOC(S.d, fS);
+    ADJ_ALLOC(S.mask, (size_t)ctx->n);
+    AC_CUDA(cudaMemsetAsync(S.rt, 0, fS, ctx->s));  // second-colour slots stay 0 (see solve_mg)
+    return AC_OK;
+  };
+  int rc = setup_solve(A.sv, &ctx->ops->adjoint);
+  if (!rc && ctx->adj_pre32) rc = setup_solve(A.sv32, &ctx->ops->adjoint32);
+  return rc;
 }
 
 // Components where a and b differ (bit patterns compared: a recomputation
@@ -2129,14 +2151,27 @@ int fcg_adjoint(ac_ctx *ctx, AdjState &A, double tol_rho, int max_iter, int *ite
       status = AC_OK;
       break;
     }
-    // z = B r: the truncated V-cycle from zero on right-hand side r
-    AC_CUDA(cudaMemcpyAsync(S.rhs, A.kr, fN, cudaMemcpyDeviceToDevice, ctx->s));
-    AC_CUDA(cudaMemsetAsync(S.x, 0, fN, ctx->s));
+    // z = B r: the truncated V-cycle from zero on right-hand side r, in
+    // FP32 (r rounded, z widened and projected onto the tangent space in
+    // FP64; the recurrence, residual and dots stay FP64, and the flexible
+    // update absorbs the preconditioner's rounding) or in FP64
     int cyc = 0;
     double rho = 0;
     int64_t sw = 0;
-    rc = solve_mg(ctx, S, 0.0, 2, &cyc, &rho, &sw);
-    if (rc && rc != AC_ERR_NOT_CONVERGED) return rc;
+    if (A.sv32.o) {
+      Solve &P = A.sv32;
+      AC_RUN(AC_PROF_SETUP, o->to_split32(A.kr, ctx->g0, (float *)P.rhs, ctx->s));
+      AC_CUDA(cudaMemsetAsync(P.x, 0, (size_t)fine_slots(ctx->n) * ctx->N * sizeof(float), ctx->s));
+      rc = solve_mg(ctx, P, 0.0, 2, &cyc, &rho, &sw);
+      if (rc && rc != AC_ERR_NOT_CONVERGED) return rc;
+      AC_RUN(AC_PROF_SETUP,
+             o->from_split32((const float *)P.x, ctx->g0, (const double *)S.ob, (double *)S.x, ctx->s));
+    } else {
+      AC_CUDA(cudaMemcpyAsync(S.rhs, A.kr, fN, cudaMemcpyDeviceToDevice, ctx->s));
+      AC_CUDA(cudaMemsetAsync(S.x, 0, fN, ctx->s));
+      rc = solve_mg(ctx, S, 0.0, 2, &cyc, &rho, &sw);
+      if (rc && rc != AC_ERR_NOT_CONVERGED) return rc;
+    }
     const double *z = (const double *)S.x;
     double beta = 0.0;
     if (it > 0) {
@@ -2234,6 +2269,7 @@ int ac_adjoint_backward(ac_ctx *ctx, const double *grad_u, double *grad_lambda, 
       const double *c = A.seg_c + (size_t)k * N * 3, *M = A.seg_M + (size_t)k * N;
       Solve &S = A.sv;
       AC_RUN(AC_PROF_SETUP, o->adj_prepare(up, A.g, ctx->n, (double *)S.ob, (double *)S.rhs, ctx->s));
+      if (A.sv32.o) AC_RUN(AC_PROF_SETUP, o->to_split32((const double *)S.ob, ctx->g0, (float *)A.sv32.ob, ctx->s));
       AC_CUDA(cudaMemsetAsync(S.x, 0, fN, ctx->s));
       AC_CUDA(cudaMemsetAsync(ctx->rho, 0, sizeof(double), ctx->s));
       AC_RUN(AC_PROF_SETUP, o->absmax((const double *)S.rhs, nN, ctx->rho, ctx->s));

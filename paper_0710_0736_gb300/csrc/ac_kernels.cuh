@@ -2898,6 +2898,45 @@ __global__ void k_pixel_labels(const double *__restrict__ u, Geo g, int r, int8_
   pix_lab[(int64_t)y * W0 + x] = (int8_t)argmax_low<N>(v);
 }
 
+// A binary64 node array in node order (N values per node) to the colour-split
+// float layout of the FP32 solves (fslot), rounded to nearest on the integer
+// pipe, and a float one back, widened exactly: the adjoint's FP32
+// preconditioner takes the FCG residual and returns its correction this way.
+template <int N>
+__global__ void k_to_split32(const double *__restrict__ in, Geo g, float *__restrict__ out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x > g.W) return;
+  double v[N];
+  ldn<double, N>(in + ((int64_t)y * g.Wn + x) * N, v);
+  float f[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) f[i] = f64_to_f32_rn(v[i]);
+  stn<float, N>(out + fslot<float>(g, x, y) * N, f);
+}
+
+// With freeset != null the widened values are projected onto the frozen
+// tangent space in binary64 (proj_box's kTangent form: the mean over the free
+// phases removed, the others zeroed): the FP32 solve keeps that space only to
+// float precision, and the CG's solution would accumulate the difference.
+template <int N>
+__global__ void k_from_split32(const float *__restrict__ in, Geo g, const double *__restrict__ freeset,
+                               double *__restrict__ out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x > g.W) return;
+  const int64_t n = (int64_t)y * g.Wn + x;
+  float f[N];
+  ldn<float, N>(in + fslot<float>(g, x, y) * N, f);
+  double v[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = f32_to_f64(f[i]);
+  if (freeset) {
+    double fr[N];
+    ldn<double, N>(freeset + n * N, fr);
+    proj_box<double, N, kTangent>(v, fr);
+  }
+  stn<double, N>(out + n * N, v);
+}
+
 // Kernel-level projection of count independent N-vectors onto the simplex.
 template <int N>
 __global__ void k_project(const double *y, double *x, int64_t count) {

@@ -339,6 +339,14 @@ struct Launch {
     }
     return k;
   }
+  static int to_split32(const double *in, const Geo &g, float *out, cudaStream_t s) {
+    k_to_split32<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(in, g, out);
+    return 1;
+  }
+  static int from_split32(const float *in, const Geo &g, const double *freeset, double *out, cudaStream_t s) {
+    k_from_split32<N><<<row_grid(g.W + 1, g.H + 1), kBlock, 0, s>>>(in, g, freeset, out);
+    return 1;
+  }
   static int adj_prepare(const double *up, const double *g, int64_t n, double *freeset, double *rhs, cudaStream_t s) {
     k_adj_prepare<N><<<blocks_for(n), kBlock, 0, s>>>(up, g, n, freeset, rhs);
     return 1;
@@ -407,6 +415,9 @@ struct Launch {
                           SolverLaunch<double, N, kDirect>::table(),
                           SolverLaunch<float, N, kShifted>::table(),
                           SolverLaunch<double, N, kTangent>::table(),
+                          SolverLaunch<float, N, kTangent>::table(),
+                          to_split32,
+                          from_split32,
                           adj_prepare,
                           adj_accum,
                           adj_back,

@@ -128,6 +128,11 @@ struct Ops {
   SolverOps fp64;     // T = double, direct form
   SolverOps mixed;    // T = float, shifted form
   SolverOps adjoint;  // T = double, tangent form (frozen free set)
+  SolverOps adjoint32;  // T = float, tangent form: the FP32 preconditioner of the adjoint's FCG
+  // node-order binary64 <-> colour-split float node arrays (N values per node);
+  // from_split32 projects onto the tangent space of freeset (nullable)
+  int (*to_split32)(const double *in, const Geo &g, float *out, cudaStream_t s);
+  int (*from_split32)(const float *in, const Geo &g, const double *freeset, double *out, cudaStream_t s);
   // adjoint of a time step
   int (*adj_prepare)(const double *up, const double *g, int64_t n, double *freeset, double *rhs, cudaStream_t s);
   // part: (blocks of the level) x (2 + 3N), tot: 2 + 3N, scal[0..1] += lambda/eps gradients

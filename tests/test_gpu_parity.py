@@ -1223,6 +1223,41 @@ def test_adjoint_recomputation_repeats_the_forward(ac, precision):
     seg.close()
 
 
+@pytest.mark.parametrize("stream", ["legacy", "side"])
+def test_adjoint_preconditioners_agree(ac, stream):
+    """The adjoint's flexible CG preconditioned by FP32 V-cycles (the default)
+    and by FP64 ones reach the same tangent solutions (both stop at 1e-13 of
+    max |Pi g|): gradients to 1e-9 relative, on the legacy stream (direct
+    launches) and on a stream of its own (graphs)."""
+    import torch
+    W, H, N, T, every = 48, 32, 4, 6, 3
+    img, u0, target = _adj_problem(4, W, H, N)
+    m0 = oracle.moments(img)[:, 0]
+    side = torch.cuda.Stream()
+    out = {}
+    for pre in (ac.AC_ADJ_PRECOND_F32, ac.AC_ADJ_PRECOND_F64):
+        kw = {"stream": side.cuda_stream} if stream == "side" else {"stream": None}
+        seg = ac.Segmenter(W, H, N, 2.0, 1.0, 4.0, tol=1e-12, max_cycles=2000, **kw)
+        ac.ac_set_adjoint_preconditioner(seg.ctx, pre)
+        seg.set_image(img)
+        seg.set_phase(u0)
+        ac.ac_adjoint_forward(seg.ctx, T, every)
+        _, gT = oracle.misfit_loss(seg.phase(), m0, target)
+        g_img = torch.zeros((H, W, 3), dtype=torch.float64, device="cuda")
+        g_u = torch.tensor(gT, device="cuda")
+        torch.cuda.synchronize()  # torch's stream and the library's are not ordered with "side"
+        gl, ge = ac.ac_adjoint_backward(seg.ctx, g_u, g_img)
+        torch.cuda.synchronize()
+        assert ac.ac_adjoint_recompute_diff(seg.ctx) == 0
+        out[pre] = (gl, ge, g_img.cpu().numpy())
+        seg.close()
+    (l32, e32, i32), (l64, e64, i64) = out[ac.AC_ADJ_PRECOND_F32], out[ac.AC_ADJ_PRECOND_F64]
+    assert l32 == pytest.approx(l64, rel=1e-9) and e32 == pytest.approx(e64, rel=1e-9)
+    assert np.abs(i32 - i64).max() <= 1e-9 * np.abs(i64).max()
+    with pytest.raises(ac.AcError):
+        ac.ac_set_adjoint_preconditioner(None, ac.AC_ADJ_PRECOND_F32)
+
+
 @pytest.fixture(scope="module")
 def c5_problem(ac):
     """The 512x512, N = 4 workload (12 disks, noise 0.08, Voronoi target of 6
