@@ -278,8 +278,11 @@ int ac_set_coarse_smoother(ac_ctx *ctx, int mode);
  *     coarse levels are too small for tiles, e.g. 1024^2 and below at N <= 8)
  *     -- and on the host otherwise;
  *   AC_LOOP_HOST: always on the host.
- * ac_get_cycle_loop sets *on_device to 1 if the next ac_step runs the loop on
- * the device.  AC_ERR_ARG for a NULL context or an unknown mode. */
+ * If the graph cannot be captured or instantiated (a driver without
+ * conditional nodes), the context switches itself to AC_LOOP_HOST and the
+ * step runs on the host loop.  ac_get_cycle_loop sets *on_device to 1 if the
+ * next ac_step runs the loop on the device.  AC_ERR_ARG for a NULL context or
+ * an unknown mode. */
 enum { AC_LOOP_AUTO = 0, AC_LOOP_HOST = 1 };
 int ac_set_cycle_loop(ac_ctx *ctx, int mode);
 int ac_get_cycle_loop(ac_ctx *ctx, int *on_device);

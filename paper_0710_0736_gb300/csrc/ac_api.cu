@@ -1206,9 +1206,6 @@ int loop_stats(ac_ctx *ctx, const StepGraph &sg, int n_steps, ac_stats *out) {
 // ac_step with the device-side loop: one graph launch per time step and one
 // synchronisation per call.
 int step_device(ac_ctx *ctx, int n_steps, ac_stats *out) {
-  int rc = capture_step(ctx, false);
-  if (!rc && out) rc = capture_step(ctx, true);
-  if (rc) return rc;
   AC_CUDA((k_ctl_reset<<<1, 1, 0, ctx->s>>>(ctx->ctl, ctx->delta_warm ? 1 : 0), cudaGetLastError()));
   for (int t = 0; t < n_steps; ++t)
     AC_CUDA(cudaGraphLaunch(ctx->step_graph[(out && t == n_steps - 1) ? 1 : 0].exec, ctx->s));
@@ -1216,7 +1213,7 @@ int step_device(ac_ctx *ctx, int n_steps, ac_stats *out) {
   if (out) AC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 1, ctx->energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
   AC_CUDA(cudaStreamSynchronize(ctx->s));
   ac_stats st{};
-  rc = loop_stats(ctx, ctx->step_graph[0], n_steps, &st);
+  int rc = loop_stats(ctx, ctx->step_graph[0], n_steps, &st);
   if (out) {
     st.energy = std::ldexp(ctx->h_scalars[1], -ctx->r);  // pixel units: E = 2^-r E(eps', lambda')
     *out = st;
@@ -1689,7 +1686,18 @@ int ac_step(ac_ctx *ctx, int n_steps, ac_stats *out) {
   if (!ctx) return fail(AC_ERR_ARG, "ctx is NULL");
   if (n_steps < 0) return fail(AC_ERR_ARG, "n_steps must be >= 0");
   if (!ctx->have_image) return fail(AC_ERR_STATE, "ac_set_image must come first");
-  if (n_steps > 0 && loop_on_device(ctx)) return step_device(ctx, n_steps, out);
+  if (n_steps > 0 && loop_on_device(ctx)) {
+    // capture the step graphs (once); a device or driver that cannot capture
+    // or instantiate them leaves the context on the host loop
+    int rc = capture_step(ctx, false);
+    if (!rc && out) rc = capture_step(ctx, true);
+    if (rc) {
+      release_step_graphs(ctx);
+      ctx->loop_mode = AC_LOOP_HOST;
+    } else {
+      return step_device(ctx, n_steps, out);
+    }
+  }
   ac_stats st{};
   st.converged = 1;
   int status = AC_OK;

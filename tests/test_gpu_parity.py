@@ -413,6 +413,8 @@ def test_device_loop_matches_host_loop(ac, precision, W, H, N, nu1, nu2, max_cyc
         for n in (1, 3, 2):  # several calls: the warm start carries across them
             rc, s = ac.ac_step(seg.ctx, n, allow_not_converged=True)
             stats.append((rc, s.as_dict()))
+        # a capture failure would drop the context to the host loop silently
+        assert seg.loop_on_device() == (mode == ac.AC_LOOP_AUTO)
         res.append((seg.phase(), stats, seg.node_labels()))
         seg.close()
     (u_h, st_h, nl_h), (u_d, st_d, nl_d) = res
