@@ -195,4 +195,134 @@ AC_HD f2 add_f2(f2 a, float bh, float bl) {
   return fast_two_sum(s.h, s.l + (a.l + bl));
 }
 
+AC_HD int popcount_hd(unsigned m) {
+#ifdef __CUDA_ARCH__
+  return __popc(m);
+#else
+  return __builtin_popcount(m);
+#endif
+}
+
+// 1/k for the kept-component counts 1..8 (exact for 1, 2, 4, 8; rounded
+// otherwise), without a division.
+template <typename T>
+AC_HD T rcp_count(int k) {
+  return k == 1 ? T(1) : k == 2 ? T(0.5) : k == 3 ? T(1.0 / 3.0) : k == 4 ? T(0.25)
+       : k == 5 ? T(0.2) : k == 6 ? T(1.0 / 6.0) : k == 7 ? T(1.0 / 7.0) : T(0.125);
+}
+
+// The mixed form's update of one node of the binary64 phase field,
+// u <- P_G(u + delta) (Sec. 3.3's simplex projection, the FP32 correction
+// delta added in binary64):
+//  - a component the float solve put on its bound (delta_i == -float(u_i))
+//    is set to exactly 0 -- u_i + delta_i would leave the rounding residue
+//    u_i - float(u_i) -- so that exact zeros (the active set) are the same
+//    as in the FP64 form; the others are v_i = u_i + delta_i in binary64;
+//  - Michelot's iteration on the kept components (target sum 1):
+//    theta = (sum of the kept v - 1)/|kept|, components at or below theta
+//    leave, repeat; then u_i = v_i - theta on the kept set, 0 elsewhere.
+// Binary64 arithmetic is slow on GB300, so the kept set is found by the
+// iteration on float(v), theta computed once in binary64 on that set, and
+// the set's conditions (kept v_i > theta, the others at or below it) checked
+// in float with a margin of 2^-21 (|v_i| + |theta|) + 2^-120.  Rounding to
+// float is monotone, so a float gap that large (a few float ulps; the
+// absolute term covers f64_to_f32_rn's flush below 2^-126) proves the
+// binary64 inequality with a gap far above the binary64 rounding of the
+// iteration's intermediate thetas.  Where the conditions hold, the binary64
+// iteration from the full set ends on the same set -- its theta does not
+// exceed the final one, so it drops no component above it, and it cannot
+// stop on a larger set -- and sums it in the same order, so the result is
+// bit-identical to that iteration's.  Elsewhere (near ties), and always
+// with FP64_ONLY, the binary64 iteration runs.
+// any_or(m) returns the OR of m over the lanes that run together (the
+// identity on the host): a binary64 operation on component i is skipped
+// when no lane needs it.  Returns 0 (float set accepted), 1 (binary64
+// iteration) or 2 (no kept component, which a feasible correction cannot
+// give: u is then zero and the caller projects it).
+template <int N, bool FP64_ONLY = false, typename AnyOr>
+AC_HD int outer_update_node(double (&uk)[N], const float (&dk)[N], AnyOr any_or) {
+  unsigned keep0 = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (!(dk[i] == -f64_to_f32_rn(uk[i]))) keep0 |= 1u << i;
+  const unsigned any0 = any_or(keep0);
+  const int cnt = popcount_hd(keep0);
+  float vf[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    vf[i] = 0.f;
+    if (((any0 >> i) & 1u) && ((keep0 >> i) & 1u)) {
+      uk[i] += f32_to_f64(dk[i]);
+      vf[i] = f64_to_f32_rn(uk[i]);
+    } else {
+      uk[i] = 0.0;
+    }
+  }
+  if (cnt == 0) return 2;
+  unsigned keep = keep0;
+  double theta = 0.0;
+  bool ok = !FP64_ONLY;
+  if (!FP64_ONLY) {
+    float sf = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if ((keep >> i) & 1u) sf += vf[i];
+    float tf = (sf - 1.f) * rcp_count<float>(cnt);
+#pragma unroll 1
+    for (int pass = 1; pass < N; ++pass) {
+      unsigned drop = 0;
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (((keep >> i) & 1u) && vf[i] <= tf) drop |= 1u << i;
+      if (!drop || drop == keep) break;
+      keep &= ~drop;
+      sf = 0.f;
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if ((keep >> i) & 1u) sf += vf[i];
+      tf = (sf - 1.f) * rcp_count<float>(popcount_hd(keep));
+    }
+    const unsigned anyk = any_or(keep);
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (((anyk >> i) & 1u) && ((keep >> i) & 1u)) s += uk[i];
+    theta = (s - 1.0) * rcp_count<double>(popcount_hd(keep));
+    const float t32 = f64_to_f32_rn(theta);
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if ((keep0 >> i) & 1u) {
+        const float d = vf[i] - t32, m = (fabsf(vf[i]) + fabsf(t32)) * 0x1.0p-21f + 0x1.0p-120f;
+        ok = ok && (((keep >> i) & 1u) ? d > m : d < -m);
+      }
+  }
+  if (!ok) {
+    keep = keep0;
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (((any0 >> i) & 1u) && ((keep >> i) & 1u)) s += uk[i];
+    theta = (s - 1.0) * rcp_count<double>(cnt);
+#pragma unroll 1
+    for (int pass = 1; pass < N; ++pass) {
+      unsigned drop = 0;
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (((any0 >> i) & 1u) && ((keep >> i) & 1u) && uk[i] <= theta) drop |= 1u << i;
+      if (!drop || drop == keep) break;
+      keep &= ~drop;
+      s = 0.0;
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (((any0 >> i) & 1u) && ((keep >> i) & 1u)) s += uk[i];
+      theta = (s - 1.0) * rcp_count<double>(popcount_hd(keep));
+    }
+  }
+  const unsigned anyf = any_or(keep);
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    uk[i] = (((anyf >> i) & 1u) && ((keep >> i) & 1u)) ? uk[i] - theta : 0.0;
+  return ok ? 0 : 1;
+}
+
 }  // namespace ac

@@ -823,13 +823,8 @@ __global__ void __launch_bounds__(kOrThreads, 2) k_outer_resid_df(const double *
   block_max_atomic(e, rho);
 }
 
-// A component the FP32 solve put on its bound (delta_i == -float(u_i)) is set
-// to exactly 0 -- u_i + delta_i would leave the rounding residue
-// u_i - float(u_i) -- and the projection then runs over the other components
-// only, so that exact zeros (the active set) are the same as in the FP64 form.
-// The float rounding of u_i and the widening of delta_i run on the integer
-// pipe, and each FP64 operation on component i is skipped by the whole warp
-// when no lane keeps that component (one or two of N at most nodes).
+// One thread per node; the node's update is outer_update_node (ac_df64.cuh),
+// its warp-wide skips of binary64 operations by __reduce_or_sync.
 template <int N>
 __global__ void k_outer_update(double *__restrict__ u, const float *__restrict__ delta, Geo g) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
@@ -840,50 +835,8 @@ __global__ void k_outer_update(double *__restrict__ u, const float *__restrict__
   float dk[N];
   ldn_rw<double, N>(u + k * N, uk);
   ldn<float, N>(delta + fslot<float>(g, x, y) * N, dk);
-  unsigned keep = 0;
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-    if (!(dk[i] == -f64_to_f32_rn(uk[i]))) keep |= 1u << i;
-  const unsigned any = __reduce_or_sync(lanes, keep);
-  double s = 0.0;
-  const int cnt = __popc(keep);
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    if ((any >> i) & 1u) {
-      if ((keep >> i) & 1u) {
-        uk[i] += f32_to_f64(dk[i]);
-        s += uk[i];
-      } else {
-        uk[i] = 0.0;
-      }
-    } else {
-      uk[i] = 0.0;
-    }
-  }
-  if (cnt == 0) {  // cannot happen for a feasible correction; fall back to the full projection
-    proj_simplex<double, N>(uk);
-    stn<double, N>(u + k * N, uk);
-    return;
-  }
-  // Michelot's iteration over the kept components (target sum 1)
-  double theta = (s - 1.0) * rcp_small<double>(cnt);
-#pragma unroll 1
-  for (int pass = 1; pass < N; ++pass) {
-    unsigned drop = 0;
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-      if (((any >> i) & 1u) && ((keep >> i) & 1u) && uk[i] <= theta) drop |= 1u << i;
-    if (!drop || drop == keep) break;
-    keep &= ~drop;
-    s = 0.0;
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-      if (((any >> i) & 1u) && ((keep >> i) & 1u)) s += uk[i];
-    theta = (s - 1.0) * rcp_small<double>(__popc(keep));
-  }
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-    if ((any >> i) & 1u) uk[i] = ((keep >> i) & 1u) ? uk[i] - theta : 0.0;
+  const int path = outer_update_node<N>(uk, dk, [lanes](unsigned m) { return __reduce_or_sync(lanes, m); });
+  if (path == 2) proj_simplex<double, N>(uk);
   stn<double, N>(u + k * N, uk);
 }
 

@@ -2,7 +2,9 @@
 correction runs on the GPU (paper_0710_0736_gb300/csrc/ac_df64.cuh): the
 integer-pipe binary64 <-> binary32 conversions and the binary64 split are
 checked against numpy's IEEE conversions and exact rational arithmetic, the
-error-free transformations against exact sums and products."""
+error-free transformations against exact sums and products, and the mixed
+form's node update u <- P_G(u + delta) (float kept set, binary64 theta)
+against the plain binary64 iteration and a sort-based simplex projection."""
 import os
 import shutil
 import subprocess
@@ -50,6 +52,22 @@ int main(int argc, char **argv) {
       std::memcpy(&d, &in[8 * i], 8);
       float o = ac::f64_head(d);
       fwrite(&o, 4, 1, stdout);
+    }
+  } else if (mode == 'u') {  // (8 doubles u, 8 floats delta) -> (u', path) and the binary64-only u'
+    size_t n = in.size() / 96;
+    for (size_t i = 0; i < n; ++i) {
+      double u[8], v[8];
+      float d[8];
+      std::memcpy(u, &in[96 * i], 64);
+      std::memcpy(d, &in[96 * i + 64], 32);
+      std::memcpy(v, u, 64);
+      auto id = [](unsigned m) { return m; };
+      const int path = ac::outer_update_node<8>(u, d, id);
+      ac::outer_update_node<8, true>(v, d, id);
+      const double p = path;
+      fwrite(u, 8, 8, stdout);
+      fwrite(&p, 8, 1, stdout);
+      fwrite(v, 8, 8, stdout);
     }
   } else if (mode == 'a') {  // float quadruples (ah, al, bh, bl) -> add_f2
     size_t n = in.size() / 16;
@@ -271,3 +289,71 @@ def test_pixel_label_filter_bound(harness):
     sure = np.abs(lead) > 4e-6
     assert sure.any() and (~sure).any()
     assert (np.sign(lead[sure]) == np.sign(sa[sure] - sb[sure])).all()
+
+
+def _proj_simplex_sort(v):
+    """Euclidean projection onto {x >= 0, sum x = 1} by sorting (the
+    textbook rule: theta from the largest prefix whose mean-shifted entries
+    stay positive), independent of Michelot's iteration."""
+    s = np.sort(v)[::-1]
+    c = np.cumsum(s) - 1.0
+    k = np.arange(1, len(v) + 1)
+    rho = np.nonzero(s - c / k > 0)[0][-1]
+    return np.maximum(v - c[rho] / (rho + 1), 0.0)
+
+
+def _update_cases(rng, n):
+    """Records (u, delta) of the mixed form's outer update at N = 8: u on the
+    simplex with exact zeros, delta float corrections, some components put on
+    their bound (delta_i = -float(u_i)); then near ties, where an updated
+    component lies within 1e-17 .. 1e-5 of the final threshold."""
+    N = 8
+    u = rng.dirichlet(np.full(N, 0.7), n)
+    u[rng.random((n, N)) < 0.3] = 0.0
+    u[np.arange(n), rng.integers(0, N, n)] += 0.05
+    u /= u.sum(1, keepdims=True)
+    d = (rng.standard_normal((n, N)) * 10.0 ** rng.uniform(-6, -1, (n, 1))).astype(np.float32)
+    bound = rng.random((n, N)) < 0.25
+    d[bound] = -u[bound].astype(np.float32)
+    # near ties: final support K, threshold t, the others just below t
+    m = n // 2
+    p = rng.dirichlet(np.ones(N), m)
+    p[rng.random((m, N)) < 0.4] = 0.0
+    p[np.arange(m), rng.integers(0, N, m)] += 0.1
+    p /= p.sum(1, keepdims=True)
+    t = rng.uniform(-0.05, 0.05, (m, 1))
+    gap = 10.0 ** rng.uniform(-17, -5, (m, N)) * rng.choice([0.0, 1.0], (m, N), p=[0.2, 0.8])
+    v = np.where(p > 0, p + t, t - gap)
+    dt = (rng.standard_normal((m, N)) * 1e-3).astype(np.float32)
+    ut = v - dt.astype(np.float64)
+    u = np.concatenate([u, ut, np.zeros((1, N)), np.full((1, N), 0.125)])
+    d = np.concatenate([d, dt, np.zeros((1, N), np.float32), -np.full((1, N), 0.125, np.float32)])
+    return u, d
+
+
+def test_outer_update_node(harness):
+    rng = np.random.default_rng(11)
+    u, d = _update_cases(rng, 40000)
+    rec = np.concatenate([u.view(np.uint8).reshape(len(u), 64), d.view(np.uint8).reshape(len(d), 32)], axis=1)
+    out = np.frombuffer(harness("u", rec), dtype=np.float64).reshape(-1, 17)
+    fast, path, plain = out[:, :8], out[:, 8], out[:, 9:]
+    # bit-identical to the binary64 iteration, whichever path ran
+    assert (fast.view(np.uint64) == plain.view(np.uint64)).all()
+    # the float set is accepted at all but near-tie nodes; the near ties take both paths
+    assert (path[:40000] == 0).mean() > 0.99
+    assert (path[40000:-2] == 0).sum() > 1000 and (path[40000:-2] == 1).sum() > 1000
+    # the all-bound record: no kept component, u zeroed for the caller's projection
+    assert path[-1] == 2 and (fast[-1] == 0).all()
+    # against the sort-based projection of v = u + delta over the kept
+    # components (the bound ones exactly 0)
+    keep = d != -u.astype(np.float32)
+    v = u + d.astype(np.float64)
+    worst = 0.0
+    for i in range(len(u) - 1):
+        if not keep[i].any():
+            continue
+        x = np.zeros(8)
+        x[keep[i]] = _proj_simplex_sort(v[i][keep[i]])
+        worst = max(worst, np.abs(x - fast[i]).max())
+        assert (fast[i][~keep[i]] == 0).all() and (fast[i] >= 0).all()
+    assert worst < 1e-15, worst
