@@ -580,10 +580,24 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
 // solution, see solve_mixed) as in the FP64 kernel.
 // Each block walks kOrRows rows of a strip of kOrThreads columns (one
 // column per thread, kOrThreads - 2 output columns plus one halo column on
-// each side), so every value of u is loaded and split once: a thread keeps
+// each side), so every value of u is loaded and split once (the halo columns
+// and rows by two blocks): a thread keeps
 // the split rows y - 1, y, y + 1 of its column in registers and finds its
 // west and east neighbours in shared memory.
-constexpr int kOrRows = 16, kOrThreads = 256;
+// 64-column strips: at 128 registers a thread, eight blocks of two warps per
+// SM wait at their own per-row barriers (256 columns, two blocks of eight
+// warps: 0.99 against 0.93 ms per launch of the defect-correction class at
+// 4096^2, N = 8)
+#ifndef AC_OR_THREADS
+#define AC_OR_THREADS 64
+#endif
+#ifndef AC_OR_ROWS
+#define AC_OR_ROWS 16
+#endif
+constexpr int kOrRows = AC_OR_ROWS, kOrThreads = AC_OR_THREADS;
+// blocks per SM: 128 registers a thread at most
+constexpr int kOrMinBlocks = 65536 / (128 * kOrThreads);
+static_assert(kOrThreads % 32 == 0 && kOrThreads <= kBlock && kOrThreads >= 64, "outer residual block");
 
 template <int N>
 __device__ __forceinline__ void or_load_row(const double *__restrict__ u, const Geo &g, bool col, int x, int y,
@@ -754,7 +768,7 @@ __device__ __forceinline__ void or_split(const double (&t)[N], float (&h)[N], fl
 }
 
 template <int N>
-__global__ void __launch_bounds__(kOrThreads, 2) k_outer_resid_df(const double *__restrict__ u,
+__global__ void __launch_bounds__(kOrThreads, kOrMinBlocks) k_outer_resid_df(const double *__restrict__ u,
                                                                const float *__restrict__ b, Geo g,
                                                                float *__restrict__ r32, float *__restrict__ u32,
                                                                double *__restrict__ rho) {
