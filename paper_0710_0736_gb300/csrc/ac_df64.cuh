@@ -214,19 +214,22 @@ AC_HD T rcp_count(int k) {
 // The mixed form's update of one node of the binary64 phase field,
 // u <- P_G(u + delta) (Sec. 3.3's simplex projection, the FP32 correction
 // delta added in binary64):
-//  - a component the float solve put on its bound (delta_i == -float(u_i))
-//    is set to exactly 0 -- u_i + delta_i would leave the rounding residue
-//    u_i - float(u_i) -- so that exact zeros (the active set) are the same
-//    as in the FP64 form; the others are v_i = u_i + delta_i in binary64;
+//  - the float solve's obstacle is u's truncated head (f64_head: the
+//    significand cut to 24 bits, so 0 <= head <= u and u + delta >= 0 on the
+//    float solve's feasible set); a component it put on its bound
+//    (delta_i == -head(u_i)) is set to exactly 0 -- u_i + delta_i would leave
+//    the residue u_i - head(u_i) -- so that exact zeros (the active set) are
+//    the same as in the FP64 form; the others are v_i = u_i + delta_i in
+//    binary64;
 //  - Michelot's iteration on the kept components (target sum 1):
 //    theta = (sum of the kept v - 1)/|kept|, components at or below theta
 //    leave, repeat; then u_i = v_i - theta on the kept set, 0 elsewhere.
 // Binary64 arithmetic is slow on GB300, so the kept set is found by the
-// iteration on float(v), theta computed once in binary64 on that set, and
-// the set's conditions (kept v_i > theta, the others at or below it) checked
-// in float with a margin of 2^-21 (|v_i| + |theta|) + 2^-120.  Rounding to
-// float is monotone, so a float gap that large (a few float ulps; the
-// absolute term covers f64_to_f32_rn's flush below 2^-126) proves the
+// iteration on the heads of v, theta computed once in binary64 on that set,
+// and the set's conditions (kept v_i > theta, the others at or below it)
+// checked on the heads with a margin of 2^-21 (|v_i| + |theta|) + 2^-120.
+// Truncation is monotone and within 2^-23 of its argument, so a float gap
+// that large (the absolute term covers the flush below 2^-126) proves the
 // binary64 inequality with a gap far above the binary64 rounding of the
 // iteration's intermediate thetas.  Where the conditions hold, the binary64
 // iteration from the full set ends on the same set -- its theta does not
@@ -244,7 +247,7 @@ AC_HD int outer_update_node(double (&uk)[N], const float (&dk)[N], AnyOr any_or)
   unsigned keep0 = 0;
 #pragma unroll
   for (int i = 0; i < N; ++i)
-    if (!(dk[i] == -f64_to_f32_rn(uk[i]))) keep0 |= 1u << i;
+    if (!(dk[i] == -f64_head(uk[i]))) keep0 |= 1u << i;
   const unsigned any0 = any_or(keep0);
   const int cnt = popcount_hd(keep0);
   float vf[N];
@@ -253,7 +256,7 @@ AC_HD int outer_update_node(double (&uk)[N], const float (&dk)[N], AnyOr any_or)
     vf[i] = 0.f;
     if (((any0 >> i) & 1u) && ((keep0 >> i) & 1u)) {
       uk[i] += f32_to_f64(dk[i]);
-      vf[i] = f64_to_f32_rn(uk[i]);
+      vf[i] = f64_head(uk[i]);
     } else {
       uk[i] = 0.0;
     }
@@ -288,7 +291,7 @@ AC_HD int outer_update_node(double (&uk)[N], const float (&dk)[N], AnyOr any_or)
     for (int i = 0; i < N; ++i)
       if (((anyk >> i) & 1u) && ((keep >> i) & 1u)) s += uk[i];
     theta = (s - 1.0) * rcp_count<double>(popcount_hd(keep));
-    const float t32 = f64_to_f32_rn(theta);
+    const float t32 = f64_head(theta);
 #pragma unroll
     for (int i = 0; i < N; ++i)
       if ((keep0 >> i) & 1u) {

@@ -498,8 +498,9 @@ __global__ void k_rhs_df(const double *__restrict__ u, const double *__restrict_
 // b is the double-float right-hand side of k_rhs_df (N heads, N tails per
 // node).
 // k_outer_resid: r = b - S u in FP64, shifted per node by max_i r_i; stores r
-// and u rounded to float (the right-hand side and obstacle of the FP32
-// correction solve) and the natural residual max_n |P_G(u_n + z_n) - u_n|,
+// rounded to float and u's truncated head (f64_head, 0 <= head <= u: the
+// right-hand side and obstacle of the FP32 correction solve) and the natural
+// residual max_n |P_G(u_n + z_n) - u_n|,
 // z = r/S_nn, computed in FP64 as a correction by the shifted projection
 // (free set found in float, theta and the optimality conditions checked in
 // FP64).  This is the FP64 check that ac_residual reports.
@@ -544,7 +545,7 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
     for (int i = 0; i < N; ++i) {
       r[i] -= mu;
       rf[i] = (float)r[i];
-      uf[i] = f64_to_f32_rn(uk[i]);  // the rounding k_outer_update tests against
+      uf[i] = f64_head(uk[i]);  // the float obstacle: u's truncated head, which k_outer_update tests against
       z[i] = r[i] * invD;
     }
     const int64_t sl = fslot<float>(g, x, y);
@@ -575,9 +576,10 @@ __global__ void __launch_bounds__(kBlock) k_outer_resid(const double *__restrict
 // weighted sum by two-sums, the products by mul_f2.  Its error is about
 // 2^-46 of the terms' magnitudes (|b|, Mhat |u|, tau eps |u_m - u|), far
 // below the float rounding of the shifted residual it produces; the FP64
-// pipe sees one conversion per block.  Shift, float rounding and the
-// natural residual in float (accurate to a few float ulps of rho near the
-// solution, see solve_mixed) as in the FP64 kernel.
+// pipe sees one conversion per block.  Shift, float rounding of r, the
+// heads of u as the obstacle and the natural residual in float (accurate to
+// a few float ulps of rho near the solution, see solve_mixed) as in the FP64
+// kernel.
 // Each block walks kOrRows rows of a strip of kOrThreads columns (one
 // column per thread, kOrThreads - 2 output columns plus one halo column on
 // each side), so every value of u is loaded and split once (the halo columns
@@ -601,18 +603,15 @@ static_assert(kOrThreads % 32 == 0 && kOrThreads <= kBlock && kOrThreads >= 64, 
 
 template <int N>
 __device__ __forceinline__ void or_load_row(const double *__restrict__ u, const Geo &g, bool col, int x, int y,
-                                            float (&h)[N], float (&l)[N], float (&f)[N]) {
+                                            float (&h)[N], float (&l)[N]) {
   if (col && y >= 0 && y <= g.H) {
     double t[N];
     ldn<double, N>(u + ((int64_t)y * g.Wn + x) * N, t);
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      split_f64(t[i], h[i], l[i]);
-      f[i] = f64_to_f32_rn(t[i]);  // the rounding k_outer_update tests against
-    }
+    for (int i = 0; i < N; ++i) split_f64(t[i], h[i], l[i]);
   } else {
 #pragma unroll
-    for (int i = 0; i < N; ++i) h[i] = l[i] = f[i] = 0.f;
+    for (int i = 0; i < N; ++i) h[i] = l[i] = 0.f;
   }
 }
 
@@ -646,7 +645,7 @@ template <int N>
 __device__ __forceinline__ float or_node(const unsigned char *bslot, const Geo &g, int x, int y,
                                          const float (&rh_s)[N][kOrThreads], const float (&rl_s)[N][kOrThreads],
                                          int tx, const float (&ph)[N], const float (&pl)[N], const float (&uh)[N],
-                                         const float (&ul)[N], const float (&uf)[N], const float (&nh)[N],
+                                         const float (&ul)[N], const float (&nh)[N],
                                          const float (&nl)[N], float *__restrict__ r32, float *__restrict__ u32) {
   float sh[N], sl[N];
   {
@@ -704,7 +703,7 @@ __device__ __forceinline__ float or_node(const unsigned char *bslot, const Geo &
   for (int i = 0; i < N; ++i) {
     const f2 a = two_sum(rh[i], -mu);
     rf[i] = a.h + (a.l + rl[i]);
-    of[i] = uf[i];
+    of[i] = uh[i];  // the float obstacle: u's truncated head
   }
   const int64_t slot = fslot<float>(g, x, y);
   stn<float, N>(r32 + slot * N, rf);
@@ -716,7 +715,7 @@ __device__ __forceinline__ float or_node(const unsigned char *bslot, const Geo &
   float e = 0.f;
 #pragma unroll
   for (int i = 0; i < N; ++i) e = nanmax<float>(e, fabsf(zf[i]));
-  return uf[0] == uf[0] ? e : __int_as_float(0x7fc00000);
+  return uh[0] == uh[0] ? e : __int_as_float(0x7fc00000);
 }
 
 // The rows of u a thread needs next (two ahead) and the b of its next node
@@ -757,14 +756,12 @@ __device__ __forceinline__ void or_read(const unsigned char *slot, int tx, T (&v
   }
 }
 
-// Split a node's u (binary64) into heads, tails and the float rounding.
+// Split a node's u (binary64) into heads and tails; the heads (the
+// significands truncated to 24 bits) are also the inner solve's obstacle.
 template <int N>
-__device__ __forceinline__ void or_split(const double (&t)[N], float (&h)[N], float (&l)[N], float (&f)[N]) {
+__device__ __forceinline__ void or_split(const double (&t)[N], float (&h)[N], float (&l)[N]) {
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    split_f64(t[i], h[i], l[i]);
-    f[i] = f64_to_f32_rn(t[i]);  // the rounding k_outer_update tests against
-  }
+  for (int i = 0; i < N; ++i) split_f64(t[i], h[i], l[i]);
 }
 
 template <int N>
@@ -785,9 +782,9 @@ __global__ void __launch_bounds__(kOrThreads, kOrMinBlocks) k_outer_resid_df(con
   auto u_ok = [&](int y) { return col && y >= 0 && y <= g.H; };
   auto u_row = [&](int y) { return u + ((int64_t)y * g.Wn + x) * N; };
   auto b_row = [&](int y) { return b + ((int64_t)y * g.Wn + x) * 2 * N; };
-  float ph[N], pl[N], ch[N], cl[N], cf[N];
-  or_load_row<N>(u, g, col, x, y0 - 1, ph, pl, cf);
-  or_load_row<N>(u, g, col, x, y0, ch, cl, cf);
+  float ph[N], pl[N], ch[N], cl[N];
+  or_load_row<N>(u, g, col, x, y0 - 1, ph, pl);
+  or_load_row<N>(u, g, col, x, y0, ch, cl);
   // the first group: u of row y0 + 1, b of row y0
   if (u_ok(y0 + 1)) or_issue<N>(uslot(0), u_row(y0 + 1), tx);
   if (out && y0 <= g.H) or_issue<N>(bslot(0), b_row(y0), tx);
@@ -805,14 +802,14 @@ __global__ void __launch_bounds__(kOrThreads, kOrMinBlocks) k_outer_resid_df(con
     }
     cp_async_commit();
     cp_async_wait<1>();  // this iteration's group (u of row y + 1, b of row y) has landed
-    float nh[N], nl[N], nf[N];
+    float nh[N], nl[N];
     if (u_ok(y + 1)) {
       double t[N];
       or_read<N>(uslot(cur), tx, t);
-      or_split<N>(t, nh, nl, nf);
+      or_split<N>(t, nh, nl);
     } else {
 #pragma unroll
-      for (int i = 0; i < N; ++i) nh[i] = nl[i] = nf[i] = 0.f;
+      for (int i = 0; i < N; ++i) nh[i] = nl[i] = 0.f;
     }
     const int buf = k & 1;
 #pragma unroll
@@ -822,7 +819,7 @@ __global__ void __launch_bounds__(kOrThreads, kOrMinBlocks) k_outer_resid_df(con
     }
     __syncthreads();  // with two buffers, one barrier per row
     if (out)
-      e = nanmax<float>(e, or_node<N>(bslot(cur), g, x, y, s_h[buf], s_l[buf], tx, ph, pl, ch, cl, cf, nh, nl, r32,
+      e = nanmax<float>(e, or_node<N>(bslot(cur), g, x, y, s_h[buf], s_l[buf], tx, ph, pl, ch, cl, nh, nl, r32,
                                       u32));
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -830,7 +827,6 @@ __global__ void __launch_bounds__(kOrThreads, kOrMinBlocks) k_outer_resid_df(con
       pl[i] = cl[i];
       ch[i] = nh[i];
       cl[i] = nl[i];
-      cf[i] = nf[i];
     }
   }
   cp_async_wait<0>();

@@ -242,6 +242,8 @@ def test_head_is_the_truncated_significand(harness):
     a = np.abs(d)
     normal = np.isfinite(d) & (a >= 2.0**-126) & (a < 2.0**128)
     assert (head[normal].view(np.uint32) == h[normal].view(np.uint32)).all()
+    # and the numpy restatement the node-update test uses
+    assert (_head32(d[normal]).view(np.uint32) == head[normal].view(np.uint32)).all()
     assert (head[a < 2.0**-126] == 0).all()
     assert np.isnan(head[~np.isfinite(d) | (a >= 2.0**128)]).all()
     for i in np.flatnonzero(normal)[:4000]:
@@ -302,10 +304,20 @@ def _proj_simplex_sort(v):
     return np.maximum(v - c[rho] / (rho + 1), 0.0)
 
 
+def _head32(x):
+    """f64_head written with numpy: the binary64 significand cut to 24 bits
+    (exact in binary32), a signed zero below 2^-126."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    h = (x.view(np.uint64) & ~np.uint64((1 << 29) - 1)).view(np.float64).astype(np.float32)
+    tiny = np.abs(x) < 2.0**-126
+    h[tiny] = np.copysign(np.float32(0), x[tiny]).astype(np.float32)
+    return h
+
+
 def _update_cases(rng, n):
     """Records (u, delta) of the mixed form's outer update at N = 8: u on the
     simplex with exact zeros, delta float corrections, some components put on
-    their bound (delta_i = -float(u_i)); then near ties, where an updated
+    their bound (delta_i = -head(u_i), the float obstacle); then near ties, where an updated
     component lies within 1e-17 .. 1e-5 of the final threshold."""
     N = 8
     u = rng.dirichlet(np.full(N, 0.7), n)
@@ -314,7 +326,7 @@ def _update_cases(rng, n):
     u /= u.sum(1, keepdims=True)
     d = (rng.standard_normal((n, N)) * 10.0 ** rng.uniform(-6, -1, (n, 1))).astype(np.float32)
     bound = rng.random((n, N)) < 0.25
-    d[bound] = -u[bound].astype(np.float32)
+    d[bound] = -_head32(u[bound])
     # near ties: final support K, threshold t, the others just below t
     m = n // 2
     p = rng.dirichlet(np.ones(N), m)
@@ -346,7 +358,7 @@ def test_outer_update_node(harness):
     assert path[-1] == 2 and (fast[-1] == 0).all()
     # against the sort-based projection of v = u + delta over the kept
     # components (the bound ones exactly 0)
-    keep = d != -u.astype(np.float32)
+    keep = d != -_head32(u)
     v = u + d.astype(np.float64)
     worst = 0.0
     for i in range(len(u) - 1):
