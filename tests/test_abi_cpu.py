@@ -68,3 +68,57 @@ def test_oracle_is_not_linked(ac):
     import subprocess
     out = subprocess.run(["nm", "-D", ac._LIB_PATH], capture_output=True, text=True).stdout
     assert "or_" not in " ".join(l.split()[-1] for l in out.splitlines() if l.split())
+
+
+def _header_signatures():
+    """(return type, parameter types) of every ac_* declaration in include/."""
+    sigs = {}
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for ret, name, args in re.findall(r"([A-Za-z_][A-Za-z0-9_ \*]*?)\b(ac_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", txt,
+                                          flags=re.S):
+            args = " ".join(args.split())
+            params = [] if args in ("", "void") else [a.strip() for a in args.split(",")]
+            # a parameter's type: the declaration without its name
+            types = [re.sub(r"\s*\b[A-Za-z_][A-Za-z0-9_]*$", "", p) for p in params]
+            sigs[name] = (" ".join(ret.split()), types)
+    return sigs
+
+
+def _c_kind(t):
+    t = t.replace("const ", "").strip()
+    if "*" in t:
+        return "ptr"
+    return {"int": "i32", "unsigned": "u32", "int64_t": "i64", "double": "f64", "void": "void"}[t]
+
+
+def _ctypes_kind(ct):
+    if ct is None:
+        return "void"
+    if ct in (C.c_void_p, C.c_char_p) or (isinstance(ct, type) and issubclass(ct, C._Pointer)):
+        return "ptr"
+    if ct is C.c_int:
+        return "i32"
+    if ct is C.c_uint:
+        return "u32"
+    if ct in (C.c_int64, C.c_longlong):
+        return "i64"
+    if ct is C.c_double:
+        return "f64"
+    raise AssertionError(f"unexpected ctypes type {ct}")
+
+
+def test_binding_signatures_match_header(ac):
+    """The ctypes binding passes every call the arguments its declaration
+    names: the same count, and pointers, 32- and 64-bit integers and doubles
+    in the same places (a drift here would hand the library garbage)."""
+    sigs = _header_signatures()
+    assert set(sigs) == set(ac.EXPORTS)
+    for name, (ret, types) in sigs.items():
+        f = getattr(ac.lib, name)
+        got = [_ctypes_kind(t) for t in (f.argtypes or [])]
+        assert got == [_c_kind(t) for t in types], name
+        assert _ctypes_kind(f.restype) == _c_kind(ret), name
