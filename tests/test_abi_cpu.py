@@ -122,3 +122,32 @@ def test_binding_signatures_match_header(ac):
         got = [_ctypes_kind(t) for t in (f.argtypes or [])]
         assert got == [_c_kind(t) for t in types], name
         assert _ctypes_kind(f.restype) == _c_kind(ret), name
+
+
+def test_struct_layouts_match_header(ac, tmp_path):
+    """Every struct the ABI passes by pointer has the same size and field
+    offsets in the ctypes binding as in include/ac.h compiled as plain C."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"ac_params": ac.ac_params, "ac_stats": ac.ac_stats, "ac_profile": ac.ac_profile,
+               "ac_batch_stats": ac.ac_batch_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ac.h"', "int main(void) {"]
+    for s, cls in structs.items():
+        lines.append(f'  printf("{s} size %zu\\n", sizeof({s}));')
+        for f, _ in cls._fields_:
+            cf = "lambda" if f == "lambda_" else f
+            lines.append(f'  printf("{s} {f} %zu\\n", offsetof({s}, {cf}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {(a, b): int(c) for a, b, c in (l.split() for l in out if l.strip())}
+    for s, cls in structs.items():
+        assert got[(s, "size")] == C.sizeof(cls), s
+        for f, _ in cls._fields_:
+            assert got[(s, f)] == getattr(cls, f).offset, (s, f)
