@@ -151,3 +151,33 @@ def test_struct_layouts_match_header(ac, tmp_path):
         assert got[(s, "size")] == C.sizeof(cls), s
         for f, _ in cls._fields_:
             assert got[(s, f)] == getattr(cls, f).offset, (s, f)
+
+
+def test_constants_match_header(ac, tmp_path):
+    """Every AC_* constant of the binding has the header's value (status
+    codes, precisions, modes), and the profile classes are in the header's
+    order."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "ac.h")).read(), flags=re.S)
+    header = set(re.findall(r"\b(AC_[A-Z0-9_]+)\s*(?:=|,|\n|\})", txt)) - {"AC_H"}
+    header = sorted(header | set(re.findall(r"#define[ \t]+(AC_[A-Z0-9_]+)[ \t]+\S", txt)))
+    names = [n for n in header if hasattr(ac, n)]
+    assert len(names) >= 20
+    lines = ['#include <stdio.h>', '#include "ac.h"', "int main(void) {"]
+    lines += [f'  printf("{n} %lld\\n", (long long)({n}));' for n in names]
+    prof = [f"AC_PROF_{c.upper()}" for c in ac.PROF_CLASSES]
+    lines += [f'  printf("{n} %lld\\n", (long long)({n}));' for n in prof + ["AC_PROF_COUNT"]]
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "consts"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {a: int(b) for a, b in (l.split() for l in out if l.strip())}
+    for n in names:
+        assert getattr(ac, n) == got[n], n
+    assert [got[n] for n in prof] == list(range(len(prof))) and got["AC_PROF_COUNT"] == len(prof)
