@@ -84,7 +84,8 @@ typedef struct {
                           means, energy and residual r = b - S u of the defect correction in
                           double-float arithmetic (about 2^-46 of the terms: GB300 runs FP64
                           at 1/64 of its FP32 rate); the correction delta is solved by the
-                          same multigrid in FP32 with obstacle -u and the natural residual is
+                          same multigrid in FP32 with obstacle -u (u's significand truncated
+                          to 24 bits, so u + delta >= 0) and the natural residual is
                           checked in float on that residual shifted per node by its maximum;
                           the image is rounded to bfloat16 on input (ac_set_image only). */
   uint64_t seed;       /* seed of the random simplex initialisation in ac_set_image */
