@@ -89,8 +89,8 @@ typedef struct {
                           checked in float on that residual shifted per node by its maximum;
                           the image is rounded to bfloat16 on input (ac_set_image only). */
   uint64_t seed;       /* seed of the random simplex initialisation in ac_set_image */
-  int refine;          /* r in [0, 4]: solve on the pixel grid refined r times (Sec. 4.1, "at least four
-                          nodes per interface"): every pixel becomes 2^r x 2^r cells carrying the pixel's
+  int refine;          /* r in [0, 4]: solve on the pixel grid refined r times (Sec. 4.1: at least four
+                          nodes across an interface): every pixel becomes 2^r x 2^r cells carrying the pixel's
                           colour (data projection by copy, Sec. 4.2), with eps, tau, lambda still in pixel
                           units.  On cells of side 1 this is the plain step with eps' = 2^r eps,
                           tau' = 2^r tau, lambda' = 2^-r lambda (the system is the pixel-unit one times
