@@ -20,7 +20,28 @@ HARNESS = r"""
 #include "ac_df64.cuh"
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <vector>
+// records of (N doubles u, N floats delta) -> (u' by outer_update_node, its
+// path as a double, u' by the binary64-only iteration)
+template <int N>
+void update_records(const std::vector<unsigned char> &in) {
+  const size_t rec = 12 * N;
+  const size_t n = in.size() / rec;
+  for (size_t i = 0; i < n; ++i) {
+    double u[N], v[N];
+    float d[N];
+    std::memcpy(u, &in[rec * i], 8 * N);
+    std::memcpy(d, &in[rec * i + 8 * N], 4 * N);
+    std::memcpy(v, u, 8 * N);
+    auto id = [](unsigned m) { return m; };
+    const double p = ac::outer_update_node<N>(u, d, id);
+    ac::outer_update_node<N, true>(v, d, id);
+    fwrite(u, 8, N, stdout);
+    fwrite(&p, 8, 1, stdout);
+    fwrite(v, 8, N, stdout);
+  }
+}
 int main(int argc, char **argv) {
   std::vector<unsigned char> in;
   unsigned char buf[1 << 16];
@@ -53,21 +74,12 @@ int main(int argc, char **argv) {
       float o = ac::f64_head(d);
       fwrite(&o, 4, 1, stdout);
     }
-  } else if (mode == 'u') {  // (8 doubles u, 8 floats delta) -> (u', path) and the binary64-only u'
-    size_t n = in.size() / 96;
-    for (size_t i = 0; i < n; ++i) {
-      double u[8], v[8];
-      float d[8];
-      std::memcpy(u, &in[96 * i], 64);
-      std::memcpy(d, &in[96 * i + 64], 32);
-      std::memcpy(v, u, 64);
-      auto id = [](unsigned m) { return m; };
-      const int path = ac::outer_update_node<8>(u, d, id);
-      ac::outer_update_node<8, true>(v, d, id);
-      const double p = path;
-      fwrite(u, 8, 8, stdout);
-      fwrite(&p, 8, 1, stdout);
-      fwrite(v, 8, 8, stdout);
+  } else if (mode == 'u') {  // node updates, N from argv[2]
+    switch (argc > 2 ? std::atoi(argv[2]) : 8) {
+      case 2: update_records<2>(in); break;
+      case 3: update_records<3>(in); break;
+      case 5: update_records<5>(in); break;
+      default: update_records<8>(in); break;
     }
   } else if (mode == 'a') {  // float quadruples (ah, al, bh, bl) -> add_f2
     size_t n = in.size() / 16;
@@ -103,9 +115,9 @@ def harness(tmp_path_factory):
     exe = d / "h"
     subprocess.run([cxx, "-O2", "-std=c++17", "-ffp-contract=off", "-I", CSRC, str(src), "-o", str(exe)], check=True)
 
-    def run(mode, arr):
-        out = subprocess.run([str(exe), mode], input=np.ascontiguousarray(arr).tobytes(), capture_output=True,
-                             check=True).stdout
+    def run(mode, arr, *extra):
+        out = subprocess.run([str(exe), mode, *extra], input=np.ascontiguousarray(arr).tobytes(),
+                             capture_output=True, check=True).stdout
         return out
 
     return run
@@ -314,12 +326,11 @@ def _head32(x):
     return h
 
 
-def _update_cases(rng, n):
-    """Records (u, delta) of the mixed form's outer update at N = 8: u on the
+def _update_cases(rng, n, N):
+    """Records (u, delta) of the mixed form's outer update: u on the
     simplex with exact zeros, delta float corrections, some components put on
     their bound (delta_i = -head(u_i), the float obstacle); then near ties, where an updated
     component lies within 1e-17 .. 1e-5 of the final threshold."""
-    N = 8
     u = rng.dirichlet(np.full(N, 0.7), n)
     u[rng.random((n, N)) < 0.3] = 0.0
     u[np.arange(n), rng.integers(0, N, n)] += 0.05
@@ -343,17 +354,21 @@ def _update_cases(rng, n):
     return u, d
 
 
-def test_outer_update_node(harness):
-    rng = np.random.default_rng(11)
-    u, d = _update_cases(rng, 40000)
-    rec = np.concatenate([u.view(np.uint8).reshape(len(u), 64), d.view(np.uint8).reshape(len(d), 32)], axis=1)
-    out = np.frombuffer(harness("u", rec), dtype=np.float64).reshape(-1, 17)
-    fast, path, plain = out[:, :8], out[:, 8], out[:, 9:]
+@pytest.mark.parametrize("N,n", [(8, 40000), (5, 20000), (3, 20000), (2, 20000)])
+def test_outer_update_node(harness, N, n):
+    rng = np.random.default_rng(11 + N)
+    u, d = _update_cases(rng, n, N)
+    rec = np.concatenate([u.view(np.uint8).reshape(len(u), 8 * N), d.view(np.uint8).reshape(len(d), 4 * N)], axis=1)
+    out = np.frombuffer(harness("u", rec, str(N)), dtype=np.float64).reshape(-1, 2 * N + 1)
+    fast, path, plain = out[:, :N], out[:, N], out[:, N + 1:]
     # bit-identical to the binary64 iteration, whichever path ran
     assert (fast.view(np.uint64) == plain.view(np.uint64)).all()
-    # the float set is accepted at all but near-tie nodes; the near ties take both paths
-    assert (path[:40000] == 0).mean() > 0.99
-    assert (path[40000:-2] == 0).sum() > 1000 and (path[40000:-2] == 1).sum() > 1000
+    # the float set is accepted at all but near-tie nodes (rows with every
+    # component on its bound take path 2); the near ties take both paths
+    live = path[:n] != 2
+    assert (path[:n][live] == 0).mean() > 0.99
+    assert (fast[:n][~live] == 0).all()
+    assert (path[n:-2] == 0).sum() > n // 40 and (path[n:-2] == 1).sum() > n // 40
     # the all-bound record: no kept component, u zeroed for the caller's projection
     assert path[-1] == 2 and (fast[-1] == 0).all()
     # against the sort-based projection of v = u + delta over the kept
@@ -364,7 +379,7 @@ def test_outer_update_node(harness):
     for i in range(len(u) - 1):
         if not keep[i].any():
             continue
-        x = np.zeros(8)
+        x = np.zeros(N)
         x[keep[i]] = _proj_simplex_sort(v[i][keep[i]])
         worst = max(worst, np.abs(x - fast[i]).max())
         assert (fast[i][~keep[i]] == 0).all() and (fast[i] >= 0).all()
